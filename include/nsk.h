@@ -1,0 +1,150 @@
+/*
+ * nsk.h -- C ABI of libnsk.so, a GB300 (sm_103a) implementation of the explicit
+ * discontinuous Galerkin spectral element (DGSEM) residual and the low-storage
+ * fourth-order Runge-Kutta update of the isothermal parabolic relaxation model
+ * ("relaxation model II") of the Navier-Stokes-Korteweg equations
+ * (Hitz, Keim, Munz, Rohde, arXiv:1912.12059).
+ *
+ * The model (Sec. 2.3, Eqs. (fluxform), (modified_pressure), (fluxes_sources_model2)):
+ *   U = (rho, rho v, c),  U_t + div(F^c(U) - F^v(grad w)) = S(U, grad c),
+ *   F^c_k = (rho v_k, rho v_k v + p_alpha e_k, 0),  p_alpha = p(rho) + alpha rho^2 / 2,
+ *   F^v_k = (0, tau_{.k}, (kappa/beta) c_{x_k}),  tau = mu (grad v + grad v^T - 2/3 div v I),
+ *   S = (0, alpha rho grad c, (alpha/beta)(rho - c)),
+ *   p(rho) = 8 T rho / (3 - rho) - 3 rho^2 (Van-der-Waals, Sec. 2.1, Eqs. (vdw_p), (vdw_parameters)).
+ * Here kappa = eps^2 gamma (the paper's capillarity) and mu = eps = 1/Re.
+ *
+ * Discretisation (Sec. 3.1): uniform Cartesian periodic box, tensor-product
+ * Lagrange basis of degree N on Gauss-Legendre nodes (Gauss-Lobatto optional),
+ * collocated weak form, BR1 lifting of the primitive variables (v, c) with the
+ * central flux, local Lax-Friedrichs (Rusanov) convective face flux with the
+ * model II wave speed |v.n| + sqrt(p_alpha'(rho)) (Eq. parabolic_eigenvalues_model2),
+ * BR1 mean viscous face flux, pointwise sources with the lifted gradient of c,
+ * and the five-stage fourth-order low-storage Runge-Kutta scheme of Carpenter
+ * and Kennedy (the 2N-storage family cited in Sec. 3.1).
+ *
+ * Layout of every state array at this boundary (FP64 in all precisions):
+ * structure of arrays, variable-major [nvar][E][npe], nvar = dim + 2 with
+ * variables (rho, rho v_1 .. rho v_dim, c); elements lexicographic with x
+ * fastest (e = ex + nx (ey + ny ez)); nodes within an element lexicographic
+ * with the x index fastest (n = i + np (j + np k)), np = N + 1, npe = np^dim.
+ * Lifted gradients: [dim*(dim+1)][E][npe], component k*(dim+1) + w is
+ * d/dx_k of w, w = 0..dim-1 the velocity components and w = dim the variable c.
+ *
+ * Ownership: the library allocates and owns all device memory of a context.
+ * Pointers passed in are borrowed for the duration of the call only. With
+ * where = NSK_HOST the pointer is host memory (pageable or pinned); with
+ * where = NSK_DEVICE it is device memory of the context's device, accessed in
+ * order on the context's stream.
+ *
+ * Errors: every call returns NSK_OK (0) or a negative code; no call aborts,
+ * traps or waits without bound. Device-side checks (density outside (0, 3),
+ * a negative p_alpha', NaN) set an error word that the library reads back at
+ * the end of each call and reports as NSK_ERR_NONPHYSICAL.
+ *
+ * Call order: nsk_init_mesh -> nsk_set_params -> nsk_set_state -> any of
+ * (nsk_rhs, nsk_lift, nsk_step, nsk_compute_dt, nsk_diagnostics, nsk_get_state);
+ * violations return NSK_ERR_STATE. A context is not thread-safe.
+ */
+#ifndef NSK_H
+#define NSK_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct nsk_ctx nsk_ctx;
+
+enum {
+  NSK_OK = 0,
+  NSK_ERR_ARG = -1,          /* invalid argument */
+  NSK_ERR_CUDA = -2,         /* a CUDA runtime call failed */
+  NSK_ERR_NONPHYSICAL = -3,  /* rho <= 0, rho >= 3, p_alpha' < 0 or NaN met on the device */
+  NSK_ERR_TIMEOUT = -4,      /* a bounded device-side wait expired */
+  NSK_ERR_STATE = -5,        /* call order violated */
+  NSK_ERR_NOMEM = -6         /* device allocation failed */
+};
+
+enum { NSK_NODES_GAUSS = 0, NSK_NODES_GAUSS_LOBATTO = 1 };
+enum { NSK_FP64 = 0, NSK_FP32_MIXED = 1 };
+enum { NSK_HOST = 0, NSK_DEVICE = 1 };
+
+/* Create a context for a periodic box [lo, hi] (per direction) split into
+ * nelem[k] equal elements per direction k < dim (entries k >= dim ignored),
+ * polynomial degree N (1 <= N <= 5), node set node_type (NSK_NODES_*),
+ * arithmetic precision (NSK_FP64; NSK_FP32_MIXED computes the DG operator in
+ * FP32 with the equation of state, wave speeds, time step and sums in FP64),
+ * on the CUDA stream `cuda_stream` (a cudaStream_t; NULL = the legacy default
+ * stream) of the current device. Discretisation: Sec. 3.1, Eqs.
+ * (numerics_solutionpolynomial)-(numerics_polynomialsbasis). */
+int nsk_init_mesh(nsk_ctx** out, int dim, const int nelem[3], const double lo[3], const double hi[3], int N,
+                  int node_type, int precision, void* cuda_stream);
+
+/* Model parameters of Sec. 2.3: temperature T, kappa = eps^2 gamma (c diffusion),
+ * Korteweg parameter alpha, relaxation parameter beta, viscosity mu = eps.
+ * Rejects (NSK_ERR_ARG) T outside (0, 1), kappa <= 0, beta <= 0, mu < 0 and
+ * alpha <= alpha_*(T) = |min W''| / 2 on the spinodal interval
+ * (Eq. alpha_fullyhyperbolic_limit), below which the model II fluxes lose
+ * hyperbolicity. */
+int nsk_set_params(nsk_ctx* ctx, double T, double kappa, double alpha, double beta, double mu);
+
+/* Optional switch: 1 applies the Lax-Friedrichs jump term to c as well
+ * (default 0: c has no convective flux, Eq. fluxes_sources_model2, so its face
+ * flux is the BR1 viscous mean only). */
+int nsk_set_c_dissipation(nsk_ctx* ctx, int on);
+
+/* Copy the state in (set) or out (get); layout above, FP64. Setting the state
+ * also clears the Runge-Kutta register. */
+int nsk_set_state(nsk_ctx* ctx, const double* U, int where);
+int nsk_get_state(nsk_ctx* ctx, double* U, int where);
+
+/* Physical coordinates of all nodes, [dim][E][npe], FP64. */
+int nsk_node_coords(nsk_ctx* ctx, double* x, int where);
+
+/* Semi-discrete residual R = dU/dt of the current state (Eq. weakformulation
+ * with the fluxes and sources of Eq. fluxes_sources_model2), layout of U.
+ * t is the model time; the model is autonomous, so R does not depend on it. */
+int nsk_rhs(nsk_ctx* ctx, double t, double* Ut, int where);
+
+/* BR1-lifted gradients of the primitive variables (Sec. 3.1, lifting with the
+ * central flux), layout [dim*(dim+1)][E][npe]. */
+int nsk_lift(nsk_ctx* ctx, double* Q, int where);
+
+/* Admissible explicit time step for Courant number cfl: the minimum of the
+ * convective bound cfl / ((2N+1) max sum_k (|v_k| + sqrt(p_alpha'))/h_k), the
+ * parabolic bound of Eq. (numerics_dfl) cfl / ((2N+1)^2 lambda_v sum_k h_k^-2)
+ * with lambda_v = max(mu, kappa/beta) (Eq. numerics_nsk_visc_eigenvalues), and
+ * the relaxation-source bound cfl * 4.6 * beta / alpha. Reduced in FP64. */
+int nsk_compute_dt(nsk_ctx* ctx, double cfl, double* dt_out);
+
+/* Advance the state by nsteps steps of the five-stage low-storage RK4 with
+ * step dt (dt > 0), or, with dt <= 0, with nsk_compute_dt(ctx, -dt) recomputed
+ * before every step (so dt = -0.5 means CFL 0.5). Returns after the work is
+ * queued and checked: the call synchronises the stream once at the end to
+ * read the error word. */
+int nsk_step(nsk_ctx* ctx, double dt, int nsteps);
+
+/* Quadrature sums (FP64): mass sum w J rho; the total energy of the relaxation
+ * model sum w J (|m|^2/(2 rho) + W(rho) + alpha/2 (rho-c)^2 + kappa/2 |grad c|^2)
+ * (Eq. pararelax_elliptical_energy_dynamic, grad c from BR1); and
+ * ||rho - c||_L2. Any output pointer may be NULL. */
+int nsk_diagnostics(nsk_ctx* ctx, double* mass, double* energy, double* l2_rho_minus_c);
+
+/* Sizes of the context: number of elements, nodes per element, variables. */
+int nsk_get_sizes(nsk_ctx* ctx, long long* n_elem, int* nodes_per_elem, int* nvar);
+
+/* Kernel launches issued by this context since creation (a counter kept on
+ * the host; every launch of the library's own kernels increments it). */
+long long nsk_launch_count(nsk_ctx* ctx);
+
+/* Human-readable text of an error code; never NULL. */
+const char* nsk_error_string(int code);
+
+/* Free all resources of a context (NULL is a no-op). */
+void nsk_destroy(nsk_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NSK_H */

@@ -1,0 +1,660 @@
+/*
+ * nsk_oracle.c -- TEST INFRASTRUCTURE ONLY: plain FP64 CPU reference of the
+ * DGSEM discretisation of relaxation model II (arXiv:1912.12059).
+ *
+ * Written for a reader checking it against the paper by eye: element by
+ * element, face by face, line by line, with the weak form of Sec. 3.1
+ * (Eq. weakformulation) evaluated by Gauss quadrature, no tensor-product
+ * tricks, no fusion. Build with -ffp-contract=off.
+ *
+ * Only the test suite, the package's smoke check and the benchmark's CPU
+ * baseline may use this file. It shares no code with the CUDA library.
+ */
+#include "nsk_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_MAXNP 16
+#define ORC_OK 0
+#define ORC_ERR_ARG (-1)
+#define ORC_ERR_NONPHYSICAL (-3)
+#define ORC_ERR_NOCONV (-6)
+
+/* ------------------------------------------------------------------------ */
+/* Van-der-Waals thermodynamics, Sec. 2.1                                    */
+/* ------------------------------------------------------------------------ */
+
+/* Reduced VdW parameters, Eq. (vdw_parameters): a = 3, b = 1/3, R = 8/3. */
+static const double VDW_A = 3.0;
+static const double VDW_B = 1.0 / 3.0;
+static const double VDW_R = 8.0 / 3.0;
+
+/* Eq. (vdw_freeenergy): W = rho R T ln(rho / (1 - b rho)) - a rho^2. */
+double orc_free_energy(double T, double rho) {
+  return rho * VDW_R * T * log(rho / (1.0 - VDW_B * rho)) - VDW_A * rho * rho;
+}
+
+/* Eq. (vdw_p): p = rho R T / (1 - b rho) - a rho^2. */
+double orc_pressure(double T, double rho) {
+  return rho * VDW_R * T / (1.0 - VDW_B * rho) - VDW_A * rho * rho;
+}
+
+/* dp/drho = R T / (1 - b rho)^2 - 2 a rho (derivative of Eq. vdw_p). */
+double orc_dpressure(double T, double rho) {
+  double q = 1.0 - VDW_B * rho;
+  return VDW_R * T / (q * q) - 2.0 * VDW_A * rho;
+}
+
+/* Chemical potential W'(rho) = (W + p) / rho, from Eq. (vdw_p_as_derivative). */
+double orc_chem_potential(double T, double rho) {
+  return (orc_free_energy(T, rho) + orc_pressure(T, rho)) / rho;
+}
+
+/* W''(rho) = p'(rho) / rho (Sec. 2.1, p' = rho W''). */
+static double second_deriv_W(double T, double rho) { return orc_dpressure(T, rho) / rho; }
+
+/* Saturated states (Sec. 2.1): equal pressure and equal chemical potential,
+ * solved by Newton's method in the two unknowns (rho_vap, rho_liq). */
+int orc_maxwell(double T, double* rho_vap, double* rho_liq, double* p_sat) {
+  double v = 0.3, l = 1.8;
+  for (int it = 0; it < 200; ++it) {
+    double F1 = orc_pressure(T, l) - orc_pressure(T, v);
+    double F2 = orc_chem_potential(T, l) - orc_chem_potential(T, v);
+    double J11 = -orc_dpressure(T, v), J12 = orc_dpressure(T, l);
+    double J21 = -second_deriv_W(T, v), J22 = second_deriv_W(T, l);
+    double det = J11 * J22 - J12 * J21;
+    if (det == 0.0 || !isfinite(det)) return ORC_ERR_NOCONV;
+    double dv = (F1 * J22 - F2 * J12) / det;
+    double dl = (J11 * F2 - J21 * F1) / det;
+    v -= dv;
+    l -= dl;
+    if (fabs(dv) < 1e-15 && fabs(dl) < 1e-15) break;
+  }
+  if (!(v > 0.0 && l > v && l < 1.0 / VDW_B)) return ORC_ERR_NOCONV;
+  *rho_vap = v;
+  *rho_liq = l;
+  if (p_sat) *p_sat = orc_pressure(T, v);
+  return ORC_OK;
+}
+
+/* Spinodal densities: the two roots of p'(rho) = 0 on (0, 1/b), by bisection.
+ * alpha_* = |min W''| / 2 on (rho_sv, rho_sl), Eq. (alpha_fullyhyperbolic_limit),
+ * the minimum located by golden-section search. */
+int orc_spinodal(double T, double* rho_sv, double* rho_sl, double* alpha_star) {
+  /* p' > 0 near rho = 0 and near rho = 1/b; p' < 0 in between for T below critical.
+   * The reduced critical density is 1, so one root lies in (0,1), the other in (1,3). */
+  if (!(orc_dpressure(T, 1.0) < 0.0)) return ORC_ERR_ARG;
+  double a = 1e-9, b = 1.0;
+  for (int it = 0; it < 200; ++it) {
+    double m = 0.5 * (a + b);
+    if (orc_dpressure(T, m) > 0.0) a = m; else b = m;
+  }
+  double sv = 0.5 * (a + b);
+  a = 1.0;
+  b = 1.0 / VDW_B - 1e-9;
+  for (int it = 0; it < 200; ++it) {
+    double m = 0.5 * (a + b);
+    if (orc_dpressure(T, m) < 0.0) a = m; else b = m;
+  }
+  double sl = 0.5 * (a + b);
+  const double g = 0.5 * (sqrt(5.0) - 1.0);
+  double x0 = sv, x1 = sl;
+  for (int it = 0; it < 300; ++it) {
+    double c = x1 - g * (x1 - x0), d = x0 + g * (x1 - x0);
+    if (second_deriv_W(T, c) < second_deriv_W(T, d)) x1 = d; else x0 = c;
+  }
+  *rho_sv = sv;
+  *rho_sl = sl;
+  *alpha_star = fabs(second_deriv_W(T, 0.5 * (x0 + x1))) / 2.0;
+  return ORC_OK;
+}
+
+/* Sec. 4.3, Eq. (hoc_initialpressures): Young-Laplace pressures of the liquid and
+ * vapour phases of a spherical droplet, then the densities on the liquid and vapour
+ * branches of the isotherm with those pressures (Newton from the saturated states). */
+int orc_young_laplace(double T, double sigma, double r, double* rho_liq, double* rho_vap) {
+  double rv, rl, ps;
+  int st = orc_maxwell(T, &rv, &rl, &ps);
+  if (st) return st;
+  double pl = ps + rl / (rl - rv) * 2.0 * sigma / r;
+  double pv = ps + rv / (rl - rv) * 2.0 * sigma / r;
+  double x = rl, y = rv;
+  for (int it = 0; it < 100; ++it) x -= (orc_pressure(T, x) - pl) / orc_dpressure(T, x);
+  for (int it = 0; it < 100; ++it) y -= (orc_pressure(T, y) - pv) / orc_dpressure(T, y);
+  *rho_liq = x;
+  *rho_vap = y;
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Nodal basis, Sec. 3.1, Eqs. (solutionpolynomial)-(polynomialsbasis)        */
+/* ------------------------------------------------------------------------ */
+
+/* Legendre polynomial P_n(x) and its derivative, by the three-term recurrence. */
+static void legendre(int n, double x, double* P, double* dP) {
+  double p0 = 1.0, p1 = x;
+  if (n == 0) { *P = 1.0; *dP = 0.0; return; }
+  for (int k = 1; k < n; ++k) {
+    double p2 = ((2.0 * k + 1.0) * x * p1 - k * p0) / (k + 1.0);
+    p0 = p1;
+    p1 = p2;
+  }
+  *P = p1;
+  /* P_n' = n (x P_n - P_{n-1}) / (x^2 - 1), valid away from x = +-1. */
+  *dP = n * (x * p1 - p0) / (x * x - 1.0);
+}
+
+/* Gauss-Legendre nodes are the roots of P_{N+1}, weights 2 / ((1 - x^2) P'_{N+1}(x)^2).
+ * Gauss-Lobatto nodes are +-1 and the roots of P'_N, weights 2 / (N (N+1) P_N(x)^2).
+ * Both found by Newton's method from Chebyshev-type guesses; output ascending. */
+int orc_nodes(int N, int node_type, double* xi, double* w) {
+  if (N < 1 || N >= ORC_MAXNP) return ORC_ERR_ARG;
+  const double pi = 3.14159265358979323846;
+  int n = N + 1;
+  if (node_type == 0) {
+    for (int i = 0; i < n; ++i) {
+      double x = -cos(pi * (i + 0.75) / (n + 0.5));
+      for (int it = 0; it < 100; ++it) {
+        double P, dP;
+        legendre(n, x, &P, &dP);
+        double dx = P / dP;
+        x -= dx;
+        if (fabs(dx) < 1e-16) break;
+      }
+      double P, dP;
+      legendre(n, x, &P, &dP);
+      xi[i] = x;
+      w[i] = 2.0 / ((1.0 - x * x) * dP * dP);
+    }
+  } else if (node_type == 1) {
+    xi[0] = -1.0;
+    xi[N] = 1.0;
+    for (int i = 1; i < N; ++i) {
+      double x = -cos(pi * i / N);
+      for (int it = 0; it < 100; ++it) {
+        double P, dP;
+        legendre(N, x, &P, &dP);
+        /* Legendre's equation: (1 - x^2) P'' = 2 x P' - N (N+1) P. */
+        double d2P = (2.0 * x * dP - N * (N + 1.0) * P) / (1.0 - x * x);
+        double dx = dP / d2P;
+        x -= dx;
+        if (fabs(dx) < 1e-16) break;
+      }
+      xi[i] = x;
+    }
+    for (int i = 0; i <= N; ++i) {
+      double P, dP;
+      if (i == 0 || i == N) {
+        P = (i == 0 && (N % 2)) ? -1.0 : 1.0; /* P_N(+-1) = (+-1)^N */
+      } else {
+        legendre(N, xi[i], &P, &dP);
+      }
+      w[i] = 2.0 / (N * (N + 1.0) * P * P);
+    }
+  } else {
+    return ORC_ERR_ARG;
+  }
+  /* ascending order (the guesses already are; sort defensively) */
+  for (int i = 1; i < n; ++i)
+    for (int j = i; j > 0 && xi[j] < xi[j - 1]; --j) {
+      double t = xi[j]; xi[j] = xi[j - 1]; xi[j - 1] = t;
+      t = w[j]; w[j] = w[j - 1]; w[j - 1] = t;
+    }
+  return ORC_OK;
+}
+
+/* Lagrange polynomial l_j(x) = prod_{m != j} (x - xi_m) / (xi_j - xi_m), Eq. (polynomialsbasis). */
+double orc_lagrange_eval(int N, const double* xi, int j, double x) {
+  double l = 1.0;
+  for (int m = 0; m <= N; ++m)
+    if (m != j) l *= (x - xi[m]) / (xi[j] - xi[m]);
+  return l;
+}
+
+/* l_j'(x) by the product rule applied to the product above. */
+static double lagrange_deriv(int N, const double* xi, int j, double x) {
+  double s = 0.0;
+  for (int k = 0; k <= N; ++k) {
+    if (k == j) continue;
+    double t = 1.0 / (xi[j] - xi[k]);
+    for (int m = 0; m <= N; ++m)
+      if (m != j && m != k) t *= (x - xi[m]) / (xi[j] - xi[m]);
+    s += t;
+  }
+  return s;
+}
+
+void orc_lagrange_tables(int N, const double* xi, double* D, double* Lm, double* Lp) {
+  for (int i = 0; i <= N; ++i)
+    for (int j = 0; j <= N; ++j) D[i * (N + 1) + j] = lagrange_deriv(N, xi, j, xi[i]);
+  for (int j = 0; j <= N; ++j) {
+    Lm[j] = orc_lagrange_eval(N, xi, j, -1.0);
+    Lp[j] = orc_lagrange_eval(N, xi, j, 1.0);
+  }
+}
+
+/* Carpenter & Kennedy (1994) fourth-order, five-stage, 2N-storage RK, the
+ * low-storage family the paper cites in Sec. 3.1. */
+void orc_lsrk4_coeffs(double* A, double* B, double* C) {
+  A[0] = 0.0;
+  A[1] = -567301805773.0 / 1357537059087.0;
+  A[2] = -2404267990393.0 / 2016746695238.0;
+  A[3] = -3550918686646.0 / 2091501179385.0;
+  A[4] = -1275806237668.0 / 842570457699.0;
+  B[0] = 1432997174477.0 / 9575080441755.0;
+  B[1] = 5161836677717.0 / 13612068292357.0;
+  B[2] = 1720146321549.0 / 2090206949498.0;
+  B[3] = 3134564353537.0 / 4481467310338.0;
+  B[4] = 2277821191437.0 / 14882151754819.0;
+  C[0] = 0.0;
+  C[1] = 1432997174477.0 / 9575080441755.0;
+  C[2] = 2526269341429.0 / 6820363962896.0;
+  C[3] = 2006345519317.0 / 3224310063776.0;
+  C[4] = 2802321613138.0 / 2924317926251.0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Mesh: uniform Cartesian periodic box, affine element maps (Sec. 3.1 with   */
+/* J a^k = J (2/h_k) e_k, J = prod h_k / 2).                                 */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+  int d, np, npe, nvar, nq;
+  long E;
+  int ne[3];
+  long se[3]; /* element strides */
+  int sn[3];  /* node strides */
+  double h[3];
+  double xi[ORC_MAXNP], w[ORC_MAXNP], D[ORC_MAXNP * ORC_MAXNP], Lm[ORC_MAXNP], Lp[ORC_MAXNP];
+} mesh_t;
+
+static int make_mesh(const orc_setup* s, mesh_t* m) {
+  if (s->dim < 1 || s->dim > 3) return ORC_ERR_ARG;
+  if (s->N < 1 || s->N >= ORC_MAXNP) return ORC_ERR_ARG;
+  memset(m, 0, sizeof(*m));
+  m->d = s->dim;
+  m->np = s->N + 1;
+  m->nvar = s->dim + 2;
+  m->nq = s->dim * (s->dim + 1);
+  m->npe = 1;
+  m->E = 1;
+  for (int k = 0; k < 3; ++k) {
+    if (k < s->dim) {
+      if (s->nelem[k] < 1 || !(s->hi[k] > s->lo[k])) return ORC_ERR_ARG;
+      m->ne[k] = s->nelem[k];
+      m->h[k] = (s->hi[k] - s->lo[k]) / s->nelem[k];
+    } else {
+      m->ne[k] = 1;
+      m->h[k] = 1.0;
+    }
+  }
+  m->se[0] = 1;
+  m->se[1] = m->ne[0];
+  m->se[2] = (long)m->ne[0] * m->ne[1];
+  m->E = (long)m->ne[0] * m->ne[1] * m->ne[2];
+  for (int k = 0; k < 3; ++k) {
+    m->sn[k] = m->npe;
+    if (k < s->dim) m->npe *= m->np;
+  }
+  if (orc_nodes(s->N, s->node_type, m->xi, m->w)) return ORC_ERR_ARG;
+  orc_lagrange_tables(s->N, m->xi, m->D, m->Lm, m->Lp);
+  return ORC_OK;
+}
+
+/* neighbour of element e in direction k on side dir (-1 or +1), periodic */
+static long neighbour(const mesh_t* m, long e, int k, int dir) {
+  int c = (int)((e / m->se[k]) % m->ne[k]);
+  int cn = (c + dir + m->ne[k]) % m->ne[k];
+  return e + (long)(cn - c) * m->se[k];
+}
+
+/* index of node n along direction k: i_k */
+static int node_coord(const mesh_t* m, int n, int k) { return (n / m->sn[k]) % m->np; }
+
+/* value of the element polynomial of a nodal field f (one variable, [E][npe])
+ * at the face xi_k = side (-1 or +1), at the face node whose line in direction k
+ * starts at base node n0: sum_j l_j(side) f_j. */
+static double trace(const mesh_t* m, const double* f, long e, int k, int n0, int side) {
+  const double* L = side < 0 ? m->Lm : m->Lp;
+  double s = 0.0;
+  for (int j = 0; j < m->np; ++j) s += L[j] * f[e * m->npe + n0 + j * m->sn[k]];
+  return s;
+}
+
+static int admissible(double rho) { return rho > 0.0 && rho < 1.0 / VDW_B && isfinite(rho); }
+
+/* primitive variables w = (v_1..v_d, c) of a conservative state U = (rho, m, c) */
+static void cons_to_prim(int d, const double* U, double* w) {
+  for (int a = 0; a < d; ++a) w[a] = U[1 + a] / U[0];
+  w[d] = U[d + 1];
+}
+
+/* ------------------------------------------------------------------------ */
+/* Model II fluxes, Eq. (fluxes_sources_model2)                               */
+/* ------------------------------------------------------------------------ */
+
+/* modified pressure p_alpha = p + alpha rho^2 / 2, Eq. (modified_pressure) */
+static double p_alpha(const orc_setup* s, double rho) {
+  return orc_pressure(s->T, rho) + s->alpha * rho * rho / 2.0;
+}
+
+/* sqrt(p_alpha'(rho)), the acoustic speed of Eq. (parabolic_eigenvalues_model2) */
+static double sound_speed(const orc_setup* s, double rho) {
+  return sqrt(orc_dpressure(s->T, rho) + s->alpha * rho);
+}
+
+/* convective flux in direction k: (rho v_k, rho v_k v + p_alpha e_k, 0) */
+static void conv_flux(const orc_setup* s, int d, int k, const double* U, double* f) {
+  double rho = U[0];
+  f[0] = U[1 + k];
+  for (int a = 0; a < d; ++a) f[1 + a] = U[1 + k] * (U[1 + a] / rho);
+  f[1 + k] += p_alpha(s, rho);
+  f[d + 1] = 0.0;
+}
+
+/* viscous flux in direction k: (0, tau_{.k}, (kappa/beta) c_{x_k}),
+ * tau = mu (grad v + grad v^T - 2/3 div v I), Eq. (stress_nse).
+ * Q[k*(d+1) + a] = d v_a / d x_k, Q[k*(d+1) + d] = d c / d x_k. */
+static void visc_flux(const orc_setup* s, int d, int k, const double* Q, double* f) {
+  double div = 0.0;
+  for (int a = 0; a < d; ++a) div += Q[a * (d + 1) + a];
+  f[0] = 0.0;
+  for (int a = 0; a < d; ++a) {
+    double t = Q[k * (d + 1) + a] + Q[a * (d + 1) + k];
+    if (a == k) t -= 2.0 / 3.0 * div;
+    f[1 + a] = s->mu * t;
+  }
+  f[d + 1] = s->kappa / s->beta * Q[k * (d + 1) + d];
+}
+
+/* ------------------------------------------------------------------------ */
+/* BR1 lifting, Sec. 3.1: Q - (1/J) div_xi (J a^k w) = 0 in weak form with the */
+/* central flux w* = (w^- + w^+)/2, w = primitive variables (v, c).           */
+/* ------------------------------------------------------------------------ */
+
+static int lift(const orc_setup* s, const mesh_t* m, const double* U, double* Q) {
+  const int d = m->d, np = m->np, npe = m->npe, nw = d + 1;
+  const long E = m->E, nn = E * npe;
+  double* W = (double*)malloc(sizeof(double) * nw * nn);
+  if (!W) return ORC_ERR_ARG;
+  int status = ORC_OK;
+  /* primitive variables at the volume nodes */
+  for (long e = 0; e < E; ++e)
+    for (int n = 0; n < npe; ++n) {
+      double Un[5], wn[4];
+      for (int v = 0; v < m->nvar; ++v) Un[v] = U[v * nn + e * npe + n];
+      if (!admissible(Un[0])) status = ORC_ERR_NONPHYSICAL;
+      cons_to_prim(d, Un, wn);
+      for (int q = 0; q < nw; ++q) W[q * nn + e * npe + n] = wn[q];
+    }
+  for (long e = 0; e < E; ++e) {
+    for (int k = 0; k < d; ++k) {
+      const long eL = neighbour(m, e, k, -1), eR = neighbour(m, e, k, +1);
+      for (int n0 = 0; n0 < npe; ++n0) {
+        if (node_coord(m, n0, k) != 0) continue; /* one line per base node */
+        /* conservative traces on both sides of both faces of this line */
+        double Um[5], Up[5], UnbM[5], UnbP[5];
+        for (int v = 0; v < m->nvar; ++v) {
+          const double* f = U + v * nn;
+          Um[v] = trace(m, f, e, k, n0, -1);
+          Up[v] = trace(m, f, e, k, n0, +1);
+          UnbM[v] = trace(m, f, eL, k, n0, +1); /* left neighbour's +1 face */
+          UnbP[v] = trace(m, f, eR, k, n0, -1); /* right neighbour's -1 face */
+        }
+        if (!admissible(Um[0]) || !admissible(Up[0]) || !admissible(UnbM[0]) || !admissible(UnbP[0]))
+          status = ORC_ERR_NONPHYSICAL;
+        double wm[4], wp[4], wnm[4], wnp[4], wsm[4], wsp[4];
+        cons_to_prim(d, Um, wm);
+        cons_to_prim(d, Up, wp);
+        cons_to_prim(d, UnbM, wnm);
+        cons_to_prim(d, UnbP, wnp);
+        for (int q = 0; q < nw; ++q) {
+          wsm[q] = 0.5 * (wm[q] + wnm[q]);
+          wsp[q] = 0.5 * (wp[q] + wnp[q]);
+        }
+        for (int i = 0; i < np; ++i) {
+          const int node = n0 + i * m->sn[k];
+          for (int q = 0; q < nw; ++q) {
+            const double* f = W + q * nn + e * npe;
+            /* volume term: - sum_j w_j w_q(xi_j) l_i'(xi_j) / w_i */
+            double vol = 0.0;
+            for (int j = 0; j < np; ++j) vol += m->w[j] * f[n0 + j * m->sn[k]] * m->D[j * np + i];
+            vol /= m->w[i];
+            /* surface term: (w*_+ l_i(1) - w*_- l_i(-1)) / w_i */
+            double surf = (wsp[q] * m->Lp[i] - wsm[q] * m->Lm[i]) / m->w[i];
+            Q[(long)(k * nw + q) * nn + e * npe + node] = (2.0 / m->h[k]) * (surf - vol);
+          }
+        }
+      }
+    }
+  }
+  free(W);
+  return status;
+}
+
+int orc_lift(const orc_setup* s, const double* U, double* Q) {
+  mesh_t m;
+  int st = make_mesh(s, &m);
+  if (st) return st;
+  return lift(s, &m, U, Q);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Residual, Eq. (weakformulation):                                          */
+/*   R_i = sum_k (2/h_k) [ sum_j (w_j/w_i) l_i'(xi_j) f_k(U_j, Q_j)          */
+/*                        - (f*_{k,+} l_i(1) - f*_{k,-} l_i(-1)) / w_i ] + S_i */
+/* with f = f^c - f^v, f* the local Lax-Friedrichs convective flux minus the  */
+/* BR1 mean of the viscous fluxes, S the model II source.                    */
+/* ------------------------------------------------------------------------ */
+
+static int residual(const orc_setup* s, const mesh_t* m, const double* U, double* R) {
+  const int d = m->d, np = m->np, npe = m->npe, nv = m->nvar, nw = d + 1, nq = m->nq;
+  const long E = m->E, nn = E * npe;
+  double* Q = (double*)malloc(sizeof(double) * nq * nn);
+  if (!Q) return ORC_ERR_ARG;
+  int status = lift(s, m, U, Q);
+  for (long i = 0; i < nv * nn; ++i) R[i] = 0.0;
+
+  /* volume integral */
+  for (long e = 0; e < E; ++e) {
+    for (int k = 0; k < d; ++k) {
+      for (int n0 = 0; n0 < npe; ++n0) {
+        if (node_coord(m, n0, k) != 0) continue;
+        double F[ORC_MAXNP][5];
+        for (int j = 0; j < np; ++j) {
+          const int node = n0 + j * m->sn[k];
+          double Un[5], Qn[12], fc[5], fv[5];
+          for (int v = 0; v < nv; ++v) Un[v] = U[v * nn + e * npe + node];
+          for (int q = 0; q < nq; ++q) Qn[q] = Q[q * nn + e * npe + node];
+          conv_flux(s, d, k, Un, fc);
+          visc_flux(s, d, k, Qn, fv);
+          for (int v = 0; v < nv; ++v) F[j][v] = fc[v] - fv[v];
+        }
+        for (int i = 0; i < np; ++i) {
+          const int node = n0 + i * m->sn[k];
+          for (int v = 0; v < nv; ++v) {
+            double vol = 0.0;
+            for (int j = 0; j < np; ++j) vol += m->w[j] * F[j][v] * m->D[j * np + i];
+            R[v * nn + e * npe + node] += (2.0 / m->h[k]) * vol / m->w[i];
+          }
+        }
+      }
+    }
+  }
+
+  /* surface integral: every face once, between element e (its +1 side) and
+   * its right neighbour eR (its -1 side), outward normal of e is +e_k. */
+  for (long e = 0; e < E; ++e) {
+    for (int k = 0; k < d; ++k) {
+      const long eR = neighbour(m, e, k, +1);
+      for (int n0 = 0; n0 < npe; ++n0) {
+        if (node_coord(m, n0, k) != 0) continue;
+        double UL[5], UR[5], QL[12], QR[12];
+        for (int v = 0; v < nv; ++v) {
+          UL[v] = trace(m, U + v * nn, e, k, n0, +1);
+          UR[v] = trace(m, U + v * nn, eR, k, n0, -1);
+        }
+        for (int q = 0; q < nq; ++q) {
+          QL[q] = trace(m, Q + q * nn, e, k, n0, +1);
+          QR[q] = trace(m, Q + q * nn, eR, k, n0, -1);
+        }
+        if (!admissible(UL[0]) || !admissible(UR[0])) {
+          status = ORC_ERR_NONPHYSICAL;
+          continue;
+        }
+        double fcL[5], fcR[5], fvL[5], fvR[5], Fs[5];
+        conv_flux(s, d, k, UL, fcL);
+        conv_flux(s, d, k, UR, fcR);
+        visc_flux(s, d, k, QL, fvL);
+        visc_flux(s, d, k, QR, fvR);
+        /* local Lax-Friedrichs: largest |lambda| of Eq. (parabolic_eigenvalues_model2) */
+        double aL = sound_speed(s, UL[0]), aR = sound_speed(s, UR[0]);
+        if (!isfinite(aL) || !isfinite(aR)) status = ORC_ERR_NONPHYSICAL;
+        double lamL = fabs(UL[1 + k] / UL[0]) + aL;
+        double lamR = fabs(UR[1 + k] / UR[0]) + aR;
+        double lam = lamL > lamR ? lamL : lamR;
+        for (int v = 0; v < nv; ++v) {
+          Fs[v] = 0.5 * (fcL[v] + fcR[v]) - 0.5 * (fvL[v] + fvR[v]);
+          int dissipative = (v < d + 1) || s->c_dissipation;
+          if (dissipative) Fs[v] -= 0.5 * lam * (UR[v] - UL[v]);
+        }
+        for (int i = 0; i < np; ++i) {
+          const int node = n0 + i * m->sn[k];
+          for (int v = 0; v < nv; ++v) {
+            /* +1 face of e: -(2/h) f* l_i(1) / w_i ; -1 face of eR: +(2/h) f* l_i(-1) / w_i */
+            R[v * nn + e * npe + node] -= (2.0 / m->h[k]) * Fs[v] * m->Lp[i] / m->w[i];
+            R[v * nn + eR * npe + node] += (2.0 / m->h[k]) * Fs[v] * m->Lm[i] / m->w[i];
+          }
+        }
+      }
+    }
+  }
+
+  /* pointwise sources (0, alpha rho grad c, (alpha/beta)(rho - c)), evaluated
+   * with the lifted gradient of c (Sec. 3.1, last paragraph) */
+  for (long e = 0; e < E; ++e)
+    for (int n = 0; n < npe; ++n) {
+      const long p = e * npe + n;
+      double rho = U[p], c = U[(d + 1) * nn + p];
+      for (int a = 0; a < d; ++a) R[(1 + a) * nn + p] += s->alpha * rho * Q[(a * nw + d) * nn + p];
+      R[(d + 1) * nn + p] += s->alpha / s->beta * (rho - c);
+    }
+  (void)nw;
+  free(Q);
+  return status;
+}
+
+int orc_rhs(const orc_setup* s, const double* U, double* R) {
+  mesh_t m;
+  int st = make_mesh(s, &m);
+  if (st) return st;
+  if (!(s->beta > 0.0) || !(s->kappa >= 0.0) || !(s->mu >= 0.0)) return ORC_ERR_ARG;
+  return residual(s, &m, U, R);
+}
+
+/* 2N-storage update: K <- A_s K + dt R(U); U <- U + B_s K, s = 1..5. */
+int orc_lsrk4(const orc_setup* s, double* U, double dt, int nsteps) {
+  mesh_t m;
+  int st = make_mesh(s, &m);
+  if (st) return st;
+  const long len = (long)m.nvar * m.E * m.npe;
+  double* K = (double*)calloc(len, sizeof(double));
+  double* R = (double*)malloc(sizeof(double) * len);
+  if (!K || !R) { free(K); free(R); return ORC_ERR_ARG; }
+  double A[5], B[5], C[5];
+  orc_lsrk4_coeffs(A, B, C);
+  for (int step = 0; step < nsteps && st == ORC_OK; ++step) {
+    for (int stage = 0; stage < 5; ++stage) {
+      st = residual(s, &m, U, R);
+      if (st) break;
+      for (long i = 0; i < len; ++i) {
+        K[i] = A[stage] * K[i] + dt * R[i];
+        U[i] = U[i] + B[stage] * K[i];
+      }
+    }
+  }
+  free(K);
+  free(R);
+  return st;
+}
+
+/* Time step. Eq. (numerics_dfl) gives only the parabolic bound; the convective
+ * bound and the bound of the stiff relaxation source are added (the paper is
+ * silent on both):
+ *   dt_conv = cfl / ((2N+1) max_nodes sum_k (|v_k| + sqrt(p_alpha')) / h_k)
+ *   dt_visc = cfl / ((2N+1)^2 lambda_v sum_k 1/h_k^2), lambda_v = max(mu, kappa/beta)
+ *             (Eq. visc_eigenvalues; beta_RK folded into cfl)
+ *   dt_src  = cfl * 4.6 * beta / alpha (4.6 just inside the real-axis stability
+ *             limit of the five-stage scheme)                                   */
+int orc_timestep(const orc_setup* s, const double* U, double cfl, double* dt) {
+  mesh_t m;
+  int st = make_mesh(s, &m);
+  if (st) return st;
+  const int d = m.d;
+  const long nn = m.E * m.npe;
+  double lam_max = 0.0;
+  for (long p = 0; p < nn; ++p) {
+    double rho = U[p];
+    if (!admissible(rho)) return ORC_ERR_NONPHYSICAL;
+    double a = sound_speed(s, rho);
+    if (!isfinite(a)) return ORC_ERR_NONPHYSICAL;
+    double sum = 0.0;
+    for (int k = 0; k < d; ++k) sum += (fabs(U[(1 + k) * nn + p] / rho) + a) / m.h[k];
+    if (sum > lam_max) lam_max = sum;
+  }
+  const double twoNp1 = 2.0 * s->N + 1.0;
+  double dt_conv = cfl / (twoNp1 * lam_max);
+  double lamv = s->mu > s->kappa / s->beta ? s->mu : s->kappa / s->beta;
+  double inv_h2 = 0.0;
+  for (int k = 0; k < d; ++k) inv_h2 += 1.0 / (m.h[k] * m.h[k]);
+  double dt_visc = lamv > 0.0 ? cfl / (twoNp1 * twoNp1 * lamv * inv_h2) : INFINITY;
+  double dt_src = cfl * 4.6 * s->beta / s->alpha;
+  double r = dt_conv;
+  if (dt_visc < r) r = dt_visc;
+  if (dt_src < r) r = dt_src;
+  *dt = r;
+  return ORC_OK;
+}
+
+/* Quadrature sums over the mesh with weights w_n J, J = prod_k h_k / 2:
+ *   mass = sum rho;
+ *   energy = sum (|m|^2/(2 rho) + W(rho) + alpha/2 (rho-c)^2 + kappa/2 |Q_c|^2),
+ *            Eq. (pararelax_elliptical_energy_dynamic) with the BR1 gradient of c;
+ *   l2 = sqrt(sum (rho - c)^2). */
+int orc_diagnostics(const orc_setup* s, const double* U, double* mass, double* energy, double* l2_rho_c) {
+  mesh_t m;
+  int st = make_mesh(s, &m);
+  if (st) return st;
+  const int d = m.d, nw = d + 1;
+  const long nn = m.E * m.npe;
+  double* Q = (double*)malloc(sizeof(double) * m.nq * nn);
+  if (!Q) return ORC_ERR_ARG;
+  st = lift(s, &m, U, Q);
+  double J = 1.0;
+  for (int k = 0; k < d; ++k) J *= m.h[k] / 2.0;
+  double sm = 0.0, se = 0.0, sl = 0.0;
+  for (long e = 0; e < m.E; ++e)
+    for (int n = 0; n < m.npe; ++n) {
+      double wq = J;
+      for (int k = 0; k < d; ++k) wq *= m.w[node_coord(&m, n, k)];
+      const long p = e * m.npe + n;
+      double rho = U[p], c = U[(d + 1) * nn + p];
+      double m2 = 0.0, g2 = 0.0;
+      for (int a = 0; a < d; ++a) {
+        m2 += U[(1 + a) * nn + p] * U[(1 + a) * nn + p];
+        double gc = Q[(a * nw + d) * nn + p];
+        g2 += gc * gc;
+      }
+      sm += wq * rho;
+      se += wq * (m2 / (2.0 * rho) + orc_free_energy(s->T, rho) + s->alpha / 2.0 * (rho - c) * (rho - c) +
+                  s->kappa / 2.0 * g2);
+      sl += wq * (rho - c) * (rho - c);
+    }
+  free(Q);
+  *mass = sm;
+  *energy = se;
+  *l2_rho_c = sqrt(sl);
+  return st;
+}

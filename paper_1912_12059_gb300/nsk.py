@@ -1,0 +1,228 @@
+"""Thin ctypes binding of libnsk.so (include/nsk.h).
+
+Argument marshalling only: every step of the discretisation runs in the CUDA
+library. Host arrays are numpy float64 C-contiguous arrays; device arrays are
+torch CUDA float64 tensors (contiguous), passed by pointer with where=DEVICE on
+the context's stream. If the library is missing the import of this module
+still works, but every call raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from pathlib import Path
+
+import numpy as np
+
+PKG = Path(__file__).resolve().parent
+LIB_PATH = PKG / "libnsk.so"
+
+NSK_OK = 0
+NSK_ERR_ARG = -1
+NSK_ERR_CUDA = -2
+NSK_ERR_NONPHYSICAL = -3
+NSK_ERR_TIMEOUT = -4
+NSK_ERR_STATE = -5
+NSK_ERR_NOMEM = -6
+NSK_NODES_GAUSS = 0
+NSK_NODES_GAUSS_LOBATTO = 1
+NSK_FP64 = 0
+NSK_FP32_MIXED = 1
+NSK_HOST = 0
+NSK_DEVICE = 1
+
+#: every symbol include/nsk.h declares, with (restype, argtypes)
+_dp = C.POINTER(C.c_double)
+SIGNATURES = {
+    "nsk_init_mesh": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_int), _dp, _dp, C.c_int, C.c_int,
+                                C.c_int, C.c_void_p]),
+    "nsk_set_params": (C.c_int, [C.c_void_p, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double]),
+    "nsk_set_c_dissipation": (C.c_int, [C.c_void_p, C.c_int]),
+    "nsk_set_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
+    "nsk_get_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
+    "nsk_node_coords": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
+    "nsk_rhs": (C.c_int, [C.c_void_p, C.c_double, C.c_void_p, C.c_int]),
+    "nsk_lift": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
+    "nsk_compute_dt": (C.c_int, [C.c_void_p, C.c_double, _dp]),
+    "nsk_step": (C.c_int, [C.c_void_p, C.c_double, C.c_int]),
+    "nsk_diagnostics": (C.c_int, [C.c_void_p, _dp, _dp, _dp]),
+    "nsk_get_sizes": (C.c_int, [C.c_void_p, C.POINTER(C.c_longlong), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "nsk_launch_count": (C.c_longlong, [C.c_void_p]),
+    "nsk_error_string": (C.c_char_p, [C.c_int]),
+    "nsk_destroy": (None, [C.c_void_p]),
+}
+
+_lib = None
+
+
+class NskError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        msg = error_string(code) if _lib is not None else str(code)
+        super().__init__(f"{what}: {msg} ({code})")
+
+
+def load_library(path: str | Path | None = None):
+    """Load libnsk.so (built by build.build_library()); raises if it is absent."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = Path(path) if path else LIB_PATH
+    if not p.exists():
+        raise RuntimeError(f"libnsk.so not found at {p}: build it with paper_1912_12059_gb300.build.build_library() "
+                           "(there is no CPU fallback)")
+    L = C.CDLL(str(p))
+    for name, (res, args) in SIGNATURES.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def error_string(code: int) -> str:
+    return load_library().nsk_error_string(code).decode()
+
+
+def _check(code: int, what: str):
+    if code != NSK_OK:
+        raise NskError(code, what)
+
+
+def _buf(a, nvals: int, writable: bool):
+    """(pointer, where, keepalive) for a numpy host array or a torch CUDA tensor."""
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or not a.flags.c_contiguous or a.size != nvals:
+            raise ValueError(f"need a C-contiguous float64 array of {nvals} values")
+        if writable and not a.flags.writeable:
+            raise ValueError("output array is read-only")
+        return C.c_void_p(a.ctypes.data), NSK_HOST
+    try:
+        import torch
+    except ImportError as exc:  # pragma: no cover
+        raise TypeError("expected a numpy array") from exc
+    if isinstance(a, torch.Tensor):
+        if a.dtype != torch.float64 or not a.is_contiguous() or a.numel() != nvals:
+            raise ValueError(f"need a contiguous float64 tensor of {nvals} values")
+        return C.c_void_p(a.data_ptr()), (NSK_DEVICE if a.is_cuda else NSK_HOST)
+    raise TypeError("expected a numpy array or a torch tensor")
+
+
+# ---- same-name wrappers of the C entry points ----
+
+def nsk_init_mesh(dim, nelem, lo, hi, N, node_type=NSK_NODES_GAUSS, precision=NSK_FP64, stream=None):
+    L = load_library()
+    ctx = C.c_void_p()
+    ne = (C.c_int * 3)(*(list(nelem) + [1] * (3 - len(nelem))))
+    clo = (C.c_double * 3)(*(list(lo) + [0.0] * (3 - len(lo))))
+    chi = (C.c_double * 3)(*(list(hi) + [1.0] * (3 - len(hi))))
+    _check(L.nsk_init_mesh(C.byref(ctx), dim, ne, clo, chi, N, node_type, precision,
+                           C.c_void_p(stream) if stream else None), "nsk_init_mesh")
+    return ctx
+
+
+def nsk_set_params(ctx, T, kappa, alpha, beta, mu):
+    _check(load_library().nsk_set_params(ctx, T, kappa, alpha, beta, mu), "nsk_set_params")
+
+
+def nsk_set_c_dissipation(ctx, on):
+    _check(load_library().nsk_set_c_dissipation(ctx, int(bool(on))), "nsk_set_c_dissipation")
+
+
+def nsk_destroy(ctx):
+    load_library().nsk_destroy(ctx)
+
+
+class Solver:
+    """One context: mesh, parameters and state on the current CUDA device."""
+
+    def __init__(self, dim, nelem, N, lo=None, hi=None, node_type=NSK_NODES_GAUSS, precision=NSK_FP64,
+                 stream=None):
+        self.dim = dim
+        lo = lo if lo is not None else [0.0] * dim
+        hi = hi if hi is not None else [1.0] * dim
+        self.ctx = nsk_init_mesh(dim, nelem, lo, hi, N, node_type, precision, stream)
+        L = load_library()
+        E, npe, nv = C.c_longlong(), C.c_int(), C.c_int()
+        _check(L.nsk_get_sizes(self.ctx, C.byref(E), C.byref(npe), C.byref(nv)), "nsk_get_sizes")
+        self.E, self.npe, self.nvar = E.value, npe.value, nv.value
+        self.nq = dim * (dim + 1)
+        self.N = N
+        self.precision = precision
+
+    # -- lifecycle --
+    def close(self):
+        if self.ctx:
+            nsk_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def shape(self):
+        return (self.nvar, self.E, self.npe)
+
+    @property
+    def n_nodes(self):
+        return self.E * self.npe
+
+    # -- calls --
+    def set_params(self, T=0.85, kappa=1e-4, alpha=1e3, beta=1e-3, mu=1e-3):
+        nsk_set_params(self.ctx, T, kappa, alpha, beta, mu)
+
+    def set_c_dissipation(self, on):
+        nsk_set_c_dissipation(self.ctx, on)
+
+    def set_state(self, U):
+        ptr, where = _buf(U, self.nvar * self.n_nodes, False)
+        _check(load_library().nsk_set_state(self.ctx, ptr, where), "nsk_set_state")
+
+    def get_state(self, out=None):
+        out = np.empty(self.shape) if out is None else out
+        ptr, where = _buf(out, self.nvar * self.n_nodes, True)
+        _check(load_library().nsk_get_state(self.ctx, ptr, where), "nsk_get_state")
+        return out
+
+    def node_coords(self, out=None):
+        out = np.empty((self.dim, self.E, self.npe)) if out is None else out
+        ptr, where = _buf(out, self.dim * self.n_nodes, True)
+        _check(load_library().nsk_node_coords(self.ctx, ptr, where), "nsk_node_coords")
+        return out
+
+    def rhs(self, t=0.0, out=None):
+        out = np.empty(self.shape) if out is None else out
+        ptr, where = _buf(out, self.nvar * self.n_nodes, True)
+        _check(load_library().nsk_rhs(self.ctx, t, ptr, where), "nsk_rhs")
+        return out
+
+    def lift(self, out=None):
+        out = np.empty((self.nq, self.E, self.npe)) if out is None else out
+        ptr, where = _buf(out, self.nq * self.n_nodes, True)
+        _check(load_library().nsk_lift(self.ctx, ptr, where), "nsk_lift")
+        return out
+
+    def compute_dt(self, cfl):
+        dt = C.c_double()
+        _check(load_library().nsk_compute_dt(self.ctx, cfl, C.byref(dt)), "nsk_compute_dt")
+        return dt.value
+
+    def step(self, dt, nsteps=1):
+        _check(load_library().nsk_step(self.ctx, dt, nsteps), "nsk_step")
+
+    def diagnostics(self):
+        m, e, l2 = C.c_double(), C.c_double(), C.c_double()
+        _check(load_library().nsk_diagnostics(self.ctx, C.byref(m), C.byref(e), C.byref(l2)), "nsk_diagnostics")
+        return m.value, e.value, l2.value
+
+    @property
+    def launch_count(self):
+        return int(load_library().nsk_launch_count(self.ctx))

@@ -1,0 +1,34 @@
+import os
+import sys
+from pathlib import Path
+
+import pytest
+
+ROOT = Path(__file__).resolve().parent.parent
+if str(ROOT) not in sys.path:
+    sys.path.insert(0, str(ROOT))
+
+
+def pytest_configure(config):
+    config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
+    config.addinivalue_line("markers", "slow: long-running CPU test")
+
+
+@pytest.fixture(scope="session")
+def nsk_lib():
+    """Build (if stale) and load libnsk.so."""
+    from paper_1912_12059_gb300.build import build_library
+    from paper_1912_12059_gb300 import nsk
+
+    build_library()
+    return nsk.load_library()
+
+
+@pytest.fixture(scope="session")
+def gpu(nsk_lib):
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.fail("GPU test selected but no CUDA device is visible")
+    torch.cuda.init()
+    return torch.device("cuda:0")
