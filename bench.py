@@ -1,0 +1,356 @@
+#!/usr/bin/env python3
+"""Benchmark of the explicit DGSEM hot path of the parabolic relaxation model
+(arXiv:1912.12059, relaxation model II) on GB300.
+
+A "step" is one five-stage LSRK4 step over the whole mesh (every stage: trace
+prolongation, BR1 lifting, face fluxes, volume integral + surface lifting +
+sources + RK update). The metric is DOF-updates/s = nodes x 5 stages x steps /
+seconds, timed with CUDA events on the solver's stream with the state resident
+in HBM. `e2e` repeats the measurement through the C ABI with the state in
+pinned host memory, copied in before and read back after every step.
+
+Default workload: 3D head-on droplet collision, 64^3 elements, N = 3 (16.8M
+nodes x 5 variables), FP64, We = 40. Under torchrun each rank advances its own
+instance (independent problems: weak scaling, no data-path collective).
+
+`--impl reference` times the FP64 CPU oracle instead (test infrastructure of
+this repository) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+from pathlib import Path
+
+import numpy as np
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+MEASURED_PEAKS = ROOT / "MEASURED_PEAKS.json"
+# FP64 FMA pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (max SM clock)
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def workload_by_name(name):
+    from paper_1912_12059_gb300 import inputs
+
+    if name == "collision3d":
+        return inputs.head_on_collision_3d(we=40.0)
+    if name == "coalescence2d":
+        return inputs.coalescence_2d(alpha=1e2)
+    if name == "interface1d":
+        return inputs.static_interface_1d()
+    raise SystemExit(f"unknown workload {name}")
+
+
+# ---------------------------------------------------------------- algorithmic cost model
+def kernel_cost(kernel, d, n, fp_bytes):
+    """Algorithmic (flops, bytes) per element of one stage kernel, counted from the kernel
+    source: FMA = 2 flops, add/mul/div/sqrt = 1; bytes = compulsory loads + stores."""
+    npe, nfn, nv, nw, nf = n**d, n ** (d - 1), d + 2, d + 1, 2 * d
+    if kernel == "k_prolong":
+        return nf * nfn * nv * 2 * n, fp_bytes * (nv * npe + nf * nfn * nv)
+    if kernel == "k_lift":
+        per_node = (d + 1) + d * nw * (2 * n + 5) + 2 * d * d + 3 * d + (d - 1)
+        fl = npe * per_node + nf * nfn * (4 * d + 4) + nf * nfn * nw * 2 * n
+        by = fp_bytes * (nv * npe + 2 * nf * nfn * nv + d * nw * npe + nf * nfn * nw)
+        return fl, by
+    if kernel == "k_face":
+        return d * nfn * (58 + 13 * d), fp_bytes * d * nfn * (2 * nv + 2 * nw + nv)
+    if kernel == "k_volume":
+        per_node = 1 + 10 + (d - 1) + d * (5 * d + 5) + nv * d * (2 * n + 6) + 3 * d + 3 + 5 * nv
+        by = fp_bytes * (nv * npe + d * nw * npe + 2 * d * nfn * nv + 2 * nv * npe + nv * npe)
+        return npe * per_node, by
+    raise KeyError(kernel)
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index=0):
+        self.dev = device_index
+        self.proc = None
+        self.path = Path(tempfile.mkstemp(prefix="nsk_clocks_", suffix=".csv")[1])
+
+    def __enter__(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in self.path.read_text().splitlines():
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        except OSError:
+            pass
+        finally:
+            try:
+                self.path.unlink()
+            except OSError:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------- CPU oracle baseline
+def oracle_sample(wl, target_s=15.0):
+    """Time the FP64 CPU oracle (single thread, as it stands) on a bounded sample of the
+    workload: the same N, parameters and initial-condition recipe on a smaller periodic mesh
+    (element size unchanged in the sampled directions is not needed: the oracle's cost per node
+    does not depend on the mesh spacing). Returns (DOF-updates/s, description)."""
+    import oracle as O
+    from paper_1912_12059_gb300 import inputs
+
+    ne = {3: (8, 8, 8), 2: (32, 32), 1: (64,)}[wl.dim]
+    o = O.Oracle(wl.dim, ne, [0.0] * wl.dim, [1.0] * wl.dim, wl.N, wl.node_type, T=wl.T, kappa=wl.kappa,
+                 alpha=wl.alpha, beta=wl.beta, mu=wl.mu)
+    U = wl.initial_state(o.coords())
+    dt = o.timestep(U, wl.cfl)
+    t0 = time.perf_counter()
+    steps = 0
+    while True:
+        U = o.step(U, dt, 1)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el > target_s or steps >= 1000:
+            break
+    nodes = o.E * o.npe
+    rate = nodes * 5 * steps / el
+    return rate, f"{steps} LSRK4 steps of the oracle on a {'x'.join(map(str, ne))}-element periodic box " \
+                 f"(N={wl.N}, {nodes} nodes, same parameters and initial-condition recipe), {el:.1f} s"
+
+
+def run_reference(args, wl, rank, world):
+    """--impl reference: the FP64 CPU oracle, timed on the host cores; rank 0 only."""
+    if rank != 0:
+        return 0
+    rates = []
+    for _ in range(args.warmup):
+        oracle_sample(wl, target_s=2.0)
+    desc = ""
+    t_total = 0.0
+    for _ in range(args.steps):
+        r, desc = oracle_sample(wl, target_s=max(2.0, 40.0 / max(args.steps, 1)))
+        rates.append(r)
+    value = statistics.median(rates)
+    ms_per_step = wl.dofs * 5 / value * 1e3
+    line = {
+        "impl": "reference", "metric": "DOF-updates/s", "value": value, "unit": "DOF-updates/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl.name, "dofs": wl.dofs, "N": wl.N, "nelem": list(wl.nelem)},
+        "cpu_baseline": {"value": value, "unit": "DOF-updates/s", "cores": 1, "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": "DOF-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------- GPU arm
+def run_gpu(args, wl, rank, world):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1912_12059_gb300 import nsk
+    from paper_1912_12059_gb300.build import build_library
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if rank == 0 or not (ROOT / "paper_1912_12059_gb300" / "libnsk.so").exists():
+        build_library()
+    if world > 1:
+        dist.barrier()
+    stream = torch.cuda.Stream()
+    prec = nsk.NSK_FP32_MIXED if args.precision == "fp32" else nsk.NSK_FP64
+    s = nsk.Solver(wl.dim, wl.nelem, wl.N, list(wl.lo[:wl.dim]), list(wl.hi[:wl.dim]), wl.node_type, prec,
+                   stream=stream.cuda_stream)
+    s.set_params(T=wl.T, kappa=wl.kappa, alpha=wl.alpha, beta=wl.beta, mu=wl.mu)
+    x = s.node_coords()
+    U0 = wl.initial_state(x)
+    s.set_state(U0)
+    dt = s.compute_dt(wl.cfl)
+    nodes = s.E * s.npe
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    # warm-up
+    s.step(dt, args.warmup)
+    # timed region: device-resident state
+    s.set_profiling(True)
+    s.get_profile(reset=True)
+    launches0 = s.launch_count
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        s.step(dt, args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    ms = ev0.elapsed_time(ev1)
+    launches = s.launch_count - launches0
+    prof = s.get_profile(reset=True)
+    s.set_profiling(False)
+    clocks = clk.summary()
+
+    # end to end through the C ABI: pinned host state in, step, state out, every step
+    U_host = torch.from_numpy(s.get_state()).pin_memory()
+    nbytes = U_host.numel() * 8
+    e2e_steps = max(1, min(args.steps, 10))
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        s.set_state(U_host)
+        s.step(dt, 1)
+        s.get_state(out=U_host)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    barrier()
+
+    # aggregate over ranks: total units / max time
+    t_max = ms
+    e2e_max = e2e_s
+    total_nodes = nodes
+    if world > 1:
+        tt = torch.tensor([ms, e2e_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max, e2e_max = float(tt[0]), float(tt[1])
+        nn = torch.tensor([float(nodes)], device="cuda", dtype=torch.float64)
+        dist.all_reduce(nn, op=dist.ReduceOp.SUM)
+        total_nodes = float(nn[0])
+    value = total_nodes * 5 * args.steps / (t_max / 1e3)
+    e2e_value = total_nodes * 5 * e2e_steps / e2e_max
+
+    # roofline of the dominant kernel
+    fp_bytes = 8 if prec == nsk.NSK_FP64 else 4
+    name, (kms, kcnt) = max(prof.items(), key=lambda kv: kv[1][0])
+    avg_ms = kms / max(kcnt, 1)
+    flops_e, bytes_e = kernel_cost(name, wl.dim, wl.N + 1, fp_bytes)
+    peaks = json.loads(MEASURED_PEAKS.read_text()) if MEASURED_PEAKS.exists() else {}
+    if prec == nsk.NSK_FP64:
+        achieved = flops_e * s.E / (avg_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None, "kernel": name,
+                "peak_source": "FP64 FMA pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
+                "algorithmic_per_launch": flops_e * s.E}
+    else:
+        hbm = float(peaks.get("hbm_gbs", 6800.0))
+        achieved = bytes_e * s.E / (avg_ms / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": None, "kernel": name,
+                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+                "algorithmic_per_launch": bytes_e * s.E}
+    kernels = {k: {"avg_ms": v[0] / max(v[1], 1), "launches": v[1],
+                   "share": v[0] / max(sum(x[0] for x in prof.values()), 1e-30)} for k, v in prof.items()}
+    s.close()
+
+    if rank != 0:
+        return 0
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        rate, desc = oracle_sample(wl, target_s=args.cpu_seconds)
+        cpu = {"value": rate, "unit": "DOF-updates/s", "cores": 1, "kind": "oracle", "sample": desc}
+    line = {
+        "metric": "DOF-updates/s", "value": value, "unit": "DOF-updates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == nsk.NSK_FP64 else "f32",
+        "data": "synthetic",
+        "config": {"workload": wl.name, "dofs_per_gpu": nodes, "N": wl.N, "nelem": list(wl.nelem),
+                   "precision": args.precision, "dt": dt, "l2": "state larger than L2 (inputs > 129 MB)"
+                   if nodes * (wl.dim + 2) * fp_bytes > 129e6 else "state fits L2"},
+        "e2e": {"value": e2e_value, "unit": "DOF-updates/s", "h2d_bytes_per_step": nbytes,
+                "d2h_bytes_per_step": nbytes, "steps": e2e_steps},
+        "gpu_launches": launches,
+        "roofline": roof,
+        "kernels": kernels,
+        "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"], "reasons": clocks["reasons"]},
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="collision3d", choices=["collision3d", "coalescence2d", "interface1d"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--nelem", type=int, default=0, help="override elements per direction (profiling runs)")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    wl = workload_by_name(args.workload)
+    if args.nelem:
+        import dataclasses
+
+        wl = dataclasses.replace(wl, nelem=(args.nelem,) * wl.dim, name=f"{wl.name}_resized_E{args.nelem}")
+    if args.impl == "reference":
+        return run_reference(args, wl, rank, world)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    try:
+        return run_gpu(args, wl, rank, world)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

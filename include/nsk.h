@@ -134,6 +134,16 @@ int nsk_diagnostics(nsk_ctx* ctx, double* mass, double* energy, double* l2_rho_m
 /* Sizes of the context: number of elements, nodes per element, variables. */
 int nsk_get_sizes(nsk_ctx* ctx, long long* n_elem, int* nodes_per_elem, int* nvar);
 
+/* Per-kernel timing. With on = 1 every kernel of the stage pipeline is
+ * bracketed by CUDA events recorded on the context's stream, and the elapsed
+ * times are accumulated at the next synchronising call (nsk_step, nsk_rhs, ...).
+ * nsk_get_profile copies up to n entries of accumulated milliseconds and
+ * launch counts, index 0 = trace prolongation, 1 = BR1 lifting, 2 = face flux,
+ * 3 = volume integral + surface lifting + sources + RK update, and returns the
+ * number of entries (4); reset = 1 clears the accumulators afterwards. */
+int nsk_set_profiling(nsk_ctx* ctx, int on);
+int nsk_get_profile(nsk_ctx* ctx, double* ms, long long* launches, int n, int reset);
+
 /* Kernel launches issued by this context since creation (a counter kept on
  * the host; every launch of the library's own kernels increments it). */
 long long nsk_launch_count(nsk_ctx* ctx);

@@ -1,0 +1,555 @@
+// nsk_api.cu -- host side of libnsk.so: the C ABI declared in include/nsk.h.
+// Builds the nodal tables and the mesh, owns the device buffers of a context,
+// validates arguments and call order, and queues the stage kernels.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "nsk_internal.h"
+
+namespace {
+
+// ---- nodal basis (Sec. 3.1): Gauss-Legendre / Gauss-Lobatto nodes and weights ----
+
+// P_n(x) and P_{n-1}(x) by the Bonnet recurrence.
+void legendre_pair(int n, double x, double* pn, double* pnm1) {
+  double a = 1.0, b = x;  // P_0, P_1
+  if (n == 0) {
+    *pn = 1.0;
+    *pnm1 = 0.0;
+    return;
+  }
+  for (int k = 2; k <= n; ++k) {
+    const double c = ((2 * k - 1) * x * b - (k - 1) * a) / k;
+    a = b;
+    b = c;
+  }
+  *pn = b;
+  *pnm1 = a;
+}
+
+// Gauss-Legendre: the n = N+1 roots of P_n, Newton from Tricomi's estimate;
+// weights 2 (1 - x^2) / (n P_{n-1}(x))^2.
+void gauss_legendre(int n, double* x, double* w) {
+  const double pi = 3.141592653589793238462643;
+  for (int i = 0; i < n; ++i) {
+    const double theta = pi * (4.0 * (n - i) - 1.0) / (4.0 * n + 2.0);
+    double z = (1.0 - 1.0 / (8.0 * n * n) + 1.0 / (8.0 * n * n * n)) * cos(theta);
+    for (int it = 0; it < 60; ++it) {
+      double pn, pm;
+      legendre_pair(n, z, &pn, &pm);
+      const double dp = n * (pm - z * pn) / (1.0 - z * z);
+      const double dz = pn / dp;
+      z -= dz;
+      if (fabs(dz) <= 1e-17) break;
+    }
+    double pn, pm;
+    legendre_pair(n, z, &pn, &pm);
+    x[i] = z;
+    w[i] = 2.0 * (1.0 - z * z) / ((n * pm) * (n * pm));
+  }
+}
+
+// Gauss-Lobatto with N+1 nodes: +-1 and the roots of P_N'; Newton with
+// P_N'' from Legendre's differential equation; weights 2 / (N (N+1) P_N(x)^2).
+void gauss_lobatto(int N, double* x, double* w) {
+  const double pi = 3.141592653589793238462643;
+  x[0] = -1.0;
+  x[N] = 1.0;
+  for (int i = 1; i < N; ++i) {
+    double z = -cos(pi * i / N);
+    for (int it = 0; it < 60; ++it) {
+      double pn, pm;
+      legendre_pair(N, z, &pn, &pm);
+      const double d1 = N * (pm - z * pn) / (1.0 - z * z);
+      const double d2 = (2.0 * z * d1 - N * (N + 1.0) * pn) / (1.0 - z * z);
+      const double dz = d1 / d2;
+      z -= dz;
+      if (fabs(dz) <= 1e-17) break;
+    }
+    x[i] = z;
+  }
+  for (int i = 0; i <= N; ++i) {
+    double pn, pm;
+    legendre_pair(N, x[i], &pn, &pm);
+    w[i] = 2.0 / (N * (N + 1.0) * pn * pn);
+  }
+}
+
+// Barycentric weights, derivative matrix D_ij = l_j'(x_i) and l_j(x0).
+void barycentric(int n, const double* x, double* lam) {
+  for (int j = 0; j < n; ++j) {
+    double p = 1.0;
+    for (int m = 0; m < n; ++m)
+      if (m != j) p *= x[j] - x[m];
+    lam[j] = 1.0 / p;
+  }
+}
+double lagrange_at(int n, const double* x, const double* lam, int j, double x0) {
+  for (int m = 0; m < n; ++m)
+    if (x0 == x[m]) return m == j ? 1.0 : 0.0;
+  double s = 0.0;
+  for (int m = 0; m < n; ++m) s += lam[m] / (x0 - x[m]);
+  return lam[j] / (x0 - x[j]) / s;
+}
+
+template <typename R>
+void fill_tab(NskTab<R>& t, int n, const double* x, const double* w) {
+  double lam[NSK_MAXNP], D[NSK_MAXNP][NSK_MAXNP];
+  barycentric(n, x, lam);
+  for (int i = 0; i < n; ++i) {
+    double diag = 0.0;
+    for (int j = 0; j < n; ++j) {
+      if (i == j) continue;
+      D[i][j] = lam[j] / lam[i] / (x[i] - x[j]);
+      diag -= D[i][j];
+    }
+    D[i][i] = diag;
+  }
+  memset(&t, 0, sizeof(t));
+  for (int i = 0; i < n; ++i) {
+    for (int j = 0; j < n; ++j) t.dvol[i * NSK_MAXNP + j] = (R)(w[j] / w[i] * D[j][i]);
+    const double lm = lagrange_at(n, x, lam, i, -1.0), lp = lagrange_at(n, x, lam, i, 1.0);
+    t.lm[i] = (R)lm;
+    t.lp[i] = (R)lp;
+    t.lmw[i] = (R)(lm / w[i]);
+    t.lpw[i] = (R)(lp / w[i]);
+    t.w[i] = (R)w[i];
+  }
+}
+
+// Carpenter-Kennedy RK4(3)5[2N] (the published rational coefficients).
+const double kA[5] = {0.0, -567301805773.0 / 1357537059087.0, -2404267990393.0 / 2016746695238.0,
+                      -3550918686646.0 / 2091501179385.0, -1275806237668.0 / 842570457699.0};
+const double kB[5] = {1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612068292357.0,
+                      1720146321549.0 / 2090206949498.0, 3134564353537.0 / 4481467310338.0,
+                      2277821191437.0 / 14882151754819.0};
+
+}  // namespace
+
+struct nsk_ctx {
+  int dim, N, np, npe, nfn, nvar, nq, node_type, precision;
+  long long E, nn;
+  int ne[3];
+  double lo[3], hi[3], h[3];
+  double xi[NSK_MAXNP], w[NSK_MAXNP];
+  cudaStream_t stream;
+  NskParams p;
+  NskBuffers b;
+  void* rbuf;        // residual scratch, context precision, nvar*nn
+  double* stage64;   // FP64 staging for transfers, max(nvar, nq, dim)*nn
+  bool params_set, state_set;
+  long long launches;
+  size_t rsize;      // bytes per value in context precision
+  // per-kernel profiling (nsk_set_profiling)
+  bool prof_on;
+  std::vector<cudaEvent_t> prof_pool;  // groups of NSK_NKERN + 1 events
+  std::vector<int> prof_nk;            // kernels recorded in each used group
+  size_t prof_used;                    // groups recorded since the last sync
+  double prof_ms[NSK_NKERN];
+  long long prof_cnt[NSK_NKERN];
+};
+
+namespace {
+
+// events for the next profiled stage (NULL when profiling is off)
+cudaEvent_t* prof_group(nsk_ctx* c, int nkern) {
+  if (!c->prof_on) return nullptr;
+  const size_t g = c->prof_used;
+  if ((g + 1) * (NSK_NKERN + 1) > c->prof_pool.size()) {
+    for (int i = 0; i < NSK_NKERN + 1; ++i) {
+      cudaEvent_t ev;
+      if (cudaEventCreate(&ev) != cudaSuccess) return nullptr;
+      c->prof_pool.push_back(ev);
+    }
+  }
+  if (c->prof_nk.size() <= g) c->prof_nk.resize(g + 1);
+  c->prof_nk[g] = nkern;
+  c->prof_used = g + 1;
+  return &c->prof_pool[g * (NSK_NKERN + 1)];
+}
+
+// after a stream synchronisation: fold the recorded event pairs into the totals
+void prof_collect(nsk_ctx* c) {
+  for (size_t g = 0; g < c->prof_used; ++g) {
+    cudaEvent_t* ev = &c->prof_pool[g * (NSK_NKERN + 1)];
+    for (int k = 0; k < c->prof_nk[g]; ++k) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, ev[k], ev[k + 1]) == cudaSuccess) {
+        c->prof_ms[k] += ms;
+        c->prof_cnt[k] += 1;
+      }
+    }
+  }
+  c->prof_used = 0;
+}
+
+int sync_and_check(nsk_ctx* c) {
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return NSK_ERR_CUDA;
+  prof_collect(c);
+  int h = 0;
+  if (cudaMemcpy(&h, c->b.err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return NSK_ERR_CUDA;
+  if (h) {
+    int z = 0;
+    if (cudaMemcpy(c->b.err, &z, sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess) return NSK_ERR_CUDA;
+    if (h & NSK_EBIT_TIMEOUT) return NSK_ERR_TIMEOUT;
+    return NSK_ERR_NONPHYSICAL;
+  }
+  return NSK_OK;
+}
+
+int launch_stage(nsk_ctx* c, NskLaunch l) {
+  l.ev = prof_group(c, l.mode == NSK_MODE_LIFT ? 2 : NSK_NKERN);
+  int r;
+  const bool f32 = c->precision == NSK_FP32_MIXED;
+  switch (c->dim) {
+    case 1: r = nsk_launch_stage_d1(c->p, c->np, f32, c->b, l, c->stream); break;
+    case 2: r = nsk_launch_stage_d2(c->p, c->np, f32, c->b, l, c->stream); break;
+    default: r = nsk_launch_stage_d3(c->p, c->np, f32, c->b, l, c->stream); break;
+  }
+  if (r < 0) return r;
+  c->launches += r;
+  return NSK_OK;
+}
+
+// copy an internal nodal array (context precision, ncomp*nn values) out to dst
+int export_nodal(nsk_ctx* c, const void* src, int ncomp, double* dst, int where) {
+  const long long n = (long long)ncomp * c->nn;
+  const size_t bytes = sizeof(double) * (size_t)n;
+  if (c->precision == NSK_FP64) {
+    const cudaMemcpyKind kind = where == NSK_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (cudaMemcpyAsync(dst, src, bytes, kind, c->stream) != cudaSuccess) return NSK_ERR_CUDA;
+  } else {
+    double* tgt = where == NSK_DEVICE ? dst : c->stage64;
+    int r = nsk_launch_convert(src, false, tgt, true, n, c->stream);
+    if (r < 0) return r;
+    c->launches += r;
+    if (where == NSK_HOST &&
+        cudaMemcpyAsync(dst, c->stage64, bytes, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+      return NSK_ERR_CUDA;
+  }
+  return NSK_OK;
+}
+
+void free_ctx(nsk_ctx* c) {
+  if (!c) return;
+  void* ptrs[] = {c->b.U, c->b.K, c->b.Q, c->b.Utr, c->b.FVtr, c->b.Fstar, c->b.err, c->b.lam,
+                  c->b.dt, c->b.part, c->rbuf, c->stage64};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  for (cudaEvent_t ev : c->prof_pool) cudaEventDestroy(ev);
+  delete c;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* nsk_error_string(int code) {
+  switch (code) {
+    case NSK_OK: return "ok";
+    case NSK_ERR_ARG: return "invalid argument";
+    case NSK_ERR_CUDA: return "CUDA runtime error";
+    case NSK_ERR_NONPHYSICAL: return "non-physical state (rho outside (0,3), p_alpha' < 0 or NaN)";
+    case NSK_ERR_TIMEOUT: return "bounded device wait expired";
+    case NSK_ERR_STATE: return "call order violated";
+    case NSK_ERR_NOMEM: return "device allocation failed";
+    default: return "unknown error";
+  }
+}
+
+int nsk_init_mesh(nsk_ctx** out, int dim, const int nelem[3], const double lo[3], const double hi[3], int N,
+                  int node_type, int precision, void* cuda_stream) {
+  if (!out || !nelem || !lo || !hi) return NSK_ERR_ARG;
+  *out = nullptr;
+  if (dim < 1 || dim > 3 || N < 1 || N + 1 > NSK_MAXNP) return NSK_ERR_ARG;
+  if (node_type != NSK_NODES_GAUSS && node_type != NSK_NODES_GAUSS_LOBATTO) return NSK_ERR_ARG;
+  if (precision != NSK_FP64 && precision != NSK_FP32_MIXED) return NSK_ERR_ARG;
+  nsk_ctx* c = new (std::nothrow) nsk_ctx();
+  if (!c) return NSK_ERR_NOMEM;
+  c->dim = dim;
+  c->N = N;
+  c->np = N + 1;
+  c->node_type = node_type;
+  c->precision = precision;
+  c->nvar = dim + 2;
+  c->nq = dim * (dim + 1);
+  c->npe = 1;
+  c->nfn = 1;
+  c->E = 1;
+  for (int k = 0; k < 3; ++k) {
+    if (k < dim) {
+      if (nelem[k] < 1 || !(hi[k] > lo[k]) || !isfinite(lo[k]) || !isfinite(hi[k])) {
+        delete c;
+        return NSK_ERR_ARG;
+      }
+      c->ne[k] = nelem[k];
+      c->lo[k] = lo[k];
+      c->hi[k] = hi[k];
+      c->h[k] = (hi[k] - lo[k]) / nelem[k];
+      c->npe *= c->np;
+      if (k > 0) c->nfn *= c->np;
+    } else {
+      c->ne[k] = 1;
+      c->lo[k] = 0.0;
+      c->hi[k] = 1.0;
+      c->h[k] = 2.0;
+    }
+    c->E *= c->ne[k];
+  }
+  if (c->E > (1LL << 31) / c->npe) {  // keep every per-variable index in 32-bit blocks of the grid
+    delete c;
+    return NSK_ERR_ARG;
+  }
+  c->nn = c->E * c->npe;
+  c->stream = (cudaStream_t)cuda_stream;
+  c->rsize = precision == NSK_FP64 ? sizeof(double) : sizeof(float);
+  if (node_type == NSK_NODES_GAUSS)
+    gauss_legendre(c->np, c->xi, c->w);
+  else
+    gauss_lobatto(N, c->xi, c->w);
+
+  NskParams& p = c->p;
+  memset(&p, 0, sizeof(p));
+  p.E = c->E;
+  p.jac = 1.0;
+  for (int k = 0; k < 3; ++k) {
+    p.ne[k] = c->ne[k];
+    p.rh[k] = k < dim ? 2.0 / c->h[k] : 0.0;
+    if (k < dim) p.jac *= c->h[k] / 2.0;
+  }
+  fill_tab<double>(p.td, c->np, c->xi, c->w);
+  fill_tab<float>(p.tf, c->np, c->xi, c->w);
+
+  const size_t rs = c->rsize;
+  const long long nn = c->nn;
+  const long long faces = c->E * 2 * dim * c->nfn;
+  long long g = (nn + 255) / 256;
+  c->b.nparts = (int)(g < 152 * 8 ? (g > 0 ? g : 1) : 152 * 8);
+  int maxc = c->nq > c->nvar ? c->nq : c->nvar;
+  struct {
+    void** ptr;
+    size_t bytes;
+  } allocs[] = {
+      {&c->b.U, rs * c->nvar * nn},
+      {&c->b.K, rs * c->nvar * nn},
+      {&c->b.Q, rs * c->nq * nn},
+      {&c->b.Utr, rs * c->nvar * faces},
+      {&c->b.FVtr, rs * (dim + 1) * faces},
+      {&c->b.Fstar, rs * c->nvar * c->E * dim * c->nfn},
+      {(void**)&c->b.err, sizeof(int)},
+      {(void**)&c->b.lam, sizeof(unsigned long long)},
+      {(void**)&c->b.dt, sizeof(double)},
+      {(void**)&c->b.part, sizeof(double) * (3 * (size_t)c->b.nparts + 3)},
+      {&c->rbuf, rs * c->nvar * nn},
+      {(void**)&c->stage64, sizeof(double) * maxc * nn},
+  };
+  for (auto& a : allocs) {
+    if (cudaMalloc(a.ptr, a.bytes) != cudaSuccess) {
+      cudaGetLastError();
+      free_ctx(c);
+      return NSK_ERR_NOMEM;
+    }
+  }
+  if (cudaMemset(c->b.err, 0, sizeof(int)) != cudaSuccess || cudaMemset(c->b.K, 0, rs * c->nvar * nn) != cudaSuccess) {
+    free_ctx(c);
+    return NSK_ERR_CUDA;
+  }
+  *out = c;
+  return NSK_OK;
+}
+
+int nsk_set_params(nsk_ctx* c, double T, double kappa, double alpha, double beta, double mu) {
+  if (!c) return NSK_ERR_ARG;
+  if (!(T > 0.0 && T < 1.0) || !(kappa > 0.0) || !(beta > 0.0) || !(mu >= 0.0) || !isfinite(alpha) ||
+      !isfinite(kappa) || !isfinite(beta) || !isfinite(mu))
+    return NSK_ERR_ARG;
+  // Reduced VdW: W'' = p'/rho = 24 T / (rho (3 - rho)^2) - 6; rho (3 - rho)^2 peaks at
+  // rho = 1, so min W'' = 6 T - 6 and alpha_* = 3 (1 - T) (Eq. alpha_fullyhyperbolic_limit).
+  const double alpha_star = 3.0 * (1.0 - T);
+  if (!(alpha > alpha_star)) return NSK_ERR_ARG;
+  c->p.T = T;
+  c->p.kappa = kappa;
+  c->p.alpha = alpha;
+  c->p.beta = beta;
+  c->p.mu = mu;
+  c->params_set = true;
+  return NSK_OK;
+}
+
+int nsk_set_c_dissipation(nsk_ctx* c, int on) {
+  if (!c) return NSK_ERR_ARG;
+  c->p.c_diss = on ? 1 : 0;
+  return NSK_OK;
+}
+
+int nsk_set_state(nsk_ctx* c, const double* U, int where) {
+  if (!c || !U || (where != NSK_HOST && where != NSK_DEVICE)) return NSK_ERR_ARG;
+  if (!c->params_set) return NSK_ERR_STATE;
+  const long long n = (long long)c->nvar * c->nn;
+  const size_t bytes = sizeof(double) * (size_t)n;
+  const cudaMemcpyKind kind = where == NSK_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (c->precision == NSK_FP64) {
+    if (cudaMemcpyAsync(c->b.U, U, bytes, kind, c->stream) != cudaSuccess) return NSK_ERR_CUDA;
+  } else {
+    const double* src = U;
+    if (where == NSK_HOST) {
+      if (cudaMemcpyAsync(c->stage64, U, bytes, kind, c->stream) != cudaSuccess) return NSK_ERR_CUDA;
+      src = c->stage64;
+    }
+    int r = nsk_launch_convert(src, true, c->b.U, false, n, c->stream);
+    if (r < 0) return r;
+    c->launches += r;
+  }
+  if (cudaMemsetAsync(c->b.K, 0, c->rsize * (size_t)n, c->stream) != cudaSuccess) return NSK_ERR_CUDA;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return NSK_ERR_CUDA;
+  c->state_set = true;
+  return NSK_OK;
+}
+
+int nsk_get_state(nsk_ctx* c, double* U, int where) {
+  if (!c || !U || (where != NSK_HOST && where != NSK_DEVICE)) return NSK_ERR_ARG;
+  if (!c->state_set) return NSK_ERR_STATE;
+  int r = export_nodal(c, c->b.U, c->nvar, U, where);
+  if (r) return r;
+  return cudaStreamSynchronize(c->stream) == cudaSuccess ? NSK_OK : NSK_ERR_CUDA;
+}
+
+int nsk_node_coords(nsk_ctx* c, double* x, int where) {
+  if (!c || !x || (where != NSK_HOST && where != NSK_DEVICE)) return NSK_ERR_ARG;
+  const long long nn = c->nn;
+  double* hx = (double*)malloc(sizeof(double) * c->dim * nn);
+  if (!hx) return NSK_ERR_NOMEM;
+  for (long long e = 0; e < c->E; ++e) {
+    long long ec[3] = {e % c->ne[0], (e / c->ne[0]) % c->ne[1], e / ((long long)c->ne[0] * c->ne[1])};
+    for (int n = 0; n < c->npe; ++n) {
+      int idx = n;
+      for (int k = 0; k < c->dim; ++k) {
+        const int i = idx % c->np;
+        idx /= c->np;
+        hx[k * nn + e * c->npe + n] = c->lo[k] + c->h[k] * (ec[k] + 0.5 * (c->xi[i] + 1.0));
+      }
+    }
+  }
+  int st = NSK_OK;
+  const cudaMemcpyKind kind = where == NSK_DEVICE ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost;
+  if (cudaMemcpy(x, hx, sizeof(double) * c->dim * nn, kind) != cudaSuccess) st = NSK_ERR_CUDA;
+  free(hx);
+  return st;
+}
+
+int nsk_rhs(nsk_ctx* c, double t, double* Ut, int where) {
+  (void)t;
+  if (!c || !Ut || (where != NSK_HOST && where != NSK_DEVICE)) return NSK_ERR_ARG;
+  if (!c->state_set) return NSK_ERR_STATE;
+  NskLaunch l = {NSK_MODE_RHS, c->rbuf, 0.0, 0.0, nullptr, 0.0, nullptr};
+  int r = launch_stage(c, l);
+  if (r) return r;
+  r = export_nodal(c, c->rbuf, c->nvar, Ut, where);
+  if (r) return r;
+  return sync_and_check(c);
+}
+
+int nsk_lift(nsk_ctx* c, double* Q, int where) {
+  if (!c || !Q || (where != NSK_HOST && where != NSK_DEVICE)) return NSK_ERR_ARG;
+  if (!c->state_set) return NSK_ERR_STATE;
+  NskLaunch l = {NSK_MODE_LIFT, nullptr, 0.0, 0.0, nullptr, 0.0, nullptr};
+  int r = launch_stage(c, l);
+  if (r) return r;
+  r = export_nodal(c, c->b.Q, c->nq, Q, where);
+  if (r) return r;
+  return sync_and_check(c);
+}
+
+int nsk_compute_dt(nsk_ctx* c, double cfl, double* dt_out) {
+  if (!c || !dt_out || !(cfl > 0.0)) return NSK_ERR_ARG;
+  if (!c->state_set) return NSK_ERR_STATE;
+  int r = nsk_launch_dt(c->p, c->dim, c->np, c->precision == NSK_FP32_MIXED, c->b, cfl, c->stream);
+  if (r < 0) return r;
+  c->launches += r;
+  if (cudaMemcpyAsync(dt_out, c->b.dt, sizeof(double), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+    return NSK_ERR_CUDA;
+  return sync_and_check(c);
+}
+
+int nsk_step(nsk_ctx* c, double dt, int nsteps) {
+  if (!c || nsteps < 0 || !isfinite(dt) || dt == 0.0) return NSK_ERR_ARG;
+  if (!c->state_set) return NSK_ERR_STATE;
+  const bool adaptive = dt < 0.0;
+  for (int s = 0; s < nsteps; ++s) {
+    if (adaptive) {
+      int r = nsk_launch_dt(c->p, c->dim, c->np, c->precision == NSK_FP32_MIXED, c->b, -dt, c->stream);
+      if (r < 0) return r;
+      c->launches += r;
+    }
+    for (int st = 0; st < 5; ++st) {
+      NskLaunch l = {NSK_MODE_LSRK, nullptr, kA[st], kB[st], adaptive ? c->b.dt : nullptr, dt, nullptr};
+      int r = launch_stage(c, l);
+      if (r) return r;
+    }
+  }
+  return sync_and_check(c);
+}
+
+int nsk_diagnostics(nsk_ctx* c, double* mass, double* energy, double* l2) {
+  if (!c) return NSK_ERR_ARG;
+  if (!c->state_set) return NSK_ERR_STATE;
+  NskLaunch l = {NSK_MODE_LIFT, nullptr, 0.0, 0.0, nullptr, 0.0, nullptr};
+  int r = launch_stage(c, l);
+  if (r) return r;
+  r = nsk_launch_diag(c->p, c->dim, c->np, c->precision == NSK_FP32_MIXED, c->b, c->stream);
+  if (r < 0) return r;
+  c->launches += r;
+  double h[3];
+  if (cudaMemcpyAsync(h, c->b.part + 3 * c->b.nparts, sizeof(h), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+    return NSK_ERR_CUDA;
+  r = sync_and_check(c);
+  if (r) return r;
+  if (mass) *mass = h[0];
+  if (energy) *energy = h[1];
+  if (l2) *l2 = sqrt(h[2]);
+  return NSK_OK;
+}
+
+int nsk_get_sizes(nsk_ctx* c, long long* n_elem, int* nodes_per_elem, int* nvar) {
+  if (!c) return NSK_ERR_ARG;
+  if (n_elem) *n_elem = c->E;
+  if (nodes_per_elem) *nodes_per_elem = c->npe;
+  if (nvar) *nvar = c->nvar;
+  return NSK_OK;
+}
+
+long long nsk_launch_count(nsk_ctx* c) { return c ? c->launches : -1; }
+
+int nsk_set_profiling(nsk_ctx* c, int on) {
+  if (!c) return NSK_ERR_ARG;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return NSK_ERR_CUDA;
+  prof_collect(c);
+  c->prof_on = on != 0;
+  return NSK_OK;
+}
+
+int nsk_get_profile(nsk_ctx* c, double* ms, long long* launches, int n, int reset) {
+  if (!c || n < 0) return NSK_ERR_ARG;
+  for (int k = 0; k < n && k < NSK_NKERN; ++k) {
+    if (ms) ms[k] = c->prof_ms[k];
+    if (launches) launches[k] = c->prof_cnt[k];
+  }
+  if (reset)
+    for (int k = 0; k < NSK_NKERN; ++k) {
+      c->prof_ms[k] = 0.0;
+      c->prof_cnt[k] = 0;
+    }
+  return NSK_NKERN;
+}
+
+void nsk_destroy(nsk_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  free_ctx(c);
+}
+
+}  // extern "C"

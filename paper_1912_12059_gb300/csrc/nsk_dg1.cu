@@ -1,0 +1,8 @@
+// nsk_dg1.cu -- instantiation of the stage kernels for dimension 1 (one
+// translation unit per dimension so the library builds in parallel).
+#include "nsk_kernels.cuh"
+
+int nsk_launch_stage_d1(const NskParams& p, int np, bool fp32, const NskBuffers& b, const NskLaunch& l,
+                        cudaStream_t s) {
+  return nsk::launch_stage_np<1>(p, np, fp32, b, l, s);
+}

@@ -1,0 +1,95 @@
+// nsk_internal.h -- shared declarations of the CUDA library (host + device).
+// Not part of the public ABI (include/nsk.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "nsk.h"
+
+#define NSK_MAXNP 6  // polynomial degree N <= 5
+
+// Error-word bits set by kernels (atomicOr) and read back by the host.
+enum : int {
+  NSK_EBIT_RHO = 1,       // density outside (0, 3)
+  NSK_EBIT_SOUND = 2,     // p_alpha'(rho) < 0 (hyperbolicity lost)
+  NSK_EBIT_NAN = 4,       // NaN / Inf met
+  NSK_EBIT_TIMEOUT = 8,   // a bounded device wait expired
+};
+
+// 1D nodal tables of the tensor-product basis (Sec. 3.1), in both precisions.
+// dvol[i*NSK_MAXNP + j] = (w_j / w_i) l_i'(xi_j): weak-form volume operator;
+// lm/lp[j] = l_j(-1) / l_j(+1): prolongation to the faces;
+// lmw/lpw[i] = l_i(-1) / w_i, l_i(+1) / w_i: surface lifting.
+template <typename R>
+struct NskTab {
+  R dvol[NSK_MAXNP * NSK_MAXNP];
+  R lm[NSK_MAXNP], lp[NSK_MAXNP];
+  R lmw[NSK_MAXNP], lpw[NSK_MAXNP];
+  R w[NSK_MAXNP];  // quadrature weights
+};
+
+// Everything a kernel needs besides its buffers; passed by value.
+struct NskParams {
+  long long E;     // number of elements
+  int ne[3];       // elements per direction (1 beyond dim)
+  double rh[3];    // 2 / h_k (Cartesian metric terms)
+  double T, kappa, alpha, beta, mu;
+  double jac;      // J = prod_k h_k / 2
+  int c_diss;      // Lax-Friedrichs jump on c as well
+  NskTab<double> td;
+  NskTab<float> tf;
+};
+
+template <typename R> struct TabSel;
+template <> struct TabSel<double> {
+  __host__ __device__ static const NskTab<double>& get(const NskParams& p) { return p.td; }
+};
+template <> struct TabSel<float> {
+  __host__ __device__ static const NskTab<float>& get(const NskParams& p) { return p.tf; }
+};
+
+// Device buffers of one context (type-erased: FP64 or FP32 per precision mode).
+struct NskBuffers {
+  void* U;       // [nvar][E][npe] state
+  void* K;       // [nvar][E][npe] low-storage RK register
+  void* Q;       // [nq][E][npe] lifted gradients
+  void* Utr;     // [nvar][2d][E][nfn] traces of U on the element's own faces
+  void* FVtr;    // [d+1][2d][E][nfn] face-normal viscous flux traces (own side)
+  void* Fstar;   // [nvar][d][E][nfn] numerical flux on face (e, +k)
+  int* err;      // error word
+  unsigned long long* lam;  // dt reduction target (bits of a non-negative double)
+  double* dt;    // device time step
+  double* part;  // diagnostics partial sums [nblocks][3]
+  int nparts;
+};
+
+// What one stage pipeline launch should do.
+enum { NSK_MODE_RHS = 0, NSK_MODE_LSRK = 1, NSK_MODE_LIFT = 2 };
+
+struct NskLaunch {
+  int mode;
+  void* Rout;              // residual output (mode RHS), precision of the context
+  double A, B;             // LSRK stage coefficients (mode LSRK)
+  const double* dt_dev;    // device dt (NULL: use dt_val)
+  double dt_val;
+  cudaEvent_t* ev;         // NULL, or NSK_NKERN + 1 events bracketing the kernels
+};
+
+#define NSK_NKERN 4  // prolong, lift, face, volume
+
+// Per-dimension launchers (nsk_dg1.cu, nsk_dg2.cu, nsk_dg3.cu). Return the
+// number of kernels launched, or a negative NSK_ERR_* code.
+int nsk_launch_stage_d1(const NskParams& p, int np, bool fp32, const NskBuffers& b, const NskLaunch& l,
+                        cudaStream_t s);
+int nsk_launch_stage_d2(const NskParams& p, int np, bool fp32, const NskBuffers& b, const NskLaunch& l,
+                        cudaStream_t s);
+int nsk_launch_stage_d3(const NskParams& p, int np, bool fp32, const NskBuffers& b, const NskLaunch& l,
+                        cudaStream_t s);
+// dt: reduces max_nodes sum_k (|v_k| + sqrt(p_alpha'))/h_k into b.lam and writes b.dt.
+int nsk_launch_dt(const NskParams& p, int dim, int np, bool fp32, const NskBuffers& b, double cfl,
+                  cudaStream_t s);
+// diagnostics: needs b.Q current (run a LIFT stage first); writes b.part, final sums in b.part[0..2].
+int nsk_launch_diag(const NskParams& p, int dim, int np, bool fp32, const NskBuffers& b, cudaStream_t s);
+// precision conversion of nodal arrays (FP32 mode boundary)
+int nsk_launch_convert(const void* src, bool src64, void* dst, bool dst64, long long n, cudaStream_t s);

@@ -1,0 +1,552 @@
+// nsk_kernels.cuh -- sm_103a kernels of one explicit DGSEM stage of relaxation
+// model II (arXiv:1912.12059, Sec. 2.3 and Sec. 3.1), templated on the arithmetic
+// type R of the DG operator (double, or float with the equation of state in
+// double), the dimension D and the number of nodes per direction NP = N + 1.
+//
+// One stage is four launches:
+//   k_prolong  U -> traces of U on every element face (GL: l_j(+-1) dot a line)
+//   k_lift     U, traces -> BR1 gradients Q of (v, c) and the face-normal
+//              viscous-flux traces of the element's own faces
+//   k_face     traces -> local Lax-Friedrichs convective flux minus the BR1
+//              mean viscous flux, once per face
+//   k_volume   U, Q, face fluxes -> weak-form volume integral, surface lifting,
+//              relaxation sources, then the residual or the fused LSRK update
+// The grid-wide dependencies of BR1 (a face needs both neighbours' traces,
+// twice per residual) are the launch boundaries.
+#pragma once
+
+#include "nsk_internal.h"
+
+namespace nsk {
+
+__host__ __device__ constexpr int ipow(int b, int e) { return e == 0 ? 1 : b * ipow(b, e - 1); }
+
+template <int D, int NP>
+struct Shape {
+  static constexpr int NPE = ipow(NP, D);      // nodes per element
+  static constexpr int NFN = ipow(NP, D - 1);  // nodes per face
+  static constexpr int NV = D + 2;             // conservative variables
+  static constexpr int NW = D + 1;             // lifted primitive variables (v, c)
+  static constexpr int NQ = D * (D + 1);       // gradient components
+  static constexpr int NF = 2 * D;             // faces per element
+  static constexpr int G = (256 / NPE) > 0 ? 256 / NPE : 1;  // elements per block
+  static constexpr int TPB = G * NPE;
+};
+
+// index of node n along direction k
+template <int NP>
+__device__ __forceinline__ int coord(int n, int k) {
+  int s = 1;
+  for (int q = 0; q < k; ++q) s *= NP;
+  return (n / s) % NP;
+}
+
+// face-node index of node n on the faces normal to direction k
+template <int D, int NP>
+__device__ __forceinline__ int face_node(int n, int k) {
+  if (D == 1) return 0;
+  const int i0 = n % NP, i1 = (n / NP) % NP;
+  if (D == 2) return k == 0 ? i1 : i0;
+  const int i2 = n / (NP * NP);
+  return k == 0 ? i1 + NP * i2 : (k == 1 ? i0 + NP * i2 : i0 + NP * i1);
+}
+
+// first node of the line in direction k through face node fn
+template <int D, int NP>
+__device__ __forceinline__ int line_base(int fn, int k) {
+  if (D == 1) return 0;
+  if (D == 2) return k == 0 ? fn * NP : fn;
+  const int a = fn % NP, b = fn / NP;
+  return k == 0 ? NP * (a + NP * b) : (k == 1 ? a + NP * NP * b : a + NP * b);
+}
+
+template <int NP>
+__device__ __forceinline__ int node_stride(int k) {
+  return k == 0 ? 1 : (k == 1 ? NP : NP * NP);
+}
+
+// periodic neighbour of element e in direction k, side dir = -1 / +1
+__device__ __forceinline__ long long nbr_elem(const NskParams& p, long long e, int k, int dir) {
+  long long s = 1;
+  for (int q = 0; q < k; ++q) s *= p.ne[q];
+  const int n = p.ne[k];
+  const int c = (int)((e / s) % n);
+  int cn = c + dir;
+  cn += (cn < 0) ? n : 0;
+  cn -= (cn >= n) ? n : 0;
+  return e + (long long)(cn - c) * s;
+}
+
+// ---- Van-der-Waals EoS, Sec. 2.1 (reduced: p = 8 T rho / (3 - rho) - 3 rho^2), always FP64 ----
+__device__ __forceinline__ double eos_p_alpha(const NskParams& p, double rho) {
+  // modified pressure p + alpha rho^2 / 2, Eq. (modified_pressure)
+  return 8.0 * p.T * rho / (3.0 - rho) - 3.0 * rho * rho + 0.5 * p.alpha * rho * rho;
+}
+__device__ __forceinline__ double eos_dp_alpha(const NskParams& p, double rho) {
+  const double q = 3.0 - rho;
+  return 24.0 * p.T / (q * q) - 6.0 * rho + p.alpha * rho;
+}
+__device__ __forceinline__ double eos_free_energy(const NskParams& p, double rho) {
+  // W = rho R T ln(rho / (1 - b rho)) - a rho^2, Eq. (vdw_freeenergy)
+  return (8.0 / 3.0) * p.T * rho * log(3.0 * rho / (3.0 - rho)) - 3.0 * rho * rho;
+}
+__device__ __forceinline__ int rho_flags(double rho) {
+  if (rho > 0.0 && rho < 3.0) return 0;
+  return (rho != rho) ? (NSK_EBIT_RHO | NSK_EBIT_NAN) : NSK_EBIT_RHO;
+}
+
+// --------------------------------------------------------------------------
+// k_prolong: U -> Utr[v][slot][E][nfn], slot = 2k + (0: face xi_k=-1, 1: xi_k=+1)
+// --------------------------------------------------------------------------
+template <typename R, int D, int NP>
+__global__ void __launch_bounds__(256) k_prolong(const NskParams p, const R* __restrict__ U, R* __restrict__ Utr) {
+  using S = Shape<D, NP>;
+  const auto& t = TabSel<R>::get(p);
+  const long long nitems = p.E * S::NF * S::NFN;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= nitems) return;
+  const int fn = (int)(idx % S::NFN);
+  const long long r = idx / S::NFN;
+  const long long e = r % p.E;
+  const int slot = (int)(r / p.E);
+  const int k = slot >> 1;
+  const R* L = (slot & 1) ? t.lp : t.lm;
+  const int n0 = line_base<D, NP>(fn, k), st = node_stride<NP>(k);
+  const long long nn = p.E * S::NPE;
+  const R* u = U + e * S::NPE + n0;
+#pragma unroll
+  for (int v = 0; v < S::NV; ++v) {
+    R acc = 0;
+#pragma unroll
+    for (int j = 0; j < NP; ++j) acc += L[j] * u[v * nn + j * st];
+    Utr[((long long)(v * S::NF + slot) * p.E + e) * S::NFN + fn] = acc;
+  }
+}
+
+// --------------------------------------------------------------------------
+// k_lift: BR1 lifting (Sec. 3.1) in weak form with the central flux,
+//   Q_{k,w}(i) = (2/h_k) [ -sum_j (w_j/w_i) l_i'(xi_j) w_j
+//                          + (w*_{k,+} l_i(1) - w*_{k,-} l_i(-1)) / w_i ],
+// w = (v, c) from the conservative traces on both sides of each face; then
+// the face-normal viscous flux F^v_k = (tau_{.k}, (kappa/beta) c_{x_k}) on the
+// element's own faces for the face kernel.
+// --------------------------------------------------------------------------
+template <typename R, int D, int NP>
+__global__ void __launch_bounds__(Shape<D, NP>::TPB)
+    k_lift(const NskParams p, const R* __restrict__ U, const R* __restrict__ Utr, R* __restrict__ Q,
+           R* __restrict__ FVtr, int* __restrict__ err) {
+  using S = Shape<D, NP>;
+  constexpr int G = S::G, NPE = S::NPE, NFN = S::NFN, NW = S::NW, NF = S::NF, NV = S::NV, NQ = S::NQ;
+  constexpr int SM_A = G * NW * NPE + G * NF * NW * NFN;
+  constexpr int SM_B = G * D * NW * NPE;
+  __shared__ R sm[SM_A > SM_B ? SM_A : SM_B];
+  R* sw = sm;                  // [G][NW][NPE] primitive variables at the nodes
+  R* sws = sm + G * NW * NPE;  // [G][NF][NW][NFN] central flux w* on the faces
+  const auto& t = TabSel<R>::get(p);
+  const int le = threadIdx.x / NPE, n = threadIdx.x % NPE;
+  const long long e = (long long)blockIdx.x * G + le;
+  const bool valid = e < p.E;
+  const long long nn = p.E * NPE;
+  int eflag = 0;
+
+  if (valid) {
+    const R rho = U[e * NPE + n];
+    eflag |= rho_flags((double)rho);
+    const R inv = R(1) / rho;
+#pragma unroll
+    for (int a = 0; a < D; ++a) sw[(le * NW + a) * NPE + n] = U[(1 + a) * nn + e * NPE + n] * inv;
+    sw[(le * NW + D) * NPE + n] = U[(D + 1) * nn + e * NPE + n];
+    for (int it = n; it < NF * NFN; it += NPE) {
+      const int slot = it / NFN, fn = it % NFN, k = slot >> 1, s = slot & 1;
+      const long long en = nbr_elem(p, e, k, s ? 1 : -1);
+      const int oslot = 2 * k + (1 - s);
+      R uo[NV], un[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        uo[v] = Utr[((long long)(v * NF + slot) * p.E + e) * NFN + fn];
+        un[v] = Utr[((long long)(v * NF + oslot) * p.E + en) * NFN + fn];
+      }
+      eflag |= rho_flags((double)uo[0]) | rho_flags((double)un[0]);
+      const R io = R(1) / uo[0], in = R(1) / un[0];
+      R* ws = sws + ((le * NF + slot) * NW) * NFN + fn;
+#pragma unroll
+      for (int a = 0; a < D; ++a) ws[a * NFN] = R(0.5) * (uo[1 + a] * io + un[1 + a] * in);
+      ws[D * NFN] = R(0.5) * (uo[D + 1] + un[D + 1]);
+    }
+  }
+  __syncthreads();
+
+  R q[NQ];
+  if (valid) {
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const int i = coord<NP>(n, k), fn = face_node<D, NP>(n, k);
+      const int n0 = line_base<D, NP>(fn, k), st = node_stride<NP>(k);
+      const R rh = (R)p.rh[k];
+#pragma unroll
+      for (int w = 0; w < NW; ++w) {
+        const R* wl = sw + (le * NW + w) * NPE + n0;
+        R vol = 0;
+#pragma unroll
+        for (int j = 0; j < NP; ++j) vol += t.dvol[i * NSK_MAXNP + j] * wl[j * st];
+        const R wp = sws[((le * NF + 2 * k + 1) * NW + w) * NFN + fn];
+        const R wm = sws[((le * NF + 2 * k) * NW + w) * NFN + fn];
+        const R surf = wp * t.lpw[i] - wm * t.lmw[i];
+        q[k * NW + w] = rh * (surf - vol);
+        Q[(long long)(k * NW + w) * nn + e * NPE + n] = q[k * NW + w];
+      }
+    }
+  }
+  __syncthreads();  // shared memory is reused below
+
+  R* sfv = sm;  // [G][D][NW][NPE] viscous flux F^v_k at the nodes
+  if (valid) {
+    R div = 0;
+#pragma unroll
+    for (int a = 0; a < D; ++a) div += q[a * NW + a];
+    const R mu = (R)p.mu, kb = (R)(p.kappa / p.beta);
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        R tau = q[k * NW + a] + q[a * NW + k];
+        if (a == k) tau -= R(2.0 / 3.0) * div;
+        sfv[((le * D + k) * NW + a) * NPE + n] = mu * tau;
+      }
+      sfv[((le * D + k) * NW + D) * NPE + n] = kb * q[k * NW + D];
+    }
+  }
+  __syncthreads();
+
+  if (valid) {
+    for (int it = n; it < NF * NFN; it += NPE) {
+      const int slot = it / NFN, fn = it % NFN, k = slot >> 1;
+      const R* L = (slot & 1) ? t.lp : t.lm;
+      const int n0 = line_base<D, NP>(fn, k), st = node_stride<NP>(k);
+#pragma unroll
+      for (int c = 0; c < NW; ++c) {
+        const R* f = sfv + ((le * D + k) * NW + c) * NPE + n0;
+        R acc = 0;
+#pragma unroll
+        for (int j = 0; j < NP; ++j) acc += L[j] * f[j * st];
+        FVtr[((long long)(c * NF + slot) * p.E + e) * NFN + fn] = acc;
+      }
+    }
+  }
+  if (eflag) atomicOr(err, eflag);
+}
+
+// --------------------------------------------------------------------------
+// k_face: numerical flux on face (e, +k) between e (left, its +1 face) and its
+// right neighbour (its -1 face):
+//   F* = (F^c_k(U_L) + F^c_k(U_R))/2 - lambda/2 (U_R - U_L) - (F^v_L + F^v_R)/2,
+//   lambda = max(|v_{L,k}| + sqrt(p_alpha'(rho_L)), |v_{R,k}| + sqrt(p_alpha'(rho_R)))
+// (local Lax-Friedrichs with the model II wave speeds, Eq. parabolic_eigenvalues_model2;
+// BR1 viscous flux). The jump term acts on rho and momentum (c has no convective flux)
+// unless c_diss is set. EoS and wave speed in FP64.
+// --------------------------------------------------------------------------
+template <typename R, int D, int NP>
+__global__ void __launch_bounds__(256) k_face(const NskParams p, const R* __restrict__ Utr,
+                                              const R* __restrict__ FVtr, R* __restrict__ Fstar,
+                                              int* __restrict__ err) {
+  using S = Shape<D, NP>;
+  constexpr int NFN = S::NFN, NF = S::NF, NV = S::NV, NW = S::NW;
+  const long long nitems = (long long)D * p.E * NFN;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= nitems) return;
+  const int fn = (int)(idx % NFN);
+  const long long r = idx / NFN;
+  const long long e = r % p.E;
+  const int k = (int)(r / p.E);
+  const long long eR = nbr_elem(p, e, k, 1);
+  R UL[NV], UR[NV], VL[NW], VR[NW];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    UL[v] = Utr[((long long)(v * NF + 2 * k + 1) * p.E + e) * NFN + fn];
+    UR[v] = Utr[((long long)(v * NF + 2 * k) * p.E + eR) * NFN + fn];
+  }
+#pragma unroll
+  for (int c = 0; c < NW; ++c) {
+    VL[c] = FVtr[((long long)(c * NF + 2 * k + 1) * p.E + e) * NFN + fn];
+    VR[c] = FVtr[((long long)(c * NF + 2 * k) * p.E + eR) * NFN + fn];
+  }
+  const double rl = (double)UL[0], rr = (double)UR[0];
+  int eflag = rho_flags(rl) | rho_flags(rr);
+  const double dl = eos_dp_alpha(p, rl), dr = eos_dp_alpha(p, rr);
+  if (!(dl >= 0.0) || !(dr >= 0.0)) eflag |= NSK_EBIT_SOUND;
+  const R pl = (R)eos_p_alpha(p, rl), pr = (R)eos_p_alpha(p, rr);
+  const R il = R(1) / UL[0], ir = R(1) / UR[0];
+  const double vl = (double)(UL[1 + k] * il), vr = (double)(UR[1 + k] * ir);
+  const double lam_l = fabs(vl) + sqrt(dl), lam_r = fabs(vr) + sqrt(dr);
+  const R lam = (R)(lam_l > lam_r ? lam_l : lam_r);
+  R F[NV];
+  F[0] = R(0.5) * (UL[1 + k] + UR[1 + k]);
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    R fl = UL[1 + k] * (UL[1 + a] * il), fr = UR[1 + k] * (UR[1 + a] * ir);
+    if (a == k) {
+      fl += pl;
+      fr += pr;
+    }
+    F[1 + a] = R(0.5) * (fl + fr) - R(0.5) * (VL[a] + VR[a]);
+  }
+  F[D + 1] = -R(0.5) * (VL[D] + VR[D]);
+  const int ndiss = p.c_diss ? NV : NV - 1;
+  for (int v = 0; v < ndiss; ++v) F[v] -= R(0.5) * lam * (UR[v] - UL[v]);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) Fstar[((long long)(v * D + k) * p.E + e) * NFN + fn] = F[v];
+  if (eflag) atomicOr(err, eflag);
+}
+
+// --------------------------------------------------------------------------
+// k_volume: weak-form volume integral and surface lifting (Eq. weakformulation),
+//   R_i = sum_k (2/h_k) [ sum_j (w_j/w_i) l_i'(xi_j) F_k(U_j, Q_j)
+//                         - (F*_{k,+} l_i(1) - F*_{k,-} l_i(-1)) / w_i ] + S_i,
+// F_k = F^c_k - F^v_k, S = (0, alpha rho grad c, (alpha/beta)(rho - c)); then
+// mode RHS: Rout = R; mode LSRK: K <- A K + dt R, U <- U + B K.
+// --------------------------------------------------------------------------
+template <typename R, int D, int NP>
+__global__ void __launch_bounds__(Shape<D, NP>::TPB)
+    k_volume(const NskParams p, R* __restrict__ U, const R* __restrict__ Q, const R* __restrict__ Fstar,
+             R* __restrict__ K, R* __restrict__ Rout, const int mode, const double A, const double B,
+             const double* __restrict__ dtp, const double dtv) {
+  using S = Shape<D, NP>;
+  constexpr int G = S::G, NPE = S::NPE, NFN = S::NFN, NW = S::NW, NV = S::NV, NQ = S::NQ;
+  __shared__ R sf[G * D * NV * NPE];  // [G][D][NV][NPE] fluxes F_k at the nodes
+  const auto& t = TabSel<R>::get(p);
+  const int le = threadIdx.x / NPE, n = threadIdx.x % NPE;
+  const long long e = (long long)blockIdx.x * G + le;
+  const bool valid = e < p.E;
+  const long long nn = p.E * NPE;
+  const long long g = e * NPE + n;
+
+  R u[NV], q[NQ];
+  if (valid) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) u[v] = U[v * nn + g];
+#pragma unroll
+    for (int c = 0; c < NQ; ++c) q[c] = Q[c * nn + g];
+    const R inv = R(1) / u[0];
+    const R pa = (R)eos_p_alpha(p, (double)u[0]);
+    R div = 0;
+#pragma unroll
+    for (int a = 0; a < D; ++a) div += q[a * NW + a];
+    const R mu = (R)p.mu, kb = (R)(p.kappa / p.beta);
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      R* f = sf + ((le * D + k) * NV) * NPE + n;
+      f[0] = u[1 + k];
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        R fc = u[1 + k] * (u[1 + a] * inv);
+        if (a == k) fc += pa;
+        R tau = q[k * NW + a] + q[a * NW + k];
+        if (a == k) tau -= R(2.0 / 3.0) * div;
+        f[(1 + a) * NPE] = fc - mu * tau;
+      }
+      f[(D + 1) * NPE] = -(kb * q[k * NW + D]);
+    }
+  }
+  __syncthreads();
+  if (!valid) return;
+
+  long long eL[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) eL[k] = nbr_elem(p, e, k, -1);
+  R res[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    R acc = 0;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const int i = coord<NP>(n, k), fn = face_node<D, NP>(n, k);
+      const int n0 = line_base<D, NP>(fn, k), st = node_stride<NP>(k);
+      const R* f = sf + ((le * D + k) * NV + v) * NPE + n0;
+      R vol = 0;
+#pragma unroll
+      for (int j = 0; j < NP; ++j) vol += t.dvol[i * NSK_MAXNP + j] * f[j * st];
+      const R fp = Fstar[((long long)(v * D + k) * p.E + e) * NFN + fn];
+      const R fm = Fstar[((long long)(v * D + k) * p.E + eL[k]) * NFN + fn];
+      acc += (R)p.rh[k] * (vol - (fp * t.lpw[i] - fm * t.lmw[i]));
+    }
+    res[v] = acc;
+  }
+  const R alpha = (R)p.alpha;
+#pragma unroll
+  for (int a = 0; a < D; ++a) res[1 + a] += alpha * u[0] * q[a * NW + D];
+  res[D + 1] += (R)(p.alpha / p.beta) * (u[0] - u[D + 1]);
+
+  if (mode == NSK_MODE_RHS) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Rout[v * nn + g] = res[v];
+  } else {
+    const R dt = (R)(dtp ? *dtp : dtv);
+    const R a = (R)A, b = (R)B;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const R kv = a * K[v * nn + g] + dt * res[v];
+      K[v * nn + g] = kv;
+      U[v * nn + g] = u[v] + b * kv;
+    }
+  }
+}
+
+// --------------------------------------------------------------------------
+// k_dt: max over nodes of sum_k (|v_k| + sqrt(p_alpha'(rho))) / h_k (FP64), as
+// the bits of a non-negative double (monotone as unsigned integers).
+// --------------------------------------------------------------------------
+template <typename R, int D>
+__global__ void __launch_bounds__(256) k_dt(const NskParams p, const long long nn, const R* __restrict__ U,
+                                            unsigned long long* __restrict__ lam, int* __restrict__ err) {
+  double m = 0.0;
+  int eflag = 0;
+  for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < nn; g += (long long)gridDim.x * blockDim.x) {
+    const double rho = (double)U[g];
+    eflag |= rho_flags(rho);
+    const double dp = eos_dp_alpha(p, rho);
+    if (!(dp >= 0.0)) eflag |= NSK_EBIT_SOUND;
+    const double a = sqrt(dp);
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < D; ++k) s += (fabs((double)U[(1 + k) * nn + g] / rho) + a) * (0.5 * p.rh[k]);
+    m = s > m ? s : m;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const double y = __shfl_xor_sync(0xffffffffu, m, o);
+    m = y > m ? y : m;
+  }
+  __shared__ double red[8];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = red[w] > m ? red[w] : m;
+    atomicMax(lam, (unsigned long long)__double_as_longlong(m));
+  }
+  if (eflag) atomicOr(err, eflag);
+}
+
+// dt = min(convective, viscous, source) bounds; see nsk_compute_dt in nsk.h
+static __global__ void k_dt_final(const NskParams p, const int dim, const int N, const double cfl,
+                           const unsigned long long* __restrict__ lam, double* __restrict__ dt) {
+  const double lmax = __longlong_as_double((long long)*lam);
+  const double tn = 2.0 * N + 1.0;
+  double r = cfl / (tn * lmax);
+  const double lamv = p.mu > p.kappa / p.beta ? p.mu : p.kappa / p.beta;
+  double ih2 = 0.0;
+  for (int k = 0; k < dim; ++k) ih2 += 0.25 * p.rh[k] * p.rh[k];
+  if (lamv > 0.0) {
+    const double dv = cfl / (tn * tn * lamv * ih2);
+    r = dv < r ? dv : r;
+  }
+  const double ds = cfl * 4.6 * p.beta / p.alpha;
+  r = ds < r ? ds : r;
+  *dt = r;
+}
+
+// --------------------------------------------------------------------------
+// k_diag: per-block partial quadrature sums (mass, energy, ||rho - c||^2), FP64,
+// summed in a fixed order by k_diag_final (deterministic).
+// --------------------------------------------------------------------------
+template <typename R, int D, int NP>
+__global__ void __launch_bounds__(256) k_diag(const NskParams p, const R* __restrict__ U, const R* __restrict__ Q,
+                                              double* __restrict__ part) {
+  using S = Shape<D, NP>;
+  const long long nn = p.E * S::NPE;
+  double sm = 0.0, se = 0.0, sl = 0.0;
+  for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < nn; g += (long long)gridDim.x * blockDim.x) {
+    const int n = (int)(g % S::NPE);
+    double wq = p.jac;
+#pragma unroll
+    for (int k = 0; k < D; ++k) wq *= p.td.w[coord<NP>(n, k)];
+    const double rho = (double)U[g], c = (double)U[(D + 1) * nn + g];
+    double m2 = 0.0, g2 = 0.0;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      const double m = (double)U[(1 + a) * nn + g];
+      const double gc = (double)Q[(long long)(a * S::NW + D) * nn + g];
+      m2 += m * m;
+      g2 += gc * gc;
+    }
+    sm += wq * rho;
+    se += wq * (m2 / (2.0 * rho) + eos_free_energy(p, rho) + 0.5 * p.alpha * (rho - c) * (rho - c) +
+                0.5 * p.kappa * g2);
+    sl += wq * (rho - c) * (rho - c);
+  }
+  __shared__ double red[3][256];
+  red[0][threadIdx.x] = sm;
+  red[1][threadIdx.x] = se;
+  red[2][threadIdx.x] = sl;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s)
+      for (int c = 0; c < 3; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int c = 0; c < 3; ++c) part[blockIdx.x * 3 + c] = red[c][0];
+}
+
+static __global__ void __launch_bounds__(256) k_diag_final(const int nparts, double* __restrict__ part) {
+  __shared__ double red[3][256];
+  double s[3] = {0.0, 0.0, 0.0};
+  for (int b = threadIdx.x; b < nparts; b += blockDim.x)
+    for (int c = 0; c < 3; ++c) s[c] += part[b * 3 + c];
+  for (int c = 0; c < 3; ++c) red[c][threadIdx.x] = s[c];
+  __syncthreads();
+  for (int st = 128; st > 0; st >>= 1) {
+    if ((int)threadIdx.x < st)
+      for (int c = 0; c < 3; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int c = 0; c < 3; ++c) part[nparts * 3 + c] = red[c][0];
+}
+
+// ---- launch helpers ------------------------------------------------------
+inline unsigned grid_for(long long items, int tpb) { return (unsigned)((items + tpb - 1) / tpb); }
+
+template <typename R, int D, int NP>
+int launch_stage(const NskParams& p, const NskBuffers& b, const NskLaunch& l, cudaStream_t s) {
+  using S = Shape<D, NP>;
+  int nl = 0;
+  if (l.ev) cudaEventRecord(l.ev[0], s);
+  const long long ptems = p.E * S::NF * S::NFN;
+  k_prolong<R, D, NP><<<grid_for(ptems, 256), 256, 0, s>>>(p, (const R*)b.U, (R*)b.Utr);
+  if (l.ev) cudaEventRecord(l.ev[1], s);
+  ++nl;
+  const unsigned eb = (unsigned)((p.E + S::G - 1) / S::G);
+  k_lift<R, D, NP><<<eb, S::TPB, 0, s>>>(p, (const R*)b.U, (const R*)b.Utr, (R*)b.Q, (R*)b.FVtr, b.err);
+  if (l.ev) cudaEventRecord(l.ev[2], s);
+  ++nl;
+  if (l.mode != NSK_MODE_LIFT) {
+    const long long ftems = (long long)D * p.E * S::NFN;
+    k_face<R, D, NP><<<grid_for(ftems, 256), 256, 0, s>>>(p, (const R*)b.Utr, (const R*)b.FVtr, (R*)b.Fstar, b.err);
+    if (l.ev) cudaEventRecord(l.ev[3], s);
+    ++nl;
+    k_volume<R, D, NP><<<eb, S::TPB, 0, s>>>(p, (R*)b.U, (const R*)b.Q, (const R*)b.Fstar, (R*)b.K, (R*)l.Rout,
+                                            l.mode, l.A, l.B, l.dt_dev, l.dt_val);
+    if (l.ev) cudaEventRecord(l.ev[4], s);
+    ++nl;
+  }
+  if (cudaGetLastError() != cudaSuccess) return NSK_ERR_CUDA;
+  return nl;
+}
+
+template <int D>
+int launch_stage_np(const NskParams& p, int np, bool fp32, const NskBuffers& b, const NskLaunch& l, cudaStream_t s) {
+  switch (np) {
+#define NSK_CASE(NPV)                                                                                     \
+  case NPV:                                                                                               \
+    return fp32 ? launch_stage<float, D, NPV>(p, b, l, s) : launch_stage<double, D, NPV>(p, b, l, s);
+    NSK_CASE(2)
+    NSK_CASE(3)
+    NSK_CASE(4)
+    NSK_CASE(5)
+    NSK_CASE(6)
+#undef NSK_CASE
+    default:
+      return NSK_ERR_ARG;
+  }
+}
+
+}  // namespace nsk

@@ -47,6 +47,8 @@ SIGNATURES = {
     "nsk_diagnostics": (C.c_int, [C.c_void_p, _dp, _dp, _dp]),
     "nsk_get_sizes": (C.c_int, [C.c_void_p, C.POINTER(C.c_longlong), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "nsk_launch_count": (C.c_longlong, [C.c_void_p]),
+    "nsk_set_profiling": (C.c_int, [C.c_void_p, C.c_int]),
+    "nsk_get_profile": (C.c_int, [C.c_void_p, _dp, C.POINTER(C.c_longlong), C.c_int, C.c_int]),
     "nsk_error_string": (C.c_char_p, [C.c_int]),
     "nsk_destroy": (None, [C.c_void_p]),
 }
@@ -222,6 +224,20 @@ class Solver:
         m, e, l2 = C.c_double(), C.c_double(), C.c_double()
         _check(load_library().nsk_diagnostics(self.ctx, C.byref(m), C.byref(e), C.byref(l2)), "nsk_diagnostics")
         return m.value, e.value, l2.value
+
+    KERNELS = ("k_prolong", "k_lift", "k_face", "k_volume")
+
+    def set_profiling(self, on=True):
+        _check(load_library().nsk_set_profiling(self.ctx, int(bool(on))), "nsk_set_profiling")
+
+    def get_profile(self, reset=False):
+        """{kernel: (total ms, launches)} accumulated while profiling was on."""
+        ms = (C.c_double * 4)()
+        cnt = (C.c_longlong * 4)()
+        n = load_library().nsk_get_profile(self.ctx, ms, cnt, 4, int(bool(reset)))
+        if n < 0:
+            raise NskError(n, "nsk_get_profile")
+        return {self.KERNELS[k]: (ms[k], cnt[k]) for k in range(min(n, 4))}
 
     @property
     def launch_count(self):

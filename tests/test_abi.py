@@ -1,0 +1,70 @@
+"""The C-ABI library builds, loads and exports every symbol include/nsk.h declares
+(no GPU: only calls that fail argument validation before touching CUDA)."""
+import ctypes as C
+import re
+import subprocess
+from pathlib import Path
+
+import pytest
+
+ROOT = Path(__file__).resolve().parent.parent
+
+
+def _declared():
+    text = (ROOT / "include" / "nsk.h").read_text()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(nsk_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for required in ("nsk_init_mesh", "nsk_set_params", "nsk_set_state", "nsk_rhs", "nsk_step", "nsk_get_state"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(nsk_lib):
+    from paper_1912_12059_gb300 import nsk
+
+    for name in _declared():
+        assert hasattr(nsk_lib, name), name
+        assert name in nsk.SIGNATURES, f"binding lacks {name}"
+    out = subprocess.run(["nm", "-D", "--defined-only", str(nsk.LIB_PATH)], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\b(nsk_[a-z0-9_]+)\b", out))
+    assert set(_declared()) <= exported
+    assert not re.search(r"\borc_", out), "product library must not contain oracle code"
+
+
+def test_error_strings_and_argument_validation(nsk_lib):
+    from paper_1912_12059_gb300 import nsk
+
+    assert nsk.error_string(nsk.NSK_ERR_NONPHYSICAL).startswith("non-physical")
+    assert nsk.error_string(12345) == "unknown error"
+    ctx = C.c_void_p()
+    ne = (C.c_int * 3)(4, 4, 4)
+    lo = (C.c_double * 3)(0, 0, 0)
+    hi = (C.c_double * 3)(1, 1, 1)
+    # invalid dimension, degree, node type and precision are rejected before any CUDA call
+    assert nsk_lib.nsk_init_mesh(C.byref(ctx), 4, ne, lo, hi, 3, 0, 0, None) == nsk.NSK_ERR_ARG
+    assert nsk_lib.nsk_init_mesh(C.byref(ctx), 3, ne, lo, hi, 9, 0, 0, None) == nsk.NSK_ERR_ARG
+    assert nsk_lib.nsk_init_mesh(C.byref(ctx), 3, ne, lo, hi, 3, 7, 0, None) == nsk.NSK_ERR_ARG
+    assert nsk_lib.nsk_init_mesh(C.byref(ctx), 3, ne, lo, hi, 3, 0, 5, None) == nsk.NSK_ERR_ARG
+    bad_hi = (C.c_double * 3)(0, 1, 1)
+    assert nsk_lib.nsk_init_mesh(C.byref(ctx), 3, ne, lo, bad_hi, 3, 0, 0, None) == nsk.NSK_ERR_ARG
+    assert nsk_lib.nsk_set_params(None, 0.85, 1e-4, 1e3, 1e-3, 1e-3) == nsk.NSK_ERR_ARG
+    assert nsk_lib.nsk_launch_count(None) == -1
+    nsk_lib.nsk_destroy(None)
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    from paper_1912_12059_gb300 import nsk
+
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        nsk.load_library(tmp_path / "absent.so")
+
+
+def test_product_never_imports_the_oracle():
+    pkg = ROOT / "paper_1912_12059_gb300"
+    for f in list(pkg.rglob("*.py")) + list(pkg.rglob("*.cu")) + list(pkg.rglob("*.cuh")) + list(pkg.rglob("*.h")):
+        text = f.read_text()
+        assert not re.search(r"^\s*(import|from)\s+oracle\b", text, flags=re.M), f
+        assert "nsk_oracle" not in text, f
