@@ -18,17 +18,41 @@ pytestmark = pytest.mark.gpu
 
 def make_pair(dim, ne, N, nt=0, lo=None, hi=None, precision=nsk.NSK_FP64, **params):
     prm = dict(T=0.85, kappa=1e-4, alpha=1e3, beta=1e-3, mu=1e-3)
+    cdiss = params.pop("c_dissipation", 0)
     prm.update(params)
     lo = lo or [0.0] * dim
     hi = hi or [1.0] * dim
     s = nsk.Solver(dim, ne, N, lo, hi, nt, precision)
     s.set_params(**prm)
-    o = O.Oracle(dim, ne, lo, hi, N, nt, **prm)
+    if cdiss:
+        s.set_c_dissipation(True)
+    o = O.Oracle(dim, ne, lo, hi, N, nt, c_dissipation=cdiss, **prm)
     return s, o
 
 
 def rel_err(a, b):
     return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def rhs_tolerance(o, U, R):
+    """Per-variable bound on |R_gpu - R_orc| derived from the arithmetic: the residual is a
+    sum of flux differences scaled by 2/h and the derivative matrix, so rounding in either
+    evaluation is a few ulps of rh * (N+1)^2 * max|flux| (the largest term that cancels),
+    plus 1e-12 of the residual itself. Fluxes: rho -> |m|; momentum -> |m m / rho| + |p_alpha|;
+    c -> (kappa/beta) |grad c|."""
+    d = o.dim
+    s = o.s
+    rh = max(2.0 * o.nelem[k] / (o.hi[k] - o.lo[k]) for k in range(d))
+    rho = U[0]
+    mom = U[1:1 + d]
+    pa = 8 * s.T * rho / (3 - rho) - 3 * rho**2 + 0.5 * s.alpha * rho**2
+    Q = o.lift(U)
+    gc = max(np.abs(Q[k * (d + 1) + d]).max() for k in range(d))
+    F = [np.abs(mom).max()]
+    F += [float((np.abs(mom) * np.abs(mom[a]) / rho).max() + np.abs(pa).max()) for a in range(d)]
+    F += [s.kappa / s.beta * gc]
+    amp = rh * (o.np ** 2)
+    return [1e-12 * np.abs(R[v]).max() + 2e-15 * amp * F[v] for v in range(o.nvar)]
 
 
 OPERATOR_CASES = [
@@ -64,15 +88,15 @@ def test_rhs_parity(gpu, dim, ne, N, nt):
     U = inputs.random_state(o.shape, seed=200 + dim * 10 + N)
     s.set_state(U)
     Rg, Ro = s.rhs(), o.rhs(U)
+    tol = rhs_tolerance(o, U, Ro)
     for v in range(o.nvar):
-        scale = np.abs(Ro[v]).max() + 1e-3 * np.abs(Ro).max()
-        assert np.abs(Rg[v] - Ro[v]).max() <= 1e-12 * scale, v
+        err = np.abs(Rg[v] - Ro[v]).max()
+        assert err <= tol[v], (v, err, tol[v])
     s.close()
 
 
 def test_rhs_parity_c_dissipation(gpu):
     s, o = make_pair(2, (6, 5), 3, 0, c_dissipation=1)
-    s.set_c_dissipation(True)
     U = inputs.random_state(o.shape, seed=7)
     s.set_state(U)
     assert rel_err(s.rhs(), o.rhs(U)) < 1e-12
@@ -233,9 +257,12 @@ def test_full_size_head_on_collision_tiled(gpu):
     s.set_params(T=0.85, kappa=1e-4, alpha=1e3, beta=1e-3, mu=1e-3)
     s.set_state(Ubig)
     Rg = s.rhs()
-    Ro, _ = _tile(o.rhs(U), small, reps)
-    scale = np.abs(Ro).max(axis=(1, 2), keepdims=True) + 1e-3 * np.abs(Ro).max()
-    assert (np.abs(Rg - Ro) <= 1e-12 * scale).all()
+    Rs = o.rhs(U)
+    tol = rhs_tolerance(o, U, Rs)
+    Ro, _ = _tile(Rs, small, reps)
+    for v in range(5):
+        err = float(np.abs(Rg[v] - Ro[v]).max())
+        assert err <= tol[v], (v, err, tol[v])
     dt = o.timestep(U, 0.5)
     s.step(dt, 3)
     Ug = s.get_state()
