@@ -148,6 +148,34 @@ int nsk_get_profile(nsk_ctx* ctx, double* ms, long long* launches, int n, int re
  * the host; every launch of the library's own kernels increments it). */
 long long nsk_launch_count(nsk_ctx* ctx);
 
+/* Allocation-free residual. The paper has no counterpart: this entry point
+ * exists for callers that cannot allocate device memory, e.g. a plugin inside a
+ * host application that owns all device memory through its own pool, or a
+ * loop that must not trigger the device-wide synchronisation a cudaMalloc or
+ * cudaFree implies. It computes the same FP64 residual as nsk_rhs (same
+ * kernels, same layout) for the periodic box described by the arguments
+ * (meaning and validation as in nsk_init_mesh and nsk_set_params, node_type as
+ * there, precision always FP64), from the device array U to the device array
+ * Ut, both [dim+2][E][npe] FP64 and owned by the caller, on cuda_stream (NULL =
+ * legacy default stream). It creates no context and calls no cudaMalloc,
+ * cudaFree or other allocating routine: the intermediate arrays live in one
+ * file-scope device array of nsk_static_scratch_bytes() = 64 MiB, which every
+ * device that loads the library holds until the process exits. Sizes whose
+ * scratch does not fit are rejected with NSK_ERR_ARG: per element the call
+ * needs 8 * (d(d+1) np^d + (2d(2d+3) + d(d+2)) np^(d-1)) bytes (3D, N = 3:
+ * 14976 bytes, so about 4480 elements). The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress, with that device current);
+ * make that first call before any stream capture. Every call shares the array
+ * and it keeps the last call's contents (the error word is cleared at the start
+ * of each call), so calls that overlap on the GPU, on any stream, race and must
+ * be serialised by the caller. The call synchronises cuda_stream once to read
+ * the error word; returns as nsk_rhs. */
+int nsk_rhs_static_scratch(int dim, const int nelem[3], const double lo[3], const double hi[3], int N, int node_type,
+                           double T, double kappa, double alpha, double beta, double mu, const double* U, double* Ut,
+                           void* cuda_stream);
+/* Size in bytes of the file-scope scratch array of nsk_rhs_static_scratch. */
+long long nsk_static_scratch_bytes(void);
+
 /* Human-readable text of an error code; never NULL. */
 const char* nsk_error_string(int code);
 

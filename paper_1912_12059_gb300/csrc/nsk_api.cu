@@ -553,3 +553,119 @@ void nsk_destroy(nsk_ctx* c) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free residual (nsk_rhs_static_scratch). The scratch of the four
+// stage kernels (face traces, lifted gradients, face fluxes, error word) lives
+// in one file-scope device array, so a call allocates nothing. In host code
+// the array's name is only a host-side stand-in: its device address is looked
+// up once per device with cudaGetSymbolAddress and cached.
+// ---------------------------------------------------------------------------
+#define NSK_STATIC_SCRATCH_BYTES (64ull << 20)
+#define NSK_STATIC_MAX_DEVICES 64
+
+static __device__ __align__(256) unsigned char nsk_static_scratch[NSK_STATIC_SCRATCH_BYTES];
+
+namespace {
+
+void* g_static_scratch[NSK_STATIC_MAX_DEVICES];  // device address per device, set on first use
+
+int static_scratch_address(void** out) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return NSK_ERR_CUDA;
+  if (dev < 0 || dev >= NSK_STATIC_MAX_DEVICES) return NSK_ERR_ARG;
+  if (!g_static_scratch[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, nsk_static_scratch) != cudaSuccess || !p) return NSK_ERR_CUDA;
+    g_static_scratch[dev] = p;
+  }
+  *out = g_static_scratch[dev];
+  return NSK_OK;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+extern "C" long long nsk_static_scratch_bytes(void) { return (long long)NSK_STATIC_SCRATCH_BYTES; }
+
+extern "C" int nsk_rhs_static_scratch(int dim, const int nelem[3], const double lo[3], const double hi[3], int N,
+                                      int node_type, double T, double kappa, double alpha, double beta, double mu,
+                                      const double* U, double* Ut, void* cuda_stream) {
+  if (!nelem || !lo || !hi || !U || !Ut) return NSK_ERR_ARG;
+  if (dim < 1 || dim > 3 || N < 1 || N + 1 > NSK_MAXNP) return NSK_ERR_ARG;
+  if (node_type != NSK_NODES_GAUSS && node_type != NSK_NODES_GAUSS_LOBATTO) return NSK_ERR_ARG;
+  if (!(T > 0.0 && T < 1.0) || !(kappa > 0.0) || !(beta > 0.0) || !(mu >= 0.0) || !isfinite(alpha) ||
+      !isfinite(kappa) || !isfinite(beta) || !isfinite(mu) || !(alpha > 3.0 * (1.0 - T)))
+    return NSK_ERR_ARG;
+  const int np = N + 1;
+  long long E = 1, npe = 1, nfn = 1;
+  double h[3];
+  for (int k = 0; k < dim; ++k) {
+    if (nelem[k] < 1 || !(hi[k] > lo[k]) || !isfinite(lo[k]) || !isfinite(hi[k])) return NSK_ERR_ARG;
+    if (E > (1LL << 40) / nelem[k]) return NSK_ERR_ARG;
+    E *= nelem[k];
+    h[k] = (hi[k] - lo[k]) / nelem[k];
+    npe *= np;
+    if (k > 0) nfn *= np;
+  }
+  const long long nn = E * npe;
+  const int nvar = dim + 2, nw = dim + 1, nq = dim * (dim + 1), nf = 2 * dim;
+  // scratch layout: error word | Q | Utr | FVtr | Fstar, each 256-byte aligned
+  const size_t b_err = 256;
+  const size_t b_q = align256(sizeof(double) * (size_t)nq * nn);
+  const size_t b_utr = align256(sizeof(double) * (size_t)nvar * nf * E * nfn);
+  const size_t b_fv = align256(sizeof(double) * (size_t)nw * nf * E * nfn);
+  const size_t b_fs = align256(sizeof(double) * (size_t)nvar * dim * E * nfn);
+  if ((double)b_q + b_utr + b_fv + b_fs + b_err > (double)NSK_STATIC_SCRATCH_BYTES) return NSK_ERR_ARG;
+
+  NskParams p;
+  memset(&p, 0, sizeof(p));
+  double xi[NSK_MAXNP], w[NSK_MAXNP];
+  if (node_type == NSK_NODES_GAUSS)
+    gauss_legendre(np, xi, w);
+  else
+    gauss_lobatto(N, xi, w);
+  p.E = E;
+  p.jac = 1.0;
+  for (int k = 0; k < 3; ++k) {
+    p.ne[k] = k < dim ? nelem[k] : 1;
+    p.rh[k] = k < dim ? 2.0 / h[k] : 0.0;
+    if (k < dim) p.jac *= h[k] / 2.0;
+  }
+  p.T = T;
+  p.kappa = kappa;
+  p.alpha = alpha;
+  p.beta = beta;
+  p.mu = mu;
+  fill_tab<double>(p.td, np, xi, w);
+  fill_tab<float>(p.tf, np, xi, w);
+
+  void* base = nullptr;
+  int st = static_scratch_address(&base);
+  if (st) return st;
+  unsigned char* s8 = (unsigned char*)base;
+  NskBuffers b;
+  memset(&b, 0, sizeof(b));
+  b.U = (void*)U;
+  b.err = (int*)s8;
+  b.Q = s8 + b_err;
+  b.Utr = s8 + b_err + b_q;
+  b.FVtr = s8 + b_err + b_q + b_utr;
+  b.Fstar = s8 + b_err + b_q + b_utr + b_fv;
+  cudaStream_t stream = (cudaStream_t)cuda_stream;
+  if (cudaMemsetAsync(b.err, 0, sizeof(int), stream) != cudaSuccess) return NSK_ERR_CUDA;
+  NskLaunch l = {NSK_MODE_RHS, Ut, 0.0, 0.0, nullptr, 0.0, nullptr};
+  int r;
+  switch (dim) {
+    case 1: r = nsk_launch_stage_d1(p, np, false, b, l, stream); break;
+    case 2: r = nsk_launch_stage_d2(p, np, false, b, l, stream); break;
+    default: r = nsk_launch_stage_d3(p, np, false, b, l, stream); break;
+  }
+  if (r < 0) return r;
+  int herr = 0;
+  if (cudaMemcpyAsync(&herr, b.err, sizeof(int), cudaMemcpyDeviceToHost, stream) != cudaSuccess) return NSK_ERR_CUDA;
+  if (cudaStreamSynchronize(stream) != cudaSuccess) return NSK_ERR_CUDA;
+  if (herr & NSK_EBIT_TIMEOUT) return NSK_ERR_TIMEOUT;
+  return herr ? NSK_ERR_NONPHYSICAL : NSK_OK;
+}

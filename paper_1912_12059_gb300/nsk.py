@@ -49,6 +49,10 @@ SIGNATURES = {
     "nsk_launch_count": (C.c_longlong, [C.c_void_p]),
     "nsk_set_profiling": (C.c_int, [C.c_void_p, C.c_int]),
     "nsk_get_profile": (C.c_int, [C.c_void_p, _dp, C.POINTER(C.c_longlong), C.c_int, C.c_int]),
+    "nsk_rhs_static_scratch": (C.c_int, [C.c_int, C.POINTER(C.c_int), _dp, _dp, C.c_int, C.c_int, C.c_double,
+                                         C.c_double, C.c_double, C.c_double, C.c_double, C.c_void_p, C.c_void_p,
+                                         C.c_void_p]),
+    "nsk_static_scratch_bytes": (C.c_longlong, []),
     "nsk_error_string": (C.c_char_p, [C.c_int]),
     "nsk_destroy": (None, [C.c_void_p]),
 }
@@ -128,6 +132,17 @@ def nsk_set_params(ctx, T, kappa, alpha, beta, mu):
 
 def nsk_set_c_dissipation(ctx, on):
     _check(load_library().nsk_set_c_dissipation(ctx, int(bool(on))), "nsk_set_c_dissipation")
+
+
+def nsk_rhs_static_scratch(dim, nelem, lo, hi, N, node_type, T, kappa, alpha, beta, mu, U, Ut, stream=None):
+    """Residual of the device tensor U into the device tensor Ut without any device allocation
+    (see include/nsk.h); returns the status code (0 = ok)."""
+    ne = (C.c_int * 3)(*(list(nelem) + [1] * (3 - len(nelem))))
+    clo = (C.c_double * 3)(*(list(lo) + [0.0] * (3 - len(lo))))
+    chi = (C.c_double * 3)(*(list(hi) + [1.0] * (3 - len(hi))))
+    return load_library().nsk_rhs_static_scratch(dim, ne, clo, chi, N, node_type, T, kappa, alpha, beta, mu,
+                                                 C.c_void_p(U.data_ptr()), C.c_void_p(Ut.data_ptr()),
+                                                 C.c_void_p(stream) if stream else None)
 
 
 def nsk_destroy(ctx):
