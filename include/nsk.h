@@ -162,8 +162,8 @@ long long nsk_launch_count(nsk_ctx* ctx);
  * file-scope device array of nsk_static_scratch_bytes() = 64 MiB, which every
  * device that loads the library holds until the process exits. Sizes whose
  * scratch does not fit are rejected with NSK_ERR_ARG: per element the call
- * needs 8 * (d(d+1) np^d + (2d(2d+3) + d(d+2)) np^(d-1)) bytes (3D, N = 3:
- * 14976 bytes, so about 4480 elements). The first call on a device looks up the
+ * needs 8 * (d(d+1) np^d + (2d(2d+4) + d(d+2)) np^(d-1)) bytes (3D, N = 3:
+ * 15744 bytes, so about 4260 elements). The first call on a device looks up the
  * array's device address (cudaGetSymbolAddress, with that device current);
  * make that first call before any stream capture. Every call shares the array
  * and it keeps the last call's contents (the error word is cleared at the start

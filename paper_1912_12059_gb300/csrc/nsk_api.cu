@@ -121,6 +121,49 @@ void fill_tab(NskTab<R>& t, int n, const double* x, const double* w) {
   }
 }
 
+// Spinodal densities of the reduced VdW fluid: p'(rho) = 0 <=> rho (3 - rho)^2 = 4 T, one root
+// in (0, 1) and one in (1, 3) for 0 < T < 1 (bisection).
+void spinodal_interval(double T, double* lo, double* hi) {
+  auto g = [T](double r) { return r * (3.0 - r) * (3.0 - r) - 4.0 * T; };
+  double a = 0.0, b = 1.0;  // g(a) < 0 < g(b)
+  for (int it = 0; it < 200; ++it) {
+    const double m = 0.5 * (a + b);
+    (g(m) < 0.0 ? a : b) = m;
+  }
+  *lo = 0.5 * (a + b);
+  a = 1.0;
+  b = 3.0;  // g(a) > 0 > g(b)
+  for (int it = 0; it < 200; ++it) {
+    const double m = 0.5 * (a + b);
+    (g(m) > 0.0 ? a : b) = m;
+  }
+  *hi = 0.5 * (a + b);
+}
+
+// model coefficients of both operator precisions (after the mesh and the parameters are known)
+template <typename R>
+void fill_coef(NskTab<R>& t, const NskParams& p) {
+  for (int k = 0; k < 3; ++k) t.rh[k] = (R)p.rh[k];
+  t.mu = (R)p.mu;
+  t.kb = (R)(p.kappa / p.beta);
+  t.alpha = (R)p.alpha;
+  t.ab = (R)(p.alpha / p.beta);
+}
+
+void set_eos_constants(NskParams& p) {
+  fill_coef<double>(p.td, p);
+  fill_coef<float>(p.tf, p);
+  p.t8 = 8.0 * p.T;
+  p.t24 = 24.0 * p.T;
+  p.pa2 = 0.5 * p.alpha - 3.0;
+  p.dpa1 = p.alpha - 6.0;
+  p.t8f = (float)p.t8;
+  p.t24f = (float)p.t24;
+  p.pa2f = (float)p.pa2;
+  p.dpa1f = (float)p.dpa1;
+  spinodal_interval(p.T, &p.spin_lo, &p.spin_hi);
+}
+
 // Carpenter-Kennedy RK4(3)5[2N] (the published rational coefficients).
 const double kA[5] = {0.0, -567301805773.0 / 1357537059087.0, -2404267990393.0 / 2016746695238.0,
                       -3550918686646.0 / 2091501179385.0, -1275806237668.0 / 842570457699.0};
@@ -337,7 +380,7 @@ int nsk_init_mesh(nsk_ctx** out, int dim, const int nelem[3], const double lo[3]
       {&c->b.U, rs * c->nvar * nn},
       {&c->b.K, rs * c->nvar * nn},
       {&c->b.Q, rs * c->nq * nn},
-      {&c->b.Utr, rs * c->nvar * faces},
+      {&c->b.Utr, rs * (c->nvar + (precision == NSK_FP64 ? TraceComps<double>::extra : 0)) * faces},
       {&c->b.FVtr, rs * (dim + 1) * faces},
       {&c->b.Fstar, rs * c->nvar * c->E * dim * c->nfn},
       {(void**)&c->b.err, sizeof(int)},
@@ -376,6 +419,7 @@ int nsk_set_params(nsk_ctx* c, double T, double kappa, double alpha, double beta
   c->p.alpha = alpha;
   c->p.beta = beta;
   c->p.mu = mu;
+  set_eos_constants(c->p);
   c->params_set = true;
   return NSK_OK;
 }
@@ -614,7 +658,7 @@ extern "C" int nsk_rhs_static_scratch(int dim, const int nelem[3], const double 
   // scratch layout: error word | Q | Utr | FVtr | Fstar, each 256-byte aligned
   const size_t b_err = 256;
   const size_t b_q = align256(sizeof(double) * (size_t)nq * nn);
-  const size_t b_utr = align256(sizeof(double) * (size_t)nvar * nf * E * nfn);
+  const size_t b_utr = align256(sizeof(double) * (size_t)(nvar + TraceComps<double>::extra) * nf * E * nfn);
   const size_t b_fv = align256(sizeof(double) * (size_t)nw * nf * E * nfn);
   const size_t b_fs = align256(sizeof(double) * (size_t)nvar * dim * E * nfn);
   if ((double)b_q + b_utr + b_fv + b_fs + b_err > (double)NSK_STATIC_SCRATCH_BYTES) return NSK_ERR_ARG;
@@ -640,6 +684,7 @@ extern "C" int nsk_rhs_static_scratch(int dim, const int nelem[3], const double 
   p.mu = mu;
   fill_tab<double>(p.td, np, xi, w);
   fill_tab<float>(p.tf, np, xi, w);
+  set_eos_constants(p);
 
   void* base = nullptr;
   int st = static_scratch_address(&base);

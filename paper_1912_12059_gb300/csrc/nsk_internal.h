@@ -27,7 +27,16 @@ struct NskTab {
   R lm[NSK_MAXNP], lp[NSK_MAXNP];
   R lmw[NSK_MAXNP], lpw[NSK_MAXNP];
   R w[NSK_MAXNP];  // quadrature weights
+  // model coefficients in the operator's precision (no per-thread conversions or divisions)
+  R rh[3];         // 2 / h_k
+  R mu, kb, alpha, ab;  // mu, kappa / beta, alpha, alpha / beta
 };
+
+// Components of a face trace: the conservative variables, and in FP64 also
+// 1/rho and 1/(3 - rho) of the trace (shared by the lifting and face kernels,
+// so the FP64 path divides once per trace instead of four times).
+template <typename R> struct TraceComps { static constexpr int extra = 0; };
+template <> struct TraceComps<double> { static constexpr int extra = 2; };
 
 // Everything a kernel needs besides its buffers; passed by value.
 struct NskParams {
@@ -36,6 +45,10 @@ struct NskParams {
   double rh[3];    // 2 / h_k (Cartesian metric terms)
   double T, kappa, alpha, beta, mu;
   double jac;      // J = prod_k h_k / 2
+  // EoS constants: p_alpha = t8 rho q + pa2 rho^2, p_alpha' = t24 q^2 + dpa1 rho, q = 1/(3 - rho)
+  double t8, t24, pa2, dpa1;
+  float t8f, t24f, pa2f, dpa1f;
+  double spin_lo, spin_hi;  // spinodal interval (p' < 0): the FP32 operator evaluates the EoS in FP64 there
   int c_diss;      // Lax-Friedrichs jump on c as well
   NskTab<double> td;
   NskTab<float> tf;
@@ -54,7 +67,7 @@ struct NskBuffers {
   void* U;       // [nvar][E][npe] state
   void* K;       // [nvar][E][npe] low-storage RK register
   void* Q;       // [nq][E][npe] lifted gradients
-  void* Utr;     // [nvar][2d][E][nfn] traces of U on the element's own faces
+  void* Utr;     // [nvar + extra][2d][E][nfn] traces of U on the element's own faces
   void* FVtr;    // [d+1][2d][E][nfn] face-normal viscous flux traces (own side)
   void* Fstar;   // [nvar][d][E][nfn] numerical flux on face (e, +k)
   int* err;      // error word

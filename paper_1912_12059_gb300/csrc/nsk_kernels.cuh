@@ -77,21 +77,66 @@ __device__ __forceinline__ long long nbr_elem(const NskParams& p, long long e, i
   return e + (long long)(cn - c) * s;
 }
 
-// ---- Van-der-Waals EoS, Sec. 2.1 (reduced: p = 8 T rho / (3 - rho) - 3 rho^2), always FP64 ----
-__device__ __forceinline__ double eos_p_alpha(const NskParams& p, double rho) {
-  // modified pressure p + alpha rho^2 / 2, Eq. (modified_pressure)
-  return 8.0 * p.T * rho / (3.0 - rho) - 3.0 * rho * rho + 0.5 * p.alpha * rho * rho;
+// ---- Van-der-Waals EoS, Sec. 2.1 (reduced: p = 8 T rho / (3 - rho) - 3 rho^2) ----
+// Modified pressure p_alpha = p + alpha rho^2 / 2 (Eq. modified_pressure) and its derivative
+// with one reciprocal q = 1 / (3 - rho):
+//   p_alpha = 8 T rho q + (alpha/2 - 3) rho^2,   p_alpha' = 24 T q^2 + (alpha - 6) rho.
+__device__ __forceinline__ double eos_pa64(const NskParams& p, double rho) {
+  const double q = 1.0 / (3.0 - rho);
+  return p.t8 * rho * q + p.pa2 * rho * rho;
 }
-__device__ __forceinline__ double eos_dp_alpha(const NskParams& p, double rho) {
-  const double q = 3.0 - rho;
-  return 24.0 * p.T / (q * q) - 6.0 * rho + p.alpha * rho;
+__device__ __forceinline__ void eos_both64(const NskParams& p, double rho, double& pa, double& dpa) {
+  const double q = 1.0 / (3.0 - rho);
+  pa = p.t8 * rho * q + p.pa2 * rho * rho;
+  dpa = p.t24 * q * q + p.dpa1 * rho;
 }
+// Precision policy of the FP32 operator: FP32 EoS, except inside the spinodal interval and
+// wherever p_alpha' cancels (alpha close to alpha_*), where it is evaluated in FP64.
+__device__ __forceinline__ bool eos_needs64(const NskParams& p, float rho) {
+  return rho > (float)p.spin_lo && rho < (float)p.spin_hi;
+}
+template <typename R> struct Eos;
+template <> struct Eos<double> {
+  __device__ static __forceinline__ double pa(const NskParams& p, double rho) { return eos_pa64(p, rho); }
+  __device__ static __forceinline__ void both(const NskParams& p, double rho, double& pa, double& dpa) {
+    eos_both64(p, rho, pa, dpa);
+  }
+  // with q = 1/(3 - rho) already known
+  __device__ static __forceinline__ double pa_q(const NskParams& p, double rho, double q) {
+    return p.t8 * rho * q + p.pa2 * rho * rho;
+  }
+  __device__ static __forceinline__ void both_q(const NskParams& p, double rho, double q, double& pa, double& dpa) {
+    pa = p.t8 * rho * q + p.pa2 * rho * rho;
+    dpa = p.t24 * q * q + p.dpa1 * rho;
+  }
+};
+template <> struct Eos<float> {
+  __device__ static __forceinline__ float pa(const NskParams& p, float rho) {
+    if (eos_needs64(p, rho)) return (float)eos_pa64(p, (double)rho);
+    const float q = 1.0f / (3.0f - rho);
+    return p.t8f * rho * q + p.pa2f * rho * rho;
+  }
+  __device__ static __forceinline__ void both(const NskParams& p, float rho, float& pa, float& dpa) {
+    if (!eos_needs64(p, rho)) {
+      const float q = 1.0f / (3.0f - rho);
+      const float a = p.t24f * q * q, b = p.dpa1f * rho;
+      pa = p.t8f * rho * q + p.pa2f * rho * rho;
+      dpa = a + b;
+      if (fabsf(dpa) >= 1e-3f * (fabsf(a) + fabsf(b))) return;
+    }
+    double pd, dd;
+    eos_both64(p, (double)rho, pd, dd);
+    pa = (float)pd;
+    dpa = (float)dd;
+  }
+};
 __device__ __forceinline__ double eos_free_energy(const NskParams& p, double rho) {
   // W = rho R T ln(rho / (1 - b rho)) - a rho^2, Eq. (vdw_freeenergy)
   return (8.0 / 3.0) * p.T * rho * log(3.0 * rho / (3.0 - rho)) - 3.0 * rho * rho;
 }
-__device__ __forceinline__ int rho_flags(double rho) {
-  if (rho > 0.0 && rho < 3.0) return 0;
+template <typename R>
+__device__ __forceinline__ int rho_flags(R rho) {
+  if (rho > R(0) && rho < R(3)) return 0;
   return (rho != rho) ? (NSK_EBIT_RHO | NSK_EBIT_NAN) : NSK_EBIT_RHO;
 }
 
@@ -114,12 +159,20 @@ __global__ void __launch_bounds__(256) k_prolong(const NskParams p, const R* __r
   const int n0 = line_base<D, NP>(fn, k), st = node_stride<NP>(k);
   const long long nn = p.E * S::NPE;
   const R* u = U + e * S::NPE + n0;
+  R rho = 0;
 #pragma unroll
   for (int v = 0; v < S::NV; ++v) {
     R acc = 0;
 #pragma unroll
     for (int j = 0; j < NP; ++j) acc += L[j] * u[v * nn + j * st];
     Utr[((long long)(v * S::NF + slot) * p.E + e) * S::NFN + fn] = acc;
+    if (v == 0) rho = acc;
+  }
+  if constexpr (TraceComps<R>::extra > 0) {
+    // one division: d = 1/(rho (3 - rho)) gives 1/rho = (3 - rho) d and 1/(3 - rho) = rho d
+    const R d = R(1) / (rho * (R(3) - rho));
+    Utr[((long long)(S::NV * S::NF + slot) * p.E + e) * S::NFN + fn] = (R(3) - rho) * d;
+    Utr[((long long)((S::NV + 1) * S::NF + slot) * p.E + e) * S::NFN + fn] = rho * d;
   }
 }
 
@@ -151,7 +204,7 @@ __global__ void __launch_bounds__(Shape<D, NP>::TPB)
 
   if (valid) {
     const R rho = U[e * NPE + n];
-    eflag |= rho_flags((double)rho);
+    eflag |= rho_flags(rho);
     const R inv = R(1) / rho;
 #pragma unroll
     for (int a = 0; a < D; ++a) sw[(le * NW + a) * NPE + n] = U[(1 + a) * nn + e * NPE + n] * inv;
@@ -166,8 +219,15 @@ __global__ void __launch_bounds__(Shape<D, NP>::TPB)
         uo[v] = Utr[((long long)(v * NF + slot) * p.E + e) * NFN + fn];
         un[v] = Utr[((long long)(v * NF + oslot) * p.E + en) * NFN + fn];
       }
-      eflag |= rho_flags((double)uo[0]) | rho_flags((double)un[0]);
-      const R io = R(1) / uo[0], in = R(1) / un[0];
+      eflag |= rho_flags(uo[0]) | rho_flags(un[0]);
+      R io, in;
+      if constexpr (TraceComps<R>::extra > 0) {
+        io = Utr[((long long)(NV * NF + slot) * p.E + e) * NFN + fn];
+        in = Utr[((long long)(NV * NF + oslot) * p.E + en) * NFN + fn];
+      } else {
+        io = R(1) / uo[0];
+        in = R(1) / un[0];
+      }
       R* ws = sws + ((le * NF + slot) * NW) * NFN + fn;
 #pragma unroll
       for (int a = 0; a < D; ++a) ws[a * NFN] = R(0.5) * (uo[1 + a] * io + un[1 + a] * in);
@@ -182,7 +242,7 @@ __global__ void __launch_bounds__(Shape<D, NP>::TPB)
     for (int k = 0; k < D; ++k) {
       const int i = coord<NP>(n, k), fn = face_node<D, NP>(n, k);
       const int n0 = line_base<D, NP>(fn, k), st = node_stride<NP>(k);
-      const R rh = (R)p.rh[k];
+      const R rh = t.rh[k];
 #pragma unroll
       for (int w = 0; w < NW; ++w) {
         const R* wl = sw + (le * NW + w) * NPE + n0;
@@ -204,7 +264,7 @@ __global__ void __launch_bounds__(Shape<D, NP>::TPB)
     R div = 0;
 #pragma unroll
     for (int a = 0; a < D; ++a) div += q[a * NW + a];
-    const R mu = (R)p.mu, kb = (R)(p.kappa / p.beta);
+    const R mu = t.mu, kb = t.kb;
 #pragma unroll
     for (int k = 0; k < D; ++k) {
 #pragma unroll
@@ -265,20 +325,29 @@ __global__ void __launch_bounds__(256) k_face(const NskParams p, const R* __rest
     UL[v] = Utr[((long long)(v * NF + 2 * k + 1) * p.E + e) * NFN + fn];
     UR[v] = Utr[((long long)(v * NF + 2 * k) * p.E + eR) * NFN + fn];
   }
+  R pl, dl, pr, dr, il, ir;
+  if constexpr (TraceComps<R>::extra > 0) {
+    il = Utr[((long long)(NV * NF + 2 * k + 1) * p.E + e) * NFN + fn];
+    ir = Utr[((long long)(NV * NF + 2 * k) * p.E + eR) * NFN + fn];
+    const R ql = Utr[((long long)((NV + 1) * NF + 2 * k + 1) * p.E + e) * NFN + fn];
+    const R qr = Utr[((long long)((NV + 1) * NF + 2 * k) * p.E + eR) * NFN + fn];
+    Eos<R>::both_q(p, UL[0], ql, pl, dl);
+    Eos<R>::both_q(p, UR[0], qr, pr, dr);
+  } else {
+    Eos<R>::both(p, UL[0], pl, dl);
+    Eos<R>::both(p, UR[0], pr, dr);
+    il = R(1) / UL[0];
+    ir = R(1) / UR[0];
+  }
 #pragma unroll
   for (int c = 0; c < NW; ++c) {
     VL[c] = FVtr[((long long)(c * NF + 2 * k + 1) * p.E + e) * NFN + fn];
     VR[c] = FVtr[((long long)(c * NF + 2 * k) * p.E + eR) * NFN + fn];
   }
-  const double rl = (double)UL[0], rr = (double)UR[0];
-  int eflag = rho_flags(rl) | rho_flags(rr);
-  const double dl = eos_dp_alpha(p, rl), dr = eos_dp_alpha(p, rr);
-  if (!(dl >= 0.0) || !(dr >= 0.0)) eflag |= NSK_EBIT_SOUND;
-  const R pl = (R)eos_p_alpha(p, rl), pr = (R)eos_p_alpha(p, rr);
-  const R il = R(1) / UL[0], ir = R(1) / UR[0];
-  const double vl = (double)(UL[1 + k] * il), vr = (double)(UR[1 + k] * ir);
-  const double lam_l = fabs(vl) + sqrt(dl), lam_r = fabs(vr) + sqrt(dr);
-  const R lam = (R)(lam_l > lam_r ? lam_l : lam_r);
+  int eflag = rho_flags(UL[0]) | rho_flags(UR[0]);
+  if (!(dl >= R(0)) || !(dr >= R(0))) eflag |= NSK_EBIT_SOUND;
+  const R lam_l = fabs(UL[1 + k] * il) + sqrt(dl), lam_r = fabs(UR[1 + k] * ir) + sqrt(dr);
+  const R lam = lam_l > lam_r ? lam_l : lam_r;
   R F[NV];
   F[0] = R(0.5) * (UL[1 + k] + UR[1 + k]);
 #pragma unroll
@@ -308,8 +377,8 @@ __global__ void __launch_bounds__(256) k_face(const NskParams p, const R* __rest
 template <typename R, int D, int NP>
 __global__ void __launch_bounds__(Shape<D, NP>::TPB)
     k_volume(const NskParams p, R* __restrict__ U, const R* __restrict__ Q, const R* __restrict__ Fstar,
-             R* __restrict__ K, R* __restrict__ Rout, const int mode, const double A, const double B,
-             const double* __restrict__ dtp, const double dtv) {
+             R* __restrict__ K, R* __restrict__ Rout, const int mode, const R A, const R B,
+             const double* __restrict__ dtp, const R dtv) {
   using S = Shape<D, NP>;
   constexpr int G = S::G, NPE = S::NPE, NFN = S::NFN, NW = S::NW, NV = S::NV, NQ = S::NQ;
   __shared__ R sf[G * D * NV * NPE];  // [G][D][NV][NPE] fluxes F_k at the nodes
@@ -326,12 +395,19 @@ __global__ void __launch_bounds__(Shape<D, NP>::TPB)
     for (int v = 0; v < NV; ++v) u[v] = U[v * nn + g];
 #pragma unroll
     for (int c = 0; c < NQ; ++c) q[c] = Q[c * nn + g];
-    const R inv = R(1) / u[0];
-    const R pa = (R)eos_p_alpha(p, (double)u[0]);
+    R inv, pa;
+    if constexpr (TraceComps<R>::extra > 0) {  // FP64: one division for 1/rho and 1/(3 - rho)
+      const R dd = R(1) / (u[0] * (R(3) - u[0]));
+      inv = (R(3) - u[0]) * dd;
+      pa = Eos<R>::pa_q(p, u[0], u[0] * dd);
+    } else {
+      inv = R(1) / u[0];
+      pa = Eos<R>::pa(p, u[0]);
+    }
     R div = 0;
 #pragma unroll
     for (int a = 0; a < D; ++a) div += q[a * NW + a];
-    const R mu = (R)p.mu, kb = (R)(p.kappa / p.beta);
+    const R mu = t.mu, kb = t.kb;
 #pragma unroll
     for (int k = 0; k < D; ++k) {
       R* f = sf + ((le * D + k) * NV) * NPE + n;
@@ -367,21 +443,21 @@ __global__ void __launch_bounds__(Shape<D, NP>::TPB)
       for (int j = 0; j < NP; ++j) vol += t.dvol[i * NSK_MAXNP + j] * f[j * st];
       const R fp = Fstar[((long long)(v * D + k) * p.E + e) * NFN + fn];
       const R fm = Fstar[((long long)(v * D + k) * p.E + eL[k]) * NFN + fn];
-      acc += (R)p.rh[k] * (vol - (fp * t.lpw[i] - fm * t.lmw[i]));
+      acc += t.rh[k] * (vol - (fp * t.lpw[i] - fm * t.lmw[i]));
     }
     res[v] = acc;
   }
-  const R alpha = (R)p.alpha;
+  const R alpha = t.alpha;
 #pragma unroll
   for (int a = 0; a < D; ++a) res[1 + a] += alpha * u[0] * q[a * NW + D];
-  res[D + 1] += (R)(p.alpha / p.beta) * (u[0] - u[D + 1]);
+  res[D + 1] += t.ab * (u[0] - u[D + 1]);
 
   if (mode == NSK_MODE_RHS) {
 #pragma unroll
     for (int v = 0; v < NV; ++v) Rout[v * nn + g] = res[v];
   } else {
-    const R dt = (R)(dtp ? *dtp : dtv);
-    const R a = (R)A, b = (R)B;
+    const R dt = dtp ? (R)*dtp : dtv;
+    const R a = A, b = B;
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       const R kv = a * K[v * nn + g] + dt * res[v];
@@ -403,7 +479,8 @@ __global__ void __launch_bounds__(256) k_dt(const NskParams p, const long long n
   for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < nn; g += (long long)gridDim.x * blockDim.x) {
     const double rho = (double)U[g];
     eflag |= rho_flags(rho);
-    const double dp = eos_dp_alpha(p, rho);
+    double pa, dp;
+    eos_both64(p, rho, pa, dp);
     if (!(dp >= 0.0)) eflag |= NSK_EBIT_SOUND;
     const double a = sqrt(dp);
     double s = 0.0;
@@ -524,7 +601,7 @@ int launch_stage(const NskParams& p, const NskBuffers& b, const NskLaunch& l, cu
     if (l.ev) cudaEventRecord(l.ev[3], s);
     ++nl;
     k_volume<R, D, NP><<<eb, S::TPB, 0, s>>>(p, (R*)b.U, (const R*)b.Q, (const R*)b.Fstar, (R*)b.K, (R*)l.Rout,
-                                            l.mode, l.A, l.B, l.dt_dev, l.dt_val);
+                                            l.mode, (R)l.A, (R)l.B, l.dt_dev, (R)l.dt_val);
     if (l.ev) cudaEventRecord(l.ev[4], s);
     ++nl;
   }

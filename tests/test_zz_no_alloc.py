@@ -60,7 +60,7 @@ def test_static_scratch_rejects_oversized_meshes(gpu):
 
     cap = nsk.load_library().nsk_static_scratch_bytes()
     assert cap == 64 << 20
-    # 3D, N = 3 needs 14976 bytes per element: 20^3 elements do not fit in 64 MiB
+    # 3D, N = 3 needs 15744 bytes per element: 20^3 elements do not fit in 64 MiB
     U = torch.zeros(1, dtype=torch.float64, device=gpu)
     code = nsk.nsk_rhs_static_scratch(3, (20, 20, 20), (0, 0, 0), (1, 1, 1), 3, 0, 0.85, 1e-4, 1e3, 1e-3, 1e-3,
                                       U, U)
