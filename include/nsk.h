@@ -148,6 +148,55 @@ int nsk_get_profile(nsk_ctx* ctx, double* ms, long long* launches, int n, int re
  * the host; every launch of the library's own kernels increments it). */
 long long nsk_launch_count(nsk_ctx* ctx);
 
+/* Stage schedule of a context: tpb = 128 or 256 threads per block for the
+ * element kernels (elements per block = tpb / nodes per element, at least 1),
+ * fused_face = 1 evaluates the face fluxes inside the volume kernel (each
+ * face by both of its elements, bit-identically) instead of a separate face
+ * pass. Default: tpb 256, separate face pass. Every expression that could be
+ * contracted into a fused multiply-add in more than one way is written as an
+ * explicit fma, so results are bit-identical under every schedule. */
+int nsk_set_schedule(nsk_ctx* ctx, int tpb, int fused_face);
+int nsk_get_schedule(nsk_ctx* ctx, int* tpb, int* fused_face);
+/* Autotuner: times one residual evaluation under each of the four schedules
+ * on the context's current state (the state is not modified), keeps the
+ * fastest and returns it (any output may be NULL; ms_out = its time). */
+int nsk_autotune(nsk_ctx* ctx, int* tpb_out, int* fused_out, double* ms_out);
+
+/* Batched execution (many instances, one launch per stage). A batch groups n
+ * existing 3D contexts with N = 3 or 4 and the same precision; meshes may
+ * differ. Each LSRK stage of all instances runs as one persistent cooperative
+ * kernel whose phases (traces, lifting, face fluxes, volume + update) are
+ * separated by a grid barrier with a one-second bounded wait (NSK_ERR_TIMEOUT
+ * on expiry); the five stages of a step are captured once in a CUDA graph and
+ * replayed. The batch snapshots each instance's parameters and buffers at
+ * creation (call nsk_set_params / nsk_set_state before; states may be reset
+ * later through the instances), and the instances must not be used by other
+ * calls while a batch call runs. Results equal those of stepping each
+ * instance alone, bit for bit. The batch has its own stream. */
+typedef struct nsk_batch nsk_batch;
+int nsk_batch_create(nsk_batch** out, int n, nsk_ctx* const* instances);
+/* Advance every instance by nsteps steps. cfl > 0: each instance's dt is
+ * recomputed (FP64 reductions) before every step; cfl <= 0: each instance
+ * keeps the dt of its last nsk_compute_dt or adaptive nsk_step. step_ms, if
+ * not NULL, receives nsteps per-step wall times (ms, CUDA events); every
+ * instance of the batch completes a step within that time. */
+int nsk_batch_step(nsk_batch* batch, int nsteps, double cfl, double* step_ms);
+/* Batch schedule and autotuner (same meaning as for a context). */
+int nsk_batch_set_schedule(nsk_batch* batch, int tpb, int fused_face);
+int nsk_batch_get_schedule(nsk_batch* batch, int* tpb, int* fused_face);
+int nsk_batch_autotune(nsk_batch* batch, int* tpb_out, int* fused_out, double* ms_out);
+/* Persistent-kernel launches issued (graph replays count their launches);
+ * 1 if steps replay a captured CUDA graph, 0 if stages are launched directly. */
+long long nsk_batch_launch_count(nsk_batch* batch);
+int nsk_batch_uses_graph(nsk_batch* batch);
+/* Bound of every grid-barrier wait (default 1 s, at most 60 s). */
+int nsk_batch_set_timeout(nsk_batch* batch, double seconds);
+/* Failure-detection test hook: makes the next grid barrier unreachable, so the
+ * next nsk_batch_step ends every block's bounded wait and returns
+ * NSK_ERR_TIMEOUT; the batch resets its barrier and stays usable. */
+int nsk_batch_poison_barrier(nsk_batch* batch);
+void nsk_batch_destroy(nsk_batch* batch);
+
 /* Allocation-free residual. The paper has no counterpart: this entry point
  * exists for callers that cannot allocate device memory, e.g. a plugin inside a
  * host application that owns all device memory through its own pool, or a

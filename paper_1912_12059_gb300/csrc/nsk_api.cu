@@ -173,28 +173,7 @@ const double kB[5] = {1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612
 
 }  // namespace
 
-struct nsk_ctx {
-  int dim, N, np, npe, nfn, nvar, nq, node_type, precision;
-  long long E, nn;
-  int ne[3];
-  double lo[3], hi[3], h[3];
-  double xi[NSK_MAXNP], w[NSK_MAXNP];
-  cudaStream_t stream;
-  NskParams p;
-  NskBuffers b;
-  void* rbuf;        // residual scratch, context precision, nvar*nn
-  double* stage64;   // FP64 staging for transfers, max(nvar, nq, dim)*nn
-  bool params_set, state_set;
-  long long launches;
-  size_t rsize;      // bytes per value in context precision
-  // per-kernel profiling (nsk_set_profiling)
-  bool prof_on;
-  std::vector<cudaEvent_t> prof_pool;  // groups of NSK_NKERN + 1 events
-  std::vector<int> prof_nk;            // kernels recorded in each used group
-  size_t prof_used;                    // groups recorded since the last sync
-  double prof_ms[NSK_NKERN];
-  long long prof_cnt[NSK_NKERN];
-};
+
 
 namespace {
 
@@ -289,6 +268,8 @@ void free_ctx(nsk_ctx* c) {
 
 }  // namespace
 
+int nsk_ctx_launch_stage(nsk_ctx* c, NskLaunch l) { return launch_stage(c, l); }
+
 extern "C" {
 
 const char* nsk_error_string(int code) {
@@ -350,6 +331,9 @@ int nsk_init_mesh(nsk_ctx** out, int dim, const int nelem[3], const double lo[3]
   c->nn = c->E * c->npe;
   c->stream = (cudaStream_t)cuda_stream;
   c->rsize = precision == NSK_FP64 ? sizeof(double) : sizeof(float);
+  // default schedule (nsk_autotune picks per mesh): 256 threads, each face evaluated once
+  c->tpb = 256;
+  c->fused_face = 0;
   if (node_type == NSK_NODES_GAUSS)
     gauss_legendre(c->np, c->xi, c->w);
   else
@@ -397,7 +381,8 @@ int nsk_init_mesh(nsk_ctx** out, int dim, const int nelem[3], const double lo[3]
       return NSK_ERR_NOMEM;
     }
   }
-  if (cudaMemset(c->b.err, 0, sizeof(int)) != cudaSuccess || cudaMemset(c->b.K, 0, rs * c->nvar * nn) != cudaSuccess) {
+  if (cudaMemset(c->b.err, 0, sizeof(int)) != cudaSuccess || cudaMemset(c->b.K, 0, rs * c->nvar * nn) != cudaSuccess ||
+      cudaMemset(c->b.dt, 0, sizeof(double)) != cudaSuccess) {
     free_ctx(c);
     return NSK_ERR_CUDA;
   }
@@ -489,7 +474,7 @@ int nsk_rhs(nsk_ctx* c, double t, double* Ut, int where) {
   (void)t;
   if (!c || !Ut || (where != NSK_HOST && where != NSK_DEVICE)) return NSK_ERR_ARG;
   if (!c->state_set) return NSK_ERR_STATE;
-  NskLaunch l = {NSK_MODE_RHS, c->rbuf, 0.0, 0.0, nullptr, 0.0, nullptr};
+  NskLaunch l = {NSK_MODE_RHS, c->rbuf, 0.0, 0.0, nullptr, 0.0, nullptr, c->tpb, c->fused_face};
   int r = launch_stage(c, l);
   if (r) return r;
   r = export_nodal(c, c->rbuf, c->nvar, Ut, where);
@@ -500,7 +485,7 @@ int nsk_rhs(nsk_ctx* c, double t, double* Ut, int where) {
 int nsk_lift(nsk_ctx* c, double* Q, int where) {
   if (!c || !Q || (where != NSK_HOST && where != NSK_DEVICE)) return NSK_ERR_ARG;
   if (!c->state_set) return NSK_ERR_STATE;
-  NskLaunch l = {NSK_MODE_LIFT, nullptr, 0.0, 0.0, nullptr, 0.0, nullptr};
+  NskLaunch l = {NSK_MODE_LIFT, nullptr, 0.0, 0.0, nullptr, 0.0, nullptr, c->tpb, c->fused_face};
   int r = launch_stage(c, l);
   if (r) return r;
   r = export_nodal(c, c->b.Q, c->nq, Q, where);
@@ -530,7 +515,7 @@ int nsk_step(nsk_ctx* c, double dt, int nsteps) {
       c->launches += r;
     }
     for (int st = 0; st < 5; ++st) {
-      NskLaunch l = {NSK_MODE_LSRK, nullptr, kA[st], kB[st], adaptive ? c->b.dt : nullptr, dt, nullptr};
+      NskLaunch l = {NSK_MODE_LSRK, nullptr, kA[st], kB[st], adaptive ? c->b.dt : nullptr, dt, nullptr, c->tpb, c->fused_face};
       int r = launch_stage(c, l);
       if (r) return r;
     }
@@ -541,7 +526,7 @@ int nsk_step(nsk_ctx* c, double dt, int nsteps) {
 int nsk_diagnostics(nsk_ctx* c, double* mass, double* energy, double* l2) {
   if (!c) return NSK_ERR_ARG;
   if (!c->state_set) return NSK_ERR_STATE;
-  NskLaunch l = {NSK_MODE_LIFT, nullptr, 0.0, 0.0, nullptr, 0.0, nullptr};
+  NskLaunch l = {NSK_MODE_LIFT, nullptr, 0.0, 0.0, nullptr, 0.0, nullptr, c->tpb, c->fused_face};
   int r = launch_stage(c, l);
   if (r) return r;
   r = nsk_launch_diag(c->p, c->dim, c->np, c->precision == NSK_FP32_MIXED, c->b, c->stream);
@@ -567,6 +552,61 @@ int nsk_get_sizes(nsk_ctx* c, long long* n_elem, int* nodes_per_elem, int* nvar)
 }
 
 long long nsk_launch_count(nsk_ctx* c) { return c ? c->launches : -1; }
+
+int nsk_set_schedule(nsk_ctx* c, int tpb, int fused_face) {
+  if (!c || (tpb != 128 && tpb != 256)) return NSK_ERR_ARG;
+  c->tpb = tpb;
+  c->fused_face = fused_face ? 1 : 0;
+  return NSK_OK;
+}
+
+int nsk_get_schedule(nsk_ctx* c, int* tpb, int* fused_face) {
+  if (!c) return NSK_ERR_ARG;
+  if (tpb) *tpb = c->tpb;
+  if (fused_face) *fused_face = c->fused_face;
+  return NSK_OK;
+}
+
+int nsk_autotune(nsk_ctx* c, int* tpb_out, int* fused_out, double* ms_out) {
+  if (!c) return NSK_ERR_ARG;
+  if (!c->state_set) return NSK_ERR_STATE;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return NSK_ERR_CUDA;
+  const int tpbs[2] = {128, 256};
+  double best = 1e300;
+  int bt = c->tpb, bf = c->fused_face, st = NSK_OK;
+  const bool prof = c->prof_on;
+  c->prof_on = false;
+  for (int it = 0; it < 2 && st == NSK_OK; ++it)
+    for (int f = 0; f < 2 && st == NSK_OK; ++f) {
+      c->tpb = tpbs[it];
+      c->fused_face = f;
+      NskLaunch l = {NSK_MODE_RHS, c->rbuf, 0.0, 0.0, nullptr, 0.0, nullptr, c->tpb, c->fused_face};
+      st = launch_stage(c, l);  // warm-up
+      if (st) break;
+      cudaEventRecord(e0, c->stream);
+      for (int r = 0; r < 3 && st == NSK_OK; ++r) st = launch_stage(c, l);
+      cudaEventRecord(e1, c->stream);
+      if (cudaEventSynchronize(e1) != cudaSuccess) st = NSK_ERR_CUDA;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (st == NSK_OK && ms / 3.0 < best) {
+        best = ms / 3.0;
+        bt = c->tpb;
+        bf = c->fused_face;
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->prof_on = prof;
+  c->tpb = bt;
+  c->fused_face = bf;
+  if (st) return st;
+  if (tpb_out) *tpb_out = bt;
+  if (fused_out) *fused_out = bf;
+  if (ms_out) *ms_out = best;
+  return sync_and_check(c);
+}
 
 int nsk_set_profiling(nsk_ctx* c, int on) {
   if (!c) return NSK_ERR_ARG;
@@ -700,7 +740,7 @@ extern "C" int nsk_rhs_static_scratch(int dim, const int nelem[3], const double 
   b.Fstar = s8 + b_err + b_q + b_utr + b_fv;
   cudaStream_t stream = (cudaStream_t)cuda_stream;
   if (cudaMemsetAsync(b.err, 0, sizeof(int), stream) != cudaSuccess) return NSK_ERR_CUDA;
-  NskLaunch l = {NSK_MODE_RHS, Ut, 0.0, 0.0, nullptr, 0.0, nullptr};
+  NskLaunch l = {NSK_MODE_RHS, Ut, 0.0, 0.0, nullptr, 0.0, nullptr, 256, 0};
   int r;
   switch (dim) {
     case 1: r = nsk_launch_stage_d1(p, np, false, b, l, stream); break;

@@ -1,0 +1,532 @@
+// nsk_batch.cu -- batched execution of many 3D contexts (meshes of different sizes,
+// N = 3 or 4) in one persistent launch per LSRK stage.
+//
+// The four stage phases (trace prolongation, BR1 lifting, face fluxes, volume
+// integral + update) of every instance run inside one cooperative kernel,
+// separated by a grid barrier whose spin is bounded in time: on expiry the
+// kernel sets NSK_EBIT_TIMEOUT and returns instead of waiting forever. Work
+// units (trace items, element groups, face items) of all instances are
+// concatenated and striped over the grid, so small instances fill the GPU
+// together. The five stage launches of a step (and, optionally, the per-
+// instance time-step reductions) are captured once in a CUDA graph and the
+// graph is replayed per step. An autotuner times the block-size and face
+// schedules on the batch and keeps the fastest.
+#include <math.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "nsk_kernels.cuh"
+
+// Device descriptor of one instance.
+struct BatchInst {
+  NskParams p;
+  void *U, *K, *Q, *Utr, *FVtr, *Fstar, *Rout;
+  const double* dt;
+  long long off[4];  // first global work unit of this instance in each phase
+  long long cnt[4];  // work units: trace items, element groups, face items, element groups
+  int np;
+};
+
+struct nsk_batch {
+  int n, precision, tpb, fused;
+  std::vector<nsk_ctx*> inst;
+  BatchInst* d_inst;
+  unsigned* d_bar;  // grid barrier: [0] arrivals, [1] generation
+  int* d_err;
+  cudaStream_t stream;
+  long long tot[2][2][4];  // [tpb index][fused][phase]
+  std::vector<BatchInst> h_inst[2];  // per tpb choice
+  cudaGraphExec_t graph;
+  int graph_tpb, graph_fused, graph_dtmode;
+  double graph_cfl;
+  bool no_graph;          // capture or instantiation unavailable: stages launched directly
+  long long launches;
+  int grid[2][2];         // co-resident grid size per [tpb index][fused]
+  unsigned long long timeout_ns;  // bound of every grid-barrier wait
+};
+
+namespace {
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Grid-wide barrier over a cooperative launch, bounded by timeout_ns.
+__device__ bool grid_barrier(unsigned* bar, int* err, const unsigned long long timeout_ns) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok = 1;
+    volatile unsigned* vgen = bar + 1;
+    const unsigned gen = *vgen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(bar, 1u);
+    if (arrived == gridDim.x - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      const unsigned long long t0 = global_ns();
+      while (*vgen == gen) {
+        if (global_ns() - t0 > timeout_ns) {
+          atomicOr(err, NSK_EBIT_TIMEOUT);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    if (*(volatile int*)err & NSK_EBIT_TIMEOUT) ok = 0;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+constexpr int align16(int x) { return (x + 15) & ~15; }
+
+template <typename R, int TPB, bool FUSED>
+constexpr int batch_smem_bytes() {
+  constexpr int G4 = nsk::group_for<3, 4>(TPB), G5 = nsk::group_for<3, 5>(TPB);
+  constexpr int a = nsk::lift_smem<R, 3, 4, G4>(), b = nsk::lift_smem<R, 3, 5, G5>();
+  constexpr int c = nsk::volume_smem<R, 3, 4, G4, FUSED>(), d = nsk::volume_smem<R, 3, 5, G5, FUSED>();
+  constexpr int m1 = a > b ? a : b, m2 = c > d ? c : d;
+  return align16((int)sizeof(NskParams)) + (int)sizeof(R) * (m1 > m2 ? m1 : m2);
+}
+
+// copy an instance's parameters into shared memory (all threads of the block)
+__device__ __forceinline__ void load_params(NskParams* sp, const NskParams* gp) {
+  const int nw = (int)(sizeof(NskParams) / sizeof(int));
+  const int* src = (const int*)gp;
+  int* dst = (int*)sp;
+  for (int i = threadIdx.x; i < nw; i += blockDim.x) dst[i] = src[i];
+}
+
+template <typename R, int TPB, bool FUSED>
+__global__ void __launch_bounds__(TPB)
+    k_batch_stage(const BatchInst* __restrict__ inst, const int ninst, const long long tot0, const long long tot1,
+                  const long long tot2, const long long tot3, const int mode, const R A, const R B,
+                  unsigned* __restrict__ bar, int* __restrict__ err, const unsigned long long timeout_ns) {
+  constexpr int G4 = nsk::group_for<3, 4>(TPB), G5 = nsk::group_for<3, 5>(TPB);
+  extern __shared__ __align__(16) unsigned char smraw[];
+  NskParams* sp = (NskParams*)smraw;
+  R* sm = (R*)(smraw + align16((int)sizeof(NskParams)));
+  int eflag = 0;
+  const long long gth = (long long)gridDim.x * TPB;
+
+  // phase 0: traces of U on every face
+  {
+    int i = 0;
+    for (long long it = (long long)blockIdx.x * TPB + threadIdx.x; it < tot0; it += gth) {
+      while (it >= inst[i].off[0] + inst[i].cnt[0]) ++i;
+      const BatchInst& b = inst[i];
+      const long long loc = it - b.off[0];
+      if (b.np == 4)
+        nsk::prolong_item<R, 3, 4>(b.p, (const R*)b.U, (R*)b.Utr, loc);
+      else
+        nsk::prolong_item<R, 3, 5>(b.p, (const R*)b.U, (R*)b.Utr, loc);
+    }
+  }
+  if (!grid_barrier(bar, err, timeout_ns)) return;
+
+  // phase 1: BR1 lifting, one element group per block iteration
+  {
+    int i = 0, cur = -1;
+    for (long long gi = blockIdx.x; gi < tot1; gi += gridDim.x) {
+      while (gi >= inst[i].off[1] + inst[i].cnt[1]) ++i;
+      if (i != cur) {
+        __syncthreads();
+        load_params(sp, &inst[i].p);
+        __syncthreads();
+        cur = i;
+      }
+      const BatchInst& b = inst[i];
+      const long long loc = gi - b.off[1];
+      if (b.np == 4)
+        nsk::lift_group<R, 3, 4, G4>(*sp, (const R*)b.U, (const R*)b.Utr, (R*)b.Q, (R*)b.FVtr, loc * G4, sm, eflag);
+      else
+        nsk::lift_group<R, 3, 5, G5>(*sp, (const R*)b.U, (const R*)b.Utr, (R*)b.Q, (R*)b.FVtr, loc * G5, sm, eflag);
+    }
+  }
+  if (!grid_barrier(bar, err, timeout_ns)) return;
+
+  // phase 2: face fluxes (separate face schedule)
+  if (!FUSED) {
+    int i = 0;
+    for (long long it = (long long)blockIdx.x * TPB + threadIdx.x; it < tot2; it += gth) {
+      while (it >= inst[i].off[2] + inst[i].cnt[2]) ++i;
+      const BatchInst& b = inst[i];
+      const long long loc = it - b.off[2];
+      if (b.np == 4)
+        nsk::face_item<R, 3, 4>(b.p, (const R*)b.Utr, (const R*)b.FVtr, (R*)b.Fstar, loc, eflag);
+      else
+        nsk::face_item<R, 3, 5>(b.p, (const R*)b.Utr, (const R*)b.FVtr, (R*)b.Fstar, loc, eflag);
+    }
+    if (!grid_barrier(bar, err, timeout_ns)) return;
+  }
+
+  // phase 3: volume integral, surface lifting, sources, update
+  {
+    int i = 0, cur = -1;
+    R dt = 0;
+    for (long long gi = blockIdx.x; gi < tot3; gi += gridDim.x) {
+      while (gi >= inst[i].off[3] + inst[i].cnt[3]) ++i;
+      if (i != cur) {
+        __syncthreads();
+        load_params(sp, &inst[i].p);
+        __syncthreads();
+        cur = i;
+        dt = inst[i].dt ? (R)*inst[i].dt : R(0);
+      }
+      const BatchInst& b = inst[i];
+      const long long loc = gi - b.off[3];
+      if (b.np == 4)
+        nsk::volume_group<R, 3, 4, G4, FUSED>(*sp, (R*)b.U, (const R*)b.Q, (const R*)b.Fstar, (const R*)b.Utr,
+                                              (const R*)b.FVtr, (R*)b.K, (R*)b.Rout, mode, A, B, dt, loc * G4, sm,
+                                              eflag);
+      else
+        nsk::volume_group<R, 3, 5, G5, FUSED>(*sp, (R*)b.U, (const R*)b.Q, (const R*)b.Fstar, (const R*)b.Utr,
+                                              (const R*)b.FVtr, (R*)b.K, (R*)b.Rout, mode, A, B, dt, loc * G5, sm,
+                                              eflag);
+    }
+  }
+  if (eflag) atomicOr(err, eflag);
+}
+
+const double kA[5] = {0.0, -567301805773.0 / 1357537059087.0, -2404267990393.0 / 2016746695238.0,
+                      -3550918686646.0 / 2091501179385.0, -1275806237668.0 / 842570457699.0};
+const double kB[5] = {1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612068292357.0,
+                      1720146321549.0 / 2090206949498.0, 3134564353537.0 / 4481467310338.0,
+                      2277821191437.0 / 14882151754819.0};
+
+// shared-memory attribute and co-resident grid size of one variant (outside any capture)
+template <typename R, int TPB, bool FUSED>
+int prepare_batch_t(nsk_batch* bt) {
+  auto kern = k_batch_stage<R, TPB, FUSED>;
+  constexpr int smem = batch_smem_bytes<R, TPB, FUSED>();
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+    return NSK_ERR_CUDA;
+  int per_sm = 0, dev = 0, sms = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TPB, smem) != cudaSuccess || per_sm < 1)
+    return NSK_ERR_CUDA;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return NSK_ERR_CUDA;
+  const int ti = TPB == 128 ? 0 : 1;
+  const long long* tot = bt->tot[ti][FUSED ? 1 : 0];
+  const long long want = tot[1] > tot[3] ? tot[1] : tot[3];
+  long long grid = (long long)per_sm * sms;
+  if (want < grid) grid = want > 0 ? want : 1;
+  bt->grid[ti][FUSED ? 1 : 0] = (int)grid;
+  return NSK_OK;
+}
+
+template <typename R, int TPB, bool FUSED>
+int launch_batch_t(nsk_batch* bt, int mode, double A, double B) {
+  auto kern = k_batch_stage<R, TPB, FUSED>;
+  constexpr int smem = batch_smem_bytes<R, TPB, FUSED>();
+  const int ti = TPB == 128 ? 0 : 1;
+  const long long* tot = bt->tot[ti][FUSED ? 1 : 0];
+  const int grid = bt->grid[ti][FUSED ? 1 : 0];
+  if (grid < 1) return NSK_ERR_CUDA;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(TPB);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = bt->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const BatchInst* d_inst = bt->d_inst + (size_t)ti * bt->n;
+  if (cudaLaunchKernelEx(&cfg, kern, d_inst, bt->n, tot[0], tot[1], tot[2], tot[3], mode, (R)A, (R)B, bt->d_bar,
+                         bt->d_err, bt->timeout_ns) != cudaSuccess)
+    return NSK_ERR_CUDA;
+  bt->launches += 1;
+  return NSK_OK;
+}
+
+int launch_batch(nsk_batch* bt, int mode, double A, double B, int tpb, int fused) {
+  const bool f32 = bt->precision == NSK_FP32_MIXED;
+  if (tpb == 128) {
+    if (f32) return fused ? launch_batch_t<float, 128, true>(bt, mode, A, B) : launch_batch_t<float, 128, false>(bt, mode, A, B);
+    return fused ? launch_batch_t<double, 128, true>(bt, mode, A, B) : launch_batch_t<double, 128, false>(bt, mode, A, B);
+  }
+  if (f32) return fused ? launch_batch_t<float, 256, true>(bt, mode, A, B) : launch_batch_t<float, 256, false>(bt, mode, A, B);
+  return fused ? launch_batch_t<double, 256, true>(bt, mode, A, B) : launch_batch_t<double, 256, false>(bt, mode, A, B);
+}
+
+int prepare_batch(nsk_batch* bt) {
+  int st;
+  if (bt->precision == NSK_FP32_MIXED) {
+    if ((st = prepare_batch_t<float, 128, false>(bt)) || (st = prepare_batch_t<float, 128, true>(bt)) ||
+        (st = prepare_batch_t<float, 256, false>(bt)) || (st = prepare_batch_t<float, 256, true>(bt)))
+      return st;
+  } else {
+    if ((st = prepare_batch_t<double, 128, false>(bt)) || (st = prepare_batch_t<double, 128, true>(bt)) ||
+        (st = prepare_batch_t<double, 256, false>(bt)) || (st = prepare_batch_t<double, 256, true>(bt)))
+      return st;
+  }
+  return NSK_OK;
+}
+
+int read_error(nsk_batch* bt) {
+  int h = 0;
+  if (cudaMemcpyAsync(&h, bt->d_err, sizeof(int), cudaMemcpyDeviceToHost, bt->stream) != cudaSuccess ||
+      cudaStreamSynchronize(bt->stream) != cudaSuccess)
+    return NSK_ERR_CUDA;
+  if (h) {
+    // clear the error word and the barrier (a timed-out barrier leaves arrivals behind)
+    cudaMemsetAsync(bt->d_err, 0, sizeof(int), bt->stream);
+    cudaMemsetAsync(bt->d_bar, 0, 2 * sizeof(unsigned), bt->stream);
+    cudaStreamSynchronize(bt->stream);
+    return (h & NSK_EBIT_TIMEOUT) ? NSK_ERR_TIMEOUT : NSK_ERR_NONPHYSICAL;
+  }
+  return NSK_OK;
+}
+
+void destroy_graph(nsk_batch* bt) {
+  if (bt->graph) cudaGraphExecDestroy(bt->graph);
+  bt->graph = nullptr;
+}
+
+}  // namespace
+
+extern "C" {
+
+int nsk_batch_create(nsk_batch** out, int n, nsk_ctx* const* instances) {
+  if (!out || n < 1 || !instances) return NSK_ERR_ARG;
+  *out = nullptr;
+  const int prec = instances[0] ? instances[0]->precision : -1;
+  for (int i = 0; i < n; ++i) {
+    nsk_ctx* c = instances[i];
+    if (!c || c->dim != 3 || (c->np != 4 && c->np != 5) || c->precision != prec) return NSK_ERR_ARG;
+    if (!c->state_set) return NSK_ERR_STATE;
+  }
+  nsk_batch* bt = new (std::nothrow) nsk_batch();
+  if (!bt) return NSK_ERR_NOMEM;
+  bt->n = n;
+  bt->precision = prec;
+  bt->tpb = 256;
+  bt->fused = 0;
+  bt->timeout_ns = 1000000000ull;  // one second per barrier wait
+  bt->inst.assign(instances, instances + n);
+  const int tpbs[2] = {128, 256};
+  for (int ti = 0; ti < 2; ++ti) {
+    bt->h_inst[ti].resize(n);
+    for (int f = 0; f < 2; ++f)
+      for (int ph = 0; ph < 4; ++ph) bt->tot[ti][f][ph] = 0;
+    for (int i = 0; i < n; ++i) {
+      nsk_ctx* c = instances[i];
+      BatchInst& b = bt->h_inst[ti][i];
+      memset(&b, 0, sizeof(b));
+      b.p = c->p;
+      b.U = c->b.U;
+      b.K = c->b.K;
+      b.Q = c->b.Q;
+      b.Utr = c->b.Utr;
+      b.FVtr = c->b.FVtr;
+      b.Fstar = c->b.Fstar;
+      b.Rout = c->rbuf;
+      b.dt = c->b.dt;
+      b.np = c->np;
+      const int G = c->np == 4 ? (tpbs[ti] / 64 > 0 ? tpbs[ti] / 64 : 1) : (tpbs[ti] / 125 > 0 ? tpbs[ti] / 125 : 1);
+      b.cnt[0] = c->E * 6 * c->nfn;
+      b.cnt[1] = (c->E + G - 1) / G;
+      b.cnt[2] = c->E * 3 * c->nfn;
+      b.cnt[3] = b.cnt[1];
+      for (int ph = 0; ph < 4; ++ph) {
+        b.off[ph] = bt->tot[ti][0][ph];
+        bt->tot[ti][0][ph] += b.cnt[ph];
+      }
+    }
+    for (int ph = 0; ph < 4; ++ph) bt->tot[ti][1][ph] = bt->tot[ti][0][ph];
+  }
+  if (cudaStreamCreateWithFlags(&bt->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaMalloc(&bt->d_inst, 2 * sizeof(BatchInst) * n) != cudaSuccess ||
+      cudaMalloc(&bt->d_bar, 2 * sizeof(unsigned)) != cudaSuccess || cudaMalloc(&bt->d_err, sizeof(int)) != cudaSuccess) {
+    nsk_batch_destroy(bt);
+    return NSK_ERR_NOMEM;
+  }
+  for (int ti = 0; ti < 2; ++ti)
+    if (cudaMemcpy(bt->d_inst + (size_t)ti * n, bt->h_inst[ti].data(), sizeof(BatchInst) * n,
+                   cudaMemcpyHostToDevice) != cudaSuccess) {
+      nsk_batch_destroy(bt);
+      return NSK_ERR_CUDA;
+    }
+  if (cudaMemset(bt->d_bar, 0, 2 * sizeof(unsigned)) != cudaSuccess || cudaMemset(bt->d_err, 0, sizeof(int)) != cudaSuccess) {
+    nsk_batch_destroy(bt);
+    return NSK_ERR_CUDA;
+  }
+  const int pst = prepare_batch(bt);
+  if (pst) {
+    nsk_batch_destroy(bt);
+    return pst;
+  }
+  *out = bt;
+  return NSK_OK;
+}
+
+int nsk_batch_set_schedule(nsk_batch* bt, int tpb, int fused_face) {
+  if (!bt || (tpb != 128 && tpb != 256)) return NSK_ERR_ARG;
+  bt->tpb = tpb;
+  bt->fused = fused_face ? 1 : 0;
+  return NSK_OK;
+}
+
+int nsk_batch_get_schedule(nsk_batch* bt, int* tpb, int* fused_face) {
+  if (!bt) return NSK_ERR_ARG;
+  if (tpb) *tpb = bt->tpb;
+  if (fused_face) *fused_face = bt->fused;
+  return NSK_OK;
+}
+
+int nsk_batch_autotune(nsk_batch* bt, int* tpb_out, int* fused_out, double* ms_out) {
+  if (!bt) return NSK_ERR_ARG;
+  for (nsk_ctx* c : bt->inst)
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return NSK_ERR_CUDA;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return NSK_ERR_CUDA;
+  double best = 1e300;
+  int bt_tpb = bt->tpb, bt_f = bt->fused, st = NSK_OK;
+  const int tpbs[2] = {128, 256};
+  for (int ti = 0; ti < 2 && st == NSK_OK; ++ti)
+    for (int f = 0; f < 2 && st == NSK_OK; ++f) {
+      st = launch_batch(bt, NSK_MODE_RHS, 0.0, 0.0, tpbs[ti], f);  // warm-up (residual mode: state untouched)
+      if (st) break;
+      cudaEventRecord(e0, bt->stream);
+      for (int r = 0; r < 3 && st == NSK_OK; ++r) st = launch_batch(bt, NSK_MODE_RHS, 0.0, 0.0, tpbs[ti], f);
+      cudaEventRecord(e1, bt->stream);
+      if (cudaEventSynchronize(e1) != cudaSuccess) st = NSK_ERR_CUDA;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (st == NSK_OK && ms / 3.0 < best) {
+        best = ms / 3.0;
+        bt_tpb = tpbs[ti];
+        bt_f = f;
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st) return st;
+  st = read_error(bt);
+  if (st) return st;
+  bt->tpb = bt_tpb;
+  bt->fused = bt_f;
+  if (tpb_out) *tpb_out = bt_tpb;
+  if (fused_out) *fused_out = bt_f;
+  if (ms_out) *ms_out = best;
+  return NSK_OK;
+}
+
+int nsk_batch_step(nsk_batch* bt, int nsteps, double cfl, double* step_ms) {
+  if (!bt || nsteps < 0) return NSK_ERR_ARG;
+  for (nsk_ctx* c : bt->inst)
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return NSK_ERR_CUDA;
+  const int dtmode = cfl > 0.0 ? 1 : 0;
+  if (!bt->no_graph &&
+      (!bt->graph || bt->graph_tpb != bt->tpb || bt->graph_fused != bt->fused || bt->graph_dtmode != dtmode ||
+       (dtmode && bt->graph_cfl != cfl))) {
+    destroy_graph(bt);
+    cudaGraph_t g;
+    if (cudaStreamBeginCapture(bt->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return NSK_ERR_CUDA;
+    int st = NSK_OK;
+    if (dtmode)
+      for (nsk_ctx* c : bt->inst) {
+        const int r = nsk_launch_dt(c->p, c->dim, c->np, c->precision == NSK_FP32_MIXED, c->b, cfl, bt->stream);
+        if (r < 0) st = r;
+      }
+    for (int s = 0; s < 5 && st == NSK_OK; ++s) st = launch_batch(bt, NSK_MODE_LSRK, kA[s], kB[s], bt->tpb, bt->fused);
+    const cudaError_t ce = cudaStreamEndCapture(bt->stream, &g);
+    cudaError_t ie = cudaErrorUnknown;
+    if (st == NSK_OK && ce == cudaSuccess) {
+      ie = cudaGraphInstantiate(&bt->graph, g, 0);
+      cudaGraphDestroy(g);
+    }
+    if (ie != cudaSuccess) {  // capture refused: fall back to direct launches
+      cudaGetLastError();
+      bt->graph = nullptr;
+      bt->no_graph = true;
+    }
+    bt->graph_tpb = bt->tpb;
+    bt->graph_fused = bt->fused;
+    bt->graph_dtmode = dtmode;
+    bt->graph_cfl = cfl;
+    bt->launches -= 5;  // counted again per replay below
+  }
+  std::vector<cudaEvent_t> ev;
+  if (step_ms) {
+    ev.resize(nsteps + 1);
+    for (auto& e : ev)
+      if (cudaEventCreate(&e) != cudaSuccess) return NSK_ERR_CUDA;
+    cudaEventRecord(ev[0], bt->stream);
+  }
+  for (int s = 0; s < nsteps; ++s) {
+    if (bt->no_graph) {
+      if (dtmode)
+        for (nsk_ctx* c : bt->inst) {
+          const int r = nsk_launch_dt(c->p, c->dim, c->np, c->precision == NSK_FP32_MIXED, c->b, cfl, bt->stream);
+          if (r < 0) return r;
+        }
+      for (int st = 0; st < 5; ++st) {
+        const int r = launch_batch(bt, NSK_MODE_LSRK, kA[st], kB[st], bt->tpb, bt->fused);
+        if (r) return r;
+      }
+      if (dtmode) bt->launches += 2 * bt->n;
+    } else {
+      if (cudaGraphLaunch(bt->graph, bt->stream) != cudaSuccess) return NSK_ERR_CUDA;
+      bt->launches += 5 + (dtmode ? 2 * bt->n : 0);
+    }
+    if (step_ms) cudaEventRecord(ev[s + 1], bt->stream);
+  }
+  int st = read_error(bt);
+  if (step_ms) {
+    for (int s = 0; s < nsteps; ++s) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ev[s], ev[s + 1]);
+      step_ms[s] = ms;
+    }
+    for (auto& e : ev) cudaEventDestroy(e);
+  }
+  return st;
+}
+
+long long nsk_batch_launch_count(nsk_batch* bt) { return bt ? bt->launches : -1; }
+
+int nsk_batch_uses_graph(nsk_batch* bt) { return bt ? (bt->graph != nullptr ? 1 : 0) : NSK_ERR_ARG; }
+
+int nsk_batch_set_timeout(nsk_batch* bt, double seconds) {
+  if (!bt || !(seconds > 0.0) || seconds > 60.0) return NSK_ERR_ARG;
+  bt->timeout_ns = (unsigned long long)(seconds * 1e9);
+  destroy_graph(bt);  // the bound is a launch argument baked into the captured graph
+  return NSK_OK;
+}
+
+int nsk_batch_poison_barrier(nsk_batch* bt) {
+  if (!bt) return NSK_ERR_ARG;
+  // arrivals start far above the grid size, so the next barrier can never complete and
+  // every block's bounded wait expires
+  const unsigned poison[2] = {0x40000000u, 0u};
+  if (cudaMemcpyAsync(bt->d_bar, poison, sizeof(poison), cudaMemcpyHostToDevice, bt->stream) != cudaSuccess ||
+      cudaStreamSynchronize(bt->stream) != cudaSuccess)
+    return NSK_ERR_CUDA;
+  return NSK_OK;
+}
+
+void nsk_batch_destroy(nsk_batch* bt) {
+  if (!bt) return;
+  if (bt->stream) cudaStreamSynchronize(bt->stream);
+  destroy_graph(bt);
+  if (bt->d_inst) cudaFree(bt->d_inst);
+  if (bt->d_bar) cudaFree(bt->d_bar);
+  if (bt->d_err) cudaFree(bt->d_err);
+  if (bt->stream) cudaStreamDestroy(bt->stream);
+  delete bt;
+}
+
+}  // extern "C"

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "nsk.h"
 
 #define NSK_MAXNP 6  // polynomial degree N <= 5
@@ -87,6 +89,8 @@ struct NskLaunch {
   const double* dt_dev;    // device dt (NULL: use dt_val)
   double dt_val;
   cudaEvent_t* ev;         // NULL, or NSK_NKERN + 1 events bracketing the kernels
+  int tpb;                 // block-size schedule: 128 or 256 threads (elements per block follow)
+  int fused_face;          // 1: face fluxes evaluated inside the volume kernel
 };
 
 #define NSK_NKERN 4  // prolong, lift, face, volume
@@ -106,3 +110,31 @@ int nsk_launch_dt(const NskParams& p, int dim, int np, bool fp32, const NskBuffe
 int nsk_launch_diag(const NskParams& p, int dim, int np, bool fp32, const NskBuffers& b, cudaStream_t s);
 // precision conversion of nodal arrays (FP32 mode boundary)
 int nsk_launch_convert(const void* src, bool src64, void* dst, bool dst64, long long n, cudaStream_t s);
+
+// One context (the opaque nsk_ctx of the ABI): mesh, parameters, device buffers.
+struct nsk_ctx {
+  int dim, N, np, npe, nfn, nvar, nq, node_type, precision;
+  long long E, nn;
+  int ne[3];
+  double lo[3], hi[3], h[3];
+  double xi[NSK_MAXNP], w[NSK_MAXNP];
+  cudaStream_t stream;
+  NskParams p;
+  NskBuffers b;
+  void* rbuf;        // residual scratch, context precision, nvar*nn
+  double* stage64;   // FP64 staging for transfers, max(nvar, nq, dim)*nn
+  bool params_set, state_set;
+  long long launches;
+  size_t rsize;      // bytes per value in context precision
+  // per-kernel profiling (nsk_set_profiling)
+  bool prof_on;
+  std::vector<cudaEvent_t> prof_pool;  // groups of NSK_NKERN + 1 events
+  std::vector<int> prof_nk;            // kernels recorded in each used group
+  size_t prof_used;                    // groups recorded since the last sync
+  double prof_ms[NSK_NKERN];
+  long long prof_cnt[NSK_NKERN];
+  int tpb, fused_face;  // stage schedule (nsk_set_schedule / nsk_autotune)
+};
+
+// host helpers shared by the translation units of the library
+int nsk_ctx_launch_stage(nsk_ctx* c, NskLaunch l);  // queues one stage on the context's stream

@@ -3,14 +3,15 @@
 // type R of the DG operator (double, or float with the equation of state in
 // double), the dimension D and the number of nodes per direction NP = N + 1.
 //
-// One stage is four launches:
+// One stage is four launches (three with the fused face schedule):
 //   k_prolong  U -> traces of U on every element face (GL: l_j(+-1) dot a line)
 //   k_lift     U, traces -> BR1 gradients Q of (v, c) and the face-normal
 //              viscous-flux traces of the element's own faces
 //   k_face     traces -> local Lax-Friedrichs convective flux minus the BR1
-//              mean viscous flux, once per face
+//              mean viscous flux, once per face (separate schedule only)
 //   k_volume   U, Q, face fluxes -> weak-form volume integral, surface lifting,
-//              relaxation sources, then the residual or the fused LSRK update
+//              relaxation sources, then the residual or the fused LSRK update;
+//              with the fused face schedule it evaluates its own faces' fluxes
 // The grid-wide dependencies of BR1 (a face needs both neighbours' traces,
 // twice per residual) are the launch boundaries.
 #pragma once
@@ -81,14 +82,17 @@ __device__ __forceinline__ long long nbr_elem(const NskParams& p, long long e, i
 // Modified pressure p_alpha = p + alpha rho^2 / 2 (Eq. modified_pressure) and its derivative
 // with one reciprocal q = 1 / (3 - rho):
 //   p_alpha = 8 T rho q + (alpha/2 - 3) rho^2,   p_alpha' = 24 T q^2 + (alpha - 6) rho.
+// Expressions with two products are written as explicit fused multiply-adds so
+// that every kernel that inlines them rounds identically (results then do not
+// depend on the schedule or on which kernel evaluates them).
 __device__ __forceinline__ double eos_pa64(const NskParams& p, double rho) {
   const double q = 1.0 / (3.0 - rho);
-  return p.t8 * rho * q + p.pa2 * rho * rho;
+  return fma(p.t8 * rho, q, (p.pa2 * rho) * rho);
 }
 __device__ __forceinline__ void eos_both64(const NskParams& p, double rho, double& pa, double& dpa) {
   const double q = 1.0 / (3.0 - rho);
-  pa = p.t8 * rho * q + p.pa2 * rho * rho;
-  dpa = p.t24 * q * q + p.dpa1 * rho;
+  pa = fma(p.t8 * rho, q, (p.pa2 * rho) * rho);
+  dpa = fma(p.t24 * q, q, p.dpa1 * rho);
 }
 // Precision policy of the FP32 operator: FP32 EoS, except inside the spinodal interval and
 // wherever p_alpha' cancels (alpha close to alpha_*), where it is evaluated in FP64.
@@ -103,25 +107,25 @@ template <> struct Eos<double> {
   }
   // with q = 1/(3 - rho) already known
   __device__ static __forceinline__ double pa_q(const NskParams& p, double rho, double q) {
-    return p.t8 * rho * q + p.pa2 * rho * rho;
+    return fma(p.t8 * rho, q, (p.pa2 * rho) * rho);
   }
   __device__ static __forceinline__ void both_q(const NskParams& p, double rho, double q, double& pa, double& dpa) {
-    pa = p.t8 * rho * q + p.pa2 * rho * rho;
-    dpa = p.t24 * q * q + p.dpa1 * rho;
+    pa = fma(p.t8 * rho, q, (p.pa2 * rho) * rho);
+    dpa = fma(p.t24 * q, q, p.dpa1 * rho);
   }
 };
 template <> struct Eos<float> {
   __device__ static __forceinline__ float pa(const NskParams& p, float rho) {
     if (eos_needs64(p, rho)) return (float)eos_pa64(p, (double)rho);
     const float q = 1.0f / (3.0f - rho);
-    return p.t8f * rho * q + p.pa2f * rho * rho;
+    return fmaf(p.t8f * rho, q, (p.pa2f * rho) * rho);
   }
   __device__ static __forceinline__ void both(const NskParams& p, float rho, float& pa, float& dpa) {
     if (!eos_needs64(p, rho)) {
       const float q = 1.0f / (3.0f - rho);
-      const float a = p.t24f * q * q, b = p.dpa1f * rho;
-      pa = p.t8f * rho * q + p.pa2f * rho * rho;
-      dpa = a + b;
+      const float a = (p.t24f * q) * q, b = p.dpa1f * rho;
+      pa = fmaf(p.t8f * rho, q, (p.pa2f * rho) * rho);
+      dpa = fmaf(p.t24f * q, q, b);
       if (fabsf(dpa) >= 1e-3f * (fabsf(a) + fabsf(b))) return;
     }
     double pd, dd;
@@ -141,15 +145,23 @@ __device__ __forceinline__ int rho_flags(R rho) {
 }
 
 // --------------------------------------------------------------------------
-// k_prolong: U -> Utr[v][slot][E][nfn], slot = 2k + (0: face xi_k=-1, 1: xi_k=+1)
+// Stage bodies. Every stage kernel below (and the batched persistent kernel in
+// nsk_batch.cu) is a thin wrapper around these device functions:
+//   prolong_item  one (element, face slot, face node) trace of U
+//   lift_group    BR1 lifting of G consecutive elements
+//   face_item     numerical flux of one face node
+//   volume_group  volume integral + surface lifting + sources + update of G elements
+// Element groups use threads [0, G*NPE) of the block; the remaining threads
+// only take part in the block barriers.
 // --------------------------------------------------------------------------
+
+// Utr[v][slot][E][nfn], slot = 2k + (0: face xi_k = -1, 1: xi_k = +1): the trace
+// sum_j l_j(+-1) U_j along the line in direction k through face node fn.
 template <typename R, int D, int NP>
-__global__ void __launch_bounds__(256) k_prolong(const NskParams p, const R* __restrict__ U, R* __restrict__ Utr) {
+__device__ __forceinline__ void prolong_item(const NskParams& p, const R* __restrict__ U, R* __restrict__ Utr,
+                                             const long long idx) {
   using S = Shape<D, NP>;
   const auto& t = TabSel<R>::get(p);
-  const long long nitems = p.E * S::NF * S::NFN;
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= nitems) return;
   const int fn = (int)(idx % S::NFN);
   const long long r = idx / S::NFN;
   const long long e = r % p.E;
@@ -164,7 +176,7 @@ __global__ void __launch_bounds__(256) k_prolong(const NskParams p, const R* __r
   for (int v = 0; v < S::NV; ++v) {
     R acc = 0;
 #pragma unroll
-    for (int j = 0; j < NP; ++j) acc += L[j] * u[v * nn + j * st];
+    for (int j = 0; j < NP; ++j) acc = fma(L[j], u[v * nn + j * st], acc);
     Utr[((long long)(v * S::NF + slot) * p.E + e) * S::NFN + fn] = acc;
     if (v == 0) rho = acc;
   }
@@ -176,31 +188,33 @@ __global__ void __launch_bounds__(256) k_prolong(const NskParams p, const R* __r
   }
 }
 
-// --------------------------------------------------------------------------
-// k_lift: BR1 lifting (Sec. 3.1) in weak form with the central flux,
-//   Q_{k,w}(i) = (2/h_k) [ -sum_j (w_j/w_i) l_i'(xi_j) w_j
-//                          + (w*_{k,+} l_i(1) - w*_{k,-} l_i(-1)) / w_i ],
-// w = (v, c) from the conservative traces on both sides of each face; then
-// the face-normal viscous flux F^v_k = (tau_{.k}, (kappa/beta) c_{x_k}) on the
-// element's own faces for the face kernel.
-// --------------------------------------------------------------------------
-template <typename R, int D, int NP>
-__global__ void __launch_bounds__(Shape<D, NP>::TPB)
-    k_lift(const NskParams p, const R* __restrict__ U, const R* __restrict__ Utr, R* __restrict__ Q,
-           R* __restrict__ FVtr, int* __restrict__ err) {
+// shared memory (in units of R) of lift_group
+template <typename R, int D, int NP, int G>
+__host__ __device__ constexpr int lift_smem() {
   using S = Shape<D, NP>;
-  constexpr int G = S::G, NPE = S::NPE, NFN = S::NFN, NW = S::NW, NF = S::NF, NV = S::NV, NQ = S::NQ;
-  constexpr int SM_A = G * NW * NPE + G * NF * NW * NFN;
-  constexpr int SM_B = G * D * NW * NPE;
-  __shared__ R sm[SM_A > SM_B ? SM_A : SM_B];
+  return (G * S::NW * S::NPE + G * S::NF * S::NW * S::NFN) > (G * D * S::NW * S::NPE)
+             ? (G * S::NW * S::NPE + G * S::NF * S::NW * S::NFN)
+             : (G * D * S::NW * S::NPE);
+}
+
+// BR1 lifting (Sec. 3.1) in weak form with the central flux,
+//   Q_{k,w}(i) = (2/h_k) [ -sum_j (w_j/w_i) l_i'(xi_j) w_j + (w*_{k,+} l_i(1) - w*_{k,-} l_i(-1)) / w_i ],
+// w = (v, c) formed from the conservative traces on both sides of each face; then the
+// face-normal viscous flux F^v_k = (tau_{.k}, (kappa/beta) c_{x_k}) traced onto the
+// element's own faces (FVtr[c][slot][E][nfn]) for the face flux.
+template <typename R, int D, int NP, int G>
+__device__ __forceinline__ void lift_group(const NskParams& p, const R* __restrict__ U, const R* __restrict__ Utr,
+                                           R* __restrict__ Q, R* __restrict__ FVtr, const long long e0, R* sm,
+                                           int& eflag) {
+  using S = Shape<D, NP>;
+  constexpr int NPE = S::NPE, NFN = S::NFN, NW = S::NW, NF = S::NF, NV = S::NV, NQ = S::NQ;
   R* sw = sm;                  // [G][NW][NPE] primitive variables at the nodes
   R* sws = sm + G * NW * NPE;  // [G][NF][NW][NFN] central flux w* on the faces
   const auto& t = TabSel<R>::get(p);
   const int le = threadIdx.x / NPE, n = threadIdx.x % NPE;
-  const long long e = (long long)blockIdx.x * G + le;
-  const bool valid = e < p.E;
+  const long long e = e0 + le;
+  const bool valid = le < G && e < p.E;
   const long long nn = p.E * NPE;
-  int eflag = 0;
 
   if (valid) {
     const R rho = U[e * NPE + n];
@@ -230,7 +244,7 @@ __global__ void __launch_bounds__(Shape<D, NP>::TPB)
       }
       R* ws = sws + ((le * NF + slot) * NW) * NFN + fn;
 #pragma unroll
-      for (int a = 0; a < D; ++a) ws[a * NFN] = R(0.5) * (uo[1 + a] * io + un[1 + a] * in);
+      for (int a = 0; a < D; ++a) ws[a * NFN] = R(0.5) * fma(uo[1 + a], io, un[1 + a] * in);
       ws[D * NFN] = R(0.5) * (uo[D + 1] + un[D + 1]);
     }
   }
@@ -248,10 +262,10 @@ __global__ void __launch_bounds__(Shape<D, NP>::TPB)
         const R* wl = sw + (le * NW + w) * NPE + n0;
         R vol = 0;
 #pragma unroll
-        for (int j = 0; j < NP; ++j) vol += t.dvol[i * NSK_MAXNP + j] * wl[j * st];
+        for (int j = 0; j < NP; ++j) vol = fma(t.dvol[i * NSK_MAXNP + j], wl[j * st], vol);
         const R wp = sws[((le * NF + 2 * k + 1) * NW + w) * NFN + fn];
         const R wm = sws[((le * NF + 2 * k) * NW + w) * NFN + fn];
-        const R surf = wp * t.lpw[i] - wm * t.lmw[i];
+        const R surf = fma(wp, t.lpw[i], -(wm * t.lmw[i]));
         q[k * NW + w] = rh * (surf - vol);
         Q[(long long)(k * NW + w) * nn + e * NPE + n] = q[k * NW + w];
       }
@@ -270,7 +284,7 @@ __global__ void __launch_bounds__(Shape<D, NP>::TPB)
 #pragma unroll
       for (int a = 0; a < D; ++a) {
         R tau = q[k * NW + a] + q[a * NW + k];
-        if (a == k) tau -= R(2.0 / 3.0) * div;
+        if (a == k) tau = fma(-R(2.0 / 3.0), div, tau);
         sfv[((le * D + k) * NW + a) * NPE + n] = mu * tau;
       }
       sfv[((le * D + k) * NW + D) * NPE + n] = kb * q[k * NW + D];
@@ -288,48 +302,38 @@ __global__ void __launch_bounds__(Shape<D, NP>::TPB)
         const R* f = sfv + ((le * D + k) * NW + c) * NPE + n0;
         R acc = 0;
 #pragma unroll
-        for (int j = 0; j < NP; ++j) acc += L[j] * f[j * st];
+        for (int j = 0; j < NP; ++j) acc = fma(L[j], f[j * st], acc);
         FVtr[((long long)(c * NF + slot) * p.E + e) * NFN + fn] = acc;
       }
     }
   }
-  if (eflag) atomicOr(err, eflag);
+  __syncthreads();  // the caller may reuse shared memory
 }
 
-// --------------------------------------------------------------------------
-// k_face: numerical flux on face (e, +k) between e (left, its +1 face) and its
-// right neighbour (its -1 face):
+// Numerical flux on the face between eL (its +1 side, slot 2k+1) and eR (its -1 side,
+// slot 2k), face node fn:
 //   F* = (F^c_k(U_L) + F^c_k(U_R))/2 - lambda/2 (U_R - U_L) - (F^v_L + F^v_R)/2,
 //   lambda = max(|v_{L,k}| + sqrt(p_alpha'(rho_L)), |v_{R,k}| + sqrt(p_alpha'(rho_R)))
 // (local Lax-Friedrichs with the model II wave speeds, Eq. parabolic_eigenvalues_model2;
 // BR1 viscous flux). The jump term acts on rho and momentum (c has no convective flux)
-// unless c_diss is set. EoS and wave speed in FP64.
-// --------------------------------------------------------------------------
+// unless c_diss is set.
 template <typename R, int D, int NP>
-__global__ void __launch_bounds__(256) k_face(const NskParams p, const R* __restrict__ Utr,
-                                              const R* __restrict__ FVtr, R* __restrict__ Fstar,
-                                              int* __restrict__ err) {
+__device__ __forceinline__ void face_flux(const NskParams& p, const R* __restrict__ Utr, const R* __restrict__ FVtr,
+                                          const long long eL, const long long eR, const int k, const int fn,
+                                          R* F, int& eflag) {
   using S = Shape<D, NP>;
   constexpr int NFN = S::NFN, NF = S::NF, NV = S::NV, NW = S::NW;
-  const long long nitems = (long long)D * p.E * NFN;
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= nitems) return;
-  const int fn = (int)(idx % NFN);
-  const long long r = idx / NFN;
-  const long long e = r % p.E;
-  const int k = (int)(r / p.E);
-  const long long eR = nbr_elem(p, e, k, 1);
   R UL[NV], UR[NV], VL[NW], VR[NW];
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
-    UL[v] = Utr[((long long)(v * NF + 2 * k + 1) * p.E + e) * NFN + fn];
+    UL[v] = Utr[((long long)(v * NF + 2 * k + 1) * p.E + eL) * NFN + fn];
     UR[v] = Utr[((long long)(v * NF + 2 * k) * p.E + eR) * NFN + fn];
   }
   R pl, dl, pr, dr, il, ir;
   if constexpr (TraceComps<R>::extra > 0) {
-    il = Utr[((long long)(NV * NF + 2 * k + 1) * p.E + e) * NFN + fn];
+    il = Utr[((long long)(NV * NF + 2 * k + 1) * p.E + eL) * NFN + fn];
     ir = Utr[((long long)(NV * NF + 2 * k) * p.E + eR) * NFN + fn];
-    const R ql = Utr[((long long)((NV + 1) * NF + 2 * k + 1) * p.E + e) * NFN + fn];
+    const R ql = Utr[((long long)((NV + 1) * NF + 2 * k + 1) * p.E + eL) * NFN + fn];
     const R qr = Utr[((long long)((NV + 1) * NF + 2 * k) * p.E + eR) * NFN + fn];
     Eos<R>::both_q(p, UL[0], ql, pl, dl);
     Eos<R>::both_q(p, UR[0], qr, pr, dr);
@@ -341,51 +345,68 @@ __global__ void __launch_bounds__(256) k_face(const NskParams p, const R* __rest
   }
 #pragma unroll
   for (int c = 0; c < NW; ++c) {
-    VL[c] = FVtr[((long long)(c * NF + 2 * k + 1) * p.E + e) * NFN + fn];
+    VL[c] = FVtr[((long long)(c * NF + 2 * k + 1) * p.E + eL) * NFN + fn];
     VR[c] = FVtr[((long long)(c * NF + 2 * k) * p.E + eR) * NFN + fn];
   }
-  int eflag = rho_flags(UL[0]) | rho_flags(UR[0]);
+  eflag |= rho_flags(UL[0]) | rho_flags(UR[0]);
   if (!(dl >= R(0)) || !(dr >= R(0))) eflag |= NSK_EBIT_SOUND;
   const R lam_l = fabs(UL[1 + k] * il) + sqrt(dl), lam_r = fabs(UR[1 + k] * ir) + sqrt(dr);
   const R lam = lam_l > lam_r ? lam_l : lam_r;
-  R F[NV];
   F[0] = R(0.5) * (UL[1 + k] + UR[1 + k]);
 #pragma unroll
   for (int a = 0; a < D; ++a) {
-    R fl = UL[1 + k] * (UL[1 + a] * il), fr = UR[1 + k] * (UR[1 + a] * ir);
-    if (a == k) {
-      fl += pl;
-      fr += pr;
-    }
-    F[1 + a] = R(0.5) * (fl + fr) - R(0.5) * (VL[a] + VR[a]);
+    const R ml = UL[1 + a] * il, mr = UR[1 + a] * ir;
+    const R sum = (a == k) ? fma(UL[1 + k], ml, pl) + fma(UR[1 + k], mr, pr) : fma(UL[1 + k], ml, UR[1 + k] * mr);
+    F[1 + a] = fma(R(0.5), sum, -(R(0.5) * (VL[a] + VR[a])));
   }
   F[D + 1] = -R(0.5) * (VL[D] + VR[D]);
   const int ndiss = p.c_diss ? NV : NV - 1;
-  for (int v = 0; v < ndiss; ++v) F[v] -= R(0.5) * lam * (UR[v] - UL[v]);
-#pragma unroll
-  for (int v = 0; v < NV; ++v) Fstar[((long long)(v * D + k) * p.E + e) * NFN + fn] = F[v];
-  if (eflag) atomicOr(err, eflag);
+  for (int v = 0; v < ndiss; ++v) F[v] = fma(-(R(0.5) * lam), UR[v] - UL[v], F[v]);
 }
 
-// --------------------------------------------------------------------------
-// k_volume: weak-form volume integral and surface lifting (Eq. weakformulation),
-//   R_i = sum_k (2/h_k) [ sum_j (w_j/w_i) l_i'(xi_j) F_k(U_j, Q_j)
-//                         - (F*_{k,+} l_i(1) - F*_{k,-} l_i(-1)) / w_i ] + S_i,
+// Fstar[v][k][E][nfn]: the flux on face (e, +k), item idx = (k, e, fn).
+template <typename R, int D, int NP>
+__device__ __forceinline__ void face_item(const NskParams& p, const R* __restrict__ Utr, const R* __restrict__ FVtr,
+                                          R* __restrict__ Fstar, const long long idx, int& eflag) {
+  using S = Shape<D, NP>;
+  constexpr int NFN = S::NFN, NV = S::NV;
+  const int fn = (int)(idx % NFN);
+  const long long r = idx / NFN;
+  const long long e = r % p.E;
+  const int k = (int)(r / p.E);
+  R F[NV];
+  face_flux<R, D, NP>(p, Utr, FVtr, e, nbr_elem(p, e, k, 1), k, fn, F, eflag);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) Fstar[((long long)(v * D + k) * p.E + e) * NFN + fn] = F[v];
+}
+
+// shared memory (in units of R) of volume_group
+template <typename R, int D, int NP, int G, bool FUSED>
+__host__ __device__ constexpr int volume_smem() {
+  using S = Shape<D, NP>;
+  return G * D * S::NV * S::NPE + (FUSED ? G * S::NF * S::NV * S::NFN : 0);
+}
+
+// Weak-form volume integral and surface lifting (Eq. weakformulation),
+//   R_i = sum_k (2/h_k) [ sum_j (w_j/w_i) l_i'(xi_j) F_k(U_j, Q_j) - (F*_{k,+} l_i(1) - F*_{k,-} l_i(-1)) / w_i ] + S_i,
 // F_k = F^c_k - F^v_k, S = (0, alpha rho grad c, (alpha/beta)(rho - c)); then
 // mode RHS: Rout = R; mode LSRK: K <- A K + dt R, U <- U + B K.
-// --------------------------------------------------------------------------
-template <typename R, int D, int NP>
-__global__ void __launch_bounds__(Shape<D, NP>::TPB)
-    k_volume(const NskParams p, R* __restrict__ U, const R* __restrict__ Q, const R* __restrict__ Fstar,
-             R* __restrict__ K, R* __restrict__ Rout, const int mode, const R A, const R B,
-             const double* __restrict__ dtp, const R dtv) {
+// FUSED: the element evaluates the fluxes of its own 2d faces (each face is then
+// evaluated by both neighbours, bit-identically) instead of reading Fstar.
+template <typename R, int D, int NP, int G, bool FUSED>
+__device__ __forceinline__ void volume_group(const NskParams& p, R* __restrict__ U, const R* __restrict__ Q,
+                                             const R* __restrict__ Fstar, const R* __restrict__ Utr,
+                                             const R* __restrict__ FVtr, R* __restrict__ K, R* __restrict__ Rout,
+                                             const int mode, const R A, const R B, const R dt, const long long e0,
+                                             R* sm, int& eflag) {
   using S = Shape<D, NP>;
-  constexpr int G = S::G, NPE = S::NPE, NFN = S::NFN, NW = S::NW, NV = S::NV, NQ = S::NQ;
-  __shared__ R sf[G * D * NV * NPE];  // [G][D][NV][NPE] fluxes F_k at the nodes
+  constexpr int NPE = S::NPE, NFN = S::NFN, NW = S::NW, NV = S::NV, NQ = S::NQ, NF = S::NF;
+  R* sf = sm;                          // [G][D][NV][NPE] fluxes F_k at the nodes
+  R* sfs = sm + G * D * NV * NPE;      // [G][NF][NV][NFN] face fluxes (FUSED)
   const auto& t = TabSel<R>::get(p);
   const int le = threadIdx.x / NPE, n = threadIdx.x % NPE;
-  const long long e = (long long)blockIdx.x * G + le;
-  const bool valid = e < p.E;
+  const long long e = e0 + le;
+  const bool valid = le < G && e < p.E;
   const long long nn = p.E * NPE;
   const long long g = e * NPE + n;
 
@@ -414,57 +435,117 @@ __global__ void __launch_bounds__(Shape<D, NP>::TPB)
       f[0] = u[1 + k];
 #pragma unroll
       for (int a = 0; a < D; ++a) {
-        R fc = u[1 + k] * (u[1 + a] * inv);
-        if (a == k) fc += pa;
+        const R fc = (a == k) ? fma(u[1 + k], u[1 + a] * inv, pa) : u[1 + k] * (u[1 + a] * inv);
         R tau = q[k * NW + a] + q[a * NW + k];
-        if (a == k) tau -= R(2.0 / 3.0) * div;
-        f[(1 + a) * NPE] = fc - mu * tau;
+        if (a == k) tau = fma(-R(2.0 / 3.0), div, tau);
+        f[(1 + a) * NPE] = fma(-mu, tau, fc);
       }
       f[(D + 1) * NPE] = -(kb * q[k * NW + D]);
     }
+    if constexpr (FUSED) {
+      for (int it = n; it < NF * NFN; it += NPE) {
+        const int slot = it / NFN, fn = it % NFN, k = slot >> 1;
+        R F[NV];
+        if (slot & 1)
+          face_flux<R, D, NP>(p, Utr, FVtr, e, nbr_elem(p, e, k, 1), k, fn, F, eflag);
+        else
+          face_flux<R, D, NP>(p, Utr, FVtr, nbr_elem(p, e, k, -1), e, k, fn, F, eflag);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) sfs[((le * NF + slot) * NV + v) * NFN + fn] = F[v];
+      }
+    }
   }
   __syncthreads();
-  if (!valid) return;
 
-  long long eL[D];
+  if (valid) {
+    long long eL[D];
+    if constexpr (!FUSED) {
 #pragma unroll
-  for (int k = 0; k < D; ++k) eL[k] = nbr_elem(p, e, k, -1);
-  R res[NV];
-#pragma unroll
-  for (int v = 0; v < NV; ++v) {
-    R acc = 0;
-#pragma unroll
-    for (int k = 0; k < D; ++k) {
-      const int i = coord<NP>(n, k), fn = face_node<D, NP>(n, k);
-      const int n0 = line_base<D, NP>(fn, k), st = node_stride<NP>(k);
-      const R* f = sf + ((le * D + k) * NV + v) * NPE + n0;
-      R vol = 0;
-#pragma unroll
-      for (int j = 0; j < NP; ++j) vol += t.dvol[i * NSK_MAXNP + j] * f[j * st];
-      const R fp = Fstar[((long long)(v * D + k) * p.E + e) * NFN + fn];
-      const R fm = Fstar[((long long)(v * D + k) * p.E + eL[k]) * NFN + fn];
-      acc += t.rh[k] * (vol - (fp * t.lpw[i] - fm * t.lmw[i]));
+      for (int k = 0; k < D; ++k) eL[k] = nbr_elem(p, e, k, -1);
     }
-    res[v] = acc;
-  }
-  const R alpha = t.alpha;
-#pragma unroll
-  for (int a = 0; a < D; ++a) res[1 + a] += alpha * u[0] * q[a * NW + D];
-  res[D + 1] += t.ab * (u[0] - u[D + 1]);
-
-  if (mode == NSK_MODE_RHS) {
-#pragma unroll
-    for (int v = 0; v < NV; ++v) Rout[v * nn + g] = res[v];
-  } else {
-    const R dt = dtp ? (R)*dtp : dtv;
-    const R a = A, b = B;
+    R res[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      const R kv = a * K[v * nn + g] + dt * res[v];
-      K[v * nn + g] = kv;
-      U[v * nn + g] = u[v] + b * kv;
+      R acc = 0;
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        const int i = coord<NP>(n, k), fn = face_node<D, NP>(n, k);
+        const int n0 = line_base<D, NP>(fn, k), st = node_stride<NP>(k);
+        const R* f = sf + ((le * D + k) * NV + v) * NPE + n0;
+        R vol = 0;
+#pragma unroll
+        for (int j = 0; j < NP; ++j) vol = fma(t.dvol[i * NSK_MAXNP + j], f[j * st], vol);
+        R fp, fm;
+        if constexpr (FUSED) {
+          fp = sfs[((le * NF + 2 * k + 1) * NV + v) * NFN + fn];
+          fm = sfs[((le * NF + 2 * k) * NV + v) * NFN + fn];
+        } else {
+          fp = Fstar[((long long)(v * D + k) * p.E + e) * NFN + fn];
+          fm = Fstar[((long long)(v * D + k) * p.E + eL[k]) * NFN + fn];
+        }
+        acc = fma(t.rh[k], vol - fma(fp, t.lpw[i], -(fm * t.lmw[i])), acc);
+      }
+      res[v] = acc;
+    }
+    const R alpha = t.alpha;
+#pragma unroll
+    for (int a = 0; a < D; ++a) res[1 + a] = fma(alpha * u[0], q[a * NW + D], res[1 + a]);
+    res[D + 1] = fma(t.ab, u[0] - u[D + 1], res[D + 1]);
+
+    if (mode == NSK_MODE_RHS) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) Rout[v * nn + g] = res[v];
+    } else {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const R kv = fma(A, K[v * nn + g], dt * res[v]);
+        K[v * nn + g] = kv;
+        U[v * nn + g] = fma(B, kv, u[v]);
+      }
     }
   }
+  __syncthreads();  // the caller may reuse shared memory
+}
+
+// ---- stand-alone stage kernels ---------------------------------------------
+template <typename R, int D, int NP>
+__global__ void __launch_bounds__(256) k_prolong(const NskParams p, const R* __restrict__ U, R* __restrict__ Utr) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx < p.E * Shape<D, NP>::NF * Shape<D, NP>::NFN) prolong_item<R, D, NP>(p, U, Utr, idx);
+}
+
+template <typename R, int D, int NP, int G>
+__global__ void __launch_bounds__(G * Shape<D, NP>::NPE)
+    k_lift(const NskParams p, const R* __restrict__ U, const R* __restrict__ Utr, R* __restrict__ Q,
+           R* __restrict__ FVtr, int* __restrict__ err) {
+  __shared__ R sm[lift_smem<R, D, NP, G>()];
+  int eflag = 0;
+  lift_group<R, D, NP, G>(p, U, Utr, Q, FVtr, (long long)blockIdx.x * G, sm, eflag);
+  if (eflag) atomicOr(err, eflag);
+}
+
+template <typename R, int D, int NP>
+__global__ void __launch_bounds__(256) k_face(const NskParams p, const R* __restrict__ Utr,
+                                              const R* __restrict__ FVtr, R* __restrict__ Fstar,
+                                              int* __restrict__ err) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  int eflag = 0;
+  if (idx < (long long)D * p.E * Shape<D, NP>::NFN) face_item<R, D, NP>(p, Utr, FVtr, Fstar, idx, eflag);
+  if (eflag) atomicOr(err, eflag);
+}
+
+template <typename R, int D, int NP, int G, bool FUSED>
+__global__ void __launch_bounds__(G * Shape<D, NP>::NPE)
+    k_volume(const NskParams p, R* __restrict__ U, const R* __restrict__ Q, const R* __restrict__ Fstar,
+             const R* __restrict__ Utr, const R* __restrict__ FVtr, R* __restrict__ K, R* __restrict__ Rout,
+             const int mode, const R A, const R B, const double* __restrict__ dtp, const R dtv,
+             int* __restrict__ err) {
+  __shared__ R sm[volume_smem<R, D, NP, G, FUSED>()];
+  const R dt = dtp ? (R)*dtp : dtv;
+  int eflag = 0;
+  volume_group<R, D, NP, G, FUSED>(p, U, Q, Fstar, Utr, FVtr, K, Rout, mode, A, B, dt, (long long)blockIdx.x * G,
+                                   sm, eflag);
+  if (eflag) atomicOr(err, eflag);
 }
 
 // --------------------------------------------------------------------------
@@ -582,8 +663,14 @@ static __global__ void __launch_bounds__(256) k_diag_final(const int nparts, dou
 // ---- launch helpers ------------------------------------------------------
 inline unsigned grid_for(long long items, int tpb) { return (unsigned)((items + tpb - 1) / tpb); }
 
-template <typename R, int D, int NP>
-int launch_stage(const NskParams& p, const NskBuffers& b, const NskLaunch& l, cudaStream_t s) {
+// elements per block for a block-size choice tpb (at least one element)
+template <int D, int NP>
+__host__ __device__ constexpr int group_for(int tpb) {
+  return tpb / Shape<D, NP>::NPE > 0 ? tpb / Shape<D, NP>::NPE : 1;
+}
+
+template <typename R, int D, int NP, int G, bool FUSED>
+int launch_stage_g(const NskParams& p, const NskBuffers& b, const NskLaunch& l, cudaStream_t s) {
   using S = Shape<D, NP>;
   int nl = 0;
   if (l.ev) cudaEventRecord(l.ev[0], s);
@@ -591,22 +678,35 @@ int launch_stage(const NskParams& p, const NskBuffers& b, const NskLaunch& l, cu
   k_prolong<R, D, NP><<<grid_for(ptems, 256), 256, 0, s>>>(p, (const R*)b.U, (R*)b.Utr);
   if (l.ev) cudaEventRecord(l.ev[1], s);
   ++nl;
-  const unsigned eb = (unsigned)((p.E + S::G - 1) / S::G);
-  k_lift<R, D, NP><<<eb, S::TPB, 0, s>>>(p, (const R*)b.U, (const R*)b.Utr, (R*)b.Q, (R*)b.FVtr, b.err);
+  const unsigned eb = (unsigned)((p.E + G - 1) / G);
+  k_lift<R, D, NP, G><<<eb, G * S::NPE, 0, s>>>(p, (const R*)b.U, (const R*)b.Utr, (R*)b.Q, (R*)b.FVtr, b.err);
   if (l.ev) cudaEventRecord(l.ev[2], s);
   ++nl;
   if (l.mode != NSK_MODE_LIFT) {
-    const long long ftems = (long long)D * p.E * S::NFN;
-    k_face<R, D, NP><<<grid_for(ftems, 256), 256, 0, s>>>(p, (const R*)b.Utr, (const R*)b.FVtr, (R*)b.Fstar, b.err);
+    if (!FUSED) {
+      const long long ftems = (long long)D * p.E * S::NFN;
+      k_face<R, D, NP><<<grid_for(ftems, 256), 256, 0, s>>>(p, (const R*)b.Utr, (const R*)b.FVtr, (R*)b.Fstar, b.err);
+      ++nl;
+    }
     if (l.ev) cudaEventRecord(l.ev[3], s);
-    ++nl;
-    k_volume<R, D, NP><<<eb, S::TPB, 0, s>>>(p, (R*)b.U, (const R*)b.Q, (const R*)b.Fstar, (R*)b.K, (R*)l.Rout,
-                                            l.mode, (R)l.A, (R)l.B, l.dt_dev, (R)l.dt_val);
+    k_volume<R, D, NP, G, FUSED><<<eb, G * S::NPE, 0, s>>>(
+        p, (R*)b.U, (const R*)b.Q, (const R*)b.Fstar, (const R*)b.Utr, (const R*)b.FVtr, (R*)b.K, (R*)l.Rout,
+        l.mode, (R)l.A, (R)l.B, l.dt_dev, (R)l.dt_val, b.err);
     if (l.ev) cudaEventRecord(l.ev[4], s);
     ++nl;
   }
   if (cudaGetLastError() != cudaSuccess) return NSK_ERR_CUDA;
   return nl;
+}
+
+// schedule: tpb in {128, 256} (elements per block = tpb / nodes per element), fused face flux or not
+template <typename R, int D, int NP>
+int launch_stage(const NskParams& p, const NskBuffers& b, const NskLaunch& l, cudaStream_t s) {
+  constexpr int G128 = group_for<D, NP>(128), G256 = group_for<D, NP>(256);
+  const bool fused = l.fused_face != 0;
+  if (l.tpb == 128)
+    return fused ? launch_stage_g<R, D, NP, G128, true>(p, b, l, s) : launch_stage_g<R, D, NP, G128, false>(p, b, l, s);
+  return fused ? launch_stage_g<R, D, NP, G256, true>(p, b, l, s) : launch_stage_g<R, D, NP, G256, false>(p, b, l, s);
 }
 
 template <int D>

@@ -53,6 +53,19 @@ SIGNATURES = {
                                          C.c_double, C.c_double, C.c_double, C.c_double, C.c_void_p, C.c_void_p,
                                          C.c_void_p]),
     "nsk_static_scratch_bytes": (C.c_longlong, []),
+    "nsk_set_schedule": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    "nsk_get_schedule": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "nsk_autotune": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), _dp]),
+    "nsk_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_void_p)]),
+    "nsk_batch_step": (C.c_int, [C.c_void_p, C.c_int, C.c_double, _dp]),
+    "nsk_batch_set_schedule": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    "nsk_batch_get_schedule": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "nsk_batch_autotune": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), _dp]),
+    "nsk_batch_launch_count": (C.c_longlong, [C.c_void_p]),
+    "nsk_batch_uses_graph": (C.c_int, [C.c_void_p]),
+    "nsk_batch_set_timeout": (C.c_int, [C.c_void_p, C.c_double]),
+    "nsk_batch_poison_barrier": (C.c_int, [C.c_void_p]),
+    "nsk_batch_destroy": (None, [C.c_void_p]),
     "nsk_error_string": (C.c_char_p, [C.c_int]),
     "nsk_destroy": (None, [C.c_void_p]),
 }
@@ -240,6 +253,20 @@ class Solver:
         _check(load_library().nsk_diagnostics(self.ctx, C.byref(m), C.byref(e), C.byref(l2)), "nsk_diagnostics")
         return m.value, e.value, l2.value
 
+    def set_schedule(self, tpb=256, fused_face=False):
+        _check(load_library().nsk_set_schedule(self.ctx, tpb, int(bool(fused_face))), "nsk_set_schedule")
+
+    def get_schedule(self):
+        t, f = C.c_int(), C.c_int()
+        _check(load_library().nsk_get_schedule(self.ctx, C.byref(t), C.byref(f)), "nsk_get_schedule")
+        return t.value, bool(f.value)
+
+    def autotune(self):
+        """Time the four stage schedules on the current state; keep and return the fastest."""
+        t, f, ms = C.c_int(), C.c_int(), C.c_double()
+        _check(load_library().nsk_autotune(self.ctx, C.byref(t), C.byref(f), C.byref(ms)), "nsk_autotune")
+        return t.value, bool(f.value), ms.value
+
     KERNELS = ("k_prolong", "k_lift", "k_face", "k_volume")
 
     def set_profiling(self, on=True):
@@ -257,3 +284,60 @@ class Solver:
     @property
     def launch_count(self):
         return int(load_library().nsk_launch_count(self.ctx))
+
+
+class Batch:
+    """Many 3D contexts (N = 3 or 4, same precision) advanced together by one
+    persistent launch per RK stage, replayed from a CUDA graph."""
+
+    def __init__(self, solvers):
+        self.solvers = list(solvers)  # keep the contexts alive
+        arr = (C.c_void_p * len(self.solvers))(*[s.ctx.value for s in self.solvers])
+        h = C.c_void_p()
+        _check(load_library().nsk_batch_create(C.byref(h), len(self.solvers), arr), "nsk_batch_create")
+        self.h = h
+
+    def step(self, nsteps=1, cfl=0.0, timings=False):
+        """Advance all instances; cfl > 0 recomputes each instance's dt every step.
+        With timings=True returns the per-step wall times in ms."""
+        ms = (C.c_double * max(nsteps, 1))() if timings else None
+        _check(load_library().nsk_batch_step(self.h, nsteps, cfl, ms), "nsk_batch_step")
+        return list(ms)[:nsteps] if timings else None
+
+    def set_schedule(self, tpb=256, fused_face=True):
+        _check(load_library().nsk_batch_set_schedule(self.h, tpb, int(bool(fused_face))), "nsk_batch_set_schedule")
+
+    def get_schedule(self):
+        t, f = C.c_int(), C.c_int()
+        _check(load_library().nsk_batch_get_schedule(self.h, C.byref(t), C.byref(f)), "nsk_batch_get_schedule")
+        return t.value, bool(f.value)
+
+    def autotune(self):
+        t, f, ms = C.c_int(), C.c_int(), C.c_double()
+        _check(load_library().nsk_batch_autotune(self.h, C.byref(t), C.byref(f), C.byref(ms)), "nsk_batch_autotune")
+        return t.value, bool(f.value), ms.value
+
+    def set_timeout(self, seconds):
+        _check(load_library().nsk_batch_set_timeout(self.h, seconds), "nsk_batch_set_timeout")
+
+    def poison_barrier(self):
+        _check(load_library().nsk_batch_poison_barrier(self.h), "nsk_batch_poison_barrier")
+
+    @property
+    def uses_graph(self):
+        return bool(load_library().nsk_batch_uses_graph(self.h))
+
+    @property
+    def launch_count(self):
+        return int(load_library().nsk_batch_launch_count(self.h))
+
+    def close(self):
+        if self.h:
+            load_library().nsk_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass

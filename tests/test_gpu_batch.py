@@ -1,0 +1,143 @@
+"""Stage schedules, autotuner and batched persistent execution.
+
+Every schedule (block size 128/256, face flux separate or fused into the volume
+kernel) evaluates the same per-node arithmetic, so results must agree bit for
+bit. A batch of uneven 3D instances (different meshes, N = 3 and 4) advanced by
+the persistent cooperative kernel must reproduce, bit for bit, each instance
+stepped alone; the bounded grid-barrier wait must end with NSK_ERR_TIMEOUT
+(not a hang) when the barrier is made unreachable, leaving the batch usable.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1912_12059_gb300 import inputs, nsk
+
+pytestmark = pytest.mark.gpu
+
+PRM = dict(T=0.85, kappa=1e-4, alpha=1e3, beta=1e-3, mu=1e-3)
+
+
+def _state(s, seed):
+    """In-range random state (these coarse test meshes cannot resolve a 0.02-wide interface)."""
+    return inputs.random_state(s.shape, seed=seed)
+
+
+@pytest.mark.parametrize("precision", [nsk.NSK_FP64, nsk.NSK_FP32_MIXED])
+@pytest.mark.parametrize("N", [2, 3, 4])
+def test_schedules_are_bit_identical(gpu, precision, N):
+    s = nsk.Solver(3, (5, 4, 3), N, [0, 0, 0], [1, 1, 1], 0, precision)
+    s.set_params(**PRM)
+    U = _state(s, 1)
+    results = []
+    for tpb in (128, 256):
+        for fused in (False, True):
+            s.set_schedule(tpb, fused)
+            s.set_state(U)
+            R = s.rhs()
+            s.step(1e-6, 2)
+            results.append((R, s.get_state()))
+    for R, Us in results[1:]:
+        assert np.array_equal(R, results[0][0])
+        assert np.array_equal(Us, results[0][1])
+    s.close()
+
+
+def test_autotune_keeps_state(gpu):
+    s = nsk.Solver(3, (8, 8, 8), 3, [0, 0, 0], [1, 1, 1], 0, nsk.NSK_FP32_MIXED)
+    s.set_params(**PRM)
+    U = _state(s, 2)
+    s.set_state(U)
+    before = s.get_state()
+    tpb, fused, ms = s.autotune()
+    assert tpb in (128, 256) and ms > 0
+    assert s.get_schedule() == (tpb, fused)
+    assert np.array_equal(s.get_state(), before)
+    s.close()
+
+
+def _instances(precision):
+    specs = [((6, 5, 4), 3, 10), ((4, 4, 4), 4, 11), ((7, 3, 5), 3, 12), ((3, 5, 4), 4, 13)]
+    out = []
+    for ne, N, seed in specs:
+        s = nsk.Solver(3, ne, N, [0, 0, 0], [1, 1, 1], 0, precision)
+        s.set_params(**PRM)
+        out.append((s, _state(s, seed)))
+    return out
+
+
+@pytest.mark.parametrize("precision", [nsk.NSK_FP32_MIXED, nsk.NSK_FP64])
+@pytest.mark.parametrize("adaptive", [False, True])
+def test_batch_equals_solo_runs(gpu, precision, adaptive):
+    solo = _instances(precision)
+    expect = []
+    for s, U in solo:
+        s.set_state(U)
+        if adaptive:
+            s.step(-0.5, 3)
+        else:
+            dt = s.compute_dt(0.5)
+            s.step(dt, 3)
+        expect.append(s.get_state())
+        s.close()
+    inst = _instances(precision)
+    for s, U in inst:
+        s.set_state(U)
+        s.compute_dt(0.5)
+    b = nsk.Batch([s for s, _ in inst])
+    for tpb, fused in ((256, True), (128, False)):
+        for s, U in inst:
+            s.set_state(U)
+            s.compute_dt(0.5)
+        b.set_schedule(tpb, fused)
+        ms = b.step(3, cfl=0.5 if adaptive else 0.0, timings=True)
+        assert len(ms) == 3 and all(m > 0 for m in ms)
+        for (s, _), want in zip(inst, expect):
+            assert np.array_equal(s.get_state(), want)
+    b.close()
+    for s, _ in inst:
+        s.close()
+
+
+def test_batch_autotune_graph_and_launch_count(gpu):
+    inst = _instances(nsk.NSK_FP32_MIXED)
+    for s, U in inst:
+        s.set_state(U)
+        s.compute_dt(0.5)
+    b = nsk.Batch([s for s, _ in inst])
+    tpb, fused, ms = b.autotune()
+    assert tpb in (128, 256) and ms > 0 and b.get_schedule() == (tpb, fused)
+    n0 = b.launch_count
+    b.step(2)
+    assert b.uses_graph
+    assert b.launch_count - n0 == 2 * 5
+    b.close()
+    for s, _ in inst:
+        s.close()
+
+
+def test_batch_barrier_wait_is_bounded(gpu):
+    """A barrier that can never complete ends every block's wait after the bound and
+    reports NSK_ERR_TIMEOUT; the batch then steps normally again."""
+    import time
+
+    inst = _instances(nsk.NSK_FP32_MIXED)[:2]
+    for s, U in inst:
+        s.set_state(U)
+        s.compute_dt(0.5)
+    b = nsk.Batch([s for s, _ in inst])
+    b.set_timeout(0.05)
+    b.poison_barrier()
+    t0 = time.perf_counter()
+    with pytest.raises(nsk.NskError) as ei:
+        b.step(1)
+    assert ei.value.code == nsk.NSK_ERR_TIMEOUT
+    assert time.perf_counter() - t0 < 30.0
+    for s, U in inst:
+        s.set_state(U)
+        s.compute_dt(0.5)
+    b.set_timeout(1.0)
+    b.step(1)
+    b.close()
+    for s, _ in inst:
+        s.close()
