@@ -210,6 +210,7 @@ def run_gpu(args, wl, rank, world):
     x = s.node_coords()
     U0 = wl.initial_state(x)
     s.set_state(U0)
+    tpb, fused, _ = s.autotune()  # setup: pick the fastest stage schedule for this mesh
     dt = s.compute_dt(wl.cfl)
     nodes = s.E * s.npe
 
@@ -302,7 +303,8 @@ def run_gpu(args, wl, rank, world):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == nsk.NSK_FP64 else "f32",
         "data": "synthetic",
         "config": {"workload": wl.name, "dofs_per_gpu": nodes, "N": wl.N, "nelem": list(wl.nelem),
-                   "precision": args.precision, "dt": dt, "l2": "state larger than L2 (inputs > 129 MB)"
+                   "precision": args.precision, "dt": dt, "schedule": {"tpb": tpb, "fused_face": fused},
+                   "l2": "state larger than L2 (inputs > 129 MB)"
                    if nodes * (wl.dim + 2) * fp_bytes > 129e6 else "state fits L2"},
         "e2e": {"value": e2e_value, "unit": "DOF-updates/s", "h2d_bytes_per_step": nbytes,
                 "d2h_bytes_per_step": nbytes, "steps": e2e_steps},
@@ -316,13 +318,122 @@ def run_gpu(args, wl, rank, world):
     return 0
 
 
+def run_batch(args, rank, world):
+    """32 uneven 3D collision instances (16^3..48^3 elements, N in {3,4}) advanced together by the
+    persistent batched kernel (CUDA-graph replay of the five stage launches)."""
+    import torch
+
+    from paper_1912_12059_gb300 import inputs, nsk
+    from paper_1912_12059_gb300.build import build_library
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    build_library()
+    prec = nsk.NSK_FP32_MIXED if args.precision != "fp64" else nsk.NSK_FP64
+    wls = inputs.serving_batch_3d(args.batch, seed=inputs.SEED + rank)
+    solvers = []
+    for wl in wls:
+        s = nsk.Solver(3, wl.nelem, wl.N, [0, 0, 0], [1, 1, 1], 0, prec)
+        s.set_params(T=wl.T, kappa=wl.kappa, alpha=wl.alpha, beta=wl.beta, mu=wl.mu)
+        s.set_state(wl.initial_state(s.node_coords()))
+        s.compute_dt(wl.cfl)
+        solvers.append(s)
+    nodes = sum(s.E * s.npe for s in solvers)
+    b = nsk.Batch(solvers)
+    tpb, fused, persistent, _ = b.autotune()
+    b.step(args.warmup)
+    n0 = b.launch_count
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        torch.cuda.synchronize()
+        step_ms = b.step(args.steps, timings=True)
+        torch.cuda.synchronize()
+    launches = b.launch_count - n0
+    clocks = clk.summary()
+    total_ms = sum(step_ms)
+    value = nodes * 5 * args.steps / (total_ms / 1e3)
+    # the same instances stepped one after another (no batching) for comparison
+    seq_ms = 0.0
+    for s in solvers:
+        s.set_schedule(tpb, fused)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        s.step(s.compute_dt(0.5), 2)
+        e1.record()
+        torch.cuda.synchronize()
+        seq_ms += e0.elapsed_time(e1) / 2
+    b.close()
+    for s in solvers:
+        s.close()
+    small = batch_vs_sequential_small(nsk, prec)
+    if rank != 0:
+        return 0
+    sm = sorted(step_ms)
+    line = {
+        "metric": "DOF-updates/s", "value": value, "unit": "DOF-updates/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if prec == nsk.NSK_FP32_MIXED else "f64", "data": "synthetic",
+        "config": {"workload": f"batched_{args.batch}x_collision3d_E16-48_N3-4", "instances": args.batch,
+                   "nodes_total": nodes, "schedule": {"tpb": tpb, "fused_face": fused, "persistent": persistent},
+                   "cuda_graph": True,
+                   "step_latency_ms_p50": sm[len(sm) // 2], "step_latency_ms_p99": sm[min(len(sm) - 1,
+                                                                                         int(0.99 * len(sm)))],
+                   "sequential_value": nodes * 5 / (seq_ms / 1e3),
+                   "small_instances": small,
+                   "l2": "state larger than L2"},
+        "gpu_launches": launches,
+        "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"], "reasons": clocks["reasons"]},
+        "e2e": None, "roofline": None, "cpu_baseline": None,
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def batch_vs_sequential_small(nsk, prec, n=64, steps=20):
+    """Serving-style comparison: many small instances (6^3..12^3 elements), batched graph replay
+    vs stepping the instances one after another."""
+    import torch
+
+    from paper_1912_12059_gb300 import inputs
+
+    wls = inputs.serving_batch_3d(n, seed=inputs.SEED + 7, e_range=(6, 12))
+    solvers = []
+    for wl in wls:
+        s = nsk.Solver(3, wl.nelem, wl.N, [0, 0, 0], [1, 1, 1], 0, prec)
+        s.set_params(T=wl.T, kappa=wl.kappa, alpha=wl.alpha, beta=wl.beta, mu=wl.mu)
+        s.set_state(wl.initial_state(s.node_coords()))
+        s.compute_dt(wl.cfl)
+        solvers.append(s)
+    nodes = sum(s.E * s.npe for s in solvers)
+    b = nsk.Batch(solvers)
+    tpb, fused, persistent, _ = b.autotune()
+    b.step(3)
+    ms = b.step(steps, timings=True)
+    batched = nodes * 5 * steps / (sum(ms) / 1e3)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        for s in solvers:
+            s.step(s.compute_dt(0.5), 1)
+    torch.cuda.synchronize()
+    seq = nodes * 5 * steps / (time.perf_counter() - t0)
+    b.close()
+    for s in solvers:
+        s.close()
+    sm = sorted(ms)
+    return {"instances": n, "nodes_total": nodes, "batched_value": batched, "sequential_value": seq,
+            "schedule": {"tpb": tpb, "fused_face": fused, "persistent": persistent},
+            "step_latency_ms_p50": sm[len(sm) // 2], "step_latency_ms_p99": sm[-1]}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="collision3d", choices=["collision3d", "coalescence2d", "interface1d"])
+    ap.add_argument("--workload", default="collision3d",
+                    choices=["collision3d", "coalescence2d", "interface1d", "batch"])
+    ap.add_argument("--batch", type=int, default=32, help="instances of the batch workload")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -332,6 +443,10 @@ def main():
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
+    if args.workload == "batch":
+        if args.precision == "fp64" and "--precision" not in sys.argv:
+            args.precision = "fp32"
+        return run_batch(args, rank, world)
     wl = workload_by_name(args.workload)
     if args.nelem:
         import dataclasses

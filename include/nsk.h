@@ -162,13 +162,14 @@ int nsk_get_schedule(nsk_ctx* ctx, int* tpb, int* fused_face);
  * fastest and returns it (any output may be NULL; ms_out = its time). */
 int nsk_autotune(nsk_ctx* ctx, int* tpb_out, int* fused_out, double* ms_out);
 
-/* Batched execution (many instances, one launch per stage). A batch groups n
- * existing 3D contexts with N = 3 or 4 and the same precision; meshes may
- * differ. Each LSRK stage of all instances runs as one persistent cooperative
- * kernel whose phases (traces, lifting, face fluxes, volume + update) are
- * separated by a grid barrier with a one-second bounded wait (NSK_ERR_TIMEOUT
- * on expiry); the five stages of a step are captured once in a CUDA graph and
- * replayed. The batch snapshots each instance's parameters and buffers at
+/* Batched execution (many instances per launch). A batch groups n existing
+ * 3D contexts with N = 3 or 4 and the same precision; meshes may differ.
+ * Persistent schedule (default): each LSRK stage of all instances runs as one
+ * persistent cooperative kernel whose phases (traces, lifting, face fluxes,
+ * volume + update) are separated by a grid barrier with a one-second bounded
+ * wait (NSK_ERR_TIMEOUT on expiry). Phase schedule: one ordinary launch per
+ * phase covering all instances. Either way the stage launches of a step are
+ * captured once in a CUDA graph and replayed. The batch snapshots each instance's parameters and buffers at
  * creation (call nsk_set_params / nsk_set_state before; states may be reset
  * later through the instances), and the instances must not be used by other
  * calls while a batch call runs. Results equal those of stepping each
@@ -181,12 +182,15 @@ int nsk_batch_create(nsk_batch** out, int n, nsk_ctx* const* instances);
  * not NULL, receives nsteps per-step wall times (ms, CUDA events); every
  * instance of the batch completes a step within that time. */
 int nsk_batch_step(nsk_batch* batch, int nsteps, double cfl, double* step_ms);
-/* Batch schedule and autotuner (same meaning as for a context). */
-int nsk_batch_set_schedule(nsk_batch* batch, int tpb, int fused_face);
-int nsk_batch_get_schedule(nsk_batch* batch, int* tpb, int* fused_face);
-int nsk_batch_autotune(nsk_batch* batch, int* tpb_out, int* fused_out, double* ms_out);
-/* Persistent-kernel launches issued (graph replays count their launches);
- * 1 if steps replay a captured CUDA graph, 0 if stages are launched directly. */
+/* Batch schedule (tpb and fused_face as for a context; persistent = 1 for
+ * the cooperative persistent kernel, 0 for one launch per phase) and the
+ * autotuner over all eight schedules (times one residual of the whole batch
+ * under each; the instances' states are not modified). */
+int nsk_batch_set_schedule(nsk_batch* batch, int tpb, int fused_face, int persistent);
+int nsk_batch_get_schedule(nsk_batch* batch, int* tpb, int* fused_face, int* persistent);
+int nsk_batch_autotune(nsk_batch* batch, int* tpb_out, int* fused_out, int* persistent_out, double* ms_out);
+/* Kernel launches issued (graph replays count their launches); and 1 if
+ * steps replay a captured CUDA graph, 0 if stages are launched directly. */
 long long nsk_batch_launch_count(nsk_batch* batch);
 int nsk_batch_uses_graph(nsk_batch* batch);
 /* Bound of every grid-barrier wait (default 1 s, at most 60 s). */

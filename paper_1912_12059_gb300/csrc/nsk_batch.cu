@@ -25,12 +25,13 @@ struct BatchInst {
   void *U, *K, *Q, *Utr, *FVtr, *Fstar, *Rout;
   const double* dt;
   long long off[4];  // first global work unit of this instance in each phase
-  long long cnt[4];  // work units: trace items, element groups, face items, element groups
+  long long cnt[4];  // work units: chunks of blockDim trace items, element groups, chunks of face items, groups
+  long long items[4];  // trace items and face items (phases 0 and 2)
   int np;
 };
 
 struct nsk_batch {
-  int n, precision, tpb, fused;
+  int n, precision, tpb, fused, persistent;
   std::vector<nsk_ctx*> inst;
   BatchInst* d_inst;
   unsigned* d_bar;  // grid barrier: [0] arrivals, [1] generation
@@ -39,10 +40,16 @@ struct nsk_batch {
   long long tot[2][2][4];  // [tpb index][fused][phase]
   std::vector<BatchInst> h_inst[2];  // per tpb choice
   cudaGraphExec_t graph;
-  int graph_tpb, graph_fused, graph_dtmode;
+  int graph_tpb, graph_fused, graph_dtmode, graph_persistent;
   double graph_cfl;
   bool no_graph;          // capture or instantiation unavailable: stages launched directly
   long long launches;
+  long long graph_launches;  // kernel launches of the captured stages of one step
+  // per-phase schedule: its own work-unit offsets (item phases in chunks of TPB * items per
+  // thread) and block -> instance maps
+  BatchInst* d_pinst;
+  long long ptot[2][4];
+  int* d_blk2inst[2][4];
   int grid[2][2];         // co-resident grid size per [tpb index][fused]
   unsigned long long timeout_ns;  // bound of every grid-barrier wait
 };
@@ -106,8 +113,15 @@ __device__ __forceinline__ void load_params(NskParams* sp, const NskParams* gp) 
   for (int i = threadIdx.x; i < nw; i += blockDim.x) dst[i] = src[i];
 }
 
+// occupancy target of the persistent kernel: it carries every phase's registers at once,
+// so the bound keeps 32 (FP32) or 24 (FP64) warps per SM resident
+template <typename R, int TPB>
+constexpr int batch_min_blocks() {
+  return (sizeof(R) == 4 ? 1024 : 768) / TPB;
+}
+
 template <typename R, int TPB, bool FUSED>
-__global__ void __launch_bounds__(TPB)
+__global__ void __launch_bounds__(TPB, batch_min_blocks<R, TPB>())
     k_batch_stage(const BatchInst* __restrict__ inst, const int ninst, const long long tot0, const long long tot1,
                   const long long tot2, const long long tot3, const int mode, const R A, const R B,
                   unsigned* __restrict__ bar, int* __restrict__ err, const unsigned long long timeout_ns) {
@@ -116,19 +130,26 @@ __global__ void __launch_bounds__(TPB)
   NskParams* sp = (NskParams*)smraw;
   R* sm = (R*)(smraw + align16((int)sizeof(NskParams)));
   int eflag = 0;
-  const long long gth = (long long)gridDim.x * TPB;
 
-  // phase 0: traces of U on every face
+  // phase 0: traces of U on every face, one chunk of TPB items of one instance per block iteration
   {
-    int i = 0;
-    for (long long it = (long long)blockIdx.x * TPB + threadIdx.x; it < tot0; it += gth) {
-      while (it >= inst[i].off[0] + inst[i].cnt[0]) ++i;
+    int i = 0, cur = -1;
+    for (long long ci = blockIdx.x; ci < tot0; ci += gridDim.x) {
+      while (ci >= inst[i].off[0] + inst[i].cnt[0]) ++i;
+      if (i != cur) {
+        __syncthreads();
+        load_params(sp, &inst[i].p);
+        __syncthreads();
+        cur = i;
+      }
       const BatchInst& b = inst[i];
-      const long long loc = it - b.off[0];
-      if (b.np == 4)
-        nsk::prolong_item<R, 3, 4>(b.p, (const R*)b.U, (R*)b.Utr, loc);
-      else
-        nsk::prolong_item<R, 3, 5>(b.p, (const R*)b.U, (R*)b.Utr, loc);
+      const long long it = (ci - b.off[0]) * TPB + threadIdx.x;
+      if (it < b.items[0]) {
+        if (b.np == 4)
+          nsk::prolong_item<R, 3, 4>(*sp, (const R*)b.U, (R*)b.Utr, it);
+        else
+          nsk::prolong_item<R, 3, 5>(*sp, (const R*)b.U, (R*)b.Utr, it);
+      }
     }
   }
   if (!grid_barrier(bar, err, timeout_ns)) return;
@@ -156,15 +177,23 @@ __global__ void __launch_bounds__(TPB)
 
   // phase 2: face fluxes (separate face schedule)
   if (!FUSED) {
-    int i = 0;
-    for (long long it = (long long)blockIdx.x * TPB + threadIdx.x; it < tot2; it += gth) {
-      while (it >= inst[i].off[2] + inst[i].cnt[2]) ++i;
+    int i = 0, cur = -1;
+    for (long long ci = blockIdx.x; ci < tot2; ci += gridDim.x) {
+      while (ci >= inst[i].off[2] + inst[i].cnt[2]) ++i;
+      if (i != cur) {
+        __syncthreads();
+        load_params(sp, &inst[i].p);
+        __syncthreads();
+        cur = i;
+      }
       const BatchInst& b = inst[i];
-      const long long loc = it - b.off[2];
-      if (b.np == 4)
-        nsk::face_item<R, 3, 4>(b.p, (const R*)b.Utr, (const R*)b.FVtr, (R*)b.Fstar, loc, eflag);
-      else
-        nsk::face_item<R, 3, 5>(b.p, (const R*)b.Utr, (const R*)b.FVtr, (R*)b.Fstar, loc, eflag);
+      const long long it = (ci - b.off[2]) * TPB + threadIdx.x;
+      if (it < b.items[2]) {
+        if (b.np == 4)
+          nsk::face_item<R, 3, 4>(*sp, (const R*)b.Utr, (const R*)b.FVtr, (R*)b.Fstar, it, eflag);
+        else
+          nsk::face_item<R, 3, 5>(*sp, (const R*)b.Utr, (const R*)b.FVtr, (R*)b.Fstar, it, eflag);
+      }
     }
     if (!grid_barrier(bar, err, timeout_ns)) return;
   }
@@ -197,6 +226,106 @@ __global__ void __launch_bounds__(TPB)
   if (eflag) atomicOr(err, eflag);
 }
 
+// ---- per-phase batched kernels: one launch per phase over all instances ---------
+// Block b handles work unit b of the phase: the instance is found by binary search
+// over the per-instance offsets (uniform in the block), its parameters staged in
+// shared memory. Each phase is its own kernel, so each keeps its own register budget.
+constexpr int kItemsPerThread = 4;  // item phases of the per-phase schedule: items per thread
+
+template <typename R, int TPB>
+__global__ void __launch_bounds__(TPB) k_bphase_prolong(const BatchInst* __restrict__ inst,
+                                                        const int* __restrict__ blk2inst) {
+  __shared__ __align__(16) unsigned char spraw[sizeof(NskParams)];
+  NskParams* sp = (NskParams*)spraw;
+  const int i = blk2inst[blockIdx.x];
+  load_params(sp, &inst[i].p);
+  __syncthreads();
+  const BatchInst& b = inst[i];
+  const long long base = ((long long)blockIdx.x - b.off[0]) * TPB * kItemsPerThread + threadIdx.x;
+#pragma unroll
+  for (int r = 0; r < kItemsPerThread; ++r) {
+    const long long it = base + (long long)r * TPB;
+    if (it < b.items[0]) {
+      if (b.np == 4)
+        nsk::prolong_item<R, 3, 4>(*sp, (const R*)b.U, (R*)b.Utr, it);
+      else
+        nsk::prolong_item<R, 3, 5>(*sp, (const R*)b.U, (R*)b.Utr, it);
+    }
+  }
+}
+
+template <typename R, int TPB>
+__global__ void __launch_bounds__(TPB) k_bphase_lift(const BatchInst* __restrict__ inst,
+                                                     const int* __restrict__ blk2inst, int* __restrict__ err) {
+  constexpr int G4 = nsk::group_for<3, 4>(TPB), G5 = nsk::group_for<3, 5>(TPB);
+  constexpr int a = nsk::lift_smem<R, 3, 4, G4>(), c = nsk::lift_smem<R, 3, 5, G5>();
+  __shared__ R sm[a > c ? a : c];
+  __shared__ __align__(16) unsigned char spraw[sizeof(NskParams)];
+  NskParams* sp = (NskParams*)spraw;
+  const int i = blk2inst[blockIdx.x];
+  load_params(sp, &inst[i].p);
+  __syncthreads();
+  const BatchInst& b = inst[i];
+  const long long loc = (long long)blockIdx.x - b.off[1];
+  int eflag = 0;
+  if (b.np == 4)
+    nsk::lift_group<R, 3, 4, G4>(*sp, (const R*)b.U, (const R*)b.Utr, (R*)b.Q, (R*)b.FVtr, loc * G4, sm, eflag);
+  else
+    nsk::lift_group<R, 3, 5, G5>(*sp, (const R*)b.U, (const R*)b.Utr, (R*)b.Q, (R*)b.FVtr, loc * G5, sm, eflag);
+  if (eflag) atomicOr(err, eflag);
+}
+
+template <typename R, int TPB>
+__global__ void __launch_bounds__(TPB) k_bphase_face(const BatchInst* __restrict__ inst,
+                                                     const int* __restrict__ blk2inst, int* __restrict__ err) {
+  __shared__ __align__(16) unsigned char spraw[sizeof(NskParams)];
+  NskParams* sp = (NskParams*)spraw;
+  const int i = blk2inst[blockIdx.x];
+  load_params(sp, &inst[i].p);
+  __syncthreads();
+  const BatchInst& b = inst[i];
+  const long long base = ((long long)blockIdx.x - b.off[2]) * TPB * kItemsPerThread + threadIdx.x;
+  int eflag = 0;
+#pragma unroll
+  for (int r = 0; r < kItemsPerThread; ++r) {
+    const long long it = base + (long long)r * TPB;
+    if (it < b.items[2]) {
+      if (b.np == 4)
+        nsk::face_item<R, 3, 4>(*sp, (const R*)b.Utr, (const R*)b.FVtr, (R*)b.Fstar, it, eflag);
+      else
+        nsk::face_item<R, 3, 5>(*sp, (const R*)b.Utr, (const R*)b.FVtr, (R*)b.Fstar, it, eflag);
+    }
+  }
+  if (eflag) atomicOr(err, eflag);
+}
+
+template <typename R, int TPB, bool FUSED>
+__global__ void __launch_bounds__(TPB) k_bphase_volume(const BatchInst* __restrict__ inst,
+                                                       const int* __restrict__ blk2inst, const int mode, const R A,
+                                                       const R B, int* __restrict__ err) {
+  constexpr int G4 = nsk::group_for<3, 4>(TPB), G5 = nsk::group_for<3, 5>(TPB);
+  constexpr int a = nsk::volume_smem<R, 3, 4, G4, FUSED>(), c = nsk::volume_smem<R, 3, 5, G5, FUSED>();
+  __shared__ R sm[a > c ? a : c];
+  __shared__ __align__(16) unsigned char spraw[sizeof(NskParams)];
+  NskParams* sp = (NskParams*)spraw;
+  const int i = blk2inst[blockIdx.x];
+  load_params(sp, &inst[i].p);
+  __syncthreads();
+  const BatchInst& b = inst[i];
+  const long long loc = (long long)blockIdx.x - b.off[3];
+  const R dt = b.dt ? (R)*b.dt : R(0);
+  int eflag = 0;
+  if (b.np == 4)
+    nsk::volume_group<R, 3, 4, G4, FUSED>(*sp, (R*)b.U, (const R*)b.Q, (const R*)b.Fstar, (const R*)b.Utr,
+                                          (const R*)b.FVtr, (R*)b.K, (R*)b.Rout, mode, A, B, dt, loc * G4, sm,
+                                          eflag);
+  else
+    nsk::volume_group<R, 3, 5, G5, FUSED>(*sp, (R*)b.U, (const R*)b.Q, (const R*)b.Fstar, (const R*)b.Utr,
+                                          (const R*)b.FVtr, (R*)b.K, (R*)b.Rout, mode, A, B, dt, loc * G5, sm,
+                                          eflag);
+  if (eflag) atomicOr(err, eflag);
+}
+
 const double kA[5] = {0.0, -567301805773.0 / 1357537059087.0, -2404267990393.0 / 2016746695238.0,
                       -3550918686646.0 / 2091501179385.0, -1275806237668.0 / 842570457699.0};
 const double kB[5] = {1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612068292357.0,
@@ -218,7 +347,8 @@ int prepare_batch_t(nsk_batch* bt) {
     return NSK_ERR_CUDA;
   const int ti = TPB == 128 ? 0 : 1;
   const long long* tot = bt->tot[ti][FUSED ? 1 : 0];
-  const long long want = tot[1] > tot[3] ? tot[1] : tot[3];
+  long long want = tot[0];
+  for (int ph = 1; ph < 4; ++ph) want = tot[ph] > want ? tot[ph] : want;
   long long grid = (long long)per_sm * sms;
   if (want < grid) grid = want > 0 ? want : 1;
   bt->grid[ti][FUSED ? 1 : 0] = (int)grid;
@@ -251,7 +381,38 @@ int launch_batch_t(nsk_batch* bt, int mode, double A, double B) {
   return NSK_OK;
 }
 
-int launch_batch(nsk_batch* bt, int mode, double A, double B, int tpb, int fused) {
+template <typename R, int TPB, bool FUSED>
+int launch_phases_t(nsk_batch* bt, int mode, double A, double B) {
+  const int ti = TPB == 128 ? 0 : 1;
+  const long long* tot = bt->ptot[ti];
+  const BatchInst* d_inst = bt->d_pinst + (size_t)ti * bt->n;
+  const int* const* map = bt->d_blk2inst[ti];
+  cudaStream_t s = bt->stream;
+  k_bphase_prolong<R, TPB><<<(unsigned)tot[0], TPB, 0, s>>>(d_inst, map[0]);
+  k_bphase_lift<R, TPB><<<(unsigned)tot[1], TPB, 0, s>>>(d_inst, map[1], bt->d_err);
+  int nl = 2;
+  if (!FUSED) {
+    k_bphase_face<R, TPB><<<(unsigned)tot[2], TPB, 0, s>>>(d_inst, map[2], bt->d_err);
+    ++nl;
+  }
+  k_bphase_volume<R, TPB, FUSED><<<(unsigned)tot[3], TPB, 0, s>>>(d_inst, map[3], mode, (R)A, (R)B, bt->d_err);
+  ++nl;
+  if (cudaGetLastError() != cudaSuccess) return NSK_ERR_CUDA;
+  bt->launches += nl;
+  return NSK_OK;
+}
+
+int launch_phases(nsk_batch* bt, int mode, double A, double B, int tpb, int fused) {
+  const bool f32 = bt->precision == NSK_FP32_MIXED;
+  if (tpb == 128) {
+    if (f32) return fused ? launch_phases_t<float, 128, true>(bt, mode, A, B) : launch_phases_t<float, 128, false>(bt, mode, A, B);
+    return fused ? launch_phases_t<double, 128, true>(bt, mode, A, B) : launch_phases_t<double, 128, false>(bt, mode, A, B);
+  }
+  if (f32) return fused ? launch_phases_t<float, 256, true>(bt, mode, A, B) : launch_phases_t<float, 256, false>(bt, mode, A, B);
+  return fused ? launch_phases_t<double, 256, true>(bt, mode, A, B) : launch_phases_t<double, 256, false>(bt, mode, A, B);
+}
+
+int launch_persistent(nsk_batch* bt, int mode, double A, double B, int tpb, int fused) {
   const bool f32 = bt->precision == NSK_FP32_MIXED;
   if (tpb == 128) {
     if (f32) return fused ? launch_batch_t<float, 128, true>(bt, mode, A, B) : launch_batch_t<float, 128, false>(bt, mode, A, B);
@@ -273,6 +434,11 @@ int prepare_batch(nsk_batch* bt) {
       return st;
   }
   return NSK_OK;
+}
+
+// one stage of the whole batch under a schedule (persistent: one cooperative launch)
+int launch_batch(nsk_batch* bt, int mode, double A, double B, int tpb, int fused, int persistent) {
+  return persistent ? launch_persistent(bt, mode, A, B, tpb, fused) : launch_phases(bt, mode, A, B, tpb, fused);
 }
 
 int read_error(nsk_batch* bt) {
@@ -314,6 +480,7 @@ int nsk_batch_create(nsk_batch** out, int n, nsk_ctx* const* instances) {
   bt->precision = prec;
   bt->tpb = 256;
   bt->fused = 0;
+  bt->persistent = 1;
   bt->timeout_ns = 1000000000ull;  // one second per barrier wait
   bt->inst.assign(instances, instances + n);
   const int tpbs[2] = {128, 256};
@@ -336,9 +503,11 @@ int nsk_batch_create(nsk_batch** out, int n, nsk_ctx* const* instances) {
       b.dt = c->b.dt;
       b.np = c->np;
       const int G = c->np == 4 ? (tpbs[ti] / 64 > 0 ? tpbs[ti] / 64 : 1) : (tpbs[ti] / 125 > 0 ? tpbs[ti] / 125 : 1);
-      b.cnt[0] = c->E * 6 * c->nfn;
+      b.items[0] = c->E * 6 * c->nfn;
+      b.items[2] = c->E * 3 * c->nfn;
+      b.cnt[0] = (b.items[0] + tpbs[ti] - 1) / tpbs[ti];
       b.cnt[1] = (c->E + G - 1) / G;
-      b.cnt[2] = c->E * 3 * c->nfn;
+      b.cnt[2] = (b.items[2] + tpbs[ti] - 1) / tpbs[ti];
       b.cnt[3] = b.cnt[1];
       for (int ph = 0; ph < 4; ++ph) {
         b.off[ph] = bt->tot[ti][0][ph];
@@ -347,18 +516,47 @@ int nsk_batch_create(nsk_batch** out, int n, nsk_ctx* const* instances) {
     }
     for (int ph = 0; ph < 4; ++ph) bt->tot[ti][1][ph] = bt->tot[ti][0][ph];
   }
+  std::vector<BatchInst> pinst[2];
+  std::vector<int> maps[2][4];
+  for (int ti = 0; ti < 2; ++ti) {
+    pinst[ti] = bt->h_inst[ti];
+    for (int ph = 0; ph < 4; ++ph) bt->ptot[ti][ph] = 0;
+    for (int i = 0; i < n; ++i) {
+      BatchInst& b = pinst[ti][i];
+      const long long chunk = (long long)tpbs[ti] * kItemsPerThread;
+      b.cnt[0] = (b.items[0] + chunk - 1) / chunk;
+      b.cnt[2] = (b.items[2] + chunk - 1) / chunk;
+      for (int ph = 0; ph < 4; ++ph) {
+        b.off[ph] = bt->ptot[ti][ph];
+        bt->ptot[ti][ph] += b.cnt[ph];
+        maps[ti][ph].insert(maps[ti][ph].end(), (size_t)b.cnt[ph], i);
+      }
+    }
+  }
   if (cudaStreamCreateWithFlags(&bt->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaMalloc(&bt->d_pinst, 2 * sizeof(BatchInst) * n) != cudaSuccess ||
       cudaMalloc(&bt->d_inst, 2 * sizeof(BatchInst) * n) != cudaSuccess ||
       cudaMalloc(&bt->d_bar, 2 * sizeof(unsigned)) != cudaSuccess || cudaMalloc(&bt->d_err, sizeof(int)) != cudaSuccess) {
     nsk_batch_destroy(bt);
     return NSK_ERR_NOMEM;
   }
-  for (int ti = 0; ti < 2; ++ti)
+  for (int ti = 0; ti < 2; ++ti) {
     if (cudaMemcpy(bt->d_inst + (size_t)ti * n, bt->h_inst[ti].data(), sizeof(BatchInst) * n,
+                   cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(bt->d_pinst + (size_t)ti * n, pinst[ti].data(), sizeof(BatchInst) * n,
                    cudaMemcpyHostToDevice) != cudaSuccess) {
       nsk_batch_destroy(bt);
       return NSK_ERR_CUDA;
     }
+    for (int ph = 0; ph < 4; ++ph) {
+      const size_t bytes = sizeof(int) * maps[ti][ph].size();
+      if (cudaMalloc(&bt->d_blk2inst[ti][ph], bytes) != cudaSuccess ||
+          cudaMemcpy(bt->d_blk2inst[ti][ph], maps[ti][ph].data(), bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
+        nsk_batch_destroy(bt);
+        return NSK_ERR_NOMEM;
+      }
+    }
+  }
   if (cudaMemset(bt->d_bar, 0, 2 * sizeof(unsigned)) != cudaSuccess || cudaMemset(bt->d_err, 0, sizeof(int)) != cudaSuccess) {
     nsk_batch_destroy(bt);
     return NSK_ERR_CUDA;
@@ -372,45 +570,49 @@ int nsk_batch_create(nsk_batch** out, int n, nsk_ctx* const* instances) {
   return NSK_OK;
 }
 
-int nsk_batch_set_schedule(nsk_batch* bt, int tpb, int fused_face) {
+int nsk_batch_set_schedule(nsk_batch* bt, int tpb, int fused_face, int persistent) {
   if (!bt || (tpb != 128 && tpb != 256)) return NSK_ERR_ARG;
   bt->tpb = tpb;
   bt->fused = fused_face ? 1 : 0;
+  bt->persistent = persistent ? 1 : 0;
   return NSK_OK;
 }
 
-int nsk_batch_get_schedule(nsk_batch* bt, int* tpb, int* fused_face) {
+int nsk_batch_get_schedule(nsk_batch* bt, int* tpb, int* fused_face, int* persistent) {
   if (!bt) return NSK_ERR_ARG;
   if (tpb) *tpb = bt->tpb;
   if (fused_face) *fused_face = bt->fused;
+  if (persistent) *persistent = bt->persistent;
   return NSK_OK;
 }
 
-int nsk_batch_autotune(nsk_batch* bt, int* tpb_out, int* fused_out, double* ms_out) {
+int nsk_batch_autotune(nsk_batch* bt, int* tpb_out, int* fused_out, int* persistent_out, double* ms_out) {
   if (!bt) return NSK_ERR_ARG;
   for (nsk_ctx* c : bt->inst)
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return NSK_ERR_CUDA;
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return NSK_ERR_CUDA;
   double best = 1e300;
-  int bt_tpb = bt->tpb, bt_f = bt->fused, st = NSK_OK;
+  int bt_tpb = bt->tpb, bt_f = bt->fused, bt_p = bt->persistent, st = NSK_OK;
   const int tpbs[2] = {128, 256};
-  for (int ti = 0; ti < 2 && st == NSK_OK; ++ti)
-    for (int f = 0; f < 2 && st == NSK_OK; ++f) {
-      st = launch_batch(bt, NSK_MODE_RHS, 0.0, 0.0, tpbs[ti], f);  // warm-up (residual mode: state untouched)
-      if (st) break;
-      cudaEventRecord(e0, bt->stream);
-      for (int r = 0; r < 3 && st == NSK_OK; ++r) st = launch_batch(bt, NSK_MODE_RHS, 0.0, 0.0, tpbs[ti], f);
-      cudaEventRecord(e1, bt->stream);
-      if (cudaEventSynchronize(e1) != cudaSuccess) st = NSK_ERR_CUDA;
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      if (st == NSK_OK && ms / 3.0 < best) {
-        best = ms / 3.0;
-        bt_tpb = tpbs[ti];
-        bt_f = f;
+  for (int per = 0; per < 2 && st == NSK_OK; ++per)
+    for (int ti = 0; ti < 2 && st == NSK_OK; ++ti)
+      for (int f = 0; f < 2 && st == NSK_OK; ++f) {
+        st = launch_batch(bt, NSK_MODE_RHS, 0.0, 0.0, tpbs[ti], f, per);  // warm-up (residual: state untouched)
+        if (st) break;
+        cudaEventRecord(e0, bt->stream);
+        for (int r = 0; r < 3 && st == NSK_OK; ++r) st = launch_batch(bt, NSK_MODE_RHS, 0.0, 0.0, tpbs[ti], f, per);
+        cudaEventRecord(e1, bt->stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess) st = NSK_ERR_CUDA;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (st == NSK_OK && ms / 3.0 < best) {
+          best = ms / 3.0;
+          bt_tpb = tpbs[ti];
+          bt_f = f;
+          bt_p = per;
+        }
       }
-    }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (st) return st;
@@ -418,8 +620,10 @@ int nsk_batch_autotune(nsk_batch* bt, int* tpb_out, int* fused_out, double* ms_o
   if (st) return st;
   bt->tpb = bt_tpb;
   bt->fused = bt_f;
+  bt->persistent = bt_p;
   if (tpb_out) *tpb_out = bt_tpb;
   if (fused_out) *fused_out = bt_f;
+  if (persistent_out) *persistent_out = bt_p;
   if (ms_out) *ms_out = best;
   return NSK_OK;
 }
@@ -431,7 +635,7 @@ int nsk_batch_step(nsk_batch* bt, int nsteps, double cfl, double* step_ms) {
   const int dtmode = cfl > 0.0 ? 1 : 0;
   if (!bt->no_graph &&
       (!bt->graph || bt->graph_tpb != bt->tpb || bt->graph_fused != bt->fused || bt->graph_dtmode != dtmode ||
-       (dtmode && bt->graph_cfl != cfl))) {
+       bt->graph_persistent != bt->persistent || (dtmode && bt->graph_cfl != cfl))) {
     destroy_graph(bt);
     cudaGraph_t g;
     if (cudaStreamBeginCapture(bt->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return NSK_ERR_CUDA;
@@ -441,7 +645,11 @@ int nsk_batch_step(nsk_batch* bt, int nsteps, double cfl, double* step_ms) {
         const int r = nsk_launch_dt(c->p, c->dim, c->np, c->precision == NSK_FP32_MIXED, c->b, cfl, bt->stream);
         if (r < 0) st = r;
       }
-    for (int s = 0; s < 5 && st == NSK_OK; ++s) st = launch_batch(bt, NSK_MODE_LSRK, kA[s], kB[s], bt->tpb, bt->fused);
+    const long long l0 = bt->launches;
+    for (int s = 0; s < 5 && st == NSK_OK; ++s)
+      st = launch_batch(bt, NSK_MODE_LSRK, kA[s], kB[s], bt->tpb, bt->fused, bt->persistent);
+    bt->graph_launches = bt->launches - l0;
+    bt->launches = l0;  // counted per replay below
     const cudaError_t ce = cudaStreamEndCapture(bt->stream, &g);
     cudaError_t ie = cudaErrorUnknown;
     if (st == NSK_OK && ce == cudaSuccess) {
@@ -456,8 +664,8 @@ int nsk_batch_step(nsk_batch* bt, int nsteps, double cfl, double* step_ms) {
     bt->graph_tpb = bt->tpb;
     bt->graph_fused = bt->fused;
     bt->graph_dtmode = dtmode;
+    bt->graph_persistent = bt->persistent;
     bt->graph_cfl = cfl;
-    bt->launches -= 5;  // counted again per replay below
   }
   std::vector<cudaEvent_t> ev;
   if (step_ms) {
@@ -474,13 +682,13 @@ int nsk_batch_step(nsk_batch* bt, int nsteps, double cfl, double* step_ms) {
           if (r < 0) return r;
         }
       for (int st = 0; st < 5; ++st) {
-        const int r = launch_batch(bt, NSK_MODE_LSRK, kA[st], kB[st], bt->tpb, bt->fused);
+        const int r = launch_batch(bt, NSK_MODE_LSRK, kA[st], kB[st], bt->tpb, bt->fused, bt->persistent);
         if (r) return r;
       }
       if (dtmode) bt->launches += 2 * bt->n;
     } else {
       if (cudaGraphLaunch(bt->graph, bt->stream) != cudaSuccess) return NSK_ERR_CUDA;
-      bt->launches += 5 + (dtmode ? 2 * bt->n : 0);
+      bt->launches += bt->graph_launches + (dtmode ? 2 * bt->n : 0);
     }
     if (step_ms) cudaEventRecord(ev[s + 1], bt->stream);
   }
@@ -523,6 +731,10 @@ void nsk_batch_destroy(nsk_batch* bt) {
   if (bt->stream) cudaStreamSynchronize(bt->stream);
   destroy_graph(bt);
   if (bt->d_inst) cudaFree(bt->d_inst);
+  if (bt->d_pinst) cudaFree(bt->d_pinst);
+  for (int ti = 0; ti < 2; ++ti)
+    for (int ph = 0; ph < 4; ++ph)
+      if (bt->d_blk2inst[ti][ph]) cudaFree(bt->d_blk2inst[ti][ph]);
   if (bt->d_bar) cudaFree(bt->d_bar);
   if (bt->d_err) cudaFree(bt->d_err);
   if (bt->stream) cudaStreamDestroy(bt->stream);

@@ -172,3 +172,21 @@ def head_on_collision_3d(we=40.0, nelem=64, N=3):
     centres (0.25,.5,.5) / (0.75,.5,.5), We in {10, 40, 80}, alpha=1e3, beta=1e-3, mu=1e-3."""
     return Workload(f"head_on_collision_3d_E{nelem}^3_N{N}_We{we:g}", 3, (nelem, nelem, nelem), N, 0,
                     steps=5000, extra={"ic": "collision", "we": we, "radius": 0.2})
+
+
+def serving_batch_3d(n=32, seed=SEED, e_range=(16, 48), n_choices=(3, 4), we_range=(5.0, 100.0),
+                     impact_max=0.5, radius=0.2):
+    """Batch of n 3D head-on collision instances of uneven size: elements per direction
+    uniform in e_range, N uniform in n_choices, We uniform in we_range, impact parameter
+    uniform in [0, impact_max] x 2 radius (centres offset in y), seeded PCG64."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for i in range(n):
+        ne = int(rng.integers(e_range[0], e_range[1] + 1))
+        N = int(rng.choice(n_choices))
+        we = float(rng.uniform(*we_range))
+        b = float(rng.uniform(0.0, impact_max)) * 2.0 * radius
+        c = ((0.25, 0.5 - b / 2, 0.5), (0.75, 0.5 + b / 2, 0.5))
+        out.append(Workload(f"collision_{i}_E{ne}^3_N{N}_We{we:.1f}_b{b:.3f}", 3, (ne, ne, ne), N, 0,
+                            extra={"ic": "collision", "we": we, "radius": radius, "centres": c}))
+    return out

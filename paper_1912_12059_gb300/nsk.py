@@ -58,9 +58,9 @@ SIGNATURES = {
     "nsk_autotune": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), _dp]),
     "nsk_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_void_p)]),
     "nsk_batch_step": (C.c_int, [C.c_void_p, C.c_int, C.c_double, _dp]),
-    "nsk_batch_set_schedule": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
-    "nsk_batch_get_schedule": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
-    "nsk_batch_autotune": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), _dp]),
+    "nsk_batch_set_schedule": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int]),
+    "nsk_batch_get_schedule": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "nsk_batch_autotune": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int), _dp]),
     "nsk_batch_launch_count": (C.c_longlong, [C.c_void_p]),
     "nsk_batch_uses_graph": (C.c_int, [C.c_void_p]),
     "nsk_batch_set_timeout": (C.c_int, [C.c_void_p, C.c_double]),
@@ -304,18 +304,22 @@ class Batch:
         _check(load_library().nsk_batch_step(self.h, nsteps, cfl, ms), "nsk_batch_step")
         return list(ms)[:nsteps] if timings else None
 
-    def set_schedule(self, tpb=256, fused_face=True):
-        _check(load_library().nsk_batch_set_schedule(self.h, tpb, int(bool(fused_face))), "nsk_batch_set_schedule")
+    def set_schedule(self, tpb=256, fused_face=False, persistent=True):
+        _check(load_library().nsk_batch_set_schedule(self.h, tpb, int(bool(fused_face)), int(bool(persistent))),
+               "nsk_batch_set_schedule")
 
     def get_schedule(self):
-        t, f = C.c_int(), C.c_int()
-        _check(load_library().nsk_batch_get_schedule(self.h, C.byref(t), C.byref(f)), "nsk_batch_get_schedule")
-        return t.value, bool(f.value)
+        t, f, p = C.c_int(), C.c_int(), C.c_int()
+        _check(load_library().nsk_batch_get_schedule(self.h, C.byref(t), C.byref(f), C.byref(p)),
+               "nsk_batch_get_schedule")
+        return t.value, bool(f.value), bool(p.value)
 
     def autotune(self):
-        t, f, ms = C.c_int(), C.c_int(), C.c_double()
-        _check(load_library().nsk_batch_autotune(self.h, C.byref(t), C.byref(f), C.byref(ms)), "nsk_batch_autotune")
-        return t.value, bool(f.value), ms.value
+        """Time all eight schedules on the batch; keep and return (tpb, fused, persistent, ms)."""
+        t, f, p, ms = C.c_int(), C.c_int(), C.c_int(), C.c_double()
+        _check(load_library().nsk_batch_autotune(self.h, C.byref(t), C.byref(f), C.byref(p), C.byref(ms)),
+               "nsk_batch_autotune")
+        return t.value, bool(f.value), bool(p.value), ms.value
 
     def set_timeout(self, seconds):
         _check(load_library().nsk_batch_set_timeout(self.h, seconds), "nsk_batch_set_timeout")

@@ -85,11 +85,11 @@ def test_batch_equals_solo_runs(gpu, precision, adaptive):
         s.set_state(U)
         s.compute_dt(0.5)
     b = nsk.Batch([s for s, _ in inst])
-    for tpb, fused in ((256, True), (128, False)):
+    for tpb, fused, persistent in ((256, True, True), (128, False, True), (256, False, False), (128, True, False)):
         for s, U in inst:
             s.set_state(U)
             s.compute_dt(0.5)
-        b.set_schedule(tpb, fused)
+        b.set_schedule(tpb, fused, persistent)
         ms = b.step(3, cfl=0.5 if adaptive else 0.0, timings=True)
         assert len(ms) == 3 and all(m > 0 for m in ms)
         for (s, _), want in zip(inst, expect):
@@ -105,12 +105,14 @@ def test_batch_autotune_graph_and_launch_count(gpu):
         s.set_state(U)
         s.compute_dt(0.5)
     b = nsk.Batch([s for s, _ in inst])
-    tpb, fused, ms = b.autotune()
-    assert tpb in (128, 256) and ms > 0 and b.get_schedule() == (tpb, fused)
-    n0 = b.launch_count
-    b.step(2)
-    assert b.uses_graph
-    assert b.launch_count - n0 == 2 * 5
+    tpb, fused, persistent, ms = b.autotune()
+    assert tpb in (128, 256) and ms > 0 and b.get_schedule() == (tpb, fused, persistent)
+    for persistent, per_stage in ((True, 1), (False, 4)):
+        b.set_schedule(256, False, persistent)
+        n0 = b.launch_count
+        b.step(2)
+        assert b.uses_graph
+        assert b.launch_count - n0 == 2 * 5 * per_stage
     b.close()
     for s, _ in inst:
         s.close()
@@ -126,6 +128,7 @@ def test_batch_barrier_wait_is_bounded(gpu):
         s.set_state(U)
         s.compute_dt(0.5)
     b = nsk.Batch([s for s, _ in inst])
+    b.set_schedule(256, False, True)
     b.set_timeout(0.05)
     b.poison_barrier()
     t0 = time.perf_counter()
