@@ -201,6 +201,26 @@ int nsk_batch_set_timeout(nsk_batch* batch, double seconds);
 int nsk_batch_poison_barrier(nsk_batch* batch);
 void nsk_batch_destroy(nsk_batch* batch);
 
+/* Dense BF16 GEMM on the tensor cores (tcgen05, FP32 accumulation in tensor
+ * memory), the building block of the learned closure's network:
+ *   C[M x N] = A[M x K] . B[N x K]^T,
+ * A and B BF16 device arrays with K contiguous (row strides lda, ldb, multiples
+ * of 8; K a multiple of 16; 16 <= N <= 256, N a multiple of 16), split over K
+ * in slices of k_split (a multiple of 64, or <= 0 for none). Epilogues:
+ * 0 store C + bias (bias may be NULL) as FP32 out[M][ldo];
+ * 1 atomicAdd C into out (split-K partial sums);
+ * 2 z = C + bias: z -> out (FP32, may be NULL), GELU(z) -> hout (BF16 [M][ldh])
+ *   and, if hout_t is not NULL, its transpose -> hout_t (BF16 [N][ldt]);
+ * 3 dz = C * GELU'(zin[M][ldz]) -> hout (BF16) and hout_t, column sums of dz
+ *   added to bias_grad (if not NULL).
+ * GELU(x) = x Phi(x) (exact, with erf). err: device int that receives
+ * NSK_EBIT_TIMEOUT (8) if a bounded tensor-core wait expires (NULL: an
+ * internal word). Queued on stream; no synchronisation. No counterpart in the
+ * paper: it serves the per-element network of the learned closure. */
+int nsk_gemm_bf16(const void* A, const void* B, int M, int N, int K, int lda, int ldb, int k_split, int epilogue,
+                  const float* bias, float* out, int ldo, void* hout, int ldh, void* hout_t, int ldt,
+                  const float* zin, int ldz, float* bias_grad, int* err, void* stream);
+
 /* Allocation-free residual. The paper has no counterpart: this entry point
  * exists for callers that cannot allocate device memory, e.g. a plugin inside a
  * host application that owns all device memory through its own pool, or a

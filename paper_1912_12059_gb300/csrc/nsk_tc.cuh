@@ -1,0 +1,262 @@
+// nsk_tc.cuh -- BF16 GEMM on the sm_103a tensor cores (tcgen05, accumulators in TMEM).
+//
+//   C[M x N] = A[M x K] . B[N x K]^T      (A and B BF16, K contiguous; FP32 accumulation)
+//
+// One CTA of 128 threads owns a 128-row tile of C and the whole N (16 <= N <= 256,
+// N % 16 == 0) and a range of K (split-K over gridDim.y). K is consumed in chunks of
+// 64: all threads stage the A and B chunks in shared memory in the canonical
+// K-major, no-swizzle core-matrix layout (8 rows x 16 bytes per core matrix), one
+// elected thread issues the tcgen05.mma instructions (M = 128, K = 16 each) into a
+// TMEM accumulator of N FP32 columns, and tcgen05.commit arrives on an mbarrier that
+// all threads wait on (bounded in time) before the chunk buffers are reused. The
+// epilogue reads the accumulator with tcgen05.ld (warp w owns TMEM lanes 32w..32w+31,
+// i.e. rows 32w..32w+31 of the tile) and applies one of the fused epilogues below.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "nsk_internal.h"
+
+namespace nsk {
+namespace tc {
+
+constexpr int kBM = 128;      // rows of C per CTA (TMEM lanes)
+constexpr int kKC = 64;       // K chunk staged per pipeline step
+constexpr int kMaxN = 256;    // TMEM columns allocated
+constexpr int kThreads = 128;
+constexpr unsigned long long kWaitNs = 1000000000ull;  // bound of every mbarrier wait
+
+enum Epilogue : int {
+  EPI_STORE = 0,   // C (+ bias) -> FP32 out
+  EPI_ATOMIC = 1,  // atomicAdd(out, C): split-K partial sums
+  EPI_GELU = 2,    // z = C + bias: z -> zout (FP32, optional), GELU(z) -> hout (BF16), optional transposed copy
+  EPI_DGELU = 3,   // dz = C * GELU'(zin): dz -> hout (BF16) and transposed copy, column sums -> bias_grad
+};
+
+struct GemmArgs {
+  const __nv_bfloat16* A;  // [M][lda]
+  const __nv_bfloat16* B;  // [N][ldb]
+  int M, N, K, lda, ldb;
+  int k_split;             // K per gridDim.y slice (multiple of kKC), or K
+  int epi;
+  const float* bias;       // [N] or NULL
+  float* out;              // FP32 [M][ldo] (STORE, ATOMIC) or z [M][ldo] (GELU, optional)
+  int ldo;
+  __nv_bfloat16* hout;     // BF16 [M][ldh] (GELU, DGELU)
+  int ldh;
+  __nv_bfloat16* hout_t;   // BF16 [N][ldt] transposed copy (optional)
+  int ldt;
+  const float* zin;        // FP32 [M][ldz] pre-activation (DGELU)
+  int ldz;
+  float* bias_grad;        // [N] column sums (DGELU, optional)
+  int* err;                // error word (NSK_EBIT_TIMEOUT on an expired wait)
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ unsigned long long tc_global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// tcgen05 shared-memory matrix descriptor: K-major, no swizzle. lbo = byte distance between
+// core matrices adjacent in K, sbo = between core matrices adjacent in M (or N).
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;  // fixed constant 0b001 in bits 46-48; swizzle mode (61-63) = 0
+  return d;
+}
+
+// instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, shape M x N
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// byte offset of element (r, k) of a [rows x kKC] chunk in the core-matrix layout
+__device__ __forceinline__ uint32_t core_off(int r, int k) {
+  return (uint32_t)((((r >> 3) * (kKC / 8) + (k >> 3)) << 7) + ((r & 7) << 4) + ((k & 7) << 1));
+}
+
+__device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_grad(float x) {
+  return 0.5f * (1.0f + erff(x * 0.70710678118654752f)) + x * 0.3989422804014327f * __expf(-0.5f * x * x);
+}
+
+// stage rows [0, nrows) of a chunk of a K-major BF16 matrix (row stride ld) at column k0
+// into shared memory; rows beyond `valid_rows` and columns beyond `kmax` are zero
+__device__ __forceinline__ void stage_chunk(unsigned char* s, const __nv_bfloat16* g, int ld, int nrows,
+                                            int valid_rows, int k0, int kmax) {
+  for (int idx = threadIdx.x; idx < nrows * (kKC / 8); idx += kThreads) {
+    const int r = idx / (kKC / 8), j = idx % (kKC / 8);
+    const int k = k0 + j * 8;
+    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+    if (r < valid_rows && k < kmax) v = *reinterpret_cast<const uint4*>(g + (size_t)r * ld + k);
+    *reinterpret_cast<uint4*>(s + core_off(r, j * 8)) = v;
+  }
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase, int* err) {
+  const unsigned long long t0 = tc_global_ns();
+  while (true) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(phase)
+        : "memory");
+    if (done) return true;
+    if (tc_global_ns() - t0 > kWaitNs) {
+      atomicOr(err, NSK_EBIT_TIMEOUT);
+      return false;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const GemmArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  unsigned char* sA = smem;                         // kBM x kKC BF16 = 16 KB
+  unsigned char* sB = smem + kBM * kKC * 2;         // kMaxN x kKC BF16 = 32 KB
+  __shared__ __align__(8) unsigned long long mbar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int aborted;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * kBM;
+  const int kb = blockIdx.y * a.k_split;
+  const int ke = min(a.K, kb + a.k_split);
+  const int rowsA = min(kBM, a.M - m0);
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(kMaxN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (threadIdx.x == 0) {
+    aborted = 0;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar)), "r"(1));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_slot;
+  const uint32_t idesc = idesc_bf16(kBM, a.N);
+  uint32_t phase = 0;
+
+  for (int k0 = kb; k0 < ke; k0 += kKC) {
+    stage_chunk(sA, a.A + (size_t)m0 * a.lda, a.lda, kBM, rowsA, k0, ke);
+    stage_chunk(sB, a.B, a.ldb, a.N, a.N, k0, ke);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const int nk = min(kKC, ke - k0) / 16;
+      for (int s = 0; s < nk; ++s) {
+        // a K step of 16 spans two core matrices along K (2 x 128 bytes)
+        const uint64_t ad = sdesc(smem_u32(sA) + s * 256, 128, (kKC / 8) * 128);
+        const uint64_t bd = sdesc(smem_u32(sB) + s * 256, 128, (kKC / 8) * 128);
+        const uint32_t acc = (k0 > kb || s > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+            "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(&mbar)));
+    }
+    const bool ok = mbar_wait(smem_u32(&mbar), phase, a.err);
+    phase ^= 1u;
+    if (!ok) aborted = 1;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    __syncthreads();
+    if (aborted) break;
+  }
+
+  if (!aborted && ke > kb) {
+    const int r = warp * 32 + lane;  // row of the tile owned by this thread
+    const int m = m0 + r;
+    const bool rv = m < a.M;
+    for (int c0 = 0; c0 < a.N; c0 += 32) {
+      uint32_t v[32];
+      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+          "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+            "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]),
+            "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]),
+            "=r"(v[30]), "=r"(v[31])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      const int ncol = min(32, a.N - c0);
+      float colsum[32];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        colsum[j] = 0.f;
+        if (j >= ncol) continue;
+        const int n = c0 + j;
+        float x = __uint_as_float(v[j]);
+        if (a.epi == EPI_STORE) {
+          if (rv) a.out[(size_t)m * a.ldo + n] = x + (a.bias ? a.bias[n] : 0.f);
+        } else if (a.epi == EPI_ATOMIC) {
+          if (rv) atomicAdd(&a.out[(size_t)m * a.ldo + n], x);
+        } else if (a.epi == EPI_GELU) {
+          const float z = x + (a.bias ? a.bias[n] : 0.f);
+          if (rv) {
+            if (a.out) a.out[(size_t)m * a.ldo + n] = z;
+            const __nv_bfloat16 h = __float2bfloat16_rn(gelu(z));
+            a.hout[(size_t)m * a.ldh + n] = h;
+            if (a.hout_t) a.hout_t[(size_t)n * a.ldt + m] = h;
+          }
+        } else {  // EPI_DGELU
+          const float dz = rv ? x * gelu_grad(a.zin[(size_t)m * a.ldz + n]) : 0.f;
+          if (rv) {
+            const __nv_bfloat16 h = __float2bfloat16_rn(dz);
+            a.hout[(size_t)m * a.ldh + n] = h;
+            if (a.hout_t) a.hout_t[(size_t)n * a.ldt + m] = h;
+          }
+          colsum[j] = dz;
+        }
+      }
+      if (a.epi == EPI_DGELU && a.bias_grad) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          float s = colsum[j];
+          for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+          if (lane == 0 && j < ncol) atomicAdd(&a.bias_grad[c0 + j], s);
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kMaxN));
+}
+
+// 48 KB of operand chunks; the launch requests 80 KB so that at most two CTAs share an SM
+// and their two 256-column TMEM allocations never contend (512 columns per SM)
+constexpr int kSmemBytes = 80 * 1024;
+
+// host launcher (grid: ceil(M/128) x ceil(K/k_split))
+inline int launch_gemm(const GemmArgs& a, cudaStream_t s) {
+  if (a.M < 1 || a.N < 16 || a.N > kMaxN || (a.N % 16) || a.K < 16 || (a.K % 16) || (a.lda % 8) || (a.ldb % 8) ||
+      a.lda < a.K || a.ldb < a.K || a.k_split < 16 || (a.k_split % kKC && a.k_split < a.K))
+    return NSK_ERR_ARG;
+  static bool attr_done = false;
+  if (!attr_done) {
+    if (cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes) != cudaSuccess)
+      return NSK_ERR_CUDA;
+    attr_done = true;
+  }
+  dim3 grid((unsigned)((a.M + kBM - 1) / kBM), (unsigned)((a.K + a.k_split - 1) / a.k_split));
+  k_gemm_tc<<<grid, kThreads, kSmemBytes, s>>>(a);
+  return cudaGetLastError() == cudaSuccess ? NSK_OK : NSK_ERR_CUDA;
+}
+
+}  // namespace tc
+}  // namespace nsk

@@ -66,6 +66,9 @@ SIGNATURES = {
     "nsk_batch_set_timeout": (C.c_int, [C.c_void_p, C.c_double]),
     "nsk_batch_poison_barrier": (C.c_int, [C.c_void_p]),
     "nsk_batch_destroy": (None, [C.c_void_p]),
+    "nsk_gemm_bf16": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                                C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_int,
+                                C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "nsk_error_string": (C.c_char_p, [C.c_int]),
     "nsk_destroy": (None, [C.c_void_p]),
 }
@@ -345,3 +348,22 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def _ptr_or_null(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def gemm_bf16(A, B, epilogue=0, bias=None, out=None, hout=None, hout_t=None, zin=None, bias_grad=None, k_split=0,
+              err=None, stream=None):
+    """C = A . B^T on the tensor cores for torch CUDA tensors (A [M,K], B [N,K] bfloat16, row-major);
+    see nsk_gemm_bf16 in include/nsk.h for the epilogues. Returns the status code."""
+    M, K = A.shape
+    N = B.shape[0]
+    lib = load_library()
+    return lib.nsk_gemm_bf16(_ptr_or_null(A), _ptr_or_null(B), M, N, K, A.stride(0), B.stride(0), k_split, epilogue,
+                             _ptr_or_null(bias), _ptr_or_null(out), out.stride(0) if out is not None else 0,
+                             _ptr_or_null(hout), hout.stride(0) if hout is not None else 0, _ptr_or_null(hout_t),
+                             hout_t.stride(0) if hout_t is not None else 0, _ptr_or_null(zin),
+                             zin.stride(0) if zin is not None else 0, _ptr_or_null(bias_grad), _ptr_or_null(err),
+                             C.c_void_p(stream) if stream else None)
