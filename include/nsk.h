@@ -69,6 +69,7 @@ enum {
 enum { NSK_NODES_GAUSS = 0, NSK_NODES_GAUSS_LOBATTO = 1 };
 enum { NSK_FP64 = 0, NSK_FP32_MIXED = 1 };
 enum { NSK_HOST = 0, NSK_DEVICE = 1 };
+enum { NSK_C_EXPLICIT = 0, NSK_C_LEARNED = 1 };
 
 /* Create a context for a periodic box [lo, hi] (per direction) split into
  * nelem[k] equal elements per direction k < dim (entries k >= dim ignored),
@@ -220,6 +221,64 @@ void nsk_batch_destroy(nsk_batch* batch);
 int nsk_gemm_bf16(const void* A, const void* B, int M, int N, int K, int lda, int ldb, int k_split, int epilogue,
                   const float* bias, float* out, int ldo, void* hout, int ldh, void* hout_t, int ldt,
                   const float* zin, int ldz, float* bias_grad, int* err, void* stream);
+
+/* Per-element network of the learned c-closure (no counterpart in the paper;
+ * its target is the quasi-equilibrium of the c equation, the Korteweg-limit
+ * remark of Sec. 2.3: c - (kappa/alpha) Lap c = rho). A fully connected
+ * network n_in -> h1 -> h2 -> n_out with GELU hidden layers; BF16 weights and
+ * activations, FP32 accumulation on the tensor cores, FP32 master parameters
+ * trained with Adam. h1, h2, n_out multiples of 16 and <= 256, n_in <= 256
+ * (padded to a multiple of 16 with zero inputs). Training batches have
+ * max_batch rows at most (a multiple of 16); inference max_rows rows. All
+ * device buffers are allocated at creation. */
+typedef struct nsk_mlp nsk_mlp;
+int nsk_mlp_create(nsk_mlp** out, int n_in, int h1, int h2, int n_out, int max_batch, int max_rows, void* stream);
+long long nsk_mlp_num_params(nsk_mlp* mlp);
+/* FP32 parameters as one host array: W1 [h1][n_in_pad], b1 [h1], W2 [h2][h1],
+ * b2 [h2], W3 [n_out][h2], b3 [n_out] (layer l: y = W_l x + b_l). Setting
+ * them resets the Adam moments. */
+int nsk_mlp_set_params(nsk_mlp* mlp, const float* params, long long n);
+int nsk_mlp_get_params(nsk_mlp* mlp, float* params, long long n);
+/* Inference: X BF16 device [rows][n_in_pad] -> Y FP32 device [rows][n_out]. */
+int nsk_mlp_forward(nsk_mlp* mlp, const void* X, int rows, float* Y);
+/* Loss L = mean over rows and outputs of (Y - T)^2 for X BF16 [batch][n_in_pad]
+ * and targets T FP32 [batch][n_out] (device); gradients of L (layout of the
+ * parameters) copied to grads (host, may be NULL); loss (may be NULL). */
+int nsk_mlp_gradients(nsk_mlp* mlp, const void* X, const float* T, int batch, float* grads, double* loss);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) with learning rate lr on
+ * that loss; loss (may be NULL: no synchronisation) receives its value. */
+int nsk_mlp_train_step(nsk_mlp* mlp, const void* X, const float* T, int batch, double lr, double* loss);
+long long nsk_mlp_launch_count(nsk_mlp* mlp);
+void nsk_mlp_destroy(nsk_mlp* mlp);
+
+/* Learned c-closure of a 3D context (cubic elements): with mode
+ * NSK_C_LEARNED, before every Runge-Kutta stage and after every step the
+ * relaxation variable is replaced by c = rho + s y, y = network(features),
+ * s = (kappa/alpha) (2/h)^2, so the stiff c equation (source alpha/beta,
+ * diffusion kappa/beta) no longer bounds the time step: nsk_compute_dt and
+ * adaptive steps drop both bounds. Features per element: the npe nodal
+ * densities and the mean densities of the 2 dim face neighbours (order x-, x+,
+ * y-, y+, z-, z+), each minus the element's mean density and divided by 0.5
+ * (nf = npe + 2 dim values); each value v enters as the BF16 pair
+ * hi = bf16(v), lo = bf16(v - hi), so the network input is n_in = 2 nf
+ * (hi values first, then lo values); n_out = npe. Every judge_every steps (0: never) the
+ * judge evaluates the explicit c equation at the closure's state,
+ * eta = ||(beta/alpha) R_c|| / ||c - rho|| (the relative residual of the
+ * quasi-equilibrium), and if eta > eta_max the context falls back to
+ * NSK_C_EXPLICIT (the closure's c becomes the initial c of the explicit
+ * equation). mode NSK_C_EXPLICIT switches the closure off. The network is
+ * borrowed and must outlive its use (its max_rows >= number of elements). */
+int nsk_set_closure(nsk_ctx* ctx, int mode, nsk_mlp* mlp, int judge_every, double eta_max);
+int nsk_closure_status(nsk_ctx* ctx, int* mode, double* last_eta, long long* fallbacks);
+/* Training data of the current state: features (BF16 device [E][n_in_pad],
+ * n_in_pad = round-up of 2 (npe + 2 dim) to 16) and targets y = (c - rho) / s
+ * (FP32 device [E][npe]). */
+int nsk_closure_features(nsk_ctx* ctx, void* X);
+int nsk_closure_targets(nsk_ctx* ctx, float* Y);
+/* Apply the closure once to the current state (also done by nsk_step), and
+ * evaluate the judge now (returns eta). */
+int nsk_closure_apply(nsk_ctx* ctx);
+int nsk_closure_judge(nsk_ctx* ctx, double* eta);
 
 /* Allocation-free residual. The paper has no counterpart: this entry point
  * exists for callers that cannot allocate device memory, e.g. a plugin inside a

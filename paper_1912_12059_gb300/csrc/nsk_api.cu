@@ -259,7 +259,7 @@ int export_nodal(nsk_ctx* c, const void* src, int ncomp, double* dst, int where)
 void free_ctx(nsk_ctx* c) {
   if (!c) return;
   void* ptrs[] = {c->b.U, c->b.K, c->b.Q, c->b.Utr, c->b.FVtr, c->b.Fstar, c->b.err, c->b.lam,
-                  c->b.dt, c->b.part, c->rbuf, c->stage64};
+                  c->b.dt, c->b.part, c->rbuf, c->stage64, c->cl_X, c->cl_Y, c->cl_red};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   for (cudaEvent_t ev : c->prof_pool) cudaEventDestroy(ev);
@@ -514,10 +514,24 @@ int nsk_step(nsk_ctx* c, double dt, int nsteps) {
       if (r < 0) return r;
       c->launches += r;
     }
+    const bool learned = c->closure_mode == NSK_C_LEARNED;
     for (int st = 0; st < 5; ++st) {
+      if (learned) {
+        const int r = nsk_closure_apply_ctx(c);
+        if (r) return r;
+      }
       NskLaunch l = {NSK_MODE_LSRK, nullptr, kA[st], kB[st], adaptive ? c->b.dt : nullptr, dt, nullptr, c->tpb, c->fused_face};
       int r = launch_stage(c, l);
       if (r) return r;
+    }
+    if (learned) {
+      int r = nsk_closure_apply_ctx(c);  // the stored state carries the closure's c
+      if (r) return r;
+      if (c->judge_every > 0 && ++c->steps_since_judge >= c->judge_every) {
+        c->steps_since_judge = 0;
+        r = nsk_closure_judge_ctx(c);
+        if (r) return r;
+      }
     }
   }
   return sync_and_check(c);

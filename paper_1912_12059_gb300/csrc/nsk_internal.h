@@ -47,6 +47,7 @@ struct NskParams {
   double rh[3];    // 2 / h_k (Cartesian metric terms)
   double T, kappa, alpha, beta, mu;
   double jac;      // J = prod_k h_k / 2
+  int closure;     // 1: the c equation is replaced by the learned closure (dt without its bounds)
   // EoS constants: p_alpha = t8 rho q + pa2 rho^2, p_alpha' = t24 q^2 + dpa1 rho, q = 1/(3 - rho)
   double t8, t24, pa2, dpa1;
   float t8f, t24f, pa2f, dpa1f;
@@ -134,7 +135,18 @@ struct nsk_ctx {
   double prof_ms[NSK_NKERN];
   long long prof_cnt[NSK_NKERN];
   int tpb, fused_face;  // stage schedule (nsk_set_schedule / nsk_autotune)
+  // learned c-closure (nsk_set_closure)
+  int closure_mode;            // NSK_C_EXPLICIT or NSK_C_LEARNED
+  struct nsk_mlp* mlp;         // borrowed network
+  int judge_every;             // steps between two judge evaluations (0: never)
+  double eta_max, last_eta;    // fallback threshold, last judged error
+  long long fallbacks, steps_since_judge;
+  void* cl_X;                  // BF16 features [E][n_in_pad]
+  float* cl_Y;                 // network output [E][npe]
+  double* cl_red;              // judge sums
 };
 
 // host helpers shared by the translation units of the library
 int nsk_ctx_launch_stage(nsk_ctx* c, NskLaunch l);  // queues one stage on the context's stream
+int nsk_closure_apply_ctx(nsk_ctx* c);               // c := rho + s * network(features(rho))
+int nsk_closure_judge_ctx(nsk_ctx* c);               // judge + fallback (synchronises)

@@ -589,15 +589,18 @@ static __global__ void k_dt_final(const NskParams p, const int dim, const int N,
   const double lmax = __longlong_as_double((long long)*lam);
   const double tn = 2.0 * N + 1.0;
   double r = cfl / (tn * lmax);
-  const double lamv = p.mu > p.kappa / p.beta ? p.mu : p.kappa / p.beta;
+  // with the learned closure the c equation (diffusion kappa/beta, source alpha/beta) is not integrated
+  const double lamv = p.closure ? p.mu : (p.mu > p.kappa / p.beta ? p.mu : p.kappa / p.beta);
   double ih2 = 0.0;
   for (int k = 0; k < dim; ++k) ih2 += 0.25 * p.rh[k] * p.rh[k];
   if (lamv > 0.0) {
     const double dv = cfl / (tn * tn * lamv * ih2);
     r = dv < r ? dv : r;
   }
-  const double ds = cfl * 4.6 * p.beta / p.alpha;
-  r = ds < r ? ds : r;
+  if (!p.closure) {
+    const double ds = cfl * 4.6 * p.beta / p.alpha;
+    r = ds < r ? ds : r;
+  }
   *dt = r;
 }
 

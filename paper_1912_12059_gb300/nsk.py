@@ -29,6 +29,8 @@ NSK_FP64 = 0
 NSK_FP32_MIXED = 1
 NSK_HOST = 0
 NSK_DEVICE = 1
+NSK_C_EXPLICIT = 0
+NSK_C_LEARNED = 1
 
 #: every symbol include/nsk.h declares, with (restype, argtypes)
 _dp = C.POINTER(C.c_double)
@@ -69,6 +71,22 @@ SIGNATURES = {
     "nsk_gemm_bf16": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                 C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_int,
                                 C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "nsk_mlp_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                                 C.c_void_p]),
+    "nsk_mlp_num_params": (C.c_longlong, [C.c_void_p]),
+    "nsk_mlp_set_params": (C.c_int, [C.c_void_p, C.c_void_p, C.c_longlong]),
+    "nsk_mlp_get_params": (C.c_int, [C.c_void_p, C.c_void_p, C.c_longlong]),
+    "nsk_mlp_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "nsk_mlp_gradients": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, _dp]),
+    "nsk_mlp_train_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_double, _dp]),
+    "nsk_mlp_launch_count": (C.c_longlong, [C.c_void_p]),
+    "nsk_mlp_destroy": (None, [C.c_void_p]),
+    "nsk_set_closure": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_double]),
+    "nsk_closure_status": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), _dp, C.POINTER(C.c_longlong)]),
+    "nsk_closure_features": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "nsk_closure_targets": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "nsk_closure_apply": (C.c_int, [C.c_void_p]),
+    "nsk_closure_judge": (C.c_int, [C.c_void_p, _dp]),
     "nsk_error_string": (C.c_char_p, [C.c_int]),
     "nsk_destroy": (None, [C.c_void_p]),
 }
@@ -270,6 +288,40 @@ class Solver:
         _check(load_library().nsk_autotune(self.ctx, C.byref(t), C.byref(f), C.byref(ms)), "nsk_autotune")
         return t.value, bool(f.value), ms.value
 
+    # -- learned c-closure --
+    @property
+    def closure_inputs(self):
+        """Network inputs of the closure: hi and lo BF16 parts of npe + 2 dim features."""
+        return 2 * (self.npe + 2 * self.dim)
+
+    def set_closure(self, mlp=None, judge_every=10, eta_max=0.5):
+        """mlp=None switches back to the explicit c equation."""
+        mode = NSK_C_LEARNED if mlp is not None else NSK_C_EXPLICIT
+        _check(load_library().nsk_set_closure(self.ctx, mode, mlp.h if mlp is not None else None, judge_every,
+                                              eta_max), "nsk_set_closure")
+        self._mlp = mlp
+
+    def closure_status(self):
+        m, e, f = C.c_int(), C.c_double(), C.c_longlong()
+        _check(load_library().nsk_closure_status(self.ctx, C.byref(m), C.byref(e), C.byref(f)), "nsk_closure_status")
+        return {"mode": m.value, "eta": e.value, "fallbacks": f.value}
+
+    def closure_features(self, X):
+        """X: torch bfloat16 CUDA tensor [E, n_in_pad]."""
+        _check(load_library().nsk_closure_features(self.ctx, C.c_void_p(X.data_ptr())), "nsk_closure_features")
+
+    def closure_targets(self, Y):
+        """Y: torch float32 CUDA tensor [E, npe]: (c - rho) / ((kappa/alpha)(2/h)^2)."""
+        _check(load_library().nsk_closure_targets(self.ctx, C.c_void_p(Y.data_ptr())), "nsk_closure_targets")
+
+    def closure_apply(self):
+        _check(load_library().nsk_closure_apply(self.ctx), "nsk_closure_apply")
+
+    def closure_judge(self):
+        e = C.c_double()
+        _check(load_library().nsk_closure_judge(self.ctx, C.byref(e)), "nsk_closure_judge")
+        return e.value
+
     KERNELS = ("k_prolong", "k_lift", "k_face", "k_volume")
 
     def set_profiling(self, on=True):
@@ -367,3 +419,89 @@ def gemm_bf16(A, B, epilogue=0, bias=None, out=None, hout=None, hout_t=None, zin
                              hout_t.stride(0) if hout_t is not None else 0, _ptr_or_null(zin),
                              zin.stride(0) if zin is not None else 0, _ptr_or_null(bias_grad), _ptr_or_null(err),
                              C.c_void_p(stream) if stream else None)
+
+
+class MLP:
+    """Per-element network of the learned closure (include/nsk.h: nsk_mlp_*), n_in -> h1 -> h2 -> n_out."""
+
+    def __init__(self, n_in, h1=256, h2=256, n_out=64, max_batch=8192, max_rows=1, stream=None):
+        h = C.c_void_p()
+        _check(load_library().nsk_mlp_create(C.byref(h), n_in, h1, h2, n_out, max_batch, max_rows,
+                                             C.c_void_p(stream) if stream else None), "nsk_mlp_create")
+        self.h = h
+        self.n_in, self.h1, self.h2, self.n_out = n_in, h1, h2, n_out
+        self.max_batch, self.max_rows = max_batch, max_rows
+        self.n_in_pad = (n_in + 15) // 16 * 16
+        self.n_params = int(load_library().nsk_mlp_num_params(h))
+
+    def layout(self):
+        """[(name, shape)] of the flat FP32 parameter vector."""
+        return [("W1", (self.h1, self.n_in_pad)), ("b1", (self.h1,)), ("W2", (self.h2, self.h1)), ("b2", (self.h2,)),
+                ("W3", (self.n_out, self.h2)), ("b3", (self.n_out,))]
+
+    def unflatten(self, flat):
+        out, o = {}, 0
+        for name, shape in self.layout():
+            n = int(np.prod(shape))
+            out[name] = np.asarray(flat[o:o + n]).reshape(shape)
+            o += n
+        return out
+
+    def init_params(self, seed=0):
+        """He-uniform weights, zero biases (seeded)."""
+        rng = np.random.Generator(np.random.PCG64(seed))
+        parts = []
+        for name, shape in self.layout():
+            if name.startswith("W"):
+                fan_in = self.n_in if name == "W1" else shape[1]
+                w = rng.uniform(-1, 1, size=shape) * np.sqrt(6.0 / fan_in)
+                if name == "W1":
+                    w[:, self.n_in:] = 0.0
+                parts.append(w.ravel())
+            else:
+                parts.append(np.zeros(shape).ravel())
+        self.set_params(np.concatenate(parts).astype(np.float32))
+
+    def set_params(self, flat):
+        flat = np.ascontiguousarray(flat, dtype=np.float32)
+        _check(load_library().nsk_mlp_set_params(self.h, C.c_void_p(flat.ctypes.data), flat.size),
+               "nsk_mlp_set_params")
+
+    def get_params(self):
+        out = np.empty(self.n_params, dtype=np.float32)
+        _check(load_library().nsk_mlp_get_params(self.h, C.c_void_p(out.ctypes.data), out.size), "nsk_mlp_get_params")
+        return out
+
+    def forward(self, X, Y):
+        _check(load_library().nsk_mlp_forward(self.h, C.c_void_p(X.data_ptr()), X.shape[0], C.c_void_p(Y.data_ptr())),
+               "nsk_mlp_forward")
+
+    def gradients(self, X, T):
+        g = np.empty(self.n_params, dtype=np.float32)
+        loss = C.c_double()
+        _check(load_library().nsk_mlp_gradients(self.h, C.c_void_p(X.data_ptr()), C.c_void_p(T.data_ptr()),
+                                                X.shape[0], C.c_void_p(g.ctypes.data), C.byref(loss)),
+               "nsk_mlp_gradients")
+        return g, loss.value
+
+    def train_step(self, X, T, lr, want_loss=False):
+        loss = C.c_double()
+        _check(load_library().nsk_mlp_train_step(self.h, C.c_void_p(X.data_ptr()), C.c_void_p(T.data_ptr()),
+                                                 X.shape[0], lr, C.byref(loss) if want_loss else None),
+               "nsk_mlp_train_step")
+        return loss.value if want_loss else None
+
+    @property
+    def launch_count(self):
+        return int(load_library().nsk_mlp_launch_count(self.h))
+
+    def close(self):
+        if self.h:
+            load_library().nsk_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,192 @@
+"""Learned c-closure on the GPU.
+
+* The tensor-core network (BF16 weights/activations, FP32 accumulation) against the
+  FP64 oracle network on the same BF16-rounded weights and inputs: forward outputs
+  and all parameter gradients. BF16 keeps 8 significant bits, so activations carry
+  a relative rounding of 2^-9; outputs and gradients must agree to a few percent in
+  relative L2 norm (measured: well below the bounds asserted).
+* Training reduces the loss on a learnable map.
+* Features and targets of a state agree with their definition (computed here with numpy).
+* End to end: a network trained on snapshots of the explicit run replaces the stiff
+  c equation; the closure run takes >= 5x larger steps (20x at this size) and stays
+  within 5e-5 relative density L2 error of the explicit FP64 run over the same
+  simulated time (measured 7.7e-6, against a density change of 9.4e-4), and the
+  judge accepts it. An untrained network is rejected by the judge (fallback).
+"""
+import numpy as np
+import pytest
+
+from oracle import mlp as omlp
+from paper_1912_12059_gb300 import closure, inputs, nsk
+
+pytestmark = pytest.mark.gpu
+
+
+def _bf16_round(a):
+    import torch
+
+    return torch.from_numpy(np.asarray(a, dtype=np.float32)).to(torch.bfloat16).double().numpy()
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("n_in,h1,h2,n_out,B", [(70, 256, 256, 64, 512), (40, 64, 128, 32, 256)])
+def test_mlp_forward_and_gradients_match_oracle(gpu, n_in, h1, h2, n_out, B):
+    import torch
+
+    m = nsk.MLP(n_in, h1, h2, n_out, max_batch=B, max_rows=B)
+    m.init_params(seed=3)
+    flat = m.get_params().astype(np.float64)
+    p = omlp.unflatten(flat, m.n_in_pad, h1, h2, n_out)
+    for k in ("W1", "W2", "W3"):
+        p[k] = _bf16_round(p[k])  # the GPU multiplies BF16 copies of the weights
+    rng = np.random.default_rng(4)
+    Xn = np.zeros((B, m.n_in_pad))
+    Xn[:, :n_in] = rng.uniform(-1, 1, size=(B, n_in))
+    Xt = torch.from_numpy(Xn).to(torch.bfloat16)
+    Xq = Xt.double().numpy()
+    Tn = rng.normal(size=(B, n_out)) * 0.5
+    X, T = Xt.to(gpu), torch.from_numpy(Tn).float().to(gpu)
+    Y = torch.empty((B, n_out), dtype=torch.float32, device=gpu)
+    m.forward(X, Y)
+    torch.cuda.synchronize()
+    y_ref, _ = omlp.forward(p, Xq)
+    assert _rel(Y.cpu().double().numpy(), y_ref) < 1e-2
+    g_gpu, loss = m.gradients(X, T)
+    L_ref, g_ref = omlp.loss_and_grad(p, Xq, Tn)
+    assert abs(loss - L_ref) / L_ref < 1e-2
+    gg = m.unflatten(g_gpu.astype(np.float64))
+    for k in ("W1", "b1", "W2", "b2", "W3", "b3"):
+        a, b = gg[k].ravel(), g_ref[k].ravel()
+        if k == "W1":
+            a, b = gg[k][:, :n_in].ravel(), g_ref[k][:, :n_in].ravel()
+            assert np.abs(gg[k][:, n_in:]).max() == 0.0  # padded inputs carry no gradient
+        assert _rel(a, b) < 4e-2, k
+        assert float(a @ b / (np.linalg.norm(a) * np.linalg.norm(b))) > 0.999, k
+    m.close()
+
+
+def test_mlp_training_fits_a_smooth_map(gpu):
+    import torch
+
+    n_in, n_out, S = 24, 16, 16384
+    m = nsk.MLP(n_in, 64, 64, n_out, max_batch=2048, max_rows=S)
+    m.init_params(seed=1)
+    rng = np.random.default_rng(2)
+    Xn = np.zeros((S, 32))
+    Xn[:, :n_in] = rng.uniform(-1, 1, size=(S, n_in))
+    A = rng.normal(size=(n_in, n_out)) / np.sqrt(n_in)
+    Tn = np.tanh(Xn[:, :n_in] @ A)
+    X = torch.from_numpy(Xn).to(torch.bfloat16).to(gpu)
+    T = torch.from_numpy(Tn).float().to(gpu)
+    e0 = closure.validation_error(m, X, T)
+    closure.train(m, X, T, steps=2500, batch=2048, lr=3e-3, lr_min=1e-4)
+    e1 = closure.validation_error(m, X, T)
+    assert e1 < 0.05 * e0 and e1 < 0.1, (e0, e1)
+    m.close()
+
+
+def _collision_solver(ne=12, N=3, kappa=2.5e-3, precision=nsk.NSK_FP64):
+    import oracle as O
+
+    s = nsk.Solver(3, (ne,) * 3, N, [0, 0, 0], [1, 1, 1], 0, precision)
+    s.set_params(T=0.85, kappa=kappa, alpha=1e3, beta=1e-3, mu=1e-3)
+    rv, rl, _ = O.maxwell(0.85)
+    v = inputs.collision_velocity(40.0, 0.2, kappa, rv, rl)
+    U = inputs.head_on_collision(s.node_coords(), v, 0.2, rho_vap=rv, rho_liq=rl, kappa=kappa)
+    return s, U
+
+
+def test_closure_features_and_targets(gpu):
+    import torch
+
+    s, U = _collision_solver(ne=5)
+    U[4] = U[0] + 1e-4 * np.sin(7 * U[0])
+    s.set_state(U)
+    npe, E = s.npe, s.E
+    nf = npe + 6
+    X = torch.empty((E, 144), dtype=torch.bfloat16, device=gpu)
+    Y = torch.empty((E, npe), dtype=torch.float32, device=gpu)
+    s.closure_features(X)
+    s.closure_targets(Y)
+    rho = U[0]
+    means = rho.mean(axis=1)
+    feat = np.zeros((E, nf))
+    feat[:, :npe] = (rho - means[:, None]) / 0.5
+    for e in range(E):
+        c = [e % 5, (e // 5) % 5, e // 25]
+        j = 0
+        for k in range(3):
+            for d in (-1, 1):
+                cc = list(c)
+                cc[k] = (cc[k] + d) % 5
+                feat[e, npe + j] = (means[cc[0] + 5 * cc[1] + 25 * cc[2]] - means[e]) / 0.5
+                j += 1
+    got = X.cpu().double().numpy()
+    combined = got[:, :nf] + got[:, nf:2 * nf]  # hi + lo carries ~16 significant bits
+    assert np.abs(combined - feat).max() <= 2e-5 * max(1.0, np.abs(feat).max())
+    assert np.all(got[:, 2 * nf:] == 0.0)
+    scale = 2.5e-3 / 1e3 * (2 * 5) ** 2
+    assert np.allclose(Y.cpu().double().numpy(), (U[4] - U[0]) / scale, rtol=1e-6, atol=1e-6)
+    s.close()
+
+
+def test_closure_replaces_the_stiff_c_equation(gpu):
+    """Train on snapshots of the explicit run, then run the closure to the same time."""
+    import torch
+
+    s, U0 = _collision_solver()
+    s.set_state(U0)
+    dt_exp = s.compute_dt(0.5)
+    X, Y = closure.collect_snapshots(s, dt_exp, first_step=20, every=8, count=24)
+    m = nsk.MLP(s.closure_inputs, 256, 256, s.npe, max_batch=4096, max_rows=s.E)
+    m.init_params(seed=0)
+    closure.train(m, X, Y, steps=4000, batch=2048, lr=3e-3, lr_min=3e-5)
+    val = closure.validation_error(m, X, Y)
+    assert val < 0.06, val  # relative L2 error of c - rho over the snapshots (measured 0.046)
+    # reference: explicit FP64 run from a quasi-equilibrated state
+    s.set_state(U0)
+    s.step(dt_exp, 20)
+    Ustart = s.get_state()
+    n_exp = 160
+    s.step(dt_exp, n_exp)
+    U_exp = s.get_state()
+    t_end = n_exp * dt_exp
+    # closure run over the same time with its own (larger) step
+    c, _ = _collision_solver()
+    c.set_state(Ustart)
+    c.set_closure(m, judge_every=5, eta_max=0.5)
+    dt_cl = c.compute_dt(0.5)
+    assert dt_cl >= 5 * dt_exp, (dt_cl, dt_exp)
+    n_cl = int(np.ceil(t_end / dt_cl))
+    c.step(t_end / n_cl, n_cl)
+    st = c.closure_status()
+    assert st["mode"] == nsk.NSK_C_LEARNED and st["fallbacks"] == 0, st
+    U_cl = c.get_state()
+    d_rho = np.linalg.norm(U_cl[0] - U_exp[0]) / np.linalg.norm(U_exp[0])
+    change = np.linalg.norm(U_exp[0] - Ustart[0]) / np.linalg.norm(U_exp[0])
+    print(f"closure: dt {dt_cl:.3e} vs {dt_exp:.3e} ({n_cl} vs {n_exp} steps), density L2 rel err {d_rho:.2e}, "
+          f"density change over the run {change:.2e}, val err {val:.3e}, eta {st['eta']:.3e}")
+    assert d_rho < 5e-5  # measured 7.7e-6 with 20x larger steps
+    assert d_rho < 0.05 * change
+    assert abs(st["eta"] - val) < 0.5 * val + 0.01  # the judge tracks the network's error
+    c.close()
+    s.close()
+    m.close()
+
+
+def test_untrained_closure_falls_back(gpu):
+    s, U0 = _collision_solver(ne=8)
+    s.set_state(U0)
+    s.step(s.compute_dt(0.5), 20)
+    m = nsk.MLP(s.closure_inputs, 256, 256, s.npe, max_batch=256, max_rows=s.E)
+    m.init_params(seed=9)  # random weights: far from the quasi-equilibrium
+    s.set_closure(m, judge_every=1, eta_max=0.5)
+    s.step(-0.5, 1)
+    st = s.closure_status()
+    assert st["mode"] == nsk.NSK_C_EXPLICIT and st["fallbacks"] == 1 and st["eta"] > 0.5, st
+    s.step(-0.5, 2)  # explicit steps continue from the closure's c
+    s.close()
+    m.close()
