@@ -238,6 +238,7 @@ def run_gpu(args, wl, rank, world):
     prof = s.get_profile(reset=True)
     s.set_profiling(False)
     clocks = clk.summary()
+    U_after = s.get_state() if (prec == nsk.NSK_FP64 and not args.no_variants and world == 1) else None
 
     # end to end through the C ABI: pinned host state in, step, state out, every step
     U_host = torch.from_numpy(s.get_state()).pin_memory()
@@ -290,6 +291,9 @@ def run_gpu(args, wl, rank, world):
     kernels = {k: {"avg_ms": v[0] / max(v[1], 1), "launches": v[1],
                    "share": v[0] / max(sum(x[0] for x in prof.values()), 1e-30)} for k, v in prof.items()}
     s.close()
+    variants = {}
+    if U_after is not None:
+        variants["fp32_mixed"] = measure_fp32_variant(args, wl, stream, U0, U_after, dt, peaks)
 
     if rank != 0:
         return 0
@@ -313,6 +317,7 @@ def run_gpu(args, wl, rank, world):
         "kernels": kernels,
         "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"], "reasons": clocks["reasons"]},
         "cpu_baseline": cpu,
+        "variants": variants,
     }
     print(json.dumps(line))
     return 0
@@ -425,6 +430,177 @@ def batch_vs_sequential_small(nsk, prec, n=64, steps=20):
             "step_latency_ms_p50": sm[len(sm) // 2], "step_latency_ms_p99": sm[-1]}
 
 
+def measure_fp32_variant(args, wl, stream, U0, U64_after, dt, peaks):
+    """The FP32 operator (FP64 EoS in the spinodal interval, FP64 dt and sums) on the same workload:
+    throughput, HBM roofline of its dominant kernel, and its density L2 error against the FP64 run
+    after the same steps from the same initial state."""
+    import torch
+
+    from paper_1912_12059_gb300 import nsk
+
+    s = nsk.Solver(wl.dim, wl.nelem, wl.N, list(wl.lo[:wl.dim]), list(wl.hi[:wl.dim]), wl.node_type,
+                   nsk.NSK_FP32_MIXED, stream=stream.cuda_stream)
+    s.set_params(T=wl.T, kappa=wl.kappa, alpha=wl.alpha, beta=wl.beta, mu=wl.mu)
+    s.set_state(U0)
+    tpb, fused, _ = s.autotune()
+    s.step(dt, args.warmup)
+    s.set_profiling(True)
+    s.get_profile(reset=True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    s.step(dt, args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    prof = s.get_profile(reset=True)
+    U32 = s.get_state()
+    s.close()
+    nodes = wl.dofs
+    err = float(np.sqrt(((U32[0] - U64_after[0]) ** 2).sum() / (U64_after[0] ** 2).sum()))
+    name, (kms, kcnt) = max(prof.items(), key=lambda kv: kv[1][0])
+    _, bytes_e = kernel_cost(name, wl.dim, wl.N + 1, 4)
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    achieved = bytes_e * wl.n_elem / (kms / max(kcnt, 1) / 1e3) / 1e9
+    return {"value": nodes * 5 * args.steps / (ms / 1e3), "unit": "DOF-updates/s", "ms_per_step": ms / args.steps,
+            "dtype": "f32", "density_l2_rel_err_vs_fp64": err, "steps_compared": args.warmup + args.steps,
+            "schedule": {"tpb": tpb, "fused_face": fused},
+            "roofline": {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"},
+            "kernels": {k: {"avg_ms": v[0] / max(v[1], 1), "launches": v[1]} for k, v in prof.items()}}
+
+
+def interface_metrics(U, x):
+    """Liquid fraction (nodes with rho above the mean saturation density 1.0634, Sec. 4.2) and the
+    distance between the liquid centroids left and right of x = 0.5 (droplet separation)."""
+    liquid = U[0] > 1.0634
+    left = liquid & (x[0] < 0.5)
+    right = liquid & (x[0] >= 0.5)
+    xl = float(x[0][left].mean()) if left.any() else float("nan")
+    xr = float(x[0][right].mean()) if right.any() else float("nan")
+    return {"liquid_fraction": float(liquid.mean()), "separation": xr - xl}
+
+
+def run_closure(args, rank, world):
+    """Learned c-closure, 3D collision at 96^3 elements, N=3 (56.6M nodes): network trained on
+    (rho, c) element snapshots of FP64 runs of the 64^3 collision at We 10, 40, 80; compared over
+    the same simulated time with the explicit FP64 method and the explicit FP32 operator."""
+    import torch
+
+    from paper_1912_12059_gb300 import closure, inputs, nsk
+    from paper_1912_12059_gb300.build import build_library
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    build_library()
+    if rank != 0:
+        return 0
+    ne_train = args.nelem_train
+    ne_eval = args.nelem or 96
+    # --- training data: snapshots of explicit FP64 runs ----------------------------------
+    t0 = time.perf_counter()
+    Xs, Ys = [], []
+    for i, we in enumerate((10.0, 40.0, 80.0)):
+        wl = inputs.head_on_collision_3d(we=we, nelem=ne_train)
+        s = nsk.Solver(3, wl.nelem, 3, [0, 0, 0], [1, 1, 1], 0, nsk.NSK_FP64)
+        s.set_params(T=wl.T, kappa=wl.kappa, alpha=wl.alpha, beta=wl.beta, mu=wl.mu)
+        s.set_state(wl.initial_state(s.node_coords()))
+        X, Y = closure.collect_snapshots(s, s.compute_dt(wl.cfl), first_step=20, every=10, count=8,
+                                         max_per_snapshot=args.samples // 24, rng=np.random.default_rng(i))
+        Xs.append(X)
+        Ys.append(Y)
+        s.close()
+    X, Y = torch.cat(Xs), torch.cat(Ys)
+    t_data = time.perf_counter() - t0
+    perm = torch.randperm(X.shape[0], device=X.device, generator=torch.Generator(device=X.device).manual_seed(0))
+    n_val = X.shape[0] // 10
+    Xv, Yv, Xt, Yt = X[perm[:n_val]], Y[perm[:n_val]], X[perm[n_val:]], Y[perm[n_val:]]
+    wl = inputs.head_on_collision_3d(we=40.0, nelem=ne_eval)
+    m = nsk.MLP(2 * (64 + 6), 256, 256, 64, max_batch=4096, max_rows=wl.n_elem)
+    m.init_params(seed=0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    closure.train(m, Xt, Yt, steps=args.train_steps, batch=4096, lr=3e-3, lr_min=3e-5)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    val_err = closure.validation_error(m, Xv, Yv)
+
+    # --- evaluation at the 96^3 size -----------------------------------------------------
+    def timed_run(solver, dt, n):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        solver.step(dt, n)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    s64 = nsk.Solver(3, wl.nelem, 3, [0, 0, 0], [1, 1, 1], 0, nsk.NSK_FP64)
+    s64.set_params(T=wl.T, kappa=wl.kappa, alpha=wl.alpha, beta=wl.beta, mu=wl.mu)
+    xnodes = s64.node_coords()
+    s64.set_state(wl.initial_state(xnodes))
+    dt_exp = s64.compute_dt(wl.cfl)
+    s64.step(dt_exp, 20)  # c reaches its quasi-equilibrium
+    U_start = s64.get_state()
+    n_exp = args.eval_steps
+    ms64 = timed_run(s64, dt_exp, n_exp)
+    U64 = s64.get_state()
+    # validation at the evaluation size: network against the explicit FP64 c
+    Xe = torch.empty((wl.n_elem, 144), dtype=torch.bfloat16, device="cuda")
+    Ye = torch.empty((wl.n_elem, 64), dtype=torch.float32, device="cuda")
+    s64.closure_features(Xe)
+    s64.closure_targets(Ye)
+    val_err_eval = closure.validation_error(m, Xe, Ye)
+    s64.close()
+    t_end = n_exp * dt_exp
+
+    s32 = nsk.Solver(3, wl.nelem, 3, [0, 0, 0], [1, 1, 1], 0, nsk.NSK_FP32_MIXED)
+    s32.set_params(T=wl.T, kappa=wl.kappa, alpha=wl.alpha, beta=wl.beta, mu=wl.mu)
+    s32.set_state(U_start)
+    s32.autotune()
+    s32.set_state(U_start)
+    ms32 = timed_run(s32, dt_exp, n_exp)
+    U32 = s32.get_state()
+    s32.set_state(U_start)
+    s32.set_closure(m, judge_every=10, eta_max=0.5)
+    dt_cl = s32.compute_dt(wl.cfl)
+    n_cl = int(math.ceil(t_end / dt_cl))
+    n0 = s32.launch_count + m.launch_count
+    mscl = timed_run(s32, t_end / n_cl, n_cl)
+    launches = s32.launch_count + m.launch_count - n0
+    st = s32.closure_status()
+    Ucl = s32.get_state()
+    s32.close()
+    m.close()
+
+    def l2(a):
+        return float(np.sqrt(((a[0] - U64[0]) ** 2).sum() / (U64[0] ** 2).sum()))
+
+    nodes = wl.dofs
+    line = {
+        "metric": "DOF-updates/s", "value": nodes * 5 * n_cl / (mscl / 1e3), "unit": "DOF-updates/s",
+        "n_gpus": 1, "steps": n_cl, "warmup": 20, "ms_per_step": mscl / n_cl, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16", "data": "synthetic",
+        "config": {"workload": f"learned_closure_3d_E{ne_eval}^3_N3_We40", "nodes": nodes,
+                   "train": {"samples": int(X.shape[0]), "source": f"FP64 {ne_train}^3 collision runs, We 10/40/80",
+                             "steps": args.train_steps, "batch": 4096, "seconds": t_train, "data_seconds": t_data,
+                             "samples_per_s": args.train_steps * 4096 / t_train,
+                             "val_rel_err": val_err, "val_rel_err_at_eval_size": val_err_eval},
+                   "simulated_time": t_end},
+        "closure": {"dt": dt_cl, "steps": n_cl, "wall_ms": mscl, "density_l2_rel_err_vs_fp64": l2(Ucl),
+                    "judge_eta": st["eta"], "fallbacks": st["fallbacks"], "interface": interface_metrics(Ucl, xnodes)},
+        "explicit_fp64": {"dt": dt_exp, "steps": n_exp, "wall_ms": ms64, "value": nodes * 5 * n_exp / (ms64 / 1e3),
+                          "interface": interface_metrics(U64, xnodes)},
+        "explicit_fp32": {"dt": dt_exp, "steps": n_exp, "wall_ms": ms32, "value": nodes * 5 * n_exp / (ms32 / 1e3),
+                          "density_l2_rel_err_vs_fp64": l2(U32), "interface": interface_metrics(U32, xnodes)},
+        "time_to_solution_speedup": {"closure_vs_fp64": ms64 / mscl, "closure_vs_fp32": ms32 / mscl,
+                                     "fp32_vs_fp64": ms64 / ms32},
+        "gpu_launches": launches,
+        "e2e": None, "roofline": None, "cpu_baseline": None,
+    }
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -432,7 +608,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="collision3d",
-                    choices=["collision3d", "coalescence2d", "interface1d", "batch"])
+                    choices=["collision3d", "coalescence2d", "interface1d", "batch", "closure"])
+    ap.add_argument("--no-variants", action="store_true", help="skip the FP32 variant of the default run")
+    ap.add_argument("--nelem-train", type=int, default=64, help="closure: training mesh (elements per direction)")
+    ap.add_argument("--samples", type=int, default=200000, help="closure: training samples")
+    ap.add_argument("--train-steps", type=int, default=4000, help="closure: Adam steps")
+    ap.add_argument("--eval-steps", type=int, default=100, help="closure: explicit steps of the comparison")
     ap.add_argument("--batch", type=int, default=32, help="instances of the batch workload")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -443,6 +624,8 @@ def main():
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
+    if args.workload == "closure":
+        return run_closure(args, rank, world)
     if args.workload == "batch":
         if args.precision == "fp64" and "--precision" not in sys.argv:
             args.precision = "fp32"

@@ -259,7 +259,7 @@ int export_nodal(nsk_ctx* c, const void* src, int ncomp, double* dst, int where)
 void free_ctx(nsk_ctx* c) {
   if (!c) return;
   void* ptrs[] = {c->b.U, c->b.K, c->b.Q, c->b.Utr, c->b.FVtr, c->b.Fstar, c->b.err, c->b.lam,
-                  c->b.dt, c->b.part, c->rbuf, c->stage64, c->cl_X, c->cl_Y, c->cl_red};
+                  c->b.dt, c->b.part, c->rbuf, c->stage64, c->cl_X, c->cl_Y, c->cl_red, c->cl_mean};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   for (cudaEvent_t ev : c->prof_pool) cudaEventDestroy(ev);
@@ -524,15 +524,17 @@ int nsk_step(nsk_ctx* c, double dt, int nsteps) {
       int r = launch_stage(c, l);
       if (r) return r;
     }
-    if (learned) {
-      int r = nsk_closure_apply_ctx(c);  // the stored state carries the closure's c
+    if (learned && c->judge_every > 0 && ++c->steps_since_judge >= c->judge_every) {
+      c->steps_since_judge = 0;
+      int r = nsk_closure_apply_ctx(c);  // judge the closure's c of the current state
       if (r) return r;
-      if (c->judge_every > 0 && ++c->steps_since_judge >= c->judge_every) {
-        c->steps_since_judge = 0;
-        r = nsk_closure_judge_ctx(c);
-        if (r) return r;
-      }
+      r = nsk_closure_judge_ctx(c);
+      if (r) return r;
     }
+  }
+  if (c->closure_mode == NSK_C_LEARNED) {  // the stored state carries the closure's c
+    const int r = nsk_closure_apply_ctx(c);
+    if (r) return r;
   }
   return sync_and_check(c);
 }

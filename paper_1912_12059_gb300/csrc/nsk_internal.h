@@ -144,6 +144,7 @@ struct nsk_ctx {
   void* cl_X;                  // BF16 features [E][n_in_pad]
   float* cl_Y;                 // network output [E][npe]
   double* cl_red;              // judge sums
+  float* cl_mean;              // element mean densities (features)
 };
 
 // host helpers shared by the translation units of the library

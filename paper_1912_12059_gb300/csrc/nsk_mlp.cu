@@ -420,26 +420,34 @@ constexpr float kFeatScale = 0.5f;  // feature scale: density deviations within 
 // lo = bf16(v - hi) (columns [0, nf) and [nf, 2 nf)), so the tensor cores see about 16
 // significant bits of the input. The quasi-equilibrium c - rho is invariant under adding a
 // constant to rho, so the element mean itself is not an input.
+// element means of rho (one warp per element)
+template <typename R>
+__global__ void k_elem_mean(const long long E, const int npe, const R* __restrict__ U, float* __restrict__ mean) {
+  const long long e = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (e >= E) return;
+  float acc = 0.f;
+  for (int n = lane; n < npe; n += 32) acc += (float)U[e * npe + n];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) mean[e] = acc / (float)npe;
+}
+
 template <typename R>
 __global__ void k_closure_features(const NskParams p, const int npe, const int dim, const R* __restrict__ U,
-                                   __nv_bfloat16* __restrict__ X, const int nin_pad) {
+                                   const float* __restrict__ mean_e, __nv_bfloat16* __restrict__ X,
+                                   const int nin_pad) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const int nf = npe + 2 * dim;
   if (i >= p.E * nf) return;
   const long long e = i / nf;
   const int f = (int)(i % nf);
-  float mean = 0.f;
-  for (int n = 0; n < npe; ++n) mean += (float)U[e * npe + n];
-  mean /= (float)npe;
+  const float mean = mean_e[e];
   float v;
   if (f < npe) {
     v = (float)U[e * npe + f] - mean;
   } else {
     const int j = f - npe;
-    const long long en = nsk::nbr_elem(p, e, j >> 1, (j & 1) ? 1 : -1);
-    float acc = 0.f;
-    for (int n = 0; n < npe; ++n) acc += (float)U[en * npe + n];
-    v = acc / (float)npe - mean;
+    v = mean_e[nsk::nbr_elem(p, e, j >> 1, (j & 1) ? 1 : -1)] - mean;
   }
   v /= kFeatScale;
   const __nv_bfloat16 hi = __float2bfloat16_rn(v);
@@ -490,13 +498,21 @@ double closure_scale(const nsk_ctx* c) { return c->p.kappa / c->p.alpha * c->p.r
 int closure_features(nsk_ctx* c, void* X) {
   const int nin_pad = round16(2 * (c->npe + 2 * c->dim));
   const long long n = c->E * (c->npe + 2 * c->dim);
-  if (c->precision == NSK_FP32_MIXED)
-    k_closure_features<float><<<nb(n), 256, 0, c->stream>>>(c->p, c->npe, c->dim, (const float*)c->b.U,
+  if (!c->cl_mean && cudaMalloc((void**)&c->cl_mean, sizeof(float) * c->E) != cudaSuccess) {
+    cudaGetLastError();
+    return NSK_ERR_NOMEM;
+  }
+  float* mean = c->cl_mean;
+  if (c->precision == NSK_FP32_MIXED) {
+    k_elem_mean<float><<<nb(c->E * 32), 256, 0, c->stream>>>(c->E, c->npe, (const float*)c->b.U, mean);
+    k_closure_features<float><<<nb(n), 256, 0, c->stream>>>(c->p, c->npe, c->dim, (const float*)c->b.U, mean,
                                                             (__nv_bfloat16*)X, nin_pad);
-  else
-    k_closure_features<double><<<nb(n), 256, 0, c->stream>>>(c->p, c->npe, c->dim, (const double*)c->b.U,
+  } else {
+    k_elem_mean<double><<<nb(c->E * 32), 256, 0, c->stream>>>(c->E, c->npe, (const double*)c->b.U, mean);
+    k_closure_features<double><<<nb(n), 256, 0, c->stream>>>(c->p, c->npe, c->dim, (const double*)c->b.U, mean,
                                                              (__nv_bfloat16*)X, nin_pad);
-  c->launches += 1;
+  }
+  c->launches += 2;
   return cudaGetLastError() == cudaSuccess ? NSK_OK : NSK_ERR_CUDA;
 }
 

@@ -117,6 +117,61 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase, int* err
   }
 }
 
+// epilogue of 32 accumulator columns [c0, c0 + 32) of row m (valid if rv) held in v
+__device__ __forceinline__ void epilogue_chunk(const GemmArgs& a, const int m, const bool rv, const int c0,
+                                               const uint32_t* v, const int lane) {
+  const int ncol = min(32, a.N - c0);
+  float colsum[32];
+#pragma unroll
+  for (int j = 0; j < 32; ++j) {
+    colsum[j] = 0.f;
+    if (j >= ncol) continue;
+    const int n = c0 + j;
+    float x = __uint_as_float(v[j]);
+    if (a.epi == EPI_STORE) {
+      if (rv) a.out[(size_t)m * a.ldo + n] = x + (a.bias ? a.bias[n] : 0.f);
+    } else if (a.epi == EPI_ATOMIC) {
+      if (rv) atomicAdd(&a.out[(size_t)m * a.ldo + n], x);
+    } else if (a.epi == EPI_GELU) {
+      const float z = x + (a.bias ? a.bias[n] : 0.f);
+      if (rv) {
+        if (a.out) a.out[(size_t)m * a.ldo + n] = z;
+        const __nv_bfloat16 h = __float2bfloat16_rn(gelu(z));
+        a.hout[(size_t)m * a.ldh + n] = h;
+        if (a.hout_t) a.hout_t[(size_t)n * a.ldt + m] = h;
+      }
+    } else {  // EPI_DGELU
+      const float dz = rv ? x * gelu_grad(a.zin[(size_t)m * a.ldz + n]) : 0.f;
+      if (rv) {
+        const __nv_bfloat16 h = __float2bfloat16_rn(dz);
+        a.hout[(size_t)m * a.ldh + n] = h;
+        if (a.hout_t) a.hout_t[(size_t)n * a.ldt + m] = h;
+      }
+      colsum[j] = dz;
+    }
+  }
+  if (a.epi == EPI_DGELU && a.bias_grad) {
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      float s = colsum[j];
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0 && j < ncol) atomicAdd(&a.bias_grad[c0 + j], s);
+    }
+  }
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* v) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+      "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+        "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+        "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
 __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const GemmArgs a) {
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char* sA = smem;                         // kBM x kKC BF16 = 16 KB
@@ -193,44 +248,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const GemmArgs a) {
             "=r"(v[30]), "=r"(v[31])
           : "r"(taddr));
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      const int ncol = min(32, a.N - c0);
-      float colsum[32];
-#pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        colsum[j] = 0.f;
-        if (j >= ncol) continue;
-        const int n = c0 + j;
-        float x = __uint_as_float(v[j]);
-        if (a.epi == EPI_STORE) {
-          if (rv) a.out[(size_t)m * a.ldo + n] = x + (a.bias ? a.bias[n] : 0.f);
-        } else if (a.epi == EPI_ATOMIC) {
-          if (rv) atomicAdd(&a.out[(size_t)m * a.ldo + n], x);
-        } else if (a.epi == EPI_GELU) {
-          const float z = x + (a.bias ? a.bias[n] : 0.f);
-          if (rv) {
-            if (a.out) a.out[(size_t)m * a.ldo + n] = z;
-            const __nv_bfloat16 h = __float2bfloat16_rn(gelu(z));
-            a.hout[(size_t)m * a.ldh + n] = h;
-            if (a.hout_t) a.hout_t[(size_t)n * a.ldt + m] = h;
-          }
-        } else {  // EPI_DGELU
-          const float dz = rv ? x * gelu_grad(a.zin[(size_t)m * a.ldz + n]) : 0.f;
-          if (rv) {
-            const __nv_bfloat16 h = __float2bfloat16_rn(dz);
-            a.hout[(size_t)m * a.ldh + n] = h;
-            if (a.hout_t) a.hout_t[(size_t)n * a.ldt + m] = h;
-          }
-          colsum[j] = dz;
-        }
-      }
-      if (a.epi == EPI_DGELU && a.bias_grad) {
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          float s = colsum[j];
-          for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-          if (lane == 0 && j < ncol) atomicAdd(&a.bias_grad[c0 + j], s);
-        }
-      }
+      epilogue_chunk(a, m, rv, c0, v, lane);
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -242,19 +260,243 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const GemmArgs a) {
 // and their two 256-column TMEM allocations never contend (512 columns per SM)
 constexpr int kSmemBytes = 80 * 1024;
 
+// ---------------------------------------------------------------------------
+// Persistent variant for a weight matrix B that fits in shared memory (K <= 256,
+// N % 64 == 0): B is staged once per CTA and stays resident; the CTA walks over
+// 128-row tiles of A with two TMEM accumulators (all 512 columns) so that the
+// epilogue of tile i-1 (8 warps: warp w reads lanes 32 (w % 4).. and the column
+// half w / 4) runs while the tensor cores compute tile i. Operands are staged
+// with cp.async (16-byte copies straight into the core-matrix layout).
+// ---------------------------------------------------------------------------
+constexpr int kRbThreads = 256;
+constexpr int kRbSmemMin = 116 * 1024;  // forces one CTA per SM: it owns all 512 TMEM columns
+constexpr int kRbStageBytes = 8 * 32 * 33 * 4;  // eight warps' epilogue staging blocks
+constexpr int kRbSmemMax = 256 * 256 * 2 + 128 * 256 * 2 + kRbStageBytes;  // B, A tiles at K = N = 256, staging
+
+__device__ __forceinline__ uint32_t core_off_k(int r, int k, int K) {
+  return (uint32_t)((((r >> 3) * (K >> 3) + (k >> 3)) << 7) + ((r & 7) << 4) + ((k & 7) << 1));
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t saddr, const void* g, int src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(saddr), "l"(g), "r"(src_bytes) : "memory");
+}
+
+__host__ __device__ constexpr int rb_b_bytes(int N, int K) { return ((N * K * 2) + 1023) & ~1023; }
+
+constexpr int kStage = 32 * 33;  // floats of one warp's 32 x 32 staging block (padded rows)
+
+// write the 32 x 32 block held transposed in `st` (st[r * 33 + c], row r = lane of the producer)
+// to rows row0.. of a row-major matrix with 16-byte vector stores (rows beyond rows_valid skipped)
+__device__ __forceinline__ void store_block_f32(const float* st, float* out, size_t ld, int row0, int col0,
+                                                int rows_valid, int lane) {
+#pragma unroll
+  for (int it = 0; it < 8; ++it) {
+    const int r = it * 4 + (lane >> 3), c = (lane & 7) * 4;
+    if (r < rows_valid) {
+      const float4 v = make_float4(st[r * 33 + c], st[r * 33 + c + 1], st[r * 33 + c + 2], st[r * 33 + c + 3]);
+      *reinterpret_cast<float4*>(out + (size_t)(row0 + r) * ld + col0 + c) = v;
+    }
+  }
+}
+__device__ __forceinline__ void store_block_bf16(const float* st, __nv_bfloat16* out, size_t ld, int row0, int col0,
+                                                 int rows_valid, int lane) {
+#pragma unroll
+  for (int it = 0; it < 4; ++it) {
+    const int r = it * 8 + (lane >> 2), c = (lane & 3) * 8;
+    if (r < rows_valid) {
+      __align__(16) __nv_bfloat16 h[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) h[j] = __float2bfloat16_rn(st[r * 33 + c + j]);
+      *reinterpret_cast<uint4*>(out + (size_t)(row0 + r) * ld + col0 + c) = *reinterpret_cast<const uint4*>(h);
+    }
+  }
+}
+
+// epilogue of the resident-B kernel for 32 columns [c0, c0 + 32) of the warp's 32 rows
+// (row0 = first row, lane = row offset); outputs go through the warp's staging block
+__device__ __forceinline__ void epilogue_chunk_rb(const GemmArgs& a, const int row0, const int lane, const int c0,
+                                                  const uint32_t* v, float* st) {
+  const int m = row0 + lane;
+  const int rows_valid = a.M - row0;
+  const bool rv = lane < rows_valid;
+  float x[32];
+#pragma unroll
+  for (int j = 0; j < 32; ++j) x[j] = __uint_as_float(v[j]) + ((a.epi != EPI_DGELU && a.bias) ? a.bias[c0 + j] : 0.f);
+  if (a.epi == EPI_STORE || (a.epi == EPI_GELU && a.out)) {
+#pragma unroll
+    for (int j = 0; j < 32; ++j) st[lane * 33 + j] = x[j];
+    __syncwarp();
+    store_block_f32(st, a.out, a.ldo, row0, c0, rows_valid, lane);
+    __syncwarp();
+    if (a.epi == EPI_STORE) return;
+  }
+  if (a.epi == EPI_DGELU) {  // stage the pre-activations of the block (coalesced loads)
+#pragma unroll
+    for (int it = 0; it < 8; ++it) {
+      const int r = it * 4 + (lane >> 3), c = (lane & 7) * 4;
+      if (r < rows_valid) {
+        const float4 z = *reinterpret_cast<const float4*>(a.zin + (size_t)(row0 + r) * a.ldz + c0 + c);
+        st[r * 33 + c] = z.x;
+        st[r * 33 + c + 1] = z.y;
+        st[r * 33 + c + 2] = z.z;
+        st[r * 33 + c + 3] = z.w;
+      }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < 32; ++j) x[j] = rv ? x[j] * gelu_grad(st[lane * 33 + j]) : 0.f;
+    __syncwarp();
+  } else {
+#pragma unroll
+    for (int j = 0; j < 32; ++j) x[j] = gelu(x[j]);
+  }
+  if (a.epi == EPI_DGELU && a.bias_grad) {  // column sums of the FP32 values
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      float sum = x[j];
+      for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+      if (lane == 0) atomicAdd(&a.bias_grad[c0 + j], sum);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 32; ++j) st[lane * 33 + j] = x[j];
+  __syncwarp();
+  store_block_bf16(st, a.hout, a.ldh, row0, c0, rows_valid, lane);
+  __syncwarp();
+  if (a.hout_t && rv) {
+#pragma unroll
+    for (int j = 0; j < 32; ++j) a.hout_t[(size_t)(c0 + j) * a.ldt + m] = __float2bfloat16_rn(x[j]);
+  }
+}
+
+__global__ void __launch_bounds__(kRbThreads, 1) k_gemm_tc_rb(const GemmArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const int K = a.K, N = a.N;
+  unsigned char* sB = smem;
+  unsigned char* sA = smem + rb_b_bytes(N, K);
+  float* stage = reinterpret_cast<float*>(sA + kBM * K * 2) + (threadIdx.x >> 5) * kStage;
+  __shared__ __align__(8) unsigned long long mbar[2];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int aborted;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int q = warp & 3, half = warp >> 2;
+  const int ntiles = (a.M + kBM - 1) / kBM;
+  const int kc = K >> 3;  // 16-byte chunks per row
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (threadIdx.x == 0) {
+    aborted = 0;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[0])), "r"(1));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[1])), "r"(1));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  // resident B
+  const uint32_t sBa = smem_u32(sB), sAa = smem_u32(sA);
+  for (int idx = threadIdx.x; idx < N * kc; idx += kRbThreads) {
+    const int r = idx / kc, j = idx % kc;
+    cp_async16(sBa + core_off_k(r, j * 8, K), a.B + (size_t)r * a.ldb + j * 8, 16);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_slot;
+  const uint32_t idesc = idesc_bf16(kBM, N);
+  uint32_t ph[2] = {0u, 0u};
+  int prev_tile = -1;
+
+  for (int t = blockIdx.x, i = 0;; t += gridDim.x, ++i) {
+    const bool have = t < ntiles;
+    if (i > 0) {  // the MMAs of tile i-1 must be done before its A buffer is refilled
+      const int b = (i - 1) & 1;
+      const bool ok = mbar_wait(smem_u32(&mbar[b]), ph[b], a.err);
+      ph[b] ^= 1u;
+      if (!ok) aborted = 1;
+      asm volatile("tcgen05.fence::after_thread_sync;");
+    }
+    if (have) {
+      const int m0 = t * kBM;
+      for (int idx = threadIdx.x; idx < kBM * kc; idx += kRbThreads) {
+        const int r = idx / kc, j = idx % kc;
+        const bool v = m0 + r < a.M;
+        cp_async16(sAa + core_off_k(r, j * 8, K), v ? (const void*)(a.A + (size_t)(m0 + r) * a.lda + j * 8)
+                                                    : (const void*)a.A, v ? 16 : 0);
+      }
+      asm volatile("cp.async.wait_all;" ::: "memory");
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    if (aborted) break;
+    if (have && threadIdx.x == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const uint32_t d = tmem + (uint32_t)((i & 1) * 256);
+      for (int st = 0; st < K / 16; ++st) {
+        const uint64_t ad = sdesc(sAa + st * 256, 128, kc * 128);
+        const uint64_t bd = sdesc(sBa + st * 256, 128, kc * 128);
+        const uint32_t acc = st > 0 ? 1u : 0u;
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+            "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(&mbar[i & 1])));
+    }
+    if (prev_tile >= 0) {  // epilogue of the previous tile overlaps the MMAs just issued
+      const int row0 = prev_tile * kBM + q * 32;
+      const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(((i - 1) & 1) * 256);
+      for (int c0 = half * (N / 2); c0 < (half + 1) * (N / 2); c0 += 32) {
+        uint32_t v[32];
+        tmem_ld32(base + (uint32_t)c0, v);
+        epilogue_chunk_rb(a, row0, lane, c0, v, stage);
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;");
+    }
+    if (!have) break;
+    prev_tile = t;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+}
+
 // host launcher (grid: ceil(M/128) x ceil(K/k_split))
 inline int launch_gemm(const GemmArgs& a, cudaStream_t s) {
   if (a.M < 1 || a.N < 16 || a.N > kMaxN || (a.N % 16) || a.K < 16 || (a.K % 16) || (a.lda % 8) || (a.ldb % 8) ||
       a.lda < a.K || a.ldb < a.K || a.k_split < 16 || (a.k_split % kKC && a.k_split < a.K))
     return NSK_ERR_ARG;
   static bool attr_done = false;
+  static int sms = 0;
   if (!attr_done) {
-    if (cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes) != cudaSuccess)
+    int dev = 0;
+    if (cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes) != cudaSuccess ||
+        cudaFuncSetAttribute(k_gemm_tc_rb, cudaFuncAttributeMaxDynamicSharedMemorySize, kRbSmemMax) != cudaSuccess ||
+        cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+      cudaGetLastError();
       return NSK_ERR_CUDA;
+    }
     attr_done = true;
   }
-  dim3 grid((unsigned)((a.M + kBM - 1) / kBM), (unsigned)((a.K + a.k_split - 1) / a.k_split));
-  k_gemm_tc<<<grid, kThreads, kSmemBytes, s>>>(a);
+  // resident-B kernel: 16-byte aligned rows of every output it writes with vector stores
+  auto a16 = [](const void* p) { return ((uintptr_t)p & 15u) == 0; };
+  const bool aligned = (a.epi == EPI_STORE ? (a.ldo % 4) == 0 && a16(a.out) : (a.ldh % 8) == 0 && a16(a.hout)) &&
+                       (!(a.epi == EPI_GELU && a.out) || ((a.ldo % 4) == 0 && a16(a.out))) &&
+                       (a.epi != EPI_DGELU || ((a.ldz % 4) == 0 && a16(a.zin)));
+  const bool resident = a.epi != EPI_ATOMIC && a.k_split >= a.K && a.K <= 256 && (a.N % 64) == 0 && aligned;
+  if (resident) {
+    int smem = rb_b_bytes(a.N, a.K) + kBM * a.K * 2 + kRbStageBytes;
+    smem = smem < kRbSmemMin ? kRbSmemMin : smem;
+    const int ntiles = (a.M + kBM - 1) / kBM;
+    if (smem > kRbSmemMax) return NSK_ERR_ARG;
+    k_gemm_tc_rb<<<(unsigned)(ntiles < sms ? ntiles : sms), kRbThreads, smem, s>>>(a);
+  } else {
+    dim3 grid((unsigned)((a.M + kBM - 1) / kBM), (unsigned)((a.K + a.k_split - 1) / a.k_split));
+    k_gemm_tc<<<grid, kThreads, kSmemBytes, s>>>(a);
+  }
   return cudaGetLastError() == cudaSuccess ? NSK_OK : NSK_ERR_CUDA;
 }
 
