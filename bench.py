@@ -601,6 +601,58 @@ def run_closure(args, rank, world):
     return 0
 
 
+def run_gemm(args, rank, world):
+    """Tensor-core GEMMs of the closure network's forward pass (BF16 in, FP32 accumulation):
+    rows = elements of the evaluation mesh, shapes [rows x 144] . [256 x 144]^T (GELU),
+    [rows x 256] . [256 x 256]^T (GELU), [rows x 256] . [64 x 256]^T (store)."""
+    import torch
+
+    from paper_1912_12059_gb300 import nsk
+    from paper_1912_12059_gb300.build import build_library
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    build_library()
+    rows = args.rows
+    g = torch.Generator(device="cuda").manual_seed(0)
+    X = torch.randn((rows, 144), device="cuda", generator=g).to(torch.bfloat16)
+    W1 = torch.randn((256, 144), device="cuda", generator=g).to(torch.bfloat16)
+    W2 = torch.randn((256, 256), device="cuda", generator=g).to(torch.bfloat16)
+    W3 = torch.randn((64, 256), device="cuda", generator=g).to(torch.bfloat16)
+    H1 = torch.empty((rows, 256), dtype=torch.bfloat16, device="cuda")
+    H2 = torch.empty((rows, 256), dtype=torch.bfloat16, device="cuda")
+    Y = torch.empty((rows, 64), dtype=torch.float32, device="cuda")
+    calls = [("layer1_gelu", lambda: nsk.gemm_bf16(X, W1, epilogue=2, hout=H1), 2 * rows * 144 * 256,
+              rows * 144 * 2 + rows * 256 * 2),
+             ("layer2_gelu", lambda: nsk.gemm_bf16(H1, W2, epilogue=2, hout=H2), 2 * rows * 256 * 256,
+              rows * 256 * 2 * 2),
+             ("layer3_store", lambda: nsk.gemm_bf16(H2, W3, epilogue=0, out=Y), 2 * rows * 256 * 64,
+              rows * 256 * 2 + rows * 64 * 4)]
+    out = {}
+    peaks = json.loads(MEASURED_PEAKS.read_text()) if MEASURED_PEAKS.exists() else {}
+    tc_peak = float(peaks.get("bf16_tflops", 1900.0))
+    for name, f, flops, nbytes in calls:
+        for _ in range(args.warmup):
+            assert f() == 0
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(args.steps):
+            f()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        out[name] = {"ms": ms, "tflops": flops / ms / 1e9, "frac_of_bf16_peak": flops / ms / 1e9 / tc_peak,
+                     "gbs": nbytes / ms / 1e6}
+    if rank == 0:
+        total_ms = sum(v["ms"] for v in out.values())
+        print(json.dumps({"metric": "closure MLP forward rows/s", "value": rows / (total_ms / 1e3), "unit": "rows/s",
+                          "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms,
+                          "higher_is_better": True, "dtype": "bf16", "data": "synthetic",
+                          "config": {"workload": f"closure_mlp_forward_rows{rows}", "layers": out,
+                                     "bf16_peak_tflops": tc_peak}}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -608,7 +660,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="collision3d",
-                    choices=["collision3d", "coalescence2d", "interface1d", "batch", "closure"])
+                    choices=["collision3d", "coalescence2d", "interface1d", "batch", "closure", "gemm"])
+    ap.add_argument("--rows", type=int, default=884736, help="gemm: rows (elements)")
     ap.add_argument("--no-variants", action="store_true", help="skip the FP32 variant of the default run")
     ap.add_argument("--nelem-train", type=int, default=64, help="closure: training mesh (elements per direction)")
     ap.add_argument("--samples", type=int, default=200000, help="closure: training samples")
@@ -626,6 +679,8 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     if args.workload == "closure":
         return run_closure(args, rank, world)
+    if args.workload == "gemm":
+        return run_gemm(args, rank, world)
     if args.workload == "batch":
         if args.precision == "fp64" and "--precision" not in sys.argv:
             args.precision = "fp32"
