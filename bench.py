@@ -53,9 +53,11 @@ def workload_by_name(name):
 
 
 # ---------------------------------------------------------------- algorithmic cost model
-def kernel_cost(kernel, d, n, fp_bytes):
+def kernel_cost(kernel, d, n, fp_bytes, traces=0.0):
     """Algorithmic (flops, bytes) per element of one stage kernel, counted from the kernel
-    source: FMA = 2 flops, add/mul/div/sqrt = 1; bytes = compulsory loads + stores."""
+    source: FMA = 2 flops, add/mul/div/sqrt = 1; bytes = compulsory loads + stores.
+    `traces`: fraction of the k_volume launches that also wrote the face traces of their
+    output state (the next stage's prolongation: its flops and trace stores)."""
     npe, nfn, nv, nw, nf = n**d, n ** (d - 1), d + 2, d + 1, 2 * d
     if kernel == "k_prolong":
         return nf * nfn * nv * 2 * n, fp_bytes * (nv * npe + nf * nfn * nv)
@@ -69,8 +71,15 @@ def kernel_cost(kernel, d, n, fp_bytes):
     if kernel == "k_volume":
         per_node = 1 + 10 + (d - 1) + d * (5 * d + 5) + nv * d * (2 * n + 6) + 3 * d + 3 + 5 * nv
         by = fp_bytes * (nv * npe + d * nw * npe + 2 * d * nfn * nv + 2 * nv * npe + nv * npe)
-        return npe * per_node, by
+        return npe * per_node + traces * nf * nfn * nv * 2 * n, by + traces * fp_bytes * nf * nfn * nv
     raise KeyError(kernel)
+
+
+def trace_fraction(prof):
+    """Share of the k_volume launches that wrote the next stage's traces: every nsk_step call
+    prolongs once at its start and skips the trace store in its last stage."""
+    nv = prof.get("k_volume", (0.0, 0))[1]
+    return (nv - prof.get("k_prolong", (0.0, 0))[1]) / nv if nv else 0.0
 
 
 # ---------------------------------------------------------------- clocks
@@ -273,7 +282,7 @@ def run_gpu(args, wl, rank, world):
     fp_bytes = 8 if prec == nsk.NSK_FP64 else 4
     name, (kms, kcnt) = max(prof.items(), key=lambda kv: kv[1][0])
     avg_ms = kms / max(kcnt, 1)
-    flops_e, bytes_e = kernel_cost(name, wl.dim, wl.N + 1, fp_bytes)
+    flops_e, bytes_e = kernel_cost(name, wl.dim, wl.N + 1, fp_bytes, traces=trace_fraction(prof))
     peaks = json.loads(MEASURED_PEAKS.read_text()) if MEASURED_PEAKS.exists() else {}
     if prec == nsk.NSK_FP64:
         achieved = flops_e * s.E / (avg_ms / 1e3) / 1e12
@@ -459,7 +468,7 @@ def measure_fp32_variant(args, wl, stream, U0, U64_after, dt, peaks):
     nodes = wl.dofs
     err = float(np.sqrt(((U32[0] - U64_after[0]) ** 2).sum() / (U64_after[0] ** 2).sum()))
     name, (kms, kcnt) = max(prof.items(), key=lambda kv: kv[1][0])
-    _, bytes_e = kernel_cost(name, wl.dim, wl.N + 1, 4)
+    _, bytes_e = kernel_cost(name, wl.dim, wl.N + 1, 4, traces=trace_fraction(prof))
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     achieved = bytes_e * wl.n_elem / (kms / max(kcnt, 1) / 1e3) / 1e9
     return {"value": nodes * 5 * args.steps / (ms / 1e3), "unit": "DOF-updates/s", "ms_per_step": ms / args.steps,

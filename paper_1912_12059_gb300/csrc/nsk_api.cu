@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <new>
+#include <utility>
 #include <vector>
 
 #include "nsk_internal.h"
@@ -178,7 +179,7 @@ const double kB[5] = {1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612
 namespace {
 
 // events for the next profiled stage (NULL when profiling is off)
-cudaEvent_t* prof_group(nsk_ctx* c, int nkern) {
+cudaEvent_t* prof_group(nsk_ctx* c, int mask) {
   if (!c->prof_on) return nullptr;
   const size_t g = c->prof_used;
   if ((g + 1) * (NSK_NKERN + 1) > c->prof_pool.size()) {
@@ -189,7 +190,7 @@ cudaEvent_t* prof_group(nsk_ctx* c, int nkern) {
     }
   }
   if (c->prof_nk.size() <= g) c->prof_nk.resize(g + 1);
-  c->prof_nk[g] = nkern;
+  c->prof_nk[g] = mask;
   c->prof_used = g + 1;
   return &c->prof_pool[g * (NSK_NKERN + 1)];
 }
@@ -198,7 +199,8 @@ cudaEvent_t* prof_group(nsk_ctx* c, int nkern) {
 void prof_collect(nsk_ctx* c) {
   for (size_t g = 0; g < c->prof_used; ++g) {
     cudaEvent_t* ev = &c->prof_pool[g * (NSK_NKERN + 1)];
-    for (int k = 0; k < c->prof_nk[g]; ++k) {
+    for (int k = 0; k < NSK_NKERN; ++k) {
+      if (!((c->prof_nk[g] >> k) & 1)) continue;
       float ms = 0.f;
       if (cudaEventElapsedTime(&ms, ev[k], ev[k + 1]) == cudaSuccess) {
         c->prof_ms[k] += ms;
@@ -224,7 +226,10 @@ int sync_and_check(nsk_ctx* c) {
 }
 
 int launch_stage(nsk_ctx* c, NskLaunch l) {
-  l.ev = prof_group(c, l.mode == NSK_MODE_LIFT ? 2 : NSK_NKERN);
+  // kernels 0..3 = prolong, lift, face, volume
+  const int mask = (l.traces_ready ? 0 : 1) | 2 |
+                   (l.mode == NSK_MODE_LIFT ? 0 : ((l.fused_face ? 0 : 4) | 8));
+  l.ev = prof_group(c, mask);
   int r;
   const bool f32 = c->precision == NSK_FP32_MIXED;
   switch (c->dim) {
@@ -258,7 +263,7 @@ int export_nodal(nsk_ctx* c, const void* src, int ncomp, double* dst, int where)
 
 void free_ctx(nsk_ctx* c) {
   if (!c) return;
-  void* ptrs[] = {c->b.U, c->b.K, c->b.Q, c->b.Utr, c->b.FVtr, c->b.Fstar, c->b.err, c->b.lam,
+  void* ptrs[] = {c->b.U, c->b.K, c->b.Q, c->b.Utr, c->utr_alt, c->b.FVtr, c->b.Fstar, c->b.err, c->b.lam,
                   c->b.dt, c->b.part, c->rbuf, c->stage64, c->cl_X, c->cl_Y, c->cl_red, c->cl_mean};
   for (void* q : ptrs)
     if (q) cudaFree(q);
@@ -365,6 +370,7 @@ int nsk_init_mesh(nsk_ctx** out, int dim, const int nelem[3], const double lo[3]
       {&c->b.K, rs * c->nvar * nn},
       {&c->b.Q, rs * c->nq * nn},
       {&c->b.Utr, rs * (c->nvar + (precision == NSK_FP64 ? TraceComps<double>::extra : 0)) * faces},
+      {&c->utr_alt, rs * (c->nvar + (precision == NSK_FP64 ? TraceComps<double>::extra : 0)) * faces},
       {&c->b.FVtr, rs * (dim + 1) * faces},
       {&c->b.Fstar, rs * c->nvar * c->E * dim * c->nfn},
       {(void**)&c->b.err, sizeof(int)},
@@ -508,6 +514,7 @@ int nsk_step(nsk_ctx* c, double dt, int nsteps) {
   if (!c || nsteps < 0 || !isfinite(dt) || dt == 0.0) return NSK_ERR_ARG;
   if (!c->state_set) return NSK_ERR_STATE;
   const bool adaptive = dt < 0.0;
+  bool ready = false;  // b.Utr holds the traces of U
   for (int s = 0; s < nsteps; ++s) {
     if (adaptive) {
       int r = nsk_launch_dt(c->p, c->dim, c->np, c->precision == NSK_FP32_MIXED, c->b, -dt, c->stream);
@@ -516,13 +523,20 @@ int nsk_step(nsk_ctx* c, double dt, int nsteps) {
     }
     const bool learned = c->closure_mode == NSK_C_LEARNED;
     for (int st = 0; st < 5; ++st) {
-      if (learned) {
+      if (learned) {  // the closure rewrites c before every stage: its traces are prolonged anew
         const int r = nsk_closure_apply_ctx(c);
         if (r) return r;
+        ready = false;
       }
       NskLaunch l = {NSK_MODE_LSRK, nullptr, kA[st], kB[st], adaptive ? c->b.dt : nullptr, dt, nullptr, c->tpb, c->fused_face};
+      // the volume kernel writes the traces of the updated state for the next stage of this call
+      const bool write = !learned && !(s == nsteps - 1 && st == 4);
+      l.traces_ready = ready;
+      l.utr_next = write ? (c->fused_face ? c->utr_alt : c->b.Utr) : nullptr;
       int r = launch_stage(c, l);
       if (r) return r;
+      if (write && c->fused_face) std::swap(c->b.Utr, c->utr_alt);
+      ready = write;
     }
     if (learned && c->judge_every > 0 && ++c->steps_since_judge >= c->judge_every) {
       c->steps_since_judge = 0;
@@ -598,8 +612,12 @@ int nsk_autotune(nsk_ctx* c, int* tpb_out, int* fused_out, double* ms_out) {
       c->tpb = tpbs[it];
       c->fused_face = f;
       NskLaunch l = {NSK_MODE_RHS, c->rbuf, 0.0, 0.0, nullptr, 0.0, nullptr, c->tpb, c->fused_face};
-      st = launch_stage(c, l);  // warm-up
+      st = launch_stage(c, l);  // warm-up; leaves b.Utr holding the traces of U
       if (st) break;
+      // time what a stage inside nsk_step runs: no prolongation pass, traces written by the
+      // volume kernel (to the spare buffer: U does not change in RHS mode)
+      l.traces_ready = 1;
+      l.utr_next = c->utr_alt;
       cudaEventRecord(e0, c->stream);
       for (int r = 0; r < 3 && st == NSK_OK; ++r) st = launch_stage(c, l);
       cudaEventRecord(e1, c->stream);

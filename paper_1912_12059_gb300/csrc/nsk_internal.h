@@ -92,6 +92,8 @@ struct NskLaunch {
   cudaEvent_t* ev;         // NULL, or NSK_NKERN + 1 events bracketing the kernels
   int tpb;                 // block-size schedule: 128 or 256 threads (elements per block follow)
   int fused_face;          // 1: face fluxes evaluated inside the volume kernel
+  int traces_ready;        // 1: Utr already holds the traces of U (no prolongation pass)
+  void* utr_next;          // non-NULL: the volume kernel writes the traces of its output state here
 };
 
 #define NSK_NKERN 4  // prolong, lift, face, volume
@@ -123,6 +125,8 @@ struct nsk_ctx {
   NskParams p;
   NskBuffers b;
   void* rbuf;        // residual scratch, context precision, nvar*nn
+  void* utr_alt;     // second trace buffer (same shape as b.Utr): the fused-face schedule writes
+                     // the next stage's traces there while neighbours still read b.Utr
   double* stage64;   // FP64 staging for transfers, max(nvar, nq, dim)*nn
   bool params_set, state_set;
   long long launches;
@@ -130,7 +134,7 @@ struct nsk_ctx {
   // per-kernel profiling (nsk_set_profiling)
   bool prof_on;
   std::vector<cudaEvent_t> prof_pool;  // groups of NSK_NKERN + 1 events
-  std::vector<int> prof_nk;            // kernels recorded in each used group
+  std::vector<int> prof_nk;            // bit k set: kernel k launched between events k and k+1
   size_t prof_used;                    // groups recorded since the last sync
   double prof_ms[NSK_NKERN];
   long long prof_cnt[NSK_NKERN];

@@ -3,7 +3,8 @@
 // type R of the DG operator (double, or float with the equation of state in
 // double), the dimension D and the number of nodes per direction NP = N + 1.
 //
-// One stage is four launches (three with the fused face schedule):
+// One stage is four launches (three with the fused face schedule, one fewer again
+// when the previous stage's volume kernel already wrote the traces of its output):
 //   k_prolong  U -> traces of U on every element face (GL: l_j(+-1) dot a line)
 //   k_lift     U, traces -> BR1 gradients Q of (v, c) and the face-normal
 //              viscous-flux traces of the element's own faces
@@ -11,7 +12,8 @@
 //              mean viscous flux, once per face (separate schedule only)
 //   k_volume   U, Q, face fluxes -> weak-form volume integral, surface lifting,
 //              relaxation sources, then the residual or the fused LSRK update;
-//              with the fused face schedule it evaluates its own faces' fluxes
+//              with the fused face schedule it evaluates its own faces' fluxes;
+//              optionally it also writes the traces of the updated state
 // The grid-wide dependencies of BR1 (a face needs both neighbours' traces,
 // twice per residual) are the launch boundaries.
 #pragma once
@@ -156,27 +158,24 @@ __device__ __forceinline__ int rho_flags(R rho) {
 // --------------------------------------------------------------------------
 
 // Utr[v][slot][E][nfn], slot = 2k + (0: face xi_k = -1, 1: xi_k = +1): the trace
-// sum_j l_j(+-1) U_j along the line in direction k through face node fn.
+// sum_j l_j(+-1) U_j along the line in direction k through face node fn of element e.
+// `u` points at node 0 of the element's first variable, variables `vs` apart (the
+// global array, or an element staged in shared memory: both give the same bits).
 template <typename R, int D, int NP>
-__device__ __forceinline__ void prolong_item(const NskParams& p, const R* __restrict__ U, R* __restrict__ Utr,
-                                             const long long idx) {
+__device__ __forceinline__ void prolong_trace(const NskParams& p, const R* __restrict__ u, const long long vs,
+                                              R* __restrict__ Utr, const long long e, const int slot, const int fn) {
   using S = Shape<D, NP>;
   const auto& t = TabSel<R>::get(p);
-  const int fn = (int)(idx % S::NFN);
-  const long long r = idx / S::NFN;
-  const long long e = r % p.E;
-  const int slot = (int)(r / p.E);
   const int k = slot >> 1;
   const R* L = (slot & 1) ? t.lp : t.lm;
   const int n0 = line_base<D, NP>(fn, k), st = node_stride<NP>(k);
-  const long long nn = p.E * S::NPE;
-  const R* u = U + e * S::NPE + n0;
+  const R* ul = u + n0;
   R rho = 0;
 #pragma unroll
   for (int v = 0; v < S::NV; ++v) {
     R acc = 0;
 #pragma unroll
-    for (int j = 0; j < NP; ++j) acc = fma(L[j], u[v * nn + j * st], acc);
+    for (int j = 0; j < NP; ++j) acc = fma(L[j], ul[v * vs + j * st], acc);
     Utr[((long long)(v * S::NF + slot) * p.E + e) * S::NFN + fn] = acc;
     if (v == 0) rho = acc;
   }
@@ -186,6 +185,18 @@ __device__ __forceinline__ void prolong_item(const NskParams& p, const R* __rest
     Utr[((long long)(S::NV * S::NF + slot) * p.E + e) * S::NFN + fn] = (R(3) - rho) * d;
     Utr[((long long)((S::NV + 1) * S::NF + slot) * p.E + e) * S::NFN + fn] = rho * d;
   }
+}
+
+// one (element, face slot, face node) item of the stand-alone prolongation, idx = (slot, e, fn)
+template <typename R, int D, int NP>
+__device__ __forceinline__ void prolong_item(const NskParams& p, const R* __restrict__ U, R* __restrict__ Utr,
+                                             const long long idx) {
+  using S = Shape<D, NP>;
+  const int fn = (int)(idx % S::NFN);
+  const long long r = idx / S::NFN;
+  const long long e = r % p.E;
+  const int slot = (int)(r / p.E);
+  prolong_trace<R, D, NP>(p, U + e * S::NPE, p.E * S::NPE, Utr, e, slot, fn);
 }
 
 // shared memory (in units of R) of lift_group
@@ -393,12 +404,15 @@ __host__ __device__ constexpr int volume_smem() {
 // mode RHS: Rout = R; mode LSRK: K <- A K + dt R, U <- U + B K.
 // FUSED: the element evaluates the fluxes of its own 2d faces (each face is then
 // evaluated by both neighbours, bit-identically) instead of reading Fstar.
+// UtrNext (optional): the traces of the element's new state (LSRK) or of its state (RHS)
+// are written there from shared memory, so the next stage needs no prolongation pass.
+// It must not alias Utr when FUSED (neighbours still read Utr).
 template <typename R, int D, int NP, int G, bool FUSED>
 __device__ __forceinline__ void volume_group(const NskParams& p, R* __restrict__ U, const R* __restrict__ Q,
                                              const R* __restrict__ Fstar, const R* __restrict__ Utr,
                                              const R* __restrict__ FVtr, R* __restrict__ K, R* __restrict__ Rout,
                                              const int mode, const R A, const R B, const R dt, const long long e0,
-                                             R* sm, int& eflag) {
+                                             R* sm, int& eflag, R* __restrict__ UtrNext = nullptr) {
   using S = Shape<D, NP>;
   constexpr int NPE = S::NPE, NFN = S::NFN, NW = S::NW, NV = S::NV, NQ = S::NQ, NF = S::NF;
   R* sf = sm;                          // [G][D][NV][NPE] fluxes F_k at the nodes
@@ -500,11 +514,25 @@ __device__ __forceinline__ void volume_group(const NskParams& p, R* __restrict__
       for (int v = 0; v < NV; ++v) {
         const R kv = fma(A, K[v * nn + g], dt * res[v]);
         K[v * nn + g] = kv;
-        U[v * nn + g] = fma(B, kv, u[v]);
+        u[v] = fma(B, kv, u[v]);
+        U[v * nn + g] = u[v];
       }
     }
   }
   __syncthreads();  // the caller may reuse shared memory
+  if (UtrNext != nullptr) {  // uniform over the block
+    R* su = sm;               // [G][NV][NPE] the element's (new) state
+    if (valid) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) su[(le * NV + v) * NPE + n] = u[v];
+    }
+    __syncthreads();
+    if (valid) {
+      for (int it = n; it < NF * NFN; it += NPE)
+        prolong_trace<R, D, NP>(p, su + le * NV * NPE, NPE, UtrNext, e, it / NFN, it % NFN);
+    }
+    __syncthreads();
+  }
 }
 
 // ---- stand-alone stage kernels ---------------------------------------------
@@ -539,12 +567,12 @@ __global__ void __launch_bounds__(G * Shape<D, NP>::NPE)
     k_volume(const NskParams p, R* __restrict__ U, const R* __restrict__ Q, const R* __restrict__ Fstar,
              const R* __restrict__ Utr, const R* __restrict__ FVtr, R* __restrict__ K, R* __restrict__ Rout,
              const int mode, const R A, const R B, const double* __restrict__ dtp, const R dtv,
-             int* __restrict__ err) {
+             int* __restrict__ err, R* __restrict__ UtrNext) {
   __shared__ R sm[volume_smem<R, D, NP, G, FUSED>()];
   const R dt = dtp ? (R)*dtp : dtv;
   int eflag = 0;
   volume_group<R, D, NP, G, FUSED>(p, U, Q, Fstar, Utr, FVtr, K, Rout, mode, A, B, dt, (long long)blockIdx.x * G,
-                                   sm, eflag);
+                                   sm, eflag, UtrNext);
   if (eflag) atomicOr(err, eflag);
 }
 
@@ -677,10 +705,12 @@ int launch_stage_g(const NskParams& p, const NskBuffers& b, const NskLaunch& l, 
   using S = Shape<D, NP>;
   int nl = 0;
   if (l.ev) cudaEventRecord(l.ev[0], s);
-  const long long ptems = p.E * S::NF * S::NFN;
-  k_prolong<R, D, NP><<<grid_for(ptems, 256), 256, 0, s>>>(p, (const R*)b.U, (R*)b.Utr);
+  if (!l.traces_ready) {
+    const long long ptems = p.E * S::NF * S::NFN;
+    k_prolong<R, D, NP><<<grid_for(ptems, 256), 256, 0, s>>>(p, (const R*)b.U, (R*)b.Utr);
+    ++nl;
+  }
   if (l.ev) cudaEventRecord(l.ev[1], s);
-  ++nl;
   const unsigned eb = (unsigned)((p.E + G - 1) / G);
   k_lift<R, D, NP, G><<<eb, G * S::NPE, 0, s>>>(p, (const R*)b.U, (const R*)b.Utr, (R*)b.Q, (R*)b.FVtr, b.err);
   if (l.ev) cudaEventRecord(l.ev[2], s);
@@ -694,7 +724,7 @@ int launch_stage_g(const NskParams& p, const NskBuffers& b, const NskLaunch& l, 
     if (l.ev) cudaEventRecord(l.ev[3], s);
     k_volume<R, D, NP, G, FUSED><<<eb, G * S::NPE, 0, s>>>(
         p, (R*)b.U, (const R*)b.Q, (const R*)b.Fstar, (const R*)b.Utr, (const R*)b.FVtr, (R*)b.K, (R*)l.Rout,
-        l.mode, (R)l.A, (R)l.B, l.dt_dev, (R)l.dt_val, b.err);
+        l.mode, (R)l.A, (R)l.B, l.dt_dev, (R)l.dt_val, b.err, (R*)l.utr_next);
     if (l.ev) cudaEventRecord(l.ev[4], s);
     ++nl;
   }

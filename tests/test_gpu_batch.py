@@ -43,6 +43,33 @@ def test_schedules_are_bit_identical(gpu, precision, N):
     s.close()
 
 
+@pytest.mark.parametrize("precision", [nsk.NSK_FP64, nsk.NSK_FP32_MIXED])
+@pytest.mark.parametrize("fused", [False, True])
+def test_volume_kernel_traces_equal_a_prolongation_pass(gpu, precision, fused):
+    """Inside one nsk_step call every stage after the first takes the face traces that the
+    previous stage's volume kernel wrote; a call starts with a prolongation pass. Four steps
+    in one call must therefore equal four calls of one step, bit for bit."""
+    s = nsk.Solver(3, (5, 4, 3), 3, [0, 0, 0], [1, 1, 1], 0, precision)
+    s.set_params(**PRM)
+    s.set_schedule(256, fused)
+    U = _state(s, 5)
+    s.set_state(U)
+    s.step(1e-6, 4)
+    one_call = s.get_state()
+    s.set_state(U)
+    for _ in range(4):
+        s.step(1e-6, 1)
+    assert np.array_equal(s.get_state(), one_call)
+    s.set_state(U)
+    s.step(-0.5, 3)  # adaptive dt between steps, traces carried across them
+    a = s.get_state()
+    s.set_state(U)
+    for _ in range(3):
+        s.step(-0.5, 1)
+    assert np.array_equal(s.get_state(), a)
+    s.close()
+
+
 def test_autotune_keeps_state(gpu):
     s = nsk.Solver(3, (8, 8, 8), 3, [0, 0, 0], [1, 1, 1], 0, nsk.NSK_FP32_MIXED)
     s.set_params(**PRM)

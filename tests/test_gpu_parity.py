@@ -198,10 +198,18 @@ def test_launch_counter_and_profile(gpu):
     n0 = s.launch_count
     s.set_profiling(True)
     s.step(1e-7, 2)
-    assert s.launch_count - n0 == 2 * 5 * 4
     prof = s.get_profile(reset=True)
-    assert all(cnt == 10 for _, cnt in prof.values())
+    # one prolongation pass per call: later stages take the traces the volume kernel wrote
+    assert prof["k_prolong"][1] == 1
+    assert prof["k_lift"][1] == 10 and prof["k_face"][1] == 10 and prof["k_volume"][1] == 10
+    assert s.launch_count - n0 == 1 + 2 * 5 * 3
     assert all(ms > 0 for ms, _ in prof.values())
+    s.set_schedule(128, True)
+    n0 = s.launch_count
+    s.step(1e-7, 1)
+    prof = s.get_profile(reset=True)
+    assert prof["k_face"][1] == 0 and prof["k_volume"][1] == 5 and prof["k_prolong"][1] == 1
+    assert s.launch_count - n0 == 1 + 5 * 2
     s.close()
 
 
