@@ -68,16 +68,17 @@ __device__ __forceinline__ int node_stride(int k) {
   return k == 0 ? 1 : (k == 1 ? NP : NP * NP);
 }
 
-// periodic neighbour of element e in direction k, side dir = -1 / +1
+// periodic neighbour of element e in direction k, side dir = -1 / +1 (element indices fit
+// in 32 bits: nsk_init_mesh rejects meshes with E * nodes per element above 2^31)
 __device__ __forceinline__ long long nbr_elem(const NskParams& p, long long e, int k, int dir) {
-  long long s = 1;
-  for (int q = 0; q < k; ++q) s *= p.ne[q];
+  unsigned s = 1;
+  for (int q = 0; q < k; ++q) s *= (unsigned)p.ne[q];
   const int n = p.ne[k];
-  const int c = (int)((e / s) % n);
+  const int c = (int)(((unsigned)e / s) % (unsigned)n);
   int cn = c + dir;
   cn += (cn < 0) ? n : 0;
   cn -= (cn >= n) ? n : 0;
-  return e + (long long)(cn - c) * s;
+  return e + (long long)(cn - c) * (long long)s;
 }
 
 // ---- Van-der-Waals EoS, Sec. 2.1 (reduced: p = 8 T rho / (3 - rho) - 3 rho^2) ----
@@ -95,6 +96,24 @@ __device__ __forceinline__ void eos_both64(const NskParams& p, double rho, doubl
   const double q = 1.0 / (3.0 - rho);
   pa = fma(p.t8 * rho, q, (p.pa2 * rho) * rho);
   dpa = fma(p.t24 * q, q, p.dpa1 * rho);
+}
+// 1/(3 - rho) in FP64 for the FP32 operator's rho: FP32 seed q0, then one Newton-Raphson
+// step for the reciprocal, q = q0 + q0 (1 - a q0), which squares the seed's relative error
+// (<= 2^-23 -> <= 2^-46; the FP64 value is rounded to FP32 afterwards). a = 3 - rho is exact
+// in FP64.
+__device__ __forceinline__ double recip_3m(float rho) {
+  const double a = 3.0 - (double)rho;
+  const double q0 = (double)(1.0f / (float)a);
+  return fma(q0, fma(-a, q0, 1.0), q0);
+}
+__device__ __forceinline__ double eos_pa64f(const NskParams& p, float rho) {
+  const double r = rho, q = recip_3m(rho);
+  return fma(p.t8 * r, q, (p.pa2 * r) * r);
+}
+__device__ __forceinline__ void eos_both64f(const NskParams& p, float rho, double& pa, double& dpa) {
+  const double r = rho, q = recip_3m(rho);
+  pa = fma(p.t8 * r, q, (p.pa2 * r) * r);
+  dpa = fma(p.t24 * q, q, p.dpa1 * r);
 }
 // Precision policy of the FP32 operator: FP32 EoS, except inside the spinodal interval and
 // wherever p_alpha' cancels (alpha close to alpha_*), where it is evaluated in FP64.
@@ -118,7 +137,7 @@ template <> struct Eos<double> {
 };
 template <> struct Eos<float> {
   __device__ static __forceinline__ float pa(const NskParams& p, float rho) {
-    if (eos_needs64(p, rho)) return (float)eos_pa64(p, (double)rho);
+    if (eos_needs64(p, rho)) return (float)eos_pa64f(p, rho);
     const float q = 1.0f / (3.0f - rho);
     return fmaf(p.t8f * rho, q, (p.pa2f * rho) * rho);
   }
@@ -131,7 +150,7 @@ template <> struct Eos<float> {
       if (fabsf(dpa) >= 1e-3f * (fabsf(a) + fabsf(b))) return;
     }
     double pd, dd;
-    eos_both64(p, (double)rho, pd, dd);
+    eos_both64f(p, rho, pd, dd);
     pa = (float)pd;
     dpa = (float)dd;
   }
@@ -395,15 +414,16 @@ __device__ __forceinline__ void face_item(const NskParams& p, const R* __restric
 template <typename R, int D, int NP, int G, bool FUSED>
 __host__ __device__ constexpr int volume_smem() {
   using S = Shape<D, NP>;
-  return G * D * S::NV * S::NPE + (FUSED ? G * S::NF * S::NV * S::NFN : 0);
+  return G * D * S::NV * S::NPE + G * S::NF * S::NV * S::NFN;
 }
 
 // Weak-form volume integral and surface lifting (Eq. weakformulation),
 //   R_i = sum_k (2/h_k) [ sum_j (w_j/w_i) l_i'(xi_j) F_k(U_j, Q_j) - (F*_{k,+} l_i(1) - F*_{k,-} l_i(-1)) / w_i ] + S_i,
 // F_k = F^c_k - F^v_k, S = (0, alpha rho grad c, (alpha/beta)(rho - c)); then
 // mode RHS: Rout = R; mode LSRK: K <- A K + dt R, U <- U + B K.
-// FUSED: the element evaluates the fluxes of its own 2d faces (each face is then
-// evaluated by both neighbours, bit-identically) instead of reading Fstar.
+// The fluxes of the element's 2d faces are staged in shared memory: read from Fstar with
+// coalesced loads, or, FUSED, evaluated by the element itself (each face is then
+// evaluated by both neighbours, bit-identically).
 // UtrNext (optional): the traces of the element's new state (LSRK) or of its state (RHS)
 // are written there from shared memory, so the next stage needs no prolongation pass.
 // It must not alias Utr when FUSED (neighbours still read Utr).
@@ -416,7 +436,7 @@ __device__ __forceinline__ void volume_group(const NskParams& p, R* __restrict__
   using S = Shape<D, NP>;
   constexpr int NPE = S::NPE, NFN = S::NFN, NW = S::NW, NV = S::NV, NQ = S::NQ, NF = S::NF;
   R* sf = sm;                          // [G][D][NV][NPE] fluxes F_k at the nodes
-  R* sfs = sm + G * D * NV * NPE;      // [G][NF][NV][NFN] face fluxes (FUSED)
+  R* sfs = sm + G * D * NV * NPE;      // [G][NF][NV][NFN] fluxes of the element's faces
   const auto& t = TabSel<R>::get(p);
   const int le = threadIdx.x / NPE, n = threadIdx.x % NPE;
   const long long e = e0 + le;
@@ -467,16 +487,22 @@ __device__ __forceinline__ void volume_group(const NskParams& p, R* __restrict__
 #pragma unroll
         for (int v = 0; v < NV; ++v) sfs[((le * NF + slot) * NV + v) * NFN + fn] = F[v];
       }
+    } else {
+      // Fstar[v][k][E][nfn] holds the flux on face (e, +k): slot 2k+1 is the element's own
+      // entry, slot 2k its -k neighbour's
+      long long eL[D];
+#pragma unroll
+      for (int k = 0; k < D; ++k) eL[k] = nbr_elem(p, e, k, -1);
+      for (int it = n; it < NF * NV * NFN; it += NPE) {
+        const int fn = it % NFN, v = (it / NFN) % NV, slot = it / (NV * NFN), k = slot >> 1;
+        const long long src = (slot & 1) ? e : eL[k];
+        sfs[((le * NF + slot) * NV + v) * NFN + fn] = Fstar[((long long)(v * D + k) * p.E + src) * NFN + fn];
+      }
     }
   }
   __syncthreads();
 
   if (valid) {
-    long long eL[D];
-    if constexpr (!FUSED) {
-#pragma unroll
-      for (int k = 0; k < D; ++k) eL[k] = nbr_elem(p, e, k, -1);
-    }
     R res[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
@@ -489,14 +515,8 @@ __device__ __forceinline__ void volume_group(const NskParams& p, R* __restrict__
         R vol = 0;
 #pragma unroll
         for (int j = 0; j < NP; ++j) vol = fma(t.dvol[i * NSK_MAXNP + j], f[j * st], vol);
-        R fp, fm;
-        if constexpr (FUSED) {
-          fp = sfs[((le * NF + 2 * k + 1) * NV + v) * NFN + fn];
-          fm = sfs[((le * NF + 2 * k) * NV + v) * NFN + fn];
-        } else {
-          fp = Fstar[((long long)(v * D + k) * p.E + e) * NFN + fn];
-          fm = Fstar[((long long)(v * D + k) * p.E + eL[k]) * NFN + fn];
-        }
+        const R fp = sfs[((le * NF + 2 * k + 1) * NV + v) * NFN + fn];
+        const R fm = sfs[((le * NF + 2 * k) * NV + v) * NFN + fn];
         acc = fma(t.rh[k], vol - fma(fp, t.lpw[i], -(fm * t.lmw[i])), acc);
       }
       res[v] = acc;
