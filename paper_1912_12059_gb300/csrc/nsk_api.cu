@@ -144,7 +144,15 @@ void spinodal_interval(double T, double* lo, double* hi) {
 // model coefficients of both operator precisions (after the mesh and the parameters are known)
 template <typename R>
 void fill_coef(NskTab<R>& t, const NskParams& p) {
-  for (int k = 0; k < 3; ++k) t.rh[k] = (R)p.rh[k];
+  const NskTab<double>& td = p.td;  // the FP64 operator tables (already filled)
+  for (int k = 0; k < 3; ++k) {
+    t.rh[k] = (R)p.rh[k];
+    for (int i = 0; i < NSK_MAXNP; ++i) {
+      for (int j = 0; j < NSK_MAXNP; ++j) t.dk[k][i * NSK_MAXNP + j] = (R)(p.rh[k] * td.dvol[i * NSK_MAXNP + j]);
+      t.lpk[k][i] = (R)(p.rh[k] * td.lpw[i]);
+      t.lmk[k][i] = (R)(p.rh[k] * td.lmw[i]);
+    }
+  }
   t.mu = (R)p.mu;
   t.kb = (R)(p.kappa / p.beta);
   t.alpha = (R)p.alpha;

@@ -159,11 +159,21 @@ __device__ __forceinline__ double eos_free_energy(const NskParams& p, double rho
   // W = rho R T ln(rho / (1 - b rho)) - a rho^2, Eq. (vdw_freeenergy)
   return (8.0 / 3.0) * p.T * rho * log(3.0 * rho / (3.0 - rho)) - 3.0 * rho * rho;
 }
+// 0 < rho < 3 tested on the bit pattern (positive IEEE numbers order like their bits; zero,
+// negatives, NaN and 3 or more fall outside), which keeps the test off the FP64 pipe. In FP64
+// the high word decides: it accepts rho >= 2^-1042 (smaller positive subnormals are flagged).
+__device__ __forceinline__ bool rho_ok(double rho) {
+  return (unsigned)__double2hiint(rho) - 1u < 0x40080000u - 1u;
+}
+__device__ __forceinline__ bool rho_ok(float rho) { return __float_as_uint(rho) - 1u < 0x40400000u - 1u; }
 template <typename R>
 __device__ __forceinline__ int rho_flags(R rho) {
-  if (rho > R(0) && rho < R(3)) return 0;
+  if (rho_ok(rho)) return 0;
   return (rho != rho) ? (NSK_EBIT_RHO | NSK_EBIT_NAN) : NSK_EBIT_RHO;
 }
+// p_alpha' >= 0 and finite, on the bit pattern (a negative sign, NaN or infinity fail; so does -0)
+__device__ __forceinline__ bool sound_ok(double d) { return (unsigned)__double2hiint(d) < 0x7FF00000u; }
+__device__ __forceinline__ bool sound_ok(float d) { return __float_as_uint(d) < 0x7F800000u; }
 
 // --------------------------------------------------------------------------
 // Stage bodies. Every stage kernel below (and the batched persistent kernel in
@@ -228,7 +238,8 @@ __host__ __device__ constexpr int lift_smem() {
 }
 
 // BR1 lifting (Sec. 3.1) in weak form with the central flux,
-//   Q_{k,w}(i) = (2/h_k) [ -sum_j (w_j/w_i) l_i'(xi_j) w_j + (w*_{k,+} l_i(1) - w*_{k,-} l_i(-1)) / w_i ],
+//   Q_{k,w}(i) = (2/h_k) [ -sum_j (w_j/w_i) l_i'(xi_j) w_j + (w*_{k,+} l_i(1) - w*_{k,-} l_i(-1)) / w_i ]
+// (evaluated with the 2/h_k-scaled tables dk, lpk, lmk),
 // w = (v, c) formed from the conservative traces on both sides of each face; then the
 // face-normal viscous flux F^v_k = (tau_{.k}, (kappa/beta) c_{x_k}) traced onto the
 // element's own faces (FVtr[c][slot][E][nfn]) for the face flux.
@@ -286,17 +297,16 @@ __device__ __forceinline__ void lift_group(const NskParams& p, const R* __restri
     for (int k = 0; k < D; ++k) {
       const int i = coord<NP>(n, k), fn = face_node<D, NP>(n, k);
       const int n0 = line_base<D, NP>(fn, k), st = node_stride<NP>(k);
-      const R rh = t.rh[k];
+      const R* dk = t.dk[k] + i * NSK_MAXNP;
 #pragma unroll
       for (int w = 0; w < NW; ++w) {
         const R* wl = sw + (le * NW + w) * NPE + n0;
         R vol = 0;
 #pragma unroll
-        for (int j = 0; j < NP; ++j) vol = fma(t.dvol[i * NSK_MAXNP + j], wl[j * st], vol);
+        for (int j = 0; j < NP; ++j) vol = fma(dk[j], wl[j * st], vol);
         const R wp = sws[((le * NF + 2 * k + 1) * NW + w) * NFN + fn];
         const R wm = sws[((le * NF + 2 * k) * NW + w) * NFN + fn];
-        const R surf = fma(wp, t.lpw[i], -(wm * t.lmw[i]));
-        q[k * NW + w] = rh * (surf - vol);
+        q[k * NW + w] = fma(wp, t.lpk[k][i], fma(-wm, t.lmk[k][i], -vol));
         Q[(long long)(k * NW + w) * nn + e * NPE + n] = q[k * NW + w];
       }
     }
@@ -379,7 +389,7 @@ __device__ __forceinline__ void face_flux(const NskParams& p, const R* __restric
     VR[c] = FVtr[((long long)(c * NF + 2 * k) * p.E + eR) * NFN + fn];
   }
   eflag |= rho_flags(UL[0]) | rho_flags(UR[0]);
-  if (!(dl >= R(0)) || !(dr >= R(0))) eflag |= NSK_EBIT_SOUND;
+  if (!sound_ok(dl) || !sound_ok(dr)) eflag |= NSK_EBIT_SOUND;
   const R lam_l = fabs(UL[1 + k] * il) + sqrt(dl), lam_r = fabs(UR[1 + k] * ir) + sqrt(dr);
   const R lam = lam_l > lam_r ? lam_l : lam_r;
   F[0] = R(0.5) * (UL[1 + k] + UR[1 + k]);
@@ -503,6 +513,7 @@ __device__ __forceinline__ void volume_group(const NskParams& p, R* __restrict__
   __syncthreads();
 
   if (valid) {
+    // acc = sum_k [ sum_j dk[i][j] F_k(j) - F*_{k,+} lpk[i] + F*_{k,-} lmk[i] ]  (2/h_k folded in)
     R res[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
@@ -512,12 +523,12 @@ __device__ __forceinline__ void volume_group(const NskParams& p, R* __restrict__
         const int i = coord<NP>(n, k), fn = face_node<D, NP>(n, k);
         const int n0 = line_base<D, NP>(fn, k), st = node_stride<NP>(k);
         const R* f = sf + ((le * D + k) * NV + v) * NPE + n0;
-        R vol = 0;
+        const R* dk = t.dk[k] + i * NSK_MAXNP;
 #pragma unroll
-        for (int j = 0; j < NP; ++j) vol = fma(t.dvol[i * NSK_MAXNP + j], f[j * st], vol);
+        for (int j = 0; j < NP; ++j) acc = fma(dk[j], f[j * st], acc);
         const R fp = sfs[((le * NF + 2 * k + 1) * NV + v) * NFN + fn];
         const R fm = sfs[((le * NF + 2 * k) * NV + v) * NFN + fn];
-        acc = fma(t.rh[k], vol - fma(fp, t.lpw[i], -(fm * t.lmw[i])), acc);
+        acc = fma(fm, t.lmk[k][i], fma(-fp, t.lpk[k][i], acc));
       }
       res[v] = acc;
     }
