@@ -228,13 +228,37 @@ __device__ __forceinline__ void prolong_item(const NskParams& p, const R* __rest
   prolong_trace<R, D, NP>(p, U + e * S::NPE, p.E * S::NPE, Utr, e, slot, fn);
 }
 
+// Shared-memory copy of the direction operators (2/h_k folded in) of one precision:
+// [D][NP][NP] dk, then [D][NP] lpk, then [D][NP] lmk. Every thread of a warp reads its own
+// row i; from shared memory the distinct rows are served in one pass, where the kernel
+// parameter bank would serialise them.
+template <int D, int NP>
+__host__ __device__ constexpr int tab_smem() {
+  return D * NP * NP + 2 * D * NP;
+}
+template <typename R, int D, int NP>
+__device__ __forceinline__ void stage_tables(const NskTab<R>& t, R* tb) {
+  for (int x = threadIdx.x; x < D * NP * NP; x += blockDim.x) {
+    const int k = x / (NP * NP), r = x % (NP * NP);
+    tb[x] = t.dk[k][(r / NP) * NSK_MAXNP + r % NP];
+  }
+  for (int x = threadIdx.x; x < D * NP; x += blockDim.x) {
+    tb[D * NP * NP + x] = t.lpk[x / NP][x % NP];
+    tb[D * NP * NP + D * NP + x] = t.lmk[x / NP][x % NP];
+  }
+}
+
 // shared memory (in units of R) of lift_group
 template <typename R, int D, int NP, int G>
-__host__ __device__ constexpr int lift_smem() {
+__host__ __device__ constexpr int lift_work_smem() {
   using S = Shape<D, NP>;
   return (G * S::NW * S::NPE + G * S::NF * S::NW * S::NFN) > (G * D * S::NW * S::NPE)
              ? (G * S::NW * S::NPE + G * S::NF * S::NW * S::NFN)
              : (G * D * S::NW * S::NPE);
+}
+template <typename R, int D, int NP, int G>
+__host__ __device__ constexpr int lift_smem() {
+  return lift_work_smem<R, D, NP, G>() + tab_smem<D, NP>();
 }
 
 // BR1 lifting (Sec. 3.1) in weak form with the central flux,
@@ -251,12 +275,14 @@ __device__ __forceinline__ void lift_group(const NskParams& p, const R* __restri
   constexpr int NPE = S::NPE, NFN = S::NFN, NW = S::NW, NF = S::NF, NV = S::NV, NQ = S::NQ;
   R* sw = sm;                  // [G][NW][NPE] primitive variables at the nodes
   R* sws = sm + G * NW * NPE;  // [G][NF][NW][NFN] central flux w* on the faces
+  R* tb = sm + lift_work_smem<R, D, NP, G>();  // direction operators
   const auto& t = TabSel<R>::get(p);
   const int le = threadIdx.x / NPE, n = threadIdx.x % NPE;
   const long long e = e0 + le;
   const bool valid = le < G && e < p.E;
   const long long nn = p.E * NPE;
 
+  stage_tables<R, D, NP>(t, tb);
   if (valid) {
     const R rho = U[e * NPE + n];
     eflag |= rho_flags(rho);
@@ -297,7 +323,10 @@ __device__ __forceinline__ void lift_group(const NskParams& p, const R* __restri
     for (int k = 0; k < D; ++k) {
       const int i = coord<NP>(n, k), fn = face_node<D, NP>(n, k);
       const int n0 = line_base<D, NP>(fn, k), st = node_stride<NP>(k);
-      const R* dk = t.dk[k] + i * NSK_MAXNP;
+      R dk[NP];
+#pragma unroll
+      for (int j = 0; j < NP; ++j) dk[j] = tb[(k * NP + i) * NP + j];
+      const R lpk = tb[D * NP * NP + k * NP + i], lmk = tb[D * NP * NP + D * NP + k * NP + i];
 #pragma unroll
       for (int w = 0; w < NW; ++w) {
         const R* wl = sw + (le * NW + w) * NPE + n0;
@@ -306,7 +335,7 @@ __device__ __forceinline__ void lift_group(const NskParams& p, const R* __restri
         for (int j = 0; j < NP; ++j) vol = fma(dk[j], wl[j * st], vol);
         const R wp = sws[((le * NF + 2 * k + 1) * NW + w) * NFN + fn];
         const R wm = sws[((le * NF + 2 * k) * NW + w) * NFN + fn];
-        q[k * NW + w] = fma(wp, t.lpk[k][i], fma(-wm, t.lmk[k][i], -vol));
+        q[k * NW + w] = fma(wp, lpk, fma(-wm, lmk, -vol));
         Q[(long long)(k * NW + w) * nn + e * NPE + n] = q[k * NW + w];
       }
     }
@@ -424,7 +453,7 @@ __device__ __forceinline__ void face_item(const NskParams& p, const R* __restric
 template <typename R, int D, int NP, int G, bool FUSED>
 __host__ __device__ constexpr int volume_smem() {
   using S = Shape<D, NP>;
-  return G * D * S::NV * S::NPE + G * S::NF * S::NV * S::NFN;
+  return G * D * S::NV * S::NPE + G * S::NF * S::NV * S::NFN + tab_smem<D, NP>();
 }
 
 // Weak-form volume integral and surface lifting (Eq. weakformulation),
@@ -447,6 +476,7 @@ __device__ __forceinline__ void volume_group(const NskParams& p, R* __restrict__
   constexpr int NPE = S::NPE, NFN = S::NFN, NW = S::NW, NV = S::NV, NQ = S::NQ, NF = S::NF;
   R* sf = sm;                          // [G][D][NV][NPE] fluxes F_k at the nodes
   R* sfs = sm + G * D * NV * NPE;      // [G][NF][NV][NFN] fluxes of the element's faces
+  R* tb = sfs + G * NF * NV * NFN;     // direction operators
   const auto& t = TabSel<R>::get(p);
   const int le = threadIdx.x / NPE, n = threadIdx.x % NPE;
   const long long e = e0 + le;
@@ -454,6 +484,7 @@ __device__ __forceinline__ void volume_group(const NskParams& p, R* __restrict__
   const long long nn = p.E * NPE;
   const long long g = e * NPE + n;
 
+  stage_tables<R, D, NP>(t, tb);
   R u[NV], q[NQ];
   if (valid) {
 #pragma unroll
@@ -513,24 +544,29 @@ __device__ __forceinline__ void volume_group(const NskParams& p, R* __restrict__
   __syncthreads();
 
   if (valid) {
-    // acc = sum_k [ sum_j dk[i][j] F_k(j) - F*_{k,+} lpk[i] + F*_{k,-} lmk[i] ]  (2/h_k folded in)
+    // res_v = sum_k [ sum_j dk[i][j] F_k(j) - F*_{k,+} lpk[i] + F*_{k,-} lmk[i] ]  (2/h_k folded in),
+    // accumulated over k in ascending order
     R res[NV];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      R acc = 0;
+    for (int v = 0; v < NV; ++v) res[v] = 0;
 #pragma unroll
-      for (int k = 0; k < D; ++k) {
-        const int i = coord<NP>(n, k), fn = face_node<D, NP>(n, k);
-        const int n0 = line_base<D, NP>(fn, k), st = node_stride<NP>(k);
+    for (int k = 0; k < D; ++k) {
+      const int i = coord<NP>(n, k), fn = face_node<D, NP>(n, k);
+      const int n0 = line_base<D, NP>(fn, k), st = node_stride<NP>(k);
+      R dk[NP];
+#pragma unroll
+      for (int j = 0; j < NP; ++j) dk[j] = tb[(k * NP + i) * NP + j];
+      const R lpk = tb[D * NP * NP + k * NP + i], lmk = tb[D * NP * NP + D * NP + k * NP + i];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
         const R* f = sf + ((le * D + k) * NV + v) * NPE + n0;
-        const R* dk = t.dk[k] + i * NSK_MAXNP;
+        R acc = res[v];
 #pragma unroll
         for (int j = 0; j < NP; ++j) acc = fma(dk[j], f[j * st], acc);
         const R fp = sfs[((le * NF + 2 * k + 1) * NV + v) * NFN + fn];
         const R fm = sfs[((le * NF + 2 * k) * NV + v) * NFN + fn];
-        acc = fma(fm, t.lmk[k][i], fma(-fp, t.lpk[k][i], acc));
+        res[v] = fma(fm, lmk, fma(-fp, lpk, acc));
       }
-      res[v] = acc;
     }
     const R alpha = t.alpha;
 #pragma unroll
