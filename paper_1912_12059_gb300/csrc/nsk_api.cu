@@ -159,6 +159,21 @@ void fill_coef(NskTab<R>& t, const NskParams& p) {
   t.ab = (R)(p.alpha / p.beta);
 }
 
+// index constants of the kernels (after E and ne are known)
+void set_index_constants(NskParams& p, int npe, int nfn) {
+  p.nne = (int)(p.E * npe);
+  p.nfe = (int)(p.E * nfn);
+  int st = 1;
+  for (int k = 0; k < 3; ++k) {
+    p.est[k] = st;
+    p.ewrap[k] = (p.ne[k] - 1) * st;
+    st *= p.ne[k];
+  }
+  p.fd_ne0 = make_fastdiv((unsigned)p.ne[0]);
+  p.fd_ne1 = make_fastdiv((unsigned)p.ne[1]);
+  p.fd_E = make_fastdiv((unsigned)p.E);
+}
+
 void set_eos_constants(NskParams& p) {
   fill_coef<double>(p.td, p);
   fill_coef<float>(p.tf, p);
@@ -361,6 +376,7 @@ int nsk_init_mesh(nsk_ctx** out, int dim, const int nelem[3], const double lo[3]
     p.rh[k] = k < dim ? 2.0 / c->h[k] : 0.0;
     if (k < dim) p.jac *= c->h[k] / 2.0;
   }
+  set_index_constants(p, c->npe, c->nfn);
   fill_tab<double>(p.td, c->np, c->xi, c->w);
   fill_tab<float>(p.tf, c->np, c->xi, c->w);
 
@@ -759,6 +775,7 @@ extern "C" int nsk_rhs_static_scratch(int dim, const int nelem[3], const double 
     p.rh[k] = k < dim ? 2.0 / h[k] : 0.0;
     if (k < dim) p.jac *= h[k] / 2.0;
   }
+  set_index_constants(p, (int)npe, (int)nfn);
   p.T = T;
   p.kappa = kappa;
   p.alpha = alpha;

@@ -45,10 +45,32 @@ struct NskTab {
 template <typename R> struct TraceComps { static constexpr int extra = 0; };
 template <> struct TraceComps<double> { static constexpr int extra = 2; };
 
+// Division by an invariant divisor d >= 1 as a multiply and a shift (Granlund and Montgomery,
+// "Division by invariant integers using multiplication", 1994): with l = ceil(log2 d),
+// s = 31 + l and m = ceil(2^s / d) (< 2^32), x / d = (x m) >> s exactly for 0 <= x < 2^31.
+struct FastDiv {
+  unsigned m;
+  int s;
+};
+inline FastDiv make_fastdiv(unsigned d) {
+  int l = 0;
+  while ((1ull << l) < d) ++l;
+  const int s = 31 + l;
+  return FastDiv{(unsigned)(((1ull << s) + d - 1) / d), s};
+}
+__host__ __device__ __forceinline__ unsigned fdiv(unsigned x, FastDiv f) {
+  return (unsigned)(((unsigned long long)x * f.m) >> f.s);
+}
+
 // Everything a kernel needs besides its buffers; passed by value.
 struct NskParams {
   long long E;     // number of elements
   int ne[3];       // elements per direction (1 beyond dim)
+  // 32-bit index arithmetic (nsk_init_mesh keeps E * nodes per element below 2^31)
+  int nne, nfe;    // E * nodes per element, E * nodes per face: the size of one variable's plane
+  int est[3];      // element-index stride of direction k (1, ne0, ne0 ne1)
+  int ewrap[3];    // (ne[k] - 1) est[k]: the periodic jump across direction k
+  FastDiv fd_ne0, fd_ne1, fd_E;
   double rh[3];    // 2 / h_k (Cartesian metric terms)
   double T, kappa, alpha, beta, mu;
   double jac;      // J = prod_k h_k / 2

@@ -81,6 +81,34 @@ __device__ __forceinline__ long long nbr_elem(const NskParams& p, long long e, i
   return e + (long long)(cn - c) * (long long)s;
 }
 
+// Cartesian position of an element for the stage kernels: 32-bit index and coordinates
+// (fast division by the invariant ne[0], ne[1]); its neighbours are a compare and an add.
+struct ElemIdx {
+  int e, c0, c1, c2;
+};
+template <int D>
+__device__ __forceinline__ ElemIdx elem_idx(const NskParams& p, int e) {
+  ElemIdx x{e, e, 0, 0};
+  if constexpr (D >= 2) {
+    const unsigned t = fdiv((unsigned)e, p.fd_ne0);
+    x.c0 = e - (int)t * p.ne[0];
+    if constexpr (D == 2) {
+      x.c1 = (int)t;
+    } else {
+      const unsigned z = fdiv(t, p.fd_ne1);
+      x.c1 = (int)t - (int)z * p.ne[1];
+      x.c2 = (int)z;
+    }
+  }
+  return x;
+}
+// periodic neighbour of x in direction k, side dir = -1 / +1 (same result as nbr_elem)
+__device__ __forceinline__ int nbr_of(const NskParams& p, const ElemIdx& x, int k, int dir) {
+  const int c = k == 0 ? x.c0 : (k == 1 ? x.c1 : x.c2);
+  if (dir > 0) return c == p.ne[k] - 1 ? x.e - p.ewrap[k] : x.e + p.est[k];
+  return c == 0 ? x.e + p.ewrap[k] : x.e - p.est[k];
+}
+
 // ---- Van-der-Waals EoS, Sec. 2.1 (reduced: p = 8 T rho / (3 - rho) - 3 rho^2) ----
 // Modified pressure p_alpha = p + alpha rho^2 / 2 (Eq. modified_pressure) and its derivative
 // with one reciprocal q = 1 / (3 - rho):
@@ -191,41 +219,44 @@ __device__ __forceinline__ bool sound_ok(float d) { return __float_as_uint(d) < 
 // `u` points at node 0 of the element's first variable, variables `vs` apart (the
 // global array, or an element staged in shared memory: both give the same bits).
 template <typename R, int D, int NP>
-__device__ __forceinline__ void prolong_trace(const NskParams& p, const R* __restrict__ u, const long long vs,
-                                              R* __restrict__ Utr, const long long e, const int slot, const int fn) {
+__device__ __forceinline__ void prolong_trace(const NskParams& p, const R* __restrict__ u, const size_t vs,
+                                              R* __restrict__ Utr, const int e, const int slot, const int fn) {
   using S = Shape<D, NP>;
   const auto& t = TabSel<R>::get(p);
   const int k = slot >> 1;
   const R* L = (slot & 1) ? t.lp : t.lm;
   const int n0 = line_base<D, NP>(fn, k), st = node_stride<NP>(k);
   const R* ul = u + n0;
+  const size_t pl = (size_t)S::NF * p.nfe;  // distance between the planes of two variables
+  R* o = Utr + (size_t)slot * p.nfe + (e * S::NFN + fn);
   R rho = 0;
 #pragma unroll
   for (int v = 0; v < S::NV; ++v) {
     R acc = 0;
 #pragma unroll
     for (int j = 0; j < NP; ++j) acc = fma(L[j], ul[v * vs + j * st], acc);
-    Utr[((long long)(v * S::NF + slot) * p.E + e) * S::NFN + fn] = acc;
+    o[v * pl] = acc;
     if (v == 0) rho = acc;
   }
   if constexpr (TraceComps<R>::extra > 0) {
     // one division: d = 1/(rho (3 - rho)) gives 1/rho = (3 - rho) d and 1/(3 - rho) = rho d
     const R d = R(1) / (rho * (R(3) - rho));
-    Utr[((long long)(S::NV * S::NF + slot) * p.E + e) * S::NFN + fn] = (R(3) - rho) * d;
-    Utr[((long long)((S::NV + 1) * S::NF + slot) * p.E + e) * S::NFN + fn] = rho * d;
+    o[S::NV * pl] = (R(3) - rho) * d;
+    o[(S::NV + 1) * pl] = rho * d;
   }
 }
 
-// one (element, face slot, face node) item of the stand-alone prolongation, idx = (slot, e, fn)
+// one (element, face slot, face node) item of the prolongation, idx = (slot, e, fn) flattened
+// (idx / nfn < 2^31 for every mesh nsk_init_mesh accepts)
 template <typename R, int D, int NP>
 __device__ __forceinline__ void prolong_item(const NskParams& p, const R* __restrict__ U, R* __restrict__ Utr,
                                              const long long idx) {
   using S = Shape<D, NP>;
   const int fn = (int)(idx % S::NFN);
-  const long long r = idx / S::NFN;
-  const long long e = r % p.E;
-  const int slot = (int)(r / p.E);
-  prolong_trace<R, D, NP>(p, U + e * S::NPE, p.E * S::NPE, Utr, e, slot, fn);
+  const unsigned r = (unsigned)(idx / S::NFN);
+  const unsigned slot = fdiv(r, p.fd_E);
+  const int e = (int)(r - slot * (unsigned)p.E);
+  prolong_trace<R, D, NP>(p, U + (size_t)e * S::NPE, (size_t)p.nne, Utr, e, (int)slot, fn);
 }
 
 // Shared-memory copy of the direction operators (2/h_k folded in) of one precision:
@@ -278,33 +309,38 @@ __device__ __forceinline__ void lift_group(const NskParams& p, const R* __restri
   R* tb = sm + lift_work_smem<R, D, NP, G>();  // direction operators
   const auto& t = TabSel<R>::get(p);
   const int le = threadIdx.x / NPE, n = threadIdx.x % NPE;
-  const long long e = e0 + le;
+  const int e = (int)e0 + le;
   const bool valid = le < G && e < p.E;
-  const long long nn = p.E * NPE;
+  const size_t nn = (size_t)p.nne;             // distance between the planes of two nodal variables
+  const size_t pl = (size_t)NF * p.nfe;        // distance between the planes of two trace variables
+  const int g = e * NPE + n;
 
   stage_tables<R, D, NP>(t, tb);
   if (valid) {
-    const R rho = U[e * NPE + n];
+    const R rho = U[g];
     eflag |= rho_flags(rho);
     const R inv = R(1) / rho;
 #pragma unroll
-    for (int a = 0; a < D; ++a) sw[(le * NW + a) * NPE + n] = U[(1 + a) * nn + e * NPE + n] * inv;
-    sw[(le * NW + D) * NPE + n] = U[(D + 1) * nn + e * NPE + n];
+    for (int a = 0; a < D; ++a) sw[(le * NW + a) * NPE + n] = U[(1 + a) * nn + g] * inv;
+    sw[(le * NW + D) * NPE + n] = U[(D + 1) * nn + g];
+    const ElemIdx ex = elem_idx<D>(p, e);
     for (int it = n; it < NF * NFN; it += NPE) {
       const int slot = it / NFN, fn = it % NFN, k = slot >> 1, s = slot & 1;
-      const long long en = nbr_elem(p, e, k, s ? 1 : -1);
+      const int en = nbr_of(p, ex, k, s ? 1 : -1);
       const int oslot = 2 * k + (1 - s);
+      const R* to = Utr + (size_t)slot * p.nfe + (e * NFN + fn);
+      const R* tn = Utr + (size_t)oslot * p.nfe + (en * NFN + fn);
       R uo[NV], un[NV];
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
-        uo[v] = Utr[((long long)(v * NF + slot) * p.E + e) * NFN + fn];
-        un[v] = Utr[((long long)(v * NF + oslot) * p.E + en) * NFN + fn];
+        uo[v] = to[v * pl];
+        un[v] = tn[v * pl];
       }
       eflag |= rho_flags(uo[0]) | rho_flags(un[0]);
       R io, in;
       if constexpr (TraceComps<R>::extra > 0) {
-        io = Utr[((long long)(NV * NF + slot) * p.E + e) * NFN + fn];
-        in = Utr[((long long)(NV * NF + oslot) * p.E + en) * NFN + fn];
+        io = to[NV * pl];
+        in = tn[NV * pl];
       } else {
         io = R(1) / uo[0];
         in = R(1) / un[0];
@@ -336,7 +372,7 @@ __device__ __forceinline__ void lift_group(const NskParams& p, const R* __restri
         const R wp = sws[((le * NF + 2 * k + 1) * NW + w) * NFN + fn];
         const R wm = sws[((le * NF + 2 * k) * NW + w) * NFN + fn];
         q[k * NW + w] = fma(wp, lpk, fma(-wm, lmk, -vol));
-        Q[(long long)(k * NW + w) * nn + e * NPE + n] = q[k * NW + w];
+        Q[(k * NW + w) * nn + g] = q[k * NW + w];
       }
     }
   }
@@ -366,13 +402,14 @@ __device__ __forceinline__ void lift_group(const NskParams& p, const R* __restri
       const int slot = it / NFN, fn = it % NFN, k = slot >> 1;
       const R* L = (slot & 1) ? t.lp : t.lm;
       const int n0 = line_base<D, NP>(fn, k), st = node_stride<NP>(k);
+      R* o = FVtr + (size_t)slot * p.nfe + (e * NFN + fn);
 #pragma unroll
       for (int c = 0; c < NW; ++c) {
         const R* f = sfv + ((le * D + k) * NW + c) * NPE + n0;
         R acc = 0;
 #pragma unroll
         for (int j = 0; j < NP; ++j) acc = fma(L[j], f[j * st], acc);
-        FVtr[((long long)(c * NF + slot) * p.E + e) * NFN + fn] = acc;
+        o[c * pl] = acc;
       }
     }
   }
@@ -388,22 +425,26 @@ __device__ __forceinline__ void lift_group(const NskParams& p, const R* __restri
 // unless c_diss is set.
 template <typename R, int D, int NP>
 __device__ __forceinline__ void face_flux(const NskParams& p, const R* __restrict__ Utr, const R* __restrict__ FVtr,
-                                          const long long eL, const long long eR, const int k, const int fn,
+                                          const int eL, const int eR, const int k, const int fn,
                                           R* F, int& eflag) {
   using S = Shape<D, NP>;
   constexpr int NFN = S::NFN, NF = S::NF, NV = S::NV, NW = S::NW;
+  const size_t ps = (size_t)NF * p.nfe;  // distance between the planes of two trace variables
+  const size_t oL = (size_t)(2 * k + 1) * p.nfe + (eL * NFN + fn), oR = (size_t)(2 * k) * p.nfe + (eR * NFN + fn);
+  const R* tL = Utr + oL;
+  const R* tR = Utr + oR;
   R UL[NV], UR[NV], VL[NW], VR[NW];
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
-    UL[v] = Utr[((long long)(v * NF + 2 * k + 1) * p.E + eL) * NFN + fn];
-    UR[v] = Utr[((long long)(v * NF + 2 * k) * p.E + eR) * NFN + fn];
+    UL[v] = tL[v * ps];
+    UR[v] = tR[v * ps];
   }
   R pl, dl, pr, dr, il, ir;
   if constexpr (TraceComps<R>::extra > 0) {
-    il = Utr[((long long)(NV * NF + 2 * k + 1) * p.E + eL) * NFN + fn];
-    ir = Utr[((long long)(NV * NF + 2 * k) * p.E + eR) * NFN + fn];
-    const R ql = Utr[((long long)((NV + 1) * NF + 2 * k + 1) * p.E + eL) * NFN + fn];
-    const R qr = Utr[((long long)((NV + 1) * NF + 2 * k) * p.E + eR) * NFN + fn];
+    il = tL[NV * ps];
+    ir = tR[NV * ps];
+    const R ql = tL[(NV + 1) * ps];
+    const R qr = tR[(NV + 1) * ps];
     Eos<R>::both_q(p, UL[0], ql, pl, dl);
     Eos<R>::both_q(p, UR[0], qr, pr, dr);
   } else {
@@ -414,8 +455,8 @@ __device__ __forceinline__ void face_flux(const NskParams& p, const R* __restric
   }
 #pragma unroll
   for (int c = 0; c < NW; ++c) {
-    VL[c] = FVtr[((long long)(c * NF + 2 * k + 1) * p.E + eL) * NFN + fn];
-    VR[c] = FVtr[((long long)(c * NF + 2 * k) * p.E + eR) * NFN + fn];
+    VL[c] = FVtr[oL + c * ps];
+    VR[c] = FVtr[oR + c * ps];
   }
   eflag |= rho_flags(UL[0]) | rho_flags(UR[0]);
   if (!sound_ok(dl) || !sound_ok(dr)) eflag |= NSK_EBIT_SOUND;
@@ -429,24 +470,35 @@ __device__ __forceinline__ void face_flux(const NskParams& p, const R* __restric
     F[1 + a] = fma(R(0.5), sum, -(R(0.5) * (VL[a] + VR[a])));
   }
   F[D + 1] = -R(0.5) * (VL[D] + VR[D]);
-  const int ndiss = p.c_diss ? NV : NV - 1;
-  for (int v = 0; v < ndiss; ++v) F[v] = fma(-(R(0.5) * lam), UR[v] - UL[v], F[v]);
+  const R hl = -(R(0.5) * lam);
+#pragma unroll
+  for (int v = 0; v < NV - 1; ++v) F[v] = fma(hl, UR[v] - UL[v], F[v]);
+  if (p.c_diss) F[NV - 1] = fma(hl, UR[NV - 1] - UL[NV - 1], F[NV - 1]);
 }
 
-// Fstar[v][k][E][nfn]: the flux on face (e, +k), item idx = (k, e, fn).
+// Fstar[v][k][E][nfn]: the flux on face (e, +k) at face node fn.
+template <typename R, int D, int NP>
+__device__ __forceinline__ void face_at(const NskParams& p, const R* __restrict__ Utr, const R* __restrict__ FVtr,
+                                        R* __restrict__ Fstar, const int k, const int e, const int fn, int& eflag) {
+  using S = Shape<D, NP>;
+  constexpr int NFN = S::NFN, NV = S::NV;
+  R F[NV];
+  face_flux<R, D, NP>(p, Utr, FVtr, e, nbr_of(p, elem_idx<D>(p, e), k, 1), k, fn, F, eflag);
+  R* o = Fstar + (size_t)k * p.nfe + (e * NFN + fn);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) o[(size_t)v * D * p.nfe] = F[v];
+}
+
+// one item of the face pass, idx = (k, e, fn) flattened (idx / nfn < 2^31)
 template <typename R, int D, int NP>
 __device__ __forceinline__ void face_item(const NskParams& p, const R* __restrict__ Utr, const R* __restrict__ FVtr,
                                           R* __restrict__ Fstar, const long long idx, int& eflag) {
   using S = Shape<D, NP>;
-  constexpr int NFN = S::NFN, NV = S::NV;
-  const int fn = (int)(idx % NFN);
-  const long long r = idx / NFN;
-  const long long e = r % p.E;
-  const int k = (int)(r / p.E);
-  R F[NV];
-  face_flux<R, D, NP>(p, Utr, FVtr, e, nbr_elem(p, e, k, 1), k, fn, F, eflag);
-#pragma unroll
-  for (int v = 0; v < NV; ++v) Fstar[((long long)(v * D + k) * p.E + e) * NFN + fn] = F[v];
+  const int fn = (int)(idx % S::NFN);
+  const unsigned r = (unsigned)(idx / S::NFN);
+  const unsigned k = fdiv(r, p.fd_E);
+  const int e = (int)(r - k * (unsigned)p.E);
+  face_at<R, D, NP>(p, Utr, FVtr, Fstar, (int)k, e, fn, eflag);
 }
 
 // shared memory (in units of R) of volume_group
@@ -479,10 +531,10 @@ __device__ __forceinline__ void volume_group(const NskParams& p, R* __restrict__
   R* tb = sfs + G * NF * NV * NFN;     // direction operators
   const auto& t = TabSel<R>::get(p);
   const int le = threadIdx.x / NPE, n = threadIdx.x % NPE;
-  const long long e = e0 + le;
+  const int e = (int)e0 + le;
   const bool valid = le < G && e < p.E;
-  const long long nn = p.E * NPE;
-  const long long g = e * NPE + n;
+  const size_t nn = (size_t)p.nne;  // distance between the planes of two nodal variables
+  const int g = e * NPE + n;
 
   stage_tables<R, D, NP>(t, tb);
   R u[NV], q[NQ];
@@ -517,27 +569,25 @@ __device__ __forceinline__ void volume_group(const NskParams& p, R* __restrict__
       }
       f[(D + 1) * NPE] = -(kb * q[k * NW + D]);
     }
+    const ElemIdx ex = elem_idx<D>(p, e);
     if constexpr (FUSED) {
       for (int it = n; it < NF * NFN; it += NPE) {
         const int slot = it / NFN, fn = it % NFN, k = slot >> 1;
         R F[NV];
         if (slot & 1)
-          face_flux<R, D, NP>(p, Utr, FVtr, e, nbr_elem(p, e, k, 1), k, fn, F, eflag);
+          face_flux<R, D, NP>(p, Utr, FVtr, e, nbr_of(p, ex, k, 1), k, fn, F, eflag);
         else
-          face_flux<R, D, NP>(p, Utr, FVtr, nbr_elem(p, e, k, -1), e, k, fn, F, eflag);
+          face_flux<R, D, NP>(p, Utr, FVtr, nbr_of(p, ex, k, -1), e, k, fn, F, eflag);
 #pragma unroll
         for (int v = 0; v < NV; ++v) sfs[((le * NF + slot) * NV + v) * NFN + fn] = F[v];
       }
     } else {
       // Fstar[v][k][E][nfn] holds the flux on face (e, +k): slot 2k+1 is the element's own
       // entry, slot 2k its -k neighbour's
-      long long eL[D];
-#pragma unroll
-      for (int k = 0; k < D; ++k) eL[k] = nbr_elem(p, e, k, -1);
       for (int it = n; it < NF * NV * NFN; it += NPE) {
         const int fn = it % NFN, v = (it / NFN) % NV, slot = it / (NV * NFN), k = slot >> 1;
-        const long long src = (slot & 1) ? e : eL[k];
-        sfs[((le * NF + slot) * NV + v) * NFN + fn] = Fstar[((long long)(v * D + k) * p.E + src) * NFN + fn];
+        const int src = (slot & 1) ? e : nbr_of(p, ex, k, -1);
+        sfs[((le * NF + slot) * NV + v) * NFN + fn] = Fstar[(size_t)(v * D + k) * p.nfe + (src * NFN + fn)];
       }
     }
   }
@@ -603,10 +653,15 @@ __device__ __forceinline__ void volume_group(const NskParams& p, R* __restrict__
 }
 
 // ---- stand-alone stage kernels ---------------------------------------------
+// grid (ceil(E nfn / 256), 2d): blockIdx.y is the face slot
 template <typename R, int D, int NP>
 __global__ void __launch_bounds__(256) k_prolong(const NskParams p, const R* __restrict__ U, R* __restrict__ Utr) {
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx < p.E * Shape<D, NP>::NF * Shape<D, NP>::NFN) prolong_item<R, D, NP>(p, U, Utr, idx);
+  using S = Shape<D, NP>;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx < p.nfe) {
+    const int e = idx / S::NFN;
+    prolong_trace<R, D, NP>(p, U + (size_t)e * S::NPE, (size_t)p.nne, Utr, e, blockIdx.y, idx % S::NFN);
+  }
 }
 
 template <typename R, int D, int NP, int G>
@@ -619,13 +674,15 @@ __global__ void __launch_bounds__(G * Shape<D, NP>::NPE)
   if (eflag) atomicOr(err, eflag);
 }
 
+// grid (ceil(E nfn / 256), d): blockIdx.y is the face direction
 template <typename R, int D, int NP>
 __global__ void __launch_bounds__(256) k_face(const NskParams p, const R* __restrict__ Utr,
                                               const R* __restrict__ FVtr, R* __restrict__ Fstar,
                                               int* __restrict__ err) {
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  using S = Shape<D, NP>;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   int eflag = 0;
-  if (idx < (long long)D * p.E * Shape<D, NP>::NFN) face_item<R, D, NP>(p, Utr, FVtr, Fstar, idx, eflag);
+  if (idx < p.nfe) face_at<R, D, NP>(p, Utr, FVtr, Fstar, blockIdx.y, idx / S::NFN, idx % S::NFN, eflag);
   if (eflag) atomicOr(err, eflag);
 }
 
@@ -773,8 +830,7 @@ int launch_stage_g(const NskParams& p, const NskBuffers& b, const NskLaunch& l, 
   int nl = 0;
   if (l.ev) cudaEventRecord(l.ev[0], s);
   if (!l.traces_ready) {
-    const long long ptems = p.E * S::NF * S::NFN;
-    k_prolong<R, D, NP><<<grid_for(ptems, 256), 256, 0, s>>>(p, (const R*)b.U, (R*)b.Utr);
+    k_prolong<R, D, NP><<<dim3(grid_for(p.nfe, 256), S::NF), 256, 0, s>>>(p, (const R*)b.U, (R*)b.Utr);
     ++nl;
   }
   if (l.ev) cudaEventRecord(l.ev[1], s);
@@ -784,8 +840,8 @@ int launch_stage_g(const NskParams& p, const NskBuffers& b, const NskLaunch& l, 
   ++nl;
   if (l.mode != NSK_MODE_LIFT) {
     if (!FUSED) {
-      const long long ftems = (long long)D * p.E * S::NFN;
-      k_face<R, D, NP><<<grid_for(ftems, 256), 256, 0, s>>>(p, (const R*)b.Utr, (const R*)b.FVtr, (R*)b.Fstar, b.err);
+      k_face<R, D, NP><<<dim3(grid_for(p.nfe, 256), D), 256, 0, s>>>(p, (const R*)b.Utr, (const R*)b.FVtr,
+                                                                       (R*)b.Fstar, b.err);
       ++nl;
     }
     if (l.ev) cudaEventRecord(l.ev[3], s);
