@@ -186,6 +186,8 @@ void set_eos_constants(NskParams& p) {
   p.pa2f = (float)p.pa2;
   p.dpa1f = (float)p.dpa1;
   spinodal_interval(p.T, &p.spin_lo, &p.spin_hi);
+  p.spin_lof = nextafterf((float)p.spin_lo, 0.0f);
+  p.spin_hif = nextafterf((float)p.spin_hi, 4.0f);
 }
 
 // Carpenter-Kennedy RK4(3)5[2N] (the published rational coefficients).

@@ -79,6 +79,7 @@ struct NskParams {
   double t8, t24, pa2, dpa1;
   float t8f, t24f, pa2f, dpa1f;
   double spin_lo, spin_hi;  // spinodal interval (p' < 0): the FP32 operator evaluates the EoS in FP64 there
+  float spin_lof, spin_hif; // the same bounds rounded outward to FP32
   int c_diss;      // Lax-Friedrichs jump on c as well
   NskTab<double> td;
   NskTab<float> tf;

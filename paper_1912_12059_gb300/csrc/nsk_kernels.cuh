@@ -146,7 +146,7 @@ __device__ __forceinline__ void eos_both64f(const NskParams& p, float rho, doubl
 // Precision policy of the FP32 operator: FP32 EoS, except inside the spinodal interval and
 // wherever p_alpha' cancels (alpha close to alpha_*), where it is evaluated in FP64.
 __device__ __forceinline__ bool eos_needs64(const NskParams& p, float rho) {
-  return rho > (float)p.spin_lo && rho < (float)p.spin_hi;
+  return rho > p.spin_lof && rho < p.spin_hif;
 }
 template <typename R> struct Eos;
 template <> struct Eos<double> {
@@ -537,10 +537,14 @@ __device__ __forceinline__ void volume_group(const NskParams& p, R* __restrict__
   const int g = e * NPE + n;
 
   stage_tables<R, D, NP>(t, tb);
-  R u[NV], q[NQ];
+  R u[NV], q[NQ], kin[NV];
   if (valid) {
 #pragma unroll
     for (int v = 0; v < NV; ++v) u[v] = U[v * nn + g];
+    if (mode != NSK_MODE_RHS) {  // the RK register is needed only at the end: load it early
+#pragma unroll
+      for (int v = 0; v < NV; ++v) kin[v] = K[v * nn + g];
+    }
 #pragma unroll
     for (int c = 0; c < NQ; ++c) q[c] = Q[c * nn + g];
     R inv, pa;
@@ -629,7 +633,7 @@ __device__ __forceinline__ void volume_group(const NskParams& p, R* __restrict__
     } else {
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
-        const R kv = fma(A, K[v * nn + g], dt * res[v]);
+        const R kv = fma(A, kin[v], dt * res[v]);
         K[v * nn + g] = kv;
         u[v] = fma(B, kv, u[v]);
         U[v * nn + g] = u[v];
@@ -664,8 +668,14 @@ __global__ void __launch_bounds__(256) k_prolong(const NskParams p, const R* __r
   }
 }
 
+// FP32 lifting: a full SM of resident threads (the loads of the face loop need the latency hiding)
+template <typename R, int TPB>
+__host__ __device__ constexpr int lift_min_blocks() {
+  return sizeof(R) == 4 ? (2048 / TPB > 0 ? 2048 / TPB : 1) : 1;
+}
+
 template <typename R, int D, int NP, int G>
-__global__ void __launch_bounds__(G * Shape<D, NP>::NPE)
+__global__ void __launch_bounds__(G * Shape<D, NP>::NPE, (lift_min_blocks<R, G * Shape<D, NP>::NPE>()))
     k_lift(const NskParams p, const R* __restrict__ U, const R* __restrict__ Utr, R* __restrict__ Q,
            R* __restrict__ FVtr, int* __restrict__ err) {
   __shared__ R sm[lift_smem<R, D, NP, G>()];
