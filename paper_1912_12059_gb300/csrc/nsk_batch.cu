@@ -2,7 +2,9 @@
 // N = 3 or 4) in one persistent launch per LSRK stage.
 //
 // The four stage phases (trace prolongation, BR1 lifting, face fluxes, volume
-// integral + update) of every instance run inside one cooperative kernel,
+// integral + update) of every instance run inside one cooperative kernel (with the
+// separate face schedule the volume phase writes the next stage's traces, so a
+// step's stages skip the prolongation: one prolongation pass per nsk_batch_step),
 // separated by a grid barrier whose spin is bounded in time: on expiry the
 // kernel sets NSK_EBIT_TIMEOUT and returns instead of waiting forever. Work
 // units (trace items, element groups, face items) of all instances are
@@ -124,7 +126,8 @@ template <typename R, int TPB, bool FUSED>
 __global__ void __launch_bounds__(TPB, batch_min_blocks<R, TPB>())
     k_batch_stage(const BatchInst* __restrict__ inst, const int ninst, const long long tot0, const long long tot1,
                   const long long tot2, const long long tot3, const int mode, const R A, const R B,
-                  unsigned* __restrict__ bar, int* __restrict__ err, const unsigned long long timeout_ns) {
+                  unsigned* __restrict__ bar, int* __restrict__ err, const unsigned long long timeout_ns,
+                  const int traces) {
   constexpr int G4 = nsk::group_for<3, 4>(TPB), G5 = nsk::group_for<3, 5>(TPB);
   extern __shared__ __align__(16) unsigned char smraw[];
   NskParams* sp = (NskParams*)smraw;
@@ -132,7 +135,8 @@ __global__ void __launch_bounds__(TPB, batch_min_blocks<R, TPB>())
   int eflag = 0;
 
   // phase 0: traces of U on every face, one chunk of TPB items of one instance per block iteration
-  {
+  // (skipped when the previous stage's volume phase already wrote them: traces bit 0)
+  if (!(traces & 1)) {
     int i = 0, cur = -1;
     for (long long ci = blockIdx.x; ci < tot0; ci += gridDim.x) {
       while (ci >= inst[i].off[0] + inst[i].cnt[0]) ++i;
@@ -152,7 +156,7 @@ __global__ void __launch_bounds__(TPB, batch_min_blocks<R, TPB>())
       }
     }
   }
-  if (!grid_barrier(bar, err, timeout_ns)) return;
+  if (!(traces & 1) && !grid_barrier(bar, err, timeout_ns)) return;
 
   // phase 1: BR1 lifting, one element group per block iteration
   {
@@ -213,14 +217,17 @@ __global__ void __launch_bounds__(TPB, batch_min_blocks<R, TPB>())
       }
       const BatchInst& b = inst[i];
       const long long loc = gi - b.off[3];
+      // traces bit 1 (separate face schedule only: the volume phase then reads no traces):
+      // write the traces of the updated state in place for the next stage
+      R* tnext = (!FUSED && (traces & 2)) ? (R*)b.Utr : nullptr;
       if (b.np == 4)
         nsk::volume_group<R, 3, 4, G4, FUSED>(*sp, (R*)b.U, (const R*)b.Q, (const R*)b.Fstar, (const R*)b.Utr,
                                               (const R*)b.FVtr, (R*)b.K, (R*)b.Rout, mode, A, B, dt, loc * G4, sm,
-                                              eflag);
+                                              eflag, tnext);
       else
         nsk::volume_group<R, 3, 5, G5, FUSED>(*sp, (R*)b.U, (const R*)b.Q, (const R*)b.Fstar, (const R*)b.Utr,
                                               (const R*)b.FVtr, (R*)b.K, (R*)b.Rout, mode, A, B, dt, loc * G5, sm,
-                                              eflag);
+                                              eflag, tnext);
     }
   }
   if (eflag) atomicOr(err, eflag);
@@ -255,7 +262,7 @@ __global__ void __launch_bounds__(TPB) k_bphase_prolong(const BatchInst* __restr
 }
 
 template <typename R, int TPB>
-__global__ void __launch_bounds__(TPB) k_bphase_lift(const BatchInst* __restrict__ inst,
+__global__ void __launch_bounds__(TPB, (nsk::lift_min_blocks<R, TPB>())) k_bphase_lift(const BatchInst* __restrict__ inst,
                                                      const int* __restrict__ blk2inst, int* __restrict__ err) {
   constexpr int G4 = nsk::group_for<3, 4>(TPB), G5 = nsk::group_for<3, 5>(TPB);
   constexpr int a = nsk::lift_smem<R, 3, 4, G4>(), c = nsk::lift_smem<R, 3, 5, G5>();
@@ -302,7 +309,7 @@ __global__ void __launch_bounds__(TPB) k_bphase_face(const BatchInst* __restrict
 template <typename R, int TPB, bool FUSED>
 __global__ void __launch_bounds__(TPB) k_bphase_volume(const BatchInst* __restrict__ inst,
                                                        const int* __restrict__ blk2inst, const int mode, const R A,
-                                                       const R B, int* __restrict__ err) {
+                                                       const R B, int* __restrict__ err, const int write_traces) {
   constexpr int G4 = nsk::group_for<3, 4>(TPB), G5 = nsk::group_for<3, 5>(TPB);
   constexpr int a = nsk::volume_smem<R, 3, 4, G4, FUSED>(), c = nsk::volume_smem<R, 3, 5, G5, FUSED>();
   __shared__ R sm[a > c ? a : c];
@@ -314,15 +321,16 @@ __global__ void __launch_bounds__(TPB) k_bphase_volume(const BatchInst* __restri
   const BatchInst& b = inst[i];
   const long long loc = (long long)blockIdx.x - b.off[3];
   const R dt = b.dt ? (R)*b.dt : R(0);
+  R* tnext = (!FUSED && write_traces) ? (R*)b.Utr : nullptr;
   int eflag = 0;
   if (b.np == 4)
     nsk::volume_group<R, 3, 4, G4, FUSED>(*sp, (R*)b.U, (const R*)b.Q, (const R*)b.Fstar, (const R*)b.Utr,
                                           (const R*)b.FVtr, (R*)b.K, (R*)b.Rout, mode, A, B, dt, loc * G4, sm,
-                                          eflag);
+                                          eflag, tnext);
   else
     nsk::volume_group<R, 3, 5, G5, FUSED>(*sp, (R*)b.U, (const R*)b.Q, (const R*)b.Fstar, (const R*)b.Utr,
                                           (const R*)b.FVtr, (R*)b.K, (R*)b.Rout, mode, A, B, dt, loc * G5, sm,
-                                          eflag);
+                                          eflag, tnext);
   if (eflag) atomicOr(err, eflag);
 }
 
@@ -356,7 +364,7 @@ int prepare_batch_t(nsk_batch* bt) {
 }
 
 template <typename R, int TPB, bool FUSED>
-int launch_batch_t(nsk_batch* bt, int mode, double A, double B) {
+int launch_batch_t(nsk_batch* bt, int mode, double A, double B, int traces) {
   auto kern = k_batch_stage<R, TPB, FUSED>;
   constexpr int smem = batch_smem_bytes<R, TPB, FUSED>();
   const int ti = TPB == 128 ? 0 : 1;
@@ -375,51 +383,75 @@ int launch_batch_t(nsk_batch* bt, int mode, double A, double B) {
   cfg.numAttrs = 1;
   const BatchInst* d_inst = bt->d_inst + (size_t)ti * bt->n;
   if (cudaLaunchKernelEx(&cfg, kern, d_inst, bt->n, tot[0], tot[1], tot[2], tot[3], mode, (R)A, (R)B, bt->d_bar,
-                         bt->d_err, bt->timeout_ns) != cudaSuccess)
+                         bt->d_err, bt->timeout_ns, traces) != cudaSuccess)
     return NSK_ERR_CUDA;
   bt->launches += 1;
   return NSK_OK;
 }
 
+// traces: bit 0 = the face traces of U are current (no prolongation phase), bit 1 = the volume
+// phase writes the traces of its output state (separate face schedule only)
 template <typename R, int TPB, bool FUSED>
-int launch_phases_t(nsk_batch* bt, int mode, double A, double B) {
+int launch_phases_t(nsk_batch* bt, int mode, double A, double B, int traces) {
   const int ti = TPB == 128 ? 0 : 1;
   const long long* tot = bt->ptot[ti];
   const BatchInst* d_inst = bt->d_pinst + (size_t)ti * bt->n;
   const int* const* map = bt->d_blk2inst[ti];
   cudaStream_t s = bt->stream;
-  k_bphase_prolong<R, TPB><<<(unsigned)tot[0], TPB, 0, s>>>(d_inst, map[0]);
+  int nl = 0;
+  if (!(traces & 1)) {
+    k_bphase_prolong<R, TPB><<<(unsigned)tot[0], TPB, 0, s>>>(d_inst, map[0]);
+    ++nl;
+  }
   k_bphase_lift<R, TPB><<<(unsigned)tot[1], TPB, 0, s>>>(d_inst, map[1], bt->d_err);
-  int nl = 2;
+  ++nl;
   if (!FUSED) {
     k_bphase_face<R, TPB><<<(unsigned)tot[2], TPB, 0, s>>>(d_inst, map[2], bt->d_err);
     ++nl;
   }
-  k_bphase_volume<R, TPB, FUSED><<<(unsigned)tot[3], TPB, 0, s>>>(d_inst, map[3], mode, (R)A, (R)B, bt->d_err);
+  k_bphase_volume<R, TPB, FUSED><<<(unsigned)tot[3], TPB, 0, s>>>(d_inst, map[3], mode, (R)A, (R)B, bt->d_err,
+                                                                  (traces >> 1) & 1);
   ++nl;
   if (cudaGetLastError() != cudaSuccess) return NSK_ERR_CUDA;
   bt->launches += nl;
   return NSK_OK;
 }
 
-int launch_phases(nsk_batch* bt, int mode, double A, double B, int tpb, int fused) {
-  const bool f32 = bt->precision == NSK_FP32_MIXED;
-  if (tpb == 128) {
-    if (f32) return fused ? launch_phases_t<float, 128, true>(bt, mode, A, B) : launch_phases_t<float, 128, false>(bt, mode, A, B);
-    return fused ? launch_phases_t<double, 128, true>(bt, mode, A, B) : launch_phases_t<double, 128, false>(bt, mode, A, B);
-  }
-  if (f32) return fused ? launch_phases_t<float, 256, true>(bt, mode, A, B) : launch_phases_t<float, 256, false>(bt, mode, A, B);
-  return fused ? launch_phases_t<double, 256, true>(bt, mode, A, B) : launch_phases_t<double, 256, false>(bt, mode, A, B);
+// the prolongation phase alone (per-phase kernel), for all instances
+template <typename R, int TPB>
+int launch_prolong_t(nsk_batch* bt) {
+  const int ti = TPB == 128 ? 0 : 1;
+  k_bphase_prolong<R, TPB><<<(unsigned)bt->ptot[ti][0], TPB, 0, bt->stream>>>(bt->d_pinst + (size_t)ti * bt->n,
+                                                                               bt->d_blk2inst[ti][0]);
+  if (cudaGetLastError() != cudaSuccess) return NSK_ERR_CUDA;
+  bt->launches += 1;
+  return NSK_OK;
 }
 
-int launch_persistent(nsk_batch* bt, int mode, double A, double B, int tpb, int fused) {
+int launch_prolong(nsk_batch* bt, int tpb) {
+  const bool f32 = bt->precision == NSK_FP32_MIXED;
+  if (tpb == 128) return f32 ? launch_prolong_t<float, 128>(bt) : launch_prolong_t<double, 128>(bt);
+  return f32 ? launch_prolong_t<float, 256>(bt) : launch_prolong_t<double, 256>(bt);
+}
+
+int launch_phases(nsk_batch* bt, int mode, double A, double B, int tpb, int fused, int tr) {
   const bool f32 = bt->precision == NSK_FP32_MIXED;
   if (tpb == 128) {
-    if (f32) return fused ? launch_batch_t<float, 128, true>(bt, mode, A, B) : launch_batch_t<float, 128, false>(bt, mode, A, B);
-    return fused ? launch_batch_t<double, 128, true>(bt, mode, A, B) : launch_batch_t<double, 128, false>(bt, mode, A, B);
+    if (f32) return fused ? launch_phases_t<float, 128, true>(bt, mode, A, B, tr) : launch_phases_t<float, 128, false>(bt, mode, A, B, tr);
+    return fused ? launch_phases_t<double, 128, true>(bt, mode, A, B, tr) : launch_phases_t<double, 128, false>(bt, mode, A, B, tr);
   }
-  if (f32) return fused ? launch_batch_t<float, 256, true>(bt, mode, A, B) : launch_batch_t<float, 256, false>(bt, mode, A, B);
-  return fused ? launch_batch_t<double, 256, true>(bt, mode, A, B) : launch_batch_t<double, 256, false>(bt, mode, A, B);
+  if (f32) return fused ? launch_phases_t<float, 256, true>(bt, mode, A, B, tr) : launch_phases_t<float, 256, false>(bt, mode, A, B, tr);
+  return fused ? launch_phases_t<double, 256, true>(bt, mode, A, B, tr) : launch_phases_t<double, 256, false>(bt, mode, A, B, tr);
+}
+
+int launch_persistent(nsk_batch* bt, int mode, double A, double B, int tpb, int fused, int tr) {
+  const bool f32 = bt->precision == NSK_FP32_MIXED;
+  if (tpb == 128) {
+    if (f32) return fused ? launch_batch_t<float, 128, true>(bt, mode, A, B, tr) : launch_batch_t<float, 128, false>(bt, mode, A, B, tr);
+    return fused ? launch_batch_t<double, 128, true>(bt, mode, A, B, tr) : launch_batch_t<double, 128, false>(bt, mode, A, B, tr);
+  }
+  if (f32) return fused ? launch_batch_t<float, 256, true>(bt, mode, A, B, tr) : launch_batch_t<float, 256, false>(bt, mode, A, B, tr);
+  return fused ? launch_batch_t<double, 256, true>(bt, mode, A, B, tr) : launch_batch_t<double, 256, false>(bt, mode, A, B, tr);
 }
 
 int prepare_batch(nsk_batch* bt) {
@@ -437,9 +469,15 @@ int prepare_batch(nsk_batch* bt) {
 }
 
 // one stage of the whole batch under a schedule (persistent: one cooperative launch)
-int launch_batch(nsk_batch* bt, int mode, double A, double B, int tpb, int fused, int persistent) {
-  return persistent ? launch_persistent(bt, mode, A, B, tpb, fused) : launch_phases(bt, mode, A, B, tpb, fused);
+int launch_batch(nsk_batch* bt, int mode, double A, double B, int tpb, int fused, int persistent, int traces) {
+  if (fused) traces = 0;  // the fused volume phase reads the traces: they are prolonged every stage
+  return persistent ? launch_persistent(bt, mode, A, B, tpb, fused, traces)
+                    : launch_phases(bt, mode, A, B, tpb, fused, traces);
 }
+
+// trace flags of every stage of a step under the separate face schedule: traces come from the
+// previous stage's volume phase (the step starts from traces prolonged before the first step)
+int step_traces(int fused) { return fused ? 0 : 3; }
 
 int read_error(nsk_batch* bt) {
   int h = 0;
@@ -598,10 +636,13 @@ int nsk_batch_autotune(nsk_batch* bt, int* tpb_out, int* fused_out, int* persist
   for (int per = 0; per < 2 && st == NSK_OK; ++per)
     for (int ti = 0; ti < 2 && st == NSK_OK; ++ti)
       for (int f = 0; f < 2 && st == NSK_OK; ++f) {
-        st = launch_batch(bt, NSK_MODE_RHS, 0.0, 0.0, tpbs[ti], f, per);  // warm-up (residual: state untouched)
+        // warm-up with a prolongation pass (residual: state untouched), then time the stage as a
+        // step runs it (rewriting the traces of the unchanged state leaves them as they are)
+        st = launch_batch(bt, NSK_MODE_RHS, 0.0, 0.0, tpbs[ti], f, per, 0);
         if (st) break;
         cudaEventRecord(e0, bt->stream);
-        for (int r = 0; r < 3 && st == NSK_OK; ++r) st = launch_batch(bt, NSK_MODE_RHS, 0.0, 0.0, tpbs[ti], f, per);
+        for (int r = 0; r < 3 && st == NSK_OK; ++r)
+          st = launch_batch(bt, NSK_MODE_RHS, 0.0, 0.0, tpbs[ti], f, per, step_traces(f));
         cudaEventRecord(e1, bt->stream);
         if (cudaEventSynchronize(e1) != cudaSuccess) st = NSK_ERR_CUDA;
         float ms = 0.f;
@@ -647,7 +688,7 @@ int nsk_batch_step(nsk_batch* bt, int nsteps, double cfl, double* step_ms) {
       }
     const long long l0 = bt->launches;
     for (int s = 0; s < 5 && st == NSK_OK; ++s)
-      st = launch_batch(bt, NSK_MODE_LSRK, kA[s], kB[s], bt->tpb, bt->fused, bt->persistent);
+      st = launch_batch(bt, NSK_MODE_LSRK, kA[s], kB[s], bt->tpb, bt->fused, bt->persistent, step_traces(bt->fused));
     bt->graph_launches = bt->launches - l0;
     bt->launches = l0;  // counted per replay below
     const cudaError_t ce = cudaStreamEndCapture(bt->stream, &g);
@@ -667,6 +708,10 @@ int nsk_batch_step(nsk_batch* bt, int nsteps, double cfl, double* step_ms) {
     bt->graph_persistent = bt->persistent;
     bt->graph_cfl = cfl;
   }
+  if (nsteps > 0 && !bt->fused) {  // the traces of the current states, for the first stage
+    const int r = launch_prolong(bt, bt->tpb);
+    if (r) return r;
+  }
   std::vector<cudaEvent_t> ev;
   if (step_ms) {
     ev.resize(nsteps + 1);
@@ -682,7 +727,8 @@ int nsk_batch_step(nsk_batch* bt, int nsteps, double cfl, double* step_ms) {
           if (r < 0) return r;
         }
       for (int st = 0; st < 5; ++st) {
-        const int r = launch_batch(bt, NSK_MODE_LSRK, kA[st], kB[st], bt->tpb, bt->fused, bt->persistent);
+        const int r = launch_batch(bt, NSK_MODE_LSRK, kA[st], kB[st], bt->tpb, bt->fused, bt->persistent,
+                                   step_traces(bt->fused));
         if (r) return r;
       }
       if (dtmode) bt->launches += 2 * bt->n;

@@ -134,12 +134,18 @@ def test_batch_autotune_graph_and_launch_count(gpu):
     b = nsk.Batch([s for s, _ in inst])
     tpb, fused, persistent, ms = b.autotune()
     assert tpb in (128, 256) and ms > 0 and b.get_schedule() == (tpb, fused, persistent)
-    for persistent, per_stage in ((True, 1), (False, 4)):
+    # separate face schedule: one prolongation launch per call, then per stage the persistent
+    # kernel, or lifting, face and volume launches (the volume phase writes the next traces)
+    for persistent, per_stage in ((True, 1), (False, 3)):
         b.set_schedule(256, False, persistent)
         n0 = b.launch_count
         b.step(2)
         assert b.uses_graph
-        assert b.launch_count - n0 == 2 * 5 * per_stage
+        assert b.launch_count - n0 == 1 + 2 * 5 * per_stage
+    b.set_schedule(256, True, False)  # fused face flux: prolongation, lifting, volume per stage
+    n0 = b.launch_count
+    b.step(2)
+    assert b.launch_count - n0 == 2 * 5 * 3
     b.close()
     for s, _ in inst:
         s.close()
