@@ -549,14 +549,13 @@ int nsk_step(nsk_ctx* c, double dt, int nsteps) {
     }
     const bool learned = c->closure_mode == NSK_C_LEARNED;
     for (int st = 0; st < 5; ++st) {
-      if (learned) {  // the closure rewrites c before every stage: its traces are prolonged anew
-        const int r = nsk_closure_apply_ctx(c);
+      if (learned) {  // the closure rewrites c before every stage, and the c traces with it
+        const int r = nsk_closure_apply_ctx(c, ready ? c->b.Utr : nullptr);
         if (r) return r;
-        ready = false;
       }
       NskLaunch l = {NSK_MODE_LSRK, nullptr, kA[st], kB[st], adaptive ? c->b.dt : nullptr, dt, nullptr, c->tpb, c->fused_face};
       // the volume kernel writes the traces of the updated state for the next stage of this call
-      const bool write = !learned && !(s == nsteps - 1 && st == 4);
+      const bool write = !(s == nsteps - 1 && st == 4);
       l.traces_ready = ready;
       l.utr_next = write ? (c->fused_face ? c->utr_alt : c->b.Utr) : nullptr;
       int r = launch_stage(c, l);
@@ -566,14 +565,15 @@ int nsk_step(nsk_ctx* c, double dt, int nsteps) {
     }
     if (learned && c->judge_every > 0 && ++c->steps_since_judge >= c->judge_every) {
       c->steps_since_judge = 0;
-      int r = nsk_closure_apply_ctx(c);  // judge the closure's c of the current state
+      int r = nsk_closure_apply_ctx(c, nullptr);  // judge the closure's c of the current state
       if (r) return r;
       r = nsk_closure_judge_ctx(c);
       if (r) return r;
+      ready = false;
     }
   }
   if (c->closure_mode == NSK_C_LEARNED) {  // the stored state carries the closure's c
-    const int r = nsk_closure_apply_ctx(c);
+    const int r = nsk_closure_apply_ctx(c, nullptr);
     if (r) return r;
   }
   return sync_and_check(c);

@@ -518,7 +518,70 @@ int closure_features(nsk_ctx* c, void* X) {
 
 }  // namespace
 
-int nsk_closure_apply_ctx(nsk_ctx* c) {
+// c := rho + s y at the nodes of G elements per block, and the traces of the new c on the
+// element's faces (the c component of Utr; same arithmetic as the prolongation, so the other
+// trace components written by the previous stage stay consistent with it)
+template <typename R, int D, int NP, int G>
+__global__ void __launch_bounds__(G * nsk::Shape<D, NP>::NPE)
+    k_closure_apply_tr(const NskParams p, R* __restrict__ U, const float* __restrict__ Y, const float s,
+                       R* __restrict__ Utr) {
+  using S = nsk::Shape<D, NP>;
+  constexpr int NPE = S::NPE, NFN = S::NFN, NF = S::NF;
+  __shared__ R sc[G * NPE];
+  const int le = threadIdx.x / NPE, n = threadIdx.x % NPE;
+  const int e = blockIdx.x * G + le;
+  const bool valid = le < G && e < p.E;
+  const size_t nn = (size_t)p.nne;
+  const int g = e * NPE + n;
+  if (valid) {
+    const R cv = U[g] + (R)(s * Y[g]);
+    U[(D + 1) * nn + g] = cv;
+    sc[le * NPE + n] = cv;
+  }
+  __syncthreads();
+  if (valid) {
+    const auto& t = TabSel<R>::get(p);
+    R* o = Utr + (size_t)(D + 1) * NF * p.nfe + (e * NFN);
+    for (int it = n; it < NF * NFN; it += NPE) {
+      const int slot = it / NFN, fn = it % NFN, k = slot >> 1;
+      const R* L = (slot & 1) ? t.lp : t.lm;
+      const int n0 = nsk::line_base<D, NP>(fn, k), st = nsk::node_stride<NP>(k);
+      R acc = 0;
+#pragma unroll
+      for (int j = 0; j < NP; ++j) acc = fma(L[j], sc[le * NPE + n0 + j * st], acc);
+      o[(size_t)slot * p.nfe + fn] = acc;
+    }
+  }
+}
+
+template <typename R, int D, int NP>
+int launch_apply_tr(const nsk_ctx* c, float s, void* utr) {
+  constexpr int G = nsk::group_for<D, NP>(256);
+  k_closure_apply_tr<R, D, NP, G><<<(unsigned)((c->E + G - 1) / G), G * nsk::Shape<D, NP>::NPE, 0, c->stream>>>(
+      c->p, (R*)c->b.U, c->cl_Y, s, (R*)utr);
+  return cudaGetLastError() == cudaSuccess ? NSK_OK : NSK_ERR_CUDA;
+}
+
+template <typename R, int D>
+int launch_apply_tr_np(const nsk_ctx* c, float s, void* utr) {
+  switch (c->np) {
+    case 2: return launch_apply_tr<R, D, 2>(c, s, utr);
+    case 3: return launch_apply_tr<R, D, 3>(c, s, utr);
+    case 4: return launch_apply_tr<R, D, 4>(c, s, utr);
+    case 5: return launch_apply_tr<R, D, 5>(c, s, utr);
+    case 6: return launch_apply_tr<R, D, 6>(c, s, utr);
+    default: return NSK_ERR_ARG;
+  }
+}
+
+template <typename R>
+int launch_apply_tr_d(const nsk_ctx* c, float s, void* utr) {
+  if (c->dim == 1) return launch_apply_tr_np<R, 1>(c, s, utr);
+  if (c->dim == 2) return launch_apply_tr_np<R, 2>(c, s, utr);
+  return launch_apply_tr_np<R, 3>(c, s, utr);
+}
+
+int nsk_closure_apply_ctx(nsk_ctx* c, void* utr) {
   if (!c->mlp || !c->cl_X || !c->cl_Y) return NSK_ERR_STATE;
   int st = closure_features(c, c->cl_X);
   if (st) return st;
@@ -526,12 +589,17 @@ int nsk_closure_apply_ctx(nsk_ctx* c) {
   if (st) return st;
   c->launches += 3;
   const float s = (float)closure_scale(c);
-  if (c->precision == NSK_FP32_MIXED)
-    k_closure_apply<float><<<nb(c->nn), 256, 0, c->stream>>>(c->nn, c->dim, (float*)c->b.U, c->cl_Y, s);
-  else
-    k_closure_apply<double><<<nb(c->nn), 256, 0, c->stream>>>(c->nn, c->dim, (double*)c->b.U, c->cl_Y, s);
+  if (utr) {
+    st = c->precision == NSK_FP32_MIXED ? launch_apply_tr_d<float>(c, s, utr) : launch_apply_tr_d<double>(c, s, utr);
+  } else {
+    if (c->precision == NSK_FP32_MIXED)
+      k_closure_apply<float><<<nb(c->nn), 256, 0, c->stream>>>(c->nn, c->dim, (float*)c->b.U, c->cl_Y, s);
+    else
+      k_closure_apply<double><<<nb(c->nn), 256, 0, c->stream>>>(c->nn, c->dim, (double*)c->b.U, c->cl_Y, s);
+    st = cudaGetLastError() == cudaSuccess ? NSK_OK : NSK_ERR_CUDA;
+  }
   c->launches += 1;
-  return cudaGetLastError() == cudaSuccess ? NSK_OK : NSK_ERR_CUDA;
+  return st;
 }
 
 int nsk_closure_judge_ctx(nsk_ctx* c) {
@@ -623,7 +691,7 @@ int nsk_closure_targets(nsk_ctx* c, float* Y) {
 int nsk_closure_apply(nsk_ctx* c) {
   if (!c) return NSK_ERR_ARG;
   if (!c->state_set || c->closure_mode != NSK_C_LEARNED) return NSK_ERR_STATE;
-  const int st = nsk_closure_apply_ctx(c);
+  const int st = nsk_closure_apply_ctx(c, nullptr);
   if (st) return st;
   return cudaStreamSynchronize(c->stream) == cudaSuccess ? NSK_OK : NSK_ERR_CUDA;
 }
