@@ -75,6 +75,17 @@ def kernel_cost(kernel, d, n, fp_bytes, traces=0.0):
     raise KeyError(kernel)
 
 
+def pick_schedule(s, fixed):
+    """The autotuner's stage schedule, or a fixed "TPB,FUSED" one (profiling runs: under a
+    profiler the autotuner's timings are serialised and would pick another schedule)."""
+    if fixed:
+        tpb, fused = (int(v) for v in fixed.split(","))
+        s.set_schedule(tpb, bool(fused))
+        return tpb, bool(fused)
+    tpb, fused, _ = s.autotune()
+    return tpb, fused
+
+
 def trace_fraction(prof):
     """Share of the k_volume launches that wrote the next stage's traces: every nsk_step call
     prolongs once at its start and skips the trace store in its last stage."""
@@ -219,7 +230,7 @@ def run_gpu(args, wl, rank, world):
     x = s.node_coords()
     U0 = wl.initial_state(x)
     s.set_state(U0)
-    tpb, fused, _ = s.autotune()  # setup: pick the fastest stage schedule for this mesh
+    tpb, fused = pick_schedule(s, args.schedule)  # setup: the fastest stage schedule for this mesh
     dt = s.compute_dt(wl.cfl)
     nodes = s.E * s.npe
 
@@ -451,7 +462,7 @@ def measure_fp32_variant(args, wl, stream, U0, U64_after, dt, peaks):
                    nsk.NSK_FP32_MIXED, stream=stream.cuda_stream)
     s.set_params(T=wl.T, kappa=wl.kappa, alpha=wl.alpha, beta=wl.beta, mu=wl.mu)
     s.set_state(U0)
-    tpb, fused, _ = s.autotune()
+    tpb, fused = pick_schedule(s, args.schedule32)
     s.step(dt, args.warmup)
     s.set_profiling(True)
     s.get_profile(reset=True)
@@ -681,6 +692,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nelem", type=int, default=0, help="override elements per direction (profiling runs)")
+    ap.add_argument("--schedule", default="", help='fixed stage schedule "TPB,FUSED" instead of the autotuner')
+    ap.add_argument("--schedule32", default="", help='the same for the FP32 variant')
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
