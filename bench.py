@@ -37,6 +37,10 @@ sys.path.insert(0, str(ROOT))
 MEASURED_PEAKS = ROOT / "MEASURED_PEAKS.json"
 # FP64 FMA pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (max SM clock)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# DRAM bytes (read + write) per launch of the dominant kernels at 64^3 elements, N = 3, from one
+# ncu capture at 40^3 elements scaled by the element count (profiles/launches_fp64_collision3d_64cubed.md,
+# profiles/fp32_stage_kernels_collision3d.md); must be re-measured whenever those kernels change
+MEASURED_TRAFFIC = {("k_volume", 8, 262144): 4.69e9, ("k_volume", 4, 262144): 2.70e9}
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
@@ -298,14 +302,14 @@ def run_gpu(args, wl, rank, world):
     if prec == nsk.NSK_FP64:
         achieved = flops_e * s.E / (avg_ms / 1e3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None, "kernel": name,
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": MEASURED_TRAFFIC.get((name, 8, s.E)), "kernel": name,
                 "peak_source": "FP64 FMA pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
                 "algorithmic_per_launch": flops_e * s.E}
     else:
         hbm = float(peaks.get("hbm_gbs", 6800.0))
         achieved = bytes_e * s.E / (avg_ms / 1e3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": None, "kernel": name,
+                "traffic": MEASURED_TRAFFIC.get((name, 4, s.E)), "kernel": name,
                 "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
                 "algorithmic_per_launch": bytes_e * s.E}
     kernels = {k: {"avg_ms": v[0] / max(v[1], 1), "launches": v[1],
@@ -486,7 +490,8 @@ def measure_fp32_variant(args, wl, stream, U0, U64_after, dt, peaks):
             "dtype": "f32", "density_l2_rel_err_vs_fp64": err, "steps_compared": args.warmup + args.steps,
             "schedule": {"tpb": tpb, "fused_face": fused},
             "roofline": {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm, "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"},
+                         "frac": achieved / hbm, "traffic": MEASURED_TRAFFIC.get((name, 4, wl.n_elem)),
+                         "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"},
             "kernels": {k: {"avg_ms": v[0] / max(v[1], 1), "launches": v[1]} for k, v in prof.items()}}
 
 
