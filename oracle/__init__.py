@@ -22,6 +22,8 @@ LIB = HERE / "libnsk_oracle.so"
 
 NODES_GAUSS = 0
 NODES_LOBATTO = 1
+FLUX_LF = 0    # local Lax-Friedrichs
+FLUX_HLLC = 1  # HLLC (barotropic, modified pressure)
 
 
 class OrcSetup(C.Structure):
@@ -38,6 +40,7 @@ class OrcSetup(C.Structure):
         ("beta", C.c_double),
         ("mu", C.c_double),
         ("c_dissipation", C.c_int),
+        ("flux", C.c_int),
     ]
 
 
@@ -77,6 +80,7 @@ def lib():
         L.orc_lsrk4_coeffs.restype = None
         L.orc_lift.argtypes = [sp, dp, dp]
         L.orc_rhs.argtypes = [sp, dp, dp]
+        L.orc_numflux.argtypes = [sp, C.c_int, dp, dp, dp]
         L.orc_lsrk4.argtypes = [sp, dp, C.c_double, C.c_int]
         L.orc_timestep.argtypes = [sp, dp, C.c_double, dp]
         L.orc_diagnostics.argtypes = [sp, dp, dp, dp, dp]
@@ -162,7 +166,7 @@ class Oracle:
     [nvar][E][npe] (variables rho, rho v_1..rho v_dim, c)."""
 
     def __init__(self, dim, nelem, lo, hi, N, node_type=NODES_GAUSS, T=0.85, kappa=1e-4, alpha=1e3,
-                 beta=1e-3, mu=1e-3, c_dissipation=0):
+                 beta=1e-3, mu=1e-3, c_dissipation=0, flux=FLUX_LF):
         s = OrcSetup()
         s.dim = dim
         ne = list(nelem) + [1] * (3 - len(nelem))
@@ -176,6 +180,7 @@ class Oracle:
         s.node_type = node_type
         s.T, s.kappa, s.alpha, s.beta, s.mu = T, kappa, alpha, beta, mu
         s.c_dissipation = c_dissipation
+        s.flux = flux
         self.s = s
         self.dim = dim
         self.N = N
@@ -220,6 +225,14 @@ class Oracle:
         R = np.zeros_like(U)
         _check(lib().orc_rhs(C.byref(self.s), _ptr(U), _ptr(R)), "orc_rhs")
         return R
+
+    def numflux(self, k, UL, UR):
+        """Convective numerical flux (LF or HLLC per the setup) of one face with normal +e_k."""
+        UL = np.ascontiguousarray(UL, dtype=np.float64)
+        UR = np.ascontiguousarray(UR, dtype=np.float64)
+        F = np.zeros(self.nvar)
+        _check(lib().orc_numflux(C.byref(self.s), k, _ptr(UL), _ptr(UR), _ptr(F)), "orc_numflux")
+        return F
 
     def step(self, U, dt, nsteps):
         U = np.array(U, dtype=np.float64, order="C", copy=True)

@@ -369,6 +369,68 @@ static void visc_flux(const orc_setup* s, int d, int k, const double* Q, double*
   f[d + 1] = s->kappa / s->beta * Q[k * (d + 1) + d];
 }
 
+/* Convective numerical flux of one face, normal +e_k, left state UL, right state UR.
+ *
+ * Local Lax-Friedrichs (Sec. 3.1 names LF and HLLC): the central flux minus half the largest
+ * |lambda| of Eq. (parabolic_eigenvalues_model2) times the jump, on rho and momentum (on c
+ * too when c_dissipation is set; c has no convective flux).
+ *
+ * HLLC (Sec. 3.1 refers to Toro's textbook for it): the three-wave solver applied to the
+ * barotropic system (rho, m) with the modified pressure p_alpha. Outer wave speeds after
+ * Davis, S_L = min(u_L - a_L, u_R - a_R), S_R = max(u_L + a_L, u_R + a_R), a = sqrt(p_alpha'),
+ * u the normal velocity; contact speed
+ *   S* = (p_R - p_L + rho_L u_L (S_L - u_L) - rho_R u_R (S_R - u_R)) / (rho_L (S_L - u_L) - rho_R (S_R - u_R));
+ * star states U*_K = rho_K (S_K - u_K)/(S_K - S*) (1, v with its normal component replaced by S*);
+ * flux F_L if S_L >= 0, F_R if S_R <= 0, else F_K + S_K (U*_K - U_K) with K = L for S* >= 0 and
+ * K = R otherwise. c is not transported: its convective numerical flux is zero. */
+static void numflux(const orc_setup* s, int d, int k, const double* UL, const double* UR, double* F) {
+  double fL[5], fR[5];
+  conv_flux(s, d, k, UL, fL);
+  conv_flux(s, d, k, UR, fR);
+  const int nv = d + 2;
+  const double aL = sound_speed(s, UL[0]), aR = sound_speed(s, UR[0]);
+  const double uL = UL[1 + k] / UL[0], uR = UR[1 + k] / UR[0];
+  if (s->flux == 1) {
+    const double SL = fmin(uL - aL, uR - aR), SR = fmax(uL + aL, uR + aR);
+    if (SL >= 0.0) {
+      for (int v = 0; v < nv; ++v) F[v] = fL[v];
+    } else if (SR <= 0.0) {
+      for (int v = 0; v < nv; ++v) F[v] = fR[v];
+    } else {
+      const double pL = p_alpha(s, UL[0]), pR = p_alpha(s, UR[0]);
+      const double Ss = (pR - pL + UL[0] * uL * (SL - uL) - UR[0] * uR * (SR - uR)) /
+                        (UL[0] * (SL - uL) - UR[0] * (SR - uR));
+      const int left = Ss >= 0.0;
+      const double* UK = left ? UL : UR;
+      const double* fK = left ? fL : fR;
+      const double SK = left ? SL : SR, uK = left ? uL : uR;
+      const double coef = UK[0] * (SK - uK) / (SK - Ss);
+      double Us[5];
+      Us[0] = coef;
+      for (int a = 0; a < d; ++a) Us[1 + a] = coef * (a == k ? Ss : UK[1 + a] / UK[0]);
+      Us[d + 1] = UK[d + 1];
+      for (int v = 0; v < nv; ++v) F[v] = fK[v] + SK * (Us[v] - UK[v]);
+    }
+    F[d + 1] = 0.0;
+    return;
+  }
+  const double lamL = fabs(uL) + aL, lamR = fabs(uR) + aR;
+  const double lam = lamL > lamR ? lamL : lamR;
+  for (int v = 0; v < nv; ++v) {
+    F[v] = 0.5 * (fL[v] + fR[v]);
+    if (v < d + 1 || s->c_dissipation) F[v] -= 0.5 * lam * (UR[v] - UL[v]);
+  }
+}
+
+int orc_numflux(const orc_setup* s, int k, const double* UL, const double* UR, double* F) {
+  if (!s || k < 0 || k >= s->dim || !UL || !UR || !F) return ORC_ERR_ARG;
+  if (!admissible(UL[0]) || !admissible(UR[0])) return ORC_ERR_NONPHYSICAL;
+  numflux(s, s->dim, k, UL, UR, F);
+  for (int v = 0; v < s->dim + 2; ++v)
+    if (!isfinite(F[v])) return ORC_ERR_NONPHYSICAL;
+  return ORC_OK;
+}
+
 /* ------------------------------------------------------------------------ */
 /* BR1 lifting, Sec. 3.1: Q - (1/J) div_xi (J a^k w) = 0 in weak form with the */
 /* central flux w* = (w^- + w^+)/2, w = primitive variables (v, c).           */
@@ -504,22 +566,13 @@ static int residual(const orc_setup* s, const mesh_t* m, const double* U, double
           status = ORC_ERR_NONPHYSICAL;
           continue;
         }
-        double fcL[5], fcR[5], fvL[5], fvR[5], Fs[5];
-        conv_flux(s, d, k, UL, fcL);
-        conv_flux(s, d, k, UR, fcR);
+        double fvL[5], fvR[5], Fs[5];
         visc_flux(s, d, k, QL, fvL);
         visc_flux(s, d, k, QR, fvR);
-        /* local Lax-Friedrichs: largest |lambda| of Eq. (parabolic_eigenvalues_model2) */
-        double aL = sound_speed(s, UL[0]), aR = sound_speed(s, UR[0]);
-        if (!isfinite(aL) || !isfinite(aR)) status = ORC_ERR_NONPHYSICAL;
-        double lamL = fabs(UL[1 + k] / UL[0]) + aL;
-        double lamR = fabs(UR[1 + k] / UR[0]) + aR;
-        double lam = lamL > lamR ? lamL : lamR;
-        for (int v = 0; v < nv; ++v) {
-          Fs[v] = 0.5 * (fcL[v] + fcR[v]) - 0.5 * (fvL[v] + fvR[v]);
-          int dissipative = (v < d + 1) || s->c_dissipation;
-          if (dissipative) Fs[v] -= 0.5 * lam * (UR[v] - UL[v]);
-        }
+        if (!isfinite(sound_speed(s, UL[0])) || !isfinite(sound_speed(s, UR[0]))) status = ORC_ERR_NONPHYSICAL;
+        /* convective numerical flux (LF or HLLC) minus the BR1 mean of the viscous fluxes */
+        numflux(s, d, k, UL, UR, Fs);
+        for (int v = 0; v < nv; ++v) Fs[v] -= 0.5 * (fvL[v] + fvR[v]);
         for (int i = 0; i < np; ++i) {
           const int node = n0 + i * m->sn[k];
           for (int v = 0; v < nv; ++v) {

@@ -42,6 +42,7 @@ typedef struct {
   double beta;        /* parabolic relaxation parameter */
   double mu;          /* viscosity eps = 1/Re */
   int c_dissipation;  /* 0: Lax-Friedrichs jump acts on rho and momentum only; 1: on c too */
+  int flux;           /* convective numerical flux: 0 = local Lax-Friedrichs, 1 = HLLC */
 } orc_setup;
 
 /* Van-der-Waals EoS with the reduced parameters a=3, b=1/3, R=8/3. */
@@ -69,6 +70,9 @@ void orc_lsrk4_coeffs(double* A, double* B, double* C);
 int orc_lift(const orc_setup* s, const double* U, double* Q);
 /* Semi-discrete residual R = dU/dt (same layout as U). */
 int orc_rhs(const orc_setup* s, const double* U, double* R);
+/* Convective numerical flux (LF or HLLC per s->flux) of one face with normal +e_k between the
+ * states UL (left) and UR (right), each (rho, m_1..m_dim, c); F has dim + 2 entries. */
+int orc_numflux(const orc_setup* s, int k, const double* UL, const double* UR, double* F);
 /* Advance U by nsteps explicit LSRK4 steps of size dt (in place). */
 int orc_lsrk4(const orc_setup* s, double* U, double dt, int nsteps);
 /* Admissible explicit time step (convective, viscous and source limits). */

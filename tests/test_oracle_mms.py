@@ -72,9 +72,9 @@ def _evaluate(funcs, t, x):
     return out
 
 
-def _run(dim, ne, N, tend, exact, src):
+def _run(dim, ne, N, tend, exact, src, flux=O.FLUX_LF):
     orc = O.Oracle(dim, (ne,) * dim, (0.0,) * dim, (1.0,) * dim, N, O.NODES_GAUSS, T=T, kappa=KAPPA,
-                   alpha=ALPHA, beta=BETA, mu=MU)
+                   alpha=ALPHA, beta=BETA, mu=MU, flux=flux)
     x = orc.coords()
     U = _evaluate(exact, 0.0, x)
     A, B, Cc = O.lsrk4_coeffs()
@@ -109,6 +109,20 @@ def _run(dim, ne, N, tend, exact, src):
 def test_design_order(dim, N, meshes, tend):
     exact, src = _manufactured(dim)
     errs = [_run(dim, ne, N, tend, exact, src) for ne in meshes]
+    rates = [math.log(errs[i] / errs[i + 1]) / math.log(meshes[i + 1] / meshes[i]) for i in range(len(errs) - 1)]
+    print(dim, N, errs, rates)
+    assert errs[-1] < 1e-3
+    assert min(rates) > N + 0.5, (errs, rates)
+
+
+@pytest.mark.parametrize("dim,N,meshes,tend", [
+    (1, 3, (4, 8, 16), 0.1),
+    (2, 2, (4, 8), 0.05),
+])
+def test_design_order_hllc(dim, N, meshes, tend):
+    """The same manufactured solution with the HLLC face flux."""
+    exact, src = _manufactured(dim)
+    errs = [_run(dim, ne, N, tend, exact, src, flux=O.FLUX_HLLC) for ne in meshes]
     rates = [math.log(errs[i] / errs[i + 1]) / math.log(meshes[i + 1] / meshes[i]) for i in range(len(errs) - 1)]
     print(dim, N, errs, rates)
     assert errs[-1] < 1e-3
