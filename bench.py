@@ -318,6 +318,7 @@ def run_gpu(args, wl, rank, world):
     variants = {}
     if U_after is not None:
         variants["fp32_mixed"] = measure_fp32_variant(args, wl, stream, U0, U_after, dt, peaks)
+        variants["fp64_hllc"] = measure_hllc_variant(args, wl, stream, U0, U_after, dt)
 
     if rank != 0:
         return 0
@@ -452,6 +453,40 @@ def batch_vs_sequential_small(nsk, prec, n=64, steps=20):
     return {"instances": n, "nodes_total": nodes, "batched_value": batched, "sequential_value": seq,
             "schedule": {"tpb": tpb, "fused_face": fused, "persistent": persistent},
             "step_latency_ms_p50": sm[len(sm) // 2], "step_latency_ms_p99": sm[-1]}
+
+
+def measure_hllc_variant(args, wl, stream, U0, U_lf_after, dt):
+    """The FP64 path with the HLLC face flux instead of local Lax-Friedrichs on the same workload:
+    throughput, per-kernel times, and the density L2 difference to the Lax-Friedrichs run after
+    the same steps (two consistent schemes: a measure of the flux's dissipation, not an error)."""
+    import torch
+
+    from paper_1912_12059_gb300 import nsk
+
+    s = nsk.Solver(wl.dim, wl.nelem, wl.N, list(wl.lo[:wl.dim]), list(wl.hi[:wl.dim]), wl.node_type,
+                   nsk.NSK_FP64, stream=stream.cuda_stream)
+    s.set_params(T=wl.T, kappa=wl.kappa, alpha=wl.alpha, beta=wl.beta, mu=wl.mu)
+    s.set_flux(nsk.NSK_FLUX_HLLC)
+    s.set_state(U0)
+    tpb, fused = pick_schedule(s, args.schedule)
+    s.step(dt, args.warmup)
+    s.set_profiling(True)
+    s.get_profile(reset=True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    s.step(dt, args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    prof = s.get_profile(reset=True)
+    U = s.get_state()
+    s.close()
+    diff = float(np.sqrt(((U[0] - U_lf_after[0]) ** 2).sum() / (U_lf_after[0] ** 2).sum()))
+    return {"value": wl.dofs * 5 * args.steps / (ms / 1e3), "unit": "DOF-updates/s", "ms_per_step": ms / args.steps,
+            "dtype": "f64", "flux": "hllc", "density_l2_rel_diff_vs_lf": diff,
+            "schedule": {"tpb": tpb, "fused_face": fused},
+            "kernels": {k: {"avg_ms": v[0] / max(v[1], 1), "launches": v[1]} for k, v in prof.items()}}
 
 
 def measure_fp32_variant(args, wl, stream, U0, U64_after, dt, peaks):

@@ -70,6 +70,7 @@ enum { NSK_NODES_GAUSS = 0, NSK_NODES_GAUSS_LOBATTO = 1 };
 enum { NSK_FP64 = 0, NSK_FP32_MIXED = 1 };
 enum { NSK_HOST = 0, NSK_DEVICE = 1 };
 enum { NSK_C_EXPLICIT = 0, NSK_C_LEARNED = 1 };
+enum { NSK_FLUX_LF = 0, NSK_FLUX_HLLC = 1 };
 
 /* Create a context for a periodic box [lo, hi] (per direction) split into
  * nelem[k] equal elements per direction k < dim (entries k >= dim ignored),
@@ -94,6 +95,21 @@ int nsk_set_params(nsk_ctx* ctx, double T, double kappa, double alpha, double be
  * (default 0: c has no convective flux, Eq. fluxes_sources_model2, so its face
  * flux is the BR1 viscous mean only). */
 int nsk_set_c_dissipation(nsk_ctx* ctx, int on);
+
+/* Convective numerical flux of the faces (Sec. 3.1 uses local Lax-Friedrichs and HLLC):
+ * NSK_FLUX_LF (default): central flux minus half the largest wave speed
+ * |v.n| + sqrt(p_alpha') of either side (Eq. parabolic_eigenvalues_model2) times the jump;
+ * NSK_FLUX_HLLC: the three-wave HLLC solver of the barotropic system (rho, m) with the
+ * modified pressure p_alpha: outer speeds S_L = min(u_L - a_L, u_R - a_R),
+ * S_R = max(u_L + a_L, u_R + a_R), a = sqrt(p_alpha'), u the normal velocity; contact speed
+ * S* = (p_R - p_L + rho_L u_L (S_L - u_L) - rho_R u_R (S_R - u_R)) /
+ *      (rho_L (S_L - u_L) - rho_R (S_R - u_R));
+ * flux F_L (S_L >= 0), F_R (S_R <= 0), else F_K + S_K (U*_K - U_K) with K the side of the
+ * face's own region (K = L if S* >= 0) and U*_K = rho_K (S_K - u_K)/(S_K - S*) (1, v with the
+ * normal component replaced by S*). c is not transported: its convective numerical flux is
+ * zero under HLLC (nsk_set_c_dissipation acts on the Lax-Friedrichs flux only). Either flux
+ * keeps the time-step bound of nsk_compute_dt. Returns NSK_ERR_ARG for another value. */
+int nsk_set_flux(nsk_ctx* ctx, int flux);
 
 /* Copy the state in (set) or out (get); layout above, FP64. Setting the state
  * also clears the Runge-Kutta register. */

@@ -447,6 +447,12 @@ int nsk_set_c_dissipation(nsk_ctx* c, int on) {
   return NSK_OK;
 }
 
+int nsk_set_flux(nsk_ctx* c, int flux) {
+  if (!c || (flux != NSK_FLUX_LF && flux != NSK_FLUX_HLLC)) return NSK_ERR_ARG;
+  c->p.flux = flux;
+  return NSK_OK;
+}
+
 int nsk_set_state(nsk_ctx* c, const double* U, int where) {
   if (!c || !U || (where != NSK_HOST && where != NSK_DEVICE)) return NSK_ERR_ARG;
   if (!c->params_set) return NSK_ERR_STATE;

@@ -81,6 +81,7 @@ struct NskParams {
   double spin_lo, spin_hi;  // spinodal interval (p' < 0): the FP32 operator evaluates the EoS in FP64 there
   float spin_lof, spin_hif; // the same bounds rounded outward to FP32
   int c_diss;      // Lax-Friedrichs jump on c as well
+  int flux;        // NSK_FLUX_LF or NSK_FLUX_HLLC
   NskTab<double> td;
   NskTab<float> tf;
 };

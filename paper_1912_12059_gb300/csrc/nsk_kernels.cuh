@@ -417,7 +417,8 @@ __device__ __forceinline__ void lift_group(const NskParams& p, const R* __restri
 }
 
 // Numerical flux on the face between eL (its +1 side, slot 2k+1) and eR (its -1 side,
-// slot 2k), face node fn:
+// slot 2k), face node fn (HLLC instead of the Lax-Friedrichs flux when p.flux says so,
+// see nsk_set_flux):
 //   F* = (F^c_k(U_L) + F^c_k(U_R))/2 - lambda/2 (U_R - U_L) - (F^v_L + F^v_R)/2,
 //   lambda = max(|v_{L,k}| + sqrt(p_alpha'(rho_L)), |v_{R,k}| + sqrt(p_alpha'(rho_R)))
 // (local Lax-Friedrichs with the model II wave speeds, Eq. parabolic_eigenvalues_model2;
@@ -460,6 +461,39 @@ __device__ __forceinline__ void face_flux(const NskParams& p, const R* __restric
   }
   eflag |= rho_flags(UL[0]) | rho_flags(UR[0]);
   if (!sound_ok(dl) || !sound_ok(dr)) eflag |= NSK_EBIT_SOUND;
+  if (p.flux == NSK_FLUX_HLLC) {
+    // HLLC of the barotropic system (rho, m) with p_alpha (see nsk_set_flux): the physical flux
+    // of the upwind side K, plus S_K (U*_K - U_K) inside the star region; c is not transported
+    const R ul = UL[1 + k] * il, ur = UR[1 + k] * ir;
+    const R al = sqrt(dl), ar = sqrt(dr);
+    const R SL = fmin(ul - al, ur - ar), SR = fmax(ul + al, ur + ar);
+    const R wl = UL[0] * (SL - ul), wr = UR[0] * (SR - ur);  // rho_K (S_K - u_K), wl < 0 < wr
+    const R Ss = (pr - pl + fma(wl, ul, -(wr * ur))) / (wl - wr);
+    const bool star = SL < R(0) && SR > R(0);
+    const bool left = SL >= R(0) || (star && Ss >= R(0));
+    R uk[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) uk[v] = left ? UL[v] : UR[v];
+    const R ik = left ? il : ir, pk = left ? pl : pr;
+    const R mk = uk[1 + k];
+    F[0] = mk;
+#pragma unroll
+    for (int a = 0; a < D; ++a) F[1 + a] = (a == k) ? fma(mk, uk[1 + a] * ik, pk) : mk * (uk[1 + a] * ik);
+    if (star) {
+      const R SK = left ? SL : SR;
+      const R coef = (left ? wl : wr) / (SK - Ss);  // rho of U*_K
+      F[0] = fma(SK, coef - uk[0], F[0]);
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        const R us = (a == k) ? coef * Ss : coef * (uk[1 + a] * ik);
+        F[1 + a] = fma(SK, us - uk[1 + a], F[1 + a]);
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < D; ++a) F[1 + a] = fma(-R(0.5), VL[a] + VR[a], F[1 + a]);
+    F[D + 1] = -R(0.5) * (VL[D] + VR[D]);
+    return;
+  }
   const R lam_l = fabs(UL[1 + k] * il) + sqrt(dl), lam_r = fabs(UR[1 + k] * ir) + sqrt(dr);
   const R lam = lam_l > lam_r ? lam_l : lam_r;
   F[0] = R(0.5) * (UL[1 + k] + UR[1 + k]);

@@ -31,6 +31,8 @@ NSK_HOST = 0
 NSK_DEVICE = 1
 NSK_C_EXPLICIT = 0
 NSK_C_LEARNED = 1
+NSK_FLUX_LF = 0
+NSK_FLUX_HLLC = 1
 
 #: every symbol include/nsk.h declares, with (restype, argtypes)
 _dp = C.POINTER(C.c_double)
@@ -39,6 +41,7 @@ SIGNATURES = {
                                 C.c_int, C.c_void_p]),
     "nsk_set_params": (C.c_int, [C.c_void_p, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double]),
     "nsk_set_c_dissipation": (C.c_int, [C.c_void_p, C.c_int]),
+    "nsk_set_flux": (C.c_int, [C.c_void_p, C.c_int]),
     "nsk_set_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "nsk_get_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "nsk_node_coords": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
@@ -232,6 +235,10 @@ class Solver:
 
     def set_c_dissipation(self, on):
         nsk_set_c_dissipation(self.ctx, on)
+
+    def set_flux(self, flux):
+        """NSK_FLUX_LF (default) or NSK_FLUX_HLLC."""
+        _check(load_library().nsk_set_flux(self.ctx, int(flux)), "nsk_set_flux")
 
     def set_state(self, U):
         ptr, where = _buf(U, self.nvar * self.n_nodes, False)

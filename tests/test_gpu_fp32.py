@@ -24,12 +24,14 @@ def _solver(dim, ne, N, precision, **prm):
     return s, p
 
 
+@pytest.mark.parametrize("flux", [nsk.NSK_FLUX_LF, nsk.NSK_FLUX_HLLC])
 @pytest.mark.parametrize("dim,ne,N", [(1, (40,), 3), (2, (7, 6), 4), (3, (5, 4, 3), 3)])
-def test_fp32_rhs_within_fp32_bound(gpu, dim, ne, N):
+def test_fp32_rhs_within_fp32_bound(gpu, dim, ne, N, flux):
     from tolerances import rhs_tolerance
 
     s, p = _solver(dim, ne, N, nsk.NSK_FP32_MIXED, mu=2e-2, kappa=1e-3)
-    o = O.Oracle(dim, ne, [0.0] * dim, [1.0] * dim, N, 0, **p)
+    s.set_flux(flux)
+    o = O.Oracle(dim, ne, [0.0] * dim, [1.0] * dim, N, 0, flux=flux, **p)
     U = inputs.random_state(o.shape, seed=50 + dim)
     U32 = U.astype(np.float32).astype(np.float64)  # the FP32 context stores the state in FP32
     s.set_state(U)

@@ -20,6 +20,7 @@ pytestmark = pytest.mark.gpu
 def make_pair(dim, ne, N, nt=0, lo=None, hi=None, precision=nsk.NSK_FP64, **params):
     prm = dict(T=0.85, kappa=1e-4, alpha=1e3, beta=1e-3, mu=1e-3)
     cdiss = params.pop("c_dissipation", 0)
+    flux = params.pop("flux", nsk.NSK_FLUX_LF)
     prm.update(params)
     lo = lo or [0.0] * dim
     hi = hi or [1.0] * dim
@@ -27,7 +28,9 @@ def make_pair(dim, ne, N, nt=0, lo=None, hi=None, precision=nsk.NSK_FP64, **para
     s.set_params(**prm)
     if cdiss:
         s.set_c_dissipation(True)
-    o = O.Oracle(dim, ne, lo, hi, N, nt, c_dissipation=cdiss, **prm)
+    if flux != nsk.NSK_FLUX_LF:
+        s.set_flux(flux)
+    o = O.Oracle(dim, ne, lo, hi, N, nt, c_dissipation=cdiss, flux=flux, **prm)
     return s, o
 
 
@@ -83,6 +86,43 @@ def test_rhs_parity_c_dissipation(gpu):
     s.close()
 
 
+HLLC_CASES = [(1, (13,), 4, 1), (2, (7, 5), 4, 0), (2, (5, 6), 3, 0), (3, (5, 3, 3), 3, 0), (3, (3, 3, 2), 4, 0)]
+
+
+@pytest.mark.parametrize("dim,ne,N,nt", HLLC_CASES)
+@pytest.mark.parametrize("regime", ["subsonic", "transonic"])
+def test_rhs_parity_hllc(gpu, dim, ne, N, nt, regime):
+    """HLLC face flux. Subsonic: alpha = 1e3 (sound speed ~ 35, |v| < 0.3: every face in the star
+    region, contacts moving either way). Transonic: alpha = 2 (sound speed 1.0..1.6) and |v| up
+    to 3, so faces take all four branches of the solver (F_L, L*, R*, F_R)."""
+    prm = dict(mu=2e-2, kappa=1e-3) if regime == "subsonic" else dict(mu=2e-2, kappa=1e-3, alpha=2.0, beta=1.0)
+    s, o = make_pair(dim, ne, N, nt, hi=[1.0, 0.8, 1.3][:dim], flux=nsk.NSK_FLUX_HLLC, **prm)
+    U = inputs.random_state(o.shape, seed=300 + dim * 10 + N)
+    if regime == "transonic":
+        U[1:dim + 1] *= 15.0
+    s.set_state(U)
+    Rg, Ro = s.rhs(), o.rhs(U)
+    tol = rhs_tolerance(o, U, Ro)
+    for v in range(o.nvar):
+        err = np.abs(Rg[v] - Ro[v]).max()
+        assert err <= tol[v], (v, err, tol[v])
+    s.close()
+
+
+@pytest.mark.parametrize("name", ["droplets2d", "collision3d"])
+def test_step_parity_100_hllc(gpu, name):
+    """100 LSRK4 steps with the HLLC flux: rel. L-inf error <= 1e-11."""
+    s, o, U = _physical_case(name, flux=nsk.NSK_FLUX_HLLC)
+    dt = o.timestep(U, 0.5)
+    s.set_state(U)
+    s.step(dt, 100)
+    Ug = s.get_state()
+    Uo = o.step(U, dt, 100)
+    err = float(np.abs(Ug - Uo).max() / np.abs(Uo).max())
+    assert err <= 1e-11, err
+    s.close()
+
+
 def test_free_stream_gpu(gpu):
     s, o = make_pair(3, (4, 3, 5), 3, 0, hi=[1.0, 0.7, 1.3])
     U = np.zeros(o.shape)
@@ -92,20 +132,20 @@ def test_free_stream_gpu(gpu):
     s.close()
 
 
-def _physical_case(name):
+def _physical_case(name, flux=nsk.NSK_FLUX_LF):
     rv, rl, _ = O.maxwell(0.85)
     if name == "slab1d_gll":
-        s, o = make_pair(1, (64,), 3, 1)
+        s, o = make_pair(1, (64,), 3, 1, flux=flux)
         U = inputs.slab_1d(o.coords(), rv, rl, 1e-4)
     elif name == "slab1d_gl_paper_params":
-        s, o = make_pair(1, (64,), 3, 0, alpha=100.0, beta=1e-2, mu=1e-2)
+        s, o = make_pair(1, (64,), 3, 0, alpha=100.0, beta=1e-2, mu=1e-2, flux=flux)
         U = inputs.slab_1d(o.coords(), rv, rl, 1e-4)
     elif name == "droplets2d":
-        s, o = make_pair(2, (16, 16), 4, 0, mu=2e-3)
+        s, o = make_pair(2, (16, 16), 4, 0, mu=2e-3, flux=flux)
         U = inputs.droplets(o.coords(), ((0.35, 0.5), (0.65, 0.5)), (0.15, 0.12), rv, rl, 1e-4)
         U = inputs.add_density_noise(U, 1e-4)
     elif name == "collision3d":
-        s, o = make_pair(3, (7, 6, 5), 3, 0)
+        s, o = make_pair(3, (7, 6, 5), 3, 0, flux=flux)
         v = inputs.collision_velocity(40.0, 0.2, 1e-4, rv, rl)
         U = inputs.head_on_collision(o.coords(), v, 0.2, rho_vap=rv, rho_liq=rl, kappa=1e-4)
     else:
