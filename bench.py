@@ -79,6 +79,9 @@ def kernel_cost(kernel, d, n, fp_bytes, traces=0.0):
     raise KeyError(kernel)
 
 
+BATCH_KINDS = {0: "one launch per phase", 1: "persistent cooperative", 2: "instance launches"}
+
+
 def pick_schedule(s, fixed):
     """The autotuner's stage schedule, or a fixed "TPB,FUSED" one (profiling runs: under a
     profiler the autotuner's timings are serialised and would pick another schedule)."""
@@ -403,7 +406,7 @@ def run_batch(args, rank, world):
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32" if prec == nsk.NSK_FP32_MIXED else "f64", "data": "synthetic",
         "config": {"workload": f"batched_{args.batch}x_collision3d_E16-48_N3-4", "instances": args.batch,
-                   "nodes_total": nodes, "schedule": {"tpb": tpb, "fused_face": fused, "persistent": persistent},
+                   "nodes_total": nodes, "schedule": {"tpb": tpb, "fused_face": fused, "kind": BATCH_KINDS[persistent]},
                    "cuda_graph": True,
                    "step_latency_ms_p50": sm[len(sm) // 2], "step_latency_ms_p99": sm[min(len(sm) - 1,
                                                                                          int(0.99 * len(sm)))],
@@ -451,7 +454,7 @@ def batch_vs_sequential_small(nsk, prec, n=64, steps=20):
         s.close()
     sm = sorted(ms)
     return {"instances": n, "nodes_total": nodes, "batched_value": batched, "sequential_value": seq,
-            "schedule": {"tpb": tpb, "fused_face": fused, "persistent": persistent},
+            "schedule": {"tpb": tpb, "fused_face": fused, "kind": BATCH_KINDS[persistent]},
             "step_latency_ms_p50": sm[len(sm) // 2], "step_latency_ms_p99": sm[-1]}
 
 

@@ -185,7 +185,8 @@ int nsk_autotune(nsk_ctx* ctx, int* tpb_out, int* fused_out, double* ms_out);
  * persistent cooperative kernel whose phases (traces, lifting, face fluxes,
  * volume + update) are separated by a grid barrier with a one-second bounded
  * wait (NSK_ERR_TIMEOUT on expiry). Phase schedule: one ordinary launch per
- * phase covering all instances. Either way the stage launches of a step are
+ * phase covering all instances. Instance schedule: every instance's stage
+ * kernels in turn. Either way the stage launches of a step are
  * captured once in a CUDA graph and replayed. The batch snapshots each instance's parameters and buffers at
  * creation (call nsk_set_params / nsk_set_state before; states may be reset
  * later through the instances), and the instances must not be used by other
@@ -200,9 +201,12 @@ int nsk_batch_create(nsk_batch** out, int n, nsk_ctx* const* instances);
  * instance of the batch completes a step within that time. */
 int nsk_batch_step(nsk_batch* batch, int nsteps, double cfl, double* step_ms);
 /* Batch schedule (tpb and fused_face as for a context; persistent = 1 for
- * the cooperative persistent kernel, 0 for one launch per phase) and the
- * autotuner over all eight schedules (times one residual of the whole batch
- * under each; the instances' states are not modified). */
+ * the cooperative persistent kernel, 0 for one launch per phase covering all
+ * instances, 2 for each instance's own stage launches one after another in the
+ * captured graph: the schedule of choice when every instance fills the GPU by
+ * itself) and the autotuner over all ten schedules (times one residual of the
+ * whole batch under each; the instances' states are not modified). Returns
+ * NSK_ERR_ARG for tpb not 128 or 256 or persistent outside 0..2. */
 int nsk_batch_set_schedule(nsk_batch* batch, int tpb, int fused_face, int persistent);
 int nsk_batch_get_schedule(nsk_batch* batch, int* tpb, int* fused_face, int* persistent);
 int nsk_batch_autotune(nsk_batch* batch, int* tpb_out, int* fused_out, int* persistent_out, double* ms_out);

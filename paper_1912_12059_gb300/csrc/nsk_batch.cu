@@ -12,7 +12,8 @@
 // together. The five stage launches of a step (and, optionally, the per-
 // instance time-step reductions) are captured once in a CUDA graph and the
 // graph is replayed per step. An autotuner times the block-size and face
-// schedules on the batch and keeps the fastest.
+// schedules, and the instance schedule (each instance's own stage launches in
+// the graph, for instances that fill the GPU alone), and keeps the fastest.
 #include <math.h>
 #include <string.h>
 
@@ -468,9 +469,24 @@ int prepare_batch(nsk_batch* bt) {
   return NSK_OK;
 }
 
-// one stage of the whole batch under a schedule (persistent: one cooperative launch)
+// instance schedule: every instance's own stage kernels, one instance after another
+int launch_instances(nsk_batch* bt, int mode, double A, double B, int tpb, int fused, int traces) {
+  for (nsk_ctx* c : bt->inst) {
+    NskLaunch l = {mode, c->rbuf, A, B, c->b.dt, 0.0, nullptr, tpb, fused};
+    l.traces_ready = traces & 1;
+    l.utr_next = (traces & 2) ? c->b.Utr : nullptr;  // separate face schedule: written in place
+    const int r = nsk_launch_stage_d3(c->p, c->np, c->precision == NSK_FP32_MIXED, c->b, l, bt->stream);
+    if (r < 0) return r;
+    bt->launches += r;
+  }
+  return NSK_OK;
+}
+
+// one stage of the whole batch under a schedule (persistent 1: one cooperative launch; 0: one
+// launch per phase; 2: every instance's own launches)
 int launch_batch(nsk_batch* bt, int mode, double A, double B, int tpb, int fused, int persistent, int traces) {
   if (fused) traces = 0;  // the fused volume phase reads the traces: they are prolonged every stage
+  if (persistent == 2) return launch_instances(bt, mode, A, B, tpb, fused, traces);
   return persistent ? launch_persistent(bt, mode, A, B, tpb, fused, traces)
                     : launch_phases(bt, mode, A, B, tpb, fused, traces);
 }
@@ -609,10 +625,10 @@ int nsk_batch_create(nsk_batch** out, int n, nsk_ctx* const* instances) {
 }
 
 int nsk_batch_set_schedule(nsk_batch* bt, int tpb, int fused_face, int persistent) {
-  if (!bt || (tpb != 128 && tpb != 256)) return NSK_ERR_ARG;
+  if (!bt || (tpb != 128 && tpb != 256) || persistent < 0 || persistent > 2) return NSK_ERR_ARG;
   bt->tpb = tpb;
   bt->fused = fused_face ? 1 : 0;
-  bt->persistent = persistent ? 1 : 0;
+  bt->persistent = persistent;
   return NSK_OK;
 }
 
@@ -633,7 +649,7 @@ int nsk_batch_autotune(nsk_batch* bt, int* tpb_out, int* fused_out, int* persist
   double best = 1e300;
   int bt_tpb = bt->tpb, bt_f = bt->fused, bt_p = bt->persistent, st = NSK_OK;
   const int tpbs[2] = {128, 256};
-  for (int per = 0; per < 2 && st == NSK_OK; ++per)
+  for (int per = 0; per < 3 && st == NSK_OK; ++per)
     for (int ti = 0; ti < 2 && st == NSK_OK; ++ti)
       for (int f = 0; f < 2 && st == NSK_OK; ++f) {
         // warm-up with a prolongation pass (residual: state untouched), then time the stage as a

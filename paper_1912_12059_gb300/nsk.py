@@ -366,22 +366,27 @@ class Batch:
         _check(load_library().nsk_batch_step(self.h, nsteps, cfl, ms), "nsk_batch_step")
         return list(ms)[:nsteps] if timings else None
 
-    def set_schedule(self, tpb=256, fused_face=False, persistent=True):
-        _check(load_library().nsk_batch_set_schedule(self.h, tpb, int(bool(fused_face)), int(bool(persistent))),
+    #: values of the `persistent` schedule argument
+    PHASES, PERSISTENT, INSTANCES = 0, 1, 2
+
+    def set_schedule(self, tpb=256, fused_face=False, persistent=1):
+        """persistent: 1 cooperative persistent kernel, 0 one launch per phase, 2 each instance's
+        own stage launches (True/False map to 1/0)."""
+        _check(load_library().nsk_batch_set_schedule(self.h, tpb, int(bool(fused_face)), int(persistent)),
                "nsk_batch_set_schedule")
 
     def get_schedule(self):
         t, f, p = C.c_int(), C.c_int(), C.c_int()
         _check(load_library().nsk_batch_get_schedule(self.h, C.byref(t), C.byref(f), C.byref(p)),
                "nsk_batch_get_schedule")
-        return t.value, bool(f.value), bool(p.value)
+        return t.value, bool(f.value), p.value
 
     def autotune(self):
-        """Time all eight schedules on the batch; keep and return (tpb, fused, persistent, ms)."""
+        """Time all ten schedules on the batch; keep and return (tpb, fused, persistent, ms)."""
         t, f, p, ms = C.c_int(), C.c_int(), C.c_int(), C.c_double()
         _check(load_library().nsk_batch_autotune(self.h, C.byref(t), C.byref(f), C.byref(p), C.byref(ms)),
                "nsk_batch_autotune")
-        return t.value, bool(f.value), bool(p.value), ms.value
+        return t.value, bool(f.value), p.value, ms.value
 
     def set_timeout(self, seconds):
         _check(load_library().nsk_batch_set_timeout(self.h, seconds), "nsk_batch_set_timeout")

@@ -112,7 +112,8 @@ def test_batch_equals_solo_runs(gpu, precision, adaptive):
         s.set_state(U)
         s.compute_dt(0.5)
     b = nsk.Batch([s for s, _ in inst])
-    for tpb, fused, persistent in ((256, True, True), (128, False, True), (256, False, False), (128, True, False)):
+    for tpb, fused, persistent in ((256, True, 1), (128, False, 1), (256, False, 0), (128, True, 0), (256, False, 2),
+                                   (128, True, 2)):
         for s, U in inst:
             s.set_state(U)
             s.compute_dt(0.5)
@@ -133,10 +134,10 @@ def test_batch_autotune_graph_and_launch_count(gpu):
         s.compute_dt(0.5)
     b = nsk.Batch([s for s, _ in inst])
     tpb, fused, persistent, ms = b.autotune()
-    assert tpb in (128, 256) and ms > 0 and b.get_schedule() == (tpb, fused, persistent)
+    assert tpb in (128, 256) and persistent in (0, 1, 2) and ms > 0 and b.get_schedule() == (tpb, fused, persistent)
     # separate face schedule: one prolongation launch per call, then per stage the persistent
     # kernel, or lifting, face and volume launches (the volume phase writes the next traces)
-    for persistent, per_stage in ((True, 1), (False, 3)):
+    for persistent, per_stage in ((1, 1), (0, 3), (2, 3 * len(inst))):
         b.set_schedule(256, False, persistent)
         n0 = b.launch_count
         b.step(2)
