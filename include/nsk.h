@@ -259,8 +259,14 @@ long long nsk_mlp_num_params(nsk_mlp* mlp);
  * them resets the Adam moments. */
 int nsk_mlp_set_params(nsk_mlp* mlp, const float* params, long long n);
 int nsk_mlp_get_params(nsk_mlp* mlp, float* params, long long n);
-/* Inference: X BF16 device [rows][n_in_pad] -> Y FP32 device [rows][n_out]. */
+/* Inference: X BF16 device [rows][n_in_pad] -> Y FP32 device [rows][n_out]. When the
+ * network fits on chip (n_in_pad, h1, h2, n_out <= 256 and its shared-memory plan within
+ * 224 KB) the three layers run as one kernel that keeps the hidden activations of each
+ * 128-row tile in shared memory and TMEM; otherwise as three GEMMs. Both give the same
+ * values. */
 int nsk_mlp_forward(nsk_mlp* mlp, const void* X, int rows, float* Y);
+/* on = 0 forces the three-GEMM forward (default 1: fused where it fits). */
+int nsk_mlp_set_fused_forward(nsk_mlp* mlp, int on);
 /* Loss L = mean over rows and outputs of (Y - T)^2 for X BF16 [batch][n_in_pad]
  * and targets T FP32 [batch][n_out] (device); gradients of L (layout of the
  * parameters) copied to grads (host, may be NULL); loss (may be NULL). */

@@ -74,6 +74,7 @@ struct nsk_mlp {
   double* loss;
   int* err;
   long long adam_step, launches;
+  int fused_forward;  // 1 (default): inference forward in one kernel when the network fits
 };
 
 namespace {
@@ -239,6 +240,30 @@ int mlp_grad(nsk_mlp* m, const __nv_bfloat16* X, const float* T, int B) {
 // inference forward on a given stream and error word (used by the closure on the context's stream)
 int mlp_forward_on(nsk_mlp* m, const __nv_bfloat16* X, int rows, float* Y, cudaStream_t s, int* err) {
   int st;
+  if (m->fused_forward) {  // one kernel for the three layers when the network fits on chip
+    nsk::tc::MlpFwdArgs f;
+    f.X = X;
+    f.W1 = m->W1;
+    f.W2 = m->W2;
+    f.W3 = m->W3;
+    f.b1 = m->param + m->ob1;
+    f.b2 = m->param + m->ob2;
+    f.b3 = m->param + m->ob3;
+    f.Y = Y;
+    f.M = rows;
+    f.ldx = m->nin_pad;
+    f.ldy = m->nout;
+    f.K1 = m->nin_pad;
+    f.H1 = m->h1;
+    f.H2 = m->h2;
+    f.NO = m->nout;
+    f.err = err;
+    st = nsk::tc::launch_mlp_fwd3(f, s);
+    if (st != NSK_ERR_ARG) {
+      if (st == NSK_OK) m->launches += 1;
+      return st;
+    }
+  }
   nsk::tc::GemmArgs a = gemm_args(X, m->nin_pad, m->W1, m->nin_pad, rows, m->h1, m->nin_pad, nsk::tc::EPI_GELU, err);
   a.bias = m->param + m->ob1;
   a.hout = m->IH1;
@@ -296,6 +321,7 @@ int nsk_mlp_create(nsk_mlp** out, int n_in, int h1, int h2, int n_out, int max_b
   if (!m) return NSK_ERR_NOMEM;
   m->nin = n_in;
   m->nin_pad = round16(n_in);
+  m->fused_forward = 1;
   m->h1 = h1;
   m->h2 = h2;
   m->nout = n_out;
@@ -365,6 +391,12 @@ int nsk_mlp_get_params(nsk_mlp* m, float* host, long long n) {
   if (cudaMemcpyAsync(host, m->param, sizeof(float) * m->nparam, cudaMemcpyDeviceToHost, m->stream) != cudaSuccess ||
       cudaStreamSynchronize(m->stream) != cudaSuccess)
     return NSK_ERR_CUDA;
+  return NSK_OK;
+}
+
+int nsk_mlp_set_fused_forward(nsk_mlp* m, int on) {
+  if (!m) return NSK_ERR_ARG;
+  m->fused_forward = on ? 1 : 0;
   return NSK_OK;
 }
 

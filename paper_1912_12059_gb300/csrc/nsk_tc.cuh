@@ -463,6 +463,234 @@ __global__ void __launch_bounds__(kRbThreads, 1) k_gemm_tc_rb(const GemmArgs a) 
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
 }
 
+// ---------------------------------------------------------------------------
+// Fused inference forward of the closure network, Y = W3 g(W2 g(W1 X + b1) + b2) + b3
+// (g = GELU), for one 128-row tile at a time: the hidden activations never leave the SM.
+// One CTA of 256 threads per SM owns all 512 TMEM columns: layer 1 accumulates in columns
+// [0, H1), layer 2 in [256, 256 + H2), layer 3 in [0, NO) again (layer 1 is drained by then).
+// Shared memory: W2 resident ([H2][H1], loaded once), the row tile (X, then g(layer 1), then
+// g(layer 2), each in the K-major core-matrix layout the next MMA reads), and one streaming
+// buffer for the 64-column chunks of W1 and then for W3. The epilogues of warp w read TMEM
+// lanes 32 (w % 4).. and 32-column chunks w / 4, w / 4 + 2, ...; GELU and the BF16 rounding
+// are the same as the per-layer kernels', and so is the order of the MMAs along K, so the
+// result equals the three-GEMM chain.
+// ---------------------------------------------------------------------------
+struct MlpFwdArgs {
+  const __nv_bfloat16* X;  // [M][ldx], columns [0, K1) used
+  const __nv_bfloat16* W1; // [H1][K1]
+  const __nv_bfloat16* W2; // [H2][H1]
+  const __nv_bfloat16* W3; // [NO][H2]
+  const float *b1, *b2, *b3;
+  float* Y;                // [M][ldy]
+  int M, ldx, ldy, K1, H1, H2, NO;
+  int* err;
+};
+constexpr int kFwThreads = 256;
+constexpr int kFwChunk = 64;  // K columns of W1 per streaming step
+
+__host__ __device__ inline int fw_align(int b) { return (b + 1023) & ~1023; }
+__host__ __device__ inline int fw_w2_bytes(const MlpFwdArgs& a) { return fw_align(a.H2 * a.H1 * 2); }
+__host__ __device__ inline int fw_xh_bytes(const MlpFwdArgs& a) {
+  const int kx = a.K1 > a.H1 ? (a.K1 > a.H2 ? a.K1 : a.H2) : (a.H1 > a.H2 ? a.H1 : a.H2);
+  return fw_align(kBM * kx * 2);
+}
+__host__ __device__ inline int fw_ws_bytes(const MlpFwdArgs& a) {
+  const int w1 = a.H1 * kFwChunk * 2, w3 = a.NO * a.H2 * 2;
+  return fw_align(w1 > w3 ? w1 : w3);
+}
+__host__ __device__ inline int fw_smem_bytes(const MlpFwdArgs& a) {
+  return fw_w2_bytes(a) + fw_xh_bytes(a) + fw_ws_bytes(a);
+}
+
+// accumulator columns [0, N) of the warp's 32 rows -> + bias -> GELU -> BF16 into the row tile
+// (layout with K = N) in shared memory
+__device__ __forceinline__ void fw_gelu_to_smem(uint32_t tacc, int N, const float* __restrict__ bias,
+                                                unsigned char* sxh, int warp, int lane) {
+  const int q = warp & 3, half = warp >> 2, r = q * 32 + lane;
+  for (int c0 = half * 32; c0 < N; c0 += 64) {
+    uint32_t v[32];
+    tmem_ld32(tacc + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+      const int c = c0 + g * 8;
+      if (c < N) {
+        __align__(16) __nv_bfloat16 h[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) h[j] = __float2bfloat16_rn(gelu(__uint_as_float(v[g * 8 + j]) + bias[c + j]));
+        *reinterpret_cast<uint4*>(sxh + core_off_k(r, c, N)) = *reinterpret_cast<const uint4*>(h);
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void fw_mma(uint32_t d, uint32_t sa, uint32_t sb, int lda_k, int ldb_k, int ksteps,
+                                       uint32_t idesc, bool accumulate) {
+  for (int s = 0; s < ksteps; ++s) {
+    const uint64_t ad = sdesc(sa + s * 256, 128, (uint32_t)(lda_k / 8) * 128);
+    const uint64_t bd = sdesc(sb + s * 256, 128, (uint32_t)(ldb_k / 8) * 128);
+    const uint32_t acc = (accumulate || s > 0) ? 1u : 0u;
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+        "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+  }
+}
+
+__device__ __forceinline__ void fw_commit(uint64_t* mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(mbar)));
+}
+
+__global__ void __launch_bounds__(kFwThreads, 1) k_mlp_fwd3(const MlpFwdArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  unsigned char* sW2 = smem;
+  unsigned char* sXH = smem + fw_w2_bytes(a);
+  unsigned char* sWs = sXH + fw_xh_bytes(a);
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int aborted;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ntiles = (a.M + kBM - 1) / kBM;
+  const uint32_t aW2 = smem_u32(sW2), aXH = smem_u32(sXH), aWs = smem_u32(sWs);
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (threadIdx.x == 0) {
+    aborted = 0;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar)), "r"(1));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  for (int idx = threadIdx.x; idx < a.H2 * (a.H1 / 8); idx += kFwThreads) {  // resident W2
+    const int r = idx / (a.H1 / 8), j = idx % (a.H1 / 8);
+    cp_async16(aW2 + core_off_k(r, j * 8, a.H1), a.W2 + (size_t)r * a.H1 + j * 8, 16);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tm = tmem_slot;
+  uint32_t ph = 0;
+
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int m0 = t * kBM;
+    for (int idx = threadIdx.x; idx < kBM * (a.K1 / 8); idx += kFwThreads) {  // row tile of X
+      const int r = idx / (a.K1 / 8), j = idx % (a.K1 / 8);
+      const bool v = m0 + r < a.M;
+      cp_async16(aXH + core_off_k(r, j * 8, a.K1), v ? (const void*)(a.X + (size_t)(m0 + r) * a.ldx + j * 8)
+                                                     : (const void*)a.X, v ? 16 : 0);
+    }
+    // layer 1: W1 streamed in 64-column chunks of K
+    for (int kc = 0; kc < a.K1; kc += kFwChunk) {
+      const int kw = min(kFwChunk, a.K1 - kc);
+      for (int idx = threadIdx.x; idx < a.H1 * (kw / 8); idx += kFwThreads) {
+        const int r = idx / (kw / 8), j = idx % (kw / 8);
+        cp_async16(aWs + core_off_k(r, j * 8, kFwChunk), a.W1 + (size_t)r * a.K1 + kc + j * 8, 16);
+      }
+      asm volatile("cp.async.wait_all;" ::: "memory");
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        fw_mma(tm, aXH + (uint32_t)(kc / 8) * 128, aWs, a.K1, kFwChunk, kw / 16, idesc_bf16(kBM, a.H1), kc > 0);
+        fw_commit(&mbar);
+      }
+      if (!mbar_wait(smem_u32(&mbar), ph, a.err)) aborted = 1;
+      ph ^= 1u;
+      asm volatile("tcgen05.fence::after_thread_sync;");
+    }
+    __syncthreads();
+    if (aborted) break;
+    for (int idx = threadIdx.x; idx < a.NO * (a.H2 / 8); idx += kFwThreads) {  // W3 (lands during epilogues)
+      const int r = idx / (a.H2 / 8), j = idx % (a.H2 / 8);
+      cp_async16(aWs + core_off_k(r, j * 8, a.H2), a.W3 + (size_t)r * a.H2 + j * 8, 16);
+    }
+    fw_gelu_to_smem(tm, a.H1, a.b1, sXH, warp, lane);
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    // layer 2: g(layer 1) x W2^T -> columns [256, 256 + H2)
+    if (threadIdx.x == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      fw_mma(tm + 256u, aXH, aW2, a.H1, a.H1, a.H1 / 16, idesc_bf16(kBM, a.H2), false);
+      fw_commit(&mbar);
+    }
+    if (!mbar_wait(smem_u32(&mbar), ph, a.err)) aborted = 1;
+    ph ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    __syncthreads();
+    if (aborted) break;
+    fw_gelu_to_smem(tm + 256u, a.H2, a.b2, sXH, warp, lane);
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    // layer 3: g(layer 2) x W3^T -> columns [0, NO)
+    if (threadIdx.x == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      fw_mma(tm, aXH, aWs, a.H2, a.H2, a.H2 / 16, idesc_bf16(kBM, a.NO), false);
+      fw_commit(&mbar);
+    }
+    if (!mbar_wait(smem_u32(&mbar), ph, a.err)) aborted = 1;
+    ph ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    __syncthreads();
+    if (aborted) break;
+    {
+      const int q = warp & 3, half = warp >> 2, r = q * 32 + lane;
+      const bool rv = m0 + r < a.M;
+      for (int c0 = half * 32; c0 < a.NO; c0 += 64) {
+        uint32_t v[32];
+        tmem_ld32(tm + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
+        if (rv) {
+          float* y = a.Y + (size_t)(m0 + r) * a.ldy + c0;
+#pragma unroll
+          for (int g = 0; g < 8; ++g)
+            if (c0 + g * 4 < a.NO)
+              *reinterpret_cast<float4*>(y + g * 4) =
+                  make_float4(__uint_as_float(v[g * 4]) + a.b3[c0 + g * 4], __uint_as_float(v[g * 4 + 1]) + a.b3[c0 + g * 4 + 1],
+                              __uint_as_float(v[g * 4 + 2]) + a.b3[c0 + g * 4 + 2],
+                              __uint_as_float(v[g * 4 + 3]) + a.b3[c0 + g * 4 + 3]);
+        }
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();  // TMEM columns and the row tile are reused by the next tile
+  }
+  asm volatile("cp.async.wait_all;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tm), "r"(512));
+}
+
+// fused forward when the network fits (NSK_ERR_ARG otherwise: the caller uses the per-layer GEMMs)
+inline int launch_mlp_fwd3(const MlpFwdArgs& a, cudaStream_t s) {
+  auto a16 = [](const void* p) { return ((uintptr_t)p & 15u) == 0; };
+  if (a.M < 1 || a.K1 < 16 || a.K1 > 256 || (a.K1 % 16) || a.H1 < 16 || a.H1 > 256 || (a.H1 % 16) ||
+      a.H2 < 16 || a.H2 > 256 || (a.H2 % 16) || a.NO < 16 || a.NO > 256 || (a.NO % 16) || (a.ldx % 8) ||
+      a.ldx < a.K1 || (a.ldy % 4) || a.ldy < a.NO || !a16(a.X) || !a16(a.W1) || !a16(a.W2) || !a16(a.W3) ||
+      !a16(a.Y))
+    return NSK_ERR_ARG;
+  int smem = fw_smem_bytes(a);
+  if (smem > 224 * 1024) return NSK_ERR_ARG;
+  smem = smem < kRbSmemMin ? kRbSmemMin : smem;  // one CTA per SM: it owns all 512 TMEM columns
+  static bool attr_done = false;
+  static int sms = 0;
+  if (!attr_done) {
+    int dev = 0;
+    if (cudaFuncSetAttribute(k_mlp_fwd3, cudaFuncAttributeMaxDynamicSharedMemorySize, 224 * 1024) != cudaSuccess ||
+        cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+      cudaGetLastError();
+      return NSK_ERR_CUDA;
+    }
+    attr_done = true;
+  }
+  const int ntiles = (a.M + kBM - 1) / kBM;
+  k_mlp_fwd3<<<(unsigned)(ntiles < sms ? ntiles : sms), kFwThreads, smem, s>>>(a);
+  return cudaGetLastError() == cudaSuccess ? NSK_OK : NSK_ERR_CUDA;
+}
+
 // host launcher (grid: ceil(M/128) x ceil(K/k_split))
 inline int launch_gemm(const GemmArgs& a, cudaStream_t s) {
   if (a.M < 1 || a.N < 16 || a.N > kMaxN || (a.N % 16) || a.K < 16 || (a.K % 16) || (a.lda % 8) || (a.ldb % 8) ||

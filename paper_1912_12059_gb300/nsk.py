@@ -80,6 +80,7 @@ SIGNATURES = {
     "nsk_mlp_set_params": (C.c_int, [C.c_void_p, C.c_void_p, C.c_longlong]),
     "nsk_mlp_get_params": (C.c_int, [C.c_void_p, C.c_void_p, C.c_longlong]),
     "nsk_mlp_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "nsk_mlp_set_fused_forward": (C.c_int, [C.c_void_p, C.c_int]),
     "nsk_mlp_gradients": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, _dp]),
     "nsk_mlp_train_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_double, _dp]),
     "nsk_mlp_launch_count": (C.c_longlong, [C.c_void_p]),
@@ -487,6 +488,10 @@ class MLP:
     def forward(self, X, Y):
         _check(load_library().nsk_mlp_forward(self.h, C.c_void_p(X.data_ptr()), X.shape[0], C.c_void_p(Y.data_ptr())),
                "nsk_mlp_forward")
+
+    def set_fused_forward(self, on):
+        """False forces the three-GEMM forward (default: one fused kernel where the network fits)."""
+        _check(load_library().nsk_mlp_set_fused_forward(self.h, int(bool(on))), "nsk_mlp_set_fused_forward")
 
     def gradients(self, X, T):
         g = np.empty(self.n_params, dtype=np.float32)

@@ -68,6 +68,32 @@ def test_mlp_forward_and_gradients_match_oracle(gpu, n_in, h1, h2, n_out, B):
     m.close()
 
 
+@pytest.mark.parametrize("n_in,h1,h2,n_out,rows", [(140, 256, 256, 64, 1000), (40, 64, 128, 32, 300),
+                                                    (70, 128, 256, 16, 128)])
+def test_fused_forward_equals_gemm_chain(gpu, n_in, h1, h2, n_out, rows):
+    """The one-kernel forward (activations kept on chip) performs the same MMAs in the same
+    order and the same GELU and BF16 rounding as the three per-layer GEMMs: equal outputs,
+    also for a ragged last row tile."""
+    import torch
+
+    m = nsk.MLP(n_in, h1, h2, n_out, max_batch=256, max_rows=rows)
+    m.init_params(seed=7)
+    rng = np.random.default_rng(8)
+    Xn = np.zeros((rows, m.n_in_pad))
+    Xn[:, :n_in] = rng.uniform(-1, 1, size=(rows, n_in))
+    X = torch.from_numpy(Xn).to(torch.bfloat16).to(gpu)
+    Yf = torch.full((rows, n_out), float("nan"), dtype=torch.float32, device=gpu)
+    Yg = torch.full((rows, n_out), float("nan"), dtype=torch.float32, device=gpu)
+    m.forward(X, Yf)
+    m.set_fused_forward(False)
+    m.forward(X, Yg)
+    torch.cuda.synchronize()
+    a, b = Yf.cpu().numpy(), Yg.cpu().numpy()
+    assert np.isfinite(a).all()
+    assert np.abs(a - b).max() <= 1e-6 * np.abs(b).max(), np.abs(a - b).max()
+    m.close()
+
+
 def test_mlp_training_fits_a_smooth_map(gpu):
     import torch
 
