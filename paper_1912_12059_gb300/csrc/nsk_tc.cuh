@@ -82,7 +82,19 @@ __device__ __forceinline__ uint32_t core_off(int r, int k) {
   return (uint32_t)((((r >> 3) * (kKC / 8) + (k >> 3)) << 7) + ((r & 7) << 4) + ((k & 7) << 1));
 }
 
-__device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
+// erf after Abramowitz and Stegun, Handbook of Mathematical Functions, Eq. 7.1.26 (a rational
+// approximation due to Hastings): erf(x) = 1 - t (a1 + t (a2 + t (a3 + t (a4 + t a5)))) exp(-x^2),
+// t = 1 / (1 + p x) for x >= 0, odd extension; absolute error <= 1.5e-7 (plus FP32 rounding).
+// Two special-function-unit operations and six FMAs: the GELU epilogues are bound by it.
+__device__ __forceinline__ float erf_as(float x) {
+  const float ax = fabsf(x);
+  const float t = __fdividef(1.0f, fmaf(0.3275911f, ax, 1.0f));
+  const float poly =
+      t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.061405429f, -1.453152027f), 1.421413741f), -0.284496736f), 0.254829592f);
+  return copysignf(fmaf(-poly, __expf(-ax * ax), 1.0f), x);
+}
+// GELU(x) = x Phi(x) = x (1 + erf(x / sqrt 2)) / 2
+__device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.0f + erf_as(x * 0.70710678118654752f)); }
 __device__ __forceinline__ float gelu_grad(float x) {
   return 0.5f * (1.0f + erff(x * 0.70710678118654752f)) + x * 0.3989422804014327f * __expf(-0.5f * x * x);
 }
@@ -466,12 +478,13 @@ __global__ void __launch_bounds__(kRbThreads, 1) k_gemm_tc_rb(const GemmArgs a) 
 // ---------------------------------------------------------------------------
 // Fused inference forward of the closure network, Y = W3 g(W2 g(W1 X + b1) + b2) + b3
 // (g = GELU), for one 128-row tile at a time: the hidden activations never leave the SM.
-// One CTA of 256 threads per SM owns all 512 TMEM columns: layer 1 accumulates in columns
+// One CTA of 512 threads per SM owns all 512 TMEM columns: layer 1 accumulates in columns
 // [0, H1), layer 2 in [256, 256 + H2), layer 3 in [0, NO) again (layer 1 is drained by then).
 // Shared memory: W2 resident ([H2][H1], loaded once), the row tile (X, then g(layer 1), then
 // g(layer 2), each in the K-major core-matrix layout the next MMA reads), and one streaming
-// buffer for the 64-column chunks of W1 and then for W3. The epilogues of warp w read TMEM
-// lanes 32 (w % 4).. and 32-column chunks w / 4, w / 4 + 2, ...; GELU and the BF16 rounding
+// buffer for the 64-column chunks of W1 and then for W3 (the next tile's rows and first W1
+// chunk are loaded while layer 3 drains). The epilogues of warp w read TMEM lanes 32 (w % 4)..
+// and 32-column chunks w / 4, w / 4 + 4, ...; GELU and the BF16 rounding
 // are the same as the per-layer kernels', and so is the order of the MMAs along K, so the
 // result equals the three-GEMM chain.
 // ---------------------------------------------------------------------------
@@ -485,7 +498,8 @@ struct MlpFwdArgs {
   int M, ldx, ldy, K1, H1, H2, NO;
   int* err;
 };
-constexpr int kFwThreads = 256;
+constexpr int kFwThreads = 512;
+constexpr int kFwWarps = kFwThreads / 32;
 constexpr int kFwChunk = 64;  // K columns of W1 per streaming step
 
 __host__ __device__ inline int fw_align(int b) { return (b + 1023) & ~1023; }
@@ -503,22 +517,24 @@ __host__ __device__ inline int fw_smem_bytes(const MlpFwdArgs& a) {
 }
 
 // accumulator columns [0, N) of the warp's 32 rows -> + bias -> GELU -> BF16 into the row tile
-// (layout with K = N) in shared memory
+// (layout with K = N) in shared memory; warp w: TMEM lanes 32 (w % 4).., 32-column chunks
+// w / 4, w / 4 + 4, ...
+// (the warp's lanes share the columns: lane j loads the bias of column c0 + j, shuffles broadcast it)
 __device__ __forceinline__ void fw_gelu_to_smem(uint32_t tacc, int N, const float* __restrict__ bias,
                                                 unsigned char* sxh, int warp, int lane) {
-  const int q = warp & 3, half = warp >> 2, r = q * 32 + lane;
-  for (int c0 = half * 32; c0 < N; c0 += 64) {
+  const int q = warp & 3, part = warp >> 2, r = q * 32 + lane;
+  for (int c0 = part * 32; c0 < N; c0 += 32 * (kFwWarps / 4)) {
+    const float bl = c0 + lane < N ? bias[c0 + lane] : 0.f;
     uint32_t v[32];
     tmem_ld32(tacc + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
 #pragma unroll
     for (int g = 0; g < 4; ++g) {
       const int c = c0 + g * 8;
-      if (c < N) {
-        __align__(16) __nv_bfloat16 h[8];
+      __align__(16) __nv_bfloat16 h[8];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) h[j] = __float2bfloat16_rn(gelu(__uint_as_float(v[g * 8 + j]) + bias[c + j]));
-        *reinterpret_cast<uint4*>(sxh + core_off_k(r, c, N)) = *reinterpret_cast<const uint4*>(h);
-      }
+      for (int j = 0; j < 8; ++j)
+        h[j] = __float2bfloat16_rn(gelu(__uint_as_float(v[g * 8 + j]) + __shfl_sync(0xffffffffu, bl, g * 8 + j)));
+      if (c < N) *reinterpret_cast<uint4*>(sxh + core_off_k(r, c, N)) = *reinterpret_cast<const uint4*>(h);
     }
   }
 }
@@ -540,10 +556,30 @@ __device__ __forceinline__ void fw_commit(uint64_t* mbar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(mbar)));
 }
 
+// cp.async of the row tile t of X and of the first 64-column chunk of W1
+__device__ __forceinline__ void fw_load_tile(const MlpFwdArgs& a, int t, uint32_t aXH, uint32_t aWs) {
+  const int m0 = t * kBM;
+  for (int idx = threadIdx.x; idx < kBM * (a.K1 / 8); idx += kFwThreads) {
+    const int r = idx / (a.K1 / 8), j = idx % (a.K1 / 8);
+    const bool v = m0 + r < a.M;
+    cp_async16(aXH + core_off_k(r, j * 8, a.K1), v ? (const void*)(a.X + (size_t)(m0 + r) * a.ldx + j * 8)
+                                                   : (const void*)a.X, v ? 16 : 0);
+  }
+}
+__device__ __forceinline__ void fw_load_w1(const MlpFwdArgs& a, int kc, uint32_t aWs) {
+  const int kw = min(kFwChunk, a.K1 - kc);
+  for (int idx = threadIdx.x; idx < a.H1 * (kw / 8); idx += kFwThreads) {
+    const int r = idx / (kw / 8), j = idx % (kw / 8);
+    cp_async16(aWs + core_off_k(r, j * 8, kFwChunk), a.W1 + (size_t)r * a.K1 + kc + j * 8, 16);
+  }
+}
+
 __global__ void __launch_bounds__(kFwThreads, 1) k_mlp_fwd3(const MlpFwdArgs a) {
-  extern __shared__ __align__(1024) unsigned char smem[];
-  unsigned char* sW2 = smem;
-  unsigned char* sXH = smem + fw_w2_bytes(a);
+  // its own dynamic-shared-memory symbol: the 16-byte alignment keeps the static area at a few
+  // bytes (tcgen05 no-swizzle operands and cp.async need 16-byte alignment only)
+  extern __shared__ __align__(16) unsigned char fw_smem[];
+  unsigned char* sW2 = fw_smem;
+  unsigned char* sXH = fw_smem + fw_w2_bytes(a);
   unsigned char* sWs = sXH + fw_xh_bytes(a);
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tmem_slot;
@@ -566,6 +602,10 @@ __global__ void __launch_bounds__(kFwThreads, 1) k_mlp_fwd3(const MlpFwdArgs a) 
     const int r = idx / (a.H1 / 8), j = idx % (a.H1 / 8);
     cp_async16(aW2 + core_off_k(r, j * 8, a.H1), a.W2 + (size_t)r * a.H1 + j * 8, 16);
   }
+  if ((int)blockIdx.x < ntiles) {
+    fw_load_tile(a, blockIdx.x, aXH, aWs);
+    fw_load_w1(a, 0, aWs);
+  }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
@@ -574,19 +614,10 @@ __global__ void __launch_bounds__(kFwThreads, 1) k_mlp_fwd3(const MlpFwdArgs a) 
 
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int m0 = t * kBM;
-    for (int idx = threadIdx.x; idx < kBM * (a.K1 / 8); idx += kFwThreads) {  // row tile of X
-      const int r = idx / (a.K1 / 8), j = idx % (a.K1 / 8);
-      const bool v = m0 + r < a.M;
-      cp_async16(aXH + core_off_k(r, j * 8, a.K1), v ? (const void*)(a.X + (size_t)(m0 + r) * a.ldx + j * 8)
-                                                     : (const void*)a.X, v ? 16 : 0);
-    }
-    // layer 1: W1 streamed in 64-column chunks of K
+    // layer 1: W1 streamed in 64-column chunks of K (the tile and chunk 0 are already on their way)
     for (int kc = 0; kc < a.K1; kc += kFwChunk) {
       const int kw = min(kFwChunk, a.K1 - kc);
-      for (int idx = threadIdx.x; idx < a.H1 * (kw / 8); idx += kFwThreads) {
-        const int r = idx / (kw / 8), j = idx % (kw / 8);
-        cp_async16(aWs + core_off_k(r, j * 8, kFwChunk), a.W1 + (size_t)r * a.K1 + kc + j * 8, 16);
-      }
+      if (kc > 0) fw_load_w1(a, kc, aWs);
       asm volatile("cp.async.wait_all;" ::: "memory");
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncthreads();
@@ -636,26 +667,32 @@ __global__ void __launch_bounds__(kFwThreads, 1) k_mlp_fwd3(const MlpFwdArgs a) 
     asm volatile("tcgen05.fence::after_thread_sync;");
     __syncthreads();
     if (aborted) break;
+    // the row tile and the streaming buffer are free: start the next tile's loads, then drain layer 3
+    if (t + (int)gridDim.x < ntiles) {
+      fw_load_tile(a, t + gridDim.x, aXH, aWs);
+      fw_load_w1(a, 0, aWs);
+    }
     {
-      const int q = warp & 3, half = warp >> 2, r = q * 32 + lane;
+      const int q = warp & 3, part = warp >> 2, r = q * 32 + lane;
       const bool rv = m0 + r < a.M;
-      for (int c0 = half * 32; c0 < a.NO; c0 += 64) {
+      for (int c0 = part * 32; c0 < a.NO; c0 += 32 * (kFwWarps / 4)) {
+        const float bl = c0 + lane < a.NO ? a.b3[c0 + lane] : 0.f;
         uint32_t v[32];
         tmem_ld32(tm + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
+        float o[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) o[j] = __uint_as_float(v[j]) + __shfl_sync(0xffffffffu, bl, j);
         if (rv) {
           float* y = a.Y + (size_t)(m0 + r) * a.ldy + c0;
 #pragma unroll
           for (int g = 0; g < 8; ++g)
             if (c0 + g * 4 < a.NO)
-              *reinterpret_cast<float4*>(y + g * 4) =
-                  make_float4(__uint_as_float(v[g * 4]) + a.b3[c0 + g * 4], __uint_as_float(v[g * 4 + 1]) + a.b3[c0 + g * 4 + 1],
-                              __uint_as_float(v[g * 4 + 2]) + a.b3[c0 + g * 4 + 2],
-                              __uint_as_float(v[g * 4 + 3]) + a.b3[c0 + g * 4 + 3]);
+              *reinterpret_cast<float4*>(y + g * 4) = make_float4(o[g * 4], o[g * 4 + 1], o[g * 4 + 2], o[g * 4 + 3]);
         }
       }
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();  // TMEM columns and the row tile are reused by the next tile
+    __syncthreads();  // TMEM columns are reused by the next tile
   }
   asm volatile("cp.async.wait_all;" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -671,14 +708,15 @@ inline int launch_mlp_fwd3(const MlpFwdArgs& a, cudaStream_t s) {
       a.ldx < a.K1 || (a.ldy % 4) || a.ldy < a.NO || !a16(a.X) || !a16(a.W1) || !a16(a.W2) || !a16(a.W3) ||
       !a16(a.Y))
     return NSK_ERR_ARG;
+  constexpr int kFwSmemMax = 226 * 1024;  // the per-block limit (227 KB) minus the static area (1 KB)
   int smem = fw_smem_bytes(a);
-  if (smem > 224 * 1024) return NSK_ERR_ARG;
+  if (smem > kFwSmemMax) return NSK_ERR_ARG;
   smem = smem < kRbSmemMin ? kRbSmemMin : smem;  // one CTA per SM: it owns all 512 TMEM columns
   static bool attr_done = false;
   static int sms = 0;
   if (!attr_done) {
     int dev = 0;
-    if (cudaFuncSetAttribute(k_mlp_fwd3, cudaFuncAttributeMaxDynamicSharedMemorySize, 224 * 1024) != cudaSuccess ||
+    if (cudaFuncSetAttribute(k_mlp_fwd3, cudaFuncAttributeMaxDynamicSharedMemorySize, kFwSmemMax) != cudaSuccess ||
         cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
       cudaGetLastError();
