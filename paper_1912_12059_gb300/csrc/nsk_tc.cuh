@@ -83,18 +83,35 @@ __device__ __forceinline__ uint32_t core_off(int r, int k) {
 }
 
 // erf after Abramowitz and Stegun, Handbook of Mathematical Functions, Eq. 7.1.26 (a rational
-// approximation due to Hastings): erf(x) = 1 - t (a1 + t (a2 + t (a3 + t (a4 + t a5)))) exp(-x^2),
-// t = 1 / (1 + p x) for x >= 0, odd extension; absolute error <= 1.5e-7 (plus FP32 rounding).
-// Two special-function-unit operations and six FMAs: the GELU epilogues are bound by it.
-__device__ __forceinline__ float erf_as(float x) {
-  const float ax = fabsf(x);
-  const float t = __fdividef(1.0f, fmaf(0.3275911f, ax, 1.0f));
-  const float poly =
-      t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.061405429f, -1.453152027f), 1.421413741f), -0.284496736f), 0.254829592f);
-  return copysignf(fmaf(-poly, __expf(-ax * ax), 1.0f), x);
+// approximation due to Hastings): erf(y) = 1 - t (a1 + t (a2 + t (a3 + t (a4 + t a5)))) exp(-y^2),
+// t = 1 / (1 + p y) for y >= 0, odd extension; absolute error <= 1.5e-7 (plus FP32 rounding).
+// The GELU epilogues are bound by it, so it is written for few instructions: the argument is
+// scaled once, w = x sqrt(log2(e) / 2), so that exp(-y^2) = 2^(-w^2) and p y = (p / sqrt(log2 e)) |w|
+// with y = |x| / sqrt 2; the reciprocal and the power of two are the hardware approximations
+// (about 1 and 2 ulp), denormal results flushed to zero.
+__device__ __forceinline__ float fast_rcp(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float fast_ex2(float x) {
+  float r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
 }
 // GELU(x) = x Phi(x) = x (1 + erf(x / sqrt 2)) / 2
-__device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.0f + erf_as(x * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu(float x) {
+  constexpr float kW = 0.84932180028801904f;   // sqrt(log2(e) / 2)
+  constexpr float kP = 0.27273748087922250f;   // 0.3275911 / sqrt(log2(e))
+  const float w = x * kW;
+  const float aw = fabsf(w);
+  const float t = fast_rcp(fmaf(kP, aw, 1.0f));
+  const float poly =
+      t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.061405429f, -1.453152027f), 1.421413741f), -0.284496736f), 0.254829592f);
+  const float erf_abs = fmaf(-poly, fast_ex2(-(w * w)), 1.0f);  // erf(|x| / sqrt 2)
+  const float h = 0.5f * x;
+  return fmaf(h, copysignf(erf_abs, x), h);
+}
 __device__ __forceinline__ float gelu_grad(float x) {
   return 0.5f * (1.0f + erff(x * 0.70710678118654752f)) + x * 0.3989422804014327f * __expf(-0.5f * x * x);
 }
