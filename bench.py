@@ -216,6 +216,22 @@ def run_reference(args, wl, rank, world):
 
 
 # ---------------------------------------------------------------- GPU arm
+def aggregate_ranks(ms, e2e_s, nodes, world, device):
+    """Whole-job figures of a weak-scaling run (every rank advances its own instance): the
+    slowest rank's device time and end-to-end time, and the nodes of all ranks (collectives over
+    the default process group, on tensors of `device`)."""
+    if world <= 1:
+        return ms, e2e_s, nodes
+    import torch
+    import torch.distributed as dist
+
+    tt = torch.tensor([ms, e2e_s], device=device, dtype=torch.float64)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    nn = torch.tensor([float(nodes)], device=device, dtype=torch.float64)
+    dist.all_reduce(nn, op=dist.ReduceOp.SUM)
+    return float(tt[0]), float(tt[1]), float(nn[0])
+
+
 def run_gpu(args, wl, rank, world):
     import torch
     import torch.distributed as dist
@@ -283,16 +299,7 @@ def run_gpu(args, wl, rank, world):
     barrier()
 
     # aggregate over ranks: total units / max time
-    t_max = ms
-    e2e_max = e2e_s
-    total_nodes = nodes
-    if world > 1:
-        tt = torch.tensor([ms, e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max, e2e_max = float(tt[0]), float(tt[1])
-        nn = torch.tensor([float(nodes)], device="cuda", dtype=torch.float64)
-        dist.all_reduce(nn, op=dist.ReduceOp.SUM)
-        total_nodes = float(nn[0])
+    t_max, e2e_max, total_nodes = aggregate_ranks(ms, e2e_s, nodes, world, "cuda")
     value = total_nodes * 5 * args.steps / (t_max / 1e3)
     e2e_value = total_nodes * 5 * e2e_steps / e2e_max
 
