@@ -24,6 +24,8 @@ NODES_GAUSS = 0
 NODES_LOBATTO = 1
 FLUX_LF = 0    # local Lax-Friedrichs
 FLUX_HLLC = 1  # HLLC (barotropic, modified pressure)
+MODEL_RELAXATION = 0  # relaxation model II: state (rho, m, c)
+MODEL_NSK = 1         # original NSK equations: state (rho, m)
 
 
 class OrcSetup(C.Structure):
@@ -41,6 +43,7 @@ class OrcSetup(C.Structure):
         ("mu", C.c_double),
         ("c_dissipation", C.c_int),
         ("flux", C.c_int),
+        ("model", C.c_int),
     ]
 
 
@@ -81,6 +84,7 @@ def lib():
         L.orc_lift.argtypes = [sp, dp, dp]
         L.orc_rhs.argtypes = [sp, dp, dp]
         L.orc_numflux.argtypes = [sp, C.c_int, dp, dp, dp]
+        L.orc_lift2.argtypes = [sp, dp, dp]
         L.orc_lsrk4.argtypes = [sp, dp, C.c_double, C.c_int]
         L.orc_timestep.argtypes = [sp, dp, C.c_double, dp]
         L.orc_diagnostics.argtypes = [sp, dp, dp, dp, dp]
@@ -166,7 +170,7 @@ class Oracle:
     [nvar][E][npe] (variables rho, rho v_1..rho v_dim, c)."""
 
     def __init__(self, dim, nelem, lo, hi, N, node_type=NODES_GAUSS, T=0.85, kappa=1e-4, alpha=1e3,
-                 beta=1e-3, mu=1e-3, c_dissipation=0, flux=FLUX_LF):
+                 beta=1e-3, mu=1e-3, c_dissipation=0, flux=FLUX_LF, model=MODEL_RELAXATION):
         s = OrcSetup()
         s.dim = dim
         ne = list(nelem) + [1] * (3 - len(nelem))
@@ -181,13 +185,14 @@ class Oracle:
         s.T, s.kappa, s.alpha, s.beta, s.mu = T, kappa, alpha, beta, mu
         s.c_dissipation = c_dissipation
         s.flux = flux
+        s.model = model
         self.s = s
         self.dim = dim
         self.N = N
         self.np = N + 1
         self.npe = (N + 1) ** dim
         self.E = int(np.prod(ne[:dim]))
-        self.nvar = dim + 2
+        self.nvar = dim + 1 if model == MODEL_NSK else dim + 2
         self.nq = dim * (dim + 1)
         self.nelem = ne[:dim]
         self.lo, self.hi = lo[:dim], hi[:dim]
@@ -225,6 +230,13 @@ class Oracle:
         R = np.zeros_like(U)
         _check(lib().orc_rhs(C.byref(self.s), _ptr(U), _ptr(R)), "orc_rhs")
         return R
+
+    def lift2(self, U):
+        """Original NSK: the second lifting, lap rho = div(grad rho), [E][npe]."""
+        U = np.ascontiguousarray(U, dtype=np.float64)
+        Q2 = np.zeros((self.E, self.npe))
+        _check(lib().orc_lift2(C.byref(self.s), _ptr(U), _ptr(Q2)), "orc_lift2")
+        return Q2
 
     def numflux(self, k, UL, UR):
         """Convective numerical flux (LF or HLLC per the setup) of one face with normal +e_k."""

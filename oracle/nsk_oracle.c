@@ -1,6 +1,7 @@
 /*
  * nsk_oracle.c -- TEST INFRASTRUCTURE ONLY: plain FP64 CPU reference of the
- * DGSEM discretisation of relaxation model II (arXiv:1912.12059).
+ * DGSEM discretisation of relaxation model II (arXiv:1912.12059), and of the original
+ * third-order NSK equations it approximates (Sec. 2.2, second BR1 lifting of Sec. 3.1).
  *
  * Written for a reader checking it against the paper by eye: element by
  * element, face by face, line by line, with the weak form of Sec. 3.1
@@ -261,7 +262,7 @@ void orc_lsrk4_coeffs(double* A, double* B, double* C) {
 /* ------------------------------------------------------------------------ */
 
 typedef struct {
-  int d, np, npe, nvar, nq;
+  int d, np, npe, nvar, nq, model;
   long E;
   int ne[3];
   long se[3]; /* element strides */
@@ -274,9 +275,11 @@ static int make_mesh(const orc_setup* s, mesh_t* m) {
   if (s->dim < 1 || s->dim > 3) return ORC_ERR_ARG;
   if (s->N < 1 || s->N >= ORC_MAXNP) return ORC_ERR_ARG;
   memset(m, 0, sizeof(*m));
+  if (s->model != 0 && s->model != 1) return ORC_ERR_ARG;
   m->d = s->dim;
+  m->model = s->model;
   m->np = s->N + 1;
-  m->nvar = s->dim + 2;
+  m->nvar = s->model == 1 ? s->dim + 1 : s->dim + 2;
   m->nq = s->dim * (s->dim + 1);
   m->npe = 1;
   m->E = 1;
@@ -325,10 +328,12 @@ static double trace(const mesh_t* m, const double* f, long e, int k, int n0, int
 
 static int admissible(double rho) { return rho > 0.0 && rho < 1.0 / VDW_B && isfinite(rho); }
 
-/* primitive variables w = (v_1..v_d, c) of a conservative state U = (rho, m, c) */
-static void cons_to_prim(int d, const double* U, double* w) {
+/* lifted primitive variables: w = (v_1..v_d, c) of a model II state U = (rho, m, c);
+ * w = (v_1..v_d, rho) of an original NSK state U = (rho, m) */
+static void cons_to_prim(const mesh_t* m, const double* U, double* w) {
+  const int d = m->d;
   for (int a = 0; a < d; ++a) w[a] = U[1 + a] / U[0];
-  w[d] = U[d + 1];
+  w[d] = m->model == 1 ? U[0] : U[d + 1];
 }
 
 /* ------------------------------------------------------------------------ */
@@ -448,7 +453,7 @@ static int lift(const orc_setup* s, const mesh_t* m, const double* U, double* Q)
       double Un[5], wn[4];
       for (int v = 0; v < m->nvar; ++v) Un[v] = U[v * nn + e * npe + n];
       if (!admissible(Un[0])) status = ORC_ERR_NONPHYSICAL;
-      cons_to_prim(d, Un, wn);
+      cons_to_prim(m, Un, wn);
       for (int q = 0; q < nw; ++q) W[q * nn + e * npe + n] = wn[q];
     }
   for (long e = 0; e < E; ++e) {
@@ -468,10 +473,10 @@ static int lift(const orc_setup* s, const mesh_t* m, const double* U, double* Q)
         if (!admissible(Um[0]) || !admissible(Up[0]) || !admissible(UnbM[0]) || !admissible(UnbP[0]))
           status = ORC_ERR_NONPHYSICAL;
         double wm[4], wp[4], wnm[4], wnp[4], wsm[4], wsp[4];
-        cons_to_prim(d, Um, wm);
-        cons_to_prim(d, Up, wp);
-        cons_to_prim(d, UnbM, wnm);
-        cons_to_prim(d, UnbP, wnp);
+        cons_to_prim(m, Um, wm);
+        cons_to_prim(m, Up, wp);
+        cons_to_prim(m, UnbM, wnm);
+        cons_to_prim(m, UnbP, wnp);
         for (int q = 0; q < nw; ++q) {
           wsm[q] = 0.5 * (wm[q] + wnm[q]);
           wsp[q] = 0.5 * (wp[q] + wnp[q]);
@@ -599,12 +604,169 @@ static int residual(const orc_setup* s, const mesh_t* m, const double* U, double
   return status;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Original NSK equations, Sec. 2.2: state (rho, m), Eqs. (nsk_1), (nsk_2),    */
+/*   F_k = (m_k, m_k v + p e_k - tau_{.k} - tau^K_{.k}),                       */
+/*   tau = mu (grad v + grad v^T - 2/3 div v I)           Eq. (stress_nse)     */
+/*   tau^K = kappa (rho lap rho + |grad rho|^2 / 2) I - kappa grad rho (x) grad rho, Eq. (stress_nsk) */
+/* with grad v and grad rho from the BR1 lifting of w = (v, rho) and lap rho  */
+/* from the second BR1 lifting of grad rho (Sec. 3.1); central numerical flux */
+/* for the convective part (Sec. 3.1: the central flux is used for the       */
+/* original NSK equations) and the BR1 mean of the viscous and Korteweg parts. */
+/* ------------------------------------------------------------------------ */
+
+/* second lifting: Q2 = sum_k d/dx_k (grad rho)_k in weak form with the central flux of the
+ * traces of (grad rho)_k on the faces of direction k */
+static void lift2(const mesh_t* m, const double* Q, double* Q2) {
+  const int d = m->d, np = m->np, npe = m->npe, nw = d + 1;
+  const long E = m->E, nn = E * npe;
+  for (long i = 0; i < nn; ++i) Q2[i] = 0.0;
+  for (long e = 0; e < E; ++e) {
+    for (int k = 0; k < d; ++k) {
+      const double* g = Q + (long)(k * nw + d) * nn; /* (grad rho)_k */
+      const long eL = neighbour(m, e, k, -1), eR = neighbour(m, e, k, +1);
+      for (int n0 = 0; n0 < npe; ++n0) {
+        if (node_coord(m, n0, k) != 0) continue;
+        const double gsm = 0.5 * (trace(m, g, e, k, n0, -1) + trace(m, g, eL, k, n0, +1));
+        const double gsp = 0.5 * (trace(m, g, e, k, n0, +1) + trace(m, g, eR, k, n0, -1));
+        for (int i = 0; i < np; ++i) {
+          const int node = n0 + i * m->sn[k];
+          double vol = 0.0;
+          for (int j = 0; j < np; ++j) vol += m->w[j] * g[e * npe + n0 + j * m->sn[k]] * m->D[j * np + i];
+          vol /= m->w[i];
+          const double surf = (gsp * m->Lp[i] - gsm * m->Lm[i]) / m->w[i];
+          Q2[e * npe + node] += (2.0 / m->h[k]) * (surf - vol);
+        }
+      }
+    }
+  }
+}
+
+/* viscous plus Korteweg flux in direction k, (0, tau_{.k} + tau^K_{.k}), from rho, the lifted
+ * gradients Q (Q[k*(d+1)+a] = d v_a/dx_k, Q[k*(d+1)+d] = d rho/dx_k) and lap rho */
+static void visc_kort_flux(const orc_setup* s, int d, int k, double rho, const double* Q, double lap, double* f) {
+  double div = 0.0, g2 = 0.0;
+  for (int a = 0; a < d; ++a) {
+    div += Q[a * (d + 1) + a];
+    g2 += Q[a * (d + 1) + d] * Q[a * (d + 1) + d];
+  }
+  f[0] = 0.0;
+  for (int a = 0; a < d; ++a) {
+    double t = Q[k * (d + 1) + a] + Q[a * (d + 1) + k];
+    if (a == k) t -= 2.0 / 3.0 * div;
+    double tk = -s->kappa * Q[a * (d + 1) + d] * Q[k * (d + 1) + d];
+    if (a == k) tk += s->kappa * (rho * lap + 0.5 * g2);
+    f[1 + a] = s->mu * t + tk;
+  }
+}
+
+/* convective flux of the original NSK equations: (m_k, m_k v + p e_k) with the VdW pressure */
+static void conv_flux_nsk(const orc_setup* s, int d, int k, const double* U, double* f) {
+  f[0] = U[1 + k];
+  for (int a = 0; a < d; ++a) f[1 + a] = U[1 + k] * (U[1 + a] / U[0]);
+  f[1 + k] += orc_pressure(s->T, U[0]);
+}
+
+static int residual_nsk(const orc_setup* s, const mesh_t* m, const double* U, double* R) {
+  const int d = m->d, np = m->np, npe = m->npe, nv = m->nvar, nq = m->nq;
+  const long E = m->E, nn = E * npe;
+  double* Q = (double*)malloc(sizeof(double) * (nq + 1) * nn);
+  if (!Q) return ORC_ERR_ARG;
+  double* Q2 = Q + (long)nq * nn;
+  int status = lift(s, m, U, Q);
+  lift2(m, Q, Q2);
+  for (long i = 0; i < nv * nn; ++i) R[i] = 0.0;
+
+  /* volume integral */
+  for (long e = 0; e < E; ++e) {
+    for (int k = 0; k < d; ++k) {
+      for (int n0 = 0; n0 < npe; ++n0) {
+        if (node_coord(m, n0, k) != 0) continue;
+        double F[ORC_MAXNP][4];
+        for (int j = 0; j < np; ++j) {
+          const int node = n0 + j * m->sn[k];
+          double Un[4], Qn[12], fc[4], fv[4];
+          for (int v = 0; v < nv; ++v) Un[v] = U[v * nn + e * npe + node];
+          for (int q = 0; q < nq; ++q) Qn[q] = Q[q * nn + e * npe + node];
+          conv_flux_nsk(s, d, k, Un, fc);
+          visc_kort_flux(s, d, k, Un[0], Qn, Q2[e * npe + node], fv);
+          for (int v = 0; v < nv; ++v) F[j][v] = fc[v] - fv[v];
+        }
+        for (int i = 0; i < np; ++i) {
+          const int node = n0 + i * m->sn[k];
+          for (int v = 0; v < nv; ++v) {
+            double vol = 0.0;
+            for (int j = 0; j < np; ++j) vol += m->w[j] * F[j][v] * m->D[j * np + i];
+            R[v * nn + e * npe + node] += (2.0 / m->h[k]) * vol / m->w[i];
+          }
+        }
+      }
+    }
+  }
+
+  /* surface integral, every face once (outward normal +e_k of element e) */
+  for (long e = 0; e < E; ++e) {
+    for (int k = 0; k < d; ++k) {
+      const long eR = neighbour(m, e, k, +1);
+      for (int n0 = 0; n0 < npe; ++n0) {
+        if (node_coord(m, n0, k) != 0) continue;
+        double UL[4], UR[4], QL[12], QR[12];
+        for (int v = 0; v < nv; ++v) {
+          UL[v] = trace(m, U + v * nn, e, k, n0, +1);
+          UR[v] = trace(m, U + v * nn, eR, k, n0, -1);
+        }
+        for (int q = 0; q < nq; ++q) {
+          QL[q] = trace(m, Q + q * nn, e, k, n0, +1);
+          QR[q] = trace(m, Q + q * nn, eR, k, n0, -1);
+        }
+        const double lapL = trace(m, Q2, e, k, n0, +1), lapR = trace(m, Q2, eR, k, n0, -1);
+        if (!admissible(UL[0]) || !admissible(UR[0])) {
+          status = ORC_ERR_NONPHYSICAL;
+          continue;
+        }
+        double fcL[4], fcR[4], fvL[4], fvR[4], Fs[4];
+        conv_flux_nsk(s, d, k, UL, fcL);
+        conv_flux_nsk(s, d, k, UR, fcR);
+        visc_kort_flux(s, d, k, UL[0], QL, lapL, fvL);
+        visc_kort_flux(s, d, k, UR[0], QR, lapR, fvR);
+        for (int v = 0; v < nv; ++v) Fs[v] = 0.5 * (fcL[v] + fcR[v]) - 0.5 * (fvL[v] + fvR[v]);
+        for (int i = 0; i < np; ++i) {
+          const int node = n0 + i * m->sn[k];
+          for (int v = 0; v < nv; ++v) {
+            R[v * nn + e * npe + node] -= (2.0 / m->h[k]) * Fs[v] * m->Lp[i] / m->w[i];
+            R[v * nn + eR * npe + node] += (2.0 / m->h[k]) * Fs[v] * m->Lm[i] / m->w[i];
+          }
+        }
+      }
+    }
+  }
+  free(Q);
+  return status;
+}
+
+int orc_lift2(const orc_setup* s, const double* U, double* Q2) {
+  mesh_t m;
+  int st = make_mesh(s, &m);
+  if (st) return st;
+  if (s->model != 1) return ORC_ERR_ARG;
+  double* Q = (double*)malloc(sizeof(double) * m.nq * m.E * m.npe);
+  if (!Q) return ORC_ERR_ARG;
+  st = lift(s, &m, U, Q);
+  lift2(&m, Q, Q2);
+  free(Q);
+  return st;
+}
+
+static int rhs_any(const orc_setup* s, const mesh_t* m, const double* U, double* R) {
+  return s->model == 1 ? residual_nsk(s, m, U, R) : residual(s, m, U, R);
+}
+
 int orc_rhs(const orc_setup* s, const double* U, double* R) {
   mesh_t m;
   int st = make_mesh(s, &m);
   if (st) return st;
-  if (!(s->beta > 0.0) || !(s->kappa >= 0.0) || !(s->mu >= 0.0)) return ORC_ERR_ARG;
-  return residual(s, &m, U, R);
+  if (!(s->kappa >= 0.0) || !(s->mu >= 0.0) || (s->model == 0 && !(s->beta > 0.0))) return ORC_ERR_ARG;
+  return rhs_any(s, &m, U, R);
 }
 
 /* 2N-storage update: K <- A_s K + dt R(U); U <- U + B_s K, s = 1..5. */
@@ -620,7 +782,7 @@ int orc_lsrk4(const orc_setup* s, double* U, double dt, int nsteps) {
   orc_lsrk4_coeffs(A, B, C);
   for (int step = 0; step < nsteps && st == ORC_OK; ++step) {
     for (int stage = 0; stage < 5; ++stage) {
-      st = residual(s, &m, U, R);
+      st = rhs_any(s, &m, U, R);
       if (st) break;
       for (long i = 0; i < len; ++i) {
         K[i] = A[stage] * K[i] + dt * R[i];
@@ -647,11 +809,14 @@ int orc_timestep(const orc_setup* s, const double* U, double cfl, double* dt) {
   if (st) return st;
   const int d = m.d;
   const long nn = m.E * m.npe;
-  double lam_max = 0.0;
+  double lam_max = 0.0, rho_max = 0.0;
   for (long p = 0; p < nn; ++p) {
     double rho = U[p];
     if (!admissible(rho)) return ORC_ERR_NONPHYSICAL;
-    double a = sound_speed(s, rho);
+    if (rho > rho_max) rho_max = rho;
+    /* original NSK: p' < 0 in the spinodal interval, where the first-order part has no real
+     * sound speed (Eq. nsk_eigenvalues); only the flow speed bounds the step there */
+    double a = s->model == 1 ? sqrt(fmax(orc_dpressure(s->T, rho), 0.0)) : sound_speed(s, rho);
     if (!isfinite(a)) return ORC_ERR_NONPHYSICAL;
     double sum = 0.0;
     for (int k = 0; k < d; ++k) sum += (fabs(U[(1 + k) * nn + p] / rho) + a) / m.h[k];
@@ -659,9 +824,18 @@ int orc_timestep(const orc_setup* s, const double* U, double cfl, double* dt) {
   }
   const double twoNp1 = 2.0 * s->N + 1.0;
   double dt_conv = cfl / (twoNp1 * lam_max);
-  double lamv = s->mu > s->kappa / s->beta ? s->mu : s->kappa / s->beta;
   double inv_h2 = 0.0;
   for (int k = 0; k < d; ++k) inv_h2 += 1.0 / (m.h[k] * m.h[k]);
+  if (s->model == 1) {
+    /* viscous bound with mu, and the dispersive Korteweg term: linearised about rho_0 the
+     * waves obey omega^2 = p' k^2 + kappa rho_0 k^4, i.e. |omega| ~ sqrt(kappa rho_0) k^2 like
+     * a diffusion with coefficient sqrt(kappa rho_max) (on the imaginary axis) */
+    const double lamk = s->mu > sqrt(s->kappa * rho_max) ? s->mu : sqrt(s->kappa * rho_max);
+    const double dt_k = lamk > 0.0 ? cfl / (twoNp1 * twoNp1 * lamk * inv_h2) : INFINITY;
+    *dt = dt_conv < dt_k ? dt_conv : dt_k;
+    return ORC_OK;
+  }
+  double lamv = s->mu > s->kappa / s->beta ? s->mu : s->kappa / s->beta;
   double dt_visc = lamv > 0.0 ? cfl / (twoNp1 * twoNp1 * lamv * inv_h2) : INFINITY;
   double dt_src = cfl * 4.6 * s->beta / s->alpha;
   double r = dt_conv;
@@ -693,7 +867,9 @@ int orc_diagnostics(const orc_setup* s, const double* U, double* mass, double* e
       double wq = J;
       for (int k = 0; k < d; ++k) wq *= m.w[node_coord(&m, n, k)];
       const long p = e * m.npe + n;
-      double rho = U[p], c = U[(d + 1) * nn + p];
+      /* original NSK: Eq. (original_energy_dynamic), capillary energy kappa/2 |grad rho|^2 with
+       * the lifted density gradient (the same slot of Q as grad c of model II) and no rho - c */
+      double rho = U[p], c = s->model == 1 ? rho : U[(d + 1) * nn + p];
       double m2 = 0.0, g2 = 0.0;
       for (int a = 0; a < d; ++a) {
         m2 += U[(1 + a) * nn + p] * U[(1 + a) * nn + p];

@@ -43,6 +43,9 @@ typedef struct {
   double mu;          /* viscosity eps = 1/Re */
   int c_dissipation;  /* 0: Lax-Friedrichs jump acts on rho and momentum only; 1: on c too */
   int flux;           /* convective numerical flux: 0 = local Lax-Friedrichs, 1 = HLLC */
+  int model;          /* 0 = relaxation model II (state rho, m, c); 1 = original NSK, Sec. 2.2
+                         Eqs. (nsk_1), (nsk_2), (stress_nse), (stress_nsk) (state rho, m; kappa is
+                         the capillarity of the Korteweg stress; alpha, beta, flux unused) */
 } orc_setup;
 
 /* Van-der-Waals EoS with the reduced parameters a=3, b=1/3, R=8/3. */
@@ -68,6 +71,9 @@ void orc_lsrk4_coeffs(double* A, double* B, double* C);
 
 /* Lifted gradients (BR1) of the primitive variables: Q[dim*(dim+1)][E][npe]. */
 int orc_lift(const orc_setup* s, const double* U, double* Q);
+/* Original NSK only: the second BR1 lifting (Sec. 3.1, the Q_2 equation), Q2 = div(grad rho)
+ * from the lifted density gradient, [E][npe]. */
+int orc_lift2(const orc_setup* s, const double* U, double* Q2);
 /* Semi-discrete residual R = dU/dt (same layout as U). */
 int orc_rhs(const orc_setup* s, const double* U, double* R);
 /* Convective numerical flux (LF or HLLC per s->flux) of one face with normal +e_k between the
