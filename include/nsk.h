@@ -71,6 +71,7 @@ enum { NSK_FP64 = 0, NSK_FP32_MIXED = 1 };
 enum { NSK_HOST = 0, NSK_DEVICE = 1 };
 enum { NSK_C_EXPLICIT = 0, NSK_C_LEARNED = 1 };
 enum { NSK_FLUX_LF = 0, NSK_FLUX_HLLC = 1 };
+enum { NSK_MODEL_RELAXATION = 0, NSK_MODEL_NSK = 1 };
 
 /* Create a context for a periodic box [lo, hi] (per direction) split into
  * nelem[k] equal elements per direction k < dim (entries k >= dim ignored),
@@ -110,6 +111,24 @@ int nsk_set_c_dissipation(nsk_ctx* ctx, int on);
  * zero under HLLC (nsk_set_c_dissipation acts on the Lax-Friedrichs flux only). Either flux
  * keeps the time-step bound of nsk_compute_dt. Returns NSK_ERR_ARG for another value. */
 int nsk_set_flux(nsk_ctx* ctx, int flux);
+
+/* Model of the context. NSK_MODEL_RELAXATION (default): parabolic relaxation model II,
+ * state (rho, m, c). NSK_MODEL_NSK: the original third-order NSK equations it approximates
+ * (Sec. 2.2, Eqs. (nsk_1), (nsk_2), (stress_nse), (stress_nsk)), state (rho, m_1..m_dim), i.e.
+ * dim + 1 variables in the same layout: F_k = (m_k, m_k v + p e_k - tau_{.k} - tau^K_{.k}),
+ * p the VdW pressure, tau^K = kappa (rho lap rho + |grad rho|^2/2) I - kappa grad rho (x) grad rho
+ * with kappa of nsk_set_params as the capillarity (alpha and beta unused), grad v and grad rho
+ * from the BR1 lifting of (v, rho), lap rho from a second BR1 lifting of grad rho (Sec. 3.1), the
+ * central convective face flux and the BR1 mean of the viscous and Korteweg face fluxes; no
+ * sources. FP64 contexts only (NSK_ERR_ARG otherwise); not with the learned closure or in a
+ * batch. nsk_lift returns the gradients of (v, rho); nsk_diagnostics the energy of Eq.
+ * (original_energy_dynamic) (l2_rho_minus_c = 0); nsk_compute_dt uses
+ * min(cfl / ((2N+1) max sum_k (|v_k| + sqrt(max(p', 0))) / h_k),
+ *     cfl / ((2N+1)^2 max(mu, sqrt(kappa max rho)) sum_k h_k^-2))
+ * (the dispersive Korteweg term acts like a diffusion with coefficient sqrt(kappa rho)).
+ * Switching the model allocates the two extra arrays the second lifting needs (once) and
+ * requires a new nsk_set_state (NSK_ERR_STATE until then). */
+int nsk_set_model(nsk_ctx* ctx, int model);
 
 /* Copy the state in (set) or out (get); layout above, FP64. Setting the state
  * also clears the Runge-Kutta register. */

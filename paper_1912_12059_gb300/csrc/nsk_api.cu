@@ -252,11 +252,18 @@ int sync_and_check(nsk_ctx* c) {
 
 int launch_stage(nsk_ctx* c, NskLaunch l) {
   // kernels 0..3 = prolong, lift, face, volume
-  const int mask = (l.traces_ready ? 0 : 1) | 2 |
-                   (l.mode == NSK_MODE_LIFT ? 0 : ((l.fused_face ? 0 : 4) | 8));
+  const int mask = c->p.model == NSK_MODEL_NSK ? (l.mode == NSK_MODE_LIFT ? 3 : 15)
+                                                : ((l.traces_ready ? 0 : 1) | 2 |
+                                                   (l.mode == NSK_MODE_LIFT ? 0 : ((l.fused_face ? 0 : 4) | 8)));
   l.ev = prof_group(c, mask);
   int r;
   const bool f32 = c->precision == NSK_FP32_MIXED;
+  if (c->p.model == NSK_MODEL_NSK) {  // the original NSK equations: their own stage kernels
+    r = nsk_launch_stage_nsk(c->dim, c->p, c->np, c->b, l, c->stream);
+    if (r < 0) return r;
+    c->launches += r;
+    return NSK_OK;
+  }
   switch (c->dim) {
     case 1: r = nsk_launch_stage_d1(c->p, c->np, f32, c->b, l, c->stream); break;
     case 2: r = nsk_launch_stage_d2(c->p, c->np, f32, c->b, l, c->stream); break;
@@ -288,7 +295,8 @@ int export_nodal(nsk_ctx* c, const void* src, int ncomp, double* dst, int where)
 
 void free_ctx(nsk_ctx* c) {
   if (!c) return;
-  void* ptrs[] = {c->b.U, c->b.K, c->b.Q, c->b.Utr, c->utr_alt, c->b.FVtr, c->b.Fstar, c->b.err, c->b.lam,
+  void* ptrs[] = {c->b.U, c->b.K, c->b.Q, c->b.Utr, c->utr_alt, c->b.FVtr, c->b.Fstar, c->b.Q2, c->b.Gtr,
+                  c->b.err, c->b.lam,
                   c->b.dt, c->b.part, c->rbuf, c->stage64, c->cl_X, c->cl_Y, c->cl_red, c->cl_mean};
   for (void* q : ptrs)
     if (q) cudaFree(q);
@@ -299,6 +307,14 @@ void free_ctx(nsk_ctx* c) {
 }  // namespace
 
 int nsk_ctx_launch_stage(nsk_ctx* c, NskLaunch l) { return launch_stage(c, l); }
+
+namespace {
+// device time step of the context's model (kernel launches issued, or an NSK_ERR_* code)
+int launch_dt(nsk_ctx* c, double cfl) {
+  if (c->p.model == NSK_MODEL_NSK) return nsk_launch_dt_nsk(c->p, c->dim, c->b, cfl, c->np - 1, c->stream);
+  return nsk_launch_dt(c->p, c->dim, c->np, c->precision == NSK_FP32_MIXED, c->b, cfl, c->stream);
+}
+}  // namespace
 
 extern "C" {
 
@@ -400,7 +416,7 @@ int nsk_init_mesh(nsk_ctx** out, int dim, const int nelem[3], const double lo[3]
       {&c->b.FVtr, rs * (dim + 1) * faces},
       {&c->b.Fstar, rs * c->nvar * c->E * dim * c->nfn},
       {(void**)&c->b.err, sizeof(int)},
-      {(void**)&c->b.lam, sizeof(unsigned long long)},
+      {(void**)&c->b.lam, 2 * sizeof(unsigned long long)},
       {(void**)&c->b.dt, sizeof(double)},
       {(void**)&c->b.part, sizeof(double) * (3 * (size_t)c->b.nparts + 3)},
       {&c->rbuf, rs * c->nvar * nn},
@@ -444,6 +460,26 @@ int nsk_set_params(nsk_ctx* c, double T, double kappa, double alpha, double beta
 int nsk_set_c_dissipation(nsk_ctx* c, int on) {
   if (!c) return NSK_ERR_ARG;
   c->p.c_diss = on ? 1 : 0;
+  return NSK_OK;
+}
+
+int nsk_set_model(nsk_ctx* c, int model) {
+  if (!c || (model != NSK_MODEL_RELAXATION && model != NSK_MODEL_NSK)) return NSK_ERR_ARG;
+  if (model == NSK_MODEL_NSK) {
+    if (c->precision != NSK_FP64) return NSK_ERR_ARG;
+    if (c->closure_mode == NSK_C_LEARNED) return NSK_ERR_STATE;
+    if (!c->b.Q2) {  // lap rho, and the traces of grad rho
+      const size_t faces = (size_t)c->E * 2 * c->dim * c->nfn;
+      if (cudaMalloc(&c->b.Q2, sizeof(double) * (size_t)c->nn) != cudaSuccess ||
+          cudaMalloc(&c->b.Gtr, sizeof(double) * faces) != cudaSuccess) {
+        cudaGetLastError();
+        return NSK_ERR_NOMEM;
+      }
+    }
+  }
+  c->p.model = model;
+  c->nvar = model == NSK_MODEL_NSK ? c->dim + 1 : c->dim + 2;
+  c->state_set = false;  // the state layout changed
   return NSK_OK;
 }
 
@@ -534,7 +570,7 @@ int nsk_lift(nsk_ctx* c, double* Q, int where) {
 int nsk_compute_dt(nsk_ctx* c, double cfl, double* dt_out) {
   if (!c || !dt_out || !(cfl > 0.0)) return NSK_ERR_ARG;
   if (!c->state_set) return NSK_ERR_STATE;
-  int r = nsk_launch_dt(c->p, c->dim, c->np, c->precision == NSK_FP32_MIXED, c->b, cfl, c->stream);
+  int r = launch_dt(c, cfl);
   if (r < 0) return r;
   c->launches += r;
   if (cudaMemcpyAsync(dt_out, c->b.dt, sizeof(double), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
@@ -549,7 +585,7 @@ int nsk_step(nsk_ctx* c, double dt, int nsteps) {
   bool ready = false;  // b.Utr holds the traces of U
   for (int s = 0; s < nsteps; ++s) {
     if (adaptive) {
-      int r = nsk_launch_dt(c->p, c->dim, c->np, c->precision == NSK_FP32_MIXED, c->b, -dt, c->stream);
+      int r = launch_dt(c, -dt);
       if (r < 0) return r;
       c->launches += r;
     }
@@ -561,7 +597,7 @@ int nsk_step(nsk_ctx* c, double dt, int nsteps) {
       }
       NskLaunch l = {NSK_MODE_LSRK, nullptr, kA[st], kB[st], adaptive ? c->b.dt : nullptr, dt, nullptr, c->tpb, c->fused_face};
       // the volume kernel writes the traces of the updated state for the next stage of this call
-      const bool write = !(s == nsteps - 1 && st == 4);
+      const bool write = c->p.model != NSK_MODEL_NSK && !(s == nsteps - 1 && st == 4);
       l.traces_ready = ready;
       l.utr_next = write ? (c->fused_face ? c->utr_alt : c->b.Utr) : nullptr;
       int r = launch_stage(c, l);

@@ -525,7 +525,8 @@ int nsk_batch_create(nsk_batch** out, int n, nsk_ctx* const* instances) {
   const int prec = instances[0] ? instances[0]->precision : -1;
   for (int i = 0; i < n; ++i) {
     nsk_ctx* c = instances[i];
-    if (!c || c->dim != 3 || (c->np != 4 && c->np != 5) || c->precision != prec) return NSK_ERR_ARG;
+    if (!c || c->dim != 3 || (c->np != 4 && c->np != 5) || c->precision != prec || c->p.model != NSK_MODEL_RELAXATION)
+      return NSK_ERR_ARG;
     if (!c->state_set) return NSK_ERR_STATE;
   }
   nsk_batch* bt = new (std::nothrow) nsk_batch();

@@ -75,6 +75,7 @@ struct NskParams {
   double T, kappa, alpha, beta, mu;
   double jac;      // J = prod_k h_k / 2
   int closure;     // 1: the c equation is replaced by the learned closure (dt without its bounds)
+  int model;       // NSK_MODEL_RELAXATION (state rho, m, c) or NSK_MODEL_NSK (state rho, m)
   // EoS constants: p_alpha = t8 rho q + pa2 rho^2, p_alpha' = t24 q^2 + dpa1 rho, q = 1/(3 - rho)
   double t8, t24, pa2, dpa1;
   float t8f, t24f, pa2f, dpa1f;
@@ -107,6 +108,9 @@ struct NskBuffers {
   double* dt;    // device time step
   double* part;  // diagnostics partial sums [nblocks][3]
   int nparts;
+  // original NSK equations only (NULL otherwise)
+  void* Gtr;     // [2d][E][nfn] traces of (grad rho)_k on the faces of direction k
+  void* Q2;      // [E][npe] lap rho from the second lifting
 };
 
 // What one stage pipeline launch should do.
@@ -133,6 +137,10 @@ int nsk_launch_stage_d1(const NskParams& p, int np, bool fp32, const NskBuffers&
                         cudaStream_t s);
 int nsk_launch_stage_d2(const NskParams& p, int np, bool fp32, const NskBuffers& b, const NskLaunch& l,
                         cudaStream_t s);
+// original NSK equations (FP64), nsk_orig.cu
+int nsk_launch_stage_nsk(int dim, const NskParams& p, int np, const NskBuffers& b, const NskLaunch& l,
+                         cudaStream_t s);
+int nsk_launch_dt_nsk(const NskParams& p, int dim, const NskBuffers& b, double cfl, int N, cudaStream_t s);
 int nsk_launch_stage_d3(const NskParams& p, int np, bool fp32, const NskBuffers& b, const NskLaunch& l,
                         cudaStream_t s);
 // dt: reduces max_nodes sum_k (|v_k| + sqrt(p_alpha'))/h_k into b.lam and writes b.dt.

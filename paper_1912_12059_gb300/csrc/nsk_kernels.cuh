@@ -218,7 +218,8 @@ __device__ __forceinline__ bool sound_ok(float d) { return __float_as_uint(d) < 
 // sum_j l_j(+-1) U_j along the line in direction k through face node fn of element e.
 // `u` points at node 0 of the element's first variable, variables `vs` apart (the
 // global array, or an element staged in shared memory: both give the same bits).
-template <typename R, int D, int NP>
+// NVAR conservative variables (d + 2 for model II, d + 1 for the original NSK equations).
+template <typename R, int D, int NP, int NVAR = Shape<D, NP>::NV>
 __device__ __forceinline__ void prolong_trace(const NskParams& p, const R* __restrict__ u, const size_t vs,
                                               R* __restrict__ Utr, const int e, const int slot, const int fn) {
   using S = Shape<D, NP>;
@@ -231,7 +232,7 @@ __device__ __forceinline__ void prolong_trace(const NskParams& p, const R* __res
   R* o = Utr + (size_t)slot * p.nfe + (e * S::NFN + fn);
   R rho = 0;
 #pragma unroll
-  for (int v = 0; v < S::NV; ++v) {
+  for (int v = 0; v < NVAR; ++v) {
     R acc = 0;
 #pragma unroll
     for (int j = 0; j < NP; ++j) acc = fma(L[j], ul[v * vs + j * st], acc);
@@ -241,8 +242,8 @@ __device__ __forceinline__ void prolong_trace(const NskParams& p, const R* __res
   if constexpr (TraceComps<R>::extra > 0) {
     // one division: d = 1/(rho (3 - rho)) gives 1/rho = (3 - rho) d and 1/(3 - rho) = rho d
     const R d = R(1) / (rho * (R(3) - rho));
-    o[S::NV * pl] = (R(3) - rho) * d;
-    o[(S::NV + 1) * pl] = rho * d;
+    o[NVAR * pl] = (R(3) - rho) * d;
+    o[(NVAR + 1) * pl] = rho * d;
   }
 }
 
@@ -298,12 +299,16 @@ __host__ __device__ constexpr int lift_smem() {
 // w = (v, c) formed from the conservative traces on both sides of each face; then the
 // face-normal viscous flux F^v_k = (tau_{.k}, (kappa/beta) c_{x_k}) traced onto the
 // element's own faces (FVtr[c][slot][E][nfn]) for the face flux.
-template <typename R, int D, int NP, int G>
+// MODEL 1 (original NSK equations, state (rho, m)): w = (v, rho), and instead of the viscous
+// flux traces the kernel writes into FVtr the trace of (grad rho)_k on the element's faces of
+// direction k ([2d][E][nfn], one component), the input of the second lifting.
+template <typename R, int D, int NP, int G, int MODEL = 0>
 __device__ __forceinline__ void lift_group(const NskParams& p, const R* __restrict__ U, const R* __restrict__ Utr,
                                            R* __restrict__ Q, R* __restrict__ FVtr, const long long e0, R* sm,
                                            int& eflag) {
   using S = Shape<D, NP>;
-  constexpr int NPE = S::NPE, NFN = S::NFN, NW = S::NW, NF = S::NF, NV = S::NV, NQ = S::NQ;
+  constexpr int NPE = S::NPE, NFN = S::NFN, NW = S::NW, NF = S::NF, NQ = S::NQ;
+  constexpr int NV = MODEL == 1 ? D + 1 : S::NV;  // conservative variables
   R* sw = sm;                  // [G][NW][NPE] primitive variables at the nodes
   R* sws = sm + G * NW * NPE;  // [G][NF][NW][NFN] central flux w* on the faces
   R* tb = sm + lift_work_smem<R, D, NP, G>();  // direction operators
@@ -322,7 +327,7 @@ __device__ __forceinline__ void lift_group(const NskParams& p, const R* __restri
     const R inv = R(1) / rho;
 #pragma unroll
     for (int a = 0; a < D; ++a) sw[(le * NW + a) * NPE + n] = U[(1 + a) * nn + g] * inv;
-    sw[(le * NW + D) * NPE + n] = U[(D + 1) * nn + g];
+    sw[(le * NW + D) * NPE + n] = MODEL == 1 ? rho : U[(D + 1) * nn + g];
     const ElemIdx ex = elem_idx<D>(p, e);
     for (int it = n; it < NF * NFN; it += NPE) {
       const int slot = it / NFN, fn = it % NFN, k = slot >> 1, s = slot & 1;
@@ -348,7 +353,7 @@ __device__ __forceinline__ void lift_group(const NskParams& p, const R* __restri
       R* ws = sws + ((le * NF + slot) * NW) * NFN + fn;
 #pragma unroll
       for (int a = 0; a < D; ++a) ws[a * NFN] = R(0.5) * fma(uo[1 + a], io, un[1 + a] * in);
-      ws[D * NFN] = R(0.5) * (uo[D + 1] + un[D + 1]);
+      ws[D * NFN] = MODEL == 1 ? R(0.5) * (uo[0] + un[0]) : R(0.5) * (uo[D + 1] + un[D + 1]);
     }
   }
   __syncthreads();
@@ -377,6 +382,29 @@ __device__ __forceinline__ void lift_group(const NskParams& p, const R* __restri
     }
   }
   __syncthreads();  // shared memory is reused below
+
+  if constexpr (MODEL == 1) {
+    R* sg = sm;  // [G][D][NPE] grad rho at the nodes
+    if (valid) {
+#pragma unroll
+      for (int k = 0; k < D; ++k) sg[(le * D + k) * NPE + n] = q[k * NW + D];
+    }
+    __syncthreads();
+    if (valid) {
+      for (int it = n; it < NF * NFN; it += NPE) {
+        const int slot = it / NFN, fn = it % NFN, k = slot >> 1;
+        const R* L = (slot & 1) ? t.lp : t.lm;
+        const int n0 = line_base<D, NP>(fn, k), st = node_stride<NP>(k);
+        const R* f = sg + (le * D + k) * NPE + n0;
+        R acc = 0;
+#pragma unroll
+        for (int j = 0; j < NP; ++j) acc = fma(L[j], f[j * st], acc);
+        FVtr[(size_t)slot * p.nfe + (e * NFN + fn)] = acc;
+      }
+    }
+    __syncthreads();  // the caller may reuse shared memory
+    return;
+  }
 
   R* sfv = sm;  // [G][D][NW][NPE] viscous flux F^v_k at the nodes
   if (valid) {
@@ -815,7 +843,8 @@ __global__ void __launch_bounds__(256) k_diag(const NskParams p, const R* __rest
     double wq = p.jac;
 #pragma unroll
     for (int k = 0; k < D; ++k) wq *= p.td.w[coord<NP>(n, k)];
-    const double rho = (double)U[g], c = (double)U[(D + 1) * nn + g];
+    // the original NSK state has no c: its capillary energy uses grad rho (same slot of Q)
+    const double rho = (double)U[g], c = p.model == NSK_MODEL_NSK ? rho : (double)U[(D + 1) * nn + g];
     double m2 = 0.0, g2 = 0.0;
 #pragma unroll
     for (int a = 0; a < D; ++a) {

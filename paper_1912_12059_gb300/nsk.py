@@ -33,6 +33,8 @@ NSK_C_EXPLICIT = 0
 NSK_C_LEARNED = 1
 NSK_FLUX_LF = 0
 NSK_FLUX_HLLC = 1
+NSK_MODEL_RELAXATION = 0
+NSK_MODEL_NSK = 1
 
 #: every symbol include/nsk.h declares, with (restype, argtypes)
 _dp = C.POINTER(C.c_double)
@@ -42,6 +44,7 @@ SIGNATURES = {
     "nsk_set_params": (C.c_int, [C.c_void_p, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double]),
     "nsk_set_c_dissipation": (C.c_int, [C.c_void_p, C.c_int]),
     "nsk_set_flux": (C.c_int, [C.c_void_p, C.c_int]),
+    "nsk_set_model": (C.c_int, [C.c_void_p, C.c_int]),
     "nsk_set_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "nsk_get_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "nsk_node_coords": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
@@ -240,6 +243,15 @@ class Solver:
     def set_flux(self, flux):
         """NSK_FLUX_LF (default) or NSK_FLUX_HLLC."""
         _check(load_library().nsk_set_flux(self.ctx, int(flux)), "nsk_set_flux")
+
+    def set_model(self, model):
+        """NSK_MODEL_RELAXATION (default, state rho, m, c) or NSK_MODEL_NSK (original NSK
+        equations, state rho, m); a new set_state is required afterwards."""
+        L = load_library()
+        _check(L.nsk_set_model(self.ctx, int(model)), "nsk_set_model")
+        E, npe, nv = C.c_longlong(), C.c_int(), C.c_int()
+        _check(L.nsk_get_sizes(self.ctx, C.byref(E), C.byref(npe), C.byref(nv)), "nsk_get_sizes")
+        self.nvar = nv.value
 
     def set_state(self, U):
         ptr, where = _buf(U, self.nvar * self.n_nodes, False)
