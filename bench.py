@@ -329,6 +329,7 @@ def run_gpu(args, wl, rank, world):
     if U_after is not None:
         variants["fp32_mixed"] = measure_fp32_variant(args, wl, stream, U0, U_after, dt, peaks)
         variants["fp64_hllc"] = measure_hllc_variant(args, wl, stream, U0, U_after, dt)
+        variants["fp64_original_nsk"] = measure_nsk_variant(args, wl, stream, U0, dt)
 
     if rank != 0:
         return 0
@@ -463,6 +464,44 @@ def batch_vs_sequential_small(nsk, prec, n=64, steps=20):
     return {"instances": n, "nodes_total": nodes, "batched_value": batched, "sequential_value": seq,
             "schedule": {"tpb": tpb, "fused_face": fused, "kind": BATCH_KINDS[persistent]},
             "step_latency_ms_p50": sm[len(sm) // 2], "step_latency_ms_p99": sm[-1]}
+
+
+def measure_nsk_variant(args, wl, stream, U0, dt):
+    """The original third-order NSK equations (state rho, m; second BR1 lifting for lap rho) on the
+    same mesh and initial density and momentum, at the same dt: cost per step against model II,
+    and the explicit step size each model's own bound allows there."""
+    import torch
+
+    from paper_1912_12059_gb300 import nsk
+
+    s = nsk.Solver(wl.dim, wl.nelem, wl.N, list(wl.lo[:wl.dim]), list(wl.hi[:wl.dim]), wl.node_type,
+                   nsk.NSK_FP64, stream=stream.cuda_stream)
+    s.set_params(T=wl.T, kappa=wl.kappa, alpha=wl.alpha, beta=wl.beta, mu=wl.mu)
+    s.set_model(nsk.NSK_MODEL_NSK)
+    s.set_state(np.ascontiguousarray(U0[:wl.dim + 1]))
+    tpb, _ = pick_schedule(s, args.schedule)
+    dt_own = s.compute_dt(wl.cfl)
+    out = {"dtype": "f64", "model": "original NSK", "schedule": {"tpb": tpb}, "dt_model_ii": dt,
+           "dt_own_bound": dt_own}
+    try:
+        s.step(dt, args.warmup)
+        s.set_profiling(True)
+        s.get_profile(reset=True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        s.step(dt, args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        prof = s.get_profile(reset=True)
+        out.update({"value": wl.dofs * 5 * args.steps / (ms / 1e3), "unit": "DOF-updates/s",
+                    "ms_per_step": ms / args.steps,
+                    "kernels": {k: {"avg_ms": v[0] / max(v[1], 1), "launches": v[1]} for k, v in prof.items()}})
+    except nsk.NskError as ex:  # the central flux of the third-order system does not damp
+        out["error"] = str(ex)
+    s.close()
+    return out
 
 
 def measure_hllc_variant(args, wl, stream, U0, U_lf_after, dt):
