@@ -758,8 +758,14 @@ __global__ void __launch_bounds__(256) k_face(const NskParams p, const R* __rest
   if (eflag) atomicOr(err, eflag);
 }
 
+// FP32 volume kernel (separate face schedule): three quarters of an SM's threads resident
+template <typename R, int TPB, bool FUSED>
+__host__ __device__ constexpr int volume_min_blocks() {
+  return (sizeof(R) == 4 && !FUSED) ? (1536 / TPB > 0 ? 1536 / TPB : 1) : 1;
+}
+
 template <typename R, int D, int NP, int G, bool FUSED>
-__global__ void __launch_bounds__(G * Shape<D, NP>::NPE)
+__global__ void __launch_bounds__(G * Shape<D, NP>::NPE, (volume_min_blocks<R, G * Shape<D, NP>::NPE, FUSED>()))
     k_volume(const NskParams p, R* __restrict__ U, const R* __restrict__ Q, const R* __restrict__ Fstar,
              const R* __restrict__ Utr, const R* __restrict__ FVtr, R* __restrict__ K, R* __restrict__ Rout,
              const int mode, const R A, const R B, const double* __restrict__ dtp, const R dtv,
