@@ -733,7 +733,7 @@ __global__ void __launch_bounds__(256) k_prolong(const NskParams p, const R* __r
 // FP32 lifting: a full SM of resident threads (the loads of the face loop need the latency hiding)
 template <typename R, int TPB>
 __host__ __device__ constexpr int lift_min_blocks() {
-  return sizeof(R) == 4 ? (2048 / TPB > 0 ? 2048 / TPB : 1) : 1;
+  return sizeof(R) == 4 ? (1536 / TPB > 0 ? 1536 / TPB : 1) : 1;
 }
 
 template <typename R, int D, int NP, int G>
@@ -746,9 +746,9 @@ __global__ void __launch_bounds__(G * Shape<D, NP>::NPE, (lift_min_blocks<R, G *
   if (eflag) atomicOr(err, eflag);
 }
 
-// grid (ceil(E nfn / 256), d): blockIdx.y is the face direction
+// grid (ceil(E nfn / 256), d): blockIdx.y is the face direction; FP32: 75% of an SM's threads
 template <typename R, int D, int NP>
-__global__ void __launch_bounds__(256) k_face(const NskParams p, const R* __restrict__ Utr,
+__global__ void __launch_bounds__(256, (sizeof(R) == 4 ? 6 : 1)) k_face(const NskParams p, const R* __restrict__ Utr,
                                               const R* __restrict__ FVtr, R* __restrict__ Fstar,
                                               int* __restrict__ err) {
   using S = Shape<D, NP>;
