@@ -40,7 +40,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM bytes (read + write) per launch of the dominant kernels at 64^3 elements, N = 3, from one
 # ncu capture at 40^3 elements scaled by the element count (profiles/launches_fp64_collision3d_64cubed.md,
 # profiles/fp32_stage_kernels_collision3d.md); must be re-measured whenever those kernels change
-MEASURED_TRAFFIC = {("k_volume", 8, 262144): 4.69e9}
+MEASURED_TRAFFIC = {("k_volume", 8, 262144): 4.69e9, ("k_volume", 4, 262144): 2.70e9}
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
