@@ -139,7 +139,8 @@ int nsk_get_state(nsk_ctx* ctx, double* U, int where);
 int nsk_node_coords(nsk_ctx* ctx, double* x, int where);
 
 /* Semi-discrete residual R = dU/dt of the current state (Eq. weakformulation
- * with the fluxes and sources of Eq. fluxes_sources_model2), layout of U.
+ * with the fluxes and sources of Eq. fluxes_sources_model2, or of the original NSK
+ * equations, see nsk_set_model), layout of U.
  * t is the model time; the model is autonomous, so R does not depend on it. */
 int nsk_rhs(nsk_ctx* ctx, double t, double* Ut, int where);
 
@@ -151,14 +152,18 @@ int nsk_lift(nsk_ctx* ctx, double* Q, int where);
  * convective bound cfl / ((2N+1) max sum_k (|v_k| + sqrt(p_alpha'))/h_k), the
  * parabolic bound of Eq. (numerics_dfl) cfl / ((2N+1)^2 lambda_v sum_k h_k^-2)
  * with lambda_v = max(mu, kappa/beta) (Eq. numerics_nsk_visc_eigenvalues), and
- * the relaxation-source bound cfl * 4.6 * beta / alpha. Reduced in FP64. */
+ * the relaxation-source bound cfl * 4.6 * beta / alpha (with the learned closure
+ * lambda_v = mu and no source bound; for the original NSK equations see
+ * nsk_set_model). Reduced in FP64; dt also stays on the device for nsk_step. */
 int nsk_compute_dt(nsk_ctx* ctx, double cfl, double* dt_out);
 
 /* Advance the state by nsteps steps of the five-stage low-storage RK4 with
  * step dt (dt > 0), or, with dt <= 0, with nsk_compute_dt(ctx, -dt) recomputed
- * before every step (so dt = -0.5 means CFL 0.5). Returns after the work is
- * queued and checked: the call synchronises the stream once at the end to
- * read the error word. */
+ * before every step (so dt = -0.5 means CFL 0.5). Within one call the volume
+ * kernel of each stage writes the face traces of its updated state, so only
+ * the first stage of a call runs the prolongation pass (model II). Returns
+ * after the work is queued and checked: the call synchronises the stream once
+ * at the end to read the error word. */
 int nsk_step(nsk_ctx* ctx, double dt, int nsteps);
 
 /* Quadrature sums (FP64): mass sum w J rho; the total energy of the relaxation
