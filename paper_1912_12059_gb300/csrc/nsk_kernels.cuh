@@ -19,6 +19,7 @@
 #pragma once
 
 #include "nsk_internal.h"
+#include <type_traits>
 
 namespace nsk {
 
@@ -202,6 +203,23 @@ __device__ __forceinline__ int rho_flags(R rho) {
 // p_alpha' >= 0 and finite, on the bit pattern (a negative sign, NaN or infinity fail; so does -0)
 __device__ __forceinline__ bool sound_ok(double d) { return (unsigned)__double2hiint(d) < 0x7FF00000u; }
 __device__ __forceinline__ bool sound_ok(float d) { return __float_as_uint(d) < 0x7F800000u; }
+
+// Asynchronous global -> shared copy of one 4- or 8-byte value (cp.async, L1-allocating form);
+// both addresses are aligned to the value's size.
+template <typename R>
+__device__ __forceinline__ void cp_async_elem(R* sdst, const R* gsrc) {
+  static_assert(sizeof(R) == 4 || sizeof(R) == 8, "cp.async copies 4 or 8 bytes here");
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(sa), "l"(gsrc), "n"((int)sizeof(R)) : "memory");
+}
+// the same for 16 bytes (cp.async.cg, L2 only: each face value is read by two elements of
+// different blocks, so L1 allocation does not pay); both addresses 16-byte aligned
+__device__ __forceinline__ void cp_async_16(void* sdst, const void* gsrc) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // --------------------------------------------------------------------------
 // Stage bodies. Every stage kernel below (and the batched persistent kernel in
@@ -563,6 +581,26 @@ __device__ __forceinline__ void face_item(const NskParams& p, const R* __restric
   face_at<R, D, NP>(p, Utr, FVtr, Fstar, (int)k, e, fn, eflag);
 }
 
+// the NP values of one line from shared memory: 16-byte loads when a line fills whole
+// 16-byte units (f is then 16-byte aligned), else one value at a time
+template <typename R, int NP>
+__device__ __forceinline__ void load_line(const R* f, R (&x)[NP]) {
+  if constexpr ((NP * sizeof(R)) % 16 == 0) {
+    using V = typename std::conditional<sizeof(R) == 4, float4, double2>::type;
+    constexpr int W = 16 / (int)sizeof(R);
+#pragma unroll
+    for (int j = 0; j < NP; j += W) {
+      const V t = *reinterpret_cast<const V*>(f + j);
+      const R* tv = reinterpret_cast<const R*>(&t);
+#pragma unroll
+      for (int w = 0; w < W; ++w) x[j + w] = tv[w];
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < NP; ++j) x[j] = f[j];
+  }
+}
+
 // shared memory (in units of R) of volume_group
 template <typename R, int D, int NP, int G, bool FUSED>
 __host__ __device__ constexpr int volume_smem() {
@@ -588,7 +626,7 @@ __device__ __forceinline__ void volume_group(const NskParams& p, R* __restrict__
                                              R* sm, int& eflag, R* __restrict__ UtrNext = nullptr) {
   using S = Shape<D, NP>;
   constexpr int NPE = S::NPE, NFN = S::NFN, NW = S::NW, NV = S::NV, NQ = S::NQ, NF = S::NF;
-  R* sf = sm;                          // [G][D][NV][NPE] fluxes F_k at the nodes
+  R* sf = sm;                          // [G][D][NV][NFN][NP] fluxes F_k at the nodes, lines in k contiguous
   R* sfs = sm + G * D * NV * NPE;      // [G][NF][NV][NFN] fluxes of the element's faces
   R* tb = sfs + G * NF * NV * NFN;     // direction operators
   const auto& t = TabSel<R>::get(p);
@@ -598,6 +636,30 @@ __device__ __forceinline__ void volume_group(const NskParams& p, R* __restrict__
   const size_t nn = (size_t)p.nne;  // distance between the planes of two nodal variables
   const int g = e * NPE + n;
 
+  if constexpr (!FUSED) {
+    // Fstar[v][k][E][nfn] holds the flux on face (e, +k): slot 2k+1 is the element's own
+    // entry, slot 2k its -k neighbour's. Copied global -> shared asynchronously, so that the
+    // copies are in flight during the nodal loads and flux arithmetic below and hold no registers.
+    // A face's NFN values of one variable are contiguous on both sides: copied 16 bytes at a
+    // time when NFN values fill whole 16-byte units (the offsets below are then multiples of 16
+    // bytes: Fstar and the shared buffer start 16-byte aligned and nfe = E NFN).
+    constexpr int W = (NFN * (int)sizeof(R)) % 16 == 0 ? 16 / (int)sizeof(R) : 1;
+    constexpr int NFW = NFN / W;
+    if (valid) {
+      const ElemIdx ex = elem_idx<D>(p, e);
+      for (int it = n; it < NF * NV * NFW; it += NPE) {
+        const int fn = (it % NFW) * W, v = (it / NFW) % NV, slot = it / (NV * NFW), k = slot >> 1;
+        const int src = (slot & 1) ? e : nbr_of(p, ex, k, -1);
+        R* dst = sfs + ((le * NF + slot) * NV + v) * NFN + fn;
+        const R* srcp = Fstar + (size_t)(v * D + k) * p.nfe + (src * NFN + fn);
+        if constexpr (W > 1)
+          cp_async_16(dst, srcp);
+        else
+          cp_async_elem(dst, srcp);
+      }
+    }
+    cp_async_commit();
+  }
   stage_tables<R, D, NP>(t, tb);
   R u[NV], q[NQ], kin[NV];
   if (valid) {
@@ -624,7 +686,8 @@ __device__ __forceinline__ void volume_group(const NskParams& p, R* __restrict__
     const R mu = t.mu, kb = t.kb;
 #pragma unroll
     for (int k = 0; k < D; ++k) {
-      R* f = sf + ((le * D + k) * NV) * NPE + n;
+      // node n sits at position i_k of line face_node(n, k) in direction k
+      R* f = sf + ((le * D + k) * NV) * NPE + face_node<D, NP>(n, k) * NP + coord<NP>(n, k);
       f[0] = u[1 + k];
 #pragma unroll
       for (int a = 0; a < D; ++a) {
@@ -635,8 +698,8 @@ __device__ __forceinline__ void volume_group(const NskParams& p, R* __restrict__
       }
       f[(D + 1) * NPE] = -(kb * q[k * NW + D]);
     }
-    const ElemIdx ex = elem_idx<D>(p, e);
     if constexpr (FUSED) {
+      const ElemIdx ex = elem_idx<D>(p, e);
       for (int it = n; it < NF * NFN; it += NPE) {
         const int slot = it / NFN, fn = it % NFN, k = slot >> 1;
         R F[NV];
@@ -647,16 +710,9 @@ __device__ __forceinline__ void volume_group(const NskParams& p, R* __restrict__
 #pragma unroll
         for (int v = 0; v < NV; ++v) sfs[((le * NF + slot) * NV + v) * NFN + fn] = F[v];
       }
-    } else {
-      // Fstar[v][k][E][nfn] holds the flux on face (e, +k): slot 2k+1 is the element's own
-      // entry, slot 2k its -k neighbour's
-      for (int it = n; it < NF * NV * NFN; it += NPE) {
-        const int fn = it % NFN, v = (it / NFN) % NV, slot = it / (NV * NFN), k = slot >> 1;
-        const int src = (slot & 1) ? e : nbr_of(p, ex, k, -1);
-        sfs[((le * NF + slot) * NV + v) * NFN + fn] = Fstar[(size_t)(v * D + k) * p.nfe + (src * NFN + fn)];
-      }
     }
   }
+  if constexpr (!FUSED) cp_async_wait_all();
   __syncthreads();
 
   if (valid) {
@@ -668,17 +724,17 @@ __device__ __forceinline__ void volume_group(const NskParams& p, R* __restrict__
 #pragma unroll
     for (int k = 0; k < D; ++k) {
       const int i = coord<NP>(n, k), fn = face_node<D, NP>(n, k);
-      const int n0 = line_base<D, NP>(fn, k), st = node_stride<NP>(k);
       R dk[NP];
 #pragma unroll
       for (int j = 0; j < NP; ++j) dk[j] = tb[(k * NP + i) * NP + j];
       const R lpk = tb[D * NP * NP + k * NP + i], lmk = tb[D * NP * NP + D * NP + k * NP + i];
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
-        const R* f = sf + ((le * D + k) * NV + v) * NPE + n0;
+        R fl[NP];
+        load_line<R, NP>(sf + ((le * D + k) * NV + v) * NPE + fn * NP, fl);
         R acc = res[v];
 #pragma unroll
-        for (int j = 0; j < NP; ++j) acc = fma(dk[j], f[j * st], acc);
+        for (int j = 0; j < NP; ++j) acc = fma(dk[j], fl[j], acc);
         const R fp = sfs[((le * NF + 2 * k + 1) * NV + v) * NFN + fn];
         const R fm = sfs[((le * NF + 2 * k) * NV + v) * NFN + fn];
         res[v] = fma(fm, lmk, fma(-fp, lpk, acc));
@@ -730,10 +786,18 @@ __global__ void __launch_bounds__(256) k_prolong(const NskParams p, const R* __r
   }
 }
 
-// FP32 lifting: a full SM of resident threads (the loads of the face loop need the latency hiding)
+// blocks of TPB threads that fit in the given number of resident warps (a block holds whole
+// warps), at least one
+template <int TPB>
+__host__ __device__ constexpr int blocks_in_warps(int warps) {
+  return warps / ((TPB + 31) / 32) > 0 ? warps / ((TPB + 31) / 32) : 1;
+}
+
+// FP32 lifting: 48 resident warps, three quarters of an SM (the loads of the face loop need
+// the latency hiding)
 template <typename R, int TPB>
 __host__ __device__ constexpr int lift_min_blocks() {
-  return sizeof(R) == 4 ? (1536 / TPB > 0 ? 1536 / TPB : 1) : 1;
+  return sizeof(R) == 4 ? blocks_in_warps<TPB>(48) : 1;
 }
 
 template <typename R, int D, int NP, int G>
@@ -758,10 +822,10 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? 6 : 1)) k_face(const Ns
   if (eflag) atomicOr(err, eflag);
 }
 
-// FP32 volume kernel (separate face schedule): three quarters of an SM's threads resident
+// FP32 volume kernel (separate face schedule): 48 resident warps, three quarters of an SM
 template <typename R, int TPB, bool FUSED>
 __host__ __device__ constexpr int volume_min_blocks() {
-  return (sizeof(R) == 4 && !FUSED) ? (1536 / TPB > 0 ? 1536 / TPB : 1) : 1;
+  return (sizeof(R) == 4 && !FUSED) ? blocks_in_warps<TPB>(48) : 1;
 }
 
 template <typename R, int D, int NP, int G, bool FUSED>
@@ -770,7 +834,7 @@ __global__ void __launch_bounds__(G * Shape<D, NP>::NPE, (volume_min_blocks<R, G
              const R* __restrict__ Utr, const R* __restrict__ FVtr, R* __restrict__ K, R* __restrict__ Rout,
              const int mode, const R A, const R B, const double* __restrict__ dtp, const R dtv,
              int* __restrict__ err, R* __restrict__ UtrNext) {
-  __shared__ R sm[volume_smem<R, D, NP, G, FUSED>()];
+  __shared__ __align__(16) R sm[volume_smem<R, D, NP, G, FUSED>()];
   const R dt = dtp ? (R)*dtp : dtv;
   int eflag = 0;
   volume_group<R, D, NP, G, FUSED>(p, U, Q, Fstar, Utr, FVtr, K, Rout, mode, A, B, dt, (long long)blockIdx.x * G,
