@@ -155,6 +155,12 @@ void fill_coef(NskTab<R>& t, const NskParams& p) {
   }
   t.mu = (R)p.mu;
   t.kb = (R)(p.kappa / p.beta);
+  for (int i = 0; i < NSK_MAXNP; ++i) {
+    t.lpmu[i] = (R)(p.mu * td.lp[i]);
+    t.lmmu[i] = (R)(p.mu * td.lm[i]);
+    t.lpkb[i] = (R)(p.kappa / p.beta * td.lp[i]);
+    t.lmkb[i] = (R)(p.kappa / p.beta * td.lm[i]);
+  }
   t.alpha = (R)p.alpha;
   t.ab = (R)(p.alpha / p.beta);
 }

@@ -37,6 +37,9 @@ struct NskTab {
   // lpk = (2/h_k) lpw, lmk = (2/h_k) lmw
   R dk[3][NSK_MAXNP * NSK_MAXNP];
   R lpk[3][NSK_MAXNP], lmk[3][NSK_MAXNP];
+  // face interpolation with the viscous coefficients folded in (the lifting's traces of
+  // F^v: mu l(+-1) for the stress, (kappa/beta) l(+-1) for the c flux)
+  R lpmu[NSK_MAXNP], lmmu[NSK_MAXNP], lpkb[NSK_MAXNP], lmkb[NSK_MAXNP];
 };
 
 // Components of a face trace: the conservative variables, and in FP64 also

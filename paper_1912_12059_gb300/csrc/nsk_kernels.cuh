@@ -281,30 +281,75 @@ __device__ __forceinline__ void prolong_item(const NskParams& p, const R* __rest
 // Shared-memory copy of the direction operators (2/h_k folded in) of one precision:
 // [D][NP][NP] dk, then [D][NP] lpk, then [D][NP] lmk. Every thread of a warp reads its own
 // row i; from shared memory the distinct rows are served in one pass, where the kernel
-// parameter bank would serialise them.
+// parameter bank would serialise them. HALF: lpk and lmk scaled by 1/2 (exact), for the
+// kernels whose face values are stored doubled (the lifting's sums of two traces, the face
+// fluxes 2 F*).
 template <int D, int NP>
 __host__ __device__ constexpr int tab_smem() {
   return D * NP * NP + 2 * D * NP;
 }
-template <typename R, int D, int NP>
+template <typename R, int D, int NP, bool HALF = false>
 __device__ __forceinline__ void stage_tables(const NskTab<R>& t, R* tb) {
   for (int x = threadIdx.x; x < D * NP * NP; x += blockDim.x) {
     const int k = x / (NP * NP), r = x % (NP * NP);
     tb[x] = t.dk[k][(r / NP) * NSK_MAXNP + r % NP];
   }
   for (int x = threadIdx.x; x < D * NP; x += blockDim.x) {
-    tb[D * NP * NP + x] = t.lpk[x / NP][x % NP];
-    tb[D * NP * NP + D * NP + x] = t.lmk[x / NP][x % NP];
+    const R sc = HALF ? R(0.5) : R(1);
+    tb[D * NP * NP + x] = sc * t.lpk[x / NP][x % NP];
+    tb[D * NP * NP + D * NP + x] = sc * t.lmk[x / NP][x % NP];
   }
 }
 
+// the NP values of one line from shared memory: 16-byte loads when a line fills whole
+// 16-byte units (f is then 16-byte aligned), else one value at a time
+template <typename R, int NP>
+__device__ __forceinline__ void load_line(const R* f, R (&x)[NP]) {
+  if constexpr ((NP * sizeof(R)) % 16 == 0) {
+    using V = typename std::conditional<sizeof(R) == 4, float4, double2>::type;
+    constexpr int W = 16 / (int)sizeof(R);
+#pragma unroll
+    for (int j = 0; j < NP; j += W) {
+      const V t = *reinterpret_cast<const V*>(f + j);
+      const R* tv = reinterpret_cast<const R*>(&t);
+#pragma unroll
+      for (int w = 0; w < W; ++w) x[j + w] = tv[w];
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < NP; ++j) x[j] = f[j];
+  }
+}
+
+// node n at position i_k of line face_node(n, k): the nodes laid out with the lines in
+// direction k contiguous (k = 0 is the natural order)
+template <int D, int NP>
+__device__ __forceinline__ int line_pos(int n, int k) {
+  return face_node<D, NP>(n, k) * NP + coord<NP>(n, k);
+}
+
+// distance between two faces' central fluxes in the lifting's shared buffer: for faces of 16
+// nodes or more it is congruent to NFN modulo 32, so the face slots one warp writes in turn
+// fall on consecutive banks
+template <int D, int NP>
+__host__ __device__ constexpr int lift_slot_stride() {
+  using S = Shape<D, NP>;
+  return S::NFN >= 16 ? S::NW * S::NFN + ((S::NFN - S::NW * S::NFN) % 32 + 32) % 32 : S::NW * S::NFN;
+}
+// the lifting keeps one copy of the primitive variables per direction, lines contiguous, when
+// its lines load 16 bytes at a time and the block's buffers stay within 40 KB
+template <typename R, int D, int NP, int G>
+__host__ __device__ constexpr bool lift_lines() {
+  using S = Shape<D, NP>;
+  return D >= 2 && (NP * sizeof(R)) % 16 == 0 &&
+         (G * D * S::NW * S::NPE + G * S::NF * lift_slot_stride<D, NP>()) * (int)sizeof(R) <= 40 * 1024;
+}
 // shared memory (in units of R) of lift_group
 template <typename R, int D, int NP, int G>
 __host__ __device__ constexpr int lift_work_smem() {
   using S = Shape<D, NP>;
-  return (G * S::NW * S::NPE + G * S::NF * S::NW * S::NFN) > (G * D * S::NW * S::NPE)
-             ? (G * S::NW * S::NPE + G * S::NF * S::NW * S::NFN)
-             : (G * D * S::NW * S::NPE);
+  constexpr int front = G * (lift_lines<R, D, NP, G>() ? D : 1) * S::NW * S::NPE + G * S::NF * lift_slot_stride<D, NP>();
+  return front > G * D * S::NW * S::NPE ? front : G * D * S::NW * S::NPE;
 }
 template <typename R, int D, int NP, int G>
 __host__ __device__ constexpr int lift_smem() {
@@ -327,8 +372,10 @@ __device__ __forceinline__ void lift_group(const NskParams& p, const R* __restri
   using S = Shape<D, NP>;
   constexpr int NPE = S::NPE, NFN = S::NFN, NW = S::NW, NF = S::NF, NQ = S::NQ;
   constexpr int NV = MODEL == 1 ? D + 1 : S::NV;  // conservative variables
-  R* sw = sm;                  // [G][NW][NPE] primitive variables at the nodes
-  R* sws = sm + G * NW * NPE;  // [G][NF][NW][NFN] central flux w* on the faces
+  constexpr bool LINES = lift_lines<R, D, NP, G>();
+  constexpr int NCOPY = LINES ? D : 1, SWS = lift_slot_stride<D, NP>();
+  R* sw = sm;                           // [G][NCOPY][NW][NPE] primitive variables at the nodes
+  R* sws = sm + G * NCOPY * NW * NPE;   // [G][NF][SWS >= NW NFN] central flux w* on the faces
   R* tb = sm + lift_work_smem<R, D, NP, G>();  // direction operators
   const auto& t = TabSel<R>::get(p);
   const int le = threadIdx.x / NPE, n = threadIdx.x % NPE;
@@ -338,14 +385,21 @@ __device__ __forceinline__ void lift_group(const NskParams& p, const R* __restri
   const size_t pl = (size_t)NF * p.nfe;        // distance between the planes of two trace variables
   const int g = e * NPE + n;
 
-  stage_tables<R, D, NP>(t, tb);
+  stage_tables<R, D, NP, true>(t, tb);
   if (valid) {
     const R rho = U[g];
     eflag |= rho_flags(rho);
     const R inv = R(1) / rho;
+    R wn[NW];
 #pragma unroll
-    for (int a = 0; a < D; ++a) sw[(le * NW + a) * NPE + n] = U[(1 + a) * nn + g] * inv;
-    sw[(le * NW + D) * NPE + n] = MODEL == 1 ? rho : U[(D + 1) * nn + g];
+    for (int a = 0; a < D; ++a) wn[a] = U[(1 + a) * nn + g] * inv;
+    wn[D] = MODEL == 1 ? rho : U[(D + 1) * nn + g];
+#pragma unroll
+    for (int c = 0; c < NCOPY; ++c) {
+      const int pos = LINES ? line_pos<D, NP>(n, c) : n;
+#pragma unroll
+      for (int w = 0; w < NW; ++w) sw[((le * NCOPY + c) * NW + w) * NPE + pos] = wn[w];
+    }
     const ElemIdx ex = elem_idx<D>(p, e);
     for (int it = n; it < NF * NFN; it += NPE) {
       const int slot = it / NFN, fn = it % NFN, k = slot >> 1, s = slot & 1;
@@ -368,10 +422,11 @@ __device__ __forceinline__ void lift_group(const NskParams& p, const R* __restri
         io = R(1) / uo[0];
         in = R(1) / un[0];
       }
-      R* ws = sws + ((le * NF + slot) * NW) * NFN + fn;
+      // 2 w* (the 1/2 of the central flux is in the staged lpk, lmk: an exact scaling)
+      R* ws = sws + (le * NF + slot) * SWS + fn;
 #pragma unroll
-      for (int a = 0; a < D; ++a) ws[a * NFN] = R(0.5) * fma(uo[1 + a], io, un[1 + a] * in);
-      ws[D * NFN] = MODEL == 1 ? R(0.5) * (uo[0] + un[0]) : R(0.5) * (uo[D + 1] + un[D + 1]);
+      for (int a = 0; a < D; ++a) ws[a * NFN] = fma(uo[1 + a], io, un[1 + a] * in);
+      ws[D * NFN] = MODEL == 1 ? uo[0] + un[0] : uo[D + 1] + un[D + 1];
     }
   }
   __syncthreads();
@@ -388,12 +443,18 @@ __device__ __forceinline__ void lift_group(const NskParams& p, const R* __restri
       const R lpk = tb[D * NP * NP + k * NP + i], lmk = tb[D * NP * NP + D * NP + k * NP + i];
 #pragma unroll
       for (int w = 0; w < NW; ++w) {
-        const R* wl = sw + (le * NW + w) * NPE + n0;
+        R wl[NP];
+        if (LINES || k == 0) {  // the line is contiguous
+          load_line<R, NP>(sw + ((le * NCOPY + (LINES ? k : 0)) * NW + w) * NPE + (LINES ? fn * NP : n0), wl);
+        } else {
+#pragma unroll
+          for (int j = 0; j < NP; ++j) wl[j] = sw[(le * NW + w) * NPE + n0 + j * st];
+        }
         R vol = 0;
 #pragma unroll
-        for (int j = 0; j < NP; ++j) vol = fma(dk[j], wl[j * st], vol);
-        const R wp = sws[((le * NF + 2 * k + 1) * NW + w) * NFN + fn];
-        const R wm = sws[((le * NF + 2 * k) * NW + w) * NFN + fn];
+        for (int j = 0; j < NP; ++j) vol = fma(dk[j], wl[j], vol);
+        const R wp = sws[(le * NF + 2 * k + 1) * SWS + w * NFN + fn];
+        const R wm = sws[(le * NF + 2 * k) * SWS + w * NFN + fn];
         q[k * NW + w] = fma(wp, lpk, fma(-wm, lmk, -vol));
         Q[(k * NW + w) * nn + g] = q[k * NW + w];
       }
@@ -402,21 +463,21 @@ __device__ __forceinline__ void lift_group(const NskParams& p, const R* __restri
   __syncthreads();  // shared memory is reused below
 
   if constexpr (MODEL == 1) {
-    R* sg = sm;  // [G][D][NPE] grad rho at the nodes
+    R* sg = sm;  // [G][D][NPE] grad rho at the nodes, lines in direction k contiguous
     if (valid) {
 #pragma unroll
-      for (int k = 0; k < D; ++k) sg[(le * D + k) * NPE + n] = q[k * NW + D];
+      for (int k = 0; k < D; ++k) sg[(le * D + k) * NPE + line_pos<D, NP>(n, k)] = q[k * NW + D];
     }
     __syncthreads();
     if (valid) {
       for (int it = n; it < NF * NFN; it += NPE) {
         const int slot = it / NFN, fn = it % NFN, k = slot >> 1;
         const R* L = (slot & 1) ? t.lp : t.lm;
-        const int n0 = line_base<D, NP>(fn, k), st = node_stride<NP>(k);
-        const R* f = sg + (le * D + k) * NPE + n0;
+        R f[NP];
+        load_line<R, NP>(sg + (le * D + k) * NPE + fn * NP, f);
         R acc = 0;
 #pragma unroll
-        for (int j = 0; j < NP; ++j) acc = fma(L[j], f[j * st], acc);
+        for (int j = 0; j < NP; ++j) acc = fma(L[j], f[j], acc);
         FVtr[(size_t)slot * p.nfe + (e * NFN + fn)] = acc;
       }
     }
@@ -424,21 +485,30 @@ __device__ __forceinline__ void lift_group(const NskParams& p, const R* __restri
     return;
   }
 
-  R* sfv = sm;  // [G][D][NW][NPE] viscous flux F^v_k at the nodes
+  // [G][D][NW][NPE] the viscous flux F^v_k at the nodes without its coefficients (the stress
+  // tau / mu and grad c), lines in direction k contiguous; mu and kappa/beta are folded into
+  // the face interpolation below
+  R* sfv = sm;
   if (valid) {
     R div = 0;
 #pragma unroll
     for (int a = 0; a < D; ++a) div += q[a * NW + a];
-    const R mu = t.mu, kb = t.kb;
+    R tau[D][D];  // symmetric: each off-diagonal sum once
 #pragma unroll
     for (int k = 0; k < D; ++k) {
 #pragma unroll
-      for (int a = 0; a < D; ++a) {
-        R tau = q[k * NW + a] + q[a * NW + k];
-        if (a == k) tau = fma(-R(2.0 / 3.0), div, tau);
-        sfv[((le * D + k) * NW + a) * NPE + n] = mu * tau;
+      for (int a = k; a < D; ++a) {
+        const R sum = q[k * NW + a] + q[a * NW + k];
+        tau[k][a] = (a == k) ? fma(-R(2.0 / 3.0), div, sum) : sum;
+        tau[a][k] = tau[k][a];
       }
-      sfv[((le * D + k) * NW + D) * NPE + n] = kb * q[k * NW + D];
+    }
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const int pos = line_pos<D, NP>(n, k);
+#pragma unroll
+      for (int a = 0; a < D; ++a) sfv[((le * D + k) * NW + a) * NPE + pos] = tau[k][a];
+      sfv[((le * D + k) * NW + D) * NPE + pos] = q[k * NW + D];
     }
   }
   __syncthreads();
@@ -446,15 +516,17 @@ __device__ __forceinline__ void lift_group(const NskParams& p, const R* __restri
   if (valid) {
     for (int it = n; it < NF * NFN; it += NPE) {
       const int slot = it / NFN, fn = it % NFN, k = slot >> 1;
-      const R* L = (slot & 1) ? t.lp : t.lm;
-      const int n0 = line_base<D, NP>(fn, k), st = node_stride<NP>(k);
+      const R* Lmu = (slot & 1) ? t.lpmu : t.lmmu;  // mu l(+-1)
+      const R* Lkb = (slot & 1) ? t.lpkb : t.lmkb;  // (kappa/beta) l(+-1)
       R* o = FVtr + (size_t)slot * p.nfe + (e * NFN + fn);
 #pragma unroll
       for (int c = 0; c < NW; ++c) {
-        const R* f = sfv + ((le * D + k) * NW + c) * NPE + n0;
+        R f[NP];
+        load_line<R, NP>(sfv + ((le * D + k) * NW + c) * NPE + fn * NP, f);
+        const R* L = c < D ? Lmu : Lkb;
         R acc = 0;
 #pragma unroll
-        for (int j = 0; j < NP; ++j) acc = fma(L[j], f[j * st], acc);
+        for (int j = 0; j < NP; ++j) acc = fma(L[j], f[j], acc);
         o[c * pl] = acc;
       }
     }
@@ -469,7 +541,8 @@ __device__ __forceinline__ void lift_group(const NskParams& p, const R* __restri
 //   lambda = max(|v_{L,k}| + sqrt(p_alpha'(rho_L)), |v_{R,k}| + sqrt(p_alpha'(rho_R)))
 // (local Lax-Friedrichs with the model II wave speeds, Eq. parabolic_eigenvalues_model2;
 // BR1 viscous flux). The jump term acts on rho and momentum (c has no convective flux)
-// unless c_diss is set.
+// unless c_diss is set. F receives 2 F* (the 1/2 is applied by the volume kernel's staged
+// surface operators; scaling by 2 is exact, so the residual is unchanged bit for bit).
 template <typename R, int D, int NP>
 __device__ __forceinline__ void face_flux(const NskParams& p, const R* __restrict__ Utr, const R* __restrict__ FVtr,
                                           const int eL, const int eR, const int k, const int fn,
@@ -535,28 +608,28 @@ __device__ __forceinline__ void face_flux(const NskParams& p, const R* __restric
         F[1 + a] = fma(SK, us - uk[1 + a], F[1 + a]);
       }
     }
+    F[0] = R(2) * F[0];
 #pragma unroll
-    for (int a = 0; a < D; ++a) F[1 + a] = fma(-R(0.5), VL[a] + VR[a], F[1 + a]);
-    F[D + 1] = -R(0.5) * (VL[D] + VR[D]);
+    for (int a = 0; a < D; ++a) F[1 + a] = fma(R(2), F[1 + a], -(VL[a] + VR[a]));
+    F[D + 1] = -(VL[D] + VR[D]);
     return;
   }
   const R lam_l = fabs(UL[1 + k] * il) + sqrt(dl), lam_r = fabs(UR[1 + k] * ir) + sqrt(dr);
   const R lam = lam_l > lam_r ? lam_l : lam_r;
-  F[0] = R(0.5) * (UL[1 + k] + UR[1 + k]);
+  F[0] = UL[1 + k] + UR[1 + k];
 #pragma unroll
   for (int a = 0; a < D; ++a) {
     const R ml = UL[1 + a] * il, mr = UR[1 + a] * ir;
     const R sum = (a == k) ? fma(UL[1 + k], ml, pl) + fma(UR[1 + k], mr, pr) : fma(UL[1 + k], ml, UR[1 + k] * mr);
-    F[1 + a] = fma(R(0.5), sum, -(R(0.5) * (VL[a] + VR[a])));
+    F[1 + a] = sum - (VL[a] + VR[a]);
   }
-  F[D + 1] = -R(0.5) * (VL[D] + VR[D]);
-  const R hl = -(R(0.5) * lam);
+  F[D + 1] = -(VL[D] + VR[D]);
 #pragma unroll
-  for (int v = 0; v < NV - 1; ++v) F[v] = fma(hl, UR[v] - UL[v], F[v]);
-  if (p.c_diss) F[NV - 1] = fma(hl, UR[NV - 1] - UL[NV - 1], F[NV - 1]);
+  for (int v = 0; v < NV - 1; ++v) F[v] = fma(-lam, UR[v] - UL[v], F[v]);
+  if (p.c_diss) F[NV - 1] = fma(-lam, UR[NV - 1] - UL[NV - 1], F[NV - 1]);
 }
 
-// Fstar[v][k][E][nfn]: the flux on face (e, +k) at face node fn.
+// Fstar[v][k][E][nfn]: twice the flux on face (e, +k) at face node fn.
 template <typename R, int D, int NP>
 __device__ __forceinline__ void face_at(const NskParams& p, const R* __restrict__ Utr, const R* __restrict__ FVtr,
                                         R* __restrict__ Fstar, const int k, const int e, const int fn, int& eflag) {
@@ -581,26 +654,6 @@ __device__ __forceinline__ void face_item(const NskParams& p, const R* __restric
   face_at<R, D, NP>(p, Utr, FVtr, Fstar, (int)k, e, fn, eflag);
 }
 
-// the NP values of one line from shared memory: 16-byte loads when a line fills whole
-// 16-byte units (f is then 16-byte aligned), else one value at a time
-template <typename R, int NP>
-__device__ __forceinline__ void load_line(const R* f, R (&x)[NP]) {
-  if constexpr ((NP * sizeof(R)) % 16 == 0) {
-    using V = typename std::conditional<sizeof(R) == 4, float4, double2>::type;
-    constexpr int W = 16 / (int)sizeof(R);
-#pragma unroll
-    for (int j = 0; j < NP; j += W) {
-      const V t = *reinterpret_cast<const V*>(f + j);
-      const R* tv = reinterpret_cast<const R*>(&t);
-#pragma unroll
-      for (int w = 0; w < W; ++w) x[j + w] = tv[w];
-    }
-  } else {
-#pragma unroll
-    for (int j = 0; j < NP; ++j) x[j] = f[j];
-  }
-}
-
 // shared memory (in units of R) of volume_group
 template <typename R, int D, int NP, int G, bool FUSED>
 __host__ __device__ constexpr int volume_smem() {
@@ -614,7 +667,8 @@ __host__ __device__ constexpr int volume_smem() {
 // mode RHS: Rout = R; mode LSRK: K <- A K + dt R, U <- U + B K.
 // The fluxes of the element's 2d faces are staged in shared memory: read from Fstar with
 // coalesced loads, or, FUSED, evaluated by the element itself (each face is then
-// evaluated by both neighbours, bit-identically).
+// evaluated by both neighbours, bit-identically). Both hold 2 F*: the staged lpk, lmk
+// carry the 1/2.
 // UtrNext (optional): the traces of the element's new state (LSRK) or of its state (RHS)
 // are written there from shared memory, so the next stage needs no prolongation pass.
 // It must not alias Utr when FUSED (neighbours still read Utr).
@@ -643,9 +697,26 @@ __device__ __forceinline__ void volume_group(const NskParams& p, R* __restrict__
     // A face's NFN values of one variable are contiguous on both sides: copied 16 bytes at a
     // time when NFN values fill whole 16-byte units (the offsets below are then multiples of 16
     // bytes: Fstar and the shared buffer start 16-byte aligned and nfe = E NFN).
+    // Each thread keeps one (variable, piece) and walks the NF face slots.
     constexpr int W = (NFN * (int)sizeof(R)) % 16 == 0 ? 16 / (int)sizeof(R) : 1;
-    constexpr int NFW = NFN / W;
-    if (valid) {
+    constexpr int NFW = NFN / W, NQV = NV * NFW, PER = NPE / NQV;
+    if constexpr (PER >= 1) {
+      if (valid && n < PER * NQV) {
+        const ElemIdx ex = elem_idx<D>(p, e);
+        const int q = n % NQV, v = q / NFW, fn = (q % NFW) * W;
+        R* sb = sfs + (le * NF * NV + v) * NFN + fn;
+        for (int slot = n / NQV; slot < NF; slot += PER) {
+          const int k = slot >> 1;
+          const int src = (slot & 1) ? e : nbr_of(p, ex, k, -1);
+          R* dst = sb + slot * NV * NFN;
+          const R* srcp = Fstar + (size_t)(v * D + k) * p.nfe + (src * NFN + fn);
+          if constexpr (W > 1)
+            cp_async_16(dst, srcp);
+          else
+            cp_async_elem(dst, srcp);
+        }
+      }
+    } else if (valid) {
       const ElemIdx ex = elem_idx<D>(p, e);
       for (int it = n; it < NF * NV * NFW; it += NPE) {
         const int fn = (it % NFW) * W, v = (it / NFW) % NV, slot = it / (NV * NFW), k = slot >> 1;
@@ -660,7 +731,7 @@ __device__ __forceinline__ void volume_group(const NskParams& p, R* __restrict__
     }
     cp_async_commit();
   }
-  stage_tables<R, D, NP>(t, tb);
+  stage_tables<R, D, NP, true>(t, tb);
   R u[NV], q[NQ], kin[NV];
   if (valid) {
 #pragma unroll
@@ -804,7 +875,7 @@ template <typename R, int D, int NP, int G>
 __global__ void __launch_bounds__(G * Shape<D, NP>::NPE, (lift_min_blocks<R, G * Shape<D, NP>::NPE>()))
     k_lift(const NskParams p, const R* __restrict__ U, const R* __restrict__ Utr, R* __restrict__ Q,
            R* __restrict__ FVtr, int* __restrict__ err) {
-  __shared__ R sm[lift_smem<R, D, NP, G>()];
+  __shared__ __align__(16) R sm[lift_smem<R, D, NP, G>()];
   int eflag = 0;
   lift_group<R, D, NP, G>(p, U, Utr, Q, FVtr, (long long)blockIdx.x * G, sm, eflag);
   if (eflag) atomicOr(err, eflag);

@@ -295,7 +295,7 @@ template <int D, int NP, int G>
 __global__ void __launch_bounds__(G * Shape<D, NP>::NPE)
     k_lift_nsk(const NskParams p, const double* __restrict__ U, const double* __restrict__ Utr,
                double* __restrict__ Q, double* __restrict__ Gtr, int* __restrict__ err) {
-  __shared__ double sm[lift_smem<double, D, NP, G>()];
+  __shared__ __align__(16) double sm[lift_smem<double, D, NP, G>()];
   int eflag = 0;
   lift_group<double, D, NP, G, 1>(p, U, Utr, Q, Gtr, (long long)blockIdx.x * G, sm, eflag);
   if (eflag) atomicOr(err, eflag);
