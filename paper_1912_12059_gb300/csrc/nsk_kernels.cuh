@@ -281,23 +281,22 @@ __device__ __forceinline__ void prolong_item(const NskParams& p, const R* __rest
 // Shared-memory copy of the direction operators (2/h_k folded in) of one precision:
 // [D][NP][NP] dk, then [D][NP] lpk, then [D][NP] lmk. Every thread of a warp reads its own
 // row i; from shared memory the distinct rows are served in one pass, where the kernel
-// parameter bank would serialise them. HALF: lpk and lmk scaled by 1/2 (exact), for the
-// kernels whose face values are stored doubled (the lifting's sums of two traces, the face
-// fluxes 2 F*).
+// parameter bank would serialise them. dk is scaled by sd, lpk and lmk by sl: the kernels
+// whose face values are stored doubled (the lifting's sums of two traces, the face fluxes
+// 2 F*) take sl = 1/2 (an exact scaling); the Runge-Kutta update folds dt into both.
 template <int D, int NP>
 __host__ __device__ constexpr int tab_smem() {
   return D * NP * NP + 2 * D * NP;
 }
-template <typename R, int D, int NP, bool HALF = false>
-__device__ __forceinline__ void stage_tables(const NskTab<R>& t, R* tb) {
+template <typename R, int D, int NP>
+__device__ __forceinline__ void stage_tables(const NskTab<R>& t, R* tb, const R sd = R(1), const R sl = R(1)) {
   for (int x = threadIdx.x; x < D * NP * NP; x += blockDim.x) {
     const int k = x / (NP * NP), r = x % (NP * NP);
-    tb[x] = t.dk[k][(r / NP) * NSK_MAXNP + r % NP];
+    tb[x] = sd * t.dk[k][(r / NP) * NSK_MAXNP + r % NP];
   }
   for (int x = threadIdx.x; x < D * NP; x += blockDim.x) {
-    const R sc = HALF ? R(0.5) : R(1);
-    tb[D * NP * NP + x] = sc * t.lpk[x / NP][x % NP];
-    tb[D * NP * NP + D * NP + x] = sc * t.lmk[x / NP][x % NP];
+    tb[D * NP * NP + x] = sl * t.lpk[x / NP][x % NP];
+    tb[D * NP * NP + D * NP + x] = sl * t.lmk[x / NP][x % NP];
   }
 }
 
@@ -385,7 +384,7 @@ __device__ __forceinline__ void lift_group(const NskParams& p, const R* __restri
   const size_t pl = (size_t)NF * p.nfe;        // distance between the planes of two trace variables
   const int g = e * NPE + n;
 
-  stage_tables<R, D, NP, true>(t, tb);
+  stage_tables<R, D, NP>(t, tb, R(1), R(0.5));
   if (valid) {
     const R rho = U[g];
     eflag |= rho_flags(rho);
@@ -658,13 +657,14 @@ __device__ __forceinline__ void face_item(const NskParams& p, const R* __restric
 template <typename R, int D, int NP, int G, bool FUSED>
 __host__ __device__ constexpr int volume_smem() {
   using S = Shape<D, NP>;
-  return G * D * S::NV * S::NPE + G * S::NF * S::NV * S::NFN + tab_smem<D, NP>();
+  return G * D * S::NV * S::NPE + G * S::NF * S::NV * S::NFN + tab_smem<D, NP>() + 2;
 }
 
 // Weak-form volume integral and surface lifting (Eq. weakformulation),
 //   R_i = sum_k (2/h_k) [ sum_j (w_j/w_i) l_i'(xi_j) F_k(U_j, Q_j) - (F*_{k,+} l_i(1) - F*_{k,-} l_i(-1)) / w_i ] + S_i,
 // F_k = F^c_k - F^v_k, S = (0, alpha rho grad c, (alpha/beta)(rho - c)); then
-// mode RHS: Rout = R; mode LSRK: K <- A K + dt R, U <- U + B K.
+// mode RHS: Rout = R; mode LSRK: K <- A K + dt R, U <- U + B K (dt folded into the staged
+// operators and source coefficients, so the contraction yields dt R).
 // The fluxes of the element's 2d faces are staged in shared memory: read from Fstar with
 // coalesced loads, or, FUSED, evaluated by the element itself (each face is then
 // evaluated by both neighbours, bit-identically). Both hold 2 F*: the staged lpk, lmk
@@ -682,7 +682,7 @@ __device__ __forceinline__ void volume_group(const NskParams& p, R* __restrict__
   constexpr int NPE = S::NPE, NFN = S::NFN, NW = S::NW, NV = S::NV, NQ = S::NQ, NF = S::NF;
   R* sf = sm;                          // [G][D][NV][NFN][NP] fluxes F_k at the nodes, lines in k contiguous
   R* sfs = sm + G * D * NV * NPE;      // [G][NF][NV][NFN] fluxes of the element's faces
-  R* tb = sfs + G * NF * NV * NFN;     // direction operators
+  R* tb = sfs + G * NF * NV * NFN;     // direction operators, then the source coefficients
   const auto& t = TabSel<R>::get(p);
   const int le = threadIdx.x / NPE, n = threadIdx.x % NPE;
   const int e = (int)e0 + le;
@@ -731,7 +731,12 @@ __device__ __forceinline__ void volume_group(const NskParams& p, R* __restrict__
     }
     cp_async_commit();
   }
-  stage_tables<R, D, NP, true>(t, tb);
+  const R sc = mode == NSK_MODE_RHS ? R(1) : dt;  // the operator scale
+  stage_tables<R, D, NP>(t, tb, sc, R(0.5) * sc);
+  if (threadIdx.x == 0) {
+    tb[tab_smem<D, NP>()] = t.alpha * sc;
+    tb[tab_smem<D, NP>() + 1] = t.ab * sc;
+  }
   R u[NV], q[NQ], kin[NV];
   if (valid) {
 #pragma unroll
@@ -754,7 +759,17 @@ __device__ __forceinline__ void volume_group(const NskParams& p, R* __restrict__
     R div = 0;
 #pragma unroll
     for (int a = 0; a < D; ++a) div += q[a * NW + a];
-    const R mu = t.mu, kb = t.kb;
+    const R mu = t.mu;
+    R tau[D][D];  // symmetric: each off-diagonal sum once
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+#pragma unroll
+      for (int a = k; a < D; ++a) {
+        const R sum = q[k * NW + a] + q[a * NW + k];
+        tau[k][a] = (a == k) ? fma(-R(2.0 / 3.0), div, sum) : sum;
+        tau[a][k] = tau[k][a];
+      }
+    }
 #pragma unroll
     for (int k = 0; k < D; ++k) {
       // node n sits at position i_k of line face_node(n, k) in direction k
@@ -763,11 +778,9 @@ __device__ __forceinline__ void volume_group(const NskParams& p, R* __restrict__
 #pragma unroll
       for (int a = 0; a < D; ++a) {
         const R fc = (a == k) ? fma(u[1 + k], u[1 + a] * inv, pa) : u[1 + k] * (u[1 + a] * inv);
-        R tau = q[k * NW + a] + q[a * NW + k];
-        if (a == k) tau = fma(-R(2.0 / 3.0), div, tau);
-        f[(1 + a) * NPE] = fma(-mu, tau, fc);
+        f[(1 + a) * NPE] = fma(-mu, tau[k][a], fc);
       }
-      f[(D + 1) * NPE] = -(kb * q[k * NW + D]);
+      f[(D + 1) * NPE] = q[k * NW + D];  // the c flux -(kappa/beta) grad c, its factor applied after the sum
     }
     if constexpr (FUSED) {
       const ElemIdx ex = elem_idx<D>(p, e);
@@ -789,7 +802,9 @@ __device__ __forceinline__ void volume_group(const NskParams& p, R* __restrict__
   if (valid) {
     // res_v = sum_k [ sum_j dk[i][j] F_k(j) - F*_{k,+} lpk[i] + F*_{k,-} lmk[i] ]  (2/h_k folded in),
     // accumulated over k in ascending order
-    R res[NV];
+    // (the c equation's volume part, a sum over grad c, is kept apart and scaled by
+    // -kappa/beta once)
+    R res[NV], volc = 0;
 #pragma unroll
     for (int v = 0; v < NV; ++v) res[v] = 0;
 #pragma unroll
@@ -803,18 +818,24 @@ __device__ __forceinline__ void volume_group(const NskParams& p, R* __restrict__
       for (int v = 0; v < NV; ++v) {
         R fl[NP];
         load_line<R, NP>(sf + ((le * D + k) * NV + v) * NPE + fn * NP, fl);
-        R acc = res[v];
+        R acc = v == NV - 1 ? volc : res[v];
 #pragma unroll
         for (int j = 0; j < NP; ++j) acc = fma(dk[j], fl[j], acc);
         const R fp = sfs[((le * NF + 2 * k + 1) * NV + v) * NFN + fn];
         const R fm = sfs[((le * NF + 2 * k) * NV + v) * NFN + fn];
-        res[v] = fma(fm, lmk, fma(-fp, lpk, acc));
+        if (v == NV - 1) {
+          volc = acc;
+          res[v] = fma(fm, lmk, fma(-fp, lpk, res[v]));
+        } else {
+          res[v] = fma(fm, lmk, fma(-fp, lpk, acc));
+        }
       }
     }
-    const R alpha = t.alpha;
+    res[NV - 1] = fma(-t.kb, volc, res[NV - 1]);
+    const R alpha = tb[tab_smem<D, NP>()], ab = tb[tab_smem<D, NP>() + 1];  // scaled like the operators
 #pragma unroll
     for (int a = 0; a < D; ++a) res[1 + a] = fma(alpha * u[0], q[a * NW + D], res[1 + a]);
-    res[D + 1] = fma(t.ab, u[0] - u[D + 1], res[D + 1]);
+    res[D + 1] = fma(ab, u[0] - u[D + 1], res[D + 1]);
 
     if (mode == NSK_MODE_RHS) {
 #pragma unroll
@@ -822,7 +843,7 @@ __device__ __forceinline__ void volume_group(const NskParams& p, R* __restrict__
     } else {
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
-        const R kv = fma(A, kin[v], dt * res[v]);
+        const R kv = fma(A, kin[v], res[v]);  // res holds dt R
         K[v * nn + g] = kv;
         u[v] = fma(B, kv, u[v]);
         U[v * nn + g] = u[v];
