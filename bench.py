@@ -40,7 +40,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM bytes (read + write) per launch of the dominant kernels at 64^3 elements, N = 3, from one
 # ncu capture at 40^3 elements scaled by the element count (profiles/launches_fp64_collision3d_64cubed.md,
 # profiles/fp32_stage_kernels_collision3d.md); must be re-measured whenever those kernels change
-MEASURED_TRAFFIC = {("k_volume", 8, 262144): 4.69e9, ("k_volume", 4, 262144): 2.70e9}
+MEASURED_TRAFFIC = {("k_volume", 8, 262144): 5.99e9, ("k_volume", 4, 262144): 2.70e9}
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
@@ -59,23 +59,35 @@ def workload_by_name(name):
 # ---------------------------------------------------------------- algorithmic cost model
 def kernel_cost(kernel, d, n, fp_bytes, traces=0.0):
     """Algorithmic (flops, bytes) per element of one stage kernel, counted from the kernel
-    source: FMA = 2 flops, add/mul/div/sqrt = 1; bytes = compulsory loads + stores.
-    `traces`: fraction of the k_volume launches that also wrote the face traces of their
-    output state (the next stage's prolongation: its flops and trace stores)."""
+    source: FMA = 2 flops, add/mul/div/sqrt = 1 (negations, compares and min/max are free);
+    bytes = compulsory loads + stores. `traces`: fraction of the k_volume launches that also
+    wrote the face traces of their output state (the next stage's prolongation: its flops and
+    trace stores). FP64 traces carry 1/rho and 1/(3 - rho) (one division per trace node);
+    FP32 kernels divide where FP64 reads those planes."""
     npe, nfn, nv, nw, nf = n**d, n ** (d - 1), d + 2, d + 1, 2 * d
+    fp64 = fp_bytes == 8
+    trace_extra = 5 if fp64 else 0            # 3 - rho, rho (3 - rho), 1/x, two products
+    stress = (d - 1) + d * (d - 1) // 2 + 3 * d  # div v, off-diagonal sums, diagonal sum + fma
+    xp = 2 if fp64 else 0                     # FP64 trace planes 1/rho, 1/(3 - rho)
     if kernel == "k_prolong":
-        return nf * nfn * nv * 2 * n, fp_bytes * (nv * npe + nf * nfn * nv)
+        return nf * nfn * (nv * 2 * n + trace_extra), fp_bytes * (nv * npe + nf * nfn * (nv + xp))
     if kernel == "k_lift":
-        per_node = (d + 1) + d * nw * (2 * n + 5) + 2 * d * d + 3 * d + (d - 1)
-        fl = npe * per_node + nf * nfn * (4 * d + 4) + nf * nfn * nw * 2 * n
-        by = fp_bytes * (nv * npe + 2 * nf * nfn * nv + d * nw * npe + nf * nfn * nw)
+        per_node = (d + 1) + d * nw * (2 * n + 4) + stress          # w = (m / rho, c); grad w; tau
+        per_face = (3 * d + 1) + (0 if fp64 else 2)                  # 2 w* (and two reciprocals)
+        fl = npe * per_node + nf * nfn * per_face + nf * nfn * nw * 2 * n
+        by = fp_bytes * (nv * npe + 2 * nf * nfn * (nv + xp // 2) + d * nw * npe + nf * nfn * nw)  # + 1/rho
         return fl, by
     if kernel == "k_face":
-        return d * nfn * (58 + 13 * d), fp_bytes * d * nfn * (2 * nv + 2 * nw + nv)
+        eos = 18 if fp64 else 30                                     # both sides (FP32: + 1/rho)
+        per_fn = eos + 6 + 1 + 9 + 7 * (d - 1) + 1 + 3 * (nv - 1)    # lambda, 2 F* (LF), jump
+        return d * nfn * per_fn, fp_bytes * d * nfn * (2 * (nv + xp) + 2 * nw + nv)
     if kernel == "k_volume":
-        per_node = 1 + 10 + (d - 1) + d * (5 * d + 5) + nv * d * (2 * n + 6) + 3 * d + 3 + 5 * nv
+        eos = 10 if fp64 else 8
+        flux = d + 2 * d + d * (d - 1) + 2 * d * d                   # v_a, F^c, F^c - mu tau
+        per_node = eos + stress + flux + nv * d * (2 * n + 4) + 2 + (2 * d + 4) + 4 * nv
         by = fp_bytes * (nv * npe + d * nw * npe + 2 * d * nfn * nv + 2 * nv * npe + nv * npe)
-        return npe * per_node + traces * nf * nfn * nv * 2 * n, by + traces * fp_bytes * nf * nfn * nv
+        return (npe * per_node + traces * nf * nfn * (nv * 2 * n + trace_extra),
+                by + traces * fp_bytes * nf * nfn * (nv + xp))
     raise KeyError(kernel)
 
 

@@ -400,7 +400,11 @@ __device__ __forceinline__ void lift_group(const NskParams& p, const R* __restri
       for (int w = 0; w < NW; ++w) sw[((le * NCOPY + c) * NW + w) * NPE + pos] = wn[w];
     }
     const ElemIdx ex = elem_idx<D>(p, e);
-    for (int it = n; it < NF * NFN; it += NPE) {
+    // a fixed trip count (the last round predicated): the gathers of all rounds are in flight together
+#pragma unroll
+    for (int r = 0; r < (NF * NFN + NPE - 1) / NPE; ++r) {
+      const int it = n + r * NPE;
+      if (it >= NF * NFN) break;
       const int slot = it / NFN, fn = it % NFN, k = slot >> 1, s = slot & 1;
       const int en = nbr_of(p, ex, k, s ? 1 : -1);
       const int oslot = 2 * k + (1 - s);
@@ -859,8 +863,12 @@ __device__ __forceinline__ void volume_group(const NskParams& p, R* __restrict__
     }
     __syncthreads();
     if (valid) {
-      for (int it = n; it < NF * NFN; it += NPE)
+#pragma unroll
+      for (int r = 0; r < (NF * NFN + NPE - 1) / NPE; ++r) {
+        const int it = n + r * NPE;
+        if (it >= NF * NFN) break;
         prolong_trace<R, D, NP>(p, su + le * NV * NPE, NPE, UtrNext, e, it / NFN, it % NFN);
+      }
     }
     __syncthreads();
   }
