@@ -47,6 +47,16 @@ class OrcSetup(C.Structure):
     ]
 
 
+class OrcFvSetup(C.Structure):
+    _fields_ = [
+        ("dirichlet", C.c_int),
+        ("Ub_lo", C.c_double * 3),
+        ("Ub_hi", C.c_double * 3),
+        ("ind_upper", C.c_double),
+        ("ind_lower", C.c_double),
+    ]
+
+
 def build_oracle(force: bool = False) -> Path:
     """Compile the oracle with gcc (FP contraction off, so no fused multiply-adds)."""
     if not force and LIB.exists() and LIB.stat().st_mtime >= max(SRC.stat().st_mtime, HDR.stat().st_mtime):
@@ -88,6 +98,14 @@ def lib():
         L.orc_lsrk4.argtypes = [sp, dp, C.c_double, C.c_int]
         L.orc_timestep.argtypes = [sp, dp, C.c_double, dp]
         L.orc_diagnostics.argtypes = [sp, dp, dp, dp, dp]
+        fp = C.POINTER(OrcFvSetup)
+        ip = C.POINTER(C.c_int)
+        L.orc_fv_tables.argtypes = [C.c_int, C.c_int, dp, dp]
+        L.orc_persson.argtypes = [C.c_int, C.c_int, dp]
+        L.orc_persson.restype = C.c_double
+        L.orc_fv_rhs.argtypes = [sp, fp, ip, dp, dp]
+        L.orc_fv_switch.argtypes = [sp, fp, ip, dp, dp]
+        L.orc_fv_lsrk4.argtypes = [sp, fp, ip, dp, C.c_double, C.c_int]
         _lib = L
     return _lib
 
@@ -162,6 +180,20 @@ def lsrk4_coeffs():
     A, B, Cc = np.zeros(5), np.zeros(5), np.zeros(5)
     lib().orc_lsrk4_coeffs(_ptr(A), _ptr(B), _ptr(Cc))
     return A, B, Cc
+
+
+def fv_tables(N, node_type=NODES_GAUSS):
+    """Sub-cell mean matrix M[j][i] (mean of l_i over sub-cell j of N+1) and its inverse."""
+    M = np.zeros((N + 1) * (N + 1))
+    Minv = np.zeros((N + 1) * (N + 1))
+    _check(lib().orc_fv_tables(N, node_type, _ptr(M), _ptr(Minv)), "orc_fv_tables")
+    return M.reshape(N + 1, N + 1), Minv.reshape(N + 1, N + 1)
+
+
+def persson(u, node_type=NODES_GAUSS):
+    """Persson-Peraire indicator of the nodal values u (N + 1 of them)."""
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    return lib().orc_persson(len(u) - 1, node_type, _ptr(u))
 
 
 # ---- discretisation ----
@@ -263,3 +295,39 @@ class Oracle:
         _check(lib().orc_diagnostics(C.byref(self.s), _ptr(U), C.byref(m), C.byref(e), C.byref(l2)),
                "orc_diagnostics")
         return m.value, e.value, l2.value
+
+    # ---- sub-cell shock capturing and Dirichlet boundaries (dim = 1, model II) ----
+    def fv_setup(self, dirichlet=False, Ub_lo=(1.0, 0.0, 1.0), Ub_hi=(1.0, 0.0, 1.0), ind_upper=-6.0,
+                 ind_lower=-8.0):
+        f = OrcFvSetup()
+        f.dirichlet = 1 if dirichlet else 0
+        for v in range(3):
+            f.Ub_lo[v] = Ub_lo[v]
+            f.Ub_hi[v] = Ub_hi[v]
+        f.ind_upper, f.ind_lower = ind_upper, ind_lower
+        self.f = f
+        return f
+
+    def fv_rhs(self, U, flags):
+        U = np.ascontiguousarray(U, dtype=np.float64)
+        fl = np.ascontiguousarray(flags, dtype=np.int32)
+        R = np.zeros_like(U)
+        _check(lib().orc_fv_rhs(C.byref(self.s), C.byref(self.f), fl.ctypes.data_as(C.POINTER(C.c_int)), _ptr(U),
+                                _ptr(R)), "orc_fv_rhs")
+        return R
+
+    def fv_switch(self, U, flags):
+        """Indicator of every element and the switches it triggers: (U', flags', ind)."""
+        U = np.array(U, dtype=np.float64, order="C", copy=True)
+        fl = np.array(flags, dtype=np.int32, order="C", copy=True)
+        ind = np.zeros(self.E)
+        _check(lib().orc_fv_switch(C.byref(self.s), C.byref(self.f), fl.ctypes.data_as(C.POINTER(C.c_int)), _ptr(U),
+                                   _ptr(ind)), "orc_fv_switch")
+        return U, fl, ind
+
+    def fv_step(self, U, flags, dt, nsteps):
+        U = np.array(U, dtype=np.float64, order="C", copy=True)
+        fl = np.array(flags, dtype=np.int32, order="C", copy=True)
+        _check(lib().orc_fv_lsrk4(C.byref(self.s), C.byref(self.f), fl.ctypes.data_as(C.POINTER(C.c_int)), _ptr(U),
+                                  dt, nsteps), "orc_fv_lsrk4")
+        return U, fl

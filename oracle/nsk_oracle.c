@@ -887,3 +887,403 @@ int orc_diagnostics(const orc_setup* s, const double* U, double* mass, double* e
   *l2_rho_c = sqrt(sl);
   return st;
 }
+
+/* ======================================================================== */
+/* Finite-volume sub-cell shock capturing, Sec. 3.2 (the section "Finite    */
+/* Volume Sub-Cell Approach"), and Dirichlet boundaries, for the 1D sharp-   */
+/* interface Riemann problem of Sec. 4 (model II, one space dimension).      */
+/*                                                                           */
+/* An element is either a DG element (nodal values) or an FV element: N+1    */
+/* equidistant sub-cells holding integral means. The section fixes the       */
+/* sub-cell count, the exact Gauss conversion DG -> means, the FV weak form   */
+/* (phi = 1, midpoint rule on the faces, LF or HLLC), the second-order TVD    */
+/* reconstruction with MinMod, the gradient from a continuous reconstruction  */
+/* for the diffusive fluxes, and the Persson-Peraire indicator with two       */
+/* thresholds. Where it is silent this code takes these readings:             */
+/*   - the indicator acts on rho, as log10 of the energy of the highest       */
+/*     orthonormal Legendre mode over the total energy;                       */
+/*   - DG -> FV when Ind > upper, FV -> DG when Ind < lower (Ind of an FV     */
+/*     element from the degree-N polynomial with its sub-cell means), once    */
+/*     per time step, before the first stage (A_1 = 0 empties the RK          */
+/*     register, so only U is converted);                                     */
+/*   - FV -> DG by the inverse of the mean matrix (the unique polynomial of   */
+/*     degree N with those means);                                            */
+/*   - the reconstruction acts on (rho, v, c); across an element face the     */
+/*     neighbour value is the adjacent sub-cell mean of an FV element (one    */
+/*     sub-cell width away) or the face value of a DG element or boundary     */
+/*     state (half a width away);                                             */
+/*   - diffusive fluxes on FV faces use the difference quotient of the two    */
+/*     neighbouring values (the 1D form of Green's identity on the continuous */
+/*     piecewise-linear reconstruction); the source gradient of c in a        */
+/*     sub-cell is the mean of its two face quotients;                        */
+/*   - a face between a DG and an FV element pairs the DG trace (and its      */
+/*     lifted gradient) with the FV side's reconstructed face value (and its  */
+/*     difference quotient); the DG lifting takes the central w* of the two;  */
+/*   - a Dirichlet boundary is a ghost neighbour whose face state is the      */
+/*     given boundary state and whose gradient equals the interior side's.    */
+/* ======================================================================== */
+
+/* orthonormal Legendre polynomial phi_m = sqrt((2m+1)/2) P_m on [-1, 1] */
+static double legendre_on(int m, double x) {
+  double P, dP;
+  legendre(m, x, &P, &dP);  /* dP is not used (and not defined at x = +-1) */
+  return sqrt((2.0 * m + 1.0) / 2.0) * P;
+}
+
+/* solve A x = b (n x n, row-major, copied) by Gaussian elimination with partial pivoting */
+static int solve_dense(int n, const double* A_in, const double* b, double* x) {
+  double A[ORC_MAXNP * ORC_MAXNP], r[ORC_MAXNP];
+  memcpy(A, A_in, sizeof(double) * n * n);
+  memcpy(r, b, sizeof(double) * n);
+  for (int c = 0; c < n; ++c) {
+    int p = c;
+    for (int i = c + 1; i < n; ++i)
+      if (fabs(A[i * n + c]) > fabs(A[p * n + c])) p = i;
+    if (A[p * n + c] == 0.0) return ORC_ERR_NOCONV;
+    if (p != c) {
+      for (int j = 0; j < n; ++j) {
+        double t = A[c * n + j];
+        A[c * n + j] = A[p * n + j];
+        A[p * n + j] = t;
+      }
+      double t = r[c];
+      r[c] = r[p];
+      r[p] = t;
+    }
+    for (int i = c + 1; i < n; ++i) {
+      const double f = A[i * n + c] / A[c * n + c];
+      for (int j = c; j < n; ++j) A[i * n + j] -= f * A[c * n + j];
+      r[i] -= f * r[c];
+    }
+  }
+  for (int i = n - 1; i >= 0; --i) {
+    double s = r[i];
+    for (int j = i + 1; j < n; ++j) s -= A[i * n + j] * x[j];
+    x[i] = s / A[i * n + i];
+  }
+  return ORC_OK;
+}
+
+/* Sub-cell means of the nodal basis: sub-cell j of N+1 covers xi in [a_j, a_j + 2/(N+1)],
+ * a_j = -1 + 2j/(N+1); its mean of u is (1/2) sum_q w_q u(a_j + (xi_q + 1)/(N+1)) with the
+ * (N+1)-point Gauss rule (xi_q, w_q) on [-1, 1], exact for degree N.
+ * M[j][i] = mean of l_i over sub-cell j; Minv its inverse (means -> nodal values). */
+int orc_fv_tables(int N, int node_type, double* M, double* Minv) {
+  const int np = N + 1;
+  double xi[ORC_MAXNP], w[ORC_MAXNP], xg[ORC_MAXNP], wg[ORC_MAXNP];
+  if (N < 1 || N >= ORC_MAXNP || orc_nodes(N, node_type, xi, w) || orc_nodes(N, 0, xg, wg)) return ORC_ERR_ARG;
+  for (int j = 0; j < np; ++j) {
+    const double a = -1.0 + 2.0 * j / np;
+    for (int i = 0; i < np; ++i) {
+      double s = 0.0;
+      for (int q = 0; q < np; ++q) s += wg[q] * orc_lagrange_eval(N, xi, i, a + (xg[q] + 1.0) / np);
+      M[j * np + i] = 0.5 * s;
+    }
+  }
+  if (Minv) {
+    for (int c = 0; c < np; ++c) {  /* column c of the inverse: M x = e_c */
+      double e[ORC_MAXNP] = {0}, x[ORC_MAXNP];
+      e[c] = 1.0;
+      if (solve_dense(np, M, e, x)) return ORC_ERR_NOCONV;
+      for (int i = 0; i < np; ++i) Minv[i * np + c] = x[i];
+    }
+  }
+  return ORC_OK;
+}
+
+/* Persson-Peraire indicator of nodal values u (N+1 nodes of the given type): the modal
+ * coefficients uh in the orthonormal Legendre basis solve V uh = u, V[i][m] = phi_m(xi_i);
+ * Ind = log10(uh_N^2 / sum_m uh_m^2). */
+double orc_persson(int N, int node_type, const double* u) {
+  const int np = N + 1;
+  double xi[ORC_MAXNP], w[ORC_MAXNP], V[ORC_MAXNP * ORC_MAXNP], uh[ORC_MAXNP];
+  if (N < 1 || N >= ORC_MAXNP || orc_nodes(N, node_type, xi, w)) return NAN;
+  for (int i = 0; i < np; ++i)
+    for (int m = 0; m < np; ++m) V[i * np + m] = legendre_on(m, xi[i]);
+  if (solve_dense(np, V, u, uh)) return NAN;
+  double tot = 0.0;
+  for (int m = 0; m < np; ++m) tot += uh[m] * uh[m];
+  return log10(uh[N] * uh[N] / tot);
+}
+
+static double minmod(double a, double b) {
+  if (a * b <= 0.0) return 0.0;
+  return a > 0.0 ? fmin(a, b) : fmax(a, b);
+}
+
+/* (rho, m, c) <-> (rho, v, c) */
+static void fv_prim(const double* U, double* P) {
+  P[0] = U[0];
+  P[1] = U[1] / U[0];
+  P[2] = U[2];
+}
+static void fv_cons(const double* P, double* U) {
+  U[0] = P[0];
+  U[1] = P[0] * P[1];
+  U[2] = P[2];
+}
+
+/* Per-element face data of the 1D operator: the state on each side's face (ξ = -1: 0, +1: 1),
+ * and for FV elements the reconstruction (cell primitives and MinMod slopes) and the
+ * difference quotients of (v, c) across the element's two faces. */
+typedef struct {
+  double Uf[2][3];      /* face states */
+  double gf[2][2];      /* FV: (v_x, c_x) across the face; DG: the lifted gradient trace */
+  double P[ORC_MAXNP][3], sl[ORC_MAXNP][3];  /* FV: cell primitives, slopes (per unit length) */
+} fv_elem_t;
+
+static int fv_check(const orc_setup* s, const orc_fv_setup* f) {
+  if (!s || !f || s->dim != 1 || s->model != 0 || s->N < 1 || s->N >= ORC_MAXNP) return ORC_ERR_ARG;
+  if (s->nelem[0] < 1 || !(s->hi[0] > s->lo[0]) || !(s->beta > 0.0)) return ORC_ERR_ARG;
+  return ORC_OK;
+}
+
+/* DG trace of element e (nodal U[v][E][np]) at side (0: xi = -1, 1: xi = +1) */
+static void fv_dg_trace(const mesh_t* m, const double* U, long e, int side, double* Uf) {
+  const long nn = m->E * m->np;
+  for (int v = 0; v < 3; ++v) Uf[v] = trace(m, U + v * nn, e, 0, 0, side ? +1 : -1);
+}
+
+/* The semi-discrete residual of the mixed DG/FV mesh (see the readings above). */
+int orc_fv_rhs(const orc_setup* s, const orc_fv_setup* f, const int* fv, const double* U, double* R) {
+  int st = fv_check(s, f);
+  if (st) return st;
+  mesh_t m;
+  if ((st = make_mesh(s, &m))) return st;
+  const int np = m.np, N = np - 1;
+  const long E = m.E, nn = E * np;
+  const double h = m.h[0], dx = h / np;
+  fv_elem_t* el = (fv_elem_t*)calloc(E, sizeof(fv_elem_t));
+  double* Q = (double*)calloc(2 * nn, sizeof(double));  /* DG elements: (v_x, c_x) at the nodes */
+  if (!el || !Q) { free(el); free(Q); return ORC_ERR_ARG; }
+  for (long i = 0; i < 3 * nn; ++i) {
+    R[i] = 0.0;
+    if (i < nn && !admissible(U[i])) st = ORC_ERR_NONPHYSICAL;
+  }
+  const int per = !f->dirichlet;
+  /* 1. DG face traces */
+  for (long e = 0; e < E; ++e)
+    if (!fv[e])
+      for (int sd = 0; sd < 2; ++sd) fv_dg_trace(&m, U, e, sd, el[e].Uf[sd]);
+  /* 2. FV reconstruction: cell primitives, neighbour values across the element faces, slopes */
+  for (long e = 0; e < E; ++e) {
+    if (!fv[e]) continue;
+    fv_elem_t* x = &el[e];
+    for (int j = 0; j < np; ++j) {
+      double Uc[3] = {U[e * np + j], U[nn + e * np + j], U[2 * nn + e * np + j]};
+      fv_prim(Uc, x->P[j]);
+    }
+    double Pn[2][3], dn[2];  /* the value beyond each element face and its distance */
+    for (int sd = 0; sd < 2; ++sd) {
+      const int dir = sd ? +1 : -1;
+      const int boundary = !per && ((sd == 0 && e == 0) || (sd == 1 && e == E - 1));
+      if (boundary) {
+        fv_prim(sd ? f->Ub_hi : f->Ub_lo, Pn[sd]);
+        dn[sd] = 0.5 * dx;
+        continue;
+      }
+      const long en = neighbour(&m, e, 0, dir);
+      if (fv[en]) {
+        const int jn = sd ? 0 : N;
+        double Uc[3] = {U[en * np + jn], U[nn + en * np + jn], U[2 * nn + en * np + jn]};
+        fv_prim(Uc, Pn[sd]);
+        dn[sd] = dx;
+      } else {
+        double Ut[3];
+        fv_dg_trace(&m, U, en, sd ? 0 : 1, Ut);
+        fv_prim(Ut, Pn[sd]);
+        dn[sd] = 0.5 * dx;
+      }
+    }
+    for (int j = 0; j < np; ++j)
+      for (int q = 0; q < 3; ++q) {
+        const double left = j > 0 ? (x->P[j][q] - x->P[j - 1][q]) / dx : (x->P[0][q] - Pn[0][q]) / dn[0];
+        const double right = j < N ? (x->P[j + 1][q] - x->P[j][q]) / dx : (Pn[1][q] - x->P[N][q]) / dn[1];
+        x->sl[j][q] = minmod(left, right);
+      }
+    double Pl[3], Pr[3];
+    for (int q = 0; q < 3; ++q) {
+      Pl[q] = x->P[0][q] - 0.5 * dx * x->sl[0][q];
+      Pr[q] = x->P[N][q] + 0.5 * dx * x->sl[N][q];
+    }
+    fv_cons(Pl, x->Uf[0]);
+    fv_cons(Pr, x->Uf[1]);
+    for (int q = 0; q < 2; ++q) {
+      x->gf[0][q] = (x->P[0][1 + q] - Pn[0][1 + q]) / dn[0];
+      x->gf[1][q] = (Pn[1][1 + q] - x->P[N][1 + q]) / dn[1];
+    }
+  }
+  /* the state beyond face side sd of element e: the neighbour's face state or the boundary state */
+#define FV_OUTER(e, sd)                                                                          \
+  ((!per && (sd) == 0 && (e) == 0)       ? f->Ub_lo                                              \
+   : (!per && (sd) == 1 && (e) == E - 1) ? f->Ub_hi                                              \
+                                         : el[neighbour(&m, (e), 0, (sd) ? +1 : -1)].Uf[(sd) ? 0 : 1])
+  /* 3. BR1 lifting of w = (v, c) in the DG elements, central w* with the outer face state */
+  for (long e = 0; e < E; ++e) {
+    if (fv[e]) continue;
+    double ws[2][2];
+    for (int sd = 0; sd < 2; ++sd) {
+      const double* Uo = FV_OUTER(e, sd);
+      const double* Ui = el[e].Uf[sd];
+      ws[sd][0] = 0.5 * (Ui[1] / Ui[0] + Uo[1] / Uo[0]);
+      ws[sd][1] = 0.5 * (Ui[2] + Uo[2]);
+    }
+    for (int i = 0; i < np; ++i)
+      for (int q = 0; q < 2; ++q) {
+        double vol = 0.0;
+        for (int j = 0; j < np; ++j) {
+          const long p = e * np + j;
+          const double wj = q == 0 ? U[nn + p] / U[p] : U[2 * nn + p];
+          vol += m.w[j] * wj * m.D[j * np + i];
+        }
+        const double surf = (ws[1][q] * m.Lp[i] - ws[0][q] * m.Lm[i]) / m.w[i];
+        Q[q * nn + e * np + i] = (2.0 / h) * (surf - vol / m.w[i]);
+      }
+    for (int sd = 0; sd < 2; ++sd)
+      for (int q = 0; q < 2; ++q) el[e].gf[sd][q] = trace(&m, Q + q * nn, e, 0, 0, sd ? +1 : -1);
+  }
+  /* 4. numerical flux (convective minus the mean of the viscous fluxes) on the element faces;
+   *    face e sits between elements e - 1 and e (face E: the right boundary, Dirichlet only) */
+  const long nfaces = per ? E : E + 1;
+  double(*Fh)[3] = (double(*)[3])calloc(nfaces + 1, sizeof(double[3]));
+  if (!Fh) { free(el); free(Q); return ORC_ERR_ARG; }
+  for (long fc = 0; fc < nfaces; ++fc) {
+    const long eR = fc < E ? fc : -1, eL = fc > 0 ? fc - 1 : (per ? E - 1 : -1);
+    const double* UL = eL >= 0 ? el[eL].Uf[1] : f->Ub_lo;
+    const double* UR = eR >= 0 ? el[eR].Uf[0] : f->Ub_hi;
+    const double* gL = eL >= 0 ? el[eL].gf[1] : el[eR].gf[0];
+    const double* gR = eR >= 0 ? el[eR].gf[0] : el[eL].gf[1];
+    if (!admissible(UL[0]) || !admissible(UR[0])) st = ORC_ERR_NONPHYSICAL;
+    double QL[2] = {gL[0], gL[1]}, QR[2] = {gR[0], gR[1]}, fvL[3], fvR[3];
+    visc_flux(s, 1, 0, QL, fvL);
+    visc_flux(s, 1, 0, QR, fvR);
+    numflux(s, 1, 0, UL, UR, Fh[fc]);
+    for (int v = 0; v < 3; ++v) Fh[fc][v] -= 0.5 * (fvL[v] + fvR[v]);
+  }
+  if (per) memcpy(Fh[E], Fh[0], sizeof(double[3]));  /* the right face of element E-1 */
+  /* 5. residuals */
+  for (long e = 0; e < E; ++e) {
+    const double* Fl = Fh[e];
+    const double* Fr = Fh[e + 1];
+    if (!fv[e]) {
+      /* DG: the weak form of Eq. (weakformulation), as in residual() above */
+      double F[ORC_MAXNP][3];
+      for (int j = 0; j < np; ++j) {
+        const long p = e * np + j;
+        double Un[3] = {U[p], U[nn + p], U[2 * nn + p]}, Qn[2] = {Q[p], Q[nn + p]}, fc[3], fvv[3];
+        conv_flux(s, 1, 0, Un, fc);
+        visc_flux(s, 1, 0, Qn, fvv);
+        for (int v = 0; v < 3; ++v) F[j][v] = fc[v] - fvv[v];
+      }
+      for (int i = 0; i < np; ++i) {
+        const long p = e * np + i;
+        for (int v = 0; v < 3; ++v) {
+          double vol = 0.0;
+          for (int j = 0; j < np; ++j) vol += m.w[j] * F[j][v] * m.D[j * np + i];
+          R[v * nn + p] = (2.0 / h) * (vol / m.w[i] - (Fr[v] * m.Lp[i] - Fl[v] * m.Lm[i]) / m.w[i]);
+        }
+        R[nn + p] += s->alpha * U[p] * Q[nn + p];
+        R[2 * nn + p] += s->alpha / s->beta * (U[p] - U[2 * nn + p]);
+      }
+    } else {
+      /* FV: dU_j/dt = -(F_{j+1/2} - F_{j-1/2}) / dx + S_j over the sub-cells */
+      const fv_elem_t* x = &el[e];
+      double Fs[ORC_MAXNP + 1][3], gc[ORC_MAXNP + 1];  /* sub-cell face fluxes, c_x on them */
+      memcpy(Fs[0], Fl, sizeof(double[3]));
+      memcpy(Fs[np], Fr, sizeof(double[3]));
+      gc[0] = x->gf[0][1];
+      gc[np] = x->gf[1][1];
+      for (int j = 0; j < N; ++j) {
+        double PL[3], PR[3], UL[3], UR[3], g[2], fvv[3];
+        for (int q = 0; q < 3; ++q) {
+          PL[q] = x->P[j][q] + 0.5 * dx * x->sl[j][q];
+          PR[q] = x->P[j + 1][q] - 0.5 * dx * x->sl[j + 1][q];
+        }
+        fv_cons(PL, UL);
+        fv_cons(PR, UR);
+        if (!admissible(UL[0]) || !admissible(UR[0])) st = ORC_ERR_NONPHYSICAL;
+        g[0] = (x->P[j + 1][1] - x->P[j][1]) / dx;
+        g[1] = (x->P[j + 1][2] - x->P[j][2]) / dx;
+        gc[j + 1] = g[1];
+        numflux(s, 1, 0, UL, UR, Fs[j + 1]);
+        visc_flux(s, 1, 0, g, fvv);
+        for (int v = 0; v < 3; ++v) Fs[j + 1][v] -= fvv[v];
+      }
+      for (int j = 0; j < np; ++j) {
+        const long p = e * np + j;
+        for (int v = 0; v < 3; ++v) R[v * nn + p] = -(Fs[j + 1][v] - Fs[j][v]) / dx;
+        R[nn + p] += s->alpha * U[p] * 0.5 * (gc[j] + gc[j + 1]);
+        R[2 * nn + p] += s->alpha / s->beta * (U[p] - U[2 * nn + p]);
+      }
+    }
+  }
+#undef FV_OUTER
+  free(Fh);
+  free(el);
+  free(Q);
+  return st;
+}
+
+/* Indicator of every element (on rho, through the inverse mean matrix for FV elements) and the
+ * switches it triggers: DG -> FV above ind_upper, FV -> DG below ind_lower; U converted in place. */
+int orc_fv_switch(const orc_setup* s, const orc_fv_setup* f, int* fv, double* U, double* ind) {
+  int st = fv_check(s, f);
+  if (st) return st;
+  const int N = s->N, np = N + 1;
+  const long E = s->nelem[0], nn = E * np;
+  double M[ORC_MAXNP * ORC_MAXNP], Minv[ORC_MAXNP * ORC_MAXNP];
+  if ((st = orc_fv_tables(N, s->node_type, M, Minv))) return st;
+  for (long e = 0; e < E; ++e) {
+    double rho[ORC_MAXNP];
+    for (int i = 0; i < np; ++i) {
+      rho[i] = 0.0;
+      if (fv[e]) {
+        for (int j = 0; j < np; ++j) rho[i] += Minv[i * np + j] * U[e * np + j];
+      } else {
+        rho[i] = U[e * np + i];
+      }
+    }
+    const double x = orc_persson(N, s->node_type, rho);
+    if (ind) ind[e] = x;
+    const int to_fv = !fv[e] && x > f->ind_upper, to_dg = fv[e] && x < f->ind_lower;
+    if (!to_fv && !to_dg) continue;
+    const double* T = to_fv ? M : Minv;
+    for (int v = 0; v < 3; ++v) {
+      double u[ORC_MAXNP], out[ORC_MAXNP];
+      for (int i = 0; i < np; ++i) u[i] = U[v * nn + e * np + i];
+      for (int i = 0; i < np; ++i) {
+        out[i] = 0.0;
+        for (int j = 0; j < np; ++j) out[i] += T[i * np + j] * u[j];
+      }
+      for (int i = 0; i < np; ++i) U[v * nn + e * np + i] = out[i];
+    }
+    fv[e] = to_fv;
+  }
+  return ORC_OK;
+}
+
+/* nsteps LSRK4 steps of size dt with the sub-cell scheme: the switches before every step. */
+int orc_fv_lsrk4(const orc_setup* s, const orc_fv_setup* f, int* fv, double* U, double dt, int nsteps) {
+  int st = fv_check(s, f);
+  if (st) return st;
+  const long len = 3L * s->nelem[0] * (s->N + 1);
+  double* K = (double*)calloc(len, sizeof(double));
+  double* R = (double*)malloc(sizeof(double) * len);
+  if (!K || !R) { free(K); free(R); return ORC_ERR_ARG; }
+  double A[5], B[5], C[5];
+  orc_lsrk4_coeffs(A, B, C);
+  for (int step = 0; step < nsteps && st == ORC_OK; ++step) {
+    st = orc_fv_switch(s, f, fv, U, NULL);
+    for (int stage = 0; stage < 5 && st == ORC_OK; ++stage) {
+      st = orc_fv_rhs(s, f, fv, U, R);
+      if (st) break;
+      for (long i = 0; i < len; ++i) {
+        K[i] = A[stage] * K[i] + dt * R[i];
+        U[i] = U[i] + B[stage] * K[i];
+      }
+    }
+  }
+  free(K);
+  free(R);
+  return st;
+}

@@ -86,6 +86,25 @@ int orc_timestep(const orc_setup* s, const double* U, double cfl, double* dt);
 /* Quadrature sums: mass, total energy of the relaxation model, ||rho-c||_L2. */
 int orc_diagnostics(const orc_setup* s, const double* U, double* mass, double* energy, double* l2_rho_c);
 
+/* Finite-volume sub-cell shock capturing and Dirichlet boundaries (Sec. 3.2, the sub-cell
+ * section; the 1D sharp-interface Riemann problem of Sec. 4), model II, dim = 1 only.
+ * fv[e] = 1 marks an element holding N+1 equidistant sub-cell means instead of nodal values. */
+typedef struct {
+  int dirichlet;                /* 0: periodic; 1: the boundary states below outside lo and hi */
+  double Ub_lo[3], Ub_hi[3];    /* (rho, m, c) */
+  double ind_upper, ind_lower;  /* Persson indicator thresholds (log10): DG -> FV, FV -> DG */
+} orc_fv_setup;
+/* M[j][i]: mean of the nodal basis function l_i over sub-cell j; Minv = M^-1 (may be NULL). */
+int orc_fv_tables(int N, int node_type, double* M, double* Minv);
+/* log10 of the highest orthonormal-Legendre mode's share of the energy of nodal values u. */
+double orc_persson(int N, int node_type, const double* u);
+/* Residual of the mixed DG/FV mesh (same layout as U; FV elements hold means). */
+int orc_fv_rhs(const orc_setup* s, const orc_fv_setup* f, const int* fv, const double* U, double* R);
+/* Indicator per element (ind may be NULL) and the DG <-> FV switches it triggers, in place. */
+int orc_fv_switch(const orc_setup* s, const orc_fv_setup* f, int* fv, double* U, double* ind);
+/* nsteps LSRK4 steps with the switches before each step. */
+int orc_fv_lsrk4(const orc_setup* s, const orc_fv_setup* f, int* fv, double* U, double dt, int nsteps);
+
 #ifdef __cplusplus
 }
 #endif
