@@ -130,6 +130,45 @@ int nsk_set_flux(nsk_ctx* ctx, int flux);
  * requires a new nsk_set_state (NSK_ERR_STATE until then). */
 int nsk_set_model(nsk_ctx* ctx, int model);
 
+/* Finite-volume sub-cell shock capturing (Sec. 3.2, the section "Finite Volume Sub-Cell
+ * Approach"), for one-dimensional FP64 model II contexts (NSK_ERR_ARG otherwise, also for
+ * N > 5 or with the learned closure). With on = 1 every nsk_step step first evaluates the
+ * Persson-Peraire indicator of each element's density, Ind = log10(top orthonormal-Legendre
+ * mode energy / total energy), and converts a DG element with Ind > ind_upper to N+1
+ * equidistant sub-cells holding the exact means of its polynomial, and a sub-cell element with
+ * Ind < ind_lower (Ind of the polynomial with those means) back to nodal values
+ * (ind_lower <= ind_upper; the paper's Riemann problem uses -6 and -8 as upper and lower). Sub-cell
+ * elements advance with a second-order finite-volume scheme: MinMod-limited linear
+ * reconstruction of (rho, v, c), the flux of nsk_set_flux on every sub-cell face, difference
+ * quotients of v and c for the diffusive fluxes; a face between a DG and a sub-cell element
+ * pairs the DG trace with the reconstructed value. nsk_get_state then returns nodal values for
+ * DG elements and sub-cell means for the others (nsk_get_subcell tells which); nsk_set_state
+ * resets every element to DG; nsk_lift returns NSK_ERR_STATE while this path is active;
+ * nsk_diagnostics treats every element as nodal. on = 0 returns NSK_ERR_STATE while an element
+ * holds sub-cell means. Allocates the path's buffers (once). The stage costs four launches per
+ * stage (face states, lifting, face fluxes, update) plus one switch launch per step. */
+int nsk_set_subcell(nsk_ctx* ctx, int on, double ind_upper, double ind_lower);
+
+/* Dirichlet boundaries for one-dimensional FP64 model II contexts (the Riemann problem of
+ * Sec. 4): with on = 1 the domain is no longer periodic; outside x = lo the state is
+ * Ub_lo = (rho, m, c), outside x = hi it is Ub_hi (host arrays of 3). The boundary face sees a
+ * ghost neighbour with that state and with the interior side's gradient (its viscous flux is the
+ * interior one), in the DG lifting, the numerical flux and the sub-cell reconstruction alike.
+ * Uses the sub-cell path's kernels (with or without nsk_set_subcell). NSK_ERR_ARG for other
+ * contexts or non-finite states. */
+int nsk_set_dirichlet(nsk_ctx* ctx, int on, const double Ub_lo[3], const double Ub_hi[3]);
+
+/* Per-element representation while nsk_set_subcell or nsk_set_dirichlet is active: flags[e] = 1
+ * for an element holding sub-cell means (host array of E ints, 0 or 1; the state is then read
+ * accordingly, no conversion). nsk_get_subcell copies the flags and/or the indicator of the last
+ * switch pass (either pointer may be NULL; host arrays of E). NSK_ERR_STATE when the path is off. */
+int nsk_set_subcell_flags(nsk_ctx* ctx, const int* flags);
+int nsk_get_subcell(nsk_ctx* ctx, int* flags, double* ind);
+
+/* One indicator and switch pass of nsk_set_subcell on the current state (the pass nsk_step runs
+ * before every step). NSK_ERR_STATE unless sub-cell shock capturing is on and a state is set. */
+int nsk_subcell_switch(nsk_ctx* ctx);
+
 /* Copy the state in (set) or out (get); layout above, FP64. Setting the state
  * also clears the Runge-Kutta register. */
 int nsk_set_state(nsk_ctx* ctx, const double* U, int where);

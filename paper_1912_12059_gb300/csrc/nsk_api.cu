@@ -303,9 +303,11 @@ void free_ctx(nsk_ctx* c) {
   if (!c) return;
   void* ptrs[] = {c->b.U, c->b.K, c->b.Q, c->b.Utr, c->utr_alt, c->b.FVtr, c->b.Fstar, c->b.Q2, c->b.Gtr,
                   c->b.err, c->b.lam,
-                  c->b.dt, c->b.part, c->rbuf, c->stage64, c->cl_X, c->cl_Y, c->cl_red, c->cl_mean};
+                  c->b.dt, c->b.part, c->rbuf, c->stage64, c->cl_X, c->cl_Y, c->cl_red, c->cl_mean,
+                  c->fvb.flags, c->fvb.ind, c->fvb.Uf, c->fvb.Gf, c->fvb.SL, c->fvb.Fh};
   for (void* q : ptrs)
     if (q) cudaFree(q);
+  free(c->fv_params);
   for (cudaEvent_t ev : c->prof_pool) cudaEventDestroy(ev);
   delete c;
 }
@@ -473,7 +475,7 @@ int nsk_set_model(nsk_ctx* c, int model) {
   if (!c || (model != NSK_MODEL_RELAXATION && model != NSK_MODEL_NSK)) return NSK_ERR_ARG;
   if (model == NSK_MODEL_NSK) {
     if (c->precision != NSK_FP64) return NSK_ERR_ARG;
-    if (c->closure_mode == NSK_C_LEARNED) return NSK_ERR_STATE;
+    if (c->closure_mode == NSK_C_LEARNED || c->fv_path()) return NSK_ERR_STATE;
     if (!c->b.Q2) {  // lap rho, and the traces of grad rho
       const size_t faces = (size_t)c->E * 2 * c->dim * c->nfn;
       if (cudaMalloc(&c->b.Q2, sizeof(double) * (size_t)c->nn) != cudaSuccess ||
@@ -514,6 +516,8 @@ int nsk_set_state(nsk_ctx* c, const double* U, int where) {
     c->launches += r;
   }
   if (cudaMemsetAsync(c->b.K, 0, c->rsize * (size_t)n, c->stream) != cudaSuccess) return NSK_ERR_CUDA;
+  if (c->fvb.flags && cudaMemsetAsync(c->fvb.flags, 0, sizeof(int) * (size_t)c->E, c->stream) != cudaSuccess)
+    return NSK_ERR_CUDA;  // the given state is nodal (DG) everywhere
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) return NSK_ERR_CUDA;
   c->state_set = true;
   return NSK_OK;
@@ -550,10 +554,25 @@ int nsk_node_coords(nsk_ctx* c, double* x, int where) {
   return st;
 }
 
+// one stage of the 1D sub-cell path (nsk_fv.cu)
+int fv_stage(nsk_ctx* c, int mode, double* Rout, double A, double B, const double* dtp, double dtv) {
+  const int r = nsk_fv_launch_stage(c->p, c->fv_params, c->np, c->fvb, c->b, mode, Rout, A, B, dtp, dtv, c->stream);
+  if (r < 0) return r;
+  c->launches += r;
+  return NSK_OK;
+}
+
 int nsk_rhs(nsk_ctx* c, double t, double* Ut, int where) {
   (void)t;
   if (!c || !Ut || (where != NSK_HOST && where != NSK_DEVICE)) return NSK_ERR_ARG;
   if (!c->state_set) return NSK_ERR_STATE;
+  if (c->fv_path()) {
+    int r = fv_stage(c, NSK_MODE_RHS, (double*)c->rbuf, 0.0, 0.0, nullptr, 0.0);
+    if (r) return r;
+    r = export_nodal(c, c->rbuf, c->nvar, Ut, where);
+    if (r) return r;
+    return sync_and_check(c);
+  }
   NskLaunch l = {NSK_MODE_RHS, c->rbuf, 0.0, 0.0, nullptr, 0.0, nullptr, c->tpb, c->fused_face};
   int r = launch_stage(c, l);
   if (r) return r;
@@ -564,7 +583,7 @@ int nsk_rhs(nsk_ctx* c, double t, double* Ut, int where) {
 
 int nsk_lift(nsk_ctx* c, double* Q, int where) {
   if (!c || !Q || (where != NSK_HOST && where != NSK_DEVICE)) return NSK_ERR_ARG;
-  if (!c->state_set) return NSK_ERR_STATE;
+  if (!c->state_set || c->fv_path()) return NSK_ERR_STATE;
   NskLaunch l = {NSK_MODE_LIFT, nullptr, 0.0, 0.0, nullptr, 0.0, nullptr, c->tpb, c->fused_face};
   int r = launch_stage(c, l);
   if (r) return r;
@@ -588,6 +607,25 @@ int nsk_step(nsk_ctx* c, double dt, int nsteps) {
   if (!c || nsteps < 0 || !isfinite(dt) || dt == 0.0) return NSK_ERR_ARG;
   if (!c->state_set) return NSK_ERR_STATE;
   const bool adaptive = dt < 0.0;
+  if (c->fv_path()) {  // 1D sub-cell path: switches before every step, then the five stages
+    for (int s = 0; s < nsteps; ++s) {
+      if (adaptive) {
+        int r = launch_dt(c, -dt);
+        if (r < 0) return r;
+        c->launches += r;
+      }
+      if (c->fv_on) {
+        int r = nsk_fv_launch_switch(c->p, c->fv_params, c->np, c->fvb, (double*)c->b.U, c->stream);
+        if (r < 0) return r;
+        c->launches += r;
+      }
+      for (int st = 0; st < 5; ++st) {
+        int r = fv_stage(c, NSK_MODE_LSRK, nullptr, kA[st], kB[st], adaptive ? c->b.dt : nullptr, dt);
+        if (r) return r;
+      }
+    }
+    return sync_and_check(c);
+  }
   bool ready = false;  // b.Utr holds the traces of U
   for (int s = 0; s < nsteps; ++s) {
     if (adaptive) {
@@ -624,6 +662,104 @@ int nsk_step(nsk_ctx* c, double dt, int nsteps) {
     const int r = nsk_closure_apply_ctx(c, nullptr);
     if (r) return r;
   }
+  return sync_and_check(c);
+}
+
+// ---- 1D sub-cell shock capturing and Dirichlet boundaries ----
+static int fv_refresh(nsk_ctx* c) {
+  if (!c->fv_params) {
+    c->fv_params = malloc(nsk_fv_params_size());
+    if (!c->fv_params) return NSK_ERR_NOMEM;
+  }
+  if (!c->fvb.flags) {
+    const size_t E = (size_t)c->E;
+    struct {
+      void** ptr;
+      size_t bytes;
+    } allocs[] = {{(void**)&c->fvb.flags, sizeof(int) * E},          {(void**)&c->fvb.ind, sizeof(double) * E},
+                  {(void**)&c->fvb.Uf, sizeof(double) * 6 * E},      {(void**)&c->fvb.Gf, sizeof(double) * 4 * E},
+                  {(void**)&c->fvb.SL, sizeof(double) * 3 * E * c->np}, {(void**)&c->fvb.Fh, sizeof(double) * 3 * (E + 1)}};
+    for (auto& a : allocs)
+      if (cudaMalloc(a.ptr, a.bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return NSK_ERR_NOMEM;
+      }
+    if (cudaMemset(c->fvb.flags, 0, sizeof(int) * E) != cudaSuccess ||
+        cudaMemset(c->fvb.ind, 0, sizeof(double) * E) != cudaSuccess)
+      return NSK_ERR_CUDA;
+  }
+  double gx[NSK_MAXNP], gw[NSK_MAXNP];
+  gauss_legendre(c->np, gx, gw);
+  return nsk_fv_fill_params(c->fv_params, c->np, c->xi, gx, gw, c->h[0], c->fv_dirichlet, c->fv_Ub[0], c->fv_Ub[1],
+                            c->fv_upper, c->fv_lower);
+}
+
+static bool fv_allowed(const nsk_ctx* c) {
+  return c->dim == 1 && c->precision == NSK_FP64 && c->p.model == NSK_MODEL_RELAXATION &&
+         c->closure_mode == NSK_C_EXPLICIT && c->np <= 6;
+}
+
+int nsk_set_subcell(nsk_ctx* c, int on, double ind_upper, double ind_lower) {
+  if (!c || (on && (isnan(ind_upper) || isnan(ind_lower) || ind_lower > ind_upper))) return NSK_ERR_ARG;
+  if (on && !fv_allowed(c)) return NSK_ERR_ARG;
+  if (!on && c->fvb.flags) {  // elements holding means cannot continue as nodal values
+    std::vector<int> f((size_t)c->E);
+    if (cudaMemcpy(f.data(), c->fvb.flags, sizeof(int) * f.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return NSK_ERR_CUDA;
+    for (int x : f)
+      if (x) return NSK_ERR_STATE;
+  }
+  c->fv_on = on ? 1 : 0;
+  c->fv_upper = ind_upper;
+  c->fv_lower = ind_lower;
+  return c->fv_path() ? fv_refresh(c) : NSK_OK;
+}
+
+int nsk_set_dirichlet(nsk_ctx* c, int on, const double Ub_lo[3], const double Ub_hi[3]) {
+  if (!c || (on && (!Ub_lo || !Ub_hi))) return NSK_ERR_ARG;
+  if (on && !fv_allowed(c)) return NSK_ERR_ARG;
+  if (on)
+    for (int v = 0; v < 3; ++v) {
+      if (!isfinite(Ub_lo[v]) || !isfinite(Ub_hi[v])) return NSK_ERR_ARG;
+      c->fv_Ub[0][v] = Ub_lo[v];
+      c->fv_Ub[1][v] = Ub_hi[v];
+    }
+  if (!on && c->fv_on) {
+    c->fv_dirichlet = 0;
+    return fv_refresh(c);
+  }
+  c->fv_dirichlet = on ? 1 : 0;
+  return c->fv_path() ? fv_refresh(c) : NSK_OK;
+}
+
+int nsk_set_subcell_flags(nsk_ctx* c, const int* flags) {
+  if (!c || !flags) return NSK_ERR_ARG;
+  if (!c->fv_path()) return NSK_ERR_STATE;
+  for (long long e = 0; e < c->E; ++e)
+    if (flags[e] != 0 && flags[e] != 1) return NSK_ERR_ARG;
+  if (cudaMemcpy(c->fvb.flags, flags, sizeof(int) * (size_t)c->E, cudaMemcpyHostToDevice) != cudaSuccess)
+    return NSK_ERR_CUDA;
+  return NSK_OK;
+}
+
+int nsk_get_subcell(nsk_ctx* c, int* flags, double* ind) {
+  if (!c || (!flags && !ind)) return NSK_ERR_ARG;
+  if (!c->fv_path()) return NSK_ERR_STATE;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return NSK_ERR_CUDA;
+  if (flags && cudaMemcpy(flags, c->fvb.flags, sizeof(int) * (size_t)c->E, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return NSK_ERR_CUDA;
+  if (ind && cudaMemcpy(ind, c->fvb.ind, sizeof(double) * (size_t)c->E, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return NSK_ERR_CUDA;
+  return NSK_OK;
+}
+
+int nsk_subcell_switch(nsk_ctx* c) {
+  if (!c) return NSK_ERR_ARG;
+  if (!c->fv_on) return NSK_ERR_STATE;
+  if (!c->state_set) return NSK_ERR_STATE;
+  const int r = nsk_fv_launch_switch(c->p, c->fv_params, c->np, c->fvb, (double*)c->b.U, c->stream);
+  if (r < 0) return r;
+  c->launches += r;
   return sync_and_check(c);
 }
 

@@ -155,6 +155,23 @@ int nsk_launch_diag(const NskParams& p, int dim, int np, bool fp32, const NskBuf
 int nsk_launch_convert(const void* src, bool src64, void* dst, bool dst64, long long n, cudaStream_t s);
 
 // One context (the opaque nsk_ctx of the ABI): mesh, parameters, device buffers.
+// Device buffers of the 1D sub-cell path (nsk_fv.cu)
+struct FvBuffers {
+  int* flags;    // [E] 1: the element holds N+1 sub-cell means
+  double* ind;   // [E] last Persson indicator
+  double* Uf;    // [E][2][3] face states
+  double* Gf;    // [E][2][2] (v_x, c_x) of each element side of its faces
+  double* SL;    // [E][N+1][3] MinMod slopes of the FV elements
+  double* Fh;    // [E+1][3] element-face fluxes
+};
+int nsk_fv_launch_stage(const NskParams& p, const void* fvp, int np, const FvBuffers& fb, const NskBuffers& b,
+                        int mode, double* Rout, double A, double B, const double* dtp, double dtv, cudaStream_t s);
+int nsk_fv_launch_switch(const NskParams& p, const void* fvp, int np, const FvBuffers& fb, double* U,
+                         cudaStream_t s);
+size_t nsk_fv_params_size();
+int nsk_fv_fill_params(void* fvp, int np, const double* xi, const double* gauss_x, const double* gauss_w, double h,
+                       int dirichlet, const double* Ub_lo, const double* Ub_hi, double upper, double lower);
+
 struct nsk_ctx {
   int dim, N, np, npe, nfn, nvar, nq, node_type, precision;
   long long E, nn;
@@ -189,6 +206,13 @@ struct nsk_ctx {
   float* cl_Y;                 // network output [E][npe]
   double* cl_red;              // judge sums
   float* cl_mean;              // element mean densities (features)
+  // 1D sub-cell shock capturing and Dirichlet boundaries (nsk_set_subcell, nsk_set_dirichlet)
+  int fv_on, fv_dirichlet;     // switching on; Dirichlet (else periodic) boundaries
+  double fv_upper, fv_lower;   // indicator thresholds
+  double fv_Ub[2][3];          // boundary states
+  void* fv_params;             // host copy of the kernels' parameter block
+  FvBuffers fvb;
+  bool fv_path() const { return fv_on || fv_dirichlet; }
 };
 
 // host helpers shared by the translation units of the library

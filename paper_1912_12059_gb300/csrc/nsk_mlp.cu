@@ -666,6 +666,7 @@ extern "C" {
 int nsk_set_closure(nsk_ctx* c, int mode, nsk_mlp* mlp, int judge_every, double eta_max) {
   if (!c || (mode != NSK_C_EXPLICIT && mode != NSK_C_LEARNED) || judge_every < 0) return NSK_ERR_ARG;
   if (mode == NSK_C_LEARNED && c->p.model == NSK_MODEL_NSK) return NSK_ERR_STATE;  // no c to close
+  if (mode == NSK_C_LEARNED && c->fv_path()) return NSK_ERR_STATE;  // sub-cell path: explicit c only
   if (mode == NSK_C_EXPLICIT) {
     c->closure_mode = NSK_C_EXPLICIT;
     c->p.closure = 0;

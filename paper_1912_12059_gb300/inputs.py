@@ -68,6 +68,15 @@ def head_on_collision(x, v_rel, radius=0.2, centres=((0.25, 0.5, 0.5), (0.75, 0.
     return _pack(rho, mom, rho.copy())
 
 
+def riemann_1d(x, rho_left=2.0, rho_right=0.1, x0=0.5):
+    """Multiphase shock tube of Sec. 4 (sharp-interface limit): liquid rho_left at rest left of
+    x0, vapour rho_right at rest right of it, c = rho (a node exactly at x0 takes the right
+    state)."""
+    x = x[0]
+    rho = np.where(x < x0, rho_left, rho_right).astype(np.float64)
+    return _pack(rho, [np.zeros_like(rho)], rho.copy())
+
+
 def gradient_theory_sigma(kappa, rho_vap=PAPER_RHO_VAP, rho_liq=PAPER_RHO_LIQ):
     """Surface tension kappa * integral(rho'^2) of the tanh profile of width 2 sqrt(kappa):
     sqrt(kappa) (rho_l - rho_v)^2 / 6 (square-gradient theory; the paper fixes no value)."""
@@ -148,6 +157,8 @@ class Workload:
             v_rel = collision_velocity(self.extra["we"], self.extra["radius"], self.kappa, rho_vap, rho_liq)
             c = self.extra.get("centres", ((0.25, 0.5, 0.5), (0.75, 0.5, 0.5)))
             return head_on_collision(x, v_rel, self.extra["radius"], c, rho_vap, rho_liq, self.kappa)
+        if kind == "riemann":
+            return riemann_1d(x, self.extra["rho_left"], self.extra["rho_right"], self.extra.get("x0", 0.5))
         raise ValueError(f"unknown initial condition {kind!r}")
 
 
@@ -156,6 +167,18 @@ def static_interface_1d(N=3, node_type=1, nelem=64):
     kappa=1e-4, alpha=1e3, beta=1e-3, mu=1e-3, LSRK4 2000 steps at CFL 0.5."""
     return Workload("static_interface_1d_E64_N3", 1, (nelem,), N, node_type, steps=2000,
                     extra={"ic": "slab"})
+
+
+def riemann_1d_sharp(eps=1e-3, nelem=200, N=3, gamma=1.0):
+    """1D multiphase Riemann problem in the sharp-interface limit (Sec. 4): (0, 1), 200 elements,
+    N = 3, liquid 2.0 | vapour 0.1 at rest (c = rho), alpha = 100, beta = 1e-3, capillarity
+    gamma = 1, viscosity mu = eps in {1e-2 .. 1e-5} and kappa = eps^2 gamma, HLLC, FV sub-cell
+    shock capturing with Persson thresholds -6 / -8, Dirichlet boundaries (the initial states),
+    explicit LSRK4 at CFL 0.1, end time 0.11. T = 0.85 (the paper's temperature elsewhere)."""
+    return Workload(f"riemann_1d_sharp_E{nelem}_N{N}_eps{eps:g}", 1, (nelem,), N, 0, kappa=eps * eps * gamma,
+                    alpha=100.0, beta=1e-3, mu=eps, cfl=0.1, steps=0,
+                    extra={"ic": "riemann", "rho_left": 2.0, "rho_right": 0.1, "x0": 0.5, "flux": "hllc",
+                           "ind_upper": -6.0, "ind_lower": -8.0, "t_end": 0.11})
 
 
 def coalescence_2d(alpha=1e2, nelem=128, N=4):

@@ -45,6 +45,11 @@ SIGNATURES = {
     "nsk_set_c_dissipation": (C.c_int, [C.c_void_p, C.c_int]),
     "nsk_set_flux": (C.c_int, [C.c_void_p, C.c_int]),
     "nsk_set_model": (C.c_int, [C.c_void_p, C.c_int]),
+    "nsk_set_subcell": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_double]),
+    "nsk_set_dirichlet": (C.c_int, [C.c_void_p, C.c_int, _dp, _dp]),
+    "nsk_set_subcell_flags": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
+    "nsk_get_subcell": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), _dp]),
+    "nsk_subcell_switch": (C.c_int, [C.c_void_p]),
     "nsk_set_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "nsk_get_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "nsk_node_coords": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
@@ -252,6 +257,35 @@ class Solver:
         E, npe, nv = C.c_longlong(), C.c_int(), C.c_int()
         _check(L.nsk_get_sizes(self.ctx, C.byref(E), C.byref(npe), C.byref(nv)), "nsk_get_sizes")
         self.nvar = nv.value
+
+    def set_subcell(self, on=True, ind_upper=-6.0, ind_lower=-8.0):
+        """Finite-volume sub-cell shock capturing with the Persson indicator (1D, FP64, model II)."""
+        _check(load_library().nsk_set_subcell(self.ctx, int(bool(on)), float(ind_upper), float(ind_lower)),
+               "nsk_set_subcell")
+
+    def set_dirichlet(self, Ub_lo=None, Ub_hi=None):
+        """Dirichlet boundary states (rho, m, c) outside x = lo and x = hi (1D); None: periodic."""
+        on = Ub_lo is not None
+        lo = (C.c_double * 3)(*(Ub_lo if on else (0.0, 0.0, 0.0)))
+        hi = (C.c_double * 3)(*(Ub_hi if on else (0.0, 0.0, 0.0)))
+        _check(load_library().nsk_set_dirichlet(self.ctx, int(on), lo, hi), "nsk_set_dirichlet")
+
+    def set_subcell_flags(self, flags):
+        fl = np.ascontiguousarray(flags, dtype=np.int32)
+        assert fl.size == self.E
+        _check(load_library().nsk_set_subcell_flags(self.ctx, fl.ctypes.data_as(C.POINTER(C.c_int))),
+               "nsk_set_subcell_flags")
+
+    def subcell(self):
+        """(flags, indicator of the last switch pass), host arrays of E."""
+        fl = np.zeros(self.E, dtype=np.int32)
+        ind = np.zeros(self.E)
+        _check(load_library().nsk_get_subcell(self.ctx, fl.ctypes.data_as(C.POINTER(C.c_int)),
+                                              ind.ctypes.data_as(C.POINTER(C.c_double))), "nsk_get_subcell")
+        return fl, ind
+
+    def subcell_switch(self):
+        _check(load_library().nsk_subcell_switch(self.ctx), "nsk_subcell_switch")
 
     def set_state(self, U):
         ptr, where = _buf(U, self.nvar * self.n_nodes, False)
