@@ -342,6 +342,7 @@ def run_gpu(args, wl, rank, world):
         variants["fp32_mixed"] = measure_fp32_variant(args, wl, stream, U0, U_after, dt, peaks)
         variants["fp64_hllc"] = measure_hllc_variant(args, wl, stream, U0, U_after, dt)
         variants["fp64_original_nsk"] = measure_nsk_variant(args, wl, stream, U0, dt)
+        variants["riemann1d_subcell"] = measure_subcell_variant(args, stream)
 
     if rank != 0:
         return 0
@@ -512,6 +513,83 @@ def measure_nsk_variant(args, wl, stream, U0, dt):
                     "kernels": {k: {"avg_ms": v[0] / max(v[1], 1), "launches": v[1]} for k, v in prof.items()}})
     except nsk.NskError as ex:  # the central flux of the third-order system does not damp
         out["error"] = str(ex)
+    s.close()
+    return out
+
+
+def measure_subcell_variant(args, stream):
+    """The 1D multiphase Riemann problem of Sec. 4 in the sharp-interface limit with FV sub-cell
+    shock capturing and Dirichlet boundaries (nsk_set_subcell, nsk_set_dirichlet): the paper's
+    configuration (200 elements, N = 3, eps = 1e-3, HLLC, Persson thresholds -6 / -8) run to
+    t = 0.11 at CFL 0.1 (time to solution; dt recomputed every 100 steps), and the same problem
+    on 2^20 elements for throughput (fixed dt, CUDA events around the timed steps)."""
+    import torch
+
+    from paper_1912_12059_gb300 import inputs, nsk
+
+    wl = inputs.riemann_1d_sharp(eps=1e-3)
+    x = wl.extra
+
+    def make(nelem):
+        s = nsk.Solver(1, (nelem,), wl.N, [0.0], [1.0], wl.node_type, nsk.NSK_FP64, stream=stream.cuda_stream)
+        s.set_params(T=wl.T, kappa=wl.kappa, alpha=wl.alpha, beta=wl.beta, mu=wl.mu)
+        s.set_flux(nsk.NSK_FLUX_HLLC)
+        s.set_subcell(True, x["ind_upper"], x["ind_lower"])
+        left, right = (x["rho_left"], 0.0, x["rho_left"]), (x["rho_right"], 0.0, x["rho_right"])
+        s.set_dirichlet(left, right)
+        s.set_state(inputs.riemann_1d(s.node_coords(), x["rho_left"], x["rho_right"], x["x0"]))
+        return s
+
+    out = {"workload": wl.name, "dtype": "f64", "flux": "hllc", "boundaries": "dirichlet",
+           "indicator_thresholds": [x["ind_upper"], x["ind_lower"]]}
+    s = make(wl.n_elem)
+    t, steps, t_end = 0.0, 0, x["t_end"]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    while t < t_end * (1 - 1e-12):
+        dt = s.compute_dt(wl.cfl)
+        n = min(100, int(math.ceil((t_end - t) / dt)))
+        dt = min(dt, (t_end - t) / n)
+        s.step(dt, n)
+        t += n * dt
+        steps += n
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    flags, _ = s.subcell()
+    U = s.get_state()
+    out["time_to_solution"] = {"t_end": t_end, "steps": steps, "wall_ms": ms, "ms_per_step": ms / steps,
+                               "value": wl.dofs * 5 * steps / (ms / 1e3), "unit": "DOF-updates/s",
+                               "subcell_elements_at_end": int(flags.sum()),
+                               "rho_range_at_end": [float(U[0].min()), float(U[0].max())],
+                               "launch": "one cooperative launch per nsk_step call"}
+    # the same mesh with dt recomputed before every step: one launch per kernel and stage
+    n = 200
+    torch.cuda.synchronize()
+    e0.record(stream)
+    s.step(-wl.cfl, n)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    out["per_kernel_launches"] = {"steps": n, "ms_per_step": ms / n, "launches_per_step": 23,
+                                  "value": wl.dofs * 5 * n / (ms / 1e3), "unit": "DOF-updates/s"}
+    s.close()
+    big = 1 << 20
+    s = make(big)
+    dt = s.compute_dt(wl.cfl)
+    s.step(dt, args.warmup)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    s.step(dt, args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    flags, _ = s.subcell()
+    nodes = big * (wl.N + 1)
+    out["throughput"] = {"nelem": big, "nodes": nodes, "steps": args.steps, "ms_per_step": ms / args.steps,
+                         "value": nodes * 5 * args.steps / (ms / 1e3), "unit": "DOF-updates/s",
+                         "subcell_elements": int(flags.sum()), "launches_per_step": 21}
     s.close()
     return out
 
@@ -795,6 +873,25 @@ def run_gemm(args, rank, world):
     return 0
 
 
+def run_riemann1d(args, rank, world):
+    """The 1D sharp-interface Riemann problem with FV sub-cell shock capturing alone (the
+    riemann1d_subcell variant of the default run as its own line)."""
+    import torch
+
+    from paper_1912_12059_gb300.build import build_library
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    build_library()
+    stream = torch.cuda.Stream()
+    v = measure_subcell_variant(args, stream)
+    if rank == 0:
+        t = v["time_to_solution"]
+        print(json.dumps({"metric": "DOF-updates/s", "value": t["value"], "unit": "DOF-updates/s", "n_gpus": 1,
+                          "steps": t["steps"], "warmup": 0, "ms_per_step": t["ms_per_step"], "higher_is_better": True,
+                          "dtype": "f64", "data": "synthetic", "config": v}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -802,7 +899,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="collision3d",
-                    choices=["collision3d", "coalescence2d", "interface1d", "batch", "closure", "gemm"])
+                    choices=["collision3d", "coalescence2d", "interface1d", "batch", "closure", "gemm", "riemann1d"])
     ap.add_argument("--rows", type=int, default=884736, help="gemm: rows (elements)")
     ap.add_argument("--no-variants", action="store_true", help="skip the FP32 variant of the default run")
     ap.add_argument("--nelem-train", type=int, default=64, help="closure: training mesh (elements per direction)")
@@ -825,6 +922,8 @@ def main():
         return run_closure(args, rank, world)
     if args.workload == "gemm":
         return run_gemm(args, rank, world)
+    if args.workload == "riemann1d":
+        return run_riemann1d(args, rank, world)
     if args.workload == "batch":
         if args.precision == "fp64" and "--precision" not in sys.argv:
             args.precision = "fp32"

@@ -304,7 +304,7 @@ void free_ctx(nsk_ctx* c) {
   void* ptrs[] = {c->b.U, c->b.K, c->b.Q, c->b.Utr, c->utr_alt, c->b.FVtr, c->b.Fstar, c->b.Q2, c->b.Gtr,
                   c->b.err, c->b.lam,
                   c->b.dt, c->b.part, c->rbuf, c->stage64, c->cl_X, c->cl_Y, c->cl_red, c->cl_mean,
-                  c->fvb.flags, c->fvb.ind, c->fvb.Uf, c->fvb.Gf, c->fvb.SL, c->fvb.Fh};
+                  c->fvb.flags, c->fvb.ind, c->fvb.Uf, c->fvb.Gf, c->fvb.SL, c->fvb.Fh, c->fvb.bar};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   free(c->fv_params);
@@ -608,6 +608,14 @@ int nsk_step(nsk_ctx* c, double dt, int nsteps) {
   if (!c->state_set) return NSK_ERR_STATE;
   const bool adaptive = dt < 0.0;
   if (c->fv_path()) {  // 1D sub-cell path: switches before every step, then the five stages
+    if (!adaptive && c->E <= nsk_fv_coop_max_elements()) {  // small mesh: the whole call in one launch
+      int r = nsk_fv_launch_coop(c->p, c->fv_params, c->np, c->fvb, c->b, nsteps, c->fv_on, dt, kA, kB, c->stream);
+      if (r < 0) return r;
+      if (r > 0) {
+        c->launches += r;
+        return sync_and_check(c);
+      }
+    }
     for (int s = 0; s < nsteps; ++s) {
       if (adaptive) {
         int r = launch_dt(c, -dt);
@@ -678,14 +686,16 @@ static int fv_refresh(nsk_ctx* c) {
       size_t bytes;
     } allocs[] = {{(void**)&c->fvb.flags, sizeof(int) * E},          {(void**)&c->fvb.ind, sizeof(double) * E},
                   {(void**)&c->fvb.Uf, sizeof(double) * 6 * E},      {(void**)&c->fvb.Gf, sizeof(double) * 4 * E},
-                  {(void**)&c->fvb.SL, sizeof(double) * 3 * E * c->np}, {(void**)&c->fvb.Fh, sizeof(double) * 3 * (E + 1)}};
+                  {(void**)&c->fvb.SL, sizeof(double) * 3 * E * c->np}, {(void**)&c->fvb.Fh, sizeof(double) * 3 * (E + 1)},
+                  {(void**)&c->fvb.bar, sizeof(unsigned) * 2}};
     for (auto& a : allocs)
       if (cudaMalloc(a.ptr, a.bytes) != cudaSuccess) {
         cudaGetLastError();
         return NSK_ERR_NOMEM;
       }
     if (cudaMemset(c->fvb.flags, 0, sizeof(int) * E) != cudaSuccess ||
-        cudaMemset(c->fvb.ind, 0, sizeof(double) * E) != cudaSuccess)
+        cudaMemset(c->fvb.ind, 0, sizeof(double) * E) != cudaSuccess ||
+        cudaMemset(c->fvb.bar, 0, sizeof(unsigned) * 2) != cudaSuccess)
       return NSK_ERR_CUDA;
   }
   double gx[NSK_MAXNP], gw[NSK_MAXNP];

@@ -59,43 +59,7 @@ struct nsk_batch {
 
 namespace {
 
-__device__ __forceinline__ unsigned long long global_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-// Grid-wide barrier over a cooperative launch, bounded by timeout_ns.
-__device__ bool grid_barrier(unsigned* bar, int* err, const unsigned long long timeout_ns) {
-  __shared__ int ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    ok = 1;
-    volatile unsigned* vgen = bar + 1;
-    const unsigned gen = *vgen;
-    __threadfence();
-    const unsigned arrived = atomicAdd(bar, 1u);
-    if (arrived == gridDim.x - 1) {
-      atomicExch(bar, 0u);
-      __threadfence();
-      atomicAdd(bar + 1, 1u);
-    } else {
-      const unsigned long long t0 = global_ns();
-      while (*vgen == gen) {
-        if (global_ns() - t0 > timeout_ns) {
-          atomicOr(err, NSK_EBIT_TIMEOUT);
-          ok = 0;
-          break;
-        }
-        __nanosleep(64);
-      }
-    }
-    __threadfence();
-    if (*(volatile int*)err & NSK_EBIT_TIMEOUT) ok = 0;
-  }
-  __syncthreads();
-  return ok != 0;
-}
+using nsk::grid_barrier;
 
 constexpr int align16(int x) { return (x + 15) & ~15; }
 

@@ -120,9 +120,8 @@ __device__ __forceinline__ double dg_trace(const NskParams& p, const double* U, 
 
 // ---- indicator and switching --------------------------------------------------------------
 template <int NP>
-__global__ void __launch_bounds__(128) k_fv_switch(const NskParams p, const FvParams f, double* __restrict__ U,
-                                                   int* __restrict__ flags, double* __restrict__ ind) {
-  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void fv_switch_body(const NskParams& p, const FvParams& f, double* __restrict__ U,
+                                               int* __restrict__ flags, double* __restrict__ ind, const long long e) {
   if (e >= p.E) return;
   const int fl = flags[e];
   double u[3][NP];
@@ -172,11 +171,10 @@ __global__ void __launch_bounds__(128) k_fv_switch(const NskParams p, const FvPa
 // Uf[e][side][3]: face states; Gf[e][side][2]: (v_x, c_x) of the element's side of each face;
 // SL[e][j][3]: MinMod slopes of (rho, v, c) per unit length in the FV elements.
 template <int NP>
-__global__ void __launch_bounds__(128) k_fv_faces(const NskParams p, const FvParams f, const double* __restrict__ U,
-                                                  const int* __restrict__ flags, double* __restrict__ Uf,
-                                                  double* __restrict__ Gf, double* __restrict__ SL,
-                                                  int* __restrict__ err) {
-  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void fv_faces_body(const NskParams& p, const FvParams& f, const double* __restrict__ U,
+                                              const int* __restrict__ flags, double* __restrict__ Uf,
+                                              double* __restrict__ Gf, double* __restrict__ SL,
+                                              int* __restrict__ err, const long long e) {
   if (e >= p.E) return;
   int eflag = 0;
   if (!flags[e]) {
@@ -251,10 +249,9 @@ __device__ __forceinline__ const double* outer(const NskParams& p, const FvParam
 }
 
 template <int NP>
-__global__ void __launch_bounds__(128) k_fv_lift(const NskParams p, const FvParams f, const double* __restrict__ U,
-                                                 const int* __restrict__ flags, const double* __restrict__ Uf,
-                                                 double* __restrict__ Q, double* __restrict__ Gf) {
-  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void fv_lift_body(const NskParams& p, const FvParams& f, const double* __restrict__ U,
+                                             const int* __restrict__ flags, const double* __restrict__ Uf,
+                                             double* __restrict__ Q, double* __restrict__ Gf, const long long e) {
   if (e >= p.E || flags[e]) return;
   const auto& t = p.td;
   double ws[2][2];  // central w* = (v, c) on the two faces
@@ -299,10 +296,9 @@ __global__ void __launch_bounds__(128) k_fv_lift(const NskParams p, const FvPara
 
 // face fc between elements fc - 1 and fc (face 0 and, with Dirichlet boundaries, face E are
 // the boundary faces); Fh[fc][3] = convective flux - mean viscous flux
-__global__ void __launch_bounds__(128) k_fv_flux(const NskParams p, const FvParams f, const double* __restrict__ Uf,
-                                                 const double* __restrict__ Gf, double* __restrict__ Fh,
-                                                 int* __restrict__ err) {
-  const long long fc = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void fv_flux_body(const NskParams& p, const FvParams& f, const double* __restrict__ Uf,
+                                             const double* __restrict__ Gf, double* __restrict__ Fh,
+                                             int* __restrict__ err, const long long fc) {
   const long long nfaces = f.dirichlet ? p.E + 1 : p.E;
   if (fc >= nfaces) return;
   const long long eR = fc < p.E ? fc : -1;
@@ -327,13 +323,13 @@ __global__ void __launch_bounds__(128) k_fv_flux(const NskParams p, const FvPara
 
 // residual of element e (DG weak form or FV sub-cell balance) and the update
 template <int NP>
-__global__ void __launch_bounds__(128)
-    k_fv_update(const NskParams p, const FvParams f, double* __restrict__ U, double* __restrict__ K,
-                double* __restrict__ Rout, const int* __restrict__ flags, const double* __restrict__ Gf,
-                const double* __restrict__ SL, const double* __restrict__ Q, const double* __restrict__ Fh,
-                const int mode, const double A, const double B, const double* __restrict__ dtp, const double dtv,
-                int* __restrict__ err) {
-  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void fv_update_body(const NskParams& p, const FvParams& f, double* __restrict__ U,
+                                               double* __restrict__ K, double* __restrict__ Rout,
+                                               const int* __restrict__ flags, const double* __restrict__ Gf,
+                                               const double* __restrict__ SL, const double* __restrict__ Q,
+                                               const double* __restrict__ Fh, const int mode, const double A,
+                                               const double B, const double dt, int* __restrict__ err,
+                                               const long long e) {
   if (e >= p.E) return;
   const auto& t = p.td;
   int eflag = 0;
@@ -420,7 +416,6 @@ __global__ void __launch_bounds__(128)
 #pragma unroll
       for (int j = 0; j < NP; ++j) Rout[(size_t)v * p.nne + e * NP + j] = r[v][j];
   } else {
-    const double dt = dtp ? *dtp : dtv;
 #pragma unroll
     for (int v = 0; v < 3; ++v)
 #pragma unroll
@@ -432,6 +427,83 @@ __global__ void __launch_bounds__(128)
       }
   }
   if (eflag) atomicOr(err, eflag);
+}
+
+// ---- one launch per kernel (any mesh size) ----------------------------------------------------
+template <int NP>
+__global__ void __launch_bounds__(128) k_fv_switch(const NskParams p, const FvParams f, double* __restrict__ U,
+                                                   int* __restrict__ flags, double* __restrict__ ind) {
+  fv_switch_body<NP>(p, f, U, flags, ind, (long long)blockIdx.x * blockDim.x + threadIdx.x);
+}
+template <int NP>
+__global__ void __launch_bounds__(128) k_fv_faces(const NskParams p, const FvParams f, const double* __restrict__ U,
+                                                  const int* __restrict__ flags, double* __restrict__ Uf,
+                                                  double* __restrict__ Gf, double* __restrict__ SL,
+                                                  int* __restrict__ err) {
+  fv_faces_body<NP>(p, f, U, flags, Uf, Gf, SL, err, (long long)blockIdx.x * blockDim.x + threadIdx.x);
+}
+template <int NP>
+__global__ void __launch_bounds__(128) k_fv_lift(const NskParams p, const FvParams f, const double* __restrict__ U,
+                                                 const int* __restrict__ flags, const double* __restrict__ Uf,
+                                                 double* __restrict__ Q, double* __restrict__ Gf) {
+  fv_lift_body<NP>(p, f, U, flags, Uf, Q, Gf, (long long)blockIdx.x * blockDim.x + threadIdx.x);
+}
+__global__ void __launch_bounds__(128) k_fv_flux(const NskParams p, const FvParams f, const double* __restrict__ Uf,
+                                                 const double* __restrict__ Gf, double* __restrict__ Fh,
+                                                 int* __restrict__ err) {
+  fv_flux_body(p, f, Uf, Gf, Fh, err, (long long)blockIdx.x * blockDim.x + threadIdx.x);
+}
+template <int NP>
+__global__ void __launch_bounds__(128)
+    k_fv_update(const NskParams p, const FvParams f, double* __restrict__ U, double* __restrict__ K,
+                double* __restrict__ Rout, const int* __restrict__ flags, const double* __restrict__ Gf,
+                const double* __restrict__ SL, const double* __restrict__ Q, const double* __restrict__ Fh,
+                const int mode, const double A, const double B, const double* __restrict__ dtp, const double dtv,
+                int* __restrict__ err) {
+  const double dt = dtp ? *dtp : dtv;
+  fv_update_body<NP>(p, f, U, K, Rout, flags, Gf, SL, Q, Fh, mode, A, B, dt, err,
+                     (long long)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+// ---- small meshes: all steps of one call in one cooperative launch ---------------------------
+// An FP64 warp instruction occupies the SM's FP64 pipe for the same time whether 4 or 32 lanes
+// are active, so a small mesh runs fastest with one warp of up to 32 elements per SM. For
+// E <= kCoopMaxE the switch pass and the four phases of each stage run in one cooperative launch
+// of ceil(E / 32) one-warp blocks, separated by the bounded grid barrier; nsteps steps then cost
+// one launch instead of 21 per step. Fixed dt only.
+constexpr int kCoopMaxE = 4096;
+struct LsrkCoef {
+  double A[5], B[5];
+};
+
+template <int NP>
+__global__ void __launch_bounds__(32) k_fv_coop(const NskParams p, const FvParams f, double* __restrict__ U,
+                                                double* __restrict__ K, int* __restrict__ flags,
+                                                double* __restrict__ ind, double* __restrict__ Uf,
+                                                double* __restrict__ Gf, double* __restrict__ SL,
+                                                double* __restrict__ Q, double* __restrict__ Fh, const int nsteps,
+                                                const int switching, const double dt, const LsrkCoef rk,
+                                                unsigned* __restrict__ bar, int* __restrict__ err,
+                                                const unsigned long long timeout_ns) {
+  const long long first = (long long)blockIdx.x * blockDim.x + threadIdx.x, stride = (long long)gridDim.x * blockDim.x;
+  const long long nfaces = f.dirichlet ? p.E + 1 : p.E;
+  for (int step = 0; step < nsteps; ++step) {
+    if (switching) {
+      for (long long e = first; e < p.E; e += stride) fv_switch_body<NP>(p, f, U, flags, ind, e);
+      if (!grid_barrier(bar, err, timeout_ns)) return;
+    }
+    for (int st = 0; st < 5; ++st) {
+      for (long long e = first; e < p.E; e += stride) fv_faces_body<NP>(p, f, U, flags, Uf, Gf, SL, err, e);
+      if (!grid_barrier(bar, err, timeout_ns)) return;
+      for (long long e = first; e < p.E; e += stride) fv_lift_body<NP>(p, f, U, flags, Uf, Q, Gf, e);
+      if (!grid_barrier(bar, err, timeout_ns)) return;
+      for (long long fc = first; fc < nfaces; fc += stride) fv_flux_body(p, f, Uf, Gf, Fh, err, fc);
+      if (!grid_barrier(bar, err, timeout_ns)) return;
+      for (long long e = first; e < p.E; e += stride)
+        fv_update_body<NP>(p, f, U, K, nullptr, flags, Gf, SL, Q, Fh, NSK_MODE_LSRK, rk.A[st], rk.B[st], dt, err, e);
+      if (!grid_barrier(bar, err, timeout_ns)) return;
+    }
+  }
 }
 
 unsigned grid_of(long long n) { return (unsigned)((n + 127) / 128); }
@@ -449,8 +521,59 @@ int launch_stage_t(const NskParams& p, const FvParams& f, const FvBuffers& fb, c
   return cudaGetLastError() == cudaSuccess ? 4 : NSK_ERR_CUDA;
 }
 
+template <int NP>
+int launch_coop_t(const NskParams& p, const FvParams& f, const FvBuffers& fb, const NskBuffers& b, int nsteps,
+                  int switching, double dt, const double* A, const double* B, cudaStream_t s) {
+  auto kern = k_fv_coop<NP>;
+  const int grid = (int)((p.E + 1 + 31) / 32);  // every element and every face
+  int per_sm = 0, dev = 0, sms = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32, 0) != cudaSuccess ||
+      cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return NSK_ERR_CUDA;
+  if ((long long)per_sm * sms < grid) return 0;  // not co-resident: the caller launches per kernel
+  LsrkCoef rk;
+  for (int i = 0; i < 5; ++i) {
+    rk.A[i] = A[i];
+    rk.B[i] = B[i];
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(32);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const unsigned long long timeout_ns = 1000000000ull;  // one second per barrier wait
+  // a barrier that timed out in an earlier launch may have left its arrival count behind
+  if (cudaMemsetAsync(fb.bar, 0, 2 * sizeof(unsigned), s) != cudaSuccess) return NSK_ERR_CUDA;
+  if (cudaLaunchKernelEx(&cfg, kern, p, f, (double*)b.U, (double*)b.K, fb.flags, fb.ind, fb.Uf, fb.Gf, fb.SL,
+                         (double*)b.Q, fb.Fh, nsteps, switching, dt, rk, fb.bar, b.err, timeout_ns) != cudaSuccess)
+    return NSK_ERR_CUDA;
+  return 1;
+}
+
 }  // namespace fv
 }  // namespace nsk
+
+int nsk_fv_coop_max_elements() { return nsk::fv::kCoopMaxE; }
+
+// 1: launched; 0: the grid would not be co-resident (nothing launched); < 0: error
+int nsk_fv_launch_coop(const NskParams& p, const void* fvp, int np, const FvBuffers& fb, const NskBuffers& b,
+                       int nsteps, int switching, double dt, const double* A, const double* B, cudaStream_t s) {
+  const auto& f = *(const nsk::fv::FvParams*)fvp;
+  if (p.E > nsk::fv::kCoopMaxE) return NSK_ERR_ARG;
+  switch (np) {
+    case 2: return nsk::fv::launch_coop_t<2>(p, f, fb, b, nsteps, switching, dt, A, B, s);
+    case 3: return nsk::fv::launch_coop_t<3>(p, f, fb, b, nsteps, switching, dt, A, B, s);
+    case 4: return nsk::fv::launch_coop_t<4>(p, f, fb, b, nsteps, switching, dt, A, B, s);
+    case 5: return nsk::fv::launch_coop_t<5>(p, f, fb, b, nsteps, switching, dt, A, B, s);
+    case 6: return nsk::fv::launch_coop_t<6>(p, f, fb, b, nsteps, switching, dt, A, B, s);
+    default: return NSK_ERR_ARG;
+  }
+}
 
 int nsk_fv_launch_stage(const NskParams& p, const void* fvp, int np, const FvBuffers& fb, const NskBuffers& b,
                         int mode, double* Rout, double A, double B, const double* dtp, double dtv, cudaStream_t s) {

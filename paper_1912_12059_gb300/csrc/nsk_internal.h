@@ -163,12 +163,16 @@ struct FvBuffers {
   double* Gf;    // [E][2][2] (v_x, c_x) of each element side of its faces
   double* SL;    // [E][N+1][3] MinMod slopes of the FV elements
   double* Fh;    // [E+1][3] element-face fluxes
+  unsigned* bar; // [2] grid barrier of the cooperative small-mesh launch (arrivals, generation)
 };
 int nsk_fv_launch_stage(const NskParams& p, const void* fvp, int np, const FvBuffers& fb, const NskBuffers& b,
                         int mode, double* Rout, double A, double B, const double* dtp, double dtv, cudaStream_t s);
 int nsk_fv_launch_switch(const NskParams& p, const void* fvp, int np, const FvBuffers& fb, double* U,
                          cudaStream_t s);
 size_t nsk_fv_params_size();
+int nsk_fv_coop_max_elements();
+int nsk_fv_launch_coop(const NskParams& p, const void* fvp, int np, const FvBuffers& fb, const NskBuffers& b,
+                       int nsteps, int switching, double dt, const double* A, const double* B, cudaStream_t s);
 int nsk_fv_fill_params(void* fvp, int np, const double* xi, const double* gauss_x, const double* gauss_w, double h,
                        int dirichlet, const double* Ub_lo, const double* Ub_hi, double upper, double lower);
 

@@ -221,6 +221,47 @@ __device__ __forceinline__ void cp_async_16(void* sdst, const void* gsrc) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
+// nanoseconds of the global timer
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Grid-wide barrier of a cooperative launch (all blocks co-resident), bounded: a block that waits
+// longer than timeout_ns sets NSK_EBIT_TIMEOUT and every block then returns false (bar[0]: arrivals,
+// bar[1]: generation; both start at zero).
+inline __device__ bool grid_barrier(unsigned* bar, int* err, const unsigned long long timeout_ns) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok = 1;
+    volatile unsigned* vgen = bar + 1;
+    const unsigned gen = *vgen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(bar, 1u);
+    if (arrived == gridDim.x - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      const unsigned long long t0 = global_ns();
+      while (*vgen == gen) {
+        if (global_ns() - t0 > timeout_ns) {
+          atomicOr(err, NSK_EBIT_TIMEOUT);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    if (*(volatile int*)err & NSK_EBIT_TIMEOUT) ok = 0;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
 // --------------------------------------------------------------------------
 // Stage bodies. Every stage kernel below (and the batched persistent kernel in
 // nsk_batch.cu) is a thin wrapper around these device functions:

@@ -135,7 +135,8 @@ def test_switch_parity(gpu, N):
 @pytest.mark.parametrize("N", [2, 3])
 def test_riemann_problem_100_steps(gpu, N):
     """The sharp-interface Riemann problem (Sec. 4) on 40 elements: 100 LSRK4 steps with the
-    switches before every step, same dt on both sides; flags equal, state within 1e-10."""
+    switches before every step (one cooperative launch for the call), same dt on both sides;
+    flags equal, state within 1e-10."""
     E = 40
     s, o = make_pair(E, N, dirichlet=True)
     U = inputs.riemann_1d(o.coords(), 2.0, 0.1, 0.5)
@@ -177,4 +178,41 @@ def test_subcell_api_errors(gpu):
     assert s.subcell()[0].sum() == 1
     with pytest.raises(RuntimeError):
         s.set_subcell(False)  # an element holds sub-cell means
+    s.close()
+
+
+def test_riemann_problem_per_kernel_launches(gpu):
+    """4100 elements (above the 4096 of the single cooperative launch): one launch per kernel and
+    stage; 30 steps against the oracle."""
+    E, N = 4100, 3
+    s, o = make_pair(E, N, dirichlet=True)
+    U = inputs.riemann_1d(o.coords(), 2.0, 0.1, 0.5)
+    dt = o.timestep(U, 0.1)
+    s.set_state(U)
+    s.step(dt, 30)
+    Ug = s.get_state()
+    fg, _ = s.subcell()
+    Uo, fo = o.fv_step(U, np.zeros(E, np.int32), dt, 30)
+    assert fo.sum() >= 1 and np.array_equal(fg, fo)
+    for v in range(3):
+        assert np.abs(Ug[v] - Uo[v]).max() <= 1e-10 * np.abs(Uo[v]).max() + 1e-12, v
+    s.close()
+
+
+def test_riemann_problem_adaptive_dt(gpu):
+    """dt <= 0 (CFL recomputed before every step, per-kernel launches) against the oracle taking
+    its own time step before each of its steps."""
+    E, N = 40, 2
+    s, o = make_pair(E, N, dirichlet=True)
+    U = inputs.riemann_1d(o.coords(), 2.0, 0.1, 0.5)
+    s.set_state(U)
+    s.step(-0.1, 30)
+    Ug = s.get_state()
+    fg, _ = s.subcell()
+    Uo, fo = U, np.zeros(E, np.int32)
+    for _ in range(30):
+        Uo, fo = o.fv_step(Uo, fo, o.timestep(Uo, 0.1), 1)
+    assert np.array_equal(fg, fo)
+    for v in range(3):
+        assert np.abs(Ug[v] - Uo[v]).max() <= 1e-10 * np.abs(Uo[v]).max() + 1e-12, v
     s.close()
