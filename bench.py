@@ -873,6 +873,54 @@ def run_gemm(args, rank, world):
     return 0
 
 
+def run_fp32err(args, rank, world):
+    """FP32 operator against FP64 over a long run (the 64^3 collision, We = 40, fixed dt of the
+    default bench): density L2 relative error, and each run's mass drift, at checkpoints up to
+    --steps steps (5000 when not given)."""
+    import torch
+
+    from paper_1912_12059_gb300 import nsk
+    from paper_1912_12059_gb300.build import build_library
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    build_library()
+    wl = workload_by_name("collision3d")
+    total = args.steps if "--steps" in sys.argv else 5000
+    solvers = {}
+    for prec in (nsk.NSK_FP64, nsk.NSK_FP32_MIXED):
+        s = nsk.Solver(wl.dim, wl.nelem, wl.N, list(wl.lo[:wl.dim]), list(wl.hi[:wl.dim]), wl.node_type, prec)
+        s.set_params(T=wl.T, kappa=wl.kappa, alpha=wl.alpha, beta=wl.beta, mu=wl.mu)
+        solvers[prec] = s
+    s64, s32 = solvers[nsk.NSK_FP64], solvers[nsk.NSK_FP32_MIXED]
+    U0 = wl.initial_state(s64.node_coords())
+    for s in (s64, s32):
+        s.set_state(U0)
+        s.autotune()
+    dt = s64.compute_dt(wl.cfl)
+    m0 = {p: s.diagnostics()[0] for p, s in solvers.items()}
+    checkpoints = [c for c in (10, 100, 500, 1000, 2000, 5000, 10000, 20000) if c < total] + [total]
+    done, rows = 0, []
+    t0 = time.time()
+    for cp in checkpoints:
+        for s in (s64, s32):
+            s.step(dt, cp - done)
+        done = cp
+        r64, r32 = s64.get_state()[0], s32.get_state()[0]
+        err = float(np.sqrt(((r32 - r64) ** 2).sum() / (r64 ** 2).sum()))
+        rows.append({"steps": cp, "density_l2_rel_err": err,
+                     "mass_drift_fp64": (s64.diagnostics()[0] - m0[nsk.NSK_FP64]) / m0[nsk.NSK_FP64],
+                     "mass_drift_fp32": (s32.diagnostics()[0] - m0[nsk.NSK_FP32_MIXED]) / m0[nsk.NSK_FP32_MIXED]})
+    for s in solvers.values():
+        s.close()
+    if rank == 0:
+        print(json.dumps({"metric": "FP32 density L2 relative error vs FP64", "value": rows[-1]["density_l2_rel_err"],
+                          "unit": "relative L2", "n_gpus": 1, "steps": total, "warmup": 0,
+                          "higher_is_better": False, "dtype": "f32 vs f64", "data": "synthetic",
+                          "config": {"workload": wl.name, "dt": dt, "simulated_time": dt * total,
+                                     "wall_s": time.time() - t0, "checkpoints": rows}}))
+    return 0
+
+
 def run_riemann1d(args, rank, world):
     """The 1D sharp-interface Riemann problem with FV sub-cell shock capturing alone (the
     riemann1d_subcell variant of the default run as its own line)."""
@@ -899,7 +947,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="collision3d",
-                    choices=["collision3d", "coalescence2d", "interface1d", "batch", "closure", "gemm", "riemann1d"])
+                    choices=["collision3d", "coalescence2d", "interface1d", "batch", "closure", "gemm", "riemann1d",
+                             "fp32err"])
     ap.add_argument("--rows", type=int, default=884736, help="gemm: rows (elements)")
     ap.add_argument("--no-variants", action="store_true", help="skip the FP32 variant of the default run")
     ap.add_argument("--nelem-train", type=int, default=64, help="closure: training mesh (elements per direction)")
@@ -924,6 +973,8 @@ def main():
         return run_gemm(args, rank, world)
     if args.workload == "riemann1d":
         return run_riemann1d(args, rank, world)
+    if args.workload == "fp32err":
+        return run_fp32err(args, rank, world)
     if args.workload == "batch":
         if args.precision == "fp64" and "--precision" not in sys.argv:
             args.precision = "fp32"
