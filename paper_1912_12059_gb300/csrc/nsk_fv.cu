@@ -174,8 +174,9 @@ template <int NP>
 __device__ __forceinline__ void fv_faces_body(const NskParams& p, const FvParams& f, const double* __restrict__ U,
                                               const int* __restrict__ flags, double* __restrict__ Uf,
                                               double* __restrict__ Gf, double* __restrict__ SL,
-                                              int* __restrict__ err, const long long e) {
-  if (e >= p.E) return;
+                                              int* __restrict__ err, const long long e, const int role) {
+  // role 0 handles the DG elements, role 1 the FV elements (separate warps: no divergence), -1 both
+  if (e >= p.E || (role >= 0 && flags[e] != role)) return;
   int eflag = 0;
   if (!flags[e]) {
 #pragma unroll
@@ -329,8 +330,8 @@ __device__ __forceinline__ void fv_update_body(const NskParams& p, const FvParam
                                                const double* __restrict__ SL, const double* __restrict__ Q,
                                                const double* __restrict__ Fh, const int mode, const double A,
                                                const double B, const double dt, int* __restrict__ err,
-                                               const long long e) {
-  if (e >= p.E) return;
+                                               const long long e, const int role) {
+  if (e >= p.E || (role >= 0 && flags[e] != role)) return;  // role 0: DG elements, 1: FV elements, -1: both
   const auto& t = p.td;
   int eflag = 0;
   double u[3][NP], r[3][NP];
@@ -439,8 +440,12 @@ template <int NP>
 __global__ void __launch_bounds__(128) k_fv_faces(const NskParams p, const FvParams f, const double* __restrict__ U,
                                                   const int* __restrict__ flags, double* __restrict__ Uf,
                                                   double* __restrict__ Gf, double* __restrict__ SL,
-                                                  int* __restrict__ err) {
-  fv_faces_body<NP>(p, f, U, flags, Uf, Gf, SL, err, (long long)blockIdx.x * blockDim.x + threadIdx.x);
+                                                  int* __restrict__ err, const int split) {
+  // split: blocks [0, half) take the DG elements, [half, 2 half) the FV elements
+  const unsigned half = split ? gridDim.x / 2 : gridDim.x;
+  const int role = split ? (int)(blockIdx.x >= half) : -1;
+  const unsigned b = role > 0 ? blockIdx.x - half : blockIdx.x;
+  fv_faces_body<NP>(p, f, U, flags, Uf, Gf, SL, err, (long long)b * blockDim.x + threadIdx.x, role);
 }
 template <int NP>
 __global__ void __launch_bounds__(128) k_fv_lift(const NskParams p, const FvParams f, const double* __restrict__ U,
@@ -459,17 +464,21 @@ __global__ void __launch_bounds__(128)
                 double* __restrict__ Rout, const int* __restrict__ flags, const double* __restrict__ Gf,
                 const double* __restrict__ SL, const double* __restrict__ Q, const double* __restrict__ Fh,
                 const int mode, const double A, const double B, const double* __restrict__ dtp, const double dtv,
-                int* __restrict__ err) {
+                int* __restrict__ err, const int split) {
   const double dt = dtp ? *dtp : dtv;
-  fv_update_body<NP>(p, f, U, K, Rout, flags, Gf, SL, Q, Fh, mode, A, B, dt, err,
-                     (long long)blockIdx.x * blockDim.x + threadIdx.x);
+  const unsigned half = split ? gridDim.x / 2 : gridDim.x;
+  const int role = split ? (int)(blockIdx.x >= half) : -1;
+  const unsigned b = role > 0 ? blockIdx.x - half : blockIdx.x;
+  fv_update_body<NP>(p, f, U, K, Rout, flags, Gf, SL, Q, Fh, mode, A, B, dt, err, (long long)b * blockDim.x + threadIdx.x,
+                     role);
 }
 
 // ---- small meshes: all steps of one call in one cooperative launch ---------------------------
 // An FP64 warp instruction occupies the SM's FP64 pipe for the same time whether 4 or 32 lanes
 // are active, so a small mesh runs fastest with one warp of up to 32 elements per SM. For
 // E <= kCoopMaxE the switch pass and the four phases of each stage run in one cooperative launch
-// of ceil(E / 32) one-warp blocks, separated by the bounded grid barrier; nsteps steps then cost
+// of 2 ceil((E + 1) / 32) one-warp blocks (the face-state and update phases give DG and FV elements
+// to separate halves of the grid), separated by the bounded grid barrier; nsteps steps then cost
 // one launch instead of 21 per step. Fixed dt only.
 constexpr int kCoopMaxE = 4096;
 struct LsrkCoef {
@@ -487,37 +496,48 @@ __global__ void __launch_bounds__(32) k_fv_coop(const NskParams p, const FvParam
                                                 const unsigned long long timeout_ns) {
   const long long first = (long long)blockIdx.x * blockDim.x + threadIdx.x, stride = (long long)gridDim.x * blockDim.x;
   const long long nfaces = f.dirichlet ? p.E + 1 : p.E;
+  // faces and update: the first half of the blocks takes the DG elements, the second the FV ones
+  const unsigned half = gridDim.x / 2;
+  const int role = blockIdx.x >= half;
+  const long long rfirst = (long long)(blockIdx.x - role * half) * blockDim.x + threadIdx.x,
+                  rstride = (long long)half * blockDim.x;
   for (int step = 0; step < nsteps; ++step) {
     if (switching) {
       for (long long e = first; e < p.E; e += stride) fv_switch_body<NP>(p, f, U, flags, ind, e);
       if (!grid_barrier(bar, err, timeout_ns)) return;
     }
     for (int st = 0; st < 5; ++st) {
-      for (long long e = first; e < p.E; e += stride) fv_faces_body<NP>(p, f, U, flags, Uf, Gf, SL, err, e);
+      for (long long e = rfirst; e < p.E; e += rstride) fv_faces_body<NP>(p, f, U, flags, Uf, Gf, SL, err, e, role);
       if (!grid_barrier(bar, err, timeout_ns)) return;
       for (long long e = first; e < p.E; e += stride) fv_lift_body<NP>(p, f, U, flags, Uf, Q, Gf, e);
       if (!grid_barrier(bar, err, timeout_ns)) return;
       for (long long fc = first; fc < nfaces; fc += stride) fv_flux_body(p, f, Uf, Gf, Fh, err, fc);
       if (!grid_barrier(bar, err, timeout_ns)) return;
-      for (long long e = first; e < p.E; e += stride)
-        fv_update_body<NP>(p, f, U, K, nullptr, flags, Gf, SL, Q, Fh, NSK_MODE_LSRK, rk.A[st], rk.B[st], dt, err, e);
+      for (long long e = rfirst; e < p.E; e += rstride)
+        fv_update_body<NP>(p, f, U, K, nullptr, flags, Gf, SL, Q, Fh, NSK_MODE_LSRK, rk.A[st], rk.B[st], dt, err, e,
+                           role);
       if (!grid_barrier(bar, err, timeout_ns)) return;
     }
   }
 }
 
 unsigned grid_of(long long n) { return (unsigned)((n + 127) / 128); }
+constexpr long long kSplitMaxE = 65536;  // largest mesh whose per-kernel launches split DG and FV work
 
 template <int NP>
 int launch_stage_t(const NskParams& p, const FvParams& f, const FvBuffers& fb, const NskBuffers& b, int mode,
                    double* Rout, double A, double B, const double* dtp, double dtv, cudaStream_t s) {
   const long long E = p.E;
   const unsigned ge = grid_of(E);
-  k_fv_faces<NP><<<ge, 128, 0, s>>>(p, f, (const double*)b.U, fb.flags, fb.Uf, fb.Gf, fb.SL, b.err);
+  // small meshes: DG and FV elements in separate halves of a doubled grid (the slowest thread of
+  // a kernel otherwise runs both code paths); large meshes fill the GPU without it
+  const int split = E <= kSplitMaxE;
+  k_fv_faces<NP><<<(split ? 2 : 1) * ge, 128, 0, s>>>(p, f, (const double*)b.U, fb.flags, fb.Uf, fb.Gf, fb.SL, b.err,
+                                                     split);
   k_fv_lift<NP><<<ge, 128, 0, s>>>(p, f, (const double*)b.U, fb.flags, fb.Uf, (double*)b.Q, fb.Gf);
   k_fv_flux<<<grid_of(E + 1), 128, 0, s>>>(p, f, fb.Uf, fb.Gf, fb.Fh, b.err);
-  k_fv_update<NP><<<ge, 128, 0, s>>>(p, f, (double*)b.U, (double*)b.K, Rout, fb.flags, fb.Gf, fb.SL,
-                                     (const double*)b.Q, fb.Fh, mode, A, B, dtp, dtv, b.err);
+  k_fv_update<NP><<<(split ? 2 : 1) * ge, 128, 0, s>>>(p, f, (double*)b.U, (double*)b.K, Rout, fb.flags, fb.Gf, fb.SL,
+                                     (const double*)b.Q, fb.Fh, mode, A, B, dtp, dtv, b.err, split);
   return cudaGetLastError() == cudaSuccess ? 4 : NSK_ERR_CUDA;
 }
 
@@ -525,7 +545,7 @@ template <int NP>
 int launch_coop_t(const NskParams& p, const FvParams& f, const FvBuffers& fb, const NskBuffers& b, int nsteps,
                   int switching, double dt, const double* A, const double* B, cudaStream_t s) {
   auto kern = k_fv_coop<NP>;
-  const int grid = (int)((p.E + 1 + 31) / 32);  // every element and every face
+  const int grid = 2 * (int)((p.E + 1 + 31) / 32);  // every element and face, twice (DG and FV roles)
   int per_sm = 0, dev = 0, sms = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32, 0) != cudaSuccess ||
       cudaGetDevice(&dev) != cudaSuccess ||
