@@ -200,9 +200,14 @@ int nsk_compute_dt(nsk_ctx* ctx, double cfl, double* dt_out);
  * step dt (dt > 0), or, with dt <= 0, with nsk_compute_dt(ctx, -dt) recomputed
  * before every step (so dt = -0.5 means CFL 0.5). Within one call the volume
  * kernel of each stage writes the face traces of its updated state, so only
- * the first stage of a call runs the prolongation pass (model II). Returns
- * after the work is queued and checked: the call synchronises the stream once
- * at the end to read the error word. */
+ * the first stage of a call runs the prolongation pass (model II). With
+ * nsk_set_subcell or nsk_set_dirichlet active the call runs the 1D sub-cell
+ * path instead (the indicator and switch pass before every step when sub-cells
+ * are on): with dt > 0 and at most 4096 elements the whole call is one
+ * cooperative launch (bounded grid barriers; NSK_ERR_TIMEOUT if a wait expires),
+ * otherwise four launches per stage (and the switch launch per step). Returns after the work is queued and
+ * checked: the call synchronises the stream once at the end to read the error
+ * word. */
 int nsk_step(nsk_ctx* ctx, double dt, int nsteps);
 
 /* Quadrature sums (FP64): mass sum w J rho; the total energy of the relaxation
