@@ -128,8 +128,8 @@ struct NskLaunch {
   cudaEvent_t* ev;         // NULL, or NSK_NKERN + 1 events bracketing the kernels
   int tpb;                 // block-size schedule: 128 or 256 threads (elements per block follow)
   int fused_face;          // 1: face fluxes evaluated inside the volume kernel
-  int traces_ready;        // 1: Utr already holds the traces of U (no prolongation pass)
-  void* utr_next;          // non-NULL: the volume kernel writes the traces of its output state here
+  int traces_ready = 0;    // 1: Utr already holds the traces of U (no prolongation pass)
+  void* utr_next = nullptr;  // non-NULL: the volume kernel writes the traces of its output state here
 };
 
 #define NSK_NKERN 4  // prolong, lift, face, volume

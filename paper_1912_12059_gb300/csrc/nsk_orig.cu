@@ -193,7 +193,7 @@ __device__ __forceinline__ void volume_group(const NskParams& p, double* __restr
                                              const double B, const double dt, const long long e0, double* sm,
                                              int& eflag) {
   using S = Shape<D, NP>;
-  constexpr int NPE = S::NPE, NFN = S::NFN, NW = S::NW, NF = S::NF, NQ = S::NQ, NV = D + 1;
+  constexpr int NPE = S::NPE, NFN = S::NFN, NF = S::NF, NQ = S::NQ, NV = D + 1;
   double* sf = sm;                       // [G][D][NV][NPE]
   double* sfs = sm + G * D * NV * NPE;   // [G][NF][NV][NFN]
   double* tb = sfs + G * NF * NV * NFN;
