@@ -216,3 +216,21 @@ def test_riemann_problem_adaptive_dt(gpu):
     for v in range(3):
         assert np.abs(Ug[v] - Uo[v]).max() <= 1e-10 * np.abs(Uo[v]).max() + 1e-12, v
     s.close()
+
+
+def test_riemann_problem_large_mesh_unsplit_launches(gpu):
+    """70,000 elements: per-kernel launches without the DG/FV split of small meshes (above
+    65,536 elements); 5 steps against the oracle."""
+    E, N = 70000, 3
+    s, o = make_pair(E, N, dirichlet=True)
+    U = inputs.riemann_1d(o.coords(), 2.0, 0.1, 0.5)
+    dt = o.timestep(U, 0.1)
+    s.set_state(U)
+    s.step(dt, 5)
+    Ug = s.get_state()
+    fg, _ = s.subcell()
+    Uo, fo = o.fv_step(U, np.zeros(E, np.int32), dt, 5)
+    assert fo.sum() >= 1 and np.array_equal(fg, fo)
+    for v in range(3):
+        assert np.abs(Ug[v] - Uo[v]).max() <= 1e-10 * np.abs(Uo[v]).max() + 1e-12, v
+    s.close()
