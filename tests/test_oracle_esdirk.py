@@ -1,0 +1,91 @@
+"""Pins of the oracle's implicit time integration (oracle/esdirk.py: the six-stage fourth-order
+ESDIRK of Sec. 3.1, Kennedy and Carpenter's ARK4(3)6L[2]SA implicit tableau, Jacobian-free
+Newton-Krylov). No GPU.
+
+Against facts independent of the code: the order conditions of the tableau in exact rational
+arithmetic, the published abscissae, fourth-order convergence to closed-form ODE solutions,
+L-stability, GMRES against a direct solve, and the closed-form uniform relaxation of the c
+equation through the oracle's DG residual.
+"""
+import math
+from fractions import Fraction as Fr
+
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import esdirk as ES
+
+
+def test_tableau_order_conditions_exact():
+    A, b, c = ES.tableau(exact=True)
+    n = ES.STAGES
+    assert c == [Fr(0), Fr(1, 2), Fr(83, 250), Fr(31, 50), Fr(17, 20), Fr(1)]
+    assert b == A[-1]  # stiffly accurate
+    assert all(A[i][i] == Fr(1, 4) for i in range(1, n)) and A[0][0] == 0  # explicit first stage
+    s = lambda f: sum(f(i) for i in range(n))  # noqa: E731
+    Ac = [sum(A[i][j] * c[j] for j in range(n)) for i in range(n)]
+    Ac2 = [sum(A[i][j] * c[j] ** 2 for j in range(n)) for i in range(n)]
+    AAc = [sum(A[i][j] * Ac[j] for j in range(n)) for i in range(n)]
+    assert s(lambda i: b[i]) == 1
+    assert s(lambda i: b[i] * c[i]) == Fr(1, 2)
+    assert s(lambda i: b[i] * c[i] ** 2) == Fr(1, 3)
+    assert s(lambda i: b[i] * Ac[i]) == Fr(1, 6)
+    assert s(lambda i: b[i] * c[i] ** 3) == Fr(1, 4)
+    assert s(lambda i: b[i] * c[i] * Ac[i]) == Fr(1, 8)
+    assert s(lambda i: b[i] * Ac2[i]) == Fr(1, 12)
+    assert s(lambda i: b[i] * AAc[i]) == Fr(1, 24)
+
+
+def _run(rhs, y0, T, n):
+    y = np.array([y0], dtype=float)
+    for _ in range(n):
+        y, _ = ES.step(rhs, y, T / n, newton_tol=1e-14, krylov_tol=1e-14, m=5)
+    return y[0]
+
+
+@pytest.mark.parametrize("rhs,exact", [
+    (lambda y: -1.3 * y, lambda t: math.exp(-1.3 * t)),
+    (lambda y: -y * y, lambda t: 1.0 / (1.0 + t)),
+])
+def test_fourth_order_convergence(rhs, exact):
+    errs = [abs(_run(rhs, 1.0, 1.0, n) - exact(1.0)) for n in (8, 16, 32)]
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert min(rates) > 3.7, (errs, rates)
+
+
+def test_l_stability():
+    """y' = lambda y with lambda dt = -1e8: the stiffly accurate, L-stable scheme damps the mode."""
+    y = _run(lambda y: -1e8 * y, 1.0, 1.0, 1)
+    assert abs(y) < 1e-6
+
+
+def test_gmres_against_a_direct_solve():
+    rng = np.random.Generator(np.random.PCG64(4))
+    M = np.eye(40) * 3 + rng.standard_normal((40, 40)) * 0.2
+    b = rng.standard_normal(40)
+    x, its = ES.gmres(lambda v: M @ v, b, 1e-12, 15, 400)
+    assert np.linalg.norm(M @ x - b) <= 1e-11 * np.linalg.norm(b)
+    assert its > 15  # restarts happened
+
+
+def test_uniform_relaxation_through_the_dg_residual():
+    """Spatially constant rho, v = 0, c0 != rho: the residual reduces to the source, c(t) =
+    rho + (c0 - rho) exp(-alpha t / beta). Steps of 5 beta/alpha (far above the explicit bound
+    4.6 beta/alpha x cfl) converge at fourth order to the closed form."""
+    o = O.Oracle(1, (4,), (0.0,), (1.0,), 3, O.NODES_GAUSS, alpha=100.0, beta=1e-3, kappa=1e-4, mu=1e-3)
+    rho, c0 = 1.2, 1.25
+    U = np.zeros(o.shape)
+    U[0], U[2] = rho, c0
+    lam = o.s.alpha / o.s.beta
+    T = 20.0 / lam
+    errs = []
+    for n in (4, 8, 16):
+        V = U.copy()
+        for _ in range(n):
+            V, st = ES.step(o.rhs, V, T / n, newton_tol=1e-13, krylov_tol=1e-12)
+        assert st["failed"] == 0
+        errs.append(np.abs(V[2] - (rho + (c0 - rho) * math.exp(-lam * T))).max())
+        assert np.abs(V[0] - rho).max() < 1e-12
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert min(rates) > 3.5, (errs, rates)
