@@ -210,6 +210,23 @@ int nsk_compute_dt(nsk_ctx* ctx, double cfl, double* dt_out);
  * word. */
 int nsk_step(nsk_ctx* ctx, double dt, int nsteps);
 
+/* Implicit time integration (Sec. 3.1): nsteps steps of size dt of the six-stage, fourth-order
+ * ESDIRK the paper cites (the implicit tableau of Kennedy and Carpenter's ARK4(3)6L[2]SA,
+ * gamma = 1/4, stiffly accurate, L-stable) on the context's residual (nsk_rhs). Each implicit
+ * stage X - dt gamma R(X) = U_n + dt sum_{j<i} a_ij R_j is solved by Newton's method from the
+ * previous stage until the Euclidean norm of its residual is <= newton_tol times that of the
+ * right-hand side (at most 20 iterations; stats[3] counts stages that stopped there), each
+ * Newton system by restarted GMRES(krylov_dim) to the relative residual krylov_tol (at most
+ * max_krylov iterations per system), matrix-free: J v ~ (R(X + eps v) - R(X)) / eps with
+ * eps = sqrt(2^-52) (1 + ||X||) / ||v||, no preconditioner. stats (may be NULL): Newton
+ * iterations, Krylov iterations, residual evaluations, stages stopped at the iteration limit,
+ * summed over the call. FP64 contexts with the explicit c equation and without the sub-cell
+ * path only (NSK_ERR_ARG otherwise). Allocates 12 + krylov_dim state-sized FP64 buffers for the
+ * call and frees them before returning; every dot product synchronises the stream (the GMRES
+ * control runs on the host). */
+int nsk_step_esdirk(nsk_ctx* ctx, double dt, int nsteps, double newton_tol, double krylov_tol, int krylov_dim,
+                    int max_krylov, long long stats[4]);
+
 /* Quadrature sums (FP64): mass sum w J rho; the total energy of the relaxation
  * model sum w J (|m|^2/(2 rho) + W(rho) + alpha/2 (rho-c)^2 + kappa/2 |grad c|^2)
  * (Eq. pararelax_elliptical_energy_dynamic, grad c from BR1); and

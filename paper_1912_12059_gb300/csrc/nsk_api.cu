@@ -315,6 +315,7 @@ void free_ctx(nsk_ctx* c) {
 }  // namespace
 
 int nsk_ctx_launch_stage(nsk_ctx* c, NskLaunch l) { return launch_stage(c, l); }
+int nsk_ctx_sync_check(nsk_ctx* c) { return sync_and_check(c); }
 
 namespace {
 // device time step of the context's model (kernel launches issued, or an NSK_ERR_* code)

@@ -1,0 +1,268 @@
+// nsk_implicit.cu -- implicit time integration: the six-stage, fourth-order ESDIRK that Sec. 3.1
+// cites (the implicit tableau of Kennedy and Carpenter's ARK4(3)6L[2]SA, gamma = 1/4, stiffly
+// accurate) with Jacobian-free Newton-Krylov on the residual kernels of the context.
+//
+// Every implicit stage G(X) = X - dt gamma R(X) - S_i = 0, S_i = U_n + dt sum_{j<i} a_ij R_j, is
+// solved by Newton's method from the previous stage's value until ||G|| <= newton_tol ||S_i||;
+// each Newton system (I - dt gamma J) d = -G by restarted GMRES(m) (modified Gram-Schmidt,
+// Givens rotations, relative residual krylov_tol, no preconditioner) with the matrix-free
+// product J v ~ (R(X + eps v) - R(X)) / eps, eps = sqrt(2^-52) (1 + ||X||) / ||v||; the later
+// stages use R_i = (X_i - S_i) / (dt gamma). The vector algebra runs in the kernels below
+// (dot products in a fixed order: deterministic), the small GMRES least-squares problem and the
+// control flow on the host; a residual evaluation is one stage launch of the context's pipeline
+// in residual mode on the iterate.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "nsk_internal.h"
+
+namespace {
+
+constexpr int kDotThreads = 256;
+constexpr int kDotBlocks = 152 * 8;
+
+// out = a x + b y + c z (y, z may be NULL; out may be x, y or z: each element is read before it
+// is written by the same thread)
+__global__ void __launch_bounds__(256) k_lincomb(const long long n, const double a, const double* x, const double b,
+                                                 const double* y, const double c, const double* z, double* out) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    double v = a * x[i];
+    if (y) v = fma(b, y[i], v);
+    if (z) v = fma(c, z[i], v);
+    out[i] = v;
+  }
+}
+
+// per-block partial sums of x . y (grid-stride per thread, then a shared-memory tree: the same
+// order on every call)
+__global__ void __launch_bounds__(kDotThreads) k_dot_part(const long long n, const double* __restrict__ x,
+                                                          const double* __restrict__ y, double* __restrict__ part) {
+  __shared__ double red[kDotThreads];
+  double s = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    s = fma(x[i], y[i], s);
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = kDotThreads / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+__global__ void __launch_bounds__(kDotThreads) k_dot_final(const int nb, const double* __restrict__ part,
+                                                           double* __restrict__ out) {
+  __shared__ double red[kDotThreads];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) s += part[i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = kDotThreads / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = red[0];
+}
+
+// ARK4(3)6L[2]SA, implicit part (Kennedy and Carpenter 2003): a_ij for j < i; gamma = 1/4
+const double kGamma = 0.25;
+const double kA6[6][5] = {
+    {0, 0, 0, 0, 0},
+    {1.0 / 4.0, 0, 0, 0, 0},
+    {8611.0 / 62500.0, -1743.0 / 31250.0, 0, 0, 0},
+    {5012029.0 / 34652500.0, -654441.0 / 2922500.0, 174375.0 / 388108.0, 0, 0},
+    {15267082809.0 / 155376265600.0, -71443401.0 / 120774400.0, 730878875.0 / 902184768.0, 2285395.0 / 8070912.0, 0},
+    {82889.0 / 524892.0, 0.0, 15625.0 / 83664.0, 69875.0 / 102672.0, -2260.0 / 8211.0},
+};
+
+struct Implicit {
+  nsk_ctx* c;
+  long long n;          // values of a state vector
+  cudaStream_t s;
+  unsigned grid;
+  double* part;         // dot partials
+  double* dotv;         // device result of a dot product
+  long long launches = 0;
+  long long rhs_evals = 0;
+  int status = NSK_OK;
+
+  void lincomb(double a, const double* x, double b, const double* y, double cc, const double* z, double* out) {
+    k_lincomb<<<grid, 256, 0, s>>>(n, a, x, b, y, cc, z, out);
+    ++launches;
+  }
+  double dot(const double* x, const double* y) {
+    k_dot_part<<<kDotBlocks, kDotThreads, 0, s>>>(n, x, y, part);
+    k_dot_final<<<1, kDotThreads, 0, s>>>(kDotBlocks, part, dotv);
+    launches += 2;
+    double h = 0.0;
+    if (cudaMemcpyAsync(&h, dotv, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      status = NSK_ERR_CUDA;
+    return h;
+  }
+  double norm(const double* x) { return sqrt(dot(x, x)); }
+  // out = R(X): one residual-mode stage of the context's pipeline on X
+  void rhs(double* X, double* out) {
+    void* saved = c->b.U;
+    c->b.U = X;
+    NskLaunch l = {NSK_MODE_RHS, out, 0.0, 0.0, nullptr, 0.0, nullptr, c->tpb, c->fused_face};
+    const int r = nsk_ctx_launch_stage(c, l);
+    c->b.U = saved;
+    if (r) status = r;
+    ++rhs_evals;
+  }
+};
+
+}  // namespace
+
+int nsk_step_esdirk(nsk_ctx* c, double dt, int nsteps, double newton_tol, double krylov_tol, int krylov_dim,
+                    int max_krylov, long long stats[4]) {
+  if (!c || !(dt > 0.0) || !isfinite(dt) || nsteps < 0 || !(newton_tol > 0.0) || !(krylov_tol > 0.0) ||
+      krylov_dim < 1 || krylov_dim > 200 || max_krylov < 1)
+    return NSK_ERR_ARG;
+  if (c->precision != NSK_FP64 || c->closure_mode != NSK_C_EXPLICIT || c->fv_path()) return NSK_ERR_ARG;
+  if (!c->state_set) return NSK_ERR_STATE;
+  const int m = krylov_dim;
+  const long long n = (long long)c->nvar * c->nn;
+  // state-sized buffers: R_0..R_4, X, S, RX, D (Newton update), W (X + eps v), RW, V_0..V_m
+  const int nbuf = 5 + 6 + (m + 1);
+  double* pool = nullptr;
+  if (cudaMalloc(&pool, sizeof(double) * (size_t)n * nbuf) != cudaSuccess) {
+    cudaGetLastError();
+    return NSK_ERR_NOMEM;
+  }
+  double* part = nullptr;
+  if (cudaMalloc(&part, sizeof(double) * (kDotBlocks + 1)) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(pool);
+    return NSK_ERR_NOMEM;
+  }
+  auto buf = [&](int k) { return pool + (size_t)k * n; };
+  double* Rj[5] = {buf(0), buf(1), buf(2), buf(3), buf(4)};
+  double *X = buf(5), *S = buf(6), *RX = buf(7), *D = buf(8), *W = buf(9), *RW = buf(10);
+  std::vector<double*> V(m + 1);
+  for (int k = 0; k <= m; ++k) V[k] = buf(11 + k);
+
+  Implicit im;
+  im.c = c;
+  im.n = n;
+  im.s = c->stream;
+  const long long g = (n + 255) / 256;
+  im.grid = (unsigned)(g < 152 * 16 ? (g > 0 ? g : 1) : 152 * 16);
+  im.part = part;
+  im.dotv = part + kDotBlocks;
+  long long st_newton = 0, st_krylov = 0, st_fail = 0;
+  double* U = (double*)c->b.U;  // U_n, then U_{n+1}
+  const double gdt = kGamma * dt;
+  std::vector<double> H((size_t)(m + 1) * m), gv(m + 1), cs(m), sn(m), y(m);
+
+  for (int step = 0; step < nsteps && im.status == NSK_OK; ++step) {
+    im.rhs(U, Rj[0]);
+    im.lincomb(1.0, U, 0.0, nullptr, 0.0, nullptr, X);
+    for (int i = 1; i < 6 && im.status == NSK_OK; ++i) {
+      // S_i = U_n + dt sum_{j<i} a_ij R_j
+      im.lincomb(1.0, U, 0.0, nullptr, 0.0, nullptr, S);
+      for (int j = 0; j < i; ++j)
+        if (kA6[i][j] != 0.0) im.lincomb(1.0, S, dt * kA6[i][j], Rj[j], 0.0, nullptr, S);
+      const double snorm = im.norm(S);
+      for (int it = 0;; ++it) {
+        im.rhs(X, RX);
+        im.lincomb(1.0, X, -gdt, RX, -1.0, S, V[0]);  // G = X - dt gamma R(X) - S
+        const double gnorm = im.norm(V[0]);
+        if (im.status != NSK_OK || gnorm <= newton_tol * snorm) break;
+        if (it == 20) {
+          ++st_fail;
+          break;
+        }
+        // GMRES for (I - dt gamma J) D = -G, from D = 0
+        const double xn = im.norm(X);
+        const double bn = gnorm;  // ||-G||
+        if (cudaMemsetAsync(D, 0, sizeof(double) * (size_t)n, im.s) != cudaSuccess) im.status = NSK_ERR_CUDA;
+        double beta = gnorm;
+        im.lincomb(-1.0 / beta, V[0], 0.0, nullptr, 0.0, nullptr, V[0]);  // V_0 = -G / ||G||
+        int its = 0;
+        bool done = false;
+        while (!done && im.status == NSK_OK) {
+          std::fill(H.begin(), H.end(), 0.0);
+          std::fill(gv.begin(), gv.end(), 0.0);
+          gv[0] = beta;
+          int k = 0;
+          for (k = 0; k < m; ++k) {
+            // V_{k+1} = (I - dt gamma J) V_k with J V_k ~ (R(X + eps V_k) - R(X)) / eps (||V_k|| = 1)
+            const double eps = sqrt(ldexp(1.0, -52)) * (1.0 + xn);
+            im.lincomb(1.0, X, eps, V[k], 0.0, nullptr, W);
+            im.rhs(W, RW);
+            im.lincomb(1.0, V[k], -gdt / eps, RW, gdt / eps, RX, V[k + 1]);
+            ++its;
+            for (int j = 0; j <= k; ++j) {  // modified Gram-Schmidt
+              const double h = im.dot(V[k + 1], V[j]);
+              H[(size_t)j * m + k] = h;
+              im.lincomb(1.0, V[k + 1], -h, V[j], 0.0, nullptr, V[k + 1]);
+            }
+            const double hn = im.norm(V[k + 1]);
+            H[(size_t)(k + 1) * m + k] = hn;
+            if (hn > 0.0) im.lincomb(1.0 / hn, V[k + 1], 0.0, nullptr, 0.0, nullptr, V[k + 1]);
+            for (int j = 0; j < k; ++j) {  // earlier Givens rotations
+              const double a = H[(size_t)j * m + k], b = H[(size_t)(j + 1) * m + k];
+              H[(size_t)j * m + k] = cs[j] * a + sn[j] * b;
+              H[(size_t)(j + 1) * m + k] = -sn[j] * a + cs[j] * b;
+            }
+            const double a = H[(size_t)k * m + k], b = H[(size_t)(k + 1) * m + k];
+            const double d = hypot(a, b);
+            cs[k] = a / d;
+            sn[k] = b / d;
+            H[(size_t)k * m + k] = d;
+            H[(size_t)(k + 1) * m + k] = 0.0;
+            gv[k + 1] = -sn[k] * gv[k];
+            gv[k] = cs[k] * gv[k];
+            if (fabs(gv[k + 1]) <= krylov_tol * bn || its >= max_krylov) break;
+          }
+          const int kk = (k < m ? k : m - 1) + 1;
+          for (int r = kk - 1; r >= 0; --r) {  // back substitution on the triangular Hessenberg
+            double t = gv[r];
+            for (int j = r + 1; j < kk; ++j) t -= H[(size_t)r * m + j] * y[j];
+            y[r] = t / H[(size_t)r * m + r];
+          }
+          for (int j = 0; j < kk; ++j) im.lincomb(1.0, D, y[j], V[j], 0.0, nullptr, D);
+          if (fabs(gv[kk]) <= krylov_tol * bn || its >= max_krylov) {
+            done = true;
+          } else {  // restart: r = -G - (I - dt gamma J) D
+            const double dn = im.norm(D);
+            if (!(dn > 0.0)) break;  // no progress in this cycle
+            const double eps = sqrt(ldexp(1.0, -52)) * (1.0 + xn) / dn;
+            im.lincomb(1.0, X, eps, D, 0.0, nullptr, W);
+            im.rhs(W, RW);
+            // V_0 = -G - D + (dt gamma / eps)(R(X + eps D) - R(X)); -G from X, RX, S
+            im.lincomb(-1.0, X, gdt, RX, 1.0, S, V[0]);
+            im.lincomb(1.0, V[0], -1.0, D, 0.0, nullptr, V[0]);
+            im.lincomb(1.0, V[0], gdt / eps, RW, -gdt / eps, RX, V[0]);
+            beta = im.norm(V[0]);
+            if (!(beta > 0.0)) break;
+            im.lincomb(1.0 / beta, V[0], 0.0, nullptr, 0.0, nullptr, V[0]);
+          }
+        }
+        im.lincomb(1.0, X, 1.0, D, 0.0, nullptr, X);
+        ++st_newton;
+        st_krylov += its;
+      }
+      if (i < 5) im.lincomb(1.0 / gdt, X, -1.0 / gdt, S, 0.0, nullptr, Rj[i]);  // R_i = (X_i - S_i) / (dt gamma)
+    }
+    im.lincomb(1.0, X, 0.0, nullptr, 0.0, nullptr, U);  // stiffly accurate: U_{n+1} = X_6
+  }
+  int r = im.status;
+  const int rs = nsk_ctx_sync_check(c);
+  if (r == NSK_OK) r = rs;
+  c->launches += im.launches;
+  cudaFree(part);
+  cudaFree(pool);
+  if (stats) {
+    stats[0] = st_newton;
+    stats[1] = st_krylov;
+    stats[2] = im.rhs_evals;
+    stats[3] = st_fail;
+  }
+  return r;
+}

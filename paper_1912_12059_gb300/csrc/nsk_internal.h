@@ -221,6 +221,7 @@ struct nsk_ctx {
 
 // host helpers shared by the translation units of the library
 int nsk_ctx_launch_stage(nsk_ctx* c, NskLaunch l);  // queues one stage on the context's stream
+int nsk_ctx_sync_check(nsk_ctx* c);                  // synchronise the stream, read and clear the error word
 // c := rho + s * network(features(rho)); utr non-NULL: also the traces of the new c there
 int nsk_closure_apply_ctx(nsk_ctx* c, void* utr);
 int nsk_closure_judge_ctx(nsk_ctx* c);               // judge + fallback (synchronises)
