@@ -343,6 +343,7 @@ def run_gpu(args, wl, rank, world):
         variants["fp64_hllc"] = measure_hllc_variant(args, wl, stream, U0, U_after, dt)
         variants["fp64_original_nsk"] = measure_nsk_variant(args, wl, stream, U0, dt)
         variants["riemann1d_subcell"] = measure_subcell_variant(args, stream)
+        variants["esdirk4_implicit"] = measure_esdirk_variant(args, stream)
 
     if rank != 0:
         return 0
@@ -591,6 +592,57 @@ def measure_subcell_variant(args, stream):
                          "value": nodes * 5 * args.steps / (ms / 1e3), "unit": "DOF-updates/s",
                          "subcell_elements": int(flags.sum()), "launches_per_step": 21}
     s.close()
+    return out
+
+
+def measure_esdirk_variant(args, stream):
+    """Implicit ESDIRK4 with Jacobian-free Newton-Krylov (nsk_step_esdirk) against the explicit
+    LSRK4 over the same simulated time: the 1D static phase interface (64 elements, N = 3,
+    alpha = 100, beta = 1e-2, kappa = 1e-4, mu = 1e-2), T = 100 explicit CFL-0.5 steps, advanced
+    by one implicit step of 100x and by ten of 10x the explicit step: wall time, residual
+    evaluations, Newton and Krylov iterations, and the density L2 difference to the explicit run."""
+    import torch
+
+    from paper_1912_12059_gb300 import inputs, nsk
+
+    prm = dict(T=0.85, kappa=1e-4, alpha=100.0, beta=1e-2, mu=1e-2)
+    E, N = 64, 3
+
+    def make():
+        s = nsk.Solver(1, (E,), N, [0.0], [1.0], 0, nsk.NSK_FP64, stream=stream.cuda_stream)
+        s.set_params(**prm)
+        s.set_state(inputs.slab_1d(s.node_coords(), inputs.PAPER_RHO_VAP, inputs.PAPER_RHO_LIQ, prm["kappa"]))
+        return s
+
+    s = make()
+    dte = s.compute_dt(0.5)
+    out = {"workload": f"static_interface_1d_E{E}_N{N}_alpha100_beta1e-2", "explicit_dt": dte,
+           "simulated_time": 100 * dte, "newton_tol": 1e-10, "krylov_tol": 1e-3, "krylov_dim": 30}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.step(dte, 3)  # warm-up
+    s.close()
+    s = make()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    s.step(dte, 100)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ref = s.get_state()
+    out["explicit_lsrk4"] = {"steps": 100, "wall_ms": e0.elapsed_time(e1), "rhs_evaluations": 500}
+    s.close()
+    for fac in (100, 10):
+        s = make()
+        torch.cuda.synchronize()
+        t0 = time.time()
+        st = s.step_esdirk(fac * dte, 100 // fac, newton_tol=1e-10, krylov_tol=1e-3, krylov_dim=30)
+        torch.cuda.synchronize()
+        ms = (time.time() - t0) * 1e3
+        U = s.get_state()
+        err = float(np.sqrt(((U[0] - ref[0]) ** 2).sum() / (ref[0] ** 2).sum()))
+        out[f"esdirk4_{fac}x"] = {"steps": 100 // fac, "wall_ms": ms, "rhs_evaluations": st["rhs"],
+                                  "newton": st["newton"], "krylov": st["krylov"], "failed": st["failed"],
+                                  "density_l2_rel_diff_vs_explicit": err}
+        s.close()
     return out
 
 
@@ -921,6 +973,24 @@ def run_fp32err(args, rank, world):
     return 0
 
 
+def run_esdirk(args, rank, world):
+    """The implicit ESDIRK4 comparison (the esdirk4_implicit variant of the default run) alone."""
+    import torch
+
+    from paper_1912_12059_gb300.build import build_library
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    build_library()
+    stream = torch.cuda.Stream()
+    v = measure_esdirk_variant(args, stream)
+    if rank == 0:
+        x = v["esdirk4_100x"]
+        print(json.dumps({"metric": "wall ms to the same simulated time (implicit, 100x explicit dt)",
+                          "value": x["wall_ms"], "unit": "ms", "n_gpus": 1, "steps": x["steps"], "warmup": 0,
+                          "higher_is_better": False, "dtype": "f64", "data": "synthetic", "config": v}))
+    return 0
+
+
 def run_riemann1d(args, rank, world):
     """The 1D sharp-interface Riemann problem with FV sub-cell shock capturing alone (the
     riemann1d_subcell variant of the default run as its own line)."""
@@ -948,7 +1018,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="collision3d",
                     choices=["collision3d", "coalescence2d", "interface1d", "batch", "closure", "gemm", "riemann1d",
-                             "fp32err"])
+                             "fp32err", "esdirk"])
     ap.add_argument("--rows", type=int, default=884736, help="gemm: rows (elements)")
     ap.add_argument("--no-variants", action="store_true", help="skip the FP32 variant of the default run")
     ap.add_argument("--nelem-train", type=int, default=64, help="closure: training mesh (elements per direction)")
@@ -975,6 +1045,8 @@ def main():
         return run_riemann1d(args, rank, world)
     if args.workload == "fp32err":
         return run_fp32err(args, rank, world)
+    if args.workload == "esdirk":
+        return run_esdirk(args, rank, world)
     if args.workload == "batch":
         if args.precision == "fp64" and "--precision" not in sys.argv:
             args.precision = "fp32"

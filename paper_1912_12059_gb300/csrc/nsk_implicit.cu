@@ -4,8 +4,8 @@
 //
 // Every implicit stage G(X) = X - dt gamma R(X) - S_i = 0, S_i = U_n + dt sum_{j<i} a_ij R_j, is
 // solved by Newton's method from the previous stage's value until ||G|| <= newton_tol ||S_i||;
-// each Newton system (I - dt gamma J) d = -G by restarted GMRES(m) (modified Gram-Schmidt,
-// Givens rotations, relative residual krylov_tol, no preconditioner) with the matrix-free
+// each Newton system (I - dt gamma J) d = -G by restarted GMRES(m) (Gram-Schmidt applied twice
+// with batched projections, Givens rotations, relative residual krylov_tol, no preconditioner) with the matrix-free
 // product J v ~ (R(X + eps v) - R(X)) / eps, eps = sqrt(2^-52) (1 + ||X||) / ||v||; the later
 // stages use R_i = (X_i - S_i) / (dt gamma). The vector algebra runs in the kernels below
 // (dot products in a fixed order: deterministic), the small GMRES least-squares problem and the
@@ -67,6 +67,53 @@ __global__ void __launch_bounds__(kDotThreads) k_dot_final(const int nb, const d
   if (threadIdx.x == 0) *out = red[0];
 }
 
+// partial sums of V_j . w for j < nv (one shared-memory tree per j, fixed order)
+__global__ void __launch_bounds__(kDotThreads) k_mdot_part(const long long n, const int nv,
+                                                           const double* const* __restrict__ V,
+                                                           const double* __restrict__ w, double* __restrict__ part) {
+  __shared__ double red[kDotThreads];
+  for (int j = 0; j < nv; ++j) {
+    const double* v = V[j];
+    double s = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+      s = fma(v[i], w[i], s);
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int k = kDotThreads / 2; k > 0; k >>= 1) {
+      if ((int)threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) part[(size_t)j * gridDim.x + blockIdx.x] = red[0];
+    __syncthreads();
+  }
+}
+
+// out[j] = sum of the nb partials of vector j (one block per j)
+__global__ void __launch_bounds__(kDotThreads) k_mdot_final(const int nb, const double* __restrict__ part,
+                                                            double* __restrict__ out) {
+  __shared__ double red[kDotThreads];
+  const double* p = part + (size_t)blockIdx.x * nb;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) s += p[i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int k = kDotThreads / 2; k > 0; k >>= 1) {
+    if ((int)threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[blockIdx.x] = red[0];
+}
+
+// w -= sum_{j < nv} h_j V_j
+__global__ void __launch_bounds__(256) k_maxpy(const long long n, const int nv, const double* const* __restrict__ V,
+                                               const double* __restrict__ h, double* __restrict__ w) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    double v = w[i];
+    for (int j = 0; j < nv; ++j) v = fma(-h[j], V[j][i], v);
+    w[i] = v;
+  }
+}
+
 // ARK4(3)6L[2]SA, implicit part (Kennedy and Carpenter 2003): a_ij for j < i; gamma = 1/4
 const double kGamma = 0.25;
 const double kA6[6][5] = {
@@ -104,6 +151,21 @@ struct Implicit {
     return h;
   }
   double norm(const double* x) { return sqrt(dot(x, x)); }
+  // h[j] = V_j . w for j < nv (one synchronisation); dV: device copy of the basis pointers
+  void mdot(int nv, double* const* dV, const double* w, double* hdev, double* h) {
+    k_mdot_part<<<kDotBlocks, kDotThreads, 0, s>>>(n, nv, dV, w, part);
+    k_mdot_final<<<nv, kDotThreads, 0, s>>>(kDotBlocks, part, hdev);
+    launches += 2;
+    if (cudaMemcpyAsync(h, hdev, sizeof(double) * nv, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      status = NSK_ERR_CUDA;
+  }
+  // w -= sum_j h[j] V_j
+  void maxpy(int nv, double* const* dV, const double* h, double* hdev, double* w) {
+    if (cudaMemcpyAsync(hdev, h, sizeof(double) * nv, cudaMemcpyHostToDevice, s) != cudaSuccess) status = NSK_ERR_CUDA;
+    k_maxpy<<<grid, 256, 0, s>>>(n, nv, dV, hdev, w);
+    ++launches;
+  }
   // out = R(X): one residual-mode stage of the context's pipeline on X
   void rhs(double* X, double* out) {
     void* saved = c->b.U;
@@ -134,8 +196,10 @@ int nsk_step_esdirk(nsk_ctx* c, double dt, int nsteps, double newton_tol, double
     cudaGetLastError();
     return NSK_ERR_NOMEM;
   }
+  // dot partials ((m + 1) vectors x blocks), a dot result, m + 1 coefficients, m + 1 basis pointers
   double* part = nullptr;
-  if (cudaMalloc(&part, sizeof(double) * (kDotBlocks + 1)) != cudaSuccess) {
+  const size_t part_n = (size_t)(m + 1) * kDotBlocks + 1 + (m + 1) + (m + 1);
+  if (cudaMalloc(&part, sizeof(double) * part_n) != cudaSuccess) {
     cudaGetLastError();
     cudaFree(pool);
     return NSK_ERR_NOMEM;
@@ -153,7 +217,12 @@ int nsk_step_esdirk(nsk_ctx* c, double dt, int nsteps, double newton_tol, double
   const long long g = (n + 255) / 256;
   im.grid = (unsigned)(g < 152 * 16 ? (g > 0 ? g : 1) : 152 * 16);
   im.part = part;
-  im.dotv = part + kDotBlocks;
+  im.dotv = part + (size_t)(m + 1) * kDotBlocks;
+  double* hdev = im.dotv + 1;
+  double** dV = (double**)(hdev + (m + 1));
+  if (cudaMemcpyAsync(dV, V.data(), sizeof(double*) * (m + 1), cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
+    im.status = NSK_ERR_CUDA;
+  std::vector<double> h1(m + 1), h2(m + 1);
   long long st_newton = 0, st_krylov = 0, st_fail = 0;
   double* U = (double*)c->b.U;  // U_n, then U_{n+1}
   const double gdt = kGamma * dt;
@@ -197,11 +266,13 @@ int nsk_step_esdirk(nsk_ctx* c, double dt, int nsteps, double newton_tol, double
             im.rhs(W, RW);
             im.lincomb(1.0, V[k], -gdt / eps, RW, gdt / eps, RX, V[k + 1]);
             ++its;
-            for (int j = 0; j <= k; ++j) {  // modified Gram-Schmidt
-              const double h = im.dot(V[k + 1], V[j]);
-              H[(size_t)j * m + k] = h;
-              im.lincomb(1.0, V[k + 1], -h, V[j], 0.0, nullptr, V[k + 1]);
-            }
+            // classical Gram-Schmidt, twice (CGS2): all k + 1 projections of a pass in one kernel and
+            // one host read, instead of one read per projection
+            im.mdot(k + 1, dV, V[k + 1], hdev, h1.data());
+            im.maxpy(k + 1, dV, h1.data(), hdev, V[k + 1]);
+            im.mdot(k + 1, dV, V[k + 1], hdev, h2.data());
+            im.maxpy(k + 1, dV, h2.data(), hdev, V[k + 1]);
+            for (int j = 0; j <= k; ++j) H[(size_t)j * m + k] = h1[j] + h2[j];
             const double hn = im.norm(V[k + 1]);
             H[(size_t)(k + 1) * m + k] = hn;
             if (hn > 0.0) im.lincomb(1.0 / hn, V[k + 1], 0.0, nullptr, 0.0, nullptr, V[k + 1]);
