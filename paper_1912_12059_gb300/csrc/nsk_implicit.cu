@@ -140,9 +140,10 @@ struct Implicit {
     k_lincomb<<<grid, 256, 0, s>>>(n, a, x, b, y, cc, z, out);
     ++launches;
   }
+  int nblk;             // blocks of the dot-product partial sums: up to kDotBlocks, one per 256 values
   double dot(const double* x, const double* y) {
-    k_dot_part<<<kDotBlocks, kDotThreads, 0, s>>>(n, x, y, part);
-    k_dot_final<<<1, kDotThreads, 0, s>>>(kDotBlocks, part, dotv);
+    k_dot_part<<<nblk, kDotThreads, 0, s>>>(n, x, y, part);
+    k_dot_final<<<1, kDotThreads, 0, s>>>(nblk, part, dotv);
     launches += 2;
     double h = 0.0;
     if (cudaMemcpyAsync(&h, dotv, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
@@ -153,8 +154,8 @@ struct Implicit {
   double norm(const double* x) { return sqrt(dot(x, x)); }
   // h[j] = V_j . w for j < nv (one synchronisation); dV: device copy of the basis pointers
   void mdot(int nv, double* const* dV, const double* w, double* hdev, double* h) {
-    k_mdot_part<<<kDotBlocks, kDotThreads, 0, s>>>(n, nv, dV, w, part);
-    k_mdot_final<<<nv, kDotThreads, 0, s>>>(kDotBlocks, part, hdev);
+    k_mdot_part<<<nblk, kDotThreads, 0, s>>>(n, nv, dV, w, part);
+    k_mdot_final<<<nv, kDotThreads, 0, s>>>(nblk, part, hdev);
     launches += 2;
     if (cudaMemcpyAsync(h, hdev, sizeof(double) * nv, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)
@@ -216,6 +217,7 @@ int nsk_step_esdirk(nsk_ctx* c, double dt, int nsteps, double newton_tol, double
   im.s = c->stream;
   const long long g = (n + 255) / 256;
   im.grid = (unsigned)(g < 152 * 16 ? (g > 0 ? g : 1) : 152 * 16);
+  im.nblk = (int)(g < kDotBlocks ? (g > 0 ? g : 1) : kDotBlocks);
   im.part = part;
   im.dotv = part + (size_t)(m + 1) * kDotBlocks;
   double* hdev = im.dotv + 1;
