@@ -67,24 +67,30 @@ __global__ void __launch_bounds__(kDotThreads) k_dot_final(const int nb, const d
   if (threadIdx.x == 0) *out = red[0];
 }
 
-// partial sums of V_j . w for j < nv (one shared-memory tree per j, fixed order)
-__global__ void __launch_bounds__(kDotThreads) k_mdot_part(const long long n, const int nv,
-                                                           const double* const* __restrict__ V,
+// sum over a warp by xor shuffles (a fixed pattern: the same order on every call)
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// partial sums of V_j . w: vector j = blockIdx.y (all vectors at once), warp shuffles, then
+// the warps' sums
+__global__ void __launch_bounds__(kDotThreads) k_mdot_part(const long long n, const double* const* __restrict__ V,
                                                            const double* __restrict__ w, double* __restrict__ part) {
-  __shared__ double red[kDotThreads];
-  for (int j = 0; j < nv; ++j) {
-    const double* v = V[j];
-    double s = 0.0;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-      s = fma(v[i], w[i], s);
-    red[threadIdx.x] = s;
-    __syncthreads();
-    for (int k = kDotThreads / 2; k > 0; k >>= 1) {
-      if ((int)threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) part[(size_t)j * gridDim.x + blockIdx.x] = red[0];
-    __syncthreads();
+  __shared__ double red[kDotThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, j = blockIdx.y;
+  const double* v = V[j];
+  double s = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    s = fma(v[i], w[i], s);
+  s = warp_sum(s);
+  if (lane == 0) red[warp] = s;
+  __syncthreads();
+  if (warp == 0) {
+    double t = lane < kDotThreads / 32 ? red[lane] : 0.0;
+    t = warp_sum(t);
+    if (lane == 0) part[(size_t)j * gridDim.x + blockIdx.x] = t;
   }
 }
 
@@ -154,7 +160,7 @@ struct Implicit {
   double norm(const double* x) { return sqrt(dot(x, x)); }
   // h[j] = V_j . w for j < nv (one synchronisation); dV: device copy of the basis pointers
   void mdot(int nv, double* const* dV, const double* w, double* hdev, double* h) {
-    k_mdot_part<<<nblk, kDotThreads, 0, s>>>(n, nv, dV, w, part);
+    k_mdot_part<<<dim3(nblk, nv), kDotThreads, 0, s>>>(n, dV, w, part);
     k_mdot_final<<<nv, kDotThreads, 0, s>>>(nblk, part, hdev);
     launches += 2;
     if (cudaMemcpyAsync(h, hdev, sizeof(double) * nv, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
