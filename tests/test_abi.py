@@ -52,6 +52,14 @@ def test_error_strings_and_argument_validation(nsk_lib):
     assert nsk_lib.nsk_init_mesh(C.byref(ctx), 3, ne, lo, bad_hi, 3, 0, 0, None) == nsk.NSK_ERR_ARG
     assert nsk_lib.nsk_set_params(None, 0.85, 1e-4, 1e3, 1e-3, 1e-3) == nsk.NSK_ERR_ARG
     assert nsk_lib.nsk_launch_count(None) == -1
+    # the sub-cell, boundary and implicit entries validate their context first
+    ub = (C.c_double * 3)(1.0, 0.0, 1.0)
+    assert nsk_lib.nsk_set_subcell(None, 1, -6.0, -8.0) == nsk.NSK_ERR_ARG
+    assert nsk_lib.nsk_set_dirichlet(None, 1, ub, ub) == nsk.NSK_ERR_ARG
+    assert nsk_lib.nsk_set_subcell_flags(None, None) == nsk.NSK_ERR_ARG
+    assert nsk_lib.nsk_get_subcell(None, None, None) == nsk.NSK_ERR_ARG
+    assert nsk_lib.nsk_subcell_switch(None) == nsk.NSK_ERR_ARG
+    assert nsk_lib.nsk_step_esdirk(None, 1e-5, 1, 1e-10, 1e-3, 30, 600, None) == nsk.NSK_ERR_ARG
     nsk_lib.nsk_destroy(None)
 
 
