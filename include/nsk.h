@@ -218,14 +218,20 @@ int nsk_step(nsk_ctx* ctx, double dt, int nsteps);
  * right-hand side (at most 20 iterations; stats[3] counts stages that stopped there), each
  * Newton system by restarted GMRES(krylov_dim) to the relative residual krylov_tol (at most
  * max_krylov iterations per system), matrix-free: J v ~ (R(X + eps v) - R(X)) / eps with
- * eps = sqrt(2^-52) (1 + ||X||) / ||v||, no preconditioner. stats (may be NULL): Newton
+ * eps = sqrt(2^-52) (1 + ||X||) / ||v||. block_precond = 1 right-preconditions GMRES with the
+ * inverses of the element blocks of I - dt gamma J(U_n): J's diagonal blocks dR_e/dU_e by forward
+ * differences once per step, every element of an element colour perturbed at once (colours per
+ * direction: the smallest divisor >= 3 of the element count, else the count; each costs
+ * nvar npe residual evaluations, counted in stats), inverted by Gauss-Jordan per element; blocks
+ * of at most 48 unknowns (nvar npe) and E (nvar npe)^2 <= 2^28 values (NSK_ERR_ARG otherwise).
+ * stats (may be NULL): Newton
  * iterations, Krylov iterations, residual evaluations, stages stopped at the iteration limit,
  * summed over the call. FP64 contexts with the explicit c equation and without the sub-cell
  * path only (NSK_ERR_ARG otherwise). Allocates 12 + krylov_dim state-sized FP64 buffers for the
  * call and frees them before returning; every dot product synchronises the stream (the GMRES
  * control runs on the host). */
 int nsk_step_esdirk(nsk_ctx* ctx, double dt, int nsteps, double newton_tol, double krylov_tol, int krylov_dim,
-                    int max_krylov, long long stats[4]);
+                    int max_krylov, int block_precond, long long stats[4]);
 
 /* Quadrature sums (FP64): mass sum w J rho; the total energy of the relaxation
  * model sum w J (|m|^2/(2 rho) + W(rho) + alpha/2 (rho-c)^2 + kappa/2 |grad c|^2)

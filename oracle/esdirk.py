@@ -11,7 +11,9 @@ takes these readings (the GPU path takes the same ones):
   - the Newton systems (I - dt gamma J) d = -G are solved matrix-free (Jacobian-free
     Newton-Krylov): J v ~ (R(X + eps v) - R(X)) / eps, eps = sqrt(2^-52) (1 + ||X||) / ||v||,
     with restarted GMRES(m) (modified Gram-Schmidt, Givens rotations) to the relative residual
-    krylov_tol, no preconditioner;
+    krylov_tol, without or with a right element-block preconditioner (the paper's code uses one;
+    its construction is not given: here the inverses of the element blocks of I - dt gamma J(U_n),
+    J's diagonal blocks from forward differences with an element colouring, once per step);
   - the stage derivative used by the later stages is R_i = (X_i - S_i) / (dt gamma), equal to
     R(X_i) at convergence, which saves one residual evaluation per stage.
 Only tests/ (and the package smoke check / the benchmark's CPU legs) may use this module.
@@ -53,8 +55,71 @@ def tableau(exact=False):
     return A, b, c
 
 
-def gmres(apply, rhs, tol, m, maxit):
-    """Restarted GMRES(m) for apply(x) = rhs from x = 0; returns (x, iterations)."""
+def colours(ne):
+    """Colours per direction for the element-block Jacobian: with BR1 an element's residual depends
+    on the states up to two elements away, so perturbing two elements of one colour leaves each
+    one's residual to its own perturbation when they are at least three apart, across the periodic
+    wrap too: the smallest divisor K >= 3 of ne (colour = coordinate mod K), else ne itself (every
+    element its own colour)."""
+    for K in range(3, ne + 1):
+        if ne % K == 0:
+            return K
+    return ne
+
+
+def block_jacobian(rhs, U, nelem):
+    """Diagonal blocks dR_e/dU_e of the residual's Jacobian, [E][n][n] with n = nvar npe and the
+    local unknown k = v npe + node, by forward differences: for each colour class and local unknown,
+    every element of that class is perturbed at once, eps_e = sqrt(2^-52) (1 + |U_e,k|)."""
+    nvar, E, npe = U.shape
+    n = nvar * npe
+    dim = len(nelem)
+    K = [colours(ne) for ne in nelem]
+    coord = np.zeros((E, dim), dtype=int)
+    for e in range(E):
+        r = e
+        for k in range(dim):
+            coord[e, k] = r % nelem[k]
+            r //= nelem[k]
+    col = np.zeros(E, dtype=int)
+    stride = 1
+    for k in range(dim):
+        col += (coord[:, k] % K[k]) * stride
+        stride *= K[k]
+    R0 = rhs(U)
+    J = np.zeros((E, n, n))
+    for c in range(stride):
+        members = np.nonzero(col == c)[0]
+        if members.size == 0:
+            continue
+        for kk in range(n):
+            v, node = divmod(kk, npe)
+            W = U.copy()
+            eps = math.sqrt(2.0 ** -52) * (1.0 + np.abs(U[v, members, node]))
+            W[v, members, node] += eps
+            dR = rhs(W) - R0
+            for i, e in enumerate(members):
+                J[e, :, kk] = dR[:, e, :].reshape(n) / eps[i]
+    return J
+
+
+def block_preconditioner(J, dtg):
+    """Inverses of the element blocks of I - dt gamma J (right preconditioner of GMRES)."""
+    n = J.shape[1]
+    return np.linalg.inv(np.eye(n)[None] - dtg * J)
+
+
+def apply_blocks(Minv, x, shape):
+    """y_e = Minv_e x_e for the state-shaped vector x (flattened), [nvar][E][npe] layout."""
+    nvar, E, npe = shape
+    X = x.reshape(shape).transpose(1, 0, 2).reshape(E, nvar * npe)
+    Y = np.einsum("eij,ej->ei", Minv, X)
+    return Y.reshape(E, nvar, npe).transpose(1, 0, 2).reshape(-1)
+
+
+def gmres(apply, rhs, tol, m, maxit, precond=None):
+    """Restarted GMRES(m) for apply(x) = rhs from x = 0, right-preconditioned by precond (a map
+    z -> M^-1 z, or None); returns (x, iterations)."""
     n = rhs.size
     x = np.zeros(n)
     bn = float(np.linalg.norm(rhs))
@@ -72,7 +137,7 @@ def gmres(apply, rhs, tol, m, maxit):
         cs, sn = np.zeros(m), np.zeros(m)
         k = 0
         for k in range(m):
-            w = apply(V[k])
+            w = apply(V[k] if precond is None else precond(V[k]))
             its += 1
             for j in range(k + 1):  # modified Gram-Schmidt
                 H[j, k] = float(w @ V[j])
@@ -93,22 +158,33 @@ def gmres(apply, rhs, tol, m, maxit):
                 break
         kk = k + 1
         y = np.linalg.solve(np.triu(H[:kk, :kk]), g[:kk])
-        x = x + V[:kk].T @ y
+        x = x + (V[:kk].T @ y if precond is None else precond(V[:kk].T @ y))
         if abs(g[kk]) <= tol * bn or its >= maxit:
             break
         r = rhs - apply(x)
     return x, its
 
 
-def step(rhs, U, dt, newton_tol=1e-10, krylov_tol=1e-3, m=30, max_krylov=600, max_newton=20):
+def step(rhs, U, dt, newton_tol=1e-10, krylov_tol=1e-3, m=30, max_krylov=600, max_newton=20, nelem=None):
     """One ESDIRK4 step of U' = rhs(U); returns (U_new, stats) with stats = dict of Newton
-    iterations, Krylov iterations and residual evaluations."""
+    iterations, Krylov iterations and residual evaluations. nelem (elements per direction) turns
+    on the element-block preconditioner: the blocks of I - dt gamma J(U_n), built once per step
+    by coloured forward differences (their residual evaluations are counted)."""
     A, _, _ = tableau()
     g = float(GAMMA)
     shape = U.shape
     R = [rhs(U)]
     X = U.copy()
     st = {"newton": 0, "krylov": 0, "rhs": 1, "failed": 0}
+    precond = None
+    if nelem is not None:
+        J = block_jacobian(rhs, U, nelem)
+        K = 1
+        for ne in nelem:
+            K *= colours(ne)
+        st["rhs"] += 1 + K * shape[0] * shape[2]
+        Minv = block_preconditioner(J, dt * g)
+        precond = lambda z: apply_blocks(Minv, z, shape)  # noqa: E731
     for i in range(1, STAGES):
         S = U + dt * sum(A[i, j] * R[j] for j in range(i))
         sn = float(np.linalg.norm(S))
@@ -132,7 +208,7 @@ def step(rhs, U, dt, newton_tol=1e-10, krylov_tol=1e-3, m=30, max_krylov=600, ma
                 st["rhs"] += 1
                 return v - dt * g * Jv.ravel()
 
-            d, its = gmres(apply, -G.ravel(), krylov_tol, m, max_krylov)
+            d, its = gmres(apply, -G.ravel(), krylov_tol, m, max_krylov, precond)
             X = X + d.reshape(shape)
             st["newton"] += 1
             st["krylov"] += its

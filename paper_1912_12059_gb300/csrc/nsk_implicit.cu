@@ -120,6 +120,99 @@ __global__ void __launch_bounds__(256) k_maxpy(const long long n, const int nv, 
   }
 }
 
+// ---- element-block preconditioner: blocks of I - dt gamma J, J's diagonal blocks dR_e/dU_e ----
+// local unknown k = v npe + node of element e sits at v nn + e npe + node
+constexpr int kMaxBlock = 48;  // largest block (nvar npe) the shared-memory inversion takes
+
+// W = U with local unknown (v, node) of every element of colour c raised by
+// eps_e = sqrt(2^-52) (1 + |U|)
+__global__ void __launch_bounds__(256) k_fd_perturb(const long long E, const int npe, const long long nn,
+                                                    const int* __restrict__ colour, const int c, const int v,
+                                                    const int node, double* __restrict__ W) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < E; e += (long long)gridDim.x * blockDim.x) {
+    if (colour[e] != c) continue;
+    const size_t g = (size_t)v * nn + e * npe + node;
+    W[g] += sqrt(ldexp(1.0, -52)) * (1.0 + fabs(W[g]));
+  }
+}
+
+// column k of the blocks of the elements of colour c: J[e][i][k] = (R(W)_e,i - R(U)_e,i) / eps_e
+__global__ void __launch_bounds__(256) k_fd_column(const long long E, const int nvar, const int npe, const long long nn,
+                                                   const int* __restrict__ colour, const int c, const int k,
+                                                   const double* __restrict__ U, const double* __restrict__ RW,
+                                                   const double* __restrict__ R0, double* __restrict__ J) {
+  const int n = nvar * npe;
+  const int v = k / npe, node = k % npe;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < E * n; t += (long long)gridDim.x * blockDim.x) {
+    const long long e = t / n;
+    const int i = (int)(t % n);
+    if (colour[e] != c) continue;
+    const double eps = sqrt(ldexp(1.0, -52)) * (1.0 + fabs(U[(size_t)v * nn + e * npe + node]));
+    const size_t gi = (size_t)(i / npe) * nn + e * npe + i % npe;
+    J[((size_t)e * n + i) * n + k] = (RW[gi] - R0[gi]) / eps;
+  }
+}
+
+// block e: J_e <- (I - dtg J_e)^-1 by Gauss-Jordan elimination with partial pivoting in shared
+// memory ([M | I], n <= kMaxBlock); a zero pivot sets NSK_EBIT_NAN
+__global__ void __launch_bounds__(128) k_block_invert(const int n, const double dtg, double* __restrict__ J,
+                                                      int* __restrict__ err) {
+  __shared__ double A[kMaxBlock][2 * kMaxBlock];
+  __shared__ int piv;
+  double* Je = J + (size_t)blockIdx.x * n * n;
+  for (int t = threadIdx.x; t < n * 2 * n; t += blockDim.x) {
+    const int i = t / (2 * n), j = t % (2 * n);
+    A[i][j] = j < n ? (i == j ? 1.0 : 0.0) - dtg * Je[i * n + j] : (j - n == i ? 1.0 : 0.0);
+  }
+  __syncthreads();
+  for (int c = 0; c < n; ++c) {
+    if (threadIdx.x == 0) {
+      int p = c;
+      for (int i = c + 1; i < n; ++i)
+        if (fabs(A[i][c]) > fabs(A[p][c])) p = i;
+      piv = A[p][c] == 0.0 ? -1 : p;
+      if (piv < 0) atomicOr(err, NSK_EBIT_NAN);
+    }
+    __syncthreads();
+    if (piv < 0) return;  // uniform over the block
+    if (piv != c)
+      for (int j = threadIdx.x; j < 2 * n; j += blockDim.x) {
+        const double t = A[c][j];
+        A[c][j] = A[piv][j];
+        A[piv][j] = t;
+      }
+    __syncthreads();
+    const double d = A[c][c];
+    __syncthreads();
+    for (int j = threadIdx.x; j < 2 * n; j += blockDim.x) A[c][j] /= d;
+    __syncthreads();
+    for (int t = threadIdx.x; t < n * 2 * n; t += blockDim.x) {
+      const int i = t / (2 * n), j = t % (2 * n);
+      if (i != c && j != c) A[i][j] = fma(-A[i][c], A[c][j], A[i][j]);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+      if (i != c) A[i][c] = 0.0;
+    __syncthreads();
+  }
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) Je[t] = A[t / n][n + t % n];
+}
+
+// y_e = Minv_e x_e
+__global__ void __launch_bounds__(256) k_block_apply(const long long E, const int nvar, const int npe,
+                                                     const long long nn, const double* __restrict__ Minv,
+                                                     const double* __restrict__ x, double* __restrict__ y) {
+  const int n = nvar * npe;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < E * n; t += (long long)gridDim.x * blockDim.x) {
+    const long long e = t / n;
+    const int i = (int)(t % n);
+    const double* row = Minv + ((size_t)e * n + i) * n;
+    double s = 0.0;
+    for (int k = 0; k < n; ++k) s = fma(row[k], x[(size_t)(k / npe) * nn + e * npe + k % npe], s);
+    y[(size_t)(i / npe) * nn + e * npe + i % npe] = s;
+  }
+}
+
 // ARK4(3)6L[2]SA, implicit part (Kennedy and Carpenter 2003): a_ij for j < i; gamma = 1/4
 const double kGamma = 0.25;
 const double kA6[6][5] = {
@@ -187,17 +280,30 @@ struct Implicit {
 
 }  // namespace
 
+// colours per direction of the block Jacobian's forward differences: with BR1 an element's
+// residual depends on the states up to two elements away, so same-coloured elements at least
+// three apart (across the periodic wrap too) do not see each other's perturbation: the smallest
+// divisor K >= 3 of ne, else ne
+static int fd_colours(int ne) {
+  for (int K = 3; K <= ne; ++K)
+    if (ne % K == 0) return K;
+  return ne;
+}
+
 int nsk_step_esdirk(nsk_ctx* c, double dt, int nsteps, double newton_tol, double krylov_tol, int krylov_dim,
-                    int max_krylov, long long stats[4]) {
+                    int max_krylov, int block_precond, long long stats[4]) {
   if (!c || !(dt > 0.0) || !isfinite(dt) || nsteps < 0 || !(newton_tol > 0.0) || !(krylov_tol > 0.0) ||
-      krylov_dim < 1 || krylov_dim > 200 || max_krylov < 1)
+      krylov_dim < 1 || krylov_dim > 200 || max_krylov < 1 || (block_precond != 0 && block_precond != 1))
     return NSK_ERR_ARG;
   if (c->precision != NSK_FP64 || c->closure_mode != NSK_C_EXPLICIT || c->fv_path()) return NSK_ERR_ARG;
+  const int nloc = c->nvar * c->npe;
+  if (block_precond && (nloc > kMaxBlock || (double)c->E * nloc * nloc > 268435456.0)) return NSK_ERR_ARG;
   if (!c->state_set) return NSK_ERR_STATE;
   const int m = krylov_dim;
   const long long n = (long long)c->nvar * c->nn;
-  // state-sized buffers: R_0..R_4, X, S, RX, D (Newton update), W (X + eps v), RW, V_0..V_m
-  const int nbuf = 5 + 6 + (m + 1);
+  // state-sized buffers: R_0..R_4, X, S, RX, D (Newton update), W (X + eps v), RW, V_0..V_m,
+  // and with the preconditioner Z (M^-1 v) and T (the combination of the basis)
+  const int nbuf = 5 + 6 + (m + 1) + (block_precond ? 2 : 0);
   double* pool = nullptr;
   if (cudaMalloc(&pool, sizeof(double) * (size_t)n * nbuf) != cudaSuccess) {
     cudaGetLastError();
@@ -216,6 +322,32 @@ int nsk_step_esdirk(nsk_ctx* c, double dt, int nsteps, double newton_tol, double
   double *X = buf(5), *S = buf(6), *RX = buf(7), *D = buf(8), *W = buf(9), *RW = buf(10);
   std::vector<double*> V(m + 1);
   for (int k = 0; k <= m; ++k) V[k] = buf(11 + k);
+  double* Z = block_precond ? buf(12 + m) : nullptr;
+  double* T = block_precond ? buf(13 + m) : nullptr;
+  // the preconditioner's blocks and the element colours
+  double* Jb = nullptr;
+  int* colour = nullptr;
+  int ncol = 1;
+  if (block_precond) {
+    std::vector<int> hc((size_t)c->E);
+    int K[3] = {1, 1, 1};
+    for (int k = 0; k < c->dim; ++k) K[k] = fd_colours(c->ne[k]);
+    ncol = K[0] * K[1] * K[2];
+    for (long long e = 0; e < c->E; ++e) {
+      const long long c0 = e % c->ne[0], c1 = (e / c->ne[0]) % c->ne[1], c2 = e / ((long long)c->ne[0] * c->ne[1]);
+      hc[(size_t)e] = (int)(c0 % K[0] + K[0] * (c1 % K[1] + K[1] * (c2 % K[2])));
+    }
+    if (cudaMalloc(&Jb, sizeof(double) * (size_t)c->E * nloc * nloc) != cudaSuccess ||
+        cudaMalloc(&colour, sizeof(int) * (size_t)c->E) != cudaSuccess ||
+        cudaMemcpy(colour, hc.data(), sizeof(int) * hc.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(Jb);
+      cudaFree(colour);
+      cudaFree(part);
+      cudaFree(pool);
+      return NSK_ERR_NOMEM;
+    }
+  }
 
   Implicit im;
   im.c = c;
@@ -236,9 +368,27 @@ int nsk_step_esdirk(nsk_ctx* c, double dt, int nsteps, double newton_tol, double
   const double gdt = kGamma * dt;
   std::vector<double> H((size_t)(m + 1) * m), gv(m + 1), cs(m), sn(m), y(m);
 
+  const unsigned eg = (unsigned)std::min<long long>((c->E * nloc + 255) / 256, 152 * 16);
+  // z = M^-1 x (identity without the preconditioner)
+  auto precond = [&](const double* x, double* z) {
+    k_block_apply<<<eg, 256, 0, im.s>>>(c->E, c->nvar, c->npe, c->nn, Jb, x, z);
+    ++im.launches;
+  };
   for (int step = 0; step < nsteps && im.status == NSK_OK; ++step) {
     im.rhs(U, Rj[0]);
     im.lincomb(1.0, U, 0.0, nullptr, 0.0, nullptr, X);
+    if (block_precond) {  // blocks of I - dt gamma J(U_n), once per step
+      for (int col = 0; col < ncol; ++col)
+        for (int k = 0; k < nloc; ++k) {
+          im.lincomb(1.0, U, 0.0, nullptr, 0.0, nullptr, W);
+          k_fd_perturb<<<eg, 256, 0, im.s>>>(c->E, c->npe, c->nn, colour, col, k / c->npe, k % c->npe, W);
+          im.rhs(W, RW);
+          k_fd_column<<<eg, 256, 0, im.s>>>(c->E, c->nvar, c->npe, c->nn, colour, col, k, U, RW, Rj[0], Jb);
+          im.launches += 2;
+        }
+      k_block_invert<<<(unsigned)c->E, 128, 0, im.s>>>(nloc, gdt, Jb, c->b.err);
+      ++im.launches;
+    }
     for (int i = 1; i < 6 && im.status == NSK_OK; ++i) {
       // S_i = U_n + dt sum_{j<i} a_ij R_j
       im.lincomb(1.0, U, 0.0, nullptr, 0.0, nullptr, S);
@@ -268,11 +418,19 @@ int nsk_step_esdirk(nsk_ctx* c, double dt, int nsteps, double newton_tol, double
           gv[0] = beta;
           int k = 0;
           for (k = 0; k < m; ++k) {
-            // V_{k+1} = (I - dt gamma J) V_k with J V_k ~ (R(X + eps V_k) - R(X)) / eps (||V_k|| = 1)
-            const double eps = sqrt(ldexp(1.0, -52)) * (1.0 + xn);
-            im.lincomb(1.0, X, eps, V[k], 0.0, nullptr, W);
+            // V_{k+1} = (I - dt gamma J) z, z = M^-1 V_k (z = V_k, ||z|| = 1, without the
+            // preconditioner), J z ~ (R(X + eps z) - R(X)) / eps
+            const double* zk = V[k];
+            double zn = 1.0;
+            if (block_precond) {
+              precond(V[k], Z);
+              zk = Z;
+              zn = im.norm(Z);
+            }
+            const double eps = sqrt(ldexp(1.0, -52)) * (1.0 + xn) / zn;
+            im.lincomb(1.0, X, eps, zk, 0.0, nullptr, W);
             im.rhs(W, RW);
-            im.lincomb(1.0, V[k], -gdt / eps, RW, gdt / eps, RX, V[k + 1]);
+            im.lincomb(1.0, zk, -gdt / eps, RW, gdt / eps, RX, V[k + 1]);
             ++its;
             // classical Gram-Schmidt, twice (CGS2): all k + 1 projections of a pass in one kernel and
             // one host read, instead of one read per projection
@@ -305,7 +463,14 @@ int nsk_step_esdirk(nsk_ctx* c, double dt, int nsteps, double newton_tol, double
             for (int j = r + 1; j < kk; ++j) t -= H[(size_t)r * m + j] * y[j];
             y[r] = t / H[(size_t)r * m + r];
           }
-          for (int j = 0; j < kk; ++j) im.lincomb(1.0, D, y[j], V[j], 0.0, nullptr, D);
+          if (block_precond) {  // D += M^-1 sum_j y_j V_j
+            if (cudaMemsetAsync(T, 0, sizeof(double) * (size_t)n, im.s) != cudaSuccess) im.status = NSK_ERR_CUDA;
+            for (int j = 0; j < kk; ++j) im.lincomb(1.0, T, y[j], V[j], 0.0, nullptr, T);
+            precond(T, Z);
+            im.lincomb(1.0, D, 1.0, Z, 0.0, nullptr, D);
+          } else {
+            for (int j = 0; j < kk; ++j) im.lincomb(1.0, D, y[j], V[j], 0.0, nullptr, D);
+          }
           if (fabs(gv[kk]) <= krylov_tol * bn || its >= max_krylov) {
             done = true;
           } else {  // restart: r = -G - (I - dt gamma J) D
@@ -335,6 +500,8 @@ int nsk_step_esdirk(nsk_ctx* c, double dt, int nsteps, double newton_tol, double
   const int rs = nsk_ctx_sync_check(c);
   if (r == NSK_OK) r = rs;
   c->launches += im.launches;
+  cudaFree(Jb);
+  cudaFree(colour);
   cudaFree(part);
   cudaFree(pool);
   if (stats) {

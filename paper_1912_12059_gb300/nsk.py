@@ -58,7 +58,7 @@ SIGNATURES = {
     "nsk_compute_dt": (C.c_int, [C.c_void_p, C.c_double, _dp]),
     "nsk_step": (C.c_int, [C.c_void_p, C.c_double, C.c_int]),
     "nsk_step_esdirk": (C.c_int, [C.c_void_p, C.c_double, C.c_int, C.c_double, C.c_double, C.c_int, C.c_int,
-                                  C.POINTER(C.c_longlong)]),
+                                  C.c_int, C.POINTER(C.c_longlong)]),
     "nsk_diagnostics": (C.c_int, [C.c_void_p, _dp, _dp, _dp]),
     "nsk_get_sizes": (C.c_int, [C.c_void_p, C.POINTER(C.c_longlong), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "nsk_launch_count": (C.c_longlong, [C.c_void_p]),
@@ -325,12 +325,15 @@ class Solver:
     def step(self, dt, nsteps=1):
         _check(load_library().nsk_step(self.ctx, dt, nsteps), "nsk_step")
 
-    def step_esdirk(self, dt, nsteps=1, newton_tol=1e-10, krylov_tol=1e-3, krylov_dim=30, max_krylov=600):
-        """Implicit six-stage ESDIRK4 steps (Jacobian-free Newton-Krylov); returns the statistics
-        {newton, krylov, rhs, failed} summed over the call."""
+    def step_esdirk(self, dt, nsteps=1, newton_tol=1e-10, krylov_tol=1e-3, krylov_dim=30, max_krylov=600,
+                    block_precond=False):
+        """Implicit six-stage ESDIRK4 steps (Jacobian-free Newton-Krylov, optionally with the
+        element-block preconditioner); returns the statistics {newton, krylov, rhs, failed}
+        summed over the call."""
         st = (C.c_longlong * 4)()
         _check(load_library().nsk_step_esdirk(self.ctx, float(dt), int(nsteps), float(newton_tol), float(krylov_tol),
-                                              int(krylov_dim), int(max_krylov), st), "nsk_step_esdirk")
+                                              int(krylov_dim), int(max_krylov), int(bool(block_precond)), st),
+               "nsk_step_esdirk")
         return {"newton": st[0], "krylov": st[1], "rhs": st[2], "failed": st[3]}
 
     def diagnostics(self):

@@ -59,7 +59,7 @@ def test_error_strings_and_argument_validation(nsk_lib):
     assert nsk_lib.nsk_set_subcell_flags(None, None) == nsk.NSK_ERR_ARG
     assert nsk_lib.nsk_get_subcell(None, None, None) == nsk.NSK_ERR_ARG
     assert nsk_lib.nsk_subcell_switch(None) == nsk.NSK_ERR_ARG
-    assert nsk_lib.nsk_step_esdirk(None, 1e-5, 1, 1e-10, 1e-3, 30, 600, None) == nsk.NSK_ERR_ARG
+    assert nsk_lib.nsk_step_esdirk(None, 1e-5, 1, 1e-10, 1e-3, 30, 600, 0, None) == nsk.NSK_ERR_ARG
     nsk_lib.nsk_destroy(None)
 
 
