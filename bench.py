@@ -597,55 +597,67 @@ def measure_subcell_variant(args, stream):
 
 def measure_esdirk_variant(args, stream):
     """Implicit ESDIRK4 with Jacobian-free Newton-Krylov (nsk_step_esdirk) against the explicit
-    LSRK4 over the same simulated time: the 1D static phase interface (64 elements, N = 3,
-    alpha = 100, beta = 1e-2, kappa = 1e-4, mu = 1e-2), T = 100 explicit CFL-0.5 steps, advanced
-    by one implicit step of 100x and by ten of 10x the explicit step, without and with the
-    element-block preconditioner: wall time, residual evaluations (those that build the blocks
-    included), Newton and Krylov iterations, and the density L2 difference to the explicit run."""
+    LSRK4 over the same simulated time, on the 1D static phase interface (64 elements, N = 3,
+    kappa = 1e-4), in two regimes of the c equation's stiffness alpha/beta:
+      - mild, alpha = 100, beta = 1e-2, mu = 1e-2: T = 100 explicit CFL-0.5 steps, advanced by one
+        implicit step of 100x and by ten of 10x the explicit step;
+      - stiff, the paper's alpha = 1e3, beta = 1e-3, mu = 1e-3 (explicit dt bound by the source):
+        T = 1000 explicit steps, advanced by one implicit step of 1000x and by ten of 100x;
+    each without and with the element-block preconditioner: wall time, residual evaluations (those
+    that build the blocks included), Newton and Krylov iterations, and the density L2 difference to
+    the explicit run."""
     import torch
 
     from paper_1912_12059_gb300 import inputs, nsk
 
-    prm = dict(T=0.85, kappa=1e-4, alpha=100.0, beta=1e-2, mu=1e-2)
     E, N = 64, 3
 
-    def make():
-        s = nsk.Solver(1, (E,), N, [0.0], [1.0], 0, nsk.NSK_FP64, stream=stream.cuda_stream)
-        s.set_params(**prm)
-        s.set_state(inputs.slab_1d(s.node_coords(), inputs.PAPER_RHO_VAP, inputs.PAPER_RHO_LIQ, prm["kappa"]))
-        return s
+    def compare(prm, n_explicit, factors):
+        def make():
+            s = nsk.Solver(1, (E,), N, [0.0], [1.0], 0, nsk.NSK_FP64, stream=stream.cuda_stream)
+            s.set_params(**prm)
+            s.set_state(inputs.slab_1d(s.node_coords(), inputs.PAPER_RHO_VAP, inputs.PAPER_RHO_LIQ, prm["kappa"]))
+            return s
 
-    s = make()
-    dte = s.compute_dt(0.5)
-    out = {"workload": f"static_interface_1d_E{E}_N{N}_alpha100_beta1e-2", "explicit_dt": dte,
-           "simulated_time": 100 * dte, "newton_tol": 1e-10, "krylov_tol": 1e-3, "krylov_dim": 30}
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    s.step(dte, 3)  # warm-up
-    s.close()
-    s = make()
-    torch.cuda.synchronize()
-    e0.record(stream)
-    s.step(dte, 100)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ref = s.get_state()
-    out["explicit_lsrk4"] = {"steps": 100, "wall_ms": e0.elapsed_time(e1), "rhs_evaluations": 500}
-    s.close()
-    for pc in (False, True):
-        for fac in (100, 10):
-            s = make()
-            torch.cuda.synchronize()
-            t0 = time.time()
-            st = s.step_esdirk(fac * dte, 100 // fac, newton_tol=1e-10, krylov_tol=1e-3, krylov_dim=30,
-                               block_precond=pc)
-            torch.cuda.synchronize()
-            ms = (time.time() - t0) * 1e3
-            U = s.get_state()
-            err = float(np.sqrt(((U[0] - ref[0]) ** 2).sum() / (ref[0] ** 2).sum()))
-            out[f"esdirk4_{fac}x" + ("_block_precond" if pc else "")] = {
-                "steps": 100 // fac, "wall_ms": ms, "rhs_evaluations": st["rhs"], "newton": st["newton"],
-                "krylov": st["krylov"], "failed": st["failed"], "density_l2_rel_diff_vs_explicit": err}
-            s.close()
+        s = make()
+        dte = s.compute_dt(0.5)
+        out = {"workload": f"static_interface_1d_E{E}_N{N}_alpha{prm['alpha']:g}_beta{prm['beta']:g}",
+               "explicit_dt": dte, "simulated_time": n_explicit * dte, "newton_tol": 1e-10, "krylov_tol": 1e-3,
+               "krylov_dim": 30}
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.step(dte, 3)  # warm-up
+        s.close()
+        s = make()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        s.step(dte, n_explicit)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ref = s.get_state()
+        out["explicit_lsrk4"] = {"steps": n_explicit, "wall_ms": e0.elapsed_time(e1),
+                                 "rhs_evaluations": 5 * n_explicit}
+        s.close()
+        for pc in (False, True):
+            for fac in factors:
+                s = make()
+                torch.cuda.synchronize()
+                t0 = time.time()
+                st = s.step_esdirk(fac * dte, n_explicit // fac, newton_tol=1e-10, krylov_tol=1e-3, krylov_dim=30,
+                                   block_precond=pc)
+                torch.cuda.synchronize()
+                ms = (time.time() - t0) * 1e3
+                U = s.get_state()
+                err = float(np.sqrt(((U[0] - ref[0]) ** 2).sum() / (ref[0] ** 2).sum()))
+                out[f"esdirk4_{fac}x" + ("_block_precond" if pc else "")] = {
+                    "steps": n_explicit // fac, "wall_ms": ms, "rhs_evaluations": st["rhs"],
+                    "newton": st["newton"], "krylov": st["krylov"], "failed": st["failed"],
+                    "density_l2_rel_diff_vs_explicit": err}
+                s.close()
+        return out
+
+    out = compare(dict(T=0.85, kappa=1e-4, alpha=100.0, beta=1e-2, mu=1e-2), 100, (100, 10))
+    out["stiff_paper_parameters"] = compare(dict(T=0.85, kappa=1e-4, alpha=1e3, beta=1e-3, mu=1e-3), 1000,
+                                            (1000, 100))
     return out
 
 

@@ -123,3 +123,25 @@ def test_parity_block_preconditioned(gpu, E):
     plain = s.step_esdirk(dt, 1, newton_tol=NT, krylov_tol=KT)
     assert st["krylov"] < plain["krylov"]
     s.close()
+
+
+def test_parity_stiff_paper_parameters(gpu):
+    """The paper's alpha = 1e3, beta = 1e-3, mu = 1e-3 (the explicit step bound by the c equation's
+    source): one preconditioned step of 1000x the explicit CFL-0.5 step on the 1D interface
+    against the oracle's, and fewer Krylov iterations than without the preconditioner."""
+    prm = dict(T=0.85, kappa=1e-4, alpha=1e3, beta=1e-3, mu=1e-3)
+    s, o = pair(1, (16,), 3, **prm)
+    rv, rl, _ = O.maxwell(0.85)
+    U = inputs.slab_1d(o.coords(), rv, rl, 1e-4)
+    dt = 1000.0 * o.timestep(U, 0.5)
+    s.set_state(U)
+    st = s.step_esdirk(dt, 1, newton_tol=NT, krylov_tol=KT, block_precond=True)
+    Ug = s.get_state()
+    Uo, sto = ES.step(o.rhs, U, dt, newton_tol=NT, krylov_tol=KT, nelem=(16,))
+    assert st["failed"] == 0 and sto["failed"] == 0
+    for v in range(o.nvar):
+        assert np.abs(Ug[v] - Uo[v]).max() <= 1e-8 * np.abs(Uo[v]).max() + 1e-12, v
+    s.set_state(U)
+    plain = s.step_esdirk(dt, 1, newton_tol=NT, krylov_tol=KT)
+    assert plain["failed"] == 0 and st["krylov"] < plain["krylov"] / 2
+    s.close()
