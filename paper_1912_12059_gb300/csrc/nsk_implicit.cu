@@ -5,12 +5,14 @@
 // Every implicit stage G(X) = X - dt gamma R(X) - S_i = 0, S_i = U_n + dt sum_{j<i} a_ij R_j, is
 // solved by Newton's method from the previous stage's value until ||G|| <= newton_tol ||S_i||;
 // each Newton system (I - dt gamma J) d = -G by restarted GMRES(m) (Gram-Schmidt applied twice
-// with batched projections, Givens rotations, relative residual krylov_tol, no preconditioner) with the matrix-free
-// product J v ~ (R(X + eps v) - R(X)) / eps, eps = sqrt(2^-52) (1 + ||X||) / ||v||; the later
-// stages use R_i = (X_i - S_i) / (dt gamma). The vector algebra runs in the kernels below
-// (dot products in a fixed order: deterministic), the small GMRES least-squares problem and the
-// control flow on the host; a residual evaluation is one stage launch of the context's pipeline
-// in residual mode on the iterate.
+// with batched projections, Givens rotations, relative residual krylov_tol, optionally right
+// preconditioned by the inverses of the element blocks of I - dt gamma J(U_n)) with the
+// matrix-free product J v ~ (R(X + eps v) - R(X)) / eps, eps = sqrt(2^-52) (1 + ||X||) / ||v||;
+// the later stages use R_i = (X_i - S_i) / (dt gamma). The vector algebra runs in the kernels
+// below (dot products in a fixed order: deterministic), with the scales and projection
+// coefficients of a Krylov iteration kept on the device so that the iteration reads the host
+// once; the small GMRES least-squares problem and the control flow run on the host; a residual
+// evaluation is one stage launch of the context's pipeline in residual mode on the iterate.
 #include <math.h>
 #include <string.h>
 
@@ -108,6 +110,42 @@ __global__ void __launch_bounds__(kDotThreads) k_mdot_final(const int nb, const 
     __syncthreads();
   }
   if (threadIdx.x == 0) out[blockIdx.x] = red[0];
+}
+
+// out = a x + b y + c z with a, b, c read from device memory where pa, pb, pc are given (the
+// scales that the iteration computes on the device); the same arithmetic as k_lincomb
+__global__ void __launch_bounds__(256) k_lincomb_dev(const long long n, const double a, const double* pa,
+                                                     const double* x, const double* pb, const double* y,
+                                                     const double* pc, const double* z, double* out) {
+  const double aa = pa ? *pa : a, bb = pb ? *pb : 0.0, cc = pc ? *pc : 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    double v = aa * x[i];
+    if (y) v = fma(bb, y[i], v);
+    if (z) v = fma(cc, z[i], v);
+    out[i] = v;
+  }
+}
+
+// the scales of the forward-difference product J z: eps = c0 / ||z|| (c0 = sqrt(2^-52) (1 + ||X||),
+// ||z|| = sqrt(*zz), or 1 without zz), sc[0] = eps, sc[1] = -dtg / eps, sc[2] = dtg / eps
+__global__ void k_fd_scales(const double* __restrict__ zz, const double c0, const double dtg, double* __restrict__ sc) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double eps = c0 / (zz ? sqrt(*zz) : 1.0);
+  sc[0] = eps;
+  sc[1] = -dtg / eps;
+  sc[2] = dtg / eps;
+}
+
+// norm of w after the second Gram-Schmidt pass by Pythagoras: h[0..k] are that pass's
+// projections, h[k+1] = w . w before it; ||w - sum_j h_j V_j||^2 = w . w - sum_j h_j^2 for an
+// orthonormal basis. Writes the norm into h[k+1] and its reciprocal (1 for a zero vector) to *inv.
+__global__ void k_pyth_norm(const int k, double* __restrict__ h, double* __restrict__ inv) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double s = h[k + 1];
+  for (int j = 0; j <= k; ++j) s = fma(-h[j], h[j], s);
+  const double hn = s > 0.0 ? sqrt(s) : 0.0;
+  h[k + 1] = hn;
+  *inv = hn > 0.0 ? 1.0 / hn : 1.0;
 }
 
 // w -= sum_{j < nv} h_j V_j
@@ -251,19 +289,27 @@ struct Implicit {
     return h;
   }
   double norm(const double* x) { return sqrt(dot(x, x)); }
-  // h[j] = V_j . w for j < nv (one synchronisation); dV: device copy of the basis pointers
-  void mdot(int nv, double* const* dV, const double* w, double* hdev, double* h) {
+  // x . x into *dotv on the device (no synchronisation)
+  void dot_dev(const double* x) {
+    k_dot_part<<<nblk, kDotThreads, 0, s>>>(n, x, x, part);
+    k_dot_final<<<1, kDotThreads, 0, s>>>(nblk, part, dotv);
+    launches += 2;
+  }
+  // hdev[j] = V_j . w for j < nv, on the device; dV: device copy of the basis pointers
+  void mdot(int nv, double* const* dV, const double* w, double* hdev) {
     k_mdot_part<<<dim3(nblk, nv), kDotThreads, 0, s>>>(n, dV, w, part);
     k_mdot_final<<<nv, kDotThreads, 0, s>>>(nblk, part, hdev);
     launches += 2;
-    if (cudaMemcpyAsync(h, hdev, sizeof(double) * nv, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess)
-      status = NSK_ERR_CUDA;
   }
-  // w -= sum_j h[j] V_j
-  void maxpy(int nv, double* const* dV, const double* h, double* hdev, double* w) {
-    if (cudaMemcpyAsync(hdev, h, sizeof(double) * nv, cudaMemcpyHostToDevice, s) != cudaSuccess) status = NSK_ERR_CUDA;
+  // w -= sum_j hdev[j] V_j
+  void maxpy(int nv, double* const* dV, const double* hdev, double* w) {
     k_maxpy<<<grid, 256, 0, s>>>(n, nv, dV, hdev, w);
+    ++launches;
+  }
+  // out = a x + b y + c z, the coefficients given by value or (where the pointer is not NULL) on the device
+  void lincomb_dev(double a, const double* pa, const double* x, const double* pb, const double* y, const double* pc,
+                   const double* z, double* out) {
+    k_lincomb_dev<<<grid, 256, 0, s>>>(n, a, pa, x, pb, y, pc, z, out);
     ++launches;
   }
   // out = R(X): one residual-mode stage of the context's pipeline on X
@@ -309,9 +355,10 @@ int nsk_step_esdirk(nsk_ctx* c, double dt, int nsteps, double newton_tol, double
     cudaGetLastError();
     return NSK_ERR_NOMEM;
   }
-  // dot partials ((m + 1) vectors x blocks), a dot result, m + 1 coefficients, m + 1 basis pointers
+  // dot partials ((m + 1) vectors x blocks), a dot result, the two Gram-Schmidt passes'
+  // coefficients (m + 1, and m + 2 with the norm), 4 scales, m + 1 basis pointers
   double* part = nullptr;
-  const size_t part_n = (size_t)(m + 1) * kDotBlocks + 1 + (m + 1) + (m + 1);
+  const size_t part_n = (size_t)(m + 1) * kDotBlocks + 1 + (m + 1) + (m + 2) + 4 + (m + 1);
   if (cudaMalloc(&part, sizeof(double) * part_n) != cudaSuccess) {
     cudaGetLastError();
     cudaFree(pool);
@@ -358,11 +405,13 @@ int nsk_step_esdirk(nsk_ctx* c, double dt, int nsteps, double newton_tol, double
   im.nblk = (int)(g < kDotBlocks ? (g > 0 ? g : 1) : kDotBlocks);
   im.part = part;
   im.dotv = part + (size_t)(m + 1) * kDotBlocks;
-  double* hdev = im.dotv + 1;
-  double** dV = (double**)(hdev + (m + 1));
+  double* hd1 = im.dotv + 1;       // first pass: h1[0..k]
+  double* hd2 = hd1 + (m + 1);     // second pass: h2[0..k], then the new vector's norm at k + 1
+  double* sc = hd2 + (m + 2);      // eps, -dt gamma / eps, dt gamma / eps, 1 / norm
+  double** dV = (double**)(sc + 4);
   if (cudaMemcpyAsync(dV, V.data(), sizeof(double*) * (m + 1), cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
     im.status = NSK_ERR_CUDA;
-  std::vector<double> h1(m + 1), h2(m + 1);
+  std::vector<double> hh(2 * (size_t)m + 3);  // host copy of hd1 and hd2
   long long st_newton = 0, st_krylov = 0, st_fail = 0;
   double* U = (double*)c->b.U;  // U_n, then U_{n+1}
   const double gdt = kGamma * dt;
@@ -421,27 +470,37 @@ int nsk_step_esdirk(nsk_ctx* c, double dt, int nsteps, double newton_tol, double
             // V_{k+1} = (I - dt gamma J) z, z = M^-1 V_k (z = V_k, ||z|| = 1, without the
             // preconditioner), J z ~ (R(X + eps z) - R(X)) / eps
             const double* zk = V[k];
-            double zn = 1.0;
             if (block_precond) {
               precond(V[k], Z);
               zk = Z;
-              zn = im.norm(Z);
+              im.dot_dev(Z);
             }
-            const double eps = sqrt(ldexp(1.0, -52)) * (1.0 + xn) / zn;
-            im.lincomb(1.0, X, eps, zk, 0.0, nullptr, W);
+            // the scales on the device (||z|| = 1 without the preconditioner): no host read
+            k_fd_scales<<<1, 32, 0, im.s>>>(block_precond ? im.dotv : nullptr, sqrt(ldexp(1.0, -52)) * (1.0 + xn),
+                                            gdt, sc);
+            ++im.launches;
+            im.lincomb_dev(1.0, nullptr, X, sc, zk, nullptr, nullptr, W);  // W = X + eps z
             im.rhs(W, RW);
-            im.lincomb(1.0, zk, -gdt / eps, RW, gdt / eps, RX, V[k + 1]);
+            im.lincomb_dev(1.0, nullptr, zk, sc + 1, RW, sc + 2, RX, V[k + 1]);
             ++its;
-            // classical Gram-Schmidt, twice (CGS2): all k + 1 projections of a pass in one kernel and
-            // one host read, instead of one read per projection
-            im.mdot(k + 1, dV, V[k + 1], hdev, h1.data());
-            im.maxpy(k + 1, dV, h1.data(), hdev, V[k + 1]);
-            im.mdot(k + 1, dV, V[k + 1], hdev, h2.data());
-            im.maxpy(k + 1, dV, h2.data(), hdev, V[k + 1]);
+            // classical Gram-Schmidt, twice (CGS2), each pass's k + 1 projections in one kernel with
+            // the coefficients kept on the device; the second pass also takes w . w, which gives
+            // the new vector's norm by Pythagoras; one host read per iteration
+            im.mdot(k + 1, dV, V[k + 1], hd1);
+            im.maxpy(k + 1, dV, hd1, V[k + 1]);
+            im.mdot(k + 2, dV, V[k + 1], hd2);
+            im.maxpy(k + 1, dV, hd2, V[k + 1]);
+            k_pyth_norm<<<1, 32, 0, im.s>>>(k, hd2, sc + 3);
+            ++im.launches;
+            im.lincomb_dev(0.0, sc + 3, V[k + 1], nullptr, nullptr, nullptr, nullptr, V[k + 1]);
+            if (cudaMemcpyAsync(hh.data(), hd1, sizeof(double) * ((size_t)m + 1 + k + 2), cudaMemcpyDeviceToHost,
+                                im.s) != cudaSuccess ||
+                cudaStreamSynchronize(im.s) != cudaSuccess)
+              im.status = NSK_ERR_CUDA;
+            const double* h1 = hh.data();
+            const double* h2 = hh.data() + (m + 1);
             for (int j = 0; j <= k; ++j) H[(size_t)j * m + k] = h1[j] + h2[j];
-            const double hn = im.norm(V[k + 1]);
-            H[(size_t)(k + 1) * m + k] = hn;
-            if (hn > 0.0) im.lincomb(1.0 / hn, V[k + 1], 0.0, nullptr, 0.0, nullptr, V[k + 1]);
+            H[(size_t)(k + 1) * m + k] = h2[k + 1];
             for (int j = 0; j < k; ++j) {  // earlier Givens rotations
               const double a = H[(size_t)j * m + k], b = H[(size_t)(j + 1) * m + k];
               H[(size_t)j * m + k] = cs[j] * a + sn[j] * b;
