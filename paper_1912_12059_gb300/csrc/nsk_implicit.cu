@@ -96,64 +96,71 @@ __global__ void __launch_bounds__(kDotThreads) k_mdot_part(const long long n, co
   }
 }
 
-// out[j] = sum of the nb partials of vector j (one block per j)
-__global__ void __launch_bounds__(kDotThreads) k_mdot_final(const int nb, const double* __restrict__ part,
-                                                            double* __restrict__ out) {
-  __shared__ double red[kDotThreads];
-  const double* p = part + (size_t)blockIdx.x * nb;
-  double s = 0.0;
-  for (int i = threadIdx.x; i < nb; i += blockDim.x) s += p[i];
-  red[threadIdx.x] = s;
-  __syncthreads();
-  for (int k = kDotThreads / 2; k > 0; k >>= 1) {
-    if ((int)threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) out[blockIdx.x] = red[0];
-}
-
-// out = a x + b y + c z with a, b, c read from device memory where pa, pb, pc are given (the
-// scales that the iteration computes on the device); the same arithmetic as k_lincomb
-__global__ void __launch_bounds__(256) k_lincomb_dev(const long long n, const double a, const double* pa,
-                                                     const double* x, const double* pb, const double* y,
-                                                     const double* pc, const double* z, double* out) {
-  const double aa = pa ? *pa : a, bb = pb ? *pb : 0.0, cc = pc ? *pc : 0.0;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    double v = aa * x[i];
-    if (y) v = fma(bb, y[i], v);
-    if (z) v = fma(cc, z[i], v);
-    out[i] = v;
-  }
-}
-
-// the scales of the forward-difference product J z: eps = c0 / ||z|| (c0 = sqrt(2^-52) (1 + ||X||),
-// ||z|| = sqrt(*zz), or 1 without zz), sc[0] = eps, sc[1] = -dtg / eps, sc[2] = dtg / eps
-__global__ void k_fd_scales(const double* __restrict__ zz, const double c0, const double dtg, double* __restrict__ sc) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// the two vector updates of the forward-difference product J z, with eps = c0 / ||z||
+// (c0 = sqrt(2^-52) (1 + ||X||), ||z|| = sqrt(*zz), or 1 without zz) computed by every thread:
+// which = 0: out = X + eps z (the perturbed state); which = 1: out = z - (dtg / eps) RW + (dtg / eps) RX
+__global__ void __launch_bounds__(256) k_fd_combine(const long long n, const int which, const double* __restrict__ zz,
+                                                    const double c0, const double dtg, const double* __restrict__ X,
+                                                    const double* __restrict__ z, const double* __restrict__ RW,
+                                                    const double* __restrict__ RX, double* __restrict__ out) {
   const double eps = c0 / (zz ? sqrt(*zz) : 1.0);
-  sc[0] = eps;
-  sc[1] = -dtg / eps;
-  sc[2] = dtg / eps;
+  const double b = -dtg / eps, c = dtg / eps;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    if (which == 0) {
+      out[i] = fma(eps, z[i], 1.0 * X[i]);
+    } else {
+      double v = 1.0 * z[i];
+      v = fma(b, RW[i], v);
+      out[i] = fma(c, RX[i], v);
+    }
+  }
 }
 
-// norm of w after the second Gram-Schmidt pass by Pythagoras: h[0..k] are that pass's
-// projections, h[k+1] = w . w before it; ||w - sum_j h_j V_j||^2 = w . w - sum_j h_j^2 for an
-// orthonormal basis. Writes the norm into h[k+1] and its reciprocal (1 for a zero vector) to *inv.
-__global__ void k_pyth_norm(const int k, double* __restrict__ h, double* __restrict__ inv) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  double s = h[k + 1];
-  for (int j = 0; j <= k; ++j) s = fma(-h[j], h[j], s);
-  const double hn = s > 0.0 ? sqrt(s) : 0.0;
-  h[k + 1] = hn;
-  *inv = hn > 0.0 ? 1.0 / hn : 1.0;
-}
+constexpr int kMaxNv = 202;  // projections of a pass (krylov_dim + 1) plus w . w
 
-// w -= sum_{j < nv} h_j V_j
-__global__ void __launch_bounds__(256) k_maxpy(const long long n, const int nv, const double* const* __restrict__ V,
-                                               const double* __restrict__ h, double* __restrict__ w) {
+// one Gram-Schmidt pass after k_mdot_part: every block sums the nb partials of each of the nred
+// projections (one warp per projection, lanes over the partials, then a shuffle sum), then
+// w -= sum_{j < nv} h_j V_j. With NORM (nred = nv + 1, entry nv = w . w before the pass) the new
+// vector's norm follows by Pythagoras, ||w - sum_j h_j V_j||^2 = w . w - sum_j h_j^2 for an
+// orthonormal basis, h[nv] becomes that norm and w is divided by it (left as is when zero).
+// Block 0 writes the nred coefficients to hout for the host.
+template <bool NORM>
+__global__ void __launch_bounds__(256) k_gs_update(const long long n, const int nv, const double* const* __restrict__ V,
+                                                   const double* __restrict__ part, const int nb,
+                                                   double* __restrict__ w, double* __restrict__ hout) {
+  __shared__ double h[kMaxNv];
+  __shared__ const double* vp[kMaxNv];
+  __shared__ double inv;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nred = NORM ? nv + 1 : nv;
+  for (int j = warp; j < nred; j += blockDim.x / 32) {
+    double t = 0.0;
+    for (int i = lane; i < nb; i += 32) t += part[(size_t)j * nb + i];
+    t = warp_sum(t);
+    if (lane == 0) h[j] = t;
+  }
+  for (int j = threadIdx.x; j < nv; j += blockDim.x) vp[j] = V[j];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sc = 1.0;
+    if (NORM) {
+      double t = h[nv];
+      for (int j = 0; j < nv; ++j) t = fma(-h[j], h[j], t);
+      const double hn = t > 0.0 ? sqrt(t) : 0.0;
+      h[nv] = hn;
+      sc = hn > 0.0 ? 1.0 / hn : 1.0;
+    }
+    inv = sc;
+  }
+  __syncthreads();
+  if (blockIdx.x == 0)
+    for (int j = threadIdx.x; j < nred; j += blockDim.x) hout[j] = h[j];
+  const double s = inv;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     double v = w[i];
-    for (int j = 0; j < nv; ++j) v = fma(-h[j], V[j][i], v);
+#pragma unroll 4
+    for (int j = 0; j < nv; ++j) v = fma(-h[j], vp[j][i], v);
+    if (NORM) v = s * v;
     w[i] = v;
   }
 }
@@ -295,21 +302,21 @@ struct Implicit {
     k_dot_final<<<1, kDotThreads, 0, s>>>(nblk, part, dotv);
     launches += 2;
   }
-  // hdev[j] = V_j . w for j < nv, on the device; dV: device copy of the basis pointers
-  void mdot(int nv, double* const* dV, const double* w, double* hdev) {
-    k_mdot_part<<<dim3(nblk, nv), kDotThreads, 0, s>>>(n, dV, w, part);
-    k_mdot_final<<<nv, kDotThreads, 0, s>>>(nblk, part, hdev);
+  // one Gram-Schmidt pass on w against V_0..V_{nv-1} (dV: device copy of the basis pointers):
+  // the projections (and with norm, w . w, the Pythagorean norm and the normalisation) in two
+  // kernels, the coefficients left in hout on the device
+  void gs_pass(int nv, bool norm, double* const* dV, double* w, double* hout) {
+    k_mdot_part<<<dim3(nblk, norm ? nv + 1 : nv), kDotThreads, 0, s>>>(n, dV, w, part);
+    if (norm)
+      k_gs_update<true><<<grid, 256, 0, s>>>(n, nv, dV, part, nblk, w, hout);
+    else
+      k_gs_update<false><<<grid, 256, 0, s>>>(n, nv, dV, part, nblk, w, hout);
     launches += 2;
   }
-  // w -= sum_j hdev[j] V_j
-  void maxpy(int nv, double* const* dV, const double* hdev, double* w) {
-    k_maxpy<<<grid, 256, 0, s>>>(n, nv, dV, hdev, w);
-    ++launches;
-  }
-  // out = a x + b y + c z, the coefficients given by value or (where the pointer is not NULL) on the device
-  void lincomb_dev(double a, const double* pa, const double* x, const double* pb, const double* y, const double* pc,
-                   const double* z, double* out) {
-    k_lincomb_dev<<<grid, 256, 0, s>>>(n, a, pa, x, pb, y, pc, z, out);
+  // the forward-difference combinations (k_fd_combine), zz = ||z||^2 on the device or NULL
+  void fd_combine(int which, const double* zz, double c0, double dtg, const double* X, const double* z,
+                  const double* RW, const double* RX, double* out) {
+    k_fd_combine<<<grid, 256, 0, s>>>(n, which, zz, c0, dtg, X, z, RW, RX, out);
     ++launches;
   }
   // out = R(X): one residual-mode stage of the context's pipeline on X
@@ -356,9 +363,9 @@ int nsk_step_esdirk(nsk_ctx* c, double dt, int nsteps, double newton_tol, double
     return NSK_ERR_NOMEM;
   }
   // dot partials ((m + 1) vectors x blocks), a dot result, the two Gram-Schmidt passes'
-  // coefficients (m + 1, and m + 2 with the norm), 4 scales, m + 1 basis pointers
+  // coefficients (m + 1, and m + 2 with the norm), m + 1 basis pointers
   double* part = nullptr;
-  const size_t part_n = (size_t)(m + 1) * kDotBlocks + 1 + (m + 1) + (m + 2) + 4 + (m + 1);
+  const size_t part_n = (size_t)(m + 1) * kDotBlocks + 1 + (m + 1) + (m + 2) + (m + 1);
   if (cudaMalloc(&part, sizeof(double) * part_n) != cudaSuccess) {
     cudaGetLastError();
     cudaFree(pool);
@@ -407,8 +414,7 @@ int nsk_step_esdirk(nsk_ctx* c, double dt, int nsteps, double newton_tol, double
   im.dotv = part + (size_t)(m + 1) * kDotBlocks;
   double* hd1 = im.dotv + 1;       // first pass: h1[0..k]
   double* hd2 = hd1 + (m + 1);     // second pass: h2[0..k], then the new vector's norm at k + 1
-  double* sc = hd2 + (m + 2);      // eps, -dt gamma / eps, dt gamma / eps, 1 / norm
-  double** dV = (double**)(sc + 4);
+  double** dV = (double**)(hd2 + (m + 2));
   if (cudaMemcpyAsync(dV, V.data(), sizeof(double*) * (m + 1), cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
     im.status = NSK_ERR_CUDA;
   std::vector<double> hh(2 * (size_t)m + 3);  // host copy of hd1 and hd2
@@ -475,24 +481,18 @@ int nsk_step_esdirk(nsk_ctx* c, double dt, int nsteps, double newton_tol, double
               zk = Z;
               im.dot_dev(Z);
             }
-            // the scales on the device (||z|| = 1 without the preconditioner): no host read
-            k_fd_scales<<<1, 32, 0, im.s>>>(block_precond ? im.dotv : nullptr, sqrt(ldexp(1.0, -52)) * (1.0 + xn),
-                                            gdt, sc);
-            ++im.launches;
-            im.lincomb_dev(1.0, nullptr, X, sc, zk, nullptr, nullptr, W);  // W = X + eps z
+            // eps and the scales inside the combinations (||z|| = 1 without the preconditioner)
+            const double* zz = block_precond ? im.dotv : nullptr;
+            const double c0 = sqrt(ldexp(1.0, -52)) * (1.0 + xn);
+            im.fd_combine(0, zz, c0, gdt, X, zk, nullptr, nullptr, W);  // W = X + eps z
             im.rhs(W, RW);
-            im.lincomb_dev(1.0, nullptr, zk, sc + 1, RW, sc + 2, RX, V[k + 1]);
+            im.fd_combine(1, zz, c0, gdt, nullptr, zk, RW, RX, V[k + 1]);
             ++its;
-            // classical Gram-Schmidt, twice (CGS2), each pass's k + 1 projections in one kernel with
-            // the coefficients kept on the device; the second pass also takes w . w, which gives
-            // the new vector's norm by Pythagoras; one host read per iteration
-            im.mdot(k + 1, dV, V[k + 1], hd1);
-            im.maxpy(k + 1, dV, hd1, V[k + 1]);
-            im.mdot(k + 2, dV, V[k + 1], hd2);
-            im.maxpy(k + 1, dV, hd2, V[k + 1]);
-            k_pyth_norm<<<1, 32, 0, im.s>>>(k, hd2, sc + 3);
-            ++im.launches;
-            im.lincomb_dev(0.0, sc + 3, V[k + 1], nullptr, nullptr, nullptr, nullptr, V[k + 1]);
+            // classical Gram-Schmidt, twice (CGS2), each pass's k + 1 projections in one kernel and
+            // the update in another, the coefficients kept on the device; the second pass also
+            // takes w . w, which gives the new vector's norm by Pythagoras; one host read per iteration
+            im.gs_pass(k + 1, false, dV, V[k + 1], hd1);
+            im.gs_pass(k + 1, true, dV, V[k + 1], hd2);
             if (cudaMemcpyAsync(hh.data(), hd1, sizeof(double) * ((size_t)m + 1 + k + 2), cudaMemcpyDeviceToHost,
                                 im.s) != cudaSuccess ||
                 cudaStreamSynchronize(im.s) != cudaSuccess)
