@@ -989,7 +989,9 @@ def run_fp32err(args, rank, world):
 
 
 def run_esdirk(args, rank, world):
-    """The implicit ESDIRK4 comparison (the esdirk4_implicit variant of the default run) alone."""
+    """The implicit ESDIRK4 comparison (the esdirk4_implicit variant of the default run) alone; its
+    value is the preconditioned 1000x step at the paper's stiff alpha/beta, the explicit run's wall
+    time beside it."""
     import torch
 
     from paper_1912_12059_gb300.build import build_library
@@ -999,10 +1001,13 @@ def run_esdirk(args, rank, world):
     stream = torch.cuda.Stream()
     v = measure_esdirk_variant(args, stream)
     if rank == 0:
-        x = v["esdirk4_100x"]
-        print(json.dumps({"metric": "wall ms to the same simulated time (implicit, 100x explicit dt)",
+        st = v["stiff_paper_parameters"]
+        x = st["esdirk4_1000x_block_precond"]
+        print(json.dumps({"metric": "wall ms to the simulated time of 1000 explicit LSRK4 steps (one implicit ESDIRK4 "
+                                    "step at 1000x the explicit dt, element-block preconditioner, alpha 1e3, beta 1e-3)",
                           "value": x["wall_ms"], "unit": "ms", "n_gpus": 1, "steps": x["steps"], "warmup": 0,
-                          "higher_is_better": False, "dtype": "f64", "data": "synthetic", "config": v}))
+                          "higher_is_better": False, "dtype": "f64", "data": "synthetic",
+                          "explicit_wall_ms": st["explicit_lsrk4"]["wall_ms"], "config": v}))
     return 0
 
 
