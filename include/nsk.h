@@ -223,13 +223,15 @@ int nsk_step(nsk_ctx* ctx, double dt, int nsteps);
  * differences once per step, every element of an element colour perturbed at once (colours per
  * direction: the smallest divisor >= 3 of the element count, else the count; each costs
  * nvar npe residual evaluations, counted in stats), inverted by Gauss-Jordan per element; blocks
- * of at most 48 unknowns (nvar npe) and E (nvar npe)^2 <= 2^28 values (NSK_ERR_ARG otherwise).
+ * of at most 64 unknowns (nvar npe: every order in 1D, 2D up to N = 3) and E (nvar npe)^2 <= 2^28
+ * values (NSK_ERR_ARG otherwise).
  * stats (may be NULL): Newton
  * iterations, Krylov iterations, residual evaluations, stages stopped at the iteration limit,
  * summed over the call. FP64 contexts with the explicit c equation and without the sub-cell
  * path only (NSK_ERR_ARG otherwise). Allocates 12 + krylov_dim state-sized FP64 buffers for the
- * call and frees them before returning; every dot product synchronises the stream (the GMRES
- * control runs on the host). */
+ * call and frees them before returning. The GMRES control runs on the host: each Krylov iteration
+ * reads its projection coefficients and new norm back once (one stream synchronisation), and
+ * each Newton iteration its norms. */
 int nsk_step_esdirk(nsk_ctx* ctx, double dt, int nsteps, double newton_tol, double krylov_tol, int krylov_dim,
                     int max_krylov, int block_precond, long long stats[4]);
 

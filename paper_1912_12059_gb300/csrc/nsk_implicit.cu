@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(256) k_gs_update(const long long n, const int 
 
 // ---- element-block preconditioner: blocks of I - dt gamma J, J's diagonal blocks dR_e/dU_e ----
 // local unknown k = v npe + node of element e sits at v nn + e npe + node
-constexpr int kMaxBlock = 48;  // largest block (nvar npe) the shared-memory inversion takes
+constexpr int kMaxBlock = 64;  // largest block (nvar npe) the shared-memory inversion takes (2D, N = 3)
 
 // W = U with local unknown (v, node) of every element of colour c raised by
 // eps_e = sqrt(2^-52) (1 + |U|)
@@ -198,49 +198,51 @@ __global__ void __launch_bounds__(256) k_fd_column(const long long E, const int 
   }
 }
 
-// block e: J_e <- (I - dtg J_e)^-1 by Gauss-Jordan elimination with partial pivoting in shared
-// memory ([M | I], n <= kMaxBlock); a zero pivot sets NSK_EBIT_NAN
+// block e: J_e <- (I - dtg J_e)^-1 by Gauss-Jordan elimination with partial pivoting in dynamic
+// shared memory ([M | I], n x 2n doubles, n <= kMaxBlock: 64 KB at most); a zero pivot sets
+// NSK_EBIT_NAN
 __global__ void __launch_bounds__(128) k_block_invert(const int n, const double dtg, double* __restrict__ J,
                                                       int* __restrict__ err) {
-  __shared__ double A[kMaxBlock][2 * kMaxBlock];
+  extern __shared__ double A[];  // row i at A + i * 2n
   __shared__ int piv;
+  const int w = 2 * n;
   double* Je = J + (size_t)blockIdx.x * n * n;
-  for (int t = threadIdx.x; t < n * 2 * n; t += blockDim.x) {
-    const int i = t / (2 * n), j = t % (2 * n);
-    A[i][j] = j < n ? (i == j ? 1.0 : 0.0) - dtg * Je[i * n + j] : (j - n == i ? 1.0 : 0.0);
+  for (int t = threadIdx.x; t < n * w; t += blockDim.x) {
+    const int i = t / w, j = t % w;
+    A[t] = j < n ? (i == j ? 1.0 : 0.0) - dtg * Je[i * n + j] : (j - n == i ? 1.0 : 0.0);
   }
   __syncthreads();
   for (int c = 0; c < n; ++c) {
     if (threadIdx.x == 0) {
       int p = c;
       for (int i = c + 1; i < n; ++i)
-        if (fabs(A[i][c]) > fabs(A[p][c])) p = i;
-      piv = A[p][c] == 0.0 ? -1 : p;
+        if (fabs(A[i * w + c]) > fabs(A[p * w + c])) p = i;
+      piv = A[p * w + c] == 0.0 ? -1 : p;
       if (piv < 0) atomicOr(err, NSK_EBIT_NAN);
     }
     __syncthreads();
     if (piv < 0) return;  // uniform over the block
     if (piv != c)
-      for (int j = threadIdx.x; j < 2 * n; j += blockDim.x) {
-        const double t = A[c][j];
-        A[c][j] = A[piv][j];
-        A[piv][j] = t;
+      for (int j = threadIdx.x; j < w; j += blockDim.x) {
+        const double t = A[c * w + j];
+        A[c * w + j] = A[piv * w + j];
+        A[piv * w + j] = t;
       }
     __syncthreads();
-    const double d = A[c][c];
+    const double d = A[c * w + c];
     __syncthreads();
-    for (int j = threadIdx.x; j < 2 * n; j += blockDim.x) A[c][j] /= d;
+    for (int j = threadIdx.x; j < w; j += blockDim.x) A[c * w + j] /= d;
     __syncthreads();
-    for (int t = threadIdx.x; t < n * 2 * n; t += blockDim.x) {
-      const int i = t / (2 * n), j = t % (2 * n);
-      if (i != c && j != c) A[i][j] = fma(-A[i][c], A[c][j], A[i][j]);
+    for (int t = threadIdx.x; t < n * w; t += blockDim.x) {
+      const int i = t / w, j = t % w;
+      if (i != c && j != c) A[t] = fma(-A[i * w + c], A[c * w + j], A[t]);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < n; i += blockDim.x)
-      if (i != c) A[i][c] = 0.0;
+      if (i != c) A[i * w + c] = 0.0;
     __syncthreads();
   }
-  for (int t = threadIdx.x; t < n * n; t += blockDim.x) Je[t] = A[t / n][n + t % n];
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) Je[t] = A[(t / n) * w + n + t % n];
 }
 
 // y_e = Minv_e x_e
@@ -352,6 +354,13 @@ int nsk_step_esdirk(nsk_ctx* c, double dt, int nsteps, double newton_tol, double
   const int nloc = c->nvar * c->npe;
   if (block_precond && (nloc > kMaxBlock || (double)c->E * nloc * nloc > 268435456.0)) return NSK_ERR_ARG;
   if (!c->state_set) return NSK_ERR_STATE;
+  // the block inversion's shared memory: n x 2n doubles (above the 48 KB default from n = 56 on)
+  const size_t inv_smem = sizeof(double) * 2 * (size_t)nloc * nloc;
+  if (block_precond &&
+      cudaFuncSetAttribute(k_block_invert, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)inv_smem) != cudaSuccess) {
+    cudaGetLastError();
+    return NSK_ERR_CUDA;
+  }
   const int m = krylov_dim;
   const long long n = (long long)c->nvar * c->nn;
   // state-sized buffers: R_0..R_4, X, S, RX, D (Newton update), W (X + eps v), RW, V_0..V_m,
@@ -441,7 +450,7 @@ int nsk_step_esdirk(nsk_ctx* c, double dt, int nsteps, double newton_tol, double
           k_fd_column<<<eg, 256, 0, im.s>>>(c->E, c->nvar, c->npe, c->nn, colour, col, k, U, RW, Rj[0], Jb);
           im.launches += 2;
         }
-      k_block_invert<<<(unsigned)c->E, 128, 0, im.s>>>(nloc, gdt, Jb, c->b.err);
+      k_block_invert<<<(unsigned)c->E, 128, inv_smem, im.s>>>(nloc, gdt, Jb, c->b.err);
       ++im.launches;
     }
     for (int i = 1; i < 6 && im.status == NSK_OK; ++i) {

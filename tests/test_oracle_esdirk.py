@@ -129,3 +129,28 @@ def test_block_preconditioner_same_solution_fewer_krylov_iterations():
     assert s1["failed"] == 0 and s2["failed"] == 0
     assert np.abs(U1 - U2).max() <= 1e-8 * np.abs(U1).max()
     assert s2["krylov"] < s1["krylov"] / 2, (s1, s2)
+
+
+def test_coloured_block_jacobian_2d_equals_the_dense_diagonal_blocks():
+    """2D, 6 x 6 elements, N = 3 (64 unknowns per element): colours 3 x 3. Through BR1 an element's
+    residual reaches every element within Manhattan distance two (its face neighbours' lifted
+    gradients see their own face neighbours, diagonal ones included); same-coloured elements differ
+    by at least three along some axis, so the coloured blocks equal the dense ones."""
+    from paper_1912_12059_gb300 import inputs
+
+    prm = dict(T=0.85, kappa=4e-3, alpha=1e3, beta=1e-3, mu=1e-2)
+    ne = (6, 6)
+    o = O.Oracle(2, ne, (0.0, 0.0), (1.0, 1.0), 3, O.NODES_GAUSS, **prm)
+    U = np.asarray(inputs.droplets(o.coords(), [(0.5, 0.5)], [0.25], 0.3197, 1.8071, prm["kappa"]))
+    J = ES.block_jacobian(o.rhs, U, ne)
+    nvar, E, npe = U.shape
+    n = nvar * npe
+    R0 = o.rhs(U)
+    for e in (0, 7, 20, 35):  # corners, interior, across the periodic wrap
+        for kk in range(n):
+            v, node = divmod(kk, npe)
+            W = U.copy()
+            eps = math.sqrt(2.0 ** -52) * (1.0 + abs(U[v, e, node]))
+            W[v, e, node] += eps
+            col = ((o.rhs(W) - R0)[:, e, :]).reshape(n) / eps
+            assert np.allclose(J[e, :, kk], col, rtol=1e-9, atol=1e-9 * np.abs(col).max())
