@@ -220,3 +220,35 @@ def test_fv_source_and_diffusion_exact_for_quadratic_c(N):
     assert np.abs(R[0]).max() < 1e-9
     assert np.allclose(R[1].ravel()[inner], exact_m[inner], rtol=1e-10, atol=1e-8)
     assert np.allclose(R[2].ravel()[inner], exact_c[inner], rtol=1e-10, atol=1e-6)
+
+
+@pytest.mark.parametrize("N", [2, 3, 4])
+@pytest.mark.parametrize("node_type", [O.NODES_GAUSS, O.NODES_LOBATTO])
+def test_fv_element_holding_a_polynomial_switches_back_exactly(N, node_type):
+    """An FV element whose sub-cell means are those of a polynomial of degree below N (exact
+    integrals of monomials, not the oracle's mean matrix) is smooth: its indicator is that of the
+    polynomial's nodal values (no top mode), it switches back to DG and the conversion returns
+    the polynomial's nodal values."""
+    E = 5
+    o = O.Oracle(1, (E,), (0.0,), (1.0,), N, node_type, **PRM)
+    o.fv_setup()
+    xi, _ = O.nodes(N, node_type)
+    np_ = N + 1
+    edges = -1.0 + 2.0 * np.arange(np_ + 1) / np_
+    coef = {0: (1.2, 0.3, -0.2), 1: (0.1, -0.05, 0.02), 2: (1.25, 0.2, 0.1)}  # rho, m, c in xi
+    U = np.zeros(o.shape)
+    for v, (a0, a1, a2) in coef.items():
+        U[v] = a0  # the DG elements: constant states
+        poly = lambda t: a0 + a1 * t + (a2 * t * t if N > 2 else 0.0)  # noqa: E731
+        mean = [a0 + a1 * (edges[j + 1] ** 2 - edges[j] ** 2) / 2 / (edges[j + 1] - edges[j])
+                + ((a2 * (edges[j + 1] ** 3 - edges[j] ** 3) / 3 / (edges[j + 1] - edges[j])) if N > 2 else 0.0)
+                for j in range(np_)]
+        U[v, 2] = mean
+        coef[v] = poly(xi)
+    flags = np.zeros(E, np.int32)
+    flags[2] = 1
+    U2, f2, ind = o.fv_switch(U, flags)
+    assert ind[2] < -25.0 and O.persson(coef[0], node_type) < -25.0, ind  # both at round-off: no top mode
+    assert list(f2) == [0] * E
+    for v in range(3):
+        assert np.allclose(U2[v, 2], coef[v], rtol=0, atol=1e-13), v

@@ -1,0 +1,151 @@
+"""Mutation check of the oracle's pins (no GPU): a plausible mistake planted anywhere in the
+oracle must fail at least one pin.
+
+Each mutant is a copy of oracle/nsk_oracle.c with one slip of the kind a hand translation of the
+paper makes (a dropped term, a wrong sign, index or factor, a transposed operand, a one-sided
+flux where the method takes a mean), compiled into a temporary library with the oracle's own
+flags. A child process points the oracle loader at that library and runs the pin files of the
+part it touches; the child must report failing tests (exit status 1). The unmutated copy, run
+the same way, must pass every one of those files, so a failing harness cannot pass for a caught
+mutant. Nothing is written under oracle/.
+"""
+import os
+import subprocess
+import sys
+import textwrap
+from concurrent.futures import ThreadPoolExecutor
+from pathlib import Path
+
+import pytest
+
+ROOT = Path(__file__).resolve().parents[1]
+SRC = ROOT / "oracle" / "nsk_oracle.c"
+HDR = ROOT / "oracle" / "nsk_oracle.h"
+
+CORE = ["tests/test_oracle_pins.py", "tests/test_oracle_mms.py"]
+NSK = CORE + ["tests/test_oracle_nsk.py"]
+HLLC = ["tests/test_oracle_hllc.py"]
+FV = ["tests/test_oracle_fv.py"]
+
+# name: (source text, its replacement, which occurrence, how many occurrences, pin files)
+MUTANTS = {
+    # thermodynamics and fluxes of relaxation model II (Secs. 2.1, 2.3)
+    "vdw_attraction_sign": ("- VDW_A * rho * rho;\n}\n\n/* dp/drho", "+ VDW_A * rho * rho;\n}\n\n/* dp/drho", 0, 1, CORE),
+    "modified_pressure_dropped": ("return orc_pressure(s->T, rho) + s->alpha * rho * rho / 2.0;",
+                                  "return orc_pressure(s->T, rho);", 0, 1, CORE),
+    "momentum_source_dropped": ("R[(1 + a) * nn + p] += s->alpha * rho * Q[(a * nw + d) * nn + p];",
+                                "R[(1 + a) * nn + p] += 0.0 * Q[(a * nw + d) * nn + p];", 0, 1, CORE),
+    "relaxation_source_sign": ("s->alpha / s->beta * (rho - c);", "s->alpha / s->beta * (c - rho);", 0, 1, CORE),
+    "stress_without_transpose": ("double t = Q[k * (d + 1) + a] + Q[a * (d + 1) + k];",
+                                 "double t = 2.0 * Q[k * (d + 1) + a];", 0, 2, CORE),
+    "stress_divergence_factor": ("if (a == k) t -= 2.0 / 3.0 * div;", "if (a == k) t -= 1.0 / 3.0 * div;", 0, 2, CORE),
+    "c_diffusion_without_beta": ("f[d + 1] = s->kappa / s->beta * Q[k * (d + 1) + d];",
+                                 "f[d + 1] = s->kappa * Q[k * (d + 1) + d];", 0, 1, CORE),
+    "sound_speed_without_alpha": ("return sqrt(orc_dpressure(s->T, rho) + s->alpha * rho);",
+                                  "return sqrt(fabs(orc_dpressure(s->T, rho)));", 0, 1, CORE),
+    "lax_friedrichs_sign": ("F[v] -= 0.5 * lam * (UR[v] - UL[v]);", "F[v] += 0.5 * lam * (UR[v] - UL[v]);", 0, 1, CORE),
+    "lax_friedrichs_min_speed": ("const double lam = lamL > lamR ? lamL : lamR;",
+                                 "const double lam = lamL < lamR ? lamL : lamR;", 0, 1, CORE),
+    # the DGSEM operator, BR1 and the time integrator (Sec. 3.1)
+    "derivative_matrix_transposed": ("D[i * (N + 1) + j] = lagrange_deriv(N, xi, j, xi[i]);",
+                                     "D[j * (N + 1) + i] = lagrange_deriv(N, xi, j, xi[i]);", 0, 1, CORE),
+    "volume_weight_index": ("vol += m->w[j] * F[j][v] * m->D[j * np + i];",
+                            "vol += m->w[i] * F[j][v] * m->D[j * np + i];", 0, 2, CORE),
+    "surface_term_sign": ("R[v * nn + eR * npe + node] += (2.0 / m->h[k]) * Fs[v] * m->Lm[i] / m->w[i];",
+                          "R[v * nn + eR * npe + node] -= (2.0 / m->h[k]) * Fs[v] * m->Lm[i] / m->w[i];", 0, 2, CORE),
+    "neighbour_trace_side": ("UR[v] = trace(m, U + v * nn, eR, k, n0, -1);",
+                             "UR[v] = trace(m, U + v * nn, eR, k, n0, +1);", 0, 2, CORE),
+    "viscous_flux_one_sided": ("for (int v = 0; v < nv; ++v) Fs[v] -= 0.5 * (fvL[v] + fvR[v]);",
+                               "for (int v = 0; v < nv; ++v) Fs[v] -= fvL[v];", 0, 1, CORE),
+    "br1_lifting_one_sided": ("wsm[q] = 0.5 * (wm[q] + wnm[q]);", "wsm[q] = wm[q];", 0, 1, CORE),
+    "lifting_volume_sign": ("= (2.0 / m->h[k]) * (surf - vol);\n          }", "= (2.0 / m->h[k]) * (surf + vol);\n          }",
+                            0, 1, CORE),
+    "lsrk4_coefficient_typo": ("B[3] = 3134564353537.0 / 4481467310338.0;", "B[3] = 3134564353537.0 / 4481467301338.0;",
+                               0, 1, CORE),
+    # the original NSK equations (Sec. 2.2)
+    "korteweg_tensor_sign": ("double tk = -s->kappa * Q[a * (d + 1) + d] * Q[k * (d + 1) + d];",
+                             "double tk = s->kappa * Q[a * (d + 1) + d] * Q[k * (d + 1) + d];", 0, 1, NSK),
+    "korteweg_gradient_square_factor": ("tk += s->kappa * (rho * lap + 0.5 * g2);", "tk += s->kappa * (rho * lap + g2);",
+                                        0, 1, NSK),
+    "second_lifting_one_sided": ("const double gsp = 0.5 * (trace(m, g, e, k, n0, +1) + trace(m, g, eR, k, n0, -1));",
+                                 "const double gsp = trace(m, g, e, k, n0, +1);", 0, 1, NSK),
+    "nsk_stress_without_transpose": ("double t = Q[k * (d + 1) + a] + Q[a * (d + 1) + k];",
+                                     "double t = 2.0 * Q[k * (d + 1) + a];", 1, 2, NSK),
+    # HLLC (Sec. 3.1)
+    "hllc_star_normal_velocity": ("Us[1 + a] = coef * (a == k ? Ss : UK[1 + a] / UK[0]);",
+                                  "Us[1 + a] = coef * (UK[1 + a] / UK[0]);", 0, 1, HLLC),
+    "hllc_outer_speed": ("SR = fmax(uL + aL, uR + aR);", "SR = fmax(uL + aL, uR - aR);", 0, 1, HLLC),
+    "hllc_contact_side": ("const int left = Ss >= 0.0;", "const int left = Ss < 0.0;", 0, 1, HLLC),
+    # FV sub-cells, indicator, switching and Dirichlet boundaries (Sec. 3.2)
+    "minmod_inverted": ("return a > 0.0 ? fmin(a, b) : fmax(a, b);", "return a > 0.0 ? fmax(a, b) : fmin(a, b);",
+                        0, 1, FV),
+    "boundary_half_width": ("dn[sd] = 0.5 * dx;\n        continue;", "dn[sd] = dx;\n        continue;", 0, 1, FV),
+    "subcell_source_one_sided": ("R[nn + p] += s->alpha * U[p] * 0.5 * (gc[j] + gc[j + 1]);",
+                                 "R[nn + p] += s->alpha * U[p] * gc[j + 1];", 0, 1, FV),
+    "reconstruction_mirrored": ("PL[q] = x->P[j][q] + 0.5 * dx * x->sl[j][q];",
+                                "PL[q] = x->P[j][q] - 0.5 * dx * x->sl[j][q];", 0, 1, FV),
+    "subcell_viscous_sign": ("for (int v = 0; v < 3; ++v) Fs[j + 1][v] -= fvv[v];",
+                             "for (int v = 0; v < 3; ++v) Fs[j + 1][v] += fvv[v];", 0, 1, FV),
+    "back_switch_threshold": ("fv[e] && x < f->ind_lower", "fv[e] && x < f->ind_upper", 0, 1, FV),
+    "periodic_flux_shifted": ("memcpy(Fh[E], Fh[0], sizeof(double[3]));", "memcpy(Fh[E], Fh[1], sizeof(double[3]));",
+                              0, 1, FV),
+    "mixed_lifting_without_neighbour": ("ws[sd][1] = 0.5 * (Ui[2] + Uo[2]);", "ws[sd][1] = Ui[2];", 0, 1, FV),
+    "indicator_inverse_mean_transposed": ("rho[i] += Minv[i * np + j] * U[e * np + j];",
+                                          "rho[i] += Minv[j * np + i] * U[e * np + j];", 0, 1, FV),
+}
+
+DRIVER = textwrap.dedent('''
+    import sys
+    from pathlib import Path
+    root, so = sys.argv[1], Path(sys.argv[2])
+    sys.path.insert(0, root)
+    import oracle
+    oracle.build_oracle = lambda force=False: so
+    import pytest
+    sys.exit(pytest.main(["-x", "-q", "-p", "no:cacheprovider", "-m", "not gpu"] + [root + "/" + f for f in sys.argv[3:]]))
+''')
+
+
+def _mutate(src, old, new, nth):
+    i = -1
+    for _ in range(nth + 1):
+        i = src.index(old, i + 1)
+    return src[:i] + new + src[i + len(old):]
+
+
+@pytest.fixture(scope="module")
+def outcomes(tmp_path_factory):
+    tmp = tmp_path_factory.mktemp("mutants")
+    (tmp / "drive.py").write_text(DRIVER)
+    (tmp / "nsk_oracle.h").write_text(HDR.read_text())
+    src = SRC.read_text()
+    jobs = {"control": (src, sorted(set(CORE + NSK + HLLC + FV)))}
+    for name, (old, new, nth, count, files) in MUTANTS.items():
+        assert src.count(old) == count, f"{name}: the oracle source changed; update the mutant"
+        jobs[name] = (_mutate(src, old, new, nth), files)
+
+    def run(item):
+        name, (text, files) = item
+        c = tmp / f"{name}.c"
+        c.write_text(text)
+        so = tmp / f"lib{name}.so"
+        subprocess.run(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", str(c), "-o", str(so), "-lm"],
+                       check=True)
+        r = subprocess.run([sys.executable, str(tmp / "drive.py"), str(ROOT), str(so)] + files, cwd=str(tmp),
+                           capture_output=True, text=True, timeout=600)
+        failed = [ln for ln in r.stdout.splitlines() if ln.startswith("FAILED")]
+        return name, (r.returncode, failed[:1], r.stdout[-2000:])
+
+    with ThreadPoolExecutor(max(1, min(8, os.cpu_count() or 1))) as ex:
+        return dict(ex.map(run, jobs.items()))
+
+
+def test_unmutated_copy_passes_every_pin(outcomes):
+    rc, _, out = outcomes["control"]
+    assert rc == 0, out
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_mutant_fails_a_pin(outcomes, name):
+    rc, failed, out = outcomes[name]
+    assert rc == 1 and failed, f"{name} survived the pins (exit {rc}):\n{out}"

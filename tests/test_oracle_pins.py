@@ -390,3 +390,91 @@ def test_timestep_bounds():
     visc = 0.5 / (49 * 0.1 * (16 + 64))
     src = 0.5 * 4.6 * 1e-3 / 1e3
     assert abs(orc.timestep(U, 0.5) - min(conv, visc, src)) < 1e-18
+
+
+# ---------------------------------------------------------------- stress, numerical flux, symmetry
+
+@pytest.mark.parametrize("model", [O.MODEL_RELAXATION, O.MODEL_NSK])
+def test_shear_wave_residual_closed_form(model):
+    """v = (A sin(2 pi y), 0) at uniform rho = c is an exact solution of both models: the flow is
+    divergence-free, v . grad v = 0, the pressure, the Korteweg and relaxation terms are uniform,
+    so only the shear stress acts, tau_xy = mu dv_x/dy (Eq. stress_nse) and
+    d(rho v_x)/dt = mu d^2 v_x/dy^2 = -mu (2 pi)^2 A sin(2 pi y); every other residual is zero."""
+    mu, A, rho0 = 5e-2, 0.3, 2.1
+    errs = []
+    for ne in (4, 8):  # alpha = 1 keeps the Lax-Friedrichs dissipation of the face jumps small
+        o = O.Oracle(2, (ne, ne), (0, 0), (1, 1), 4, kappa=1e-4, alpha=1.0, beta=1e-3, mu=mu, model=model)
+        y = o.coords()[1]
+        U = np.zeros(o.shape)
+        U[0] = rho0
+        U[1] = rho0 * A * np.sin(2 * np.pi * y)
+        if model == O.MODEL_RELAXATION:
+            U[3] = rho0
+        R = o.rhs(U)
+        exact = -mu * (2 * np.pi) ** 2 * A * np.sin(2 * np.pi * y)
+        scale = np.abs(exact).max()
+        errs.append(np.abs(R[1] - exact).max() / scale)
+        for v in [0, 2] + ([3] if model == O.MODEL_RELAXATION else []):
+            assert np.abs(R[v]).max() < 1e-9 * scale, v
+    assert errs[1] < 1e-2 and math.log2(errs[0] / errs[1]) > 3.0, errs
+
+
+@pytest.mark.parametrize("dim,k", [(1, 0), (2, 0), (2, 1)])
+def test_lax_friedrichs_coefficient_is_the_spectral_radius(dim, k):
+    """The local Lax-Friedrichs flux of Sec. 3.1 dissipates with the larger of the two states'
+    spectral radii of the convective flux Jacobian (its eigenvalues v_k and v_k +- sqrt(p_alpha'),
+    Eq. parabolic_eigenvalues_model2). The Jacobian here is a central difference of the physical
+    flux (the numerical flux of two equal states) and its eigenvalues come from numpy."""
+    o = O.Oracle(dim, (2,) * dim, (0,) * dim, (1,) * dim, 2, alpha=10.0, beta=1e-3, kappa=1e-4, mu=1e-3)
+    nv = dim + 2
+
+    def state(rho, vel, c):
+        return np.array([rho] + [rho * u for u in vel] + [c])
+
+    UL = state(0.5, [0.3, -0.1][:dim], 0.55)
+    UR = state(2.0, [-0.2, 0.25][:dim], 1.9)
+
+    def flux(U):
+        return o.numflux(k, U, U)
+
+    def radius(U):
+        n = nv - 1  # c has no convective flux
+        J = np.zeros((n, n))
+        for j in range(n):
+            h = 1e-6 * max(1.0, abs(U[j]))
+            Up, Um = U.copy(), U.copy()
+            Up[j] += h
+            Um[j] -= h
+            J[:, j] = (flux(Up)[:n] - flux(Um)[:n]) / (2 * h)
+        return np.abs(np.linalg.eigvals(J)).max()
+
+    lam = max(radius(UL), radius(UR))
+    assert abs(radius(UL) - radius(UR)) > 0.1 * lam  # the two states' radii differ clearly
+    D = 0.5 * (flux(UL) + flux(UR)) - o.numflux(k, UL, UR)
+    for v in range(nv - 1):  # rho and the momentum components
+        assert abs(2 * D[v] / (UR[v] - UL[v]) - lam) < 1e-7 * lam, v
+    assert abs(D[nv - 1]) < 1e-15  # no dissipation on c by default
+
+
+@pytest.mark.parametrize("nt", [O.NODES_GAUSS, O.NODES_LOBATTO])
+def test_mirror_symmetry_1d(nt):
+    """x -> 1 - x (rho and c mirrored, momentum mirrored and negated) maps the residual the same
+    way: the equations are reflection invariant and BR1 with central fluxes and the local
+    Lax-Friedrichs flux keep that on a uniform mesh with symmetric nodes."""
+    E, N = 8, 3
+    o = O.Oracle(1, (E,), (0,), (1,), N, nt, alpha=100.0, beta=1e-2, kappa=1e-3, mu=2e-2)
+    x = o.coords()[0]
+    U = np.zeros(o.shape)
+    U[0] = 1.0 + 0.3 * np.sin(2 * np.pi * x) + 0.2 * np.cos(4 * np.pi * x + 0.4)
+    U[1] = U[0] * 0.1 * np.sin(2 * np.pi * x + 0.3)
+    U[2] = U[0] * (1.0 + 0.01 * np.cos(2 * np.pi * x))
+
+    def mirror(A):
+        B = A[:, ::-1, ::-1].copy()
+        B[1] = -B[1]
+        return B
+
+    R = o.rhs(U)
+    Rm = o.rhs(mirror(U))
+    for v in range(3):
+        assert np.abs(Rm[v] - mirror(R)[v]).max() < 1e-11 * np.abs(R[v]).max(), v
