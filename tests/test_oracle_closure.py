@@ -1,7 +1,8 @@
 """Pins of the closure's reference pieces (no GPU).
 
 1. The FP64 network reference (oracle/mlp.py): gradients equal central finite
-   differences of its own loss.
+   differences of its own loss; forward pass, loss and gradients equal PyTorch's float64
+   layers, mse_loss and autograd.
 2. The closure target: the steady state of the oracle's c equation at frozen rho
    (v = 0) is the quasi-equilibrium of the Korteweg-limit remark (Sec. 2.3),
    c - (kappa/alpha) c_xx = rho. For rho = rho0 + A sin(2 pi x) on the periodic unit
@@ -31,6 +32,33 @@ def test_mlp_gradient_matches_finite_differences():
         lp = mlp.loss_and_grad(mlp.unflatten(flat + e, **shapes), X, T)[0]
         lm = mlp.loss_and_grad(mlp.unflatten(flat - e, **shapes), X, T)[0]
         assert abs((lp - lm) / 2e-6 - gf[i]) < 1e-7 * max(1.0, abs(gf[i]))
+
+
+def test_mlp_matches_torch_autograd():
+    """The forward pass, the mean-squared-error loss and its gradient equal PyTorch's float64
+    Linear layers with the exact (erf) GELU, mse_loss (mean over every output) and autograd."""
+    torch = __import__("torch")
+    rng = np.random.default_rng(3)
+    shapes = dict(n_in_pad=16, h1=24, h2=20, n_out=8)
+    n = 24 * 16 + 24 + 20 * 24 + 20 + 8 * 20 + 8
+    flat = rng.normal(size=n) * 0.3
+    X = rng.normal(size=(9, 16))
+    T = rng.normal(size=(9, 8))
+    p = mlp.unflatten(flat, **shapes)
+    y, _ = mlp.forward(p, X)
+    L, g = mlp.loss_and_grad(p, X, T)
+    tp = {k: torch.tensor(v, dtype=torch.float64, requires_grad=True) for k, v in p.items()}
+    tX, tT = torch.tensor(X, dtype=torch.float64), torch.tensor(T, dtype=torch.float64)
+    F = torch.nn.functional
+    h = F.gelu(F.linear(tX, tp["W1"], tp["b1"]), approximate="none")
+    h = F.gelu(F.linear(h, tp["W2"], tp["b2"]), approximate="none")
+    ty = F.linear(h, tp["W3"], tp["b3"])
+    tL = F.mse_loss(ty, tT)
+    tL.backward()
+    assert np.allclose(y, ty.detach().numpy(), rtol=1e-13, atol=1e-14)
+    assert abs(L - tL.item()) < 1e-14 * max(1.0, abs(L))
+    for k in p:
+        assert np.allclose(g[k], tp[k].grad.numpy(), rtol=1e-12, atol=1e-15), k
 
 
 def test_gelu_closed_forms():

@@ -1,13 +1,13 @@
 """Mutation check of the oracle's pins (no GPU): a plausible mistake planted anywhere in the
 oracle must fail at least one pin.
 
-Each mutant is a copy of oracle/nsk_oracle.c with one slip of the kind a hand translation of the
-paper makes (a dropped term, a wrong sign, index or factor, a transposed operand, a one-sided
-flux where the method takes a mean), compiled into a temporary library with the oracle's own
-flags. A child process points the oracle loader at that library and runs the pin files of the
-part it touches; the child must report failing tests (exit status 1). The unmutated copy, run
-the same way, must pass every one of those files, so a failing harness cannot pass for a caught
-mutant. Nothing is written under oracle/.
+Each mutant is a copy of oracle/nsk_oracle.c (compiled into a temporary library with the
+oracle's own flags), or of one of the oracle's Python modules, with one slip of the kind a hand
+translation of the paper makes (a dropped term, a wrong sign, index or factor, a transposed
+operand, a one-sided flux where the method takes a mean). A child process points the oracle at
+the mutant and runs the pin files of the part it touches; the child must report failing tests
+(exit status 1). The unmutated copy, run the same way, must pass every one of those files, so a
+failing harness cannot pass for a caught mutant. Nothing is written under oracle/.
 """
 import os
 import subprocess
@@ -94,15 +94,45 @@ MUTANTS = {
                                           "rho[i] += Minv[j * np + i] * U[e * np + j];", 0, 1, FV),
 }
 
+ESDIRK = ["tests/test_oracle_esdirk.py"]
+CLOSURE = ["tests/test_oracle_closure.py"]
+
+# the oracle's Python modules: name: (module, source text, replacement, occurrence, count, pin files)
+PY_MUTANTS = {
+    "esdirk_tableau_entry": ("esdirk", "Fr(-1743, 31250)", "Fr(-1743, 31520)", 0, 1, ESDIRK),
+    "esdirk_gamma": ("esdirk", "GAMMA = Fr(1, 4)", "GAMMA = Fr(1, 3)", 0, 1, ESDIRK),
+    "esdirk_stage_sum_short": ("esdirk", "for j in range(i))", "for j in range(i - 1))", 0, 1, ESDIRK),
+    "esdirk_stage_derivative_scale": ("esdirk", "R.append((X - S) / (dt * g))", "R.append((X - S) / dt)", 0, 1, ESDIRK),
+    "gmres_givens_sign": ("esdirk", "H[j + 1, k] = -sn[j] * H[j, k] + cs[j] * H[j + 1, k]",
+                          "H[j + 1, k] = sn[j] * H[j, k] + cs[j] * H[j + 1, k]", 0, 1, ESDIRK),
+    "colouring_too_few": ("esdirk", "for K in range(3, ne + 1):", "for K in range(2, ne + 1):", 0, 1, ESDIRK),
+    "preconditioner_sign": ("esdirk", "np.linalg.inv(np.eye(n)[None] - dtg * J)",
+                            "np.linalg.inv(np.eye(n)[None] + dtg * J)", 0, 1, ESDIRK),
+    "gelu_scale": ("mlp", "return 0.5 * z * (1.0 + _erf(z / math.sqrt(2.0)))", "return 0.5 * z * (1.0 + _erf(z / 2.0))",
+                   0, 1, CLOSURE),
+    "gelu_grad_term_dropped": ("mlp", " + z * np.exp(-0.5 * z * z) / math.sqrt(2.0 * math.pi)", "", 0, 1, CLOSURE),
+    "second_activation_dropped": ("mlp", "h2 = gelu(z2)", "h2 = z2", 0, 1, CLOSURE),
+    "loss_mean_over_rows": ("mlp", "n = y.size", "n = y.shape[0]", 0, 1, CLOSURE),
+    "backprop_wrong_preactivation": ("mlp", "dz1 = (dz2 @ p[\"W2\"]) * gelu_grad(z1)",
+                                     "dz1 = (dz2 @ p[\"W2\"]) * gelu_grad(z2[:, :z1.shape[1]])", 0, 1, CLOSURE),
+}
+
 DRIVER = textwrap.dedent('''
+    import importlib.util
     import sys
     from pathlib import Path
-    root, so = sys.argv[1], Path(sys.argv[2])
+    root, so, module, path = sys.argv[1], Path(sys.argv[2]), sys.argv[3], sys.argv[4]
     sys.path.insert(0, root)
     import oracle
     oracle.build_oracle = lambda force=False: so
+    if module != "-":  # a mutated copy of oracle/<module>.py in place of the module
+        spec = importlib.util.spec_from_file_location("oracle." + module, path)
+        mod = importlib.util.module_from_spec(spec)
+        sys.modules["oracle." + module] = mod
+        spec.loader.exec_module(mod)
+        setattr(oracle, module, mod)
     import pytest
-    sys.exit(pytest.main(["-x", "-q", "-p", "no:cacheprovider", "-m", "not gpu"] + [root + "/" + f for f in sys.argv[3:]]))
+    sys.exit(pytest.main(["-x", "-q", "-p", "no:cacheprovider", "-m", "not gpu"] + [root + "/" + f for f in sys.argv[5:]]))
 ''')
 
 
@@ -119,20 +149,34 @@ def outcomes(tmp_path_factory):
     (tmp / "drive.py").write_text(DRIVER)
     (tmp / "nsk_oracle.h").write_text(HDR.read_text())
     src = SRC.read_text()
-    jobs = {"control": (src, sorted(set(CORE + NSK + HLLC + FV)))}
-    for name, (old, new, nth, count, files) in MUTANTS.items():
-        assert src.count(old) == count, f"{name}: the oracle source changed; update the mutant"
-        jobs[name] = (_mutate(src, old, new, nth), files)
 
-    def run(item):
-        name, (text, files) = item
+    def compile_c(name, text):
         c = tmp / f"{name}.c"
         c.write_text(text)
         so = tmp / f"lib{name}.so"
         subprocess.run(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", str(c), "-o", str(so), "-lm"],
                        check=True)
-        r = subprocess.run([sys.executable, str(tmp / "drive.py"), str(ROOT), str(so)] + files, cwd=str(tmp),
-                           capture_output=True, text=True, timeout=600)
+        return so
+
+    control_so = compile_c("control", src)
+    # name: (C source text or None for the control library, Python module or "-", its mutated text, pin files)
+    jobs = {"control": (None, "-", "", sorted(set(CORE + NSK + HLLC + FV + ESDIRK + CLOSURE)))}
+    for name, (old, new, nth, count, files) in MUTANTS.items():
+        assert src.count(old) == count, f"{name}: the oracle source changed; update the mutant"
+        jobs[name] = (_mutate(src, old, new, nth), "-", "", files)
+    for name, (module, old, new, nth, count, files) in PY_MUTANTS.items():
+        text = (ROOT / "oracle" / f"{module}.py").read_text()
+        assert text.count(old) == count, f"{name}: oracle/{module}.py changed; update the mutant"
+        jobs[name] = (None, module, _mutate(text, old, new, nth), files)
+
+    def run(item):
+        name, (c_text, module, py_text, files) = item
+        so = control_so if c_text is None else compile_c(name, c_text)
+        py = tmp / f"{name}_{module}.py"
+        if module != "-":
+            py.write_text(py_text)
+        r = subprocess.run([sys.executable, str(tmp / "drive.py"), str(ROOT), str(so), module, str(py)] + files,
+                           cwd=str(tmp), capture_output=True, text=True, timeout=600)
         failed = [ln for ln in r.stdout.splitlines() if ln.startswith("FAILED")]
         return name, (r.returncode, failed[:1], r.stdout[-2000:])
 
@@ -145,7 +189,7 @@ def test_unmutated_copy_passes_every_pin(outcomes):
     assert rc == 0, out
 
 
-@pytest.mark.parametrize("name", sorted(MUTANTS))
+@pytest.mark.parametrize("name", sorted(MUTANTS) + sorted(PY_MUTANTS))
 def test_mutant_fails_a_pin(outcomes, name):
     rc, failed, out = outcomes[name]
     assert rc == 1 and failed, f"{name} survived the pins (exit {rc}):\n{out}"
