@@ -62,6 +62,16 @@ MUTANTS = {
                             0, 1, CORE),
     "lsrk4_coefficient_typo": ("B[3] = 3134564353537.0 / 4481467310338.0;", "B[3] = 3134564353537.0 / 4481467301338.0;",
                                0, 1, CORE),
+    # time-step bounds (Eq. numerics_dfl and R9) and the diagnostics (Eq. pararelax_elliptical_energy_dynamic)
+    "source_bound_constant": ("cfl * 4.6 * s->beta / s->alpha", "cfl * 4.8 * s->beta / s->alpha", 0, 1, CORE),
+    "convective_bound_order": ("const double twoNp1 = 2.0 * s->N + 1.0;", "const double twoNp1 = s->N + 1.0;", 0, 1, CORE),
+    "parabolic_bound_without_c_diffusion": ("double lamv = s->mu > s->kappa / s->beta ? s->mu : s->kappa / s->beta;",
+                                            "double lamv = s->mu;", 0, 1, CORE),
+    "energy_kinetic_factor": ("se += wq * (m2 / (2.0 * rho)", "se += wq * (m2 / rho", 0, 1, CORE),
+    "energy_capillary_dropped": ("s->kappa / 2.0 * g2);", "0.0 * g2);", 0, 1, CORE),
+    "energy_relaxation_factor": ("s->alpha / 2.0 * (rho - c) * (rho - c) +", "s->alpha * (rho - c) * (rho - c) +", 0, 1, CORE),
+    "mass_without_node_weight": ("sm += wq * rho;", "sm += J * rho;", 0, 1, CORE),
+    "l2_without_weights": ("sl += wq * (rho - c) * (rho - c);", "sl += (rho - c) * (rho - c);", 0, 1, CORE),
     # the original NSK equations (Sec. 2.2)
     "korteweg_tensor_sign": ("double tk = -s->kappa * Q[a * (d + 1) + d] * Q[k * (d + 1) + d];",
                              "double tk = s->kappa * Q[a * (d + 1) + d] * Q[k * (d + 1) + d];", 0, 1, NSK),

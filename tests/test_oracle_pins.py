@@ -478,3 +478,82 @@ def test_mirror_symmetry_1d(nt):
     Rm = o.rhs(mirror(U))
     for v in range(3):
         assert np.abs(Rm[v] - mirror(R)[v]).max() < 1e-11 * np.abs(R[v]).max(), v
+
+
+# ---------------------------------------------------------------- time-step bounds and diagnostics
+
+def _noise_after(o, U, dt, steps, v, ref):
+    """max |U_v - ref| after the steps, inf where the state left the admissible range."""
+    try:
+        V = o.step(U, dt, steps)
+    except O.OracleError:
+        return math.inf
+    return float(np.abs(V[v] - ref).max())
+
+
+def test_source_bound_sits_at_the_real_axis_stability_limit():
+    """dt_src = 4.6 beta/alpha (R9): the uniform relaxation c - rho ~ exp(-alpha t/beta) is one
+    linear mode on the real axis, so one LSRK4 step multiplies c - rho by the scheme's stability
+    function; it must not grow at the returned step and must grow 5% above it."""
+    o = O.Oracle(1, (4,), (0,), (1,), 3, alpha=1e3, beta=1e-3, kappa=1e-4, mu=1e-3)
+    U = np.zeros(o.shape)
+    U[0], U[2] = 1.2, 1.25
+    dt = o.timestep(U, 1.0)
+    amp = lambda f: abs(o.step(U, f * dt, 1)[2][0, 0] - 1.2) / 0.05  # noqa: E731
+    assert amp(1.0) <= 1.0 < amp(1.05)
+
+
+@pytest.mark.parametrize("N", [2, 3, 4])
+def test_parabolic_bound_is_stable_and_not_vacuous(N):
+    """Diffusion-dominated c (kappa/beta = 1 >> mu): grid-scale noise in c decays over 300 steps
+    at the returned dt at CFL 0.5 (Eq. numerics_dfl with lambda^v = max(mu, kappa/beta) of
+    Eq. visc_eigenvalues) and blows up at four times that step."""
+    o = O.Oracle(1, (16,), (0,), (1,), N, alpha=1.0, beta=1e-3, kappa=1e-3, mu=1e-4)
+    x = o.coords()[0]
+    U = np.zeros(o.shape)
+    U[0] = 2.1
+    U[2] = 2.1 + 1e-6 * np.random.default_rng(1).standard_normal(x.shape)
+    dt = o.timestep(U, 0.5)
+    assert _noise_after(o, U, dt, 300, 2, 2.1) < 1e-6
+    assert _noise_after(o, U, 4.0 * dt, 300, 2, 2.1) > 1e-5
+
+
+@pytest.mark.parametrize("N", [2, 3, 4])
+def test_convective_bound_is_stable_and_not_vacuous(N):
+    """Acoustics-dominated flow (mu, kappa ~ 0): noise in rho and m stays bounded over 600 steps
+    at the returned dt at CFL 1 and blows up at twice that step (measured limits between 1.5 and
+    2 for N = 2..4): the (2N+1) scaling of the bound tracks the DGSEM's spectral radius."""
+    o = O.Oracle(1, (16,), (0,), (1,), N, alpha=10.0, beta=1.0, kappa=1e-8, mu=1e-8)
+    x = o.coords()[0]
+    rng = np.random.default_rng(2)
+    U = np.zeros(o.shape)
+    U[0] = 2.1 + 1e-6 * rng.standard_normal(x.shape)
+    U[1] = 1e-6 * rng.standard_normal(x.shape)
+    U[2] = 2.1
+    dt = o.timestep(U, 1.0)
+    assert _noise_after(o, U, dt, 600, 0, 2.1) < 1e-6
+    assert _noise_after(o, U, 2.0 * dt, 600, 0, 2.1) > 1e-5
+
+
+@pytest.mark.parametrize("dim", [1, 2])
+def test_diagnostics_closed_forms(dim):
+    """Mass, energy (Eq. pararelax_elliptical_energy_dynamic) and ||rho - c||_L2 of uniform rho,
+    v and c = rho0 + A s(x) with s = sin(2 pi x) (1D) or sin(2 pi x) cos(2 pi y) (2D) on the
+    unit box: mass = rho0, energy = rho0 |v|^2/2 + W(rho0) + alpha/2 A^2 <s^2> +
+    kappa/2 (2 pi A)^2 <|grad s|^2/(2 pi)^2>, ||rho - c|| = A sqrt(<s^2>)."""
+    rho0, A, v0, alpha, kappa = 2.1, 0.05, 0.5, 1.0, 1e-2
+    ne = (16,) if dim == 1 else (12, 10)
+    o = O.Oracle(dim, ne, (0,) * dim, (1,) * dim, 4, alpha=alpha, beta=1e-3, kappa=kappa, mu=1e-3)
+    X = o.coords()
+    s = np.sin(2 * np.pi * X[0]) * (np.cos(2 * np.pi * X[1]) if dim == 2 else 1.0)
+    U = np.zeros(o.shape)
+    U[0] = rho0
+    U[1] = rho0 * v0
+    U[dim + 1] = rho0 + A * s
+    s2, g2 = (0.5, 0.5) if dim == 1 else (0.25, 0.5)  # <s^2>, <|grad s|^2>/(2 pi)^2
+    mass, energy, l2 = o.diagnostics(U)
+    e_exact = (0.5 * rho0 * v0**2 + O.free_energy(0.85, rho0) + 0.5 * alpha * A**2 * s2
+               + 0.5 * kappa * (2 * np.pi * A) ** 2 * g2)
+    assert abs(mass - rho0) < 1e-12
+    assert abs(l2 - A * math.sqrt(s2)) < 1e-9 * A
+    assert abs(energy - e_exact) < 1e-8 * abs(e_exact)
