@@ -252,3 +252,49 @@ def test_fv_element_holding_a_polynomial_switches_back_exactly(N, node_type):
     assert list(f2) == [0] * E
     for v in range(3):
         assert np.allclose(U2[v, 2], coef[v], rtol=0, atol=1e-13), v
+
+
+@pytest.mark.parametrize("N", [2, 3])
+@pytest.mark.parametrize("pattern", [(0, 1, 1, 0, 1, 0, 0), (1, 0, 1, 1, 0, 0, 1)])
+def test_mixed_mesh_exact_for_linear_c(N, pattern):
+    """rho constant, v = 0, c linear, DG and FV elements mixed, Dirichlet states equal to the
+    exact boundary values: the lifted gradient (DG) and every face quotient (FV, across FV-FV,
+    DG-FV and boundary faces) equal the slope, so the diffusive fluxes are equal on both sides of
+    every face and cancel: R_rho = 0, R_m = alpha rho c_x and R_c = (alpha/beta)(rho - c) in every
+    DG node and FV sub-cell."""
+    E = len(pattern)
+    flags = np.array(pattern, np.int32)
+    o = O.Oracle(1, (E,), (0.0,), (1.0,), N, **PRM)
+    rho, a, b = 1.3, 0.9, 0.6  # c = a + b x
+    o.fv_setup(dirichlet=True, Ub_lo=(rho, 0.0, a), Ub_hi=(rho, 0.0, a + b))
+    xn = o.coords()[0]
+    h, dx = 1.0 / E, 1.0 / (E * (N + 1))
+    U = np.zeros(o.shape)
+    U[0] = rho
+    for e in range(E):
+        U[2, e] = (a + b * (e * h + (np.arange(N + 1) + 0.5) * dx)) if flags[e] else (a + b * xn[e])
+    R = o.fv_rhs(U, flags)
+    assert np.abs(R[0]).max() < 1e-9
+    assert np.allclose(R[1], PRM["alpha"] * rho * b, rtol=1e-10, atol=1e-8)
+    assert np.allclose(R[2], PRM["alpha"] / PRM["beta"] * (rho - U[2]), rtol=1e-10, atol=1e-6)
+
+
+@pytest.mark.parametrize("N", [2, 3, 4])
+def test_dirichlet_dg_exact_for_quadratic_c(N):
+    """rho constant, v = 0, c quadratic, every element DG, Dirichlet states equal to the exact
+    boundary values: BR1 is exact for polynomials of degree <= N, and the boundary face's viscous
+    flux takes the interior side's gradient at that face, so every node, the boundary elements
+    included, has R_m = alpha rho c'(x) and R_c = (kappa/beta) c'' + (alpha/beta)(rho - c)."""
+    E = 5
+    o = O.Oracle(1, (E,), (0.0,), (1.0,), N, **PRM)
+    rho, a, b, q = 1.3, 0.9, 0.4, 0.5  # c = a + b x + q x^2
+    o.fv_setup(dirichlet=True, Ub_lo=(rho, 0.0, a), Ub_hi=(rho, 0.0, a + b + q))
+    x = o.coords()[0]
+    U = np.zeros(o.shape)
+    U[0] = rho
+    U[2] = a + b * x + q * x * x
+    R = o.fv_rhs(U, np.zeros(E, np.int32))
+    assert np.abs(R[0]).max() < 1e-9
+    assert np.allclose(R[1], PRM["alpha"] * rho * (b + 2 * q * x), rtol=1e-10, atol=1e-8)
+    exact_c = PRM["kappa"] / PRM["beta"] * 2 * q + PRM["alpha"] / PRM["beta"] * (rho - U[2])
+    assert np.allclose(R[2], exact_c, rtol=1e-10, atol=1e-6)

@@ -60,6 +60,15 @@ MUTANTS = {
     "br1_lifting_one_sided": ("wsm[q] = 0.5 * (wm[q] + wnm[q]);", "wsm[q] = wm[q];", 0, 1, CORE),
     "lifting_volume_sign": ("= (2.0 / m->h[k]) * (surf - vol);\n          }", "= (2.0 / m->h[k]) * (surf + vol);\n          }",
                             0, 1, CORE),
+    "lagrange_denominator_sign": ("if (m != j) l *= (x - xi[m]) / (xi[j] - xi[m]);",
+                                  "if (m != j) l *= (x - xi[m]) / (xi[m] - xi[j]);", 0, 1, CORE),
+    "neighbour_direction": ("int cn = (c + dir + m->ne[k]) % m->ne[k];", "int cn = (c - dir + m->ne[k]) % m->ne[k];",
+                            0, 1, CORE),
+    "lifting_metric_factor": ("Q[(long)(k * nw + q) * nn + e * npe + node] = (2.0 / m->h[k]) * (surf - vol);",
+                              "Q[(long)(k * nw + q) * nn + e * npe + node] = (1.0 / m->h[k]) * (surf - vol);", 0, 1, CORE),
+    "volume_metric_factor": ("R[v * nn + e * npe + node] += (2.0 / m->h[k]) * vol / m->w[i];",
+                             "R[v * nn + e * npe + node] += (1.0 / m->h[k]) * vol / m->w[i];", 0, 2, CORE),
+    "lsrk4_register_skipped": ("U[i] = U[i] + B[stage] * K[i];", "U[i] = U[i] + B[stage] * dt * R[i];", 0, 2, CORE),
     "lsrk4_coefficient_typo": ("B[3] = 3134564353537.0 / 4481467310338.0;", "B[3] = 3134564353537.0 / 4481467301338.0;",
                                0, 1, CORE),
     # time-step bounds (Eq. numerics_dfl and R9) and the diagnostics (Eq. pararelax_elliptical_energy_dynamic)
@@ -85,6 +94,8 @@ MUTANTS = {
     "hllc_star_normal_velocity": ("Us[1 + a] = coef * (a == k ? Ss : UK[1 + a] / UK[0]);",
                                   "Us[1 + a] = coef * (UK[1 + a] / UK[0]);", 0, 1, HLLC),
     "hllc_outer_speed": ("SR = fmax(uL + aL, uR + aR);", "SR = fmax(uL + aL, uR - aR);", 0, 1, HLLC),
+    "hllc_supersonic_branch": ("for (int v = 0; v < nv; ++v) F[v] = fL[v];", "for (int v = 0; v < nv; ++v) F[v] = fR[v];",
+                               0, 1, HLLC),
     "hllc_contact_side": ("const int left = Ss >= 0.0;", "const int left = Ss < 0.0;", 0, 1, HLLC),
     # FV sub-cells, indicator, switching and Dirichlet boundaries (Sec. 3.2)
     "minmod_inverted": ("return a > 0.0 ? fmin(a, b) : fmax(a, b);", "return a > 0.0 ? fmax(a, b) : fmin(a, b);",
@@ -100,6 +111,16 @@ MUTANTS = {
     "periodic_flux_shifted": ("memcpy(Fh[E], Fh[0], sizeof(double[3]));", "memcpy(Fh[E], Fh[1], sizeof(double[3]));",
                               0, 1, FV),
     "mixed_lifting_without_neighbour": ("ws[sd][1] = 0.5 * (Ui[2] + Uo[2]);", "ws[sd][1] = Ui[2];", 0, 1, FV),
+    "indicator_normalisation": ("return log10(uh[N] * uh[N] / tot);",
+                                "return log10(uh[N] * uh[N] / (tot - uh[0] * uh[0] + 1e-300));", 0, 1, FV),
+    "legendre_modes_not_normalised": ("return sqrt((2.0 * m + 1.0) / 2.0) * P;", "return P;", 0, 1, FV),
+    "subcell_mean_factor": ("M[j * np + i] = 0.5 * s;", "M[j * np + i] = s;", 0, 1, FV),
+    "subcell_offset": ("const double a = -1.0 + 2.0 * j / np;", "const double a = -1.0 + 2.0 * j / (np + 1);", 0, 1, FV),
+    "conversion_matrices_swapped": ("const double* T = to_fv ? M : Minv;", "const double* T = to_fv ? Minv : M;", 0, 1, FV),
+    "dirichlet_ghost_gradient_side": ("const double* gL = eL >= 0 ? el[eL].gf[1] : el[eR].gf[0];",
+                                      "const double* gL = eL >= 0 ? el[eL].gf[1] : el[eR].gf[1];", 0, 1, FV),
+    "dg_neighbour_trace_side": ("fv_dg_trace(&m, U, en, sd ? 0 : 1, Ut);", "fv_dg_trace(&m, U, en, sd ? 1 : 0, Ut);",
+                                0, 1, FV),
     "indicator_inverse_mean_transposed": ("rho[i] += Minv[i * np + j] * U[e * np + j];",
                                           "rho[i] += Minv[j * np + i] * U[e * np + j];", 0, 1, FV),
 }
