@@ -209,7 +209,6 @@ def run_reference(args, wl, rank, world):
     for _ in range(args.warmup):
         oracle_sample(wl, target_s=2.0)
     desc = ""
-    t_total = 0.0
     for _ in range(args.steps):
         r, desc = oracle_sample(wl, target_s=max(2.0, 40.0 / max(args.steps, 1)))
         rates.append(r)
