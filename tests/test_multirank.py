@@ -7,8 +7,6 @@ import sys
 from contextlib import redirect_stdout
 from pathlib import Path
 
-import pytest
-
 ROOT = Path(__file__).resolve().parents[1]
 
 
