@@ -442,6 +442,7 @@ int orc_numflux(const orc_setup* s, int k, const double* UL, const double* UR, d
 /* ------------------------------------------------------------------------ */
 
 static int lift(const orc_setup* s, const mesh_t* m, const double* U, double* Q) {
+  (void)s; /* the lifting needs no physical parameter */
   const int d = m->d, np = m->np, npe = m->npe, nw = d + 1;
   const long E = m->E, nn = E * npe;
   double* W = (double*)malloc(sizeof(double) * nw * nn);
