@@ -10,7 +10,10 @@ each against what the mathematics fixes:
 * the Korteweg limit (Sec. 2.3): relaxation model II, with c in its quasi-equilibrium, tends to
   the same operator at rate 1/alpha;
 * the solution converges on a manufactured solution (at least order N; N + 1 less the order
-  that the liftings of the third-order term may cost).
+  that the liftings of the third-order term may cost);
+* long-time physics: a planar liquid slab started off the saturation densities comes to rest with
+  the bulk densities the paper prints for T = 0.85 (Sec. 4.1.1), the equal-pressure,
+  equal-chemical-potential states of a flat interface.
 """
 import math
 
@@ -191,3 +194,29 @@ def test_design_order_nsk(dim, N, meshes, tend):
     # (measured 3.3 / 2.5 in 1D, 3.7 in 2D for N = 3); a dropped or mis-signed term does not
     # converge at all
     assert errs[-1] < 1e-4 and min(rates) > N - 1, (errs, rates)
+
+
+def test_planar_slab_comes_to_rest_at_the_printed_saturation_densities():
+    """A periodic liquid slab (tanh interfaces at 0.25 and 0.75, width 2 sqrt(kappa)) with bulk
+    densities 0.36 / 1.74, off saturation, integrated to t = 10 (viscosity damps the acoustic
+    transients, the interfaces move to conserve mass). A flat interface at rest needs equal
+    pressure and equal chemical potential on both sides, so the bulk densities at the slab's
+    centre and at the vapour's centre must be those printed in Sec. 4.1.1 (tests/golden, 4
+    significant digits)."""
+    from pathlib import Path
+
+    rows = [ln.split() for ln in (Path(__file__).resolve().parent / "golden" / "maxwell_T085.txt").read_text()
+            .splitlines() if ln.strip() and not ln.startswith("#")]
+    (Tg, rv_p, rl_p), = [tuple(map(float, r)) for r in rows]
+    kappa = 1e-3
+    o = O.Oracle(1, (32,), (0,), (1,), 3, T=Tg, kappa=kappa, mu=2e-2, model=NSK)
+    x = o.coords()[0]
+    wd = 2 * math.sqrt(kappa)
+    U = np.zeros(o.shape)
+    U[0] = 0.36 + 0.5 * (1.74 - 0.36) * (np.tanh((x - 0.25) / wd) - np.tanh((x - 0.75) / wd))
+    dt = o.timestep(U, 0.5)
+    U = o.step(U, dt, int(10.0 / dt))
+    xs, r = x.ravel(), U[0].ravel()
+    rho_liq, rho_vap = r[np.argmin(np.abs(xs - 0.5))], r[np.argmin(np.abs(xs - 0.0))]
+    assert abs(rho_vap - rv_p) < 1e-4 and abs(rho_liq - rl_p) < 1e-4, (rho_vap, rho_liq)
+    assert np.abs(U[1]).max() < 1e-3  # at rest up to a decaying acoustic residue
