@@ -227,6 +227,7 @@ static double lagrange_deriv(int N, const double* xi, int j, double x) {
   return s;
 }
 
+/* Sec. 3.1 operators of the nodal Lagrange basis: D[i][j] = l_j'(xi_i), Lm[j] = l_j(-1), Lp[j] = l_j(+1). */
 void orc_lagrange_tables(int N, const double* xi, double* D, double* Lm, double* Lp) {
   for (int i = 0; i <= N; ++i)
     for (int j = 0; j <= N; ++j) D[i * (N + 1) + j] = lagrange_deriv(N, xi, j, xi[i]);
@@ -271,6 +272,7 @@ typedef struct {
   double xi[ORC_MAXNP], w[ORC_MAXNP], D[ORC_MAXNP * ORC_MAXNP], Lm[ORC_MAXNP], Lp[ORC_MAXNP];
 } mesh_t;
 
+/* the mesh of a setup: element and node strides, spacings, nodes, weights and Lagrange tables */
 static int make_mesh(const orc_setup* s, mesh_t* m) {
   if (s->dim < 1 || s->dim > 3) return ORC_ERR_ARG;
   if (s->N < 1 || s->N >= ORC_MAXNP) return ORC_ERR_ARG;
@@ -326,6 +328,7 @@ static double trace(const mesh_t* m, const double* f, long e, int k, int n0, int
   return s;
 }
 
+/* the Van-der-Waals state space of Sec. 2.1: 0 < rho < 1/b (finite) */
 static int admissible(double rho) { return rho > 0.0 && rho < 1.0 / VDW_B && isfinite(rho); }
 
 /* lifted primitive variables: w = (v_1..v_d, c) of a model II state U = (rho, m, c);
@@ -427,6 +430,7 @@ static void numflux(const orc_setup* s, int d, int k, const double* UL, const do
   }
 }
 
+/* public entry of the convective numerical flux above (model II), with its argument checks */
 int orc_numflux(const orc_setup* s, int k, const double* UL, const double* UR, double* F) {
   if (!s || k < 0 || k >= s->dim || !UL || !UR || !F) return ORC_ERR_ARG;
   if (!admissible(UL[0]) || !admissible(UR[0])) return ORC_ERR_NONPHYSICAL;
@@ -502,6 +506,7 @@ static int lift(const orc_setup* s, const mesh_t* m, const double* U, double* Q)
   return status;
 }
 
+/* public entry of the BR1 lifting above */
 int orc_lift(const orc_setup* s, const double* U, double* Q) {
   mesh_t m;
   int st = make_mesh(s, &m);
@@ -668,6 +673,8 @@ static void conv_flux_nsk(const orc_setup* s, int d, int k, const double* U, dou
   f[1 + k] += orc_pressure(s->T, U[0]);
 }
 
+/* residual of the original NSK equations (Sec. 2.2, Eqs. nsk_1 and nsk_2) in the weak form of
+ * Eq. (weakformulation), the fluxes above, the central convective flux on the faces */
 static int residual_nsk(const orc_setup* s, const mesh_t* m, const double* U, double* R) {
   const int d = m->d, np = m->np, npe = m->npe, nv = m->nvar, nq = m->nq;
   const long E = m->E, nn = E * npe;
@@ -758,10 +765,12 @@ int orc_lift2(const orc_setup* s, const double* U, double* Q2) {
   return st;
 }
 
+/* the residual of the setup's model: relaxation model II or the original NSK equations */
 static int rhs_any(const orc_setup* s, const mesh_t* m, const double* U, double* R) {
   return s->model == 1 ? residual_nsk(s, m, U, R) : residual(s, m, U, R);
 }
 
+/* public entry of the semi-discrete residual R(U) */
 int orc_rhs(const orc_setup* s, const double* U, double* R) {
   mesh_t m;
   int st = make_mesh(s, &m);
@@ -1007,6 +1016,8 @@ double orc_persson(int N, int node_type, const double* u) {
   return log10(uh[N] * uh[N] / tot);
 }
 
+/* the MinMod limiter of the second-order TVD reconstruction (Sec. 3.2): the smaller slope in
+ * magnitude when both have the same sign, else zero */
 static double minmod(double a, double b) {
   if (a * b <= 0.0) return 0.0;
   return a > 0.0 ? fmin(a, b) : fmax(a, b);
@@ -1033,6 +1044,7 @@ typedef struct {
   double P[ORC_MAXNP][3], sl[ORC_MAXNP][3];  /* FV: cell primitives, slopes (per unit length) */
 } fv_elem_t;
 
+/* the sub-cell scheme's scope: one space dimension, relaxation model II, a valid mesh, beta > 0 */
 static int fv_check(const orc_setup* s, const orc_fv_setup* f) {
   if (!s || !f || s->dim != 1 || s->model != 0 || s->N < 1 || s->N >= ORC_MAXNP) return ORC_ERR_ARG;
   if (s->nelem[0] < 1 || !(s->hi[0] > s->lo[0]) || !(s->beta > 0.0)) return ORC_ERR_ARG;
