@@ -951,7 +951,7 @@ def run_fp32err(args, rank, world):
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     build_library()
     wl = workload_by_name("collision3d")
-    total = args.steps if "--steps" in sys.argv else 5000
+    total = args.steps if "--steps" in args.argv else 5000
     solvers = {}
     for prec in (nsk.NSK_FP64, nsk.NSK_FP32_MIXED):
         s = nsk.Solver(wl.dim, wl.nelem, wl.N, list(wl.lo[:wl.dim]), list(wl.hi[:wl.dim]), wl.node_type, prec)
@@ -1029,7 +1029,8 @@ def run_riemann1d(args, rank, world):
     return 0
 
 
-def main():
+def make_parser():
+    """The command line of the benchmark."""
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
@@ -1039,7 +1040,8 @@ def main():
                     choices=["collision3d", "coalescence2d", "interface1d", "batch", "closure", "gemm", "riemann1d",
                              "fp32err", "esdirk"])
     ap.add_argument("--rows", type=int, default=884736, help="gemm: rows (elements)")
-    ap.add_argument("--no-variants", action="store_true", help="skip the FP32 variant of the default run")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the variants of the default run (FP32, HLLC, original NSK, sub-cell, ESDIRK4)")
     ap.add_argument("--nelem-train", type=int, default=64, help="closure: training mesh (elements per direction)")
     ap.add_argument("--samples", type=int, default=200000, help="closure: training samples")
     ap.add_argument("--train-steps", type=int, default=4000, help="closure: Adam steps")
@@ -1051,7 +1053,13 @@ def main():
     ap.add_argument("--nelem", type=int, default=0, help="override elements per direction (profiling runs)")
     ap.add_argument("--schedule", default="", help='fixed stage schedule "TPB,FUSED" instead of the autotuner')
     ap.add_argument("--schedule32", default="", help='the same for the FP32 variant')
-    args = ap.parse_args()
+    return ap
+
+
+def main(argv=None):
+    argv = sys.argv[1:] if argv is None else list(argv)
+    args = make_parser().parse_args(argv)
+    args.argv = argv  # the flags given explicitly (some workloads default differently without them)
     args.warmup = max(args.warmup, 3)
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -1067,7 +1075,7 @@ def main():
     if args.workload == "esdirk":
         return run_esdirk(args, rank, world)
     if args.workload == "batch":
-        if args.precision == "fp64" and "--precision" not in sys.argv:
+        if args.precision == "fp64" and "--precision" not in argv:
             args.precision = "fp32"
         return run_batch(args, rank, world)
     wl = workload_by_name(args.workload)
