@@ -103,7 +103,8 @@ def test_mass_and_momentum_conservation_on_a_mixed_periodic_mesh(N, flux):
 
 @pytest.mark.parametrize("flux", [O.FLUX_LF, O.FLUX_HLLC])
 @pytest.mark.parametrize("N", [1, 3, 4])
-def test_fv_residual_is_exact_for_linear_data(flux, N):
+@pytest.mark.parametrize("ends", [(0.6, 1.9, 0.7, 1.6), (1.9, 0.6, 1.6, 0.7)], ids=["rising", "falling"])
+def test_fv_residual_is_exact_for_linear_data(flux, N, ends):
     """rho and c linear, v = 0, every element FV, Dirichlet states equal to the exact boundary
     values: MinMod returns the exact slope, the reconstruction is exact, both face states agree,
     so each cell's residual equals the exact cell average of the right-hand side:
@@ -111,7 +112,7 @@ def test_fv_residual_is_exact_for_linear_data(flux, N):
       c: (alpha / beta) (rho_mean - c_mean)  (the diffusive fluxes are constant and cancel)."""
     E = 7
     o = O.Oracle(1, (E,), (0.0,), (1.0,), N, flux=flux, **PRM)
-    r0, r1, c0, c1 = 0.6, 1.9, 0.7, 1.6
+    r0, r1, c0, c1 = ends
     o.fv_setup(dirichlet=True, Ub_lo=(r0, 0.0, c0), Ub_hi=(r1, 0.0, c1))
     nc = E * (N + 1)
     dx = 1.0 / nc

@@ -80,12 +80,18 @@ MUTANTS = {
     "energy_capillary_dropped": ("s->kappa / 2.0 * g2);", "0.0 * g2);", 0, 1, CORE),
     "energy_relaxation_factor": ("s->alpha / 2.0 * (rho - c) * (rho - c) +", "s->alpha * (rho - c) * (rho - c) +", 0, 1, CORE),
     "mass_without_node_weight": ("sm += wq * rho;", "sm += J * rho;", 0, 1, CORE),
+    "bound_order_2n_minus_1": ("const double twoNp1 = 2.0 * s->N + 1.0;", "const double twoNp1 = 2.0 * s->N - 1.0;",
+                               0, 1, CORE),
+    "energy_momentum_index": ("m2 += U[(1 + a) * nn + p] * U[(1 + a) * nn + p];",
+                              "m2 += U[(1 - a) * nn + p] * U[(1 + a) * nn + p];", 0, 1, CORE),
     "l2_without_weights": ("sl += wq * (rho - c) * (rho - c);", "sl += (rho - c) * (rho - c);", 0, 1, CORE),
     # the original NSK equations (Sec. 2.2)
     "korteweg_tensor_sign": ("double tk = -s->kappa * Q[a * (d + 1) + d] * Q[k * (d + 1) + d];",
                              "double tk = s->kappa * Q[a * (d + 1) + d] * Q[k * (d + 1) + d];", 0, 1, NSK),
     "korteweg_gradient_square_factor": ("tk += s->kappa * (rho * lap + 0.5 * g2);", "tk += s->kappa * (rho * lap + g2);",
                                         0, 1, NSK),
+    "korteweg_gradient_index": ("double tk = -s->kappa * Q[a * (d + 1) + d] * Q[k * (d + 1) + d];",
+                                "double tk = -s->kappa * Q[a * (d - 1) + d] * Q[k * (d + 1) + d];", 0, 1, NSK),
     "second_lifting_one_sided": ("const double gsp = 0.5 * (trace(m, g, e, k, n0, +1) + trace(m, g, eR, k, n0, -1));",
                                  "const double gsp = trace(m, g, e, k, n0, +1);", 0, 1, NSK),
     "nsk_stress_without_transpose": ("double t = Q[k * (d + 1) + a] + Q[a * (d + 1) + k];",
@@ -100,6 +106,7 @@ MUTANTS = {
     # FV sub-cells, indicator, switching and Dirichlet boundaries (Sec. 3.2)
     "minmod_inverted": ("return a > 0.0 ? fmin(a, b) : fmax(a, b);", "return a > 0.0 ? fmax(a, b) : fmin(a, b);",
                         0, 1, FV),
+    "minmod_left_slope_sum": ("(x->P[j][q] - x->P[j - 1][q]) / dx", "(x->P[j][q] + x->P[j - 1][q]) / dx", 0, 1, FV),
     "boundary_half_width": ("dn[sd] = 0.5 * dx;\n        continue;", "dn[sd] = dx;\n        continue;", 0, 1, FV),
     "subcell_source_one_sided": ("R[nn + p] += s->alpha * U[p] * 0.5 * (gc[j] + gc[j + 1]);",
                                  "R[nn + p] += s->alpha * U[p] * gc[j + 1];", 0, 1, FV),

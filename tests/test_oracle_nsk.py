@@ -105,6 +105,27 @@ def test_momentum_operator_at_rest_converges_to_the_korteweg_form():
     assert errs[-1] < 1e-5 and min(rates) > 2.5, (errs, rates)
 
 
+def test_momentum_operator_at_rest_2d_converges_to_the_korteweg_form():
+    """2D, rho = rho0 + A sin(2 pi x) cos(2 pi y), v = 0: the momentum residual converges to
+    -p'(rho) grad rho + kappa rho grad(lap rho) (the non-conservative form of div tau^K,
+    Eq. stress_nonconservative), here (-p'(rho) - 2 (2 pi)^2 kappa rho) grad rho; both components,
+    so every index of the Korteweg tensor (grad rho x grad rho, |grad rho|^2) is exercised."""
+    kappa, A, rho0 = 1e-3, 0.05, 1.2
+    errs = []
+    for ne in (8, 16):
+        o = O.Oracle(2, (ne, ne), (0, 0), (1, 1), 4, model=NSK, mu=0.0, kappa=kappa)
+        x, y = o.coords()
+        rho = rho0 + A * np.sin(2 * np.pi * x) * np.cos(2 * np.pi * y)
+        gx = 2 * np.pi * A * np.cos(2 * np.pi * x) * np.cos(2 * np.pi * y)
+        gy = -2 * np.pi * A * np.sin(2 * np.pi * x) * np.sin(2 * np.pi * y)
+        f = -_dp(rho) - 2 * (2 * np.pi) ** 2 * kappa * rho
+        R = o.rhs(np.stack([rho, 0 * rho, 0 * rho]))
+        assert np.abs(R[0]).max() < 1e-12
+        scale = max(np.abs(f * gx).max(), np.abs(f * gy).max())
+        errs.append(max(np.abs(R[1] - f * gx).max(), np.abs(R[2] - f * gy).max()) / scale)
+    assert errs[-1] < 1e-3 and math.log2(errs[0] / errs[1]) > 2.5, errs
+
+
 def test_korteweg_limit_of_relaxation_model_ii():
     """Model II momentum residual with c = (1 - (kappa/alpha) d_xx)^-1 rho (exact for one Fourier
     mode) approaches the same analytic operator with error ~ 1/alpha (Sec. 2.3, Korteweg limit)."""

@@ -503,11 +503,12 @@ def test_source_bound_sits_at_the_real_axis_stability_limit():
     assert amp(1.0) <= 1.0 < amp(1.05)
 
 
-@pytest.mark.parametrize("N", [2, 3, 4])
+@pytest.mark.parametrize("N", [1, 2, 3, 4])
 def test_parabolic_bound_is_stable_and_not_vacuous(N):
     """Diffusion-dominated c (kappa/beta = 1 >> mu): grid-scale noise in c decays over 300 steps
     at the returned dt at CFL 0.5 (Eq. numerics_dfl with lambda^v = max(mu, kappa/beta) of
-    Eq. visc_eigenvalues) and blows up at four times that step."""
+    Eq. visc_eigenvalues) and blows up at eight times that step (measured limits between CFL 0.5
+    and 3 for N = 4..1)."""
     o = O.Oracle(1, (16,), (0,), (1,), N, alpha=1.0, beta=1e-3, kappa=1e-3, mu=1e-4)
     x = o.coords()[0]
     U = np.zeros(o.shape)
@@ -515,14 +516,15 @@ def test_parabolic_bound_is_stable_and_not_vacuous(N):
     U[2] = 2.1 + 1e-6 * np.random.default_rng(1).standard_normal(x.shape)
     dt = o.timestep(U, 0.5)
     assert _noise_after(o, U, dt, 300, 2, 2.1) < 1e-6
-    assert _noise_after(o, U, 4.0 * dt, 300, 2, 2.1) > 1e-5
+    assert _noise_after(o, U, 8.0 * dt, 300, 2, 2.1) > 1e-5
 
 
-@pytest.mark.parametrize("N", [2, 3, 4])
+@pytest.mark.parametrize("N", [1, 2, 3, 4])
 def test_convective_bound_is_stable_and_not_vacuous(N):
     """Acoustics-dominated flow (mu, kappa ~ 0): noise in rho and m stays bounded over 600 steps
-    at the returned dt at CFL 1 and blows up at twice that step (measured limits between 1.5 and
-    2 for N = 2..4): the (2N+1) scaling of the bound tracks the DGSEM's spectral radius."""
+    at the returned dt at CFL 1 and blows up at three times that step (measured limits between
+    CFL 1.25 and 2.5 for N = 4..1): the (2N+1) scaling of the bound tracks the DGSEM's spectral
+    radius."""
     o = O.Oracle(1, (16,), (0,), (1,), N, alpha=10.0, beta=1.0, kappa=1e-8, mu=1e-8)
     x = o.coords()[0]
     rng = np.random.default_rng(2)
@@ -532,7 +534,7 @@ def test_convective_bound_is_stable_and_not_vacuous(N):
     U[2] = 2.1
     dt = o.timestep(U, 1.0)
     assert _noise_after(o, U, dt, 600, 0, 2.1) < 1e-6
-    assert _noise_after(o, U, 2.0 * dt, 600, 0, 2.1) > 1e-5
+    assert _noise_after(o, U, 3.0 * dt, 600, 0, 2.1) > 1e-5
 
 
 @pytest.mark.parametrize("dim", [1, 2])
@@ -541,18 +543,20 @@ def test_diagnostics_closed_forms(dim):
     v and c = rho0 + A s(x) with s = sin(2 pi x) (1D) or sin(2 pi x) cos(2 pi y) (2D) on the
     unit box: mass = rho0, energy = rho0 |v|^2/2 + W(rho0) + alpha/2 A^2 <s^2> +
     kappa/2 (2 pi A)^2 <|grad s|^2/(2 pi)^2>, ||rho - c|| = A sqrt(<s^2>)."""
-    rho0, A, v0, alpha, kappa = 2.1, 0.05, 0.5, 1.0, 1e-2
+    rho0, A, alpha, kappa = 2.1, 0.05, 1.0, 1e-2
+    vel = [0.5, -0.3][:dim]
     ne = (16,) if dim == 1 else (12, 10)
     o = O.Oracle(dim, ne, (0,) * dim, (1,) * dim, 4, alpha=alpha, beta=1e-3, kappa=kappa, mu=1e-3)
     X = o.coords()
     s = np.sin(2 * np.pi * X[0]) * (np.cos(2 * np.pi * X[1]) if dim == 2 else 1.0)
     U = np.zeros(o.shape)
     U[0] = rho0
-    U[1] = rho0 * v0
+    for a in range(dim):
+        U[1 + a] = rho0 * vel[a]
     U[dim + 1] = rho0 + A * s
     s2, g2 = (0.5, 0.5) if dim == 1 else (0.25, 0.5)  # <s^2>, <|grad s|^2>/(2 pi)^2
     mass, energy, l2 = o.diagnostics(U)
-    e_exact = (0.5 * rho0 * v0**2 + O.free_energy(0.85, rho0) + 0.5 * alpha * A**2 * s2
+    e_exact = (0.5 * rho0 * sum(u * u for u in vel) + O.free_energy(0.85, rho0) + 0.5 * alpha * A**2 * s2
                + 0.5 * kappa * (2 * np.pi * A) ** 2 * g2)
     assert abs(mass - rho0) < 1e-12
     assert abs(l2 - A * math.sqrt(s2)) < 1e-9 * A
