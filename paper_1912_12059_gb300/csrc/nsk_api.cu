@@ -477,13 +477,20 @@ int nsk_set_model(nsk_ctx* c, int model) {
   if (model == NSK_MODEL_NSK) {
     if (c->precision != NSK_FP64) return NSK_ERR_ARG;
     if (c->closure_mode == NSK_C_LEARNED || c->fv_path()) return NSK_ERR_STATE;
-    if (!c->b.Q2) {  // lap rho, and the traces of grad rho
+    if (!c->b.Q2) {  // lap rho, and the traces of grad rho; the context takes both or neither
       const size_t faces = (size_t)c->E * 2 * c->dim * c->nfn;
-      if (cudaMalloc(&c->b.Q2, sizeof(double) * (size_t)c->nn) != cudaSuccess ||
-          cudaMalloc(&c->b.Gtr, sizeof(double) * faces) != cudaSuccess) {
+      void *q2 = nullptr, *gtr = nullptr;
+      if (cudaMalloc(&q2, sizeof(double) * (size_t)c->nn) != cudaSuccess) {
         cudaGetLastError();
         return NSK_ERR_NOMEM;
       }
+      if (cudaMalloc(&gtr, sizeof(double) * faces) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(q2);
+        return NSK_ERR_NOMEM;
+      }
+      c->b.Q2 = q2;
+      c->b.Gtr = gtr;
     }
   }
   c->p.model = model;
@@ -680,24 +687,36 @@ static int fv_refresh(nsk_ctx* c) {
     c->fv_params = malloc(nsk_fv_params_size());
     if (!c->fv_params) return NSK_ERR_NOMEM;
   }
-  if (!c->fvb.flags) {
+  if (!c->fvb.flags) {  // the context takes the whole group, allocated and cleared, or none of it
     const size_t E = (size_t)c->E;
+    FvBuffers fb = {};
     struct {
       void** ptr;
       size_t bytes;
-    } allocs[] = {{(void**)&c->fvb.flags, sizeof(int) * E},          {(void**)&c->fvb.ind, sizeof(double) * E},
-                  {(void**)&c->fvb.Uf, sizeof(double) * 6 * E},      {(void**)&c->fvb.Gf, sizeof(double) * 4 * E},
-                  {(void**)&c->fvb.SL, sizeof(double) * 3 * E * c->np}, {(void**)&c->fvb.Fh, sizeof(double) * 3 * (E + 1)},
-                  {(void**)&c->fvb.bar, sizeof(unsigned) * 2}};
-    for (auto& a : allocs)
-      if (cudaMalloc(a.ptr, a.bytes) != cudaSuccess) {
+    } allocs[] = {{(void**)&fb.flags, sizeof(int) * E},          {(void**)&fb.ind, sizeof(double) * E},
+                  {(void**)&fb.Uf, sizeof(double) * 6 * E},      {(void**)&fb.Gf, sizeof(double) * 4 * E},
+                  {(void**)&fb.SL, sizeof(double) * 3 * E * c->np}, {(void**)&fb.Fh, sizeof(double) * 3 * (E + 1)},
+                  {(void**)&fb.bar, sizeof(unsigned) * 2}};
+    int st = NSK_OK;
+    for (auto& a : allocs) {
+      void* q = nullptr;
+      if (cudaMalloc(&q, a.bytes) != cudaSuccess) {
         cudaGetLastError();
-        return NSK_ERR_NOMEM;
+        st = NSK_ERR_NOMEM;
+        break;
       }
-    if (cudaMemset(c->fvb.flags, 0, sizeof(int) * E) != cudaSuccess ||
-        cudaMemset(c->fvb.ind, 0, sizeof(double) * E) != cudaSuccess ||
-        cudaMemset(c->fvb.bar, 0, sizeof(unsigned) * 2) != cudaSuccess)
-      return NSK_ERR_CUDA;
+      *a.ptr = q;
+    }
+    if (st == NSK_OK && (cudaMemset(fb.flags, 0, sizeof(int) * E) != cudaSuccess ||
+                         cudaMemset(fb.ind, 0, sizeof(double) * E) != cudaSuccess ||
+                         cudaMemset(fb.bar, 0, sizeof(unsigned) * 2) != cudaSuccess))
+      st = NSK_ERR_CUDA;
+    if (st != NSK_OK) {
+      for (auto& a : allocs)
+        if (*a.ptr) cudaFree(*a.ptr);
+      return st;
+    }
+    c->fvb = fb;
   }
   double gx[NSK_MAXNP], gw[NSK_MAXNP];
   gauss_legendre(c->np, gx, gw);

@@ -676,13 +676,21 @@ int nsk_set_closure(nsk_ctx* c, int mode, nsk_mlp* mlp, int judge_every, double 
   if (mlp->nin != 2 * (c->npe + 2 * c->dim) || mlp->nout != c->npe || mlp->max_rows < c->E) return NSK_ERR_ARG;
   for (int k = 1; k < c->dim; ++k)
     if (fabs(c->h[k] - c->h[0]) > 1e-12 * c->h[0]) return NSK_ERR_ARG;  // cubic elements only
-  if (!c->cl_X) {
-    if (cudaMalloc(&c->cl_X, sizeof(__nv_bfloat16) * c->E * mlp->nin_pad) != cudaSuccess ||
-        cudaMalloc((void**)&c->cl_Y, sizeof(float) * c->nn) != cudaSuccess ||
-        cudaMalloc((void**)&c->cl_red, 2 * sizeof(double)) != cudaSuccess) {
-      cudaGetLastError();
-      return NSK_ERR_NOMEM;
+  if (!c->cl_X) {  // the context takes the three buffers together or none of them
+    const size_t bytes[3] = {sizeof(__nv_bfloat16) * c->E * mlp->nin_pad, sizeof(float) * c->nn, 2 * sizeof(double)};
+    void* got[3] = {nullptr, nullptr, nullptr};
+    for (int i = 0; i < 3; ++i) {
+      void* q = nullptr;
+      if (cudaMalloc(&q, bytes[i]) != cudaSuccess) {
+        cudaGetLastError();
+        for (int j = 0; j < i; ++j) cudaFree(got[j]);
+        return NSK_ERR_NOMEM;
+      }
+      got[i] = q;
     }
+    c->cl_X = got[0];
+    c->cl_Y = (float*)got[1];
+    c->cl_red = (double*)got[2];
   }
   c->mlp = mlp;
   c->closure_mode = NSK_C_LEARNED;
