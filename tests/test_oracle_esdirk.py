@@ -154,3 +154,28 @@ def test_coloured_block_jacobian_2d_equals_the_dense_diagonal_blocks():
             W[v, e, node] += eps
             col = ((o.rhs(W) - R0)[:, e, :]).reshape(n) / eps
             assert np.allclose(J[e, :, kk], col, rtol=1e-9, atol=1e-9 * np.abs(col).max())
+
+
+def test_gmres_terminates_after_as_many_iterations_as_distinct_eigenvalues():
+    """For a diagonal (normal) matrix the Krylov space of any right-hand side has the dimension of
+    the number of distinct eigenvalues, so GMRES reaches the exact solution in that many
+    iterations: three here, out of a 30 x 30 system."""
+    rng = np.random.Generator(np.random.PCG64(5))
+    d = np.repeat([1.0, 2.0, 3.5], 10)
+    b = rng.standard_normal(30)
+    x, its = ES.gmres(lambda v: d * v, b, 1e-12, 20, 100)
+    assert its == 3
+    assert np.abs(d * x - b).max() < 1e-13
+
+
+def test_step_statistics_of_a_scalar_linear_ode():
+    """y' = -1.3 y, one unknown: every stage's Newton system is linear and one-dimensional, so
+    one Newton iteration with one GMRES iteration solves it (to the forward difference's
+    accuracy, within newton_tol = 1e-6); the residual evaluations are the first stage's, then per
+    implicit stage the Newton residual, one Jacobian product and the converged check:
+    1 + 5 x 3 = 16. A zero Newton limit stops all five stages at their initial iterate."""
+    y = np.array([[1.0]])
+    _, st = ES.step(lambda u: -1.3 * u, y, 0.1, newton_tol=1e-6, krylov_tol=1e-12)
+    assert st == {"newton": 5, "krylov": 5, "rhs": 16, "failed": 0}
+    _, st = ES.step(lambda u: -1.3 * u, y, 0.1, newton_tol=1e-6, krylov_tol=1e-12, max_newton=0)
+    assert st == {"newton": 0, "krylov": 0, "rhs": 6, "failed": 5}

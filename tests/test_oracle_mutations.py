@@ -143,6 +143,9 @@ PY_MUTANTS = {
     "esdirk_stage_derivative_scale": ("esdirk", "R.append((X - S) / (dt * g))", "R.append((X - S) / dt)", 0, 1, ESDIRK),
     "gmres_givens_sign": ("esdirk", "H[j + 1, k] = -sn[j] * H[j, k] + cs[j] * H[j + 1, k]",
                           "H[j + 1, k] = sn[j] * H[j, k] + cs[j] * H[j + 1, k]", 0, 1, ESDIRK),
+    "gmres_stale_residual_estimate": ("esdirk", "if abs(g[k + 1]) <= tol * bn or its >= maxit:\n                break",
+                                      "if abs(g[k - 1]) <= tol * bn or its >= maxit:\n                break", 0, 1, ESDIRK),
+    "newton_count_lost": ("esdirk", 'st["newton"] += 1', 'st["newton"] += 0', 0, 1, ESDIRK),
     "colouring_too_few": ("esdirk", "for K in range(3, ne + 1):", "for K in range(2, ne + 1):", 0, 1, ESDIRK),
     "preconditioner_sign": ("esdirk", "np.linalg.inv(np.eye(n)[None] - dtg * J)",
                             "np.linalg.inv(np.eye(n)[None] + dtg * J)", 0, 1, ESDIRK),
