@@ -15,8 +15,6 @@ import math
 
 import numpy as np
 
-from . import nsk
-
 
 def collect_snapshots(solver, dt, first_step, every, count, interface_frac=0.85, rng=None, max_per_snapshot=None):
     """Advance `solver` (explicit c equation) and gather (features, targets) of elements.
