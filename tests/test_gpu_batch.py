@@ -10,7 +10,6 @@ stepped alone; the bounded grid-barrier wait must end with NSK_ERR_TIMEOUT
 import numpy as np
 import pytest
 
-import oracle as O
 from paper_1912_12059_gb300 import inputs, nsk
 
 pytestmark = pytest.mark.gpu
