@@ -82,6 +82,15 @@ MUTANTS = {
     "mass_without_node_weight": ("sm += wq * rho;", "sm += J * rho;", 0, 1, CORE),
     "bound_order_2n_minus_1": ("const double twoNp1 = 2.0 * s->N + 1.0;", "const double twoNp1 = 2.0 * s->N - 1.0;",
                                0, 1, CORE),
+    "bound_offset_2n_plus_2": ("const double twoNp1 = 2.0 * s->N + 1.0;", "const double twoNp1 = 2.0 * s->N + 2.0;",
+                               0, 1, CORE),
+    "bound_offset_2n_plus_half": ("const double twoNp1 = 2.0 * s->N + 1.0;", "const double twoNp1 = 2.0 * s->N + 0.5;",
+                                  0, 1, CORE),
+    "parabolic_bound_offset": ("double dt_visc = lamv > 0.0 ? cfl / (twoNp1 * twoNp1 * lamv * inv_h2) : INFINITY;",
+                               "double dt_visc = lamv > 0.0 ? cfl / ((twoNp1 + 1.0) * twoNp1 * lamv * inv_h2) : INFINITY;",
+                               0, 1, CORE),
+    "convective_bound_offset": ("double dt_conv = cfl / (twoNp1 * lam_max);", "double dt_conv = cfl / ((twoNp1 - 0.5) * lam_max);",
+                                0, 1, CORE),
     "energy_momentum_index": ("m2 += U[(1 + a) * nn + p] * U[(1 + a) * nn + p];",
                               "m2 += U[(1 - a) * nn + p] * U[(1 + a) * nn + p];", 0, 1, CORE),
     "l2_without_weights": ("sl += wq * (rho - c) * (rho - c);", "sl += (rho - c) * (rho - c);", 0, 1, CORE),
@@ -165,7 +174,7 @@ DRIVER = textwrap.dedent('''
     root, so, module, path = sys.argv[1], Path(sys.argv[2]), sys.argv[3], sys.argv[4]
     sys.path.insert(0, root)
     import oracle
-    oracle.build_oracle = lambda force=False: so
+    oracle.build_oracle = lambda force=False, parallel=False: so
     if module != "-":  # a mutated copy of oracle/<module>.py in place of the module
         spec = importlib.util.spec_from_file_location("oracle." + module, path)
         mod = importlib.util.module_from_spec(spec)

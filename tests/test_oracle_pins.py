@@ -392,6 +392,46 @@ def test_timestep_bounds():
     assert abs(orc.timestep(U, 0.5) - min(conv, visc, src)) < 1e-18
 
 
+
+def _vdw_sound_speed(T, alpha, rho):
+    """sqrt(p_alpha'(rho)) from the reduced Van-der-Waals pressure p = 8 T rho/(3 - rho) - 3 rho^2
+    (Eq. vdw_p) and p_alpha = p + alpha rho^2/2 (Eq. modified_pressure), differentiated by hand."""
+    return math.sqrt(24.0 * T / (3.0 - rho) ** 2 - 6.0 * rho + alpha * rho)
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4])
+@pytest.mark.parametrize("nelem", [16, 24])
+def test_parabolic_bound_is_the_printed_formula(N, nelem):
+    """Eq. numerics_dfl prints dt <= CFL beta_RK(N) dxi^2 / (lambda^v (2N+1)^2) with
+    lambda^v = max(eps, eps^2 gamma/beta) (Eq. numerics_nsk_visc_eigenvalues; here mu and kappa/beta).
+    With beta_RK(N) folded into the CFL number (reading R9) and the parabolic bound the active one
+    (fluid at rest, kappa/beta = 1 >> mu, mild alpha), the oracle's step is that formula on the
+    element size h: a (2N+2) or (2N+1/2) offset misses it by 6% or more."""
+    o = O.Oracle(1, (nelem,), (0,), (1,), N, alpha=2.0, beta=1.0, kappa=1.0, mu=1e-3)
+    U = np.zeros(o.shape)
+    U[0], U[2] = 2.1, 2.1
+    h = 1.0 / nelem
+    printed = 0.5 * h * h / (1.0 * (2 * N + 1) ** 2)
+    conv = 0.5 * h / ((2 * N + 1) * _vdw_sound_speed(0.85, 2.0, 2.1))
+    assert printed < conv and printed < 0.5 * 4.6 * 1.0 / 2.0  # the parabolic bound is the active one
+    assert abs(o.timestep(U, 0.5) - printed) <= 1e-15 * printed
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4])
+def test_convective_bound_has_the_stated_scaling(N):
+    """The convective bound (reading R9, the Cockburn-Shu CFL scaling of Runge-Kutta DG, which the
+    paper leaves unstated) is dt = CFL h / ((2N+1) max(|v| + sqrt(p_alpha'))): with the convective
+    bound active (inviscid limit, mild relaxation) the step times (2N+1) (|v| + a)/h equals the CFL
+    number, on two element sizes; an offset other than 2N+1 changes the N-dependence."""
+    for nelem in (12, 20):
+        o = O.Oracle(1, (nelem,), (0,), (1,), N, alpha=10.0, beta=1.0, kappa=1e-8, mu=1e-8)
+        U = np.zeros(o.shape)
+        U[0], U[1], U[2] = 2.1, 2.1 * 0.4, 2.1
+        lam = (0.4 + _vdw_sound_speed(0.85, 10.0, 2.1)) * nelem
+        dt = o.timestep(U, 0.8)
+        assert abs(dt * (2 * N + 1) * lam - 0.8) <= 1e-14
+
+
 # ---------------------------------------------------------------- stress, numerical flux, symmetry
 
 @pytest.mark.parametrize("model", [O.MODEL_RELAXATION, O.MODEL_NSK])
