@@ -57,24 +57,33 @@ class OrcFvSetup(C.Structure):
     ]
 
 
-def build_oracle(force: bool = False) -> Path:
-    """Compile the oracle with gcc (FP contraction off, so no fused multiply-adds)."""
-    if not force and LIB.exists() and LIB.stat().st_mtime >= max(SRC.stat().st_mtime, HDR.stat().st_mtime):
-        return LIB
-    tmp = LIB.with_suffix(".so.tmp")
+LIB_OMP = HERE / "libnsk_oracle_omp.so"
+
+
+def build_oracle(force: bool = False, parallel: bool = False) -> Path:
+    """Compile the oracle with gcc (FP contraction off, so no fused multiply-adds). parallel=True
+    builds the same source a second time with OpenMP (-fopenmp) for the timed CPU baseline on all
+    host cores: its loops over elements and faces share out iterations that write disjoint
+    results, and every sum keeps its order, so both libraries compute the same bits."""
+    target = LIB_OMP if parallel else LIB
+    if not force and target.exists() and target.stat().st_mtime >= max(SRC.stat().st_mtime, HDR.stat().st_mtime):
+        return target
+    tmp = target.with_suffix(".so.tmp")
     cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", str(SRC), "-o", str(tmp), "-lm"]
+    if parallel:
+        cmd.insert(1, "-fopenmp")
     subprocess.run(cmd, check=True)
-    tmp.replace(LIB)
-    return LIB
+    tmp.replace(target)
+    return target
 
 
-_lib = None
+_libs = {}
 
 
-def lib():
-    global _lib
-    if _lib is None:
-        L = C.CDLL(str(build_oracle()))
+def lib(parallel: bool = False):
+    """The loaded oracle library: the plain build, or (parallel=True) the OpenMP build."""
+    if parallel not in _libs:
+        L = C.CDLL(str(build_oracle(parallel=parallel)))
         dp = C.POINTER(C.c_double)
         sp = C.POINTER(OrcSetup)
         for name in ("orc_pressure", "orc_dpressure", "orc_free_energy", "orc_chem_potential"):
@@ -106,8 +115,14 @@ def lib():
         L.orc_fv_rhs.argtypes = [sp, fp, ip, dp, dp]
         L.orc_fv_switch.argtypes = [sp, fp, ip, dp, dp]
         L.orc_fv_lsrk4.argtypes = [sp, fp, ip, dp, C.c_double, C.c_int]
-        _lib = L
-    return _lib
+        L.orc_threads.argtypes = []
+        _libs[parallel] = L
+    return _libs[parallel]
+
+
+def threads(parallel: bool = False) -> int:
+    """Threads the oracle's loops run on in that build (1 for the plain build)."""
+    return lib(parallel).orc_threads()
 
 
 def _ptr(a: np.ndarray):
@@ -202,7 +217,8 @@ class Oracle:
     [nvar][E][npe] (variables rho, rho v_1..rho v_dim, c)."""
 
     def __init__(self, dim, nelem, lo, hi, N, node_type=NODES_GAUSS, T=0.85, kappa=1e-4, alpha=1e3,
-                 beta=1e-3, mu=1e-3, c_dissipation=0, flux=FLUX_LF, model=MODEL_RELAXATION):
+                 beta=1e-3, mu=1e-3, c_dissipation=0, flux=FLUX_LF, model=MODEL_RELAXATION, parallel=False):
+        self.L = lib(parallel)  # the plain build, or the OpenMP build of the same source
         s = OrcSetup()
         s.dim = dim
         ne = list(nelem) + [1] * (3 - len(nelem))
@@ -235,39 +251,39 @@ class Oracle:
         return (self.nvar, self.E, self.npe)
 
     def coords(self):
-        """Physical node coordinates [dim][E][npe] of the affine element maps."""
+        """Physical node coordinates [dim][E][npe] of the affine element maps:
+        x_k = lo_k + h_k (e_k + (xi_{i_k} + 1)/2) with e_k the element's and i_k the node's index
+        along direction k (lexicographic, x fastest)."""
         x = np.zeros((self.dim, self.E, self.npe))
         h = [(self.hi[k] - self.lo[k]) / self.nelem[k] for k in range(self.dim)]
-        for e in range(self.E):
-            ec, r = [], e
-            for k in range(self.dim):
-                ec.append(r % self.nelem[k])
-                r //= self.nelem[k]
-            for n in range(self.npe):
-                r = n
-                for k in range(self.dim):
-                    i = r % self.np
-                    r //= self.np
-                    x[k, e, n] = self.lo[k] + h[k] * (ec[k] + 0.5 * (self.xi[i] + 1.0))
+        e = np.arange(self.E)
+        n = np.arange(self.npe)
+        se, sn = 1, 1
+        for k in range(self.dim):
+            ec = (e // se) % self.nelem[k]
+            i = (n // sn) % self.np
+            x[k] = self.lo[k] + h[k] * (ec[:, None] + 0.5 * (self.xi[i][None, :] + 1.0))
+            se *= self.nelem[k]
+            sn *= self.np
         return x
 
     def lift(self, U):
         U = np.ascontiguousarray(U, dtype=np.float64)
         Q = np.zeros((self.nq, self.E, self.npe))
-        _check(lib().orc_lift(C.byref(self.s), _ptr(U), _ptr(Q)), "orc_lift")
+        _check(self.L.orc_lift(C.byref(self.s), _ptr(U), _ptr(Q)), "orc_lift")
         return Q
 
     def rhs(self, U):
         U = np.ascontiguousarray(U, dtype=np.float64)
         R = np.zeros_like(U)
-        _check(lib().orc_rhs(C.byref(self.s), _ptr(U), _ptr(R)), "orc_rhs")
+        _check(self.L.orc_rhs(C.byref(self.s), _ptr(U), _ptr(R)), "orc_rhs")
         return R
 
     def lift2(self, U):
         """Original NSK: the second lifting, lap rho = div(grad rho), [E][npe]."""
         U = np.ascontiguousarray(U, dtype=np.float64)
         Q2 = np.zeros((self.E, self.npe))
-        _check(lib().orc_lift2(C.byref(self.s), _ptr(U), _ptr(Q2)), "orc_lift2")
+        _check(self.L.orc_lift2(C.byref(self.s), _ptr(U), _ptr(Q2)), "orc_lift2")
         return Q2
 
     def numflux(self, k, UL, UR):
@@ -275,24 +291,24 @@ class Oracle:
         UL = np.ascontiguousarray(UL, dtype=np.float64)
         UR = np.ascontiguousarray(UR, dtype=np.float64)
         F = np.zeros(self.nvar)
-        _check(lib().orc_numflux(C.byref(self.s), k, _ptr(UL), _ptr(UR), _ptr(F)), "orc_numflux")
+        _check(self.L.orc_numflux(C.byref(self.s), k, _ptr(UL), _ptr(UR), _ptr(F)), "orc_numflux")
         return F
 
     def step(self, U, dt, nsteps):
         U = np.array(U, dtype=np.float64, order="C", copy=True)
-        _check(lib().orc_lsrk4(C.byref(self.s), _ptr(U), dt, nsteps), "orc_lsrk4")
+        _check(self.L.orc_lsrk4(C.byref(self.s), _ptr(U), dt, nsteps), "orc_lsrk4")
         return U
 
     def timestep(self, U, cfl):
         U = np.ascontiguousarray(U, dtype=np.float64)
         dt = C.c_double()
-        _check(lib().orc_timestep(C.byref(self.s), _ptr(U), cfl, C.byref(dt)), "orc_timestep")
+        _check(self.L.orc_timestep(C.byref(self.s), _ptr(U), cfl, C.byref(dt)), "orc_timestep")
         return dt.value
 
     def diagnostics(self, U):
         U = np.ascontiguousarray(U, dtype=np.float64)
         m, e, l2 = C.c_double(), C.c_double(), C.c_double()
-        _check(lib().orc_diagnostics(C.byref(self.s), _ptr(U), C.byref(m), C.byref(e), C.byref(l2)),
+        _check(self.L.orc_diagnostics(C.byref(self.s), _ptr(U), C.byref(m), C.byref(e), C.byref(l2)),
                "orc_diagnostics")
         return m.value, e.value, l2.value
 
@@ -312,7 +328,7 @@ class Oracle:
         U = np.ascontiguousarray(U, dtype=np.float64)
         fl = np.ascontiguousarray(flags, dtype=np.int32)
         R = np.zeros_like(U)
-        _check(lib().orc_fv_rhs(C.byref(self.s), C.byref(self.f), fl.ctypes.data_as(C.POINTER(C.c_int)), _ptr(U),
+        _check(self.L.orc_fv_rhs(C.byref(self.s), C.byref(self.f), fl.ctypes.data_as(C.POINTER(C.c_int)), _ptr(U),
                                 _ptr(R)), "orc_fv_rhs")
         return R
 
@@ -321,13 +337,13 @@ class Oracle:
         U = np.array(U, dtype=np.float64, order="C", copy=True)
         fl = np.array(flags, dtype=np.int32, order="C", copy=True)
         ind = np.zeros(self.E)
-        _check(lib().orc_fv_switch(C.byref(self.s), C.byref(self.f), fl.ctypes.data_as(C.POINTER(C.c_int)), _ptr(U),
+        _check(self.L.orc_fv_switch(C.byref(self.s), C.byref(self.f), fl.ctypes.data_as(C.POINTER(C.c_int)), _ptr(U),
                                    _ptr(ind)), "orc_fv_switch")
         return U, fl, ind
 
     def fv_step(self, U, flags, dt, nsteps):
         U = np.array(U, dtype=np.float64, order="C", copy=True)
         fl = np.array(flags, dtype=np.int32, order="C", copy=True)
-        _check(lib().orc_fv_lsrk4(C.byref(self.s), C.byref(self.f), fl.ctypes.data_as(C.POINTER(C.c_int)), _ptr(U),
+        _check(self.L.orc_fv_lsrk4(C.byref(self.s), C.byref(self.f), fl.ctypes.data_as(C.POINTER(C.c_int)), _ptr(U),
                                   dt, nsteps), "orc_fv_lsrk4")
         return U, fl

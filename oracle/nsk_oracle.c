@@ -17,6 +17,10 @@
 #include <stdlib.h>
 #include <string.h>
 
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
 #define ORC_MAXNP 16
 #define ORC_OK 0
 #define ORC_ERR_ARG (-1)
@@ -452,7 +456,10 @@ static int lift(const orc_setup* s, const mesh_t* m, const double* U, double* Q)
   double* W = (double*)malloc(sizeof(double) * nw * nn);
   if (!W) return ORC_ERR_ARG;
   int status = ORC_OK;
-  /* primitive variables at the volume nodes */
+  /* primitive variables at the volume nodes (elements are independent: the OpenMP build of the
+   * timed CPU baseline shares them among threads; every result is written by one iteration, so
+   * both builds give the same bits) */
+#pragma omp parallel for reduction(min : status) schedule(static)
   for (long e = 0; e < E; ++e)
     for (int n = 0; n < npe; ++n) {
       double Un[5], wn[4];
@@ -461,6 +468,7 @@ static int lift(const orc_setup* s, const mesh_t* m, const double* U, double* Q)
       cons_to_prim(m, Un, wn);
       for (int q = 0; q < nw; ++q) W[q * nn + e * npe + n] = wn[q];
     }
+#pragma omp parallel for reduction(min : status) schedule(static)
   for (long e = 0; e < E; ++e) {
     for (int k = 0; k < d; ++k) {
       const long eL = neighbour(m, e, k, -1), eR = neighbour(m, e, k, +1);
@@ -530,7 +538,8 @@ static int residual(const orc_setup* s, const mesh_t* m, const double* U, double
   int status = lift(s, m, U, Q);
   for (long i = 0; i < nv * nn; ++i) R[i] = 0.0;
 
-  /* volume integral */
+  /* volume integral (each iteration writes its own element only) */
+#pragma omp parallel for schedule(static)
   for (long e = 0; e < E; ++e) {
     for (int k = 0; k < d; ++k) {
       for (int n0 = 0; n0 < npe; ++n0) {
@@ -558,12 +567,27 @@ static int residual(const orc_setup* s, const mesh_t* m, const double* U, double
   }
 
   /* surface integral: every face once, between element e (its +1 side) and
-   * its right neighbour eR (its -1 side), outward normal of e is +e_k. */
+   * its right neighbour eR (its -1 side), outward normal of e is +e_k. First the
+   * numerical flux f* of every face line (faces are independent), then its
+   * lifting onto both elements, face after face in the same order, so every
+   * node receives its surface terms in one fixed order. */
+  const int nl = npe / np; /* face lines per element and direction */
+  double* Fsall = (double*)malloc(sizeof(double) * nv * E * d * nl);
+  char* skip = (char*)calloc((size_t)E * d * nl, 1);
+  if (!Fsall || !skip) {
+    free(Fsall);
+    free(skip);
+    free(Q);
+    return ORC_ERR_ARG;
+  }
+#pragma omp parallel for reduction(min : status) schedule(static)
   for (long e = 0; e < E; ++e) {
     for (int k = 0; k < d; ++k) {
       const long eR = neighbour(m, e, k, +1);
+      int line = 0;
       for (int n0 = 0; n0 < npe; ++n0) {
         if (node_coord(m, n0, k) != 0) continue;
+        const long fl = (e * d + k) * nl + line++;
         double UL[5], UR[5], QL[12], QR[12];
         for (int v = 0; v < nv; ++v) {
           UL[v] = trace(m, U + v * nn, e, k, n0, +1);
@@ -575,6 +599,7 @@ static int residual(const orc_setup* s, const mesh_t* m, const double* U, double
         }
         if (!admissible(UL[0]) || !admissible(UR[0])) {
           status = ORC_ERR_NONPHYSICAL;
+          skip[fl] = 1;
           continue;
         }
         double fvL[5], fvR[5], Fs[5];
@@ -584,6 +609,19 @@ static int residual(const orc_setup* s, const mesh_t* m, const double* U, double
         /* convective numerical flux (LF or HLLC) minus the BR1 mean of the viscous fluxes */
         numflux(s, d, k, UL, UR, Fs);
         for (int v = 0; v < nv; ++v) Fs[v] -= 0.5 * (fvL[v] + fvR[v]);
+        for (int v = 0; v < nv; ++v) Fsall[fl * nv + v] = Fs[v];
+      }
+    }
+  }
+  for (long e = 0; e < E; ++e) {
+    for (int k = 0; k < d; ++k) {
+      const long eR = neighbour(m, e, k, +1);
+      int line = 0;
+      for (int n0 = 0; n0 < npe; ++n0) {
+        if (node_coord(m, n0, k) != 0) continue;
+        const long fl = (e * d + k) * nl + line++;
+        if (skip[fl]) continue;
+        const double* Fs = Fsall + fl * nv;
         for (int i = 0; i < np; ++i) {
           const int node = n0 + i * m->sn[k];
           for (int v = 0; v < nv; ++v) {
@@ -596,8 +634,12 @@ static int residual(const orc_setup* s, const mesh_t* m, const double* U, double
     }
   }
 
+  free(Fsall);
+  free(skip);
+
   /* pointwise sources (0, alpha rho grad c, (alpha/beta)(rho - c)), evaluated
    * with the lifted gradient of c (Sec. 3.1, last paragraph) */
+#pragma omp parallel for schedule(static)
   for (long e = 0; e < E; ++e)
     for (int n = 0; n < npe; ++n) {
       const long p = e * npe + n;
@@ -779,6 +821,16 @@ int orc_rhs(const orc_setup* s, const double* U, double* R) {
   return rhs_any(s, &m, U, R);
 }
 
+/* Threads the loops above run on: 1 in the plain build, the OpenMP team size in
+ * the build for the timed CPU baseline (the same source compiled with -fopenmp). */
+int orc_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
 /* 2N-storage update: K <- A_s K + dt R(U); U <- U + B_s K, s = 1..5. */
 int orc_lsrk4(const orc_setup* s, double* U, double dt, int nsteps) {
   mesh_t m;
@@ -794,6 +846,7 @@ int orc_lsrk4(const orc_setup* s, double* U, double dt, int nsteps) {
     for (int stage = 0; stage < 5; ++stage) {
       st = rhs_any(s, &m, U, R);
       if (st) break;
+#pragma omp parallel for schedule(static)
       for (long i = 0; i < len; ++i) {
         K[i] = A[stage] * K[i] + dt * R[i];
         U[i] = U[i] + B[stage] * K[i];

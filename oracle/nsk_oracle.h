@@ -105,6 +105,10 @@ int orc_fv_switch(const orc_setup* s, const orc_fv_setup* f, int* fv, double* U,
 /* nsteps LSRK4 steps with the switches before each step. */
 int orc_fv_lsrk4(const orc_setup* s, const orc_fv_setup* f, int* fv, double* U, double dt, int nsteps);
 
+/* Threads of this build: 1 for the plain library, the OpenMP team size for the
+ * OpenMP build of the timed CPU baseline (same source, same results bit for bit). */
+int orc_threads(void);
+
 #ifdef __cplusplus
 }
 #endif
