@@ -258,6 +258,17 @@ int nsk_get_profile(nsk_ctx* ctx, double* ms, long long* launches, int n, int re
  * the host; every launch of the library's own kernels increments it). */
 long long nsk_launch_count(nsk_ctx* ctx);
 
+/* Measured fused multiply-add throughput of the current device (the ALU
+ * roofline denominator of the stage kernels; no counterpart in the paper):
+ * precision NSK_FP64 or NSK_FP32_MIXED (FP32 FMAs). One launch of 8 blocks of
+ * 256 threads per SM, every thread running 8 independent chains
+ * x <- x a + b for iters iterations (after a shorter warm-up launch), timed
+ * with CUDA events on stream (NULL = legacy default stream); tflops receives
+ * 2 x 8 x iters x threads / time in TFLOP/s, ms the launch's time (either may
+ * be NULL). Synchronises the stream. NSK_ERR_ARG for iters outside
+ * 1..2^24 or another precision. */
+int nsk_measure_fma_rate(int precision, int iters, double* tflops, double* ms, void* stream);
+
 /* Stage schedule of a context: tpb = 128 or 256 threads per block for the
  * element kernels (elements per block = tpb / nodes per element, at least 1),
  * fused_face = 1 evaluates the face fluxes inside the volume kernel (each
@@ -291,8 +302,18 @@ int nsk_batch_create(nsk_batch** out, int n, nsk_ctx* const* instances);
  * recomputed (FP64 reductions) before every step; cfl <= 0: each instance
  * keeps the dt of its last nsk_compute_dt or adaptive nsk_step. step_ms, if
  * not NULL, receives nsteps per-step wall times (ms, CUDA events); every
- * instance of the batch completes a step within that time. */
-int nsk_batch_step(nsk_batch* batch, int nsteps, double cfl, double* step_ms);
+ * instance of the batch completes a step within that time.
+ * per_instance_latency_ms, if not NULL, receives nsteps x n values
+ * ([step][instance], ms): the time from the start of the step to the moment
+ * that instance's new state is complete in device memory, from the GPU's
+ * global timer read by one-thread kernels at the start of the step and right
+ * after the launch that finishes the instance (the instance schedule
+ * finishes instances one after another; the single-launch schedules finish
+ * all of them with their last launch). The stamps add n + 1 tiny launches
+ * to a measured step (a separately captured graph) and a device-to-device
+ * copy of n + 1 words after it; the batch keeps their buffers until it is
+ * destroyed. Returns as nsk_step. */
+int nsk_batch_step(nsk_batch* batch, int nsteps, double cfl, double* step_ms, double* per_instance_latency_ms);
 /* Batch schedule (tpb and fused_face as for a context; persistent = 1 for
  * the cooperative persistent kernel, 0 for one launch per phase covering all
  * instances, 2 for each instance's own stage launches one after another in the
@@ -309,10 +330,6 @@ long long nsk_batch_launch_count(nsk_batch* batch);
 int nsk_batch_uses_graph(nsk_batch* batch);
 /* Bound of every grid-barrier wait (default 1 s, at most 60 s). */
 int nsk_batch_set_timeout(nsk_batch* batch, double seconds);
-/* Failure-detection test hook: makes the next grid barrier unreachable, so the
- * next nsk_batch_step ends every block's bounded wait and returns
- * NSK_ERR_TIMEOUT; the batch resets its barrier and stays usable. */
-int nsk_batch_poison_barrier(nsk_batch* batch);
 void nsk_batch_destroy(nsk_batch* batch);
 
 /* Dense BF16 GEMM on the tensor cores (tcgen05, FP32 accumulation in tensor
@@ -408,19 +425,27 @@ int nsk_closure_judge(nsk_ctx* ctx, double* eta);
  * (meaning and validation as in nsk_init_mesh and nsk_set_params, node_type as
  * there, precision always FP64), from the device array U to the device array
  * Ut, both [dim+2][E][npe] FP64 and owned by the caller, on cuda_stream (NULL =
- * legacy default stream). It creates no context and calls no cudaMalloc,
+ * legacy default stream); U and Ut must be distinct arrays (aliasing them is
+ * rejected with NSK_ERR_ARG). It creates no context and calls no cudaMalloc,
  * cudaFree or other allocating routine: the intermediate arrays live in one
  * file-scope device array of nsk_static_scratch_bytes() = 64 MiB, which every
  * device that loads the library holds until the process exits. Sizes whose
  * scratch does not fit are rejected with NSK_ERR_ARG: per element the call
- * needs 8 * (d(d+1) np^d + (2d(2d+4) + d(d+2)) np^(d-1)) bytes (3D, N = 3:
- * 15744 bytes, so about 4260 elements). The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress, with that device current);
- * make that first call before any stream capture. Every call shares the array
- * and it keeps the last call's contents (the error word is cleared at the start
- * of each call), so calls that overlap on the GPU, on any stream, race and must
- * be serialised by the caller. The call synchronises cuda_stream once to read
- * the error word; returns as nsk_rhs. */
+ * needs 8 * (d(d+1) np^d + (2d(2d+5) + d(d+2)) np^(d-1)) bytes (face traces
+ * with their two FP64 reciprocal planes, viscous-flux traces, face fluxes and
+ * lifted gradients; 3D, N = 3: 16512 bytes, so about 4060 elements). The
+ * first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current). With lazy module loading
+ * (the CUDA default) that first call, or the first kernel launch of the
+ * library on the device, also loads the library's device code, and that load
+ * is when the 64 MiB array is committed on the device: the first call may
+ * itself allocate, or fail for lack of memory. The "allocates nothing"
+ * guarantee therefore holds from the second call per device on; make one
+ * warm-up call at start-up, before any stream capture. Every call shares the
+ * array and it keeps the last call's contents (the error word is cleared at
+ * the start of each call), so calls that overlap on the GPU, on any stream,
+ * race and must be serialised by the caller. The call synchronises
+ * cuda_stream once to read the error word; returns as nsk_rhs. */
 int nsk_rhs_static_scratch(int dim, const int nelem[3], const double lo[3], const double hi[3], int N, int node_type,
                            double T, double kappa, double alpha, double beta, double mu, const double* U, double* Ut,
                            void* cuda_stream);

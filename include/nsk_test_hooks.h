@@ -1,0 +1,38 @@
+/* nsk_test_hooks.h -- test-only entry points of libnsk.so.
+ *
+ * Not part of the solver's interface (include/nsk.h): these calls exist so that
+ * the test suite can drive the library's failure detection from the host,
+ * without faulting or hanging a GPU. Production code has no reason to call them.
+ * Same conventions as nsk.h: plain C, status codes, never abort. */
+#ifndef NSK_TEST_HOOKS_H
+#define NSK_TEST_HOOKS_H
+
+#include "nsk.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Failure-detection hook of a batch: writes an arrival count far above any grid
+ * size into the batch's grid barrier, so the next barrier of the persistent
+ * schedule can never complete. The next nsk_batch_step (persistent schedule)
+ * then ends every block's bounded wait after the batch's timeout
+ * (nsk_batch_set_timeout) and returns NSK_ERR_TIMEOUT; the batch clears its
+ * barrier and error word and stays usable. Synchronises the batch's stream.
+ * NSK_ERR_ARG for a NULL batch. */
+int nsk_test_hook_block_batch_barrier(nsk_batch* batch);
+
+/* Caps the grid of the persistent tensor-core kernels (the resident-weight
+ * GEMM behind nsk_gemm_bf16 and the network's training GEMMs, and the fused
+ * inference forward of nsk_mlp_forward) at max_ctas CTAs; 0 (the default)
+ * removes the cap (one CTA per SM, or fewer when there are fewer 128-row
+ * tiles). With a cap a small problem runs several row tiles per CTA, the
+ * schedule of large problems: both TMEM accumulators in turn, and the next
+ * tile's loads while the previous tile drains. Process-wide; results are
+ * the same with and without a cap. NSK_ERR_ARG for a negative cap. */
+int nsk_test_hook_tc_grid_cap(int max_ctas);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NSK_TEST_HOOKS_H */

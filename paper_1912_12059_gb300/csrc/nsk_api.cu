@@ -5,6 +5,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <atomic>
 #include <new>
 #include <utility>
 #include <vector>
@@ -926,18 +927,20 @@ static __device__ __align__(256) unsigned char nsk_static_scratch[NSK_STATIC_SCR
 
 namespace {
 
-void* g_static_scratch[NSK_STATIC_MAX_DEVICES];  // device address per device, set on first use
+// device address per device, set on first use; atomic, so host threads that make their first
+// calls concurrently each look the address up (the same value) without a data race
+std::atomic<void*> g_static_scratch[NSK_STATIC_MAX_DEVICES];
 
 int static_scratch_address(void** out) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess) return NSK_ERR_CUDA;
   if (dev < 0 || dev >= NSK_STATIC_MAX_DEVICES) return NSK_ERR_ARG;
-  if (!g_static_scratch[dev]) {
-    void* p = nullptr;
+  void* p = g_static_scratch[dev].load(std::memory_order_acquire);
+  if (!p) {
     if (cudaGetSymbolAddress(&p, nsk_static_scratch) != cudaSuccess || !p) return NSK_ERR_CUDA;
-    g_static_scratch[dev] = p;
+    g_static_scratch[dev].store(p, std::memory_order_release);
   }
-  *out = g_static_scratch[dev];
+  *out = p;
   return NSK_OK;
 }
 
@@ -950,7 +953,8 @@ extern "C" long long nsk_static_scratch_bytes(void) { return (long long)NSK_STAT
 extern "C" int nsk_rhs_static_scratch(int dim, const int nelem[3], const double lo[3], const double hi[3], int N,
                                       int node_type, double T, double kappa, double alpha, double beta, double mu,
                                       const double* U, double* Ut, void* cuda_stream) {
-  if (!nelem || !lo || !hi || !U || !Ut) return NSK_ERR_ARG;
+  // U is read by every stage kernel while Ut is written: the two must not alias
+  if (!nelem || !lo || !hi || !U || !Ut || (const void*)U == (const void*)Ut) return NSK_ERR_ARG;
   if (dim < 1 || dim > 3 || N < 1 || N + 1 > NSK_MAXNP) return NSK_ERR_ARG;
   if (node_type != NSK_NODES_GAUSS && node_type != NSK_NODES_GAUSS_LOBATTO) return NSK_ERR_ARG;
   if (!(T > 0.0 && T < 1.0) || !(kappa > 0.0) || !(beta > 0.0) || !(mu >= 0.0) || !isfinite(alpha) ||
