@@ -21,3 +21,17 @@ def rhs_tolerance(o, U, R):
     F += [s.kappa / s.beta * gc]
     amp = rh * (o.np ** 2)
     return [1e-12 * np.abs(R[v]).max() + 2e-15 * amp * F[v] for v in range(o.nvar)]
+
+
+def state_rel_err(Ug, Uo):
+    """Relative L-infinity error of a state, each variable against its own scale:
+    max over v of max|Ug[v] - Uo[v]| / max|Uo[v]|, so that a small variable (momentum of a
+    fluid nearly at rest next to rho and c of order one) is held to its own size. A variable
+    that is identically zero in the oracle's state is measured against the largest variable's
+    scale. Returns (the maximum, the per-variable list)."""
+    big = float(np.abs(Uo).max())
+    errs = []
+    for v in range(Uo.shape[0]):
+        sc = float(np.abs(Uo[v]).max())
+        errs.append(float(np.abs(Ug[v] - Uo[v]).max()) / (sc if sc > 0.0 else max(big, 1e-300)))
+    return max(errs), errs
