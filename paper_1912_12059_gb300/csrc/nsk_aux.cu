@@ -77,3 +77,69 @@ int nsk_launch_convert(const void* src, bool src64, void* dst, bool dst64, long 
     k_convert<float><<<reduce_grid(n), 256, 0, s>>>((const float*)src, dst, dst64, n);
   return cudaGetLastError() == cudaSuccess ? 1 : NSK_ERR_CUDA;
 }
+
+// ---------------------------------------------------------------------------
+// Arithmetic-rate probe (nsk_measure_fma_rate): the FMA throughput of this GPU
+// in FP64 and FP32, the denominator of the ALU roofline of the FP64 stage
+// kernels. Every thread runs CHAINS independent chains x <- x a + b (a, b
+// runtime values: nothing folds) so the pipe, not the dependency latency, is
+// the limit; |x| stays near b / (1 - a) = 1 (no overflow, no subnormals).
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kProbeChains = 8;
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_fma_rate(R* __restrict__ sink, const int iters, const R a, const R b) {
+  R x[kProbeChains];
+#pragma unroll
+  for (int c = 0; c < kProbeChains; ++c) x[c] = R(threadIdx.x + c) * R(1e-3);
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int c = 0; c < kProbeChains; ++c) x[c] = fma(x[c], a, b);
+  }
+  R s = 0;
+#pragma unroll
+  for (int c = 0; c < kProbeChains; ++c) s += x[c];
+  if (s == R(-1)) sink[threadIdx.x] = s;  // never true for these chains; keeps the work alive
+}
+
+template <typename R>
+int fma_rate_t(int iters, double* tflops, double* ms_out, cudaStream_t s) {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+    return NSK_ERR_CUDA;
+  const unsigned blocks = (unsigned)sms * 8;  // 64 resident warps per SM
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return NSK_ERR_CUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return NSK_ERR_CUDA;
+  }
+  const R a = R(0.999999), b = R(1e-6);
+  k_fma_rate<R><<<blocks, 256, 0, s>>>(nullptr, iters / 8 > 0 ? iters / 8 : 1, a, b);  // warm-up
+  cudaEventRecord(e0, s);
+  k_fma_rate<R><<<blocks, 256, 0, s>>>(nullptr, iters, a, b);
+  cudaEventRecord(e1, s);
+  int st = NSK_OK;
+  float ms = 0.f;
+  if (cudaGetLastError() != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+      cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess || !(ms > 0.f))
+    st = NSK_ERR_CUDA;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st) return st;
+  const double flops = 2.0 * kProbeChains * (double)iters * (double)blocks * 256.0;
+  if (tflops) *tflops = flops / ((double)ms * 1e-3) / 1e12;
+  if (ms_out) *ms_out = ms;
+  return NSK_OK;
+}
+
+}  // namespace
+
+extern "C" int nsk_measure_fma_rate(int precision, int iters, double* tflops, double* ms, void* stream) {
+  if (iters < 1 || iters > (1 << 24) || (precision != NSK_FP64 && precision != NSK_FP32_MIXED)) return NSK_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  return precision == NSK_FP64 ? fma_rate_t<double>(iters, tflops, ms, s) : fma_rate_t<float>(iters, tflops, ms, s);
+}

@@ -21,6 +21,7 @@
 #include <vector>
 
 #include "nsk_kernels.cuh"
+#include "nsk_test_hooks.h"
 
 // Device descriptor of one instance.
 struct BatchInst {
@@ -55,6 +56,13 @@ struct nsk_batch {
   int* d_blk2inst[2][4];
   int grid[2][2];         // co-resident grid size per [tpb index][fused]
   unsigned long long timeout_ns;  // bound of every grid-barrier wait
+  // per-instance step latency (nsk_batch_step with per_instance_latency_ms): global-timer stamps
+  // [0] step start, [1 + i] step done for instance i, written by tiny kernels inside the step's
+  // graph; after every step they are copied into a history of steps read back at the end
+  unsigned long long* d_stamp;
+  unsigned long long* d_hist;
+  long long hist_cap;      // steps the history holds
+  int graph_stamps;        // the captured graph carries the stamp kernels
 };
 
 namespace {
@@ -433,31 +441,79 @@ int prepare_batch(nsk_batch* bt) {
   return NSK_OK;
 }
 
-// instance schedule: every instance's own stage kernels, one instance after another
-int launch_instances(nsk_batch* bt, int mode, double A, double B, int tpb, int fused, int traces) {
-  for (nsk_ctx* c : bt->inst) {
+// slot[i] = the global timer (ns), i < n: the step-start stamp (n = 1) or the completion stamp
+// of instances whose work ended with the previous launch on the stream (stream order)
+__global__ void k_stamp(unsigned long long* __restrict__ slot, const int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) slot[i] = nsk::global_ns();
+}
+
+int launch_stamp(nsk_batch* bt, unsigned long long* slot, int n) {
+  k_stamp<<<(n + 255) / 256, 256, 0, bt->stream>>>(slot, n);
+  ++bt->launches;
+  return cudaGetLastError() == cudaSuccess ? NSK_OK : NSK_ERR_CUDA;
+}
+
+// instance schedule: every instance's own stage kernels, one instance after another; with
+// stamps (the last stage of a step whose latencies are measured) each instance's completion
+// is stamped right after its last kernel
+int launch_instances(nsk_batch* bt, int mode, double A, double B, int tpb, int fused, int traces,
+                     bool stamps = false) {
+  for (int i = 0; i < bt->n; ++i) {
+    nsk_ctx* c = bt->inst[i];
     NskLaunch l = {mode, c->rbuf, A, B, c->b.dt, 0.0, nullptr, tpb, fused};
     l.traces_ready = traces & 1;
     l.utr_next = (traces & 2) ? c->b.Utr : nullptr;  // separate face schedule: written in place
     const int r = nsk_launch_stage_d3(c->p, c->np, c->precision == NSK_FP32_MIXED, c->b, l, bt->stream);
     if (r < 0) return r;
     bt->launches += r;
+    if (stamps) {
+      const int st = launch_stamp(bt, bt->d_stamp + 1 + i, 1);
+      if (st) return st;
+    }
   }
   return NSK_OK;
 }
 
 // one stage of the whole batch under a schedule (persistent 1: one cooperative launch; 0: one
 // launch per phase; 2: every instance's own launches)
-int launch_batch(nsk_batch* bt, int mode, double A, double B, int tpb, int fused, int persistent, int traces) {
-  if (fused) traces = 0;  // the fused volume phase reads the traces: they are prolonged every stage
-  if (persistent == 2) return launch_instances(bt, mode, A, B, tpb, fused, traces);
-  return persistent ? launch_persistent(bt, mode, A, B, tpb, fused, traces)
-                    : launch_phases(bt, mode, A, B, tpb, fused, traces);
-}
-
 // trace flags of every stage of a step under the separate face schedule: traces come from the
 // previous stage's volume phase (the step starts from traces prolonged before the first step)
 int step_traces(int fused) { return fused ? 0 : 3; }
+
+// stamps: the last stage of a step whose per-instance latencies are measured (each instance's
+// completion stamped after its last kernel; one launch for all instances stamps them together)
+int launch_batch(nsk_batch* bt, int mode, double A, double B, int tpb, int fused, int persistent, int traces,
+                 bool stamps = false) {
+  if (fused) traces = 0;  // the fused volume phase reads the traces: they are prolonged every stage
+  if (persistent == 2) return launch_instances(bt, mode, A, B, tpb, fused, traces, stamps);
+  const int r = persistent ? launch_persistent(bt, mode, A, B, tpb, fused, traces)
+                           : launch_phases(bt, mode, A, B, tpb, fused, traces);
+  if (r || !stamps) return r;
+  return launch_stamp(bt, bt->d_stamp + 1, bt->n);
+}
+
+// the launches of one step: per-instance dt reductions (cfl > 0), then the five stages; with
+// stamps the step start and every instance's completion are stamped
+int launch_step(nsk_batch* bt, int dtmode, double cfl, bool stamps) {
+  if (stamps) {
+    const int st = launch_stamp(bt, bt->d_stamp, 1);
+    if (st) return st;
+  }
+  if (dtmode)
+    for (nsk_ctx* c : bt->inst) {
+      const int r = nsk_launch_dt(c->p, c->dim, c->np, c->precision == NSK_FP32_MIXED, c->b, cfl, bt->stream);
+      if (r < 0) return r;
+      bt->launches += r;
+    }
+  for (int s = 0; s < 5; ++s) {
+    const int r = launch_batch(bt, NSK_MODE_LSRK, kA[s], kB[s], bt->tpb, bt->fused, bt->persistent,
+                               step_traces(bt->fused), stamps && s == 4);
+    if (r) return r;
+  }
+  return NSK_OK;
+}
+
 
 int read_error(nsk_batch* bt) {
   int h = 0;
@@ -650,26 +706,33 @@ int nsk_batch_autotune(nsk_batch* bt, int* tpb_out, int* fused_out, int* persist
   return NSK_OK;
 }
 
-int nsk_batch_step(nsk_batch* bt, int nsteps, double cfl, double* step_ms) {
+int nsk_batch_step(nsk_batch* bt, int nsteps, double cfl, double* step_ms, double* per_instance_latency_ms) {
   if (!bt || nsteps < 0) return NSK_ERR_ARG;
   for (nsk_ctx* c : bt->inst)
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return NSK_ERR_CUDA;
   const int dtmode = cfl > 0.0 ? 1 : 0;
+  const bool stamps = per_instance_latency_ms != nullptr && nsteps > 0;
+  if (stamps) {  // stamp slots and a history of nsteps steps
+    if (!bt->d_stamp && cudaMalloc(&bt->d_stamp, sizeof(unsigned long long) * (bt->n + 1)) != cudaSuccess)
+      return NSK_ERR_NOMEM;
+    if (bt->hist_cap < nsteps) {
+      if (bt->d_hist) cudaFree(bt->d_hist);
+      bt->d_hist = nullptr;
+      bt->hist_cap = 0;
+      if (cudaMalloc(&bt->d_hist, sizeof(unsigned long long) * (bt->n + 1) * (size_t)nsteps) != cudaSuccess)
+        return NSK_ERR_NOMEM;
+      bt->hist_cap = nsteps;
+    }
+  }
   if (!bt->no_graph &&
       (!bt->graph || bt->graph_tpb != bt->tpb || bt->graph_fused != bt->fused || bt->graph_dtmode != dtmode ||
-       bt->graph_persistent != bt->persistent || (dtmode && bt->graph_cfl != cfl))) {
+       bt->graph_persistent != bt->persistent || (dtmode && bt->graph_cfl != cfl) ||
+       bt->graph_stamps != (int)stamps)) {
     destroy_graph(bt);
     cudaGraph_t g;
     if (cudaStreamBeginCapture(bt->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return NSK_ERR_CUDA;
-    int st = NSK_OK;
-    if (dtmode)
-      for (nsk_ctx* c : bt->inst) {
-        const int r = nsk_launch_dt(c->p, c->dim, c->np, c->precision == NSK_FP32_MIXED, c->b, cfl, bt->stream);
-        if (r < 0) st = r;
-      }
     const long long l0 = bt->launches;
-    for (int s = 0; s < 5 && st == NSK_OK; ++s)
-      st = launch_batch(bt, NSK_MODE_LSRK, kA[s], kB[s], bt->tpb, bt->fused, bt->persistent, step_traces(bt->fused));
+    const int st = launch_step(bt, dtmode, cfl, stamps);
     bt->graph_launches = bt->launches - l0;
     bt->launches = l0;  // counted per replay below
     const cudaError_t ce = cudaStreamEndCapture(bt->stream, &g);
@@ -688,6 +751,7 @@ int nsk_batch_step(nsk_batch* bt, int nsteps, double cfl, double* step_ms) {
     bt->graph_dtmode = dtmode;
     bt->graph_persistent = bt->persistent;
     bt->graph_cfl = cfl;
+    bt->graph_stamps = (int)stamps;
   }
   if (nsteps > 0 && !bt->fused) {  // the traces of the current states, for the first stage
     const int r = launch_prolong(bt, bt->tpb);
@@ -700,24 +764,19 @@ int nsk_batch_step(nsk_batch* bt, int nsteps, double cfl, double* step_ms) {
       if (cudaEventCreate(&e) != cudaSuccess) return NSK_ERR_CUDA;
     cudaEventRecord(ev[0], bt->stream);
   }
+  const size_t srow = (size_t)(bt->n + 1);
   for (int s = 0; s < nsteps; ++s) {
     if (bt->no_graph) {
-      if (dtmode)
-        for (nsk_ctx* c : bt->inst) {
-          const int r = nsk_launch_dt(c->p, c->dim, c->np, c->precision == NSK_FP32_MIXED, c->b, cfl, bt->stream);
-          if (r < 0) return r;
-        }
-      for (int st = 0; st < 5; ++st) {
-        const int r = launch_batch(bt, NSK_MODE_LSRK, kA[st], kB[st], bt->tpb, bt->fused, bt->persistent,
-                                   step_traces(bt->fused));
-        if (r) return r;
-      }
-      if (dtmode) bt->launches += 2 * bt->n;
+      const int r = launch_step(bt, dtmode, cfl, stamps);
+      if (r) return r;
     } else {
       if (cudaGraphLaunch(bt->graph, bt->stream) != cudaSuccess) return NSK_ERR_CUDA;
-      bt->launches += bt->graph_launches + (dtmode ? 2 * bt->n : 0);
+      bt->launches += bt->graph_launches;
     }
     if (step_ms) cudaEventRecord(ev[s + 1], bt->stream);
+    if (stamps && cudaMemcpyAsync(bt->d_hist + s * srow, bt->d_stamp, sizeof(unsigned long long) * srow,
+                                  cudaMemcpyDeviceToDevice, bt->stream) != cudaSuccess)
+      return NSK_ERR_CUDA;
   }
   int st = read_error(bt);
   if (step_ms) {
@@ -727,6 +786,15 @@ int nsk_batch_step(nsk_batch* bt, int nsteps, double cfl, double* step_ms) {
       step_ms[s] = ms;
     }
     for (auto& e : ev) cudaEventDestroy(e);
+  }
+  if (stamps && nsteps > 0) {
+    std::vector<unsigned long long> h(srow * (size_t)nsteps);
+    if (cudaMemcpy(h.data(), bt->d_hist, sizeof(unsigned long long) * h.size(), cudaMemcpyDeviceToHost) !=
+        cudaSuccess)
+      return NSK_ERR_CUDA;
+    for (int s = 0; s < nsteps; ++s)
+      for (int i = 0; i < bt->n; ++i)
+        per_instance_latency_ms[(size_t)s * bt->n + i] = 1e-6 * (double)(h[s * srow + 1 + i] - h[s * srow]);
   }
   return st;
 }
@@ -742,7 +810,7 @@ int nsk_batch_set_timeout(nsk_batch* bt, double seconds) {
   return NSK_OK;
 }
 
-int nsk_batch_poison_barrier(nsk_batch* bt) {
+int nsk_test_hook_block_batch_barrier(nsk_batch* bt) {
   if (!bt) return NSK_ERR_ARG;
   // arrivals start far above the grid size, so the next barrier can never complete and
   // every block's bounded wait expires
@@ -764,6 +832,8 @@ void nsk_batch_destroy(nsk_batch* bt) {
       if (bt->d_blk2inst[ti][ph]) cudaFree(bt->d_blk2inst[ti][ph]);
   if (bt->d_bar) cudaFree(bt->d_bar);
   if (bt->d_err) cudaFree(bt->d_err);
+  if (bt->d_stamp) cudaFree(bt->d_stamp);
+  if (bt->d_hist) cudaFree(bt->d_hist);
   if (bt->stream) cudaStreamDestroy(bt->stream);
   delete bt;
 }

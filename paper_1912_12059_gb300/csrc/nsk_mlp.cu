@@ -2,6 +2,19 @@
 // GEMM exposed through the C ABI (nsk_gemm_bf16) for testing and reuse.
 #include "nsk_kernels.cuh"
 #include "nsk_tc.cuh"
+#include "nsk_test_hooks.h"
+
+namespace nsk {
+namespace tc {
+int g_grid_cap = 0;
+}  // namespace tc
+}  // namespace nsk
+
+extern "C" int nsk_test_hook_tc_grid_cap(int max_ctas) {
+  if (max_ctas < 0) return NSK_ERR_ARG;
+  nsk::tc::g_grid_cap = max_ctas;
+  return NSK_OK;
+}
 
 namespace {
 __device__ int g_gemm_err;  // error word of calls that pass none

@@ -27,6 +27,16 @@ constexpr int kMaxN = 256;    // TMEM columns allocated
 constexpr int kThreads = 128;
 constexpr unsigned long long kWaitNs = 1000000000ull;  // bound of every mbarrier wait
 
+// Upper bound on the grid of the persistent kernels (k_gemm_tc_rb, k_mlp_fwd3), 0 = none (one CTA
+// per SM, or fewer when there are fewer row tiles). Set only by the test hook
+// nsk_test_hook_tc_grid_cap, so that small problems run several row tiles per CTA.
+extern int g_grid_cap;
+inline unsigned persistent_grid(int ntiles, int sms) {
+  int g = ntiles < sms ? ntiles : sms;
+  if (g_grid_cap > 0 && g > g_grid_cap) g = g_grid_cap;
+  return (unsigned)g;
+}
+
 enum Epilogue : int {
   EPI_STORE = 0,   // C (+ bias) -> FP32 out
   EPI_ATOMIC = 1,  // atomicAdd(out, C): split-K partial sums
@@ -742,7 +752,7 @@ inline int launch_mlp_fwd3(const MlpFwdArgs& a, cudaStream_t s) {
     attr_done = true;
   }
   const int ntiles = (a.M + kBM - 1) / kBM;
-  k_mlp_fwd3<<<(unsigned)(ntiles < sms ? ntiles : sms), kFwThreads, smem, s>>>(a);
+  k_mlp_fwd3<<<persistent_grid(ntiles, sms), kFwThreads, smem, s>>>(a);
   return cudaGetLastError() == cudaSuccess ? NSK_OK : NSK_ERR_CUDA;
 }
 
@@ -775,7 +785,7 @@ inline int launch_gemm(const GemmArgs& a, cudaStream_t s) {
     smem = smem < kRbSmemMin ? kRbSmemMin : smem;
     const int ntiles = (a.M + kBM - 1) / kBM;
     if (smem > kRbSmemMax) return NSK_ERR_ARG;
-    k_gemm_tc_rb<<<(unsigned)(ntiles < sms ? ntiles : sms), kRbThreads, smem, s>>>(a);
+    k_gemm_tc_rb<<<persistent_grid(ntiles, sms), kRbThreads, smem, s>>>(a);
   } else {
     dim3 grid((unsigned)((a.M + kBM - 1) / kBM), (unsigned)((a.K + a.k_split - 1) / a.k_split));
     k_gemm_tc<<<grid, kThreads, kSmemBytes, s>>>(a);

@@ -72,14 +72,16 @@ SIGNATURES = {
     "nsk_get_schedule": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "nsk_autotune": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), _dp]),
     "nsk_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_void_p)]),
-    "nsk_batch_step": (C.c_int, [C.c_void_p, C.c_int, C.c_double, _dp]),
+    "nsk_measure_fma_rate": (C.c_int, [C.c_int, C.c_int, _dp, _dp, C.c_void_p]),
+    "nsk_batch_step": (C.c_int, [C.c_void_p, C.c_int, C.c_double, _dp, _dp]),
     "nsk_batch_set_schedule": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int]),
     "nsk_batch_get_schedule": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "nsk_batch_autotune": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int), _dp]),
     "nsk_batch_launch_count": (C.c_longlong, [C.c_void_p]),
     "nsk_batch_uses_graph": (C.c_int, [C.c_void_p]),
     "nsk_batch_set_timeout": (C.c_int, [C.c_void_p, C.c_double]),
-    "nsk_batch_poison_barrier": (C.c_int, [C.c_void_p]),
+    "nsk_test_hook_block_batch_barrier": (C.c_int, [C.c_void_p]),
+    "nsk_test_hook_tc_grid_cap": (C.c_int, [C.c_int]),
     "nsk_batch_destroy": (None, [C.c_void_p]),
     "nsk_gemm_bf16": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                 C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_int,
@@ -191,6 +193,19 @@ def nsk_rhs_static_scratch(dim, nelem, lo, hi, N, node_type, T, kappa, alpha, be
     return load_library().nsk_rhs_static_scratch(dim, ne, clo, chi, N, node_type, T, kappa, alpha, beta, mu,
                                                  C.c_void_p(U.data_ptr()), C.c_void_p(Ut.data_ptr()),
                                                  C.c_void_p(stream) if stream else None)
+
+
+def _test_hook_tc_grid_cap(max_ctas):
+    """Test-only (include/nsk_test_hooks.h): cap the persistent tensor-core grids (0: no cap)."""
+    _check(load_library().nsk_test_hook_tc_grid_cap(int(max_ctas)), "nsk_test_hook_tc_grid_cap")
+
+
+def measure_fma_rate(precision=NSK_FP64, iters=1 << 16, stream=None):
+    """Measured FMA throughput of the current device, (TFLOP/s, ms of the timed launch)."""
+    tf, ms = C.c_double(), C.c_double()
+    _check(load_library().nsk_measure_fma_rate(int(precision), int(iters), C.byref(tf), C.byref(ms),
+                                               C.c_void_p(stream) if stream else None), "nsk_measure_fma_rate")
+    return tf.value, ms.value
 
 
 def nsk_destroy(ctx):
@@ -414,17 +429,25 @@ class Batch:
 
     def __init__(self, solvers):
         self.solvers = list(solvers)  # keep the contexts alive
+        self.n = len(self.solvers)
         arr = (C.c_void_p * len(self.solvers))(*[s.ctx.value for s in self.solvers])
         h = C.c_void_p()
         _check(load_library().nsk_batch_create(C.byref(h), len(self.solvers), arr), "nsk_batch_create")
         self.h = h
 
-    def step(self, nsteps=1, cfl=0.0, timings=False):
+    def step(self, nsteps=1, cfl=0.0, timings=False, latencies=False):
         """Advance all instances; cfl > 0 recomputes each instance's dt every step.
-        With timings=True returns the per-step wall times in ms."""
+        With timings=True returns the per-step wall times in ms; with latencies=True (also)
+        the per-instance step latencies, an array [nsteps][instances] in ms (time from the
+        step's start until that instance's new state is complete)."""
         ms = (C.c_double * max(nsteps, 1))() if timings else None
-        _check(load_library().nsk_batch_step(self.h, nsteps, cfl, ms), "nsk_batch_step")
-        return list(ms)[:nsteps] if timings else None
+        lat = (C.c_double * max(nsteps * self.n, 1))() if latencies else None
+        _check(load_library().nsk_batch_step(self.h, nsteps, cfl, ms, lat), "nsk_batch_step")
+        out_ms = list(ms)[:nsteps] if timings else None
+        if not latencies:
+            return out_ms
+        L = np.frombuffer(lat, dtype=np.float64, count=nsteps * self.n).reshape(nsteps, self.n).copy()
+        return (out_ms, L) if timings else L
 
     #: values of the `persistent` schedule argument
     PHASES, PERSISTENT, INSTANCES = 0, 1, 2
@@ -451,8 +474,9 @@ class Batch:
     def set_timeout(self, seconds):
         _check(load_library().nsk_batch_set_timeout(self.h, seconds), "nsk_batch_set_timeout")
 
-    def poison_barrier(self):
-        _check(load_library().nsk_batch_poison_barrier(self.h), "nsk_batch_poison_barrier")
+    def _test_hook_block_barrier(self):
+        """Test-only (include/nsk_test_hooks.h): make the next grid barrier unreachable."""
+        _check(load_library().nsk_test_hook_block_batch_barrier(self.h), "nsk_test_hook_block_batch_barrier")
 
     @property
     def uses_graph(self):

@@ -126,6 +126,39 @@ def test_batch_equals_solo_runs(gpu, precision, adaptive):
         s.close()
 
 
+
+@pytest.mark.parametrize("persistent", [0, 1, 2])
+def test_batch_per_instance_latency(gpu, persistent):
+    """Per-instance step latencies (nsk_batch_step's per_instance_latency_ms): one value per step
+    and instance, positive and within the step's wall time; the instance schedule finishes the
+    instances one after another (non-decreasing in instance order), a single launch finishes all
+    of them together. The stamps do not change the results: the states equal those of a run
+    without them, bit for bit."""
+    inst = _instances(nsk.NSK_FP32_MIXED)
+    for s, U in inst:
+        s.set_state(U)
+        s.compute_dt(0.5)
+    b = nsk.Batch([s for s, _ in inst])
+    b.set_schedule(256, False, persistent)
+    b.step(2)
+    plain = [s.get_state() for s, _ in inst]
+    for s, U in inst:
+        s.set_state(U)
+        s.compute_dt(0.5)
+    ms, lat = b.step(2, timings=True, latencies=True)
+    assert lat.shape == (2, len(inst))
+    for (s, _), want in zip(inst, plain):
+        assert np.array_equal(s.get_state(), want)
+    for k in range(2):
+        assert (lat[k] > 0).all() and (lat[k] <= ms[k] * 1.001 + 1e-3).all(), (lat[k], ms[k])
+        if persistent == 2:
+            assert (np.diff(lat[k]) >= 0).all(), lat[k]
+        else:
+            assert lat[k].max() - lat[k].min() <= 0.05 * lat[k].max() + 5e-3, lat[k]
+    b.close()
+    for s, _ in inst:
+        s.close()
+
 def test_batch_autotune_graph_and_launch_count(gpu):
     inst = _instances(nsk.NSK_FP32_MIXED)
     for s, U in inst:
@@ -163,7 +196,7 @@ def test_batch_barrier_wait_is_bounded(gpu):
     b = nsk.Batch([s for s, _ in inst])
     b.set_schedule(256, False, True)
     b.set_timeout(0.05)
-    b.poison_barrier()
+    b._test_hook_block_barrier()
     t0 = time.perf_counter()
     with pytest.raises(nsk.NskError) as ei:
         b.step(1)
