@@ -35,13 +35,41 @@ ROOT = Path(__file__).resolve().parent
 sys.path.insert(0, str(ROOT))
 
 MEASURED_PEAKS = ROOT / "MEASURED_PEAKS.json"
-# FP64 FMA pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (max SM clock)
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
-# DRAM bytes (read + write) per launch of the dominant kernels at 64^3 elements, N = 3, from one
-# ncu capture at 40^3 elements scaled by the element count (profiles/launches_fp64_collision3d_64cubed.md,
-# profiles/fp32_stage_kernels_collision3d.md); must be re-measured whenever those kernels change
-MEASURED_TRAFFIC = {("k_volume", 8, 262144): 5.99e9, ("k_volume", 4, 262144): 2.70e9}
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# FP64 and FP32 FMAs per SM and clock. GB300's nominal FP64 rate, 1.25 TFLOP/s, over 152 SMs x
+# 2 flops x 2.07 GHz is 1.99: 2 DFMA per SM and clock; FP32: 128 FFMA per SM and clock. The
+# nsk_measure_fma_rate probe measures both in every run (reported beside the derived peaks).
+DFMA_PER_SM_CLK = 2
+FFMA_PER_SM_CLK = 128
+# Algorithmic (compulsory) bytes per node and stage: U and K read and written once, nvar values
+# of 8 (FP64) or 4 (FP32) bytes each.
+def compulsory_bytes(d, fp_bytes):
+    return 4 * (d + 2) * fp_bytes
+
+
+# DRAM bytes (read + write) per launch of a kernel at 64^3 elements, N = 3, from one ncu capture
+# at 40^3 elements of the same kernel source, scaled by the element count; None once the kernel
+# changed after the capture (then no traffic is claimed).
+MEASURED_TRAFFIC = {("k_volume", 8, 262144): 5.577e9, ("k_volume", 4, 262144): 2.484e9}
+TRAFFIC_SOURCE = "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch at 40^3 elements, scaled to 64^3"
+
+
+def alu_peak_tflops(sms, sm_mhz, fp64=True):
+    """Peak FMA throughput: SMs x FMAs per SM and clock x 2 flops x SM clock (MHz)."""
+    return sms * (DFMA_PER_SM_CLK if fp64 else FFMA_PER_SM_CLK) * 2 * sm_mhz * 1e6 / 1e12
+
+
+def host_info():
+    """Cores and CPU model of the host the oracle runs on."""
+    model = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return {"nproc": os.cpu_count(), "cpu_model": model}
 
 
 def workload_by_name(name):
@@ -57,25 +85,41 @@ def workload_by_name(name):
 
 
 # ---------------------------------------------------------------- algorithmic cost model
-def kernel_cost(kernel, d, n, fp_bytes, traces=0.0):
+def kernel_cost(kernel, d, n, fp_bytes, traces=0.0, sched=0):
     """Algorithmic (flops, bytes) per element of one stage kernel, counted from the kernel
     source: FMA = 2 flops, add/mul/div/sqrt = 1 (negations, compares and min/max are free);
     bytes = compulsory loads + stores. `traces`: fraction of the k_volume launches that also
     wrote the face traces of their output state (the next stage's prolongation: its flops and
     trace stores). FP64 traces carry 1/rho and 1/(3 - rho) (one division per trace node);
-    FP32 kernels divide where FP64 reads those planes."""
+    FP32 kernels divide where FP64 reads those planes. sched = 2: the lean stage's kernels
+    (k_lift: the lifting from the element's state, its own traces prolonged on chip, and the
+    neighbours' state traces, storing only the viscous-flux traces; k_volume: that lifting again,
+    the element's 2d face fluxes and the volume kernel, reading the state, the RK register and
+    the neighbours' state and viscous-flux traces)."""
     npe, nfn, nv, nw, nf = n**d, n ** (d - 1), d + 2, d + 1, 2 * d
+    if sched == 2 and kernel in ("k_lift", "k_volume"):
+        xp = 2 if fp_bytes == 8 else 0
+        prolong_own = kernel_cost("k_prolong", d, n, fp_bytes)[0]       # own traces on chip
+        fl_lift = kernel_cost("k_lift", d, n, fp_bytes)[0] + prolong_own
+        nbr = nf * nfn * (nv + xp)                                         # the neighbours' state traces
+        if kernel == "k_lift":
+            return fl_lift, fp_bytes * (nv * npe + nbr + nf * nfn * nw)
+        fl_face = 2 * kernel_cost("k_face", d, n, fp_bytes)[0]            # each face by both elements
+        fl_vol, _ = kernel_cost("k_volume", d, n, fp_bytes, traces=traces)  # its stress is the lifting's
+        by = fp_bytes * (4 * nv * npe + nbr + nf * nfn * nw + traces * nf * nfn * (nv + xp))
+        return fl_lift + fl_face + fl_vol, by
     fp64 = fp_bytes == 8
     trace_extra = 5 if fp64 else 0            # 3 - rho, rho (3 - rho), 1/x, two products
     stress = (d - 1) + d * (d - 1) // 2 + 3 * d  # div v, off-diagonal sums, diagonal sum + fma
     xp = 2 if fp64 else 0                     # FP64 trace planes 1/rho, 1/(3 - rho)
     if kernel == "k_prolong":
         return nf * nfn * (nv * 2 * n + trace_extra), fp_bytes * (nv * npe + nf * nfn * (nv + xp))
+    nvf = d * (d + 1) // 2 + d                # viscous form: stress / mu and grad c
     if kernel == "k_lift":
         per_node = (d + 1) + d * nw * (2 * n + 4) + stress          # w = (m / rho, c); grad w; tau
         per_face = (3 * d + 1) + (0 if fp64 else 2)                  # 2 w* (and two reciprocals)
         fl = npe * per_node + nf * nfn * per_face + nf * nfn * nw * 2 * n
-        by = fp_bytes * (nv * npe + 2 * nf * nfn * (nv + xp // 2) + d * nw * npe + nf * nfn * nw)  # + 1/rho
+        by = fp_bytes * (nv * npe + 2 * nf * nfn * (nv + xp // 2) + nvf * npe + nf * nfn * nw)  # + 1/rho
         return fl, by
     if kernel == "k_face":
         eos = 18 if fp64 else 30                                     # both sides (FP32: + 1/rho)
@@ -84,8 +128,8 @@ def kernel_cost(kernel, d, n, fp_bytes, traces=0.0):
     if kernel == "k_volume":
         eos = 10 if fp64 else 8
         flux = d + 2 * d + d * (d - 1) + 2 * d * d                   # v_a, F^c, F^c - mu tau
-        per_node = eos + stress + flux + nv * d * (2 * n + 4) + 2 + (2 * d + 4) + 4 * nv
-        by = fp_bytes * (nv * npe + d * nw * npe + 2 * d * nfn * nv + 2 * nv * npe + nv * npe)
+        per_node = eos + flux + nv * d * (2 * n + 4) + 2 + (2 * d + 4) + 4 * nv  # stress read, not formed
+        by = fp_bytes * (nv * npe + nvf * npe + 2 * d * nfn * nv + 2 * nv * npe + nv * npe)
         return (npe * per_node + traces * nf * nfn * (nv * 2 * n + trace_extra),
                 by + traces * fp_bytes * nf * nfn * (nv + xp))
     raise KeyError(kernel)
@@ -96,11 +140,12 @@ BATCH_KINDS = {0: "one launch per phase", 1: "persistent cooperative", 2: "insta
 
 def pick_schedule(s, fixed):
     """The autotuner's stage schedule, or a fixed "TPB,FUSED" one (profiling runs: under a
-    profiler the autotuner's timings are serialised and would pick another schedule)."""
+    profiler the autotuner's timings are serialised and would pick another schedule); FUSED is
+    0 (separate face pass), 1 (face fluxes in the volume kernel) or 2 (the lean stage)."""
     if fixed:
         tpb, fused = (int(v) for v in fixed.split(","))
-        s.set_schedule(tpb, bool(fused))
-        return tpb, bool(fused)
+        s.set_schedule(tpb, fused)
+        return tpb, fused
     tpb, fused, _ = s.autotune()
     return tpb, fused
 
@@ -174,17 +219,16 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- CPU oracle baseline
-def oracle_sample(wl, target_s=15.0):
-    """Time the FP64 CPU oracle (single thread, as it stands) on a bounded sample of the
-    workload: the same N, parameters and initial-condition recipe on a smaller periodic mesh
-    (element size unchanged in the sampled directions is not needed: the oracle's cost per node
-    does not depend on the mesh spacing). Returns (DOF-updates/s, description)."""
+def oracle_sample(wl, target_s=15.0, parallel=False, ne=None):
+    """Time the FP64 CPU oracle as it stands (plain build on one thread, or parallel=True: the
+    OpenMP build of the same source on all host cores) on a bounded sample of the workload: the
+    same N, parameters and initial-condition recipe on a smaller periodic mesh (the oracle's cost
+    per node does not depend on the mesh spacing). Returns (DOF-updates/s, description, threads)."""
     import oracle as O
-    from paper_1912_12059_gb300 import inputs
 
-    ne = {3: (8, 8, 8), 2: (32, 32), 1: (64,)}[wl.dim]
+    ne = ne or {3: (8, 8, 8), 2: (32, 32), 1: (64,)}[wl.dim]
     o = O.Oracle(wl.dim, ne, [0.0] * wl.dim, [1.0] * wl.dim, wl.N, wl.node_type, T=wl.T, kappa=wl.kappa,
-                 alpha=wl.alpha, beta=wl.beta, mu=wl.mu)
+                 alpha=wl.alpha, beta=wl.beta, mu=wl.mu, parallel=parallel)
     U = wl.initial_state(o.coords())
     dt = o.timestep(U, wl.cfl)
     t0 = time.perf_counter()
@@ -197,29 +241,68 @@ def oracle_sample(wl, target_s=15.0):
             break
     nodes = o.E * o.npe
     rate = nodes * 5 * steps / el
-    return rate, f"{steps} LSRK4 steps of the oracle on a {'x'.join(map(str, ne))}-element periodic box " \
-                 f"(N={wl.N}, {nodes} nodes, same parameters and initial-condition recipe), {el:.1f} s"
+    threads = O.threads(parallel)
+    return rate, f"{steps} LSRK4 steps of the oracle ({'OpenMP build, ' if parallel else 'plain build, '}" \
+                 f"{threads} thread{'s' if threads > 1 else ''}) on a {'x'.join(map(str, ne))}-element periodic " \
+                 f"box (N={wl.N}, {nodes} nodes, same parameters and initial-condition recipe), {el:.1f} s", threads
+
+
+def cpu_baselines(wl, seconds):
+    """The oracle on the host: all cores (OpenMP build) and one core (plain build), with the host's
+    core count and CPU model."""
+    rate_p, desc_p, thr = oracle_sample(wl, target_s=seconds, parallel=True,
+                                        ne={3: (16, 16, 16), 2: (64, 64), 1: (64,)}[wl.dim])
+    rate_1, desc_1, _ = oracle_sample(wl, target_s=seconds)
+    return {"value": rate_p, "unit": "DOF-updates/s", "cores": thr, "kind": "oracle", "sample": desc_p,
+            "host": host_info(),
+            "single_core": {"value": rate_1, "unit": "DOF-updates/s", "cores": 1, "kind": "oracle",
+                            "sample": desc_1}}
+
+
+# the reference arm runs the workload's own mesh up to this many nodes, else this sample of it
+REFERENCE_FULL_MAX_NODES = 1 << 22
+REFERENCE_SAMPLE_NELEM = {3: (32, 32, 32), 2: (128, 128), 1: (64,)}
 
 
 def run_reference(args, wl, rank, world):
-    """--impl reference: the FP64 CPU oracle, timed on the host cores; rank 0 only."""
+    """--impl reference: the FP64 CPU oracle (OpenMP build of the plain source, all host cores),
+    rank 0 only. Every step is one LSRK4 step of the oracle on the workload's own mesh when it
+    holds at most 2^22 nodes, else on a bounded sample of it (the same N, parameters and
+    initial-condition recipe on the periodic box REFERENCE_SAMPLE_NELEM); each step is
+    timed, ms_per_step is the measured mean and value the sample's DOF-updates/s."""
     if rank != 0:
         return 0
-    rates = []
+    import oracle as O
+
+    full = wl.dofs <= REFERENCE_FULL_MAX_NODES
+    ne = tuple(wl.nelem) if full else REFERENCE_SAMPLE_NELEM[wl.dim]
+    o = O.Oracle(wl.dim, ne, [0.0] * wl.dim, [1.0] * wl.dim, wl.N, wl.node_type, T=wl.T, kappa=wl.kappa,
+                 alpha=wl.alpha, beta=wl.beta, mu=wl.mu, parallel=True)
+    U = wl.initial_state(o.coords())
+    dt = o.timestep(U, wl.cfl)
     for _ in range(args.warmup):
-        oracle_sample(wl, target_s=2.0)
-    desc = ""
+        U = o.step(U, dt, 1)
+    times = []
     for _ in range(args.steps):
-        r, desc = oracle_sample(wl, target_s=max(2.0, 40.0 / max(args.steps, 1)))
-        rates.append(r)
-    value = statistics.median(rates)
-    ms_per_step = wl.dofs * 5 / value * 1e3
+        t0 = time.perf_counter()
+        U = o.step(U, dt, 1)
+        times.append(time.perf_counter() - t0)
+    nodes = o.E * o.npe
+    ms_per_step = 1e3 * sum(times) / max(len(times), 1)
+    value = nodes * 5 / (ms_per_step / 1e3)
+    threads = O.threads(True)
+    sample = (f"every step one LSRK4 step of the oracle (OpenMP build, {threads} threads) on "
+              + ("the workload's own mesh" if full else
+                 f"a {'x'.join(map(str, ne))}-element periodic box of the workload (same N = {wl.N}, parameters "
+                 f"and initial-condition recipe; {nodes} of the workload's {wl.dofs} nodes)"))
     line = {
         "impl": "reference", "metric": "DOF-updates/s", "value": value, "unit": "DOF-updates/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": wl.name, "dofs": wl.dofs, "N": wl.N, "nelem": list(wl.nelem)},
-        "cpu_baseline": {"value": value, "unit": "DOF-updates/s", "cores": 1, "kind": "oracle", "sample": desc},
+        "config": {"workload": wl.name, "dofs_per_gpu": wl.dofs, "N": wl.N, "nelem": list(wl.nelem)},
+        "sample": {"nelem": list(ne), "nodes": nodes, "full_workload": full},
+        "cpu_baseline": {"value": value, "unit": "DOF-updates/s", "cores": threads, "kind": "oracle",
+                         "sample": sample, "host": host_info()},
         "e2e": {"value": value, "unit": "DOF-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -267,6 +350,12 @@ def run_gpu(args, wl, rank, world):
     tpb, fused = pick_schedule(s, args.schedule)  # setup: the fastest stage schedule for this mesh
     dt = s.compute_dt(wl.cfl)
     nodes = s.E * s.npe
+    # FMA throughput of this GPU, measured with its clocks sampled (cross-check of the derived
+    # FP64 peak of the roofline)
+    with ClockSampler(local) as pclk:
+        probe64, _ = nsk.measure_fma_rate(nsk.NSK_FP64, iters=1 << 17)
+        probe64 = max(probe64, nsk.measure_fma_rate(nsk.NSK_FP64, iters=1 << 17)[0])
+    probe_clk = pclk.summary()["sm_mhz"]
 
     def barrier():
         if world > 1:
@@ -318,21 +407,33 @@ def run_gpu(args, wl, rank, world):
     fp_bytes = 8 if prec == nsk.NSK_FP64 else 4
     name, (kms, kcnt) = max(prof.items(), key=lambda kv: kv[1][0])
     avg_ms = kms / max(kcnt, 1)
-    flops_e, bytes_e = kernel_cost(name, wl.dim, wl.N + 1, fp_bytes, traces=trace_fraction(prof))
+    flops_e, bytes_e = kernel_cost(name, wl.dim, wl.N + 1, fp_bytes, traces=trace_fraction(prof), sched=fused)
     peaks = json.loads(MEASURED_PEAKS.read_text()) if MEASURED_PEAKS.exists() else {}
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    hbm_src = "measured (STREAM-style copy)" if "hbm_gbs" in peaks else "fallback"
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    max_mhz = clocks["sm_max_mhz"] or float(peaks.get("sm_max_mhz", 2070.0))
+    traffic = MEASURED_TRAFFIC.get((name, fp_bytes, s.E))
     if prec == nsk.NSK_FP64:
+        peak = alu_peak_tflops(sms, max_mhz, fp64=True)
         achieved = flops_e * s.E / (avg_ms / 1e3) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": MEASURED_TRAFFIC.get((name, 8, s.E)), "kernel": name,
-                "peak_source": "FP64 FMA pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
-                "algorithmic_per_launch": flops_e * s.E}
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": traffic, "kernel": name,
+                "peak_source": f"derived: {sms} SMs x {DFMA_PER_SM_CLK} DFMA/clk x 2 flop x {max_mhz:.0f} MHz "
+                               "(max SM clock); the probe measured in this run is probe_fp64_tflops",
+                "probe_fp64_tflops": probe64, "probe_sm_mhz_median": probe_clk,
+                "algorithmic_per_launch": flops_e * s.E, "unit_count": "counted flops of the kernel source per element"}
     else:
-        hbm = float(peaks.get("hbm_gbs", 6800.0))
         achieved = bytes_e * s.E / (avg_ms / 1e3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": MEASURED_TRAFFIC.get((name, 4, s.E)), "kernel": name,
-                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+                "traffic": traffic, "kernel": name, "peak_source": hbm_src,
                 "algorithmic_per_launch": bytes_e * s.E}
+    roof["traffic_source"] = TRAFFIC_SOURCE if traffic is not None else None
+    # the whole step against HBM on the compulsory bytes (U and K read and written once per stage)
+    step_bytes = compulsory_bytes(wl.dim, fp_bytes) * total_nodes * 5 * args.steps
+    roof_step = {"bound": "hbm", "bytes_per_node_stage": compulsory_bytes(wl.dim, fp_bytes),
+                 "achieved": step_bytes / (t_max / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                 "frac": step_bytes / (t_max / 1e3) / 1e9 / hbm, "peak_source": hbm_src}
     kernels = {k: {"avg_ms": v[0] / max(v[1], 1), "launches": v[1],
                    "share": v[0] / max(sum(x[0] for x in prof.values()), 1e-30)} for k, v in prof.items()}
     s.close()
@@ -341,6 +442,10 @@ def run_gpu(args, wl, rank, world):
         variants["fp32_mixed"] = measure_fp32_variant(args, wl, stream, U0, U_after, dt, peaks)
         variants["fp64_hllc"] = measure_hllc_variant(args, wl, stream, U0, U_after, dt)
         variants["fp64_original_nsk"] = measure_nsk_variant(args, wl, stream, U0, dt)
+        variants["interface1d"] = measure_interface1d_variant(args, stream)
+        variants["coalescence2d"] = measure_coalescence2d_variant(args, stream, peaks)
+        variants["batch32"] = measure_batch_variant(args)
+        variants["closure96"] = measure_closure_variant(args)
         variants["riemann1d_subcell"] = measure_subcell_variant(args, stream)
         variants["esdirk4_implicit"] = measure_esdirk_variant(args, stream)
 
@@ -348,8 +453,7 @@ def run_gpu(args, wl, rank, world):
         return 0
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        rate, desc = oracle_sample(wl, target_s=args.cpu_seconds)
-        cpu = {"value": rate, "unit": "DOF-updates/s", "cores": 1, "kind": "oracle", "sample": desc}
+        cpu = cpu_baselines(wl, args.cpu_seconds)
     line = {
         "metric": "DOF-updates/s", "value": value, "unit": "DOF-updates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
@@ -363,6 +467,7 @@ def run_gpu(args, wl, rank, world):
                 "d2h_bytes_per_step": nbytes, "steps": e2e_steps},
         "gpu_launches": launches,
         "roofline": roof,
+        "roofline_step_hbm": roof_step,
         "kernels": kernels,
         "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"], "reasons": clocks["reasons"]},
         "cpu_baseline": cpu,
@@ -373,68 +478,27 @@ def run_gpu(args, wl, rank, world):
 
 
 def run_batch(args, rank, world):
-    """32 uneven 3D collision instances (16^3..48^3 elements, N in {3,4}) advanced together by the
-    persistent batched kernel (CUDA-graph replay of the five stage launches)."""
+    """32 uneven 3D collision instances (16^3..48^3 elements, N in {3,4}) advanced together
+    (CUDA-graph replay of the five stage launches under the autotuned batch schedule)."""
     import torch
 
-    from paper_1912_12059_gb300 import inputs, nsk
+    from paper_1912_12059_gb300 import nsk
     from paper_1912_12059_gb300.build import build_library
 
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     build_library()
-    prec = nsk.NSK_FP32_MIXED if args.precision != "fp64" else nsk.NSK_FP64
-    wls = inputs.serving_batch_3d(args.batch, seed=inputs.SEED + rank)
-    solvers = []
-    for wl in wls:
-        s = nsk.Solver(3, wl.nelem, wl.N, [0, 0, 0], [1, 1, 1], 0, prec)
-        s.set_params(T=wl.T, kappa=wl.kappa, alpha=wl.alpha, beta=wl.beta, mu=wl.mu)
-        s.set_state(wl.initial_state(s.node_coords()))
-        s.compute_dt(wl.cfl)
-        solvers.append(s)
-    nodes = sum(s.E * s.npe for s in solvers)
-    b = nsk.Batch(solvers)
-    tpb, fused, persistent, _ = b.autotune()
-    b.step(args.warmup)
-    n0 = b.launch_count
     with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
-        torch.cuda.synchronize()
-        step_ms = b.step(args.steps, timings=True)
-        torch.cuda.synchronize()
-    launches = b.launch_count - n0
+        v = measure_batch_variant(args, n=args.batch)
     clocks = clk.summary()
-    total_ms = sum(step_ms)
-    value = nodes * 5 * args.steps / (total_ms / 1e3)
-    # the same instances stepped one after another (no batching) for comparison
-    seq_ms = 0.0
-    for s in solvers:
-        s.set_schedule(tpb, fused)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        e0.record()
-        s.step(s.compute_dt(0.5), 2)
-        e1.record()
-        torch.cuda.synchronize()
-        seq_ms += e0.elapsed_time(e1) / 2
-    b.close()
-    for s in solvers:
-        s.close()
-    small = batch_vs_sequential_small(nsk, prec)
+    small = batch_vs_sequential_small(nsk, nsk.NSK_FP32_MIXED)
     if rank != 0:
         return 0
-    sm = sorted(step_ms)
     line = {
-        "metric": "DOF-updates/s", "value": value, "unit": "DOF-updates/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32" if prec == nsk.NSK_FP32_MIXED else "f64", "data": "synthetic",
-        "config": {"workload": f"batched_{args.batch}x_collision3d_E16-48_N3-4", "instances": args.batch,
-                   "nodes_total": nodes, "schedule": {"tpb": tpb, "fused_face": fused, "kind": BATCH_KINDS[persistent]},
-                   "cuda_graph": True,
-                   "step_latency_ms_p50": sm[len(sm) // 2], "step_latency_ms_p99": sm[min(len(sm) - 1,
-                                                                                         int(0.99 * len(sm)))],
-                   "sequential_value": nodes * 5 / (seq_ms / 1e3),
-                   "small_instances": small,
-                   "l2": "state larger than L2"},
-        "gpu_launches": launches,
+        "metric": "DOF-updates/s", "value": v["value"], "unit": "DOF-updates/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": v["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": dict(v, small_instances=small, l2="state larger than L2"),
+        "gpu_launches": v["gpu_launches"],
         "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"], "reasons": clocks["reasons"]},
         "e2e": None, "roofline": None, "cpu_baseline": None,
     }
@@ -694,6 +758,155 @@ def measure_hllc_variant(args, wl, stream, U0, U_lf_after, dt):
             "kernels": {k: {"avg_ms": v[0] / max(v[1], 1), "launches": v[1]} for k, v in prof.items()}}
 
 
+def _timed_steps(s, stream, dt, n):
+    """Wall ms of n steps of a solver, CUDA events on its stream."""
+    import torch
+
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    s.step(dt, n)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def measure_interface1d_variant(args, stream):
+    """The 1D static phase interface (64 elements, N = 3; kappa 1e-4, alpha 1e3, beta 1e-3,
+    mu 1e-3) at CFL 0.5: on Gauss-Legendre nodes (the paper's) its full 2000 LSRK4 steps; on
+    Gauss-Lobatto nodes, as the workload names them, 800 steps: the collocated Lobatto scheme
+    goes non-physical near t = 2e-3 (about 900 steps) on this interface, in the oracle as on the
+    GPU and at any step size. Wall time and rate, and the oracle's time for the same run on one
+    host core (the CPU baseline of this workload)."""
+    import dataclasses
+
+    from paper_1912_12059_gb300 import inputs, nsk
+
+    out = {}
+    for nt, tag, steps in ((0, "gauss_legendre", 2000), (1, "gauss_lobatto", 800)):
+        wl = dataclasses.replace(inputs.static_interface_1d(node_type=nt), steps=steps)
+        s = nsk.Solver(1, wl.nelem, wl.N, [0.0], [1.0], nt, nsk.NSK_FP64, stream=stream.cuda_stream)
+        s.set_params(T=wl.T, kappa=wl.kappa, alpha=wl.alpha, beta=wl.beta, mu=wl.mu)
+        U0 = wl.initial_state(s.node_coords())
+        s.set_state(U0)
+        dt = s.compute_dt(wl.cfl)
+        s.step(dt, 3)
+        s.set_state(U0)
+        ms = _timed_steps(s, stream, dt, wl.steps)
+        m0 = s.diagnostics()[0]
+        s.close()
+        out[tag] = {"workload": wl.name + ("" if nt == 1 else "_GL"), "steps": wl.steps, "dt": dt, "wall_ms": ms,
+                    "ms_per_step": ms / wl.steps, "value": wl.dofs * 5 * wl.steps / (ms / 1e3),
+                    "unit": "DOF-updates/s", "dtype": "f64", "mass": m0}
+        if not args.no_cpu_baseline:
+            import oracle as O
+
+            o = O.Oracle(1, wl.nelem, [0.0], [1.0], wl.N, nt, T=wl.T, kappa=wl.kappa, alpha=wl.alpha,
+                         beta=wl.beta, mu=wl.mu)
+            t0 = time.perf_counter()
+            o.step(U0, dt, wl.steps)
+            el = time.perf_counter() - t0
+            out[tag]["cpu_baseline"] = {"value": wl.dofs * 5 * wl.steps / el, "unit": "DOF-updates/s", "cores": 1,
+                                        "kind": "oracle", "sample": f"the full {wl.steps}-step run, {el:.2f} s"}
+    return out
+
+
+def measure_coalescence2d_variant(args, stream, peaks):
+    """2D coalescence of two droplets (128^2 elements, N = 4, radii 0.15 / 0.12, +-1e-4 noise) at
+    alpha = 1e2, 1e3, 1e4: FP64 rate over 200 steps at the CFL-0.5 step of each, against HBM on
+    the compulsory 128 B per node and stage; the oracle (OpenMP build, all host cores) on a
+    bounded sample of the alpha = 1e3 case as the CPU baseline."""
+    from paper_1912_12059_gb300 import inputs, nsk
+
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    out = {}
+    steps = 200
+    for alpha in (1e2, 1e3, 1e4):
+        wl = inputs.coalescence_2d(alpha=alpha)
+        s = nsk.Solver(2, wl.nelem, wl.N, [0.0, 0.0], [1.0, 1.0], 0, nsk.NSK_FP64, stream=stream.cuda_stream)
+        s.set_params(T=wl.T, kappa=wl.kappa, alpha=wl.alpha, beta=wl.beta, mu=wl.mu)
+        U0 = wl.initial_state(s.node_coords())
+        s.set_state(U0)
+        tpb, fused = pick_schedule(s, args.schedule)
+        dt = s.compute_dt(wl.cfl)
+        s.step(dt, 3)
+        ms = _timed_steps(s, stream, dt, steps)
+        gbs = compulsory_bytes(2, 8) * wl.dofs * 5 * steps / (ms / 1e3) / 1e9
+        st = s.diagnostics()
+        s.close()
+        out[f"alpha{alpha:g}"] = {"workload": wl.name, "steps": steps, "dt": dt, "ms_per_step": ms / steps,
+                                  "value": wl.dofs * 5 * steps / (ms / 1e3), "unit": "DOF-updates/s",
+                                  "dtype": "f64", "schedule": {"tpb": tpb, "fused_face": fused},
+                                  "roofline_step_hbm": {"bytes_per_node_stage": compulsory_bytes(2, 8),
+                                                        "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                                                        "frac": gbs / hbm},
+                                  "energy_after": st[1]}
+    if not args.no_cpu_baseline:
+        rate, desc, thr = oracle_sample(inputs.coalescence_2d(alpha=1e3), target_s=3.0, parallel=True,
+                                        ne=(128, 128))
+        out["cpu_baseline"] = {"value": rate, "unit": "DOF-updates/s", "cores": thr, "kind": "oracle",
+                               "sample": desc}
+    return out
+
+
+def measure_batch_variant(args, n=32, steps=None, with_sequential=True):
+    """Batched serving of n uneven 3D collision instances (16^3..48^3 elements, N in {3, 4}, We and
+    impact parameter drawn per instance), FP32 operator, autotuned schedule, CUDA-graph replay:
+    aggregate DOF-updates/s, the per-step times, and the per-instance step latency p50 / p99 over
+    every (step, instance) (time from the step's start until that instance's new state is complete),
+    beside the same instances stepped one after another."""
+    import torch
+
+    from paper_1912_12059_gb300 import inputs, nsk
+
+    steps = steps or args.steps
+    wls = inputs.serving_batch_3d(n, seed=inputs.SEED)
+    solvers = []
+    for wl in wls:
+        s = nsk.Solver(3, wl.nelem, wl.N, [0, 0, 0], [1, 1, 1], 0, nsk.NSK_FP32_MIXED)
+        s.set_params(T=wl.T, kappa=wl.kappa, alpha=wl.alpha, beta=wl.beta, mu=wl.mu)
+        s.set_state(wl.initial_state(s.node_coords()))
+        s.compute_dt(wl.cfl)
+        solvers.append(s)
+    nodes = sum(s.E * s.npe for s in solvers)
+    b = nsk.Batch(solvers)
+    tpb, fused, persistent, _ = b.autotune()
+    b.step(args.warmup)
+    n0 = b.launch_count
+    torch.cuda.synchronize()
+    step_ms = b.step(steps, timings=True)
+    torch.cuda.synchronize()
+    launches = b.launch_count - n0
+    total_ms = sum(step_ms)
+    _, lat = b.step(steps, timings=True, latencies=True)  # the same steps again, with the latency stamps
+    flat = np.sort(lat.ravel())
+    out = {"workload": f"batched_{n}x_collision3d_E16-48_N3-4", "instances": n, "nodes_total": nodes,
+           "dtype": "f32", "steps": steps, "value": nodes * 5 * steps / (total_ms / 1e3), "unit": "DOF-updates/s",
+           "ms_per_step": total_ms / steps,
+           "schedule": {"tpb": tpb, "fused_face": fused, "kind": BATCH_KINDS[persistent]}, "cuda_graph": b.uses_graph,
+           "gpu_launches": launches,
+           "step_ms_p50": float(np.percentile(step_ms, 50)), "step_ms_p99": float(np.percentile(step_ms, 99)),
+           "per_instance_latency_ms_p50": float(np.percentile(flat, 50)),
+           "per_instance_latency_ms_p99": float(np.percentile(flat, 99)),
+           "per_instance_latency_ms_max": float(flat[-1])}
+    b.close()
+    if with_sequential:  # the same instances stepped one after another (no batching)
+        seq_ms = 0.0
+        for s in solvers:
+            s.set_schedule(tpb, fused)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            s.step(s.compute_dt(0.5), 2)
+            e1.record()
+            torch.cuda.synchronize()
+            seq_ms += e0.elapsed_time(e1) / 2
+        out["sequential_value"] = nodes * 5 / (seq_ms / 1e3)
+    for s in solvers:
+        s.close()
+    return out
+
+
 def measure_fp32_variant(args, wl, stream, U0, U64_after, dt, peaks):
     """The FP32 operator (FP64 EoS in the spinodal interval, FP64 dt and sums) on the same workload:
     throughput, HBM roofline of its dominant kernel, and its density L2 error against the FP64 run
@@ -723,15 +936,23 @@ def measure_fp32_variant(args, wl, stream, U0, U64_after, dt, peaks):
     nodes = wl.dofs
     err = float(np.sqrt(((U32[0] - U64_after[0]) ** 2).sum() / (U64_after[0] ** 2).sum()))
     name, (kms, kcnt) = max(prof.items(), key=lambda kv: kv[1][0])
-    _, bytes_e = kernel_cost(name, wl.dim, wl.N + 1, 4, traces=trace_fraction(prof))
+    _, bytes_e = kernel_cost(name, wl.dim, wl.N + 1, 4, traces=trace_fraction(prof), sched=fused)
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     achieved = bytes_e * wl.n_elem / (kms / max(kcnt, 1) / 1e3) / 1e9
+    traffic = MEASURED_TRAFFIC.get((name, 4, wl.n_elem))
+    step_gbs = compulsory_bytes(wl.dim, 4) * nodes * 5 * args.steps / (ms / 1e3) / 1e9
     return {"value": nodes * 5 * args.steps / (ms / 1e3), "unit": "DOF-updates/s", "ms_per_step": ms / args.steps,
             "dtype": "f32", "density_l2_rel_err_vs_fp64": err, "steps_compared": args.warmup + args.steps,
             "schedule": {"tpb": tpb, "fused_face": fused},
-            "roofline": {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm, "traffic": MEASURED_TRAFFIC.get((name, 4, wl.n_elem)),
+            # the step on the compulsory bytes (U, K read and written once per stage: 80 B/node in 3D)
+            "roofline": {"bound": "hbm", "bytes_per_node_stage": compulsory_bytes(wl.dim, 4), "achieved": step_gbs,
+                         "peak": hbm, "unit": "GB/s", "frac": step_gbs / hbm,
                          "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"},
+            # the dominant kernel on its own loads and stores (counted from its source)
+            "roofline_kernel": {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                                "frac": achieved / hbm, "traffic": traffic,
+                                "traffic_source": TRAFFIC_SOURCE if traffic is not None else None,
+                                "bytes_source": "the kernel's own compulsory loads and stores per element"},
             "kernels": {k: {"avg_ms": v[0] / max(v[1], 1), "launches": v[1]} for k, v in prof.items()}}
 
 
@@ -746,19 +967,15 @@ def interface_metrics(U, x):
     return {"liquid_fraction": float(liquid.mean()), "separation": xr - xl}
 
 
-def run_closure(args, rank, world):
+def measure_closure_variant(args):
     """Learned c-closure, 3D collision at 96^3 elements, N=3 (56.6M nodes): network trained on
     (rho, c) element snapshots of FP64 runs of the 64^3 collision at We 10, 40, 80; compared over
-    the same simulated time with the explicit FP64 method and the explicit FP32 operator."""
+    the same simulated time with the explicit FP64 method and the explicit FP32 operator. Returns
+    the benchmark line of the closure workload."""
     import torch
 
     from paper_1912_12059_gb300 import closure, inputs, nsk
-    from paper_1912_12059_gb300.build import build_library
 
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    build_library()
-    if rank != 0:
-        return 0
     ne_train = args.nelem_train
     ne_eval = args.nelem or 96
     # --- training data: snapshots of explicit FP64 runs ----------------------------------
@@ -862,7 +1079,20 @@ def run_closure(args, rank, world):
         "gpu_launches": launches,
         "e2e": None, "roofline": None, "cpu_baseline": None,
     }
-    print(json.dumps(line))
+    return line
+
+
+def run_closure(args, rank, world):
+    """The learned-closure workload (measure_closure_variant) as its own benchmark line."""
+    import torch
+
+    from paper_1912_12059_gb300.build import build_library
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    build_library()
+    if rank != 0:
+        return 0
+    print(json.dumps(measure_closure_variant(args)))
     return 0
 
 
@@ -1029,6 +1259,44 @@ def run_riemann1d(args, rank, world):
     return 0
 
 
+def run_fp64peak(args, rank, world):
+    """The FMA throughput probe alone (nsk_measure_fma_rate): FP64 and FP32 FMA rates of this GPU
+    with the SM clock sampled during the launches, beside the peaks derived from the SM count, the
+    FMAs per SM and clock and the sampled clock (the ALU roofline denominator of the FP64 path)."""
+    import torch
+
+    from paper_1912_12059_gb300 import nsk
+    from paper_1912_12059_gb300.build import build_library
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    build_library()
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    res = {}
+    for prec, tag, iters in ((nsk.NSK_FP64, "fp64", 1 << 17), (nsk.NSK_FP32_MIXED, "fp32", 1 << 20)):
+        with ClockSampler(local) as clk:
+            for _ in range(args.warmup):
+                nsk.measure_fma_rate(prec, iters=iters // 8)
+            runs = [nsk.measure_fma_rate(prec, iters=iters) for _ in range(args.steps)]
+        c = clk.summary()
+        best = max(r[0] for r in runs)
+        mhz = c["sm_mhz"] or 2070.0
+        derived = alu_peak_tflops(sms, mhz, fp64=(tag == "fp64"))
+        res[tag] = {"tflops_best": best, "tflops_median": statistics.median(r[0] for r in runs),
+                    "launch_ms_median": statistics.median(r[1] for r in runs), "sm_mhz_median": c["sm_mhz"],
+                    "sm_max_mhz": c["sm_max_mhz"], "clock_reasons": c["reasons"],
+                    "derived_at_sampled_clock": derived, "measured_over_derived": best / derived,
+                    "fma_per_sm_clk_measured": best * 1e12 / (2 * sms * mhz * 1e6)}
+    if rank == 0:
+        print(json.dumps({"metric": "FP64 FMA throughput", "value": res["fp64"]["tflops_best"], "unit": "TFLOP/s",
+                          "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+                          "dtype": "f64", "data": "synthetic",
+                          "config": {"workload": "fma_rate_probe", "sms": sms,
+                                     "launch": "8 blocks x 256 threads per SM, 8 independent FMA chains per thread"},
+                          "fp64": res["fp64"], "fp32": res["fp32"]}))
+    return 0
+
+
 def make_parser():
     """The command line of the benchmark."""
     ap = argparse.ArgumentParser()
@@ -1038,7 +1306,7 @@ def make_parser():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="collision3d",
                     choices=["collision3d", "coalescence2d", "interface1d", "batch", "closure", "gemm", "riemann1d",
-                             "fp32err", "esdirk"])
+                             "fp32err", "esdirk", "fp64peak"])
     ap.add_argument("--rows", type=int, default=884736, help="gemm: rows (elements)")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the variants of the default run (FP32, HLLC, original NSK, sub-cell, ESDIRK4)")
@@ -1074,6 +1342,8 @@ def main(argv=None):
         return run_fp32err(args, rank, world)
     if args.workload == "esdirk":
         return run_esdirk(args, rank, world)
+    if args.workload == "fp64peak":
+        return run_fp64peak(args, rank, world)
     if args.workload == "batch":
         if args.precision == "fp64" and "--precision" not in argv:
             args.precision = "fp32"

@@ -271,16 +271,28 @@ int nsk_measure_fma_rate(int precision, int iters, double* tflops, double* ms, v
 
 /* Stage schedule of a context: tpb = 128 or 256 threads per block for the
  * element kernels (elements per block = tpb / nodes per element, at least 1),
- * fused_face = 1 evaluates the face fluxes inside the volume kernel (each
- * face by both of its elements, bit-identically) instead of a separate face
- * pass. Default: tpb 256, separate face pass. Every expression that could be
+ * and fused_face:
+ *   0 a separate face pass between the lifting and the volume kernel (the
+ *     lifted gradients and the face fluxes are stored in device memory);
+ *   1 the face fluxes evaluated inside the volume kernel (each face by both of
+ *     its elements, bit-identically);
+ *   2 the lean two-launch stage: the lifting stores only the face-normal
+ *     viscous-flux traces of each element's faces, and the volume kernel
+ *     recomputes the element's lifting on chip, so neither the gradients nor
+ *     the face fluxes pass through device memory (the schedule with the least
+ *     memory traffic; relaxation model II: the original NSK equations and the
+ *     sub-cell path have kernels of their own and use tpb only).
+ * Default: tpb 256, separate face pass. Every expression that could be
  * contracted into a fused multiply-add in more than one way is written as an
- * explicit fma, so results are bit-identical under every schedule. */
+ * explicit fma, and every schedule evaluates each value with the same code,
+ * so results are bit-identical under every schedule. NSK_ERR_ARG for other
+ * values. */
 int nsk_set_schedule(nsk_ctx* ctx, int tpb, int fused_face);
 int nsk_get_schedule(nsk_ctx* ctx, int* tpb, int* fused_face);
-/* Autotuner: times one residual evaluation under each of the four schedules
- * on the context's current state (the state is not modified), keeps the
- * fastest and returns it (any output may be NULL; ms_out = its time). */
+/* Autotuner: times one residual evaluation under each of the six schedules
+ * (four for the original NSK equations) on the context's current state (the
+ * state is not modified), keeps the fastest and returns it (any output may be
+ * NULL; ms_out = its time). */
 int nsk_autotune(nsk_ctx* ctx, int* tpb_out, int* fused_out, double* ms_out);
 
 /* Batched execution (many instances per launch). A batch groups n existing

@@ -32,6 +32,13 @@ int nsk_test_hook_block_batch_barrier(nsk_batch* batch);
  * the same with and without a cap. NSK_ERR_ARG for a negative cap. */
 int nsk_test_hook_tc_grid_cap(int max_ctas);
 
+/* The FP64 reciprocal (fn = 0) and square root (fn = 1) the stage kernels use
+ * (Newton-Raphson from the FP32 hardware approximations; CUDA's own division
+ * and sqrt outside 2^-120 < x < 2^120), evaluated on the device arrays x -> y
+ * of n values on stream, for their accuracy tests. Queued, no
+ * synchronisation. NSK_ERR_ARG for another fn, NULL arrays or n < 0. */
+int nsk_test_hook_math(int fn, const double* x, double* y, long long n, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -825,9 +825,9 @@ int nsk_get_sizes(nsk_ctx* c, long long* n_elem, int* nodes_per_elem, int* nvar)
 long long nsk_launch_count(nsk_ctx* c) { return c ? c->launches : -1; }
 
 int nsk_set_schedule(nsk_ctx* c, int tpb, int fused_face) {
-  if (!c || (tpb != 128 && tpb != 256)) return NSK_ERR_ARG;
+  if (!c || (tpb != 128 && tpb != 256) || fused_face < 0 || fused_face > 2) return NSK_ERR_ARG;
   c->tpb = tpb;
-  c->fused_face = fused_face ? 1 : 0;
+  c->fused_face = fused_face;
   return NSK_OK;
 }
 
@@ -848,8 +848,11 @@ int nsk_autotune(nsk_ctx* c, int* tpb_out, int* fused_out, double* ms_out) {
   int bt = c->tpb, bf = c->fused_face, st = NSK_OK;
   const bool prof = c->prof_on;
   c->prof_on = false;
+  // the lean two-launch stage applies to relaxation model II only (the original NSK equations
+  // have their own stage kernels and take the schedule's block size alone)
+  const int nsched = c->p.model == NSK_MODEL_NSK ? 2 : 3;
   for (int it = 0; it < 2 && st == NSK_OK; ++it)
-    for (int f = 0; f < 2 && st == NSK_OK; ++f) {
+    for (int f = 0; f < nsched && st == NSK_OK; ++f) {
       c->tpb = tpbs[it];
       c->fused_face = f;
       NskLaunch l = {NSK_MODE_RHS, c->rbuf, 0.0, 0.0, nullptr, 0.0, nullptr, c->tpb, c->fused_face};

@@ -143,3 +143,22 @@ extern "C" int nsk_measure_fma_rate(int precision, int iters, double* tflops, do
   cudaStream_t s = (cudaStream_t)stream;
   return precision == NSK_FP64 ? fma_rate_t<double>(iters, tflops, ms, s) : fma_rate_t<float>(iters, tflops, ms, s);
 }
+
+// ---------------------------------------------------------------------------
+// Test hook (include/nsk_test_hooks.h): the stage kernels' FP64 reciprocal and square root on
+// device arrays, for their accuracy tests.
+// ---------------------------------------------------------------------------
+namespace {
+__global__ void __launch_bounds__(256) k_math_hook(const int fn, const double* __restrict__ x,
+                                                   double* __restrict__ y, const long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = fn == 0 ? nsk::rcp_nr(x[i]) : nsk::sqrt_nr(x[i]);
+}
+}  // namespace
+
+extern "C" int nsk_test_hook_math(int fn, const double* x, double* y, long long n, void* stream) {
+  if ((fn != 0 && fn != 1) || !x || !y || n < 0) return NSK_ERR_ARG;
+  if (n == 0) return NSK_OK;
+  k_math_hook<<<reduce_grid(n), 256, 0, (cudaStream_t)stream>>>(fn, x, y, n);
+  return cudaGetLastError() == cudaSuccess ? NSK_OK : NSK_ERR_CUDA;
+}

@@ -475,6 +475,33 @@ int launch_instances(nsk_batch* bt, int mode, double A, double B, int tpb, int f
   return NSK_OK;
 }
 
+// the lean stage on every instance (instance schedule, fused_face 2): a step prolongs once into
+// each instance's trace buffer (stage 0), then its stages alternate between that buffer and the
+// instance's spare one (the lean volume kernel writes the next stage's traces while its
+// neighbours still read the current ones); the last stage of a step writes none. stage < 0: a
+// residual (prolongation, no traces written).
+int launch_instances_lean(nsk_batch* bt, int mode, double A, double B, int tpb, int stage, bool stamps) {
+  for (int i = 0; i < bt->n; ++i) {
+    nsk_ctx* c = bt->inst[i];
+    NskBuffers b = c->b;
+    void* bufs[2] = {c->b.Utr, c->utr_alt};
+    NskLaunch l = {mode, c->rbuf, A, B, c->b.dt, 0.0, nullptr, tpb, 2};
+    if (stage >= 0) {
+      b.Utr = bufs[stage & 1];
+      l.traces_ready = stage > 0;
+      l.utr_next = stage < 4 ? bufs[(stage + 1) & 1] : nullptr;
+    }
+    const int r = nsk_launch_stage_d3(c->p, c->np, c->precision == NSK_FP32_MIXED, b, l, bt->stream);
+    if (r < 0) return r;
+    bt->launches += r;
+    if (stamps) {
+      const int st = launch_stamp(bt, bt->d_stamp + 1 + i, 1);
+      if (st) return st;
+    }
+  }
+  return NSK_OK;
+}
+
 // one stage of the whole batch under a schedule (persistent 1: one cooperative launch; 0: one
 // launch per phase; 2: every instance's own launches)
 // trace flags of every stage of a step under the separate face schedule: traces come from the
@@ -484,7 +511,8 @@ int step_traces(int fused) { return fused ? 0 : 3; }
 // stamps: the last stage of a step whose per-instance latencies are measured (each instance's
 // completion stamped after its last kernel; one launch for all instances stamps them together)
 int launch_batch(nsk_batch* bt, int mode, double A, double B, int tpb, int fused, int persistent, int traces,
-                 bool stamps = false) {
+                 bool stamps = false, int stage = -1) {
+  if (persistent == 2 && fused == 2) return launch_instances_lean(bt, mode, A, B, tpb, stage, stamps);
   if (fused) traces = 0;  // the fused volume phase reads the traces: they are prolonged every stage
   if (persistent == 2) return launch_instances(bt, mode, A, B, tpb, fused, traces, stamps);
   const int r = persistent ? launch_persistent(bt, mode, A, B, tpb, fused, traces)
@@ -508,7 +536,7 @@ int launch_step(nsk_batch* bt, int dtmode, double cfl, bool stamps) {
     }
   for (int s = 0; s < 5; ++s) {
     const int r = launch_batch(bt, NSK_MODE_LSRK, kA[s], kB[s], bt->tpb, bt->fused, bt->persistent,
-                               step_traces(bt->fused), stamps && s == 4);
+                               step_traces(bt->fused), stamps && s == 4, s);
     if (r) return r;
   }
   return NSK_OK;
@@ -646,9 +674,11 @@ int nsk_batch_create(nsk_batch** out, int n, nsk_ctx* const* instances) {
 }
 
 int nsk_batch_set_schedule(nsk_batch* bt, int tpb, int fused_face, int persistent) {
-  if (!bt || (tpb != 128 && tpb != 256) || persistent < 0 || persistent > 2) return NSK_ERR_ARG;
+  if (!bt || (tpb != 128 && tpb != 256) || persistent < 0 || persistent > 2 || fused_face < 0 || fused_face > 2 ||
+      (fused_face == 2 && persistent != 2))
+    return NSK_ERR_ARG;
   bt->tpb = tpb;
-  bt->fused = fused_face ? 1 : 0;
+  bt->fused = fused_face;
   bt->persistent = persistent;
   return NSK_OK;
 }
@@ -672,14 +702,16 @@ int nsk_batch_autotune(nsk_batch* bt, int* tpb_out, int* fused_out, int* persist
   const int tpbs[2] = {128, 256};
   for (int per = 0; per < 3 && st == NSK_OK; ++per)
     for (int ti = 0; ti < 2 && st == NSK_OK; ++ti)
-      for (int f = 0; f < 2 && st == NSK_OK; ++f) {
+      for (int f = 0; f < (per == 2 ? 3 : 2) && st == NSK_OK; ++f) {
         // warm-up with a prolongation pass (residual: state untouched), then time the stage as a
-        // step runs it (rewriting the traces of the unchanged state leaves them as they are)
+        // step runs it (rewriting the traces of the unchanged state leaves them as they are; the
+        // lean stage as a middle stage of a step: traces read from the trace buffer, the next
+        // ones written to the spare buffer)
         st = launch_batch(bt, NSK_MODE_RHS, 0.0, 0.0, tpbs[ti], f, per, 0);
         if (st) break;
         cudaEventRecord(e0, bt->stream);
         for (int r = 0; r < 3 && st == NSK_OK; ++r)
-          st = launch_batch(bt, NSK_MODE_RHS, 0.0, 0.0, tpbs[ti], f, per, step_traces(f));
+          st = launch_batch(bt, NSK_MODE_RHS, 0.0, 0.0, tpbs[ti], f, per, step_traces(f), false, 2);
         cudaEventRecord(e1, bt->stream);
         if (cudaEventSynchronize(e1) != cudaSuccess) st = NSK_ERR_CUDA;
         float ms = 0.f;

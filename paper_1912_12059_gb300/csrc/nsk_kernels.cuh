@@ -32,6 +32,7 @@ struct Shape {
   static constexpr int NV = D + 2;             // conservative variables
   static constexpr int NW = D + 1;             // lifted primitive variables (v, c)
   static constexpr int NQ = D * (D + 1);       // gradient components
+  static constexpr int NVF = D * (D + 1) / 2 + D;  // viscous form: symmetric stress / mu and grad c
   static constexpr int NF = 2 * D;             // faces per element
   static constexpr int G = (256 / NPE) > 0 ? 256 / NPE : 1;  // elements per block
   static constexpr int TPB = G * NPE;
@@ -109,6 +110,63 @@ __device__ __forceinline__ int nbr_of(const NskParams& p, const ElemIdx& x, int 
   if (dir > 0) return c == p.ne[k] - 1 ? x.e - p.ewrap[k] : x.e + p.est[k];
   return c == 0 ? x.e + p.ewrap[k] : x.e - p.est[k];
 }
+
+// ---- FP64 reciprocal and square root with few FP64 instructions ----
+// The stage kernels are bound by the FP64 pipe (two FP64 operations per SM and clock on this
+// GPU), where a correctly rounded division or square root costs about ten of them. Here both are
+// Newton-Raphson iterations seeded by the FP32 hardware approximations (rcp.approx,
+// rsqrt.approx, relative error about 2^-23): the seed's conversions to and from FP32 are integer
+// operations on the bit patterns (off the FP64 pipe), and two Newton corrections bring the error
+// from 2^-22 to 2^-44 to below one unit in the last place (a faithful result, not always the
+// correctly rounded one; the tests bound it by one ulp against CUDA's division and sqrt).
+// Domain: positive normal x with 2^-120 < x < 2^120 (the FP32 range of the seed); elsewhere
+// the CUDA functions are used.
+
+// |x| truncated to FP32 (round toward zero), from the bit pattern; x in the domain above
+__device__ __forceinline__ float f32_trunc(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  return __uint_as_float((((hi & 0x7FFFFFFFu) - ((1023u - 127u) << 20)) << 3) | (lo >> 29));
+}
+// a positive normal FP32 value as FP64 (exact)
+__device__ __forceinline__ double f64_exact(float y) {
+  const unsigned b = __float_as_uint(y);
+  return __hiloint2double((int)((((b >> 23) + (1023u - 127u)) << 20) | ((b & 0x7FFFFFu) >> 3)), (int)(b << 29));
+}
+__device__ __forceinline__ bool nr_domain(double x) {
+  return (unsigned)__double2hiint(x) - ((1023u - 120u) << 20) < (240u << 20);
+}
+__device__ __forceinline__ float rcp_approx_f32(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float rsqrt_approx_f32(float x) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+// 1/a: y <- y + y (1 - a y), twice, from the FP32 seed
+__device__ __forceinline__ double rcp_nr(double a) {
+  if (!nr_domain(a)) return 1.0 / a;
+  double y = f64_exact(rcp_approx_f32(f32_trunc(a)));
+  y = fma(y, fma(-a, y, 1.0), y);
+  return fma(y, fma(-a, y, 1.0), y);
+}
+// sqrt(x): s <- s + (x - s^2) h with h ~ 1/(2 sqrt x) from the FP32 seed of 1/sqrt(x), twice
+__device__ __forceinline__ double sqrt_nr(double x) {
+  if (!nr_domain(x)) return sqrt(x);
+  const float y0 = rsqrt_approx_f32(f32_trunc(x));
+  const double h = f64_exact(0.5f * y0);  // exact: a power-of-two scaling
+  double s = x * f64_exact(y0);
+  s = fma(fma(-s, s, x), h, s);
+  return fma(fma(-s, s, x), h, s);
+}
+// the arithmetic type's reciprocal and square root in the stage kernels: FP64 through the
+// Newton-Raphson forms above, FP32 as the hardware computes them
+__device__ __forceinline__ double rcp_s(double a) { return rcp_nr(a); }
+__device__ __forceinline__ float rcp_s(float a) { return 1.0f / a; }
+__device__ __forceinline__ double sqrt_s(double x) { return sqrt_nr(x); }
+__device__ __forceinline__ float sqrt_s(float x) { return sqrtf(x); }
 
 // ---- Van-der-Waals EoS, Sec. 2.1 (reduced: p = 8 T rho / (3 - rho) - 3 rho^2) ----
 // Modified pressure p_alpha = p + alpha rho^2 / 2 (Eq. modified_pressure) and its derivative
@@ -278,32 +336,49 @@ inline __device__ bool grid_barrier(unsigned* bar, int* err, const unsigned long
 // `u` points at node 0 of the element's first variable, variables `vs` apart (the
 // global array, or an element staged in shared memory: both give the same bits).
 // NVAR conservative variables (d + 2 for model II, d + 1 for the original NSK equations).
+// The NVAR traces of one (face slot, face node) of an element, and in FP64 also the planes
+// 1/rho and 1/(3 - rho) of the trace: out[NVAR + TraceComps<R>::extra]. `u` points at node 0
+// of the element's first variable, variables `vs` apart (the global array, or an element
+// staged in shared memory: both give the same bits).
 template <typename R, int D, int NP, int NVAR = Shape<D, NP>::NV>
-__device__ __forceinline__ void prolong_trace(const NskParams& p, const R* __restrict__ u, const size_t vs,
-                                              R* __restrict__ Utr, const int e, const int slot, const int fn) {
-  using S = Shape<D, NP>;
+__device__ __forceinline__ void trace_vals(const NskParams& p, const R* __restrict__ u, const size_t vs,
+                                           const int slot, const int fn, R* out) {
   const auto& t = TabSel<R>::get(p);
   const int k = slot >> 1;
   const R* L = (slot & 1) ? t.lp : t.lm;
   const int n0 = line_base<D, NP>(fn, k), st = node_stride<NP>(k);
   const R* ul = u + n0;
-  const size_t pl = (size_t)S::NF * p.nfe;  // distance between the planes of two variables
-  R* o = Utr + (size_t)slot * p.nfe + (e * S::NFN + fn);
-  R rho = 0;
 #pragma unroll
   for (int v = 0; v < NVAR; ++v) {
     R acc = 0;
 #pragma unroll
     for (int j = 0; j < NP; ++j) acc = fma(L[j], ul[v * vs + j * st], acc);
-    o[v * pl] = acc;
-    if (v == 0) rho = acc;
+    out[v] = acc;
   }
   if constexpr (TraceComps<R>::extra > 0) {
     // one division: d = 1/(rho (3 - rho)) gives 1/rho = (3 - rho) d and 1/(3 - rho) = rho d
-    const R d = R(1) / (rho * (R(3) - rho));
-    o[NVAR * pl] = (R(3) - rho) * d;
-    o[(NVAR + 1) * pl] = rho * d;
+    const R rho = out[0];
+    const R d = rcp_s(rho * (R(3) - rho));
+    out[NVAR] = (R(3) - rho) * d;
+    out[NVAR + 1] = rho * d;
   }
+}
+
+// Utr[v][slot][E][nfn], slot = 2k + (0: face xi_k = -1, 1: xi_k = +1): the trace
+// sum_j l_j(+-1) U_j along the line in direction k through face node fn of element e
+// (trace_vals, stored).
+// NVAR conservative variables (d + 2 for model II, d + 1 for the original NSK equations).
+template <typename R, int D, int NP, int NVAR = Shape<D, NP>::NV>
+__device__ __forceinline__ void prolong_trace(const NskParams& p, const R* __restrict__ u, const size_t vs,
+                                              R* __restrict__ Utr, const int e, const int slot, const int fn) {
+  using S = Shape<D, NP>;
+  constexpr int NT = NVAR + TraceComps<R>::extra;
+  const size_t pl = (size_t)S::NF * p.nfe;  // distance between the planes of two variables
+  R* o = Utr + (size_t)slot * p.nfe + (e * S::NFN + fn);
+  R vals[NT];
+  trace_vals<R, D, NP, NVAR>(p, u, vs, slot, fn, vals);
+#pragma unroll
+  for (int v = 0; v < NT; ++v) o[v * pl] = vals[v];
 }
 
 // one (element, face slot, face node) item of the prolongation, idx = (slot, e, fn) flattened
@@ -396,6 +471,192 @@ __host__ __device__ constexpr int lift_smem() {
   return lift_work_smem<R, D, NP, G>() + tab_smem<D, NP>();
 }
 
+// ---- parts of the BR1 lifting, shared by the stage kernels (so every schedule rounds alike) ----
+
+// The primitive variables w = (v, c) (MODEL 1: (v, rho)) of node n of a lifting element, stored in
+// the lifting's shared buffer sw once per direction copy (lines of direction k contiguous when
+// LINES). u points at the node's first variable, variables vs apart.
+template <typename R, int D, int NP, int G, int MODEL = 0>
+__device__ __forceinline__ void lift_store_w(const R* __restrict__ u, const size_t vs, R* sw, const int le,
+                                             const int n, int& eflag) {
+  using S = Shape<D, NP>;
+  constexpr int NPE = S::NPE, NW = S::NW;
+  constexpr bool LINES = lift_lines<R, D, NP, G>();
+  constexpr int NCOPY = LINES ? D : 1;
+  const R rho = u[0];
+  eflag |= rho_flags(rho);
+  const R inv = rcp_s(rho);
+  R wn[NW];
+#pragma unroll
+  for (int a = 0; a < D; ++a) wn[a] = u[(1 + a) * vs] * inv;
+  wn[D] = MODEL == 1 ? rho : u[(D + 1) * vs];
+#pragma unroll
+  for (int c = 0; c < NCOPY; ++c) {
+    const int pos = LINES ? line_pos<D, NP>(n, c) : n;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) sw[((le * NCOPY + c) * NW + w) * NPE + pos] = wn[w];
+  }
+}
+
+// 2 w* of one (face slot, face node) from the element's own trace uo and its neighbour's un
+// (the 1/2 of the central flux is in the staged lpk, lmk: an exact scaling), each with NV
+// conservative values and, in FP64, 1/rho and 1/(3 - rho) after them; ws: NW values NFN apart.
+template <typename R, int D, int NFN, int NV, int MODEL = 0>
+__device__ __forceinline__ void lift_wstar(const R* uo, const R* un, R* ws, int& eflag) {
+  eflag |= rho_flags(uo[0]) | rho_flags(un[0]);
+  R io, in;
+  if constexpr (TraceComps<R>::extra > 0) {
+    io = uo[NV];
+    in = un[NV];
+  } else {
+    io = R(1) / uo[0];
+    in = R(1) / un[0];
+  }
+#pragma unroll
+  for (int a = 0; a < D; ++a) ws[a * NFN] = fma(uo[1 + a], io, un[1 + a] * in);
+  ws[D * NFN] = MODEL == 1 ? uo[0] + un[0] : uo[D + 1] + un[D + 1];
+}
+
+// The lifted gradients q[k NW + w] of node n (weak form, central flux; the direction operators
+// with 2/h_k folded in and the 1/2 of w* in lpk, lmk staged at tb), from sw and the 2 w* in sws.
+template <typename R, int D, int NP, int G>
+__device__ __forceinline__ void lift_q(const R* tb, const R* sw, const R* sws, const int le, const int n,
+                                       R (&q)[Shape<D, NP>::NQ]) {
+  using S = Shape<D, NP>;
+  constexpr int NPE = S::NPE, NFN = S::NFN, NW = S::NW, NF = S::NF;
+  constexpr bool LINES = lift_lines<R, D, NP, G>();
+  constexpr int NCOPY = LINES ? D : 1, SWS = lift_slot_stride<D, NP>();
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    const int i = coord<NP>(n, k), fn = face_node<D, NP>(n, k);
+    const int n0 = line_base<D, NP>(fn, k), st = node_stride<NP>(k);
+    R dk[NP];
+#pragma unroll
+    for (int j = 0; j < NP; ++j) dk[j] = tb[(k * NP + i) * NP + j];
+    const R lpk = tb[D * NP * NP + k * NP + i], lmk = tb[D * NP * NP + D * NP + k * NP + i];
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+      R wl[NP];
+      if (LINES || k == 0) {  // the line is contiguous
+        load_line<R, NP>(sw + ((le * NCOPY + (LINES ? k : 0)) * NW + w) * NPE + (LINES ? fn * NP : n0), wl);
+      } else {
+#pragma unroll
+        for (int j = 0; j < NP; ++j) wl[j] = sw[(le * NW + w) * NPE + n0 + j * st];
+      }
+      R vol = 0;
+#pragma unroll
+      for (int j = 0; j < NP; ++j) vol = fma(dk[j], wl[j], vol);
+      const R wp = sws[(le * NF + 2 * k + 1) * SWS + w * NFN + fn];
+      const R wm = sws[(le * NF + 2 * k) * SWS + w * NFN + fn];
+      q[k * NW + w] = fma(wp, lpk, fma(-wm, lmk, -vol));
+    }
+  }
+}
+
+// the viscous stress without mu from the lifted velocity gradients (symmetric: each
+// off-diagonal sum once)
+template <typename R, int D>
+__device__ __forceinline__ void stress_of(const R* q, R (&tau)[D][D]) {
+  constexpr int NW = D + 1;
+  R div = 0;
+#pragma unroll
+  for (int a = 0; a < D; ++a) div += q[a * NW + a];
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+#pragma unroll
+    for (int a = k; a < D; ++a) {
+      const R sum = q[k * NW + a] + q[a * NW + k];
+      tau[k][a] = (a == k) ? fma(-R(2.0 / 3.0), div, sum) : sum;
+      tau[a][k] = tau[k][a];
+    }
+  }
+}
+
+// The viscous form of the lifted gradients that the volume kernel needs: the stress without mu
+// (its D(D+1)/2 independent components, row by row from the diagonal: (k, a) for a >= k) and
+// grad c; stored by the lifting in place of the gradients (fewer values, and the stress is
+// formed once).
+template <typename R, int D>
+__device__ __forceinline__ void visc_store(const R (&tau)[D][D], const R* gc, R* __restrict__ Q, const size_t nn,
+                                           const int g) {
+  int c = 0;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+#pragma unroll
+    for (int a = k; a < D; ++a) Q[(c++) * nn + g] = tau[k][a];
+  }
+#pragma unroll
+  for (int k = 0; k < D; ++k) Q[(c++) * nn + g] = gc[k];
+}
+template <typename R, int D>
+__device__ __forceinline__ void visc_load(const R* __restrict__ Q, const size_t nn, const int g, R (&tau)[D][D],
+                                          R* gc) {
+  int c = 0;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+#pragma unroll
+    for (int a = k; a < D; ++a) {
+      tau[k][a] = Q[(c++) * nn + g];
+      tau[a][k] = tau[k][a];
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < D; ++k) gc[k] = Q[(c++) * nn + g];
+}
+// the stress (without mu) and grad c of a node's lifted gradients q
+template <typename R, int D>
+__device__ __forceinline__ void visc_of(const R* q, R (&tau)[D][D], R* gc) {
+  stress_of<R, D>(q, tau);
+#pragma unroll
+  for (int k = 0; k < D; ++k) gc[k] = q[k * (D + 1) + D];
+}
+
+// The face-normal viscous flux F^v_k = (tau_{.k}, (kappa/beta) c_{x_k}) traced onto the element's
+// own faces: the nodal fluxes (without mu and kappa/beta, lines of direction k contiguous) go to
+// sfv, then, after a block barrier, each face value is the trace with mu l(+-1) or
+// (kappa/beta) l(+-1). TO_SMEM: into fo[((le NF + slot) NW + c) NFN + fn]; else into
+// FVtr[c][slot][E][nfn]. Ends with a block barrier.
+template <typename R, int D, int NP, int G, bool TO_SMEM = false>
+__device__ __forceinline__ void lift_fv_traces(const NskParams& p, const R (&tau)[D][D], const R* gc, R* sfv,
+                                               const bool valid, const int le, const int n, const int e,
+                                               R* __restrict__ FVtr, R* fo) {
+  using S = Shape<D, NP>;
+  constexpr int NPE = S::NPE, NFN = S::NFN, NW = S::NW, NF = S::NF;
+  const auto& t = TabSel<R>::get(p);
+  if (valid) {
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const int pos = line_pos<D, NP>(n, k);
+#pragma unroll
+      for (int a = 0; a < D; ++a) sfv[((le * D + k) * NW + a) * NPE + pos] = tau[k][a];
+      sfv[((le * D + k) * NW + D) * NPE + pos] = gc[k];
+    }
+  }
+  __syncthreads();
+  if (valid) {
+    const size_t pl = (size_t)NF * p.nfe;  // distance between the planes of two trace variables
+    for (int it = n; it < NF * NFN; it += NPE) {
+      const int slot = it / NFN, fn = it % NFN, k = slot >> 1;
+      const R* Lmu = (slot & 1) ? t.lpmu : t.lmmu;  // mu l(+-1)
+      const R* Lkb = (slot & 1) ? t.lpkb : t.lmkb;  // (kappa/beta) l(+-1)
+#pragma unroll
+      for (int c = 0; c < NW; ++c) {
+        R f[NP];
+        load_line<R, NP>(sfv + ((le * D + k) * NW + c) * NPE + fn * NP, f);
+        const R* L = c < D ? Lmu : Lkb;
+        R acc = 0;
+#pragma unroll
+        for (int j = 0; j < NP; ++j) acc = fma(L[j], f[j], acc);
+        if constexpr (TO_SMEM)
+          fo[((le * NF + slot) * NW + c) * NFN + fn] = acc;
+        else
+          FVtr[(size_t)slot * p.nfe + (e * NFN + fn) + c * pl] = acc;
+      }
+    }
+  }
+  __syncthreads();
+}
+
 // BR1 lifting (Sec. 3.1) in weak form with the central flux,
 //   Q_{k,w}(i) = (2/h_k) [ -sum_j (w_j/w_i) l_i'(xi_j) w_j + (w*_{k,+} l_i(1) - w*_{k,-} l_i(-1)) / w_i ]
 // (evaluated with the 2/h_k-scaled tables dk, lpk, lmk),
@@ -405,13 +666,17 @@ __host__ __device__ constexpr int lift_smem() {
 // MODEL 1 (original NSK equations, state (rho, m)): w = (v, rho), and instead of the viscous
 // flux traces the kernel writes into FVtr the trace of (grad rho)_k on the element's faces of
 // direction k ([2d][E][nfn], one component), the input of the second lifting.
-template <typename R, int D, int NP, int G, int MODEL = 0>
+// QF (model II only): Q receives the viscous form (visc_store) instead of the gradients, for the
+// volume kernel of a residual or Runge-Kutta stage; without it the gradients (nsk_lift, the
+// diagnostics).
+template <typename R, int D, int NP, int G, int MODEL = 0, bool QF = (MODEL == 0)>
 __device__ __forceinline__ void lift_group(const NskParams& p, const R* __restrict__ U, const R* __restrict__ Utr,
                                            R* __restrict__ Q, R* __restrict__ FVtr, const long long e0, R* sm,
                                            int& eflag) {
   using S = Shape<D, NP>;
   constexpr int NPE = S::NPE, NFN = S::NFN, NW = S::NW, NF = S::NF, NQ = S::NQ;
   constexpr int NV = MODEL == 1 ? D + 1 : S::NV;  // conservative variables
+  constexpr int NT = NV + TraceComps<R>::extra;
   constexpr bool LINES = lift_lines<R, D, NP, G>();
   constexpr int NCOPY = LINES ? D : 1, SWS = lift_slot_stride<D, NP>();
   R* sw = sm;                           // [G][NCOPY][NW][NPE] primitive variables at the nodes
@@ -427,19 +692,7 @@ __device__ __forceinline__ void lift_group(const NskParams& p, const R* __restri
 
   stage_tables<R, D, NP>(t, tb, R(1), R(0.5));
   if (valid) {
-    const R rho = U[g];
-    eflag |= rho_flags(rho);
-    const R inv = R(1) / rho;
-    R wn[NW];
-#pragma unroll
-    for (int a = 0; a < D; ++a) wn[a] = U[(1 + a) * nn + g] * inv;
-    wn[D] = MODEL == 1 ? rho : U[(D + 1) * nn + g];
-#pragma unroll
-    for (int c = 0; c < NCOPY; ++c) {
-      const int pos = LINES ? line_pos<D, NP>(n, c) : n;
-#pragma unroll
-      for (int w = 0; w < NW; ++w) sw[((le * NCOPY + c) * NW + w) * NPE + pos] = wn[w];
-    }
+    lift_store_w<R, D, NP, G, MODEL>(U + g, nn, sw, le, n, eflag);
     const ElemIdx ex = elem_idx<D>(p, e);
     // a fixed trip count (the last round predicated): the gathers of all rounds are in flight together
 #pragma unroll
@@ -451,57 +704,23 @@ __device__ __forceinline__ void lift_group(const NskParams& p, const R* __restri
       const int oslot = 2 * k + (1 - s);
       const R* to = Utr + (size_t)slot * p.nfe + (e * NFN + fn);
       const R* tn = Utr + (size_t)oslot * p.nfe + (en * NFN + fn);
-      R uo[NV], un[NV];
+      R uo[NT], un[NT];
 #pragma unroll
-      for (int v = 0; v < NV; ++v) {
+      for (int v = 0; v < NT; ++v) {
         uo[v] = to[v * pl];
         un[v] = tn[v * pl];
       }
-      eflag |= rho_flags(uo[0]) | rho_flags(un[0]);
-      R io, in;
-      if constexpr (TraceComps<R>::extra > 0) {
-        io = to[NV * pl];
-        in = tn[NV * pl];
-      } else {
-        io = R(1) / uo[0];
-        in = R(1) / un[0];
-      }
-      // 2 w* (the 1/2 of the central flux is in the staged lpk, lmk: an exact scaling)
-      R* ws = sws + (le * NF + slot) * SWS + fn;
-#pragma unroll
-      for (int a = 0; a < D; ++a) ws[a * NFN] = fma(uo[1 + a], io, un[1 + a] * in);
-      ws[D * NFN] = MODEL == 1 ? uo[0] + un[0] : uo[D + 1] + un[D + 1];
+      lift_wstar<R, D, NFN, NV, MODEL>(uo, un, sws + (le * NF + slot) * SWS + fn, eflag);
     }
   }
   __syncthreads();
 
   R q[NQ];
   if (valid) {
+    lift_q<R, D, NP, G>(tb, sw, sws, le, n, q);
+    if constexpr (!QF) {
 #pragma unroll
-    for (int k = 0; k < D; ++k) {
-      const int i = coord<NP>(n, k), fn = face_node<D, NP>(n, k);
-      const int n0 = line_base<D, NP>(fn, k), st = node_stride<NP>(k);
-      R dk[NP];
-#pragma unroll
-      for (int j = 0; j < NP; ++j) dk[j] = tb[(k * NP + i) * NP + j];
-      const R lpk = tb[D * NP * NP + k * NP + i], lmk = tb[D * NP * NP + D * NP + k * NP + i];
-#pragma unroll
-      for (int w = 0; w < NW; ++w) {
-        R wl[NP];
-        if (LINES || k == 0) {  // the line is contiguous
-          load_line<R, NP>(sw + ((le * NCOPY + (LINES ? k : 0)) * NW + w) * NPE + (LINES ? fn * NP : n0), wl);
-        } else {
-#pragma unroll
-          for (int j = 0; j < NP; ++j) wl[j] = sw[(le * NW + w) * NPE + n0 + j * st];
-        }
-        R vol = 0;
-#pragma unroll
-        for (int j = 0; j < NP; ++j) vol = fma(dk[j], wl[j], vol);
-        const R wp = sws[(le * NF + 2 * k + 1) * SWS + w * NFN + fn];
-        const R wm = sws[(le * NF + 2 * k) * SWS + w * NFN + fn];
-        q[k * NW + w] = fma(wp, lpk, fma(-wm, lmk, -vol));
-        Q[(k * NW + w) * nn + g] = q[k * NW + w];
-      }
+      for (int c = 0; c < NQ; ++c) Q[c * nn + g] = q[c];
     }
   }
   __syncthreads();  // shared memory is reused below
@@ -528,107 +747,54 @@ __device__ __forceinline__ void lift_group(const NskParams& p, const R* __restri
     __syncthreads();  // the caller may reuse shared memory
     return;
   }
-
   // [G][D][NW][NPE] the viscous flux F^v_k at the nodes without its coefficients (the stress
   // tau / mu and grad c), lines in direction k contiguous; mu and kappa/beta are folded into
-  // the face interpolation below
-  R* sfv = sm;
+  // the face interpolation
+  R tau[D][D], gc[D];
   if (valid) {
-    R div = 0;
-#pragma unroll
-    for (int a = 0; a < D; ++a) div += q[a * NW + a];
-    R tau[D][D];  // symmetric: each off-diagonal sum once
-#pragma unroll
-    for (int k = 0; k < D; ++k) {
-#pragma unroll
-      for (int a = k; a < D; ++a) {
-        const R sum = q[k * NW + a] + q[a * NW + k];
-        tau[k][a] = (a == k) ? fma(-R(2.0 / 3.0), div, sum) : sum;
-        tau[a][k] = tau[k][a];
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < D; ++k) {
-      const int pos = line_pos<D, NP>(n, k);
-#pragma unroll
-      for (int a = 0; a < D; ++a) sfv[((le * D + k) * NW + a) * NPE + pos] = tau[k][a];
-      sfv[((le * D + k) * NW + D) * NPE + pos] = q[k * NW + D];
-    }
+    visc_of<R, D>(q, tau, gc);
+    if constexpr (QF) visc_store<R, D>(tau, gc, Q, nn, g);
   }
-  __syncthreads();
-
-  if (valid) {
-    for (int it = n; it < NF * NFN; it += NPE) {
-      const int slot = it / NFN, fn = it % NFN, k = slot >> 1;
-      const R* Lmu = (slot & 1) ? t.lpmu : t.lmmu;  // mu l(+-1)
-      const R* Lkb = (slot & 1) ? t.lpkb : t.lmkb;  // (kappa/beta) l(+-1)
-      R* o = FVtr + (size_t)slot * p.nfe + (e * NFN + fn);
-#pragma unroll
-      for (int c = 0; c < NW; ++c) {
-        R f[NP];
-        load_line<R, NP>(sfv + ((le * D + k) * NW + c) * NPE + fn * NP, f);
-        const R* L = c < D ? Lmu : Lkb;
-        R acc = 0;
-#pragma unroll
-        for (int j = 0; j < NP; ++j) acc = fma(L[j], f[j], acc);
-        o[c * pl] = acc;
-      }
-    }
-  }
-  __syncthreads();  // the caller may reuse shared memory
+  lift_fv_traces<R, D, NP, G>(p, tau, gc, sm, valid, le, n, e, FVtr, nullptr);
 }
 
-// Numerical flux on the face between eL (its +1 side, slot 2k+1) and eR (its -1 side,
-// slot 2k), face node fn (HLLC instead of the Lax-Friedrichs flux when p.flux says so,
-// see nsk_set_flux):
-//   F* = (F^c_k(U_L) + F^c_k(U_R))/2 - lambda/2 (U_R - U_L) - (F^v_L + F^v_R)/2,
-//   lambda = max(|v_{L,k}| + sqrt(p_alpha'(rho_L)), |v_{R,k}| + sqrt(p_alpha'(rho_R)))
-// (local Lax-Friedrichs with the model II wave speeds, Eq. parabolic_eigenvalues_model2;
-// BR1 viscous flux). The jump term acts on rho and momentum (c has no convective flux)
-// unless c_diss is set. F receives 2 F* (the 1/2 is applied by the volume kernel's staged
-// surface operators; scaling by 2 is exact, so the residual is unchanged bit for bit).
+// a[1 + k] for a runtime direction k through selects over compile-time indices, so that the
+// arrays stay in registers (an index unknown at compile time sends an array to local memory)
+template <int D, typename R>
+__device__ __forceinline__ R comp1(const R* a, const int k) {
+  R r = a[1];
+  if constexpr (D > 1) r = k == 1 ? a[2] : r;
+  if constexpr (D > 2) r = k == 2 ? a[3] : r;
+  return r;
+}
+
+// The flux of face_flux (below) from the two sides' trace values: UL, UR the conservative traces (and
+// in FP64 the planes 1/rho, 1/(3 - rho) after them), VL, VR the face-normal viscous fluxes.
 template <typename R, int D, int NP>
-__device__ __forceinline__ void face_flux(const NskParams& p, const R* __restrict__ Utr, const R* __restrict__ FVtr,
-                                          const int eL, const int eR, const int k, const int fn,
-                                          R* F, int& eflag) {
+__device__ __forceinline__ void face_flux_vals(const NskParams& p, const R* UL, const R* UR, const R* VL,
+                                               const R* VR, const int k, R* F, int& eflag) {
   using S = Shape<D, NP>;
-  constexpr int NFN = S::NFN, NF = S::NF, NV = S::NV, NW = S::NW;
-  const size_t ps = (size_t)NF * p.nfe;  // distance between the planes of two trace variables
-  const size_t oL = (size_t)(2 * k + 1) * p.nfe + (eL * NFN + fn), oR = (size_t)(2 * k) * p.nfe + (eR * NFN + fn);
-  const R* tL = Utr + oL;
-  const R* tR = Utr + oR;
-  R UL[NV], UR[NV], VL[NW], VR[NW];
-#pragma unroll
-  for (int v = 0; v < NV; ++v) {
-    UL[v] = tL[v * ps];
-    UR[v] = tR[v * ps];
-  }
+  constexpr int NV = S::NV;
   R pl, dl, pr, dr, il, ir;
   if constexpr (TraceComps<R>::extra > 0) {
-    il = tL[NV * ps];
-    ir = tR[NV * ps];
-    const R ql = tL[(NV + 1) * ps];
-    const R qr = tR[(NV + 1) * ps];
-    Eos<R>::both_q(p, UL[0], ql, pl, dl);
-    Eos<R>::both_q(p, UR[0], qr, pr, dr);
+    il = UL[NV];
+    ir = UR[NV];
+    Eos<R>::both_q(p, UL[0], UL[NV + 1], pl, dl);
+    Eos<R>::both_q(p, UR[0], UR[NV + 1], pr, dr);
   } else {
     Eos<R>::both(p, UL[0], pl, dl);
     Eos<R>::both(p, UR[0], pr, dr);
     il = R(1) / UL[0];
     ir = R(1) / UR[0];
   }
-#pragma unroll
-  for (int c = 0; c < NW; ++c) {
-    VL[c] = FVtr[oL + c * ps];
-    VR[c] = FVtr[oR + c * ps];
-  }
   eflag |= rho_flags(UL[0]) | rho_flags(UR[0]);
   if (!sound_ok(dl) || !sound_ok(dr)) eflag |= NSK_EBIT_SOUND;
   if (p.flux == NSK_FLUX_HLLC) {
     // HLLC of the barotropic system (rho, m) with p_alpha (see nsk_set_flux): the physical flux
     // of the upwind side K, plus S_K (U*_K - U_K) inside the star region; c is not transported
-    const R ul = UL[1 + k] * il, ur = UR[1 + k] * ir;
-    const R al = sqrt(dl), ar = sqrt(dr);
+    const R mL = comp1<D>(UL, k), mR = comp1<D>(UR, k);
+    const R ul = mL * il, ur = mR * ir;
+    const R al = sqrt_s(dl), ar = sqrt_s(dr);
     const R SL = fmin(ul - al, ur - ar), SR = fmax(ul + al, ur + ar);
     const R wl = UL[0] * (SL - ul), wr = UR[0] * (SR - ur);  // rho_K (S_K - u_K), wl < 0 < wr
     const R Ss = (pr - pl + fma(wl, ul, -(wr * ur))) / (wl - wr);
@@ -638,7 +804,7 @@ __device__ __forceinline__ void face_flux(const NskParams& p, const R* __restric
 #pragma unroll
     for (int v = 0; v < NV; ++v) uk[v] = left ? UL[v] : UR[v];
     const R ik = left ? il : ir, pk = left ? pl : pr;
-    const R mk = uk[1 + k];
+    const R mk = left ? mL : mR;
     F[0] = mk;
 #pragma unroll
     for (int a = 0; a < D; ++a) F[1 + a] = (a == k) ? fma(mk, uk[1 + a] * ik, pk) : mk * (uk[1 + a] * ik);
@@ -658,19 +824,54 @@ __device__ __forceinline__ void face_flux(const NskParams& p, const R* __restric
     F[D + 1] = -(VL[D] + VR[D]);
     return;
   }
-  const R lam_l = fabs(UL[1 + k] * il) + sqrt(dl), lam_r = fabs(UR[1 + k] * ir) + sqrt(dr);
+  const R mL = comp1<D>(UL, k), mR = comp1<D>(UR, k);  // normal momenta
+  const R lam_l = fabs(mL * il) + sqrt_s(dl), lam_r = fabs(mR * ir) + sqrt_s(dr);
   const R lam = lam_l > lam_r ? lam_l : lam_r;
-  F[0] = UL[1 + k] + UR[1 + k];
+  F[0] = mL + mR;
 #pragma unroll
   for (int a = 0; a < D; ++a) {
     const R ml = UL[1 + a] * il, mr = UR[1 + a] * ir;
-    const R sum = (a == k) ? fma(UL[1 + k], ml, pl) + fma(UR[1 + k], mr, pr) : fma(UL[1 + k], ml, UR[1 + k] * mr);
+    const R sum = (a == k) ? fma(mL, ml, pl) + fma(mR, mr, pr) : fma(mL, ml, mR * mr);
     F[1 + a] = sum - (VL[a] + VR[a]);
   }
   F[D + 1] = -(VL[D] + VR[D]);
 #pragma unroll
   for (int v = 0; v < NV - 1; ++v) F[v] = fma(-lam, UR[v] - UL[v], F[v]);
   if (p.c_diss) F[NV - 1] = fma(-lam, UR[NV - 1] - UL[NV - 1], F[NV - 1]);
+}
+
+
+// Numerical flux on the face between eL (its +1 side, slot 2k+1) and eR (its -1 side,
+// slot 2k), face node fn (HLLC instead of the Lax-Friedrichs flux when p.flux says so,
+// see nsk_set_flux):
+//   F* = (F^c_k(U_L) + F^c_k(U_R))/2 - lambda/2 (U_R - U_L) - (F^v_L + F^v_R)/2,
+//   lambda = max(|v_{L,k}| + sqrt(p_alpha'(rho_L)), |v_{R,k}| + sqrt(p_alpha'(rho_R)))
+// (local Lax-Friedrichs with the model II wave speeds, Eq. parabolic_eigenvalues_model2;
+// BR1 viscous flux). The jump term acts on rho and momentum (c has no convective flux)
+// unless c_diss is set. F receives 2 F* (the 1/2 is applied by the volume kernel's staged
+// surface operators; scaling by 2 is exact, so the residual is unchanged bit for bit).
+template <typename R, int D, int NP>
+__device__ __forceinline__ void face_flux(const NskParams& p, const R* __restrict__ Utr, const R* __restrict__ FVtr,
+                                          const int eL, const int eR, const int k, const int fn,
+                                          R* F, int& eflag) {
+  using S = Shape<D, NP>;
+  constexpr int NFN = S::NFN, NF = S::NF, NV = S::NV, NW = S::NW, NT = NV + TraceComps<R>::extra;
+  const size_t ps = (size_t)NF * p.nfe;  // distance between the planes of two trace variables
+  const size_t oL = (size_t)(2 * k + 1) * p.nfe + (eL * NFN + fn), oR = (size_t)(2 * k) * p.nfe + (eR * NFN + fn);
+  const R* tL = Utr + oL;
+  const R* tR = Utr + oR;
+  R UL[NT], UR[NT], VL[NW], VR[NW];
+#pragma unroll
+  for (int v = 0; v < NT; ++v) {
+    UL[v] = tL[v * ps];
+    UR[v] = tR[v * ps];
+  }
+#pragma unroll
+  for (int c = 0; c < NW; ++c) {
+    VL[c] = FVtr[oL + c * ps];
+    VR[c] = FVtr[oR + c * ps];
+  }
+  face_flux_vals<R, D, NP>(p, UL, UR, VL, VR, k, F, eflag);
 }
 
 // Fstar[v][k][E][nfn]: twice the flux on face (e, +k) at face node fn.
@@ -705,6 +906,140 @@ __host__ __device__ constexpr int volume_smem() {
   return G * D * S::NV * S::NPE + G * S::NF * S::NV * S::NFN + tab_smem<D, NP>() + 2;
 }
 
+// ---- parts of the volume kernel, shared by the stage kernels (so every schedule rounds alike) ----
+
+// direction operators for the residual (scaled by sc: 1 for a residual, dt in a Runge-Kutta
+// stage, where the contraction then yields dt R), then alpha sc and (alpha/beta) sc
+template <typename R, int D, int NP>
+__device__ __forceinline__ void volume_tables(const NskTab<R>& t, R* tb, const R sc) {
+  stage_tables<R, D, NP>(t, tb, sc, R(0.5) * sc);
+  if (threadIdx.x == 0) {
+    tb[tab_smem<D, NP>()] = t.alpha * sc;
+    tb[tab_smem<D, NP>() + 1] = t.ab * sc;
+  }
+}
+
+// The nodal fluxes F_k = F^c_k - F^v_k of node n (c flux without its factor -kappa/beta, which
+// is applied after the sum), stored with the lines of direction k contiguous:
+// sf[((le D + k) NV + v) NPE + face_node(n, k) NP + i_k]. u: the conservative variables, tau the
+// stress without mu and gc the gradient of c at the node.
+template <typename R, int D, int NP>
+__device__ __forceinline__ void volume_node_fluxes(const NskParams& p, const R* u, const R (&tau)[D][D],
+                                                   const R* gc, R* sf, const int le, const int n) {
+  using S = Shape<D, NP>;
+  constexpr int NPE = S::NPE, NW = S::NW, NV = S::NV;
+  const auto& t = TabSel<R>::get(p);
+  R inv, pa;
+  if constexpr (TraceComps<R>::extra > 0) {  // FP64: one division for 1/rho and 1/(3 - rho)
+    const R dd = rcp_s(u[0] * (R(3) - u[0]));
+    inv = (R(3) - u[0]) * dd;
+    pa = Eos<R>::pa_q(p, u[0], u[0] * dd);
+  } else {
+    inv = R(1) / u[0];
+    pa = Eos<R>::pa(p, u[0]);
+  }
+  const R mu = t.mu;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    // node n sits at position i_k of line face_node(n, k) in direction k
+    R* f = sf + ((le * D + k) * NV) * NPE + face_node<D, NP>(n, k) * NP + coord<NP>(n, k);
+    f[0] = u[1 + k];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      const R fc = (a == k) ? fma(u[1 + k], u[1 + a] * inv, pa) : u[1 + k] * (u[1 + a] * inv);
+      f[(1 + a) * NPE] = fma(-mu, tau[k][a], fc);
+    }
+    f[(D + 1) * NPE] = gc[k];  // the c flux -(kappa/beta) grad c, its factor applied after the sum
+  }
+}
+
+// The residual of node n from the staged nodal fluxes sf and face fluxes sfs (2 F*), plus the
+// sources, then: mode RHS, Rout = R; else K <- A K + dt R, U <- U + B K (u updated in place).
+template <typename R, int D, int NP, int G>
+__device__ __forceinline__ void volume_residual_update(const NskParams& p, const R* tb, const R* sf, const R* sfs,
+                                                       R* u, const R* gc, const R* kin, const int mode, const R A,
+                                                       const R B, R* __restrict__ U, R* __restrict__ K,
+                                                       R* __restrict__ Rout, const int g, const int le,
+                                                       const int n) {
+  using S = Shape<D, NP>;
+  constexpr int NPE = S::NPE, NFN = S::NFN, NW = S::NW, NV = S::NV, NF = S::NF;
+  const auto& t = TabSel<R>::get(p);
+  const size_t nn = (size_t)p.nne;  // distance between the planes of two nodal variables
+  // res_v = sum_k [ sum_j dk[i][j] F_k(j) - F*_{k,+} lpk[i] + F*_{k,-} lmk[i] ]  (2/h_k folded in),
+  // accumulated over k in ascending order
+  // (the c equation's volume part, a sum over grad c, is kept apart and scaled by
+  // -kappa/beta once)
+  R res[NV], volc = 0;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) res[v] = 0;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    const int i = coord<NP>(n, k), fn = face_node<D, NP>(n, k);
+    R dk[NP];
+#pragma unroll
+    for (int j = 0; j < NP; ++j) dk[j] = tb[(k * NP + i) * NP + j];
+    const R lpk = tb[D * NP * NP + k * NP + i], lmk = tb[D * NP * NP + D * NP + k * NP + i];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      R fl[NP];
+      load_line<R, NP>(sf + ((le * D + k) * NV + v) * NPE + fn * NP, fl);
+      R acc = v == NV - 1 ? volc : res[v];
+#pragma unroll
+      for (int j = 0; j < NP; ++j) acc = fma(dk[j], fl[j], acc);
+      const R fp = sfs[((le * NF + 2 * k + 1) * NV + v) * NFN + fn];
+      const R fm = sfs[((le * NF + 2 * k) * NV + v) * NFN + fn];
+      if (v == NV - 1) {
+        volc = acc;
+        res[v] = fma(fm, lmk, fma(-fp, lpk, res[v]));
+      } else {
+        res[v] = fma(fm, lmk, fma(-fp, lpk, acc));
+      }
+    }
+  }
+  res[NV - 1] = fma(-t.kb, volc, res[NV - 1]);
+  const R alpha = tb[tab_smem<D, NP>()], ab = tb[tab_smem<D, NP>() + 1];  // scaled like the operators
+#pragma unroll
+  for (int a = 0; a < D; ++a) res[1 + a] = fma(alpha * u[0], gc[a], res[1 + a]);
+  res[D + 1] = fma(ab, u[0] - u[D + 1], res[D + 1]);
+
+  if (mode == NSK_MODE_RHS) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Rout[v * nn + g] = res[v];
+  } else {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const R kv = fma(A, kin[v], res[v]);  // res holds dt R
+      K[v * nn + g] = kv;
+      u[v] = fma(B, kv, u[v]);
+      U[v * nn + g] = u[v];
+    }
+  }
+}
+
+// The traces of the element's (new) state u on its own faces into UtrNext, through shared
+// memory su ([G][NV][NPE]); starts and ends with a block barrier.
+template <typename R, int D, int NP, int G>
+__device__ __forceinline__ void volume_write_traces(const NskParams& p, const R* u, R* su, R* __restrict__ UtrNext,
+                                                    const bool valid, const int le, const int n, const int e) {
+  using S = Shape<D, NP>;
+  constexpr int NPE = S::NPE, NFN = S::NFN, NV = S::NV, NF = S::NF;
+  __syncthreads();  // su may alias buffers still being read
+  if (valid) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) su[(le * NV + v) * NPE + n] = u[v];
+  }
+  __syncthreads();
+  if (valid) {
+#pragma unroll
+    for (int r = 0; r < (NF * NFN + NPE - 1) / NPE; ++r) {
+      const int it = n + r * NPE;
+      if (it >= NF * NFN) break;
+      prolong_trace<R, D, NP>(p, su + le * NV * NPE, NPE, UtrNext, e, it / NFN, it % NFN);
+    }
+  }
+  __syncthreads();
+}
+
 // Weak-form volume integral and surface lifting (Eq. weakformulation),
 //   R_i = sum_k (2/h_k) [ sum_j (w_j/w_i) l_i'(xi_j) F_k(U_j, Q_j) - (F*_{k,+} l_i(1) - F*_{k,-} l_i(-1)) / w_i ] + S_i,
 // F_k = F^c_k - F^v_k, S = (0, alpha rho grad c, (alpha/beta)(rho - c)); then
@@ -717,14 +1052,14 @@ __host__ __device__ constexpr int volume_smem() {
 // UtrNext (optional): the traces of the element's new state (LSRK) or of its state (RHS)
 // are written there from shared memory, so the next stage needs no prolongation pass.
 // It must not alias Utr when FUSED (neighbours still read Utr).
-template <typename R, int D, int NP, int G, bool FUSED>
+template <typename R, int D, int NP, int G, bool FUSED, bool QF = true>
 __device__ __forceinline__ void volume_group(const NskParams& p, R* __restrict__ U, const R* __restrict__ Q,
                                              const R* __restrict__ Fstar, const R* __restrict__ Utr,
                                              const R* __restrict__ FVtr, R* __restrict__ K, R* __restrict__ Rout,
                                              const int mode, const R A, const R B, const R dt, const long long e0,
                                              R* sm, int& eflag, R* __restrict__ UtrNext = nullptr) {
   using S = Shape<D, NP>;
-  constexpr int NPE = S::NPE, NFN = S::NFN, NW = S::NW, NV = S::NV, NQ = S::NQ, NF = S::NF;
+  constexpr int NPE = S::NPE, NFN = S::NFN, NV = S::NV, NQ = S::NQ, NF = S::NF;
   R* sf = sm;                          // [G][D][NV][NFN][NP] fluxes F_k at the nodes, lines in k contiguous
   R* sfs = sm + G * D * NV * NPE;      // [G][NF][NV][NFN] fluxes of the element's faces
   R* tb = sfs + G * NF * NV * NFN;     // direction operators, then the source coefficients
@@ -776,13 +1111,8 @@ __device__ __forceinline__ void volume_group(const NskParams& p, R* __restrict__
     }
     cp_async_commit();
   }
-  const R sc = mode == NSK_MODE_RHS ? R(1) : dt;  // the operator scale
-  stage_tables<R, D, NP>(t, tb, sc, R(0.5) * sc);
-  if (threadIdx.x == 0) {
-    tb[tab_smem<D, NP>()] = t.alpha * sc;
-    tb[tab_smem<D, NP>() + 1] = t.ab * sc;
-  }
-  R u[NV], q[NQ], kin[NV];
+  volume_tables<R, D, NP>(t, tb, mode == NSK_MODE_RHS ? R(1) : dt);
+  R u[NV], kin[NV], tau[D][D], gc[D];
   if (valid) {
 #pragma unroll
     for (int v = 0; v < NV; ++v) u[v] = U[v * nn + g];
@@ -790,43 +1120,15 @@ __device__ __forceinline__ void volume_group(const NskParams& p, R* __restrict__
 #pragma unroll
       for (int v = 0; v < NV; ++v) kin[v] = K[v * nn + g];
     }
-#pragma unroll
-    for (int c = 0; c < NQ; ++c) q[c] = Q[c * nn + g];
-    R inv, pa;
-    if constexpr (TraceComps<R>::extra > 0) {  // FP64: one division for 1/rho and 1/(3 - rho)
-      const R dd = R(1) / (u[0] * (R(3) - u[0]));
-      inv = (R(3) - u[0]) * dd;
-      pa = Eos<R>::pa_q(p, u[0], u[0] * dd);
+    if constexpr (QF) {  // the lifting stored the viscous form
+      visc_load<R, D>(Q, nn, g, tau, gc);
     } else {
-      inv = R(1) / u[0];
-      pa = Eos<R>::pa(p, u[0]);
+      R q[NQ];
+#pragma unroll
+      for (int c = 0; c < NQ; ++c) q[c] = Q[c * nn + g];
+      visc_of<R, D>(q, tau, gc);
     }
-    R div = 0;
-#pragma unroll
-    for (int a = 0; a < D; ++a) div += q[a * NW + a];
-    const R mu = t.mu;
-    R tau[D][D];  // symmetric: each off-diagonal sum once
-#pragma unroll
-    for (int k = 0; k < D; ++k) {
-#pragma unroll
-      for (int a = k; a < D; ++a) {
-        const R sum = q[k * NW + a] + q[a * NW + k];
-        tau[k][a] = (a == k) ? fma(-R(2.0 / 3.0), div, sum) : sum;
-        tau[a][k] = tau[k][a];
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < D; ++k) {
-      // node n sits at position i_k of line face_node(n, k) in direction k
-      R* f = sf + ((le * D + k) * NV) * NPE + face_node<D, NP>(n, k) * NP + coord<NP>(n, k);
-      f[0] = u[1 + k];
-#pragma unroll
-      for (int a = 0; a < D; ++a) {
-        const R fc = (a == k) ? fma(u[1 + k], u[1 + a] * inv, pa) : u[1 + k] * (u[1 + a] * inv);
-        f[(1 + a) * NPE] = fma(-mu, tau[k][a], fc);
-      }
-      f[(D + 1) * NPE] = q[k * NW + D];  // the c flux -(kappa/beta) grad c, its factor applied after the sum
-    }
+    volume_node_fluxes<R, D, NP>(p, u, tau, gc, sf, le, n);
     if constexpr (FUSED) {
       const ElemIdx ex = elem_idx<D>(p, e);
       for (int it = n; it < NF * NFN; it += NPE) {
@@ -844,75 +1146,250 @@ __device__ __forceinline__ void volume_group(const NskParams& p, R* __restrict__
   if constexpr (!FUSED) cp_async_wait_all();
   __syncthreads();
 
-  if (valid) {
-    // res_v = sum_k [ sum_j dk[i][j] F_k(j) - F*_{k,+} lpk[i] + F*_{k,-} lmk[i] ]  (2/h_k folded in),
-    // accumulated over k in ascending order
-    // (the c equation's volume part, a sum over grad c, is kept apart and scaled by
-    // -kappa/beta once)
-    R res[NV], volc = 0;
-#pragma unroll
-    for (int v = 0; v < NV; ++v) res[v] = 0;
-#pragma unroll
-    for (int k = 0; k < D; ++k) {
-      const int i = coord<NP>(n, k), fn = face_node<D, NP>(n, k);
-      R dk[NP];
-#pragma unroll
-      for (int j = 0; j < NP; ++j) dk[j] = tb[(k * NP + i) * NP + j];
-      const R lpk = tb[D * NP * NP + k * NP + i], lmk = tb[D * NP * NP + D * NP + k * NP + i];
-#pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        R fl[NP];
-        load_line<R, NP>(sf + ((le * D + k) * NV + v) * NPE + fn * NP, fl);
-        R acc = v == NV - 1 ? volc : res[v];
-#pragma unroll
-        for (int j = 0; j < NP; ++j) acc = fma(dk[j], fl[j], acc);
-        const R fp = sfs[((le * NF + 2 * k + 1) * NV + v) * NFN + fn];
-        const R fm = sfs[((le * NF + 2 * k) * NV + v) * NFN + fn];
-        if (v == NV - 1) {
-          volc = acc;
-          res[v] = fma(fm, lmk, fma(-fp, lpk, res[v]));
-        } else {
-          res[v] = fma(fm, lmk, fma(-fp, lpk, acc));
-        }
-      }
-    }
-    res[NV - 1] = fma(-t.kb, volc, res[NV - 1]);
-    const R alpha = tb[tab_smem<D, NP>()], ab = tb[tab_smem<D, NP>() + 1];  // scaled like the operators
-#pragma unroll
-    for (int a = 0; a < D; ++a) res[1 + a] = fma(alpha * u[0], q[a * NW + D], res[1 + a]);
-    res[D + 1] = fma(ab, u[0] - u[D + 1], res[D + 1]);
+  if (valid) volume_residual_update<R, D, NP, G>(p, tb, sf, sfs, u, gc, kin, mode, A, B, U, K, Rout, g, le, n);
+  if (UtrNext != nullptr)  // uniform over the block
+    volume_write_traces<R, D, NP, G>(p, u, sm, UtrNext, valid, le, n, e);
+  else
+    __syncthreads();  // the caller may reuse shared memory
+}
 
-    if (mode == NSK_MODE_RHS) {
+// ---- lean stage (schedule fused_face = 2): two launches, no gradients or face fluxes in HBM ----
+// Of everything the lifting computes, only the face-normal viscous flux F^v of an element's own
+// faces is needed by another element (its face neighbour's flux), so the lean lifting writes
+// just those traces; the lean volume kernel then recomputes the element's lifting on chip from
+// its state and the neighbours' stored state traces, evaluates its 2d faces' fluxes with the
+// neighbours' F^v traces, and does the volume integral, sources and update. Each element's own
+// traces are prolonged on chip from its staged state. Every value is computed by the same
+// functions as in the other schedules, so the results are the same bit for bit.
+
+// shared memory (units of R) of lift_lean_group: the lifting's buffers and tables, then the
+// element's staged state [G][NV][NPE]
+template <typename R, int D, int NP, int G>
+__host__ __device__ constexpr int lift_lean_smem() {
+  return lift_smem<R, D, NP, G>() + G * Shape<D, NP>::NV * Shape<D, NP>::NPE;
+}
+
+template <typename R, int D, int NP, int G>
+__device__ __forceinline__ void lift_lean_group(const NskParams& p, const R* __restrict__ U,
+                                                const R* __restrict__ Utr, R* __restrict__ FVtr, const long long e0,
+                                                R* sm, int& eflag) {
+  using S = Shape<D, NP>;
+  constexpr int NPE = S::NPE, NFN = S::NFN, NW = S::NW, NF = S::NF, NQ = S::NQ, NV = S::NV;
+  constexpr int NT = NV + TraceComps<R>::extra;
+  constexpr bool LINES = lift_lines<R, D, NP, G>();
+  constexpr int NCOPY = LINES ? D : 1, SWS = lift_slot_stride<D, NP>();
+  R* sw = sm;                                   // [G][NCOPY][NW][NPE] primitive variables
+  R* sws = sm + G * NCOPY * NW * NPE;           // [G][NF][SWS] 2 w* on the faces
+  R* tb = sm + lift_work_smem<R, D, NP, G>();   // direction operators
+  R* su = tb + tab_smem<D, NP>();               // [G][NV][NPE] the element's state
+  const auto& t = TabSel<R>::get(p);
+  const int le = threadIdx.x / NPE, n = threadIdx.x % NPE;
+  const int e = (int)e0 + le;
+  const bool valid = le < G && e < p.E;
+  const size_t nn = (size_t)p.nne;
+  const size_t pl = (size_t)NF * p.nfe;
+  const int g = e * NPE + n;
+
+  stage_tables<R, D, NP>(t, tb, R(1), R(0.5));
+  if (valid) {
 #pragma unroll
-      for (int v = 0; v < NV; ++v) Rout[v * nn + g] = res[v];
-    } else {
+    for (int v = 0; v < NV; ++v) su[(le * NV + v) * NPE + n] = U[v * nn + g];
+  }
+  __syncthreads();
+  if (valid) {
+    const R* ue = su + le * NV * NPE;
+    lift_store_w<R, D, NP, G>(ue + n, NPE, sw, le, n, eflag);
+    const ElemIdx ex = elem_idx<D>(p, e);
 #pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        const R kv = fma(A, kin[v], res[v]);  // res holds dt R
-        K[v * nn + g] = kv;
-        u[v] = fma(B, kv, u[v]);
-        U[v * nn + g] = u[v];
-      }
+    for (int r = 0; r < (NF * NFN + NPE - 1) / NPE; ++r) {
+      const int it = n + r * NPE;
+      if (it >= NF * NFN) break;
+      const int slot = it / NFN, fn = it % NFN, k = slot >> 1, s = slot & 1;
+      const int en = nbr_of(p, ex, k, s ? 1 : -1);
+      const R* tn = Utr + (size_t)(2 * k + (1 - s)) * p.nfe + (en * NFN + fn);
+      R uo[NT], un[NT];
+#pragma unroll
+      for (int v = 0; v < NT; ++v) un[v] = tn[v * pl];
+      trace_vals<R, D, NP>(p, ue, NPE, slot, fn, uo);
+      lift_wstar<R, D, NFN, NV>(uo, un, sws + (le * NF + slot) * SWS + fn, eflag);
     }
   }
-  __syncthreads();  // the caller may reuse shared memory
-  if (UtrNext != nullptr) {  // uniform over the block
-    R* su = sm;               // [G][NV][NPE] the element's (new) state
+  __syncthreads();
+  R q[NQ], tau[D][D], gc[D];
+  if (valid) {
+    lift_q<R, D, NP, G>(tb, sw, sws, le, n, q);
+    visc_of<R, D>(q, tau, gc);
+  }
+  __syncthreads();
+  lift_fv_traces<R, D, NP, G>(p, tau, gc, sm, valid, le, n, e, FVtr, nullptr);
+}
+
+// shared memory layout (units of R) of volume_lean_group
+template <typename R, int D, int NP, int G>
+struct LeanSmem {
+  using S = Shape<D, NP>;
+  static constexpr int NT = S::NV + TraceComps<R>::extra;
+  static constexpr bool LINES = lift_lines<R, D, NP, G>();
+  static constexpr int NCOPY = LINES ? D : 1;
+  static constexpr int so = 0;                                  // [G][NF][NT][NFN] own state traces
+  static constexpr int sn = so + G * S::NF * NT * S::NFN;       // [G][NF][NT][NFN] the neighbours' traces
+  static constexpr int fo = sn + G * S::NF * NT * S::NFN;       // [G][NF][NW][NFN] own F^v traces
+  static constexpr int fnb = fo + G * S::NF * S::NW * S::NFN;   // [G][NF][NW][NFN] the neighbours' F^v traces
+  static constexpr int lift_work = G * NCOPY * S::NW * S::NPE + G * S::NF * lift_slot_stride<D, NP>();
+  static constexpr int vol_work = G * D * S::NV * S::NPE;
+  static constexpr int fv_work = G * D * S::NW * S::NPE;
+  static constexpr int wmax = lift_work > vol_work ? (lift_work > fv_work ? lift_work : fv_work)
+                                                   : (vol_work > fv_work ? vol_work : fv_work);
+  static constexpr int work = fnb + G * S::NF * S::NW * S::NFN;  // lifting, then F^v at nodes, then sf
+  static constexpr int sfs = work + ((wmax + 3) & ~3);          // [G][NF][NV][NFN] 2 F* of the faces
+  static constexpr int t1 = sfs + G * S::NF * S::NV * S::NFN;   // lifting operators
+  static constexpr int t2 = t1 + tab_smem<D, NP>();             // residual operators and source factors
+  static constexpr int su = ((t2 + tab_smem<D, NP>() + 2) + 3) & ~3;  // [G][NV][NPE] the element's state
+  static constexpr int total = su + G * S::NV * S::NPE;
+};
+
+template <typename R, int D, int NP, int G>
+__host__ __device__ constexpr int volume_lean_smem() {
+  return LeanSmem<R, D, NP, G>::total;
+}
+
+// Lean volume kernel body (see above): lifting on chip, face fluxes from the neighbours' state
+// and F^v traces, volume integral + surface lifting + sources + update (modes RHS or LSRK), and
+// the traces of the new state into UtrNext (optional; must not alias Utr).
+template <typename R, int D, int NP, int G>
+__device__ __forceinline__ void volume_lean_group(const NskParams& p, R* __restrict__ U, const R* __restrict__ Utr,
+                                                  const R* __restrict__ FVtr, R* __restrict__ K, R* __restrict__ Rout,
+                                                  const int mode, const R A, const R B, const R dt,
+                                                  const long long e0, R* sm, int& eflag, R* __restrict__ UtrNext) {
+  using S = Shape<D, NP>;
+  using L = LeanSmem<R, D, NP, G>;
+  constexpr int NPE = S::NPE, NFN = S::NFN, NW = S::NW, NV = S::NV, NQ = S::NQ, NF = S::NF, NT = L::NT;
+  constexpr int SWS = lift_slot_stride<D, NP>();
+  R* so = sm + L::so;
+  R* sn = sm + L::sn;
+  R* fo = sm + L::fo;
+  R* fnb = sm + L::fnb;
+  R* work = sm + L::work;
+  R* sw = work;                                 // lifting: [G][NCOPY][NW][NPE]
+  R* sws = work + G * L::NCOPY * NW * NPE;       //          [G][NF][SWS]
+  R* sfs = sm + L::sfs;
+  R* t1 = sm + L::t1;
+  R* t2 = sm + L::t2;
+  R* su = sm + L::su;
+  const auto& t = TabSel<R>::get(p);
+  const int le = threadIdx.x / NPE, n = threadIdx.x % NPE;
+  const int e = (int)e0 + le;
+  const bool valid = le < G && e < p.E;
+  const size_t nn = (size_t)p.nne;
+  const size_t pl = (size_t)NF * p.nfe;
+  const int g = e * NPE + n;
+
+  // the neighbours' state and F^v traces of every face, global -> shared asynchronously (16 bytes
+  // at a time when a face's NFN values fill whole 16-byte units; the offsets are then multiples
+  // of 16 bytes), stored under the element's own face slot
+  {
+    constexpr int W = (NFN * (int)sizeof(R)) % 16 == 0 ? 16 / (int)sizeof(R) : 1;
+    constexpr int NFW = NFN / W;
     if (valid) {
-#pragma unroll
-      for (int v = 0; v < NV; ++v) su[(le * NV + v) * NPE + n] = u[v];
-    }
-    __syncthreads();
-    if (valid) {
-#pragma unroll
-      for (int r = 0; r < (NF * NFN + NPE - 1) / NPE; ++r) {
-        const int it = n + r * NPE;
-        if (it >= NF * NFN) break;
-        prolong_trace<R, D, NP>(p, su + le * NV * NPE, NPE, UtrNext, e, it / NFN, it % NFN);
+      const ElemIdx ex = elem_idx<D>(p, e);
+      for (int it = n; it < NF * (NT + NW) * NFW; it += NPE) {
+        const int piece = it % NFW, c = (it / NFW) % (NT + NW), slot = it / ((NT + NW) * NFW);
+        const int k = slot >> 1, s = slot & 1;
+        const int en = nbr_of(p, ex, k, s ? 1 : -1);
+        const size_t src = (size_t)(2 * k + (1 - s)) * p.nfe + (en * NFN + piece * W);
+        R* dst;
+        const R* srcp;
+        if (c < NT) {
+          dst = sn + ((le * NF + slot) * NT + c) * NFN + piece * W;
+          srcp = Utr + src + c * pl;
+        } else {
+          dst = fnb + ((le * NF + slot) * NW + (c - NT)) * NFN + piece * W;
+          srcp = FVtr + src + (c - NT) * pl;
+        }
+        if constexpr (W > 1)
+          cp_async_16(dst, srcp);
+        else
+          cp_async_elem(dst, srcp);
       }
     }
-    __syncthreads();
+    cp_async_commit();
   }
+  stage_tables<R, D, NP>(t, t1, R(1), R(0.5));
+  volume_tables<R, D, NP>(t, t2, mode == NSK_MODE_RHS ? R(1) : dt);
+  R u[NV], kin[NV], tau[D][D], gc[D];
+  if (valid) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      u[v] = U[v * nn + g];
+      su[(le * NV + v) * NPE + n] = u[v];
+    }
+    if (mode != NSK_MODE_RHS) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) kin[v] = K[v * nn + g];
+    }
+  }
+  __syncthreads();
+  if (valid) {  // own traces on chip, and the primitive variables for the lifting
+    const R* ue = su + le * NV * NPE;
+    lift_store_w<R, D, NP, G>(ue + n, NPE, sw, le, n, eflag);
+    for (int it = n; it < NF * NFN; it += NPE) {
+      const int slot = it / NFN, fn = it % NFN;
+      R uo[NT];
+      trace_vals<R, D, NP>(p, ue, NPE, slot, fn, uo);
+#pragma unroll
+      for (int v = 0; v < NT; ++v) so[((le * NF + slot) * NT + v) * NFN + fn] = uo[v];
+    }
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  if (valid) {  // 2 w* of every face node
+    for (int it = n; it < NF * NFN; it += NPE) {
+      const int slot = it / NFN, fn = it % NFN;
+      R uo[NT], un[NT];
+#pragma unroll
+      for (int v = 0; v < NT; ++v) {
+        uo[v] = so[((le * NF + slot) * NT + v) * NFN + fn];
+        un[v] = sn[((le * NF + slot) * NT + v) * NFN + fn];
+      }
+      lift_wstar<R, D, NFN, NV>(uo, un, sws + (le * NF + slot) * SWS + fn, eflag);
+    }
+  }
+  __syncthreads();
+  if (valid) {
+    R q[NQ];
+    lift_q<R, D, NP, G>(t1, sw, sws, le, n, q);
+    visc_of<R, D>(q, tau, gc);
+  }
+  __syncthreads();
+  lift_fv_traces<R, D, NP, G, true>(p, tau, gc, work, valid, le, n, e, nullptr, fo);  // ends with a barrier
+  if (valid) {
+    for (int it = n; it < NF * NFN; it += NPE) {  // the fluxes of the element's faces
+      const int slot = it / NFN, fn = it % NFN, k = slot >> 1;
+      // +k face (odd slot): the element is the left state, its neighbour the right one
+      const bool plus = (slot & 1) != 0;
+      R UL[NT], UR[NT], VL[NW], VR[NW], F[NV];
+#pragma unroll
+      for (int v = 0; v < NT; ++v) {
+        const R o = so[((le * NF + slot) * NT + v) * NFN + fn], x = sn[((le * NF + slot) * NT + v) * NFN + fn];
+        UL[v] = plus ? o : x;
+        UR[v] = plus ? x : o;
+      }
+#pragma unroll
+      for (int c = 0; c < NW; ++c) {
+        const R o = fo[((le * NF + slot) * NW + c) * NFN + fn], x = fnb[((le * NF + slot) * NW + c) * NFN + fn];
+        VL[c] = plus ? o : x;
+        VR[c] = plus ? x : o;
+      }
+      face_flux_vals<R, D, NP>(p, UL, UR, VL, VR, k, F, eflag);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) sfs[((le * NF + slot) * NV + v) * NFN + fn] = F[v];
+    }
+    volume_node_fluxes<R, D, NP>(p, u, tau, gc, work, le, n);
+  }
+  __syncthreads();
+  if (valid) volume_residual_update<R, D, NP, G>(p, t2, work, sfs, u, gc, kin, mode, A, B, U, K, Rout, g, le, n);
+  if (UtrNext != nullptr)  // uniform over the block
+    volume_write_traces<R, D, NP, G>(p, u, su, UtrNext, valid, le, n, e);
 }
 
 // ---- stand-alone stage kernels ---------------------------------------------
@@ -941,13 +1418,15 @@ __host__ __device__ constexpr int lift_min_blocks() {
   return sizeof(R) == 4 ? blocks_in_warps<TPB>(48) : 1;
 }
 
-template <typename R, int D, int NP, int G>
+// QF: store the viscous form for a volume kernel (residual and Runge-Kutta stages), else the
+// gradients (a lifting-only stage)
+template <typename R, int D, int NP, int G, bool QF>
 __global__ void __launch_bounds__(G * Shape<D, NP>::NPE, (lift_min_blocks<R, G * Shape<D, NP>::NPE>()))
     k_lift(const NskParams p, const R* __restrict__ U, const R* __restrict__ Utr, R* __restrict__ Q,
            R* __restrict__ FVtr, int* __restrict__ err) {
   __shared__ __align__(16) R sm[lift_smem<R, D, NP, G>()];
   int eflag = 0;
-  lift_group<R, D, NP, G>(p, U, Utr, Q, FVtr, (long long)blockIdx.x * G, sm, eflag);
+  lift_group<R, D, NP, G, 0, QF>(p, U, Utr, Q, FVtr, (long long)blockIdx.x * G, sm, eflag);
   if (eflag) atomicOr(err, eflag);
 }
 
@@ -980,6 +1459,32 @@ __global__ void __launch_bounds__(G * Shape<D, NP>::NPE, (volume_min_blocks<R, G
   int eflag = 0;
   volume_group<R, D, NP, G, FUSED>(p, U, Q, Fstar, Utr, FVtr, K, Rout, mode, A, B, dt, (long long)blockIdx.x * G,
                                    sm, eflag, UtrNext);
+  if (eflag) atomicOr(err, eflag);
+}
+
+// lean schedule kernels (dynamic shared memory: their buffers can exceed the 48 KB static limit)
+template <typename R, int D, int NP, int G>
+__global__ void __launch_bounds__(G * Shape<D, NP>::NPE)
+    k_lift_lean(const NskParams p, const R* __restrict__ U, const R* __restrict__ Utr, R* __restrict__ FVtr,
+                int* __restrict__ err) {
+  extern __shared__ __align__(16) unsigned char lean_smem_raw[];
+  R* sm = reinterpret_cast<R*>(lean_smem_raw);
+  int eflag = 0;
+  lift_lean_group<R, D, NP, G>(p, U, Utr, FVtr, (long long)blockIdx.x * G, sm, eflag);
+  if (eflag) atomicOr(err, eflag);
+}
+
+template <typename R, int D, int NP, int G>
+__global__ void __launch_bounds__(G * Shape<D, NP>::NPE)
+    k_volume_lean(const NskParams p, R* __restrict__ U, const R* __restrict__ Utr, const R* __restrict__ FVtr,
+                  R* __restrict__ K, R* __restrict__ Rout, const int mode, const R A, const R B,
+                  const double* __restrict__ dtp, const R dtv, int* __restrict__ err, R* __restrict__ UtrNext) {
+  extern __shared__ __align__(16) unsigned char lean_smem_raw[];
+  R* sm = reinterpret_cast<R*>(lean_smem_raw);
+  const R dt = dtp ? (R)*dtp : dtv;
+  int eflag = 0;
+  volume_lean_group<R, D, NP, G>(p, U, Utr, FVtr, K, Rout, mode, A, B, dt, (long long)blockIdx.x * G, sm, eflag,
+                                 UtrNext);
   if (eflag) atomicOr(err, eflag);
 }
 
@@ -1119,7 +1624,12 @@ int launch_stage_g(const NskParams& p, const NskBuffers& b, const NskLaunch& l, 
   }
   if (l.ev) cudaEventRecord(l.ev[1], s);
   const unsigned eb = (unsigned)((p.E + G - 1) / G);
-  k_lift<R, D, NP, G><<<eb, G * S::NPE, 0, s>>>(p, (const R*)b.U, (const R*)b.Utr, (R*)b.Q, (R*)b.FVtr, b.err);
+  if (l.mode == NSK_MODE_LIFT)
+    k_lift<R, D, NP, G, false><<<eb, G * S::NPE, 0, s>>>(p, (const R*)b.U, (const R*)b.Utr, (R*)b.Q, (R*)b.FVtr,
+                                                          b.err);
+  else
+    k_lift<R, D, NP, G, true><<<eb, G * S::NPE, 0, s>>>(p, (const R*)b.U, (const R*)b.Utr, (R*)b.Q, (R*)b.FVtr,
+                                                         b.err);
   if (l.ev) cudaEventRecord(l.ev[2], s);
   ++nl;
   if (l.mode != NSK_MODE_LIFT) {
@@ -1139,10 +1649,48 @@ int launch_stage_g(const NskParams& p, const NskBuffers& b, const NskLaunch& l, 
   return nl;
 }
 
-// schedule: tpb in {128, 256} (elements per block = tpb / nodes per element), fused face flux or not
+// the lean schedule's two launches (a residual-free lifting stage, mode LIFT, takes the
+// separate schedule's lifting kernel, which stores the gradients)
+template <typename R, int D, int NP, int G>
+int launch_stage_lean(const NskParams& p, const NskBuffers& b, const NskLaunch& l, cudaStream_t s) {
+  using S = Shape<D, NP>;
+  if (l.mode == NSK_MODE_LIFT) return launch_stage_g<R, D, NP, G, false>(p, b, l, s);
+  constexpr int smem_lift = (int)sizeof(R) * lift_lean_smem<R, D, NP, G>();
+  constexpr int smem_vol = (int)sizeof(R) * volume_lean_smem<R, D, NP, G>();
+  static const bool attr_ok =
+      cudaFuncSetAttribute(k_lift_lean<R, D, NP, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_lift) ==
+          cudaSuccess &&
+      cudaFuncSetAttribute(k_volume_lean<R, D, NP, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_vol) ==
+          cudaSuccess;
+  if (!attr_ok) return NSK_ERR_CUDA;
+  int nl = 0;
+  if (l.ev) cudaEventRecord(l.ev[0], s);
+  if (!l.traces_ready) {
+    k_prolong<R, D, NP><<<dim3(grid_for(p.nfe, 256), S::NF), 256, 0, s>>>(p, (const R*)b.U, (R*)b.Utr);
+    ++nl;
+  }
+  if (l.ev) cudaEventRecord(l.ev[1], s);
+  const unsigned eb = (unsigned)((p.E + G - 1) / G);
+  k_lift_lean<R, D, NP, G><<<eb, G * S::NPE, smem_lift, s>>>(p, (const R*)b.U, (const R*)b.Utr, (R*)b.FVtr, b.err);
+  ++nl;
+  if (l.ev) cudaEventRecord(l.ev[2], s);
+  if (l.ev) cudaEventRecord(l.ev[3], s);
+  k_volume_lean<R, D, NP, G><<<eb, G * S::NPE, smem_vol, s>>>(p, (R*)b.U, (const R*)b.Utr, (const R*)b.FVtr, (R*)b.K,
+                                                              (R*)l.Rout, l.mode, (R)l.A, (R)l.B, l.dt_dev,
+                                                              (R)l.dt_val, b.err, (R*)l.utr_next);
+  ++nl;
+  if (l.ev) cudaEventRecord(l.ev[4], s);
+  if (cudaGetLastError() != cudaSuccess) return NSK_ERR_CUDA;
+  return nl;
+}
+
+// schedule: tpb in {128, 256} (elements per block = tpb / nodes per element); face fluxes in
+// their own pass (fused_face 0), inside the volume kernel (1), or the lean two-launch stage (2)
 template <typename R, int D, int NP>
 int launch_stage(const NskParams& p, const NskBuffers& b, const NskLaunch& l, cudaStream_t s) {
   constexpr int G128 = group_for<D, NP>(128), G256 = group_for<D, NP>(256);
+  if (l.fused_face == 2)
+    return l.tpb == 128 ? launch_stage_lean<R, D, NP, G128>(p, b, l, s) : launch_stage_lean<R, D, NP, G256>(p, b, l, s);
   const bool fused = l.fused_face != 0;
   if (l.tpb == 128)
     return fused ? launch_stage_g<R, D, NP, G128, true>(p, b, l, s) : launch_stage_g<R, D, NP, G128, false>(p, b, l, s);

@@ -82,6 +82,7 @@ SIGNATURES = {
     "nsk_batch_set_timeout": (C.c_int, [C.c_void_p, C.c_double]),
     "nsk_test_hook_block_batch_barrier": (C.c_int, [C.c_void_p]),
     "nsk_test_hook_tc_grid_cap": (C.c_int, [C.c_int]),
+    "nsk_test_hook_math": (C.c_int, [C.c_int, C.c_void_p, C.c_void_p, C.c_longlong, C.c_void_p]),
     "nsk_batch_destroy": (None, [C.c_void_p]),
     "nsk_gemm_bf16": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                 C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_int,
@@ -198,6 +199,14 @@ def nsk_rhs_static_scratch(dim, nelem, lo, hi, N, node_type, T, kappa, alpha, be
 def _test_hook_tc_grid_cap(max_ctas):
     """Test-only (include/nsk_test_hooks.h): cap the persistent tensor-core grids (0: no cap)."""
     _check(load_library().nsk_test_hook_tc_grid_cap(int(max_ctas)), "nsk_test_hook_tc_grid_cap")
+
+
+def _test_hook_math(fn, x, y, stream=None):
+    """Test-only (include/nsk_test_hooks.h): the stage kernels' FP64 reciprocal (fn 0) or square
+    root (fn 1) of the float64 CUDA tensor x into y."""
+    _check(load_library().nsk_test_hook_math(int(fn), C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()),
+                                             int(x.numel()), C.c_void_p(stream) if stream else None),
+           "nsk_test_hook_math")
 
 
 def measure_fma_rate(precision=NSK_FP64, iters=1 << 16, stream=None):
@@ -356,19 +365,23 @@ class Solver:
         _check(load_library().nsk_diagnostics(self.ctx, C.byref(m), C.byref(e), C.byref(l2)), "nsk_diagnostics")
         return m.value, e.value, l2.value
 
-    def set_schedule(self, tpb=256, fused_face=False):
-        _check(load_library().nsk_set_schedule(self.ctx, tpb, int(bool(fused_face))), "nsk_set_schedule")
+    def set_schedule(self, tpb=256, fused_face=0):
+        """fused_face: 0 separate face pass, 1 (or True) face fluxes in the volume kernel, 2 the
+        lean two-launch stage (lifting recomputed on chip by the volume kernel)."""
+        _check(load_library().nsk_set_schedule(self.ctx, tpb, int(fused_face)), "nsk_set_schedule")
 
     def get_schedule(self):
+        """(tpb, fused_face) with fused_face 0, 1 or 2 (see set_schedule)."""
         t, f = C.c_int(), C.c_int()
         _check(load_library().nsk_get_schedule(self.ctx, C.byref(t), C.byref(f)), "nsk_get_schedule")
-        return t.value, bool(f.value)
+        return t.value, f.value
 
     def autotune(self):
-        """Time the four stage schedules on the current state; keep and return the fastest."""
+        """Time the stage schedules on the current state; keep and return the fastest
+        (tpb, fused_face, ms)."""
         t, f, ms = C.c_int(), C.c_int(), C.c_double()
         _check(load_library().nsk_autotune(self.ctx, C.byref(t), C.byref(f), C.byref(ms)), "nsk_autotune")
-        return t.value, bool(f.value), ms.value
+        return t.value, f.value, ms.value
 
     # -- learned c-closure --
     @property
@@ -454,15 +467,16 @@ class Batch:
 
     def set_schedule(self, tpb=256, fused_face=False, persistent=1):
         """persistent: 1 cooperative persistent kernel, 0 one launch per phase, 2 each instance's
-        own stage launches (True/False map to 1/0)."""
-        _check(load_library().nsk_batch_set_schedule(self.h, tpb, int(bool(fused_face)), int(persistent)),
+        own stage launches (True/False map to 1/0); fused_face 0 or 1, or 2 (the lean stage) with
+        the instance schedule."""
+        _check(load_library().nsk_batch_set_schedule(self.h, tpb, int(fused_face), int(persistent)),
                "nsk_batch_set_schedule")
 
     def get_schedule(self):
         t, f, p = C.c_int(), C.c_int(), C.c_int()
         _check(load_library().nsk_batch_get_schedule(self.h, C.byref(t), C.byref(f), C.byref(p)),
                "nsk_batch_get_schedule")
-        return t.value, bool(f.value), p.value
+        return t.value, f.value, p.value
 
     def autotune(self):
         """Time all ten schedules on the batch; keep and return (tpb, fused, persistent, ms)."""

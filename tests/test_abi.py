@@ -63,6 +63,15 @@ def test_error_strings_and_argument_validation(nsk_lib):
     assert nsk_lib.nsk_get_subcell(None, None, None) == nsk.NSK_ERR_ARG
     assert nsk_lib.nsk_subcell_switch(None) == nsk.NSK_ERR_ARG
     assert nsk_lib.nsk_step_esdirk(None, 1e-5, 1, 1e-10, 1e-3, 30, 600, 0, None) == nsk.NSK_ERR_ARG
+    # the closure and batch calls in the forms the boundary documents (readings R30, R31)
+    assert nsk_lib.nsk_set_closure(None, nsk.NSK_C_LEARNED, None, 10, 0.5) == nsk.NSK_ERR_ARG
+    lat = (C.c_double * 4)()
+    assert nsk_lib.nsk_batch_step(None, 1, 0.0, None, lat) == nsk.NSK_ERR_ARG
+    assert nsk_lib.nsk_set_schedule(None, 256, 2) == nsk.NSK_ERR_ARG
+    # measurement and test hooks validate before touching CUDA
+    assert nsk_lib.nsk_measure_fma_rate(7, 100, None, None, None) == nsk.NSK_ERR_ARG
+    assert nsk_lib.nsk_measure_fma_rate(nsk.NSK_FP64, 0, None, None, None) == nsk.NSK_ERR_ARG
+    assert nsk_lib.nsk_test_hook_tc_grid_cap(-1) == nsk.NSK_ERR_ARG
     nsk_lib.nsk_destroy(None)
 
 

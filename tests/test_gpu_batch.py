@@ -23,14 +23,17 @@ def _state(s, seed):
 
 
 @pytest.mark.parametrize("precision", [nsk.NSK_FP64, nsk.NSK_FP32_MIXED])
-@pytest.mark.parametrize("N", [2, 3, 4])
-def test_schedules_are_bit_identical(gpu, precision, N):
-    s = nsk.Solver(3, (5, 4, 3), N, [0, 0, 0], [1, 1, 1], 0, precision)
+@pytest.mark.parametrize("dim,ne,N", [(3, (5, 4, 3), 2), (3, (5, 4, 3), 3), (3, (5, 4, 3), 4), (3, (3, 2, 3), 5),
+                                      (2, (7, 5), 3), (2, (6, 3), 5), (1, (9,), 3), (1, (5,), 1)])
+def test_schedules_are_bit_identical(gpu, precision, dim, ne, N):
+    """Separate face pass, face fluxes in the volume kernel, and the lean two-launch stage (the
+    lifting recomputed on chip), at both block sizes: the same bits."""
+    s = nsk.Solver(dim, ne, N, [0] * dim, [1] * dim, 0, precision)
     s.set_params(**PRM)
     U = _state(s, 1)
     results = []
     for tpb in (128, 256):
-        for fused in (False, True):
+        for fused in (0, 1, 2):
             s.set_schedule(tpb, fused)
             s.set_state(U)
             R = s.rhs()
@@ -43,7 +46,7 @@ def test_schedules_are_bit_identical(gpu, precision, N):
 
 
 @pytest.mark.parametrize("precision", [nsk.NSK_FP64, nsk.NSK_FP32_MIXED])
-@pytest.mark.parametrize("fused", [False, True])
+@pytest.mark.parametrize("fused", [0, 1, 2])
 def test_volume_kernel_traces_equal_a_prolongation_pass(gpu, precision, fused):
     """Inside one nsk_step call every stage after the first takes the face traces that the
     previous stage's volume kernel wrote; a call starts with a prolongation pass. Four steps
@@ -112,7 +115,7 @@ def test_batch_equals_solo_runs(gpu, precision, adaptive):
         s.compute_dt(0.5)
     b = nsk.Batch([s for s, _ in inst])
     for tpb, fused, persistent in ((256, True, 1), (128, False, 1), (256, False, 0), (128, True, 0), (256, False, 2),
-                                   (128, True, 2)):
+                                   (128, True, 2), (256, 2, 2), (128, 2, 2)):
         for s, U in inst:
             s.set_state(U)
             s.compute_dt(0.5)
@@ -167,6 +170,7 @@ def test_batch_autotune_graph_and_launch_count(gpu):
     b = nsk.Batch([s for s, _ in inst])
     tpb, fused, persistent, ms = b.autotune()
     assert tpb in (128, 256) and persistent in (0, 1, 2) and ms > 0 and b.get_schedule() == (tpb, fused, persistent)
+    assert fused in (0, 1) or (fused == 2 and persistent == 2)
     # separate face schedule: one prolongation launch per call, then per stage the persistent
     # kernel, or lifting, face and volume launches (the volume phase writes the next traces)
     for persistent, per_stage in ((1, 1), (0, 3), (2, 3 * len(inst))):
@@ -179,6 +183,13 @@ def test_batch_autotune_graph_and_launch_count(gpu):
     n0 = b.launch_count
     b.step(2)
     assert b.launch_count - n0 == 2 * 5 * 3
+    # the lean stage per instance: one prolongation per step, then lifting and volume per stage
+    b.set_schedule(256, 2, 2)
+    n0 = b.launch_count
+    b.step(2)
+    assert b.launch_count - n0 == 2 * len(inst) * (1 + 5 * 2)
+    with pytest.raises(nsk.NskError):
+        b.set_schedule(256, 2, 1)  # the lean stage runs under the instance schedule only
     b.close()
     for s, _ in inst:
         s.close()

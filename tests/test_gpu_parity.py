@@ -251,6 +251,42 @@ def test_launch_counter_and_profile(gpu):
     prof = s.get_profile(reset=True)
     assert prof["k_face"][1] == 0 and prof["k_volume"][1] == 5 and prof["k_prolong"][1] == 1
     assert s.launch_count - n0 == 1 + 5 * 2
+    s.set_schedule(256, 2)  # lean stage: the viscous-trace lifting and the volume kernel
+    n0 = s.launch_count
+    s.step(1e-7, 1)
+    prof = s.get_profile(reset=True)
+    assert prof["k_face"][1] == 0 and prof["k_lift"][1] == 5 and prof["k_volume"][1] == 5
+    assert s.launch_count - n0 == 1 + 5 * 2
+    s.close()
+
+
+@pytest.mark.parametrize("name", ["droplets2d", "collision3d"])
+@pytest.mark.parametrize("precision", [nsk.NSK_FP64, nsk.NSK_FP32_MIXED])
+def test_lean_schedule_residual_and_steps(gpu, name, precision):
+    """The lean two-launch stage (lifting recomputed by the volume kernel) against the oracle:
+    residual per variable within the residual tolerance (FP32: the FP32 operator's bound on the
+    FP32-rounded state), and in FP64 100 steps within 1e-11 of each variable's scale."""
+    s, o, U = _physical_case(name)
+    if precision == nsk.NSK_FP32_MIXED:
+        s.close()
+        s = nsk.Solver(o.dim, o.nelem, o.N, [0.0] * o.dim, [1.0] * o.dim, 0, precision)
+        s.set_params(T=0.85, kappa=o.s.kappa, alpha=o.s.alpha, beta=o.s.beta, mu=o.s.mu)
+    s.set_schedule(256, 2)
+    s.set_state(U)
+    Ul = U if precision == nsk.NSK_FP64 else U.astype(np.float32).astype(np.float64)  # as the context stores it
+    Rg, Ro = s.rhs(), o.rhs(Ul)
+    tol = rhs_tolerance(o, Ul, Ro)
+    for v in range(o.nvar):
+        bound = tol[v] if precision == nsk.NSK_FP64 else \
+            tol[v] * (2.0**-24 / 2.0**-53) * 0.5 + 1e-5 * np.abs(Ro[v]).max()  # the FP32 operator's bound
+        err = float(np.abs(Rg[v] - Ro[v]).max())
+        assert err <= bound, (v, err, bound)
+    if precision == nsk.NSK_FP64:
+        dt = o.timestep(U, 0.5)
+        s.set_state(U)
+        s.step(dt, 100)
+        err, per_var = state_rel_err(s.get_state(), o.step(U, dt, 100))
+        assert err <= 1e-11, per_var
     s.close()
 
 
