@@ -63,7 +63,9 @@ enum {
   NSK_ERR_NONPHYSICAL = -3,  /* rho <= 0, rho >= 3, p_alpha' < 0 or NaN met on the device */
   NSK_ERR_TIMEOUT = -4,      /* a bounded device-side wait expired */
   NSK_ERR_STATE = -5,        /* call order violated */
-  NSK_ERR_NOMEM = -6         /* device allocation failed */
+  NSK_ERR_NOMEM = -6,        /* device allocation failed */
+  NSK_ERR_IO = -7,           /* a checkpoint file could not be written or read, or does not match */
+  NSK_ERR_BOUNDS = -8        /* an index check of the bounds-checking build (libnsk_check.so) failed */
 };
 
 enum { NSK_NODES_GAUSS = 0, NSK_NODES_GAUSS_LOBATTO = 1 };
@@ -249,8 +251,9 @@ int nsk_get_sizes(nsk_ctx* ctx, long long* n_elem, int* nodes_per_elem, int* nva
  * times are accumulated at the next synchronising call (nsk_step, nsk_rhs, ...).
  * nsk_get_profile copies up to n entries of accumulated milliseconds and
  * launch counts, index 0 = trace prolongation, 1 = BR1 lifting, 2 = face flux,
- * 3 = volume integral + surface lifting + sources + RK update, and returns the
- * number of entries (4); reset = 1 clears the accumulators afterwards. */
+ * 3 = volume integral + surface lifting + sources + RK update, 4 = the
+ * single-block kernel (a whole call under schedule 3), and returns the number
+ * of entries (5); reset = 1 clears the accumulators afterwards. */
 int nsk_set_profiling(nsk_ctx* ctx, int on);
 int nsk_get_profile(nsk_ctx* ctx, double* ms, long long* launches, int n, int reset);
 
@@ -281,7 +284,12 @@ int nsk_measure_fma_rate(int precision, int iters, double* tflops, double* ms, v
  *     recomputes the element's lifting on chip, so neither the gradients nor
  *     the face fluxes pass through device memory (the schedule with the least
  *     memory traffic; relaxation model II: the original NSK equations and the
- *     sub-cell path have kernels of their own and use tpb only).
+ *     sub-cell path have kernels of their own and use tpb only);
+ *   3 the single-block schedule for small meshes: one block runs all stages of
+ *     a call's steps (fixed dt, no learned closure) or one residual in a single
+ *     launch, on copies of the arrays in shared memory (relaxation model II,
+ *     meshes whose arrays fit in 200 KB, e.g. 1D up to about 400 elements at
+ *     N = 3 in FP64); where it does not apply the separate face pass runs.
  * Default: tpb 256, separate face pass. Every expression that could be
  * contracted into a fused multiply-add in more than one way is written as an
  * explicit fma, and every schedule evaluates each value with the same code,
@@ -289,10 +297,11 @@ int nsk_measure_fma_rate(int precision, int iters, double* tflops, double* ms, v
  * values. */
 int nsk_set_schedule(nsk_ctx* ctx, int tpb, int fused_face);
 int nsk_get_schedule(nsk_ctx* ctx, int* tpb, int* fused_face);
-/* Autotuner: times one residual evaluation under each of the six schedules
- * (four for the original NSK equations) on the context's current state (the
- * state is not modified), keeps the fastest and returns it (any output may be
- * NULL; ms_out = its time). */
+/* Autotuner: times one residual evaluation under each schedule (tpb 128 and
+ * 256 with fused_face 0, 1, 2, and 3 where it applies; fused_face 0 and 1 for
+ * the original NSK equations) on the context's current state (the state is not
+ * modified), keeps the fastest and returns it (any output may be NULL; ms_out =
+ * its time). */
 int nsk_autotune(nsk_ctx* ctx, int* tpb_out, int* fused_out, double* ms_out);
 
 /* Batched execution (many instances per launch). A batch groups n existing
@@ -463,6 +472,27 @@ int nsk_rhs_static_scratch(int dim, const int nelem[3], const double lo[3], cons
                            void* cuda_stream);
 /* Size in bytes of the file-scope scratch array of nsk_rhs_static_scratch. */
 long long nsk_static_scratch_bytes(void);
+
+/* Checkpoint and resume (no counterpart in the paper; a serving and restart
+ * facility). nsk_save_checkpoint writes to path (created or truncated) a binary
+ * file, little-endian: the 8 bytes "NSKCKPT\0", a format version (uint32 = 1),
+ * then int32 dim, N, node type, precision, model, flux, c dissipation, the
+ * count of sub-cell flags F (E when the 1D sub-cell path is on, else 0),
+ * nelem[3]; FP64 lo[3], hi[3], T, kappa, alpha, beta, mu, the caller's time t;
+ * int64 the caller's step counter and the count of state values V =
+ * nvar E npe; then the state as FP64 [nvar][E][npe] (exact for FP32 contexts)
+ * and F int32 flags. nsk_load_checkpoint reads such a file into a context
+ * created with the same dim, nelem, lo, hi, N, node type and precision and
+ * set to the same model (NSK_ERR_IO otherwise, or for a short or unreadable
+ * file), sets the parameters, flux and c dissipation from it, then the state
+ * and flags, and returns t and step (either pointer may be NULL). The
+ * Runge-Kutta register is zero after it; a step boundary leaves nothing else in
+ * it (the first stage coefficient of the low-storage scheme is A_1 = 0), so
+ * stepping on from a checkpoint gives the same bits as never stopping. The
+ * learned closure's network is not part of the file. Both synchronise the
+ * context's stream. */
+int nsk_save_checkpoint(nsk_ctx* ctx, const char* path, double t, long long step);
+int nsk_load_checkpoint(nsk_ctx* ctx, const char* path, double* t, long long* step);
 
 /* Human-readable text of an error code; never NULL. */
 const char* nsk_error_string(int code);

@@ -39,6 +39,16 @@ int nsk_test_hook_tc_grid_cap(int max_ctas);
  * synchronisation. NSK_ERR_ARG for another fn, NULL arrays or n < 0. */
 int nsk_test_hook_math(int fn, const double* x, double* y, long long n, void* stream);
 
+/* Bounds-checking build only (libnsk_check.so, compiled with -DNSK_BOUNDS_CHECK):
+ * makes the context's neighbour strides point far outside the mesh, so that
+ * the index checks of its next stage launches fire: they set the error word's
+ * bounds bit, keep every access inside its array, and the call returns
+ * NSK_ERR_BOUNDS. Use only with the model II stage kernels (separate, fused,
+ * lean or single-block schedule), then destroy the context. In the regular
+ * library, which has no index checks, it changes nothing and returns
+ * NSK_ERR_STATE. */
+int nsk_test_hook_corrupt_neighbours(nsk_ctx* ctx);
+
 #ifdef __cplusplus
 }
 #endif

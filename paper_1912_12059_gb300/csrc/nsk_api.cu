@@ -2,6 +2,7 @@
 // Builds the nodal tables and the mesh, owns the device buffers of a context,
 // validates arguments and call order, and queues the stage kernels.
 #include <math.h>
+#include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -11,6 +12,8 @@
 #include <vector>
 
 #include "nsk_internal.h"
+#include "nsk_nvtx.h"
+#include "nsk_test_hooks.h"
 
 namespace {
 
@@ -252,12 +255,43 @@ int sync_and_check(nsk_ctx* c) {
     int z = 0;
     if (cudaMemcpy(c->b.err, &z, sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess) return NSK_ERR_CUDA;
     if (h & NSK_EBIT_TIMEOUT) return NSK_ERR_TIMEOUT;
+    if (h & NSK_EBIT_BOUNDS) return NSK_ERR_BOUNDS;
     return NSK_ERR_NONPHYSICAL;
   }
   return NSK_OK;
 }
 
+// the single-block schedule applies: relaxation model II, no sub-cells, and the mesh's arrays fit
+// in one block's shared memory
+bool block_eligible(const nsk_ctx* c) {
+  return c->p.model == NSK_MODEL_RELAXATION && !c->fv_path() &&
+         nsk_block_bytes(c->dim, c->p, c->np, c->precision == NSK_FP32_MIXED) <= (size_t)kBlockSmemMax;
+}
+
+// one launch of the single-block kernel: nsteps LSRK steps at the fixed dt, or (nsteps = 0) one
+// residual into l.Rout; profiled as kernel 4
+int launch_block(nsk_ctx* c, int nsteps, double dt, void* Rout) {
+  cudaEvent_t* ev = prof_group(c, 16);
+  if (ev) cudaEventRecord(ev[4], c->stream);
+  NskLsrkCoef coef;
+  for (int i = 0; i < 5; ++i) {
+    coef.A[i] = kA[i];
+    coef.B[i] = kB[i];
+  }
+  const int r = nsk_launch_block(c->dim, c->p, c->np, c->precision == NSK_FP32_MIXED, c->b,
+                                 nsteps > 0 ? NSK_MODE_LSRK : NSK_MODE_RHS, coef, dt, nsteps > 0 ? nsteps : 1, Rout,
+                                 c->stream);
+  if (ev) cudaEventRecord(ev[5], c->stream);
+  if (r < 0) return r;
+  c->launches += r;
+  return NSK_OK;
+}
+
 int launch_stage(nsk_ctx* c, NskLaunch l) {
+  if (l.fused_face == 3) {  // single-block schedule: a residual in one launch; otherwise the separate face pass
+    if (l.mode == NSK_MODE_RHS && block_eligible(c)) return launch_block(c, 0, 0.0, l.Rout);
+    l.fused_face = 0;
+  }
   // kernels 0..3 = prolong, lift, face, volume
   const int mask = c->p.model == NSK_MODEL_NSK ? (l.mode == NSK_MODE_LIFT ? 3 : 15)
                                                 : ((l.traces_ready ? 0 : 1) | 2 |
@@ -337,6 +371,8 @@ const char* nsk_error_string(int code) {
     case NSK_ERR_TIMEOUT: return "bounded device wait expired";
     case NSK_ERR_STATE: return "call order violated";
     case NSK_ERR_NOMEM: return "device allocation failed";
+    case NSK_ERR_IO: return "checkpoint file error (unwritable, unreadable, short or for another mesh)";
+    case NSK_ERR_BOUNDS: return "index check of the bounds-checking build failed";
     default: return "unknown error";
   }
 }
@@ -439,6 +475,7 @@ int nsk_init_mesh(nsk_ctx** out, int dim, const int nelem[3], const double lo[3]
       return NSK_ERR_NOMEM;
     }
   }
+  c->p.berr = c->b.err;  // the bounds-checking build's index checks report here
   if (cudaMemset(c->b.err, 0, sizeof(int)) != cudaSuccess || cudaMemset(c->b.K, 0, rs * c->nvar * nn) != cudaSuccess ||
       cudaMemset(c->b.dt, 0, sizeof(double)) != cudaSuccess) {
     free_ctx(c);
@@ -507,6 +544,7 @@ int nsk_set_flux(nsk_ctx* c, int flux) {
 }
 
 int nsk_set_state(nsk_ctx* c, const double* U, int where) {
+  const NskRange nvtx_range("nsk_set_state");
   if (!c || !U || (where != NSK_HOST && where != NSK_DEVICE)) return NSK_ERR_ARG;
   if (!c->params_set) return NSK_ERR_STATE;
   const long long n = (long long)c->nvar * c->nn;
@@ -533,6 +571,7 @@ int nsk_set_state(nsk_ctx* c, const double* U, int where) {
 }
 
 int nsk_get_state(nsk_ctx* c, double* U, int where) {
+  const NskRange nvtx_range("nsk_get_state");
   if (!c || !U || (where != NSK_HOST && where != NSK_DEVICE)) return NSK_ERR_ARG;
   if (!c->state_set) return NSK_ERR_STATE;
   int r = export_nodal(c, c->b.U, c->nvar, U, where);
@@ -572,6 +611,7 @@ int fv_stage(nsk_ctx* c, int mode, double* Rout, double A, double B, const doubl
 }
 
 int nsk_rhs(nsk_ctx* c, double t, double* Ut, int where) {
+  const NskRange nvtx_range("nsk_rhs");
   (void)t;
   if (!c || !Ut || (where != NSK_HOST && where != NSK_DEVICE)) return NSK_ERR_ARG;
   if (!c->state_set) return NSK_ERR_STATE;
@@ -591,6 +631,7 @@ int nsk_rhs(nsk_ctx* c, double t, double* Ut, int where) {
 }
 
 int nsk_lift(nsk_ctx* c, double* Q, int where) {
+  const NskRange nvtx_range("nsk_lift");
   if (!c || !Q || (where != NSK_HOST && where != NSK_DEVICE)) return NSK_ERR_ARG;
   if (!c->state_set || c->fv_path()) return NSK_ERR_STATE;
   NskLaunch l = {NSK_MODE_LIFT, nullptr, 0.0, 0.0, nullptr, 0.0, nullptr, c->tpb, c->fused_face};
@@ -602,6 +643,7 @@ int nsk_lift(nsk_ctx* c, double* Q, int where) {
 }
 
 int nsk_compute_dt(nsk_ctx* c, double cfl, double* dt_out) {
+  const NskRange nvtx_range("nsk_compute_dt");
   if (!c || !dt_out || !(cfl > 0.0)) return NSK_ERR_ARG;
   if (!c->state_set) return NSK_ERR_STATE;
   int r = launch_dt(c, cfl);
@@ -613,6 +655,7 @@ int nsk_compute_dt(nsk_ctx* c, double cfl, double* dt_out) {
 }
 
 int nsk_step(nsk_ctx* c, double dt, int nsteps) {
+  const NskRange nvtx_range("nsk_step");
   if (!c || nsteps < 0 || !isfinite(dt) || dt == 0.0) return NSK_ERR_ARG;
   if (!c->state_set) return NSK_ERR_STATE;
   const bool adaptive = dt < 0.0;
@@ -643,6 +686,12 @@ int nsk_step(nsk_ctx* c, double dt, int nsteps) {
     }
     return sync_and_check(c);
   }
+  if (c->fused_face == 3 && !adaptive && c->closure_mode != NSK_C_LEARNED && block_eligible(c)) {
+    // single-block schedule: every stage of every step in one launch
+    const int r = launch_block(c, nsteps, dt, nullptr);
+    if (r) return r;
+    return sync_and_check(c);
+  }
   bool ready = false;  // b.Utr holds the traces of U
   for (int s = 0; s < nsteps; ++s) {
     if (adaptive) {
@@ -656,14 +705,16 @@ int nsk_step(nsk_ctx* c, double dt, int nsteps) {
         const int r = nsk_closure_apply_ctx(c, ready ? c->b.Utr : nullptr);
         if (r) return r;
       }
-      NskLaunch l = {NSK_MODE_LSRK, nullptr, kA[st], kB[st], adaptive ? c->b.dt : nullptr, dt, nullptr, c->tpb, c->fused_face};
+      // (the single-block schedule, where it does not apply, steps with the separate face pass)
+      const int ff = c->fused_face == 3 ? 0 : c->fused_face;
+      NskLaunch l = {NSK_MODE_LSRK, nullptr, kA[st], kB[st], adaptive ? c->b.dt : nullptr, dt, nullptr, c->tpb, ff};
       // the volume kernel writes the traces of the updated state for the next stage of this call
       const bool write = c->p.model != NSK_MODEL_NSK && !(s == nsteps - 1 && st == 4);
       l.traces_ready = ready;
-      l.utr_next = write ? (c->fused_face ? c->utr_alt : c->b.Utr) : nullptr;
+      l.utr_next = write ? (ff ? c->utr_alt : c->b.Utr) : nullptr;
       int r = launch_stage(c, l);
       if (r) return r;
-      if (write && c->fused_face) std::swap(c->b.Utr, c->utr_alt);
+      if (write && ff) std::swap(c->b.Utr, c->utr_alt);
       ready = write;
     }
     if (learned && c->judge_every > 0 && ++c->steps_since_judge >= c->judge_every) {
@@ -795,6 +846,7 @@ int nsk_subcell_switch(nsk_ctx* c) {
 }
 
 int nsk_diagnostics(nsk_ctx* c, double* mass, double* energy, double* l2) {
+  const NskRange nvtx_range("nsk_diagnostics");
   if (!c) return NSK_ERR_ARG;
   if (!c->state_set) return NSK_ERR_STATE;
   NskLaunch l = {NSK_MODE_LIFT, nullptr, 0.0, 0.0, nullptr, 0.0, nullptr, c->tpb, c->fused_face};
@@ -825,7 +877,7 @@ int nsk_get_sizes(nsk_ctx* c, long long* n_elem, int* nodes_per_elem, int* nvar)
 long long nsk_launch_count(nsk_ctx* c) { return c ? c->launches : -1; }
 
 int nsk_set_schedule(nsk_ctx* c, int tpb, int fused_face) {
-  if (!c || (tpb != 128 && tpb != 256) || fused_face < 0 || fused_face > 2) return NSK_ERR_ARG;
+  if (!c || (tpb != 128 && tpb != 256) || fused_face < 0 || fused_face > 3) return NSK_ERR_ARG;
   c->tpb = tpb;
   c->fused_face = fused_face;
   return NSK_OK;
@@ -839,6 +891,7 @@ int nsk_get_schedule(nsk_ctx* c, int* tpb, int* fused_face) {
 }
 
 int nsk_autotune(nsk_ctx* c, int* tpb_out, int* fused_out, double* ms_out) {
+  const NskRange nvtx_range("nsk_autotune");
   if (!c) return NSK_ERR_ARG;
   if (!c->state_set) return NSK_ERR_STATE;
   cudaEvent_t e0, e1;
@@ -850,7 +903,7 @@ int nsk_autotune(nsk_ctx* c, int* tpb_out, int* fused_out, double* ms_out) {
   c->prof_on = false;
   // the lean two-launch stage applies to relaxation model II only (the original NSK equations
   // have their own stage kernels and take the schedule's block size alone)
-  const int nsched = c->p.model == NSK_MODEL_NSK ? 2 : 3;
+  const int nsched = c->p.model == NSK_MODEL_NSK ? 2 : (block_eligible(c) ? 4 : 3);
   for (int it = 0; it < 2 && st == NSK_OK; ++it)
     for (int f = 0; f < nsched && st == NSK_OK; ++f) {
       c->tpb = tpbs[it];
@@ -906,6 +959,133 @@ int nsk_get_profile(nsk_ctx* c, double* ms, long long* launches, int n, int rese
       c->prof_cnt[k] = 0;
     }
   return NSK_NKERN;
+}
+
+int nsk_test_hook_corrupt_neighbours(nsk_ctx* c) {
+  if (!c) return NSK_ERR_ARG;
+#ifdef NSK_BOUNDS_CHECK
+  for (int k = 0; k < c->dim; ++k) {
+    c->p.est[k] = 1 << 29;
+    c->p.ewrap[k] = -(1 << 29);
+  }
+  return NSK_OK;
+#else
+  return NSK_ERR_STATE;
+#endif
+}
+
+// ---- checkpoint and resume ----
+}  // extern "C"
+
+namespace {
+struct CkptHead {  // written field by field (no padding in the file)
+  int32_t dim, N, node_type, precision, model, flux, c_diss, nflags, nelem[3];
+  double lo[3], hi[3], T, kappa, alpha, beta, mu, t;
+  int64_t step, nvals;
+};
+const char kCkptMagic[8] = {'N', 'S', 'K', 'C', 'K', 'P', 'T', 0};
+const uint32_t kCkptVersion = 1;
+
+template <typename X>
+bool put(FILE* f, const X* x, size_t n) { return fwrite(x, sizeof(X), n, f) == n; }
+template <typename X>
+bool get(FILE* f, X* x, size_t n) { return fread(x, sizeof(X), n, f) == n; }
+
+bool write_head(FILE* f, const CkptHead& h) {
+  return put(f, kCkptMagic, 8) && put(f, &kCkptVersion, 1) && put(f, &h.dim, 1) && put(f, &h.N, 1) &&
+         put(f, &h.node_type, 1) && put(f, &h.precision, 1) && put(f, &h.model, 1) && put(f, &h.flux, 1) &&
+         put(f, &h.c_diss, 1) && put(f, &h.nflags, 1) && put(f, h.nelem, 3) && put(f, h.lo, 3) && put(f, h.hi, 3) &&
+         put(f, &h.T, 1) && put(f, &h.kappa, 1) && put(f, &h.alpha, 1) && put(f, &h.beta, 1) && put(f, &h.mu, 1) &&
+         put(f, &h.t, 1) && put(f, &h.step, 1) && put(f, &h.nvals, 1);
+}
+bool read_head(FILE* f, CkptHead& h) {
+  char magic[8];
+  uint32_t ver = 0;
+  return get(f, magic, 8) && memcmp(magic, kCkptMagic, 8) == 0 && get(f, &ver, 1) && ver == kCkptVersion &&
+         get(f, &h.dim, 1) && get(f, &h.N, 1) && get(f, &h.node_type, 1) && get(f, &h.precision, 1) &&
+         get(f, &h.model, 1) && get(f, &h.flux, 1) && get(f, &h.c_diss, 1) && get(f, &h.nflags, 1) &&
+         get(f, h.nelem, 3) && get(f, h.lo, 3) && get(f, h.hi, 3) && get(f, &h.T, 1) && get(f, &h.kappa, 1) &&
+         get(f, &h.alpha, 1) && get(f, &h.beta, 1) && get(f, &h.mu, 1) && get(f, &h.t, 1) && get(f, &h.step, 1) &&
+         get(f, &h.nvals, 1);
+}
+}  // namespace
+
+extern "C" {
+
+int nsk_save_checkpoint(nsk_ctx* c, const char* path, double t, long long step) {
+  const NskRange nvtx_range("nsk_save_checkpoint");
+  if (!c || !path) return NSK_ERR_ARG;
+  if (!c->state_set || !c->params_set) return NSK_ERR_STATE;
+  CkptHead h;
+  memset(&h, 0, sizeof(h));
+  h.dim = c->dim;
+  h.N = c->N;
+  h.node_type = c->node_type;
+  h.precision = c->precision;
+  h.model = c->p.model;
+  h.flux = c->p.flux;
+  h.c_diss = c->p.c_diss;
+  h.nflags = c->fv_on ? (int32_t)c->E : 0;
+  for (int k = 0; k < 3; ++k) {
+    h.nelem[k] = c->ne[k];
+    h.lo[k] = c->lo[k];
+    h.hi[k] = c->hi[k];
+  }
+  h.T = c->p.T;
+  h.kappa = c->p.kappa;
+  h.alpha = c->p.alpha;
+  h.beta = c->p.beta;
+  h.mu = c->p.mu;
+  h.t = t;
+  h.step = step;
+  h.nvals = (int64_t)c->nvar * c->nn;
+  std::vector<double> U((size_t)h.nvals);
+  int r = nsk_get_state(c, U.data(), NSK_HOST);
+  if (r) return r;
+  std::vector<int> flags((size_t)h.nflags);
+  if (h.nflags && (r = nsk_get_subcell(c, flags.data(), nullptr))) return r;
+  FILE* f = fopen(path, "wb");
+  if (!f) return NSK_ERR_IO;
+  bool ok = write_head(f, h) && put(f, U.data(), U.size());
+  if (ok && h.nflags) {
+    std::vector<int32_t> f32(flags.begin(), flags.end());
+    ok = put(f, f32.data(), f32.size());
+  }
+  ok = (fclose(f) == 0) && ok;
+  return ok ? NSK_OK : NSK_ERR_IO;
+}
+
+int nsk_load_checkpoint(nsk_ctx* c, const char* path, double* t, long long* step) {
+  const NskRange nvtx_range("nsk_load_checkpoint");
+  if (!c || !path) return NSK_ERR_ARG;
+  FILE* f = fopen(path, "rb");
+  if (!f) return NSK_ERR_IO;
+  CkptHead h;
+  bool ok = read_head(f, h);
+  ok = ok && h.dim == c->dim && h.N == c->N && h.node_type == c->node_type && h.precision == c->precision &&
+       h.model == c->p.model && h.nvals == (int64_t)c->nvar * c->nn && (h.nflags == 0 || h.nflags == c->E);
+  for (int k = 0; k < 3 && ok; ++k)
+    ok = h.nelem[k] == c->ne[k] && h.lo[k] == c->lo[k] && h.hi[k] == c->hi[k];
+  std::vector<double> U;
+  std::vector<int32_t> flags;
+  if (ok) {
+    U.resize((size_t)h.nvals);
+    flags.resize((size_t)h.nflags);
+    ok = get(f, U.data(), U.size()) && (h.nflags == 0 || get(f, flags.data(), flags.size()));
+  }
+  fclose(f);
+  if (!ok) return NSK_ERR_IO;
+  int r = nsk_set_params(c, h.T, h.kappa, h.alpha, h.beta, h.mu);
+  if (r) return r;
+  if ((r = nsk_set_flux(c, h.flux)) || (r = nsk_set_c_dissipation(c, h.c_diss))) return r;
+  if ((r = nsk_set_state(c, U.data(), NSK_HOST))) return r;
+  if (h.nflags) {
+    std::vector<int> fl(flags.begin(), flags.end());
+    if ((r = nsk_set_subcell_flags(c, fl.data()))) return r;
+  }
+  if (t) *t = h.t;
+  if (step) *step = h.step;
+  return NSK_OK;
 }
 
 void nsk_destroy(nsk_ctx* c) {
@@ -1016,6 +1196,7 @@ extern "C" int nsk_rhs_static_scratch(int dim, const int nelem[3], const double 
   memset(&b, 0, sizeof(b));
   b.U = (void*)U;
   b.err = (int*)s8;
+  p.berr = b.err;
   b.Q = s8 + b_err;
   b.Utr = s8 + b_err + b_q;
   b.FVtr = s8 + b_err + b_q + b_utr;

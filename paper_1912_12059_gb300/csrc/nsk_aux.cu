@@ -162,3 +162,21 @@ extern "C" int nsk_test_hook_math(int fn, const double* x, double* y, long long 
   k_math_hook<<<reduce_grid(n), 256, 0, (cudaStream_t)stream>>>(fn, x, y, n);
   return cudaGetLastError() == cudaSuccess ? NSK_OK : NSK_ERR_CUDA;
 }
+
+// ---- single-block schedule: dispatch by dimension ----
+size_t nsk_block_bytes(int dim, const NskParams& p, int np, bool fp32) {
+  switch (dim) {
+    case 1: return nsk_block_bytes_d1(p, np, fp32);
+    case 2: return nsk_block_bytes_d2(p, np, fp32);
+    default: return nsk_block_bytes_d3(p, np, fp32);
+  }
+}
+
+int nsk_launch_block(int dim, const NskParams& p, int np, bool fp32, const NskBuffers& b, int mode,
+                     const NskLsrkCoef& coef, double dt, int nsteps, void* Rout, cudaStream_t s) {
+  switch (dim) {
+    case 1: return nsk_launch_block_d1(p, np, fp32, b, mode, coef, dt, nsteps, Rout, s);
+    case 2: return nsk_launch_block_d2(p, np, fp32, b, mode, coef, dt, nsteps, Rout, s);
+    default: return nsk_launch_block_d3(p, np, fp32, b, mode, coef, dt, nsteps, Rout, s);
+  }
+}

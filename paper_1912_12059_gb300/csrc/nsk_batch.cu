@@ -21,6 +21,7 @@
 #include <vector>
 
 #include "nsk_kernels.cuh"
+#include "nsk_nvtx.h"
 #include "nsk_test_hooks.h"
 
 // Device descriptor of one instance.
@@ -692,6 +693,7 @@ int nsk_batch_get_schedule(nsk_batch* bt, int* tpb, int* fused_face, int* persis
 }
 
 int nsk_batch_autotune(nsk_batch* bt, int* tpb_out, int* fused_out, int* persistent_out, double* ms_out) {
+  const NskRange nvtx_range("nsk_batch_autotune");
   if (!bt) return NSK_ERR_ARG;
   for (nsk_ctx* c : bt->inst)
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return NSK_ERR_CUDA;
@@ -739,6 +741,7 @@ int nsk_batch_autotune(nsk_batch* bt, int* tpb_out, int* fused_out, int* persist
 }
 
 int nsk_batch_step(nsk_batch* bt, int nsteps, double cfl, double* step_ms, double* per_instance_latency_ms) {
+  const NskRange nvtx_range("nsk_batch_step");
   if (!bt || nsteps < 0) return NSK_ERR_ARG;
   for (nsk_ctx* c : bt->inst)
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return NSK_ERR_CUDA;

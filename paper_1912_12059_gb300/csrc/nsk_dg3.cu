@@ -6,3 +6,9 @@ int nsk_launch_stage_d3(const NskParams& p, int np, bool fp32, const NskBuffers&
                         cudaStream_t s) {
   return nsk::launch_stage_np<3>(p, np, fp32, b, l, s);
 }
+
+size_t nsk_block_bytes_d3(const NskParams& p, int np, bool fp32) { return nsk::block_bytes_np<3>(p, np, fp32); }
+int nsk_launch_block_d3(const NskParams& p, int np, bool fp32, const NskBuffers& b, int mode, const NskLsrkCoef& coef,
+                        double dt, int nsteps, void* Rout, cudaStream_t s) {
+  return nsk::launch_block_np<3>(p, np, fp32, b, mode, coef, dt, nsteps, Rout, s);
+}

@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "nsk_internal.h"
+#include "nsk_nvtx.h"
 
 namespace {
 
@@ -347,6 +348,7 @@ static int fd_colours(int ne) {
 
 int nsk_step_esdirk(nsk_ctx* c, double dt, int nsteps, double newton_tol, double krylov_tol, int krylov_dim,
                     int max_krylov, int block_precond, long long stats[4]) {
+  const NskRange nvtx_range("nsk_step_esdirk");
   if (!c || !(dt > 0.0) || !isfinite(dt) || nsteps < 0 || !(newton_tol > 0.0) || !(krylov_tol > 0.0) ||
       krylov_dim < 1 || krylov_dim > 200 || max_krylov < 1 || (block_precond != 0 && block_precond != 1))
     return NSK_ERR_ARG;

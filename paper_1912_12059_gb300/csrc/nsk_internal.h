@@ -17,6 +17,7 @@ enum : int {
   NSK_EBIT_SOUND = 2,     // p_alpha'(rho) < 0 (hyperbolicity lost)
   NSK_EBIT_NAN = 4,       // NaN / Inf met
   NSK_EBIT_TIMEOUT = 8,   // a bounded device wait expired
+  NSK_EBIT_BOUNDS = 16,   // an index check of the bounds-checking build failed
 };
 
 // 1D nodal tables of the tensor-product basis (Sec. 3.1), in both precisions.
@@ -86,6 +87,7 @@ struct NskParams {
   float spin_lof, spin_hif; // the same bounds rounded outward to FP32
   int c_diss;      // Lax-Friedrichs jump on c as well
   int flux;        // NSK_FLUX_LF or NSK_FLUX_HLLC
+  int* berr;       // error word of the bounds-checking build's index checks (NULL: none)
   NskTab<double> td;
   NskTab<float> tf;
 };
@@ -132,7 +134,14 @@ struct NskLaunch {
   void* utr_next = nullptr;  // non-NULL: the volume kernel writes the traces of its output state here
 };
 
-#define NSK_NKERN 4  // prolong, lift, face, volume
+#define NSK_NKERN 5  // prolong, lift, face, volume, single-block stage/step kernel
+
+// LSRK stage coefficients passed by value to the single-block kernel
+struct NskLsrkCoef {
+  double A[5], B[5];
+};
+// dynamic shared memory the single-block schedule may use (the per-block limit, 227 KB, less a margin)
+constexpr int kBlockSmemMax = 200 * 1024;
 
 // Per-dimension launchers (nsk_dg1.cu, nsk_dg2.cu, nsk_dg3.cu). Return the
 // number of kernels launched, or a negative NSK_ERR_* code.
@@ -146,6 +155,21 @@ int nsk_launch_stage_nsk(int dim, const NskParams& p, int np, const NskBuffers& 
 int nsk_launch_dt_nsk(const NskParams& p, int dim, const NskBuffers& b, double cfl, int N, cudaStream_t s);
 int nsk_launch_stage_d3(const NskParams& p, int np, bool fp32, const NskBuffers& b, const NskLaunch& l,
                         cudaStream_t s);
+// Single-block schedule (nsk_set_schedule fused_face = 3): the bytes of shared memory a mesh
+// needs, and one launch running nsteps LSRK steps (mode LSRK, fixed dt) or one residual (mode
+// RHS, into Rout) in one block; returns 1 (launches), NSK_ERR_ARG when the mesh does not fit.
+size_t nsk_block_bytes(int dim, const NskParams& p, int np, bool fp32);
+int nsk_launch_block(int dim, const NskParams& p, int np, bool fp32, const NskBuffers& b, int mode,
+                     const NskLsrkCoef& coef, double dt, int nsteps, void* Rout, cudaStream_t s);
+size_t nsk_block_bytes_d1(const NskParams& p, int np, bool fp32);
+size_t nsk_block_bytes_d2(const NskParams& p, int np, bool fp32);
+size_t nsk_block_bytes_d3(const NskParams& p, int np, bool fp32);
+int nsk_launch_block_d1(const NskParams& p, int np, bool fp32, const NskBuffers& b, int mode, const NskLsrkCoef& coef,
+                        double dt, int nsteps, void* Rout, cudaStream_t s);
+int nsk_launch_block_d2(const NskParams& p, int np, bool fp32, const NskBuffers& b, int mode, const NskLsrkCoef& coef,
+                        double dt, int nsteps, void* Rout, cudaStream_t s);
+int nsk_launch_block_d3(const NskParams& p, int np, bool fp32, const NskBuffers& b, int mode, const NskLsrkCoef& coef,
+                        double dt, int nsteps, void* Rout, cudaStream_t s);
 // dt: reduces max_nodes sum_k (|v_k| + sqrt(p_alpha'))/h_k into b.lam and writes b.dt.
 int nsk_launch_dt(const NskParams& p, int dim, int np, bool fp32, const NskBuffers& b, double cfl,
                   cudaStream_t s);

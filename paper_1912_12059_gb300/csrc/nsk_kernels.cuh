@@ -70,6 +70,21 @@ __device__ __forceinline__ int node_stride(int k) {
   return k == 0 ? 1 : (k == 1 ? NP : NP * NP);
 }
 
+// Bounds-checking build (-DNSK_BOUNDS_CHECK, libnsk_check.so): every neighbour index is checked
+// against the element count; a failing check sets NSK_EBIT_BOUNDS in the error word p.berr and
+// the index becomes 0, so the access stays inside its array (no fault, no trap). All other
+// indices of the stage kernels follow from loop bounds and the element index.
+__device__ __forceinline__ long long chk_elem(const NskParams& p, long long e) {
+#ifdef NSK_BOUNDS_CHECK
+  if ((unsigned long long)e >= (unsigned long long)p.E) {
+    if (p.berr) atomicOr(p.berr, NSK_EBIT_BOUNDS);
+    return 0;
+  }
+#endif
+  (void)p;
+  return e;
+}
+
 // periodic neighbour of element e in direction k, side dir = -1 / +1 (element indices fit
 // in 32 bits: nsk_init_mesh rejects meshes with E * nodes per element above 2^31)
 __device__ __forceinline__ long long nbr_elem(const NskParams& p, long long e, int k, int dir) {
@@ -80,7 +95,7 @@ __device__ __forceinline__ long long nbr_elem(const NskParams& p, long long e, i
   int cn = c + dir;
   cn += (cn < 0) ? n : 0;
   cn -= (cn >= n) ? n : 0;
-  return e + (long long)(cn - c) * (long long)s;
+  return chk_elem(p, e + (long long)(cn - c) * (long long)s);
 }
 
 // Cartesian position of an element for the stage kernels: 32-bit index and coordinates
@@ -107,8 +122,8 @@ __device__ __forceinline__ ElemIdx elem_idx(const NskParams& p, int e) {
 // periodic neighbour of x in direction k, side dir = -1 / +1 (same result as nbr_elem)
 __device__ __forceinline__ int nbr_of(const NskParams& p, const ElemIdx& x, int k, int dir) {
   const int c = k == 0 ? x.c0 : (k == 1 ? x.c1 : x.c2);
-  if (dir > 0) return c == p.ne[k] - 1 ? x.e - p.ewrap[k] : x.e + p.est[k];
-  return c == 0 ? x.e + p.ewrap[k] : x.e - p.est[k];
+  if (dir > 0) return (int)chk_elem(p, c == p.ne[k] - 1 ? x.e - p.ewrap[k] : x.e + p.est[k]);
+  return (int)chk_elem(p, c == 0 ? x.e + p.ewrap[k] : x.e - p.est[k]);
 }
 
 // ---- FP64 reciprocal and square root with few FP64 instructions ----
@@ -275,6 +290,21 @@ __device__ __forceinline__ void cp_async_elem(R* sdst, const R* gsrc) {
 __device__ __forceinline__ void cp_async_16(void* sdst, const void* gsrc) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gsrc) : "memory");
+}
+// W values from src to the shared buffer dst: asynchronously (cp.async, src in global memory)
+// or, ASYNC false, with plain loads and stores (src may then be in shared memory, which cp.async
+// cannot read)
+template <bool ASYNC, int W, typename R>
+__device__ __forceinline__ void stage_copy(R* dst, const R* src) {
+  if constexpr (ASYNC) {
+    if constexpr (W > 1)
+      cp_async_16(dst, src);
+    else
+      cp_async_elem(dst, src);
+  } else {
+#pragma unroll
+    for (int w = 0; w < W; ++w) dst[w] = src[w];
+  }
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
@@ -1052,7 +1082,9 @@ __device__ __forceinline__ void volume_write_traces(const NskParams& p, const R*
 // UtrNext (optional): the traces of the element's new state (LSRK) or of its state (RHS)
 // are written there from shared memory, so the next stage needs no prolongation pass.
 // It must not alias Utr when FUSED (neighbours still read Utr).
-template <typename R, int D, int NP, int G, bool FUSED, bool QF = true>
+// ASYNC (separate face schedule): Fstar is in global memory and staged with cp.async; false when
+// it is in shared memory (the single-block kernel), where plain copies stage it.
+template <typename R, int D, int NP, int G, bool FUSED, bool QF = true, bool ASYNC = true>
 __device__ __forceinline__ void volume_group(const NskParams& p, R* __restrict__ U, const R* __restrict__ Q,
                                              const R* __restrict__ Fstar, const R* __restrict__ Utr,
                                              const R* __restrict__ FVtr, R* __restrict__ K, R* __restrict__ Rout,
@@ -1090,10 +1122,7 @@ __device__ __forceinline__ void volume_group(const NskParams& p, R* __restrict__
           const int src = (slot & 1) ? e : nbr_of(p, ex, k, -1);
           R* dst = sb + slot * NV * NFN;
           const R* srcp = Fstar + (size_t)(v * D + k) * p.nfe + (src * NFN + fn);
-          if constexpr (W > 1)
-            cp_async_16(dst, srcp);
-          else
-            cp_async_elem(dst, srcp);
+          stage_copy<ASYNC, W>(dst, srcp);
         }
       }
     } else if (valid) {
@@ -1103,13 +1132,10 @@ __device__ __forceinline__ void volume_group(const NskParams& p, R* __restrict__
         const int src = (slot & 1) ? e : nbr_of(p, ex, k, -1);
         R* dst = sfs + ((le * NF + slot) * NV + v) * NFN + fn;
         const R* srcp = Fstar + (size_t)(v * D + k) * p.nfe + (src * NFN + fn);
-        if constexpr (W > 1)
-          cp_async_16(dst, srcp);
-        else
-          cp_async_elem(dst, srcp);
+        stage_copy<ASYNC, W>(dst, srcp);
       }
     }
-    cp_async_commit();
+    if constexpr (ASYNC) cp_async_commit();
   }
   volume_tables<R, D, NP>(t, tb, mode == NSK_MODE_RHS ? R(1) : dt);
   R u[NV], kin[NV], tau[D][D], gc[D];
@@ -1143,7 +1169,7 @@ __device__ __forceinline__ void volume_group(const NskParams& p, R* __restrict__
       }
     }
   }
-  if constexpr (!FUSED) cp_async_wait_all();
+  if constexpr (!FUSED && ASYNC) cp_async_wait_all();
   __syncthreads();
 
   if (valid) volume_residual_update<R, D, NP, G>(p, tb, sf, sfs, u, gc, kin, mode, A, B, U, K, Rout, g, le, n);
@@ -1488,6 +1514,87 @@ __global__ void __launch_bounds__(G * Shape<D, NP>::NPE)
   if (eflag) atomicOr(err, eflag);
 }
 
+// ---- single-block schedule (fused_face = 3): a small mesh's whole call in one launch ----
+// One block runs the stages of every step of a call (or one residual) phase after phase
+// (prolongation, lifting, face fluxes, volume + update; block barriers between them) on copies of
+// the context's arrays in shared memory, laid out with the same plane strides (nne, nfe), so the
+// stage bodies run on them unchanged and round exactly as in the other schedules. The state and
+// the RK register are copied in at the start and out at the end (the residual goes straight to
+// global memory). Keeping the arrays on chip also keeps every value written and read again within
+// the launch out of the read-only cache path that global loads may take.
+template <typename R, int D, int NP, int G>
+struct BlockLayout {
+  using S = Shape<D, NP>;
+  static constexpr int NT = S::NV + TraceComps<R>::extra;
+  static constexpr int work = lift_smem<R, D, NP, G>() > volume_smem<R, D, NP, G, false>()
+                                  ? lift_smem<R, D, NP, G>()
+                                  : volume_smem<R, D, NP, G, false>();
+  // offsets in units of R for a mesh of E elements (every array starts 16-byte aligned)
+  static __host__ __device__ size_t up(size_t x) { return (x + 15) & ~(size_t)15; }
+  static __host__ __device__ size_t U(long long) { return 0; }
+  static __host__ __device__ size_t K(long long E) { return U(E) + up((size_t)S::NV * E * S::NPE); }
+  static __host__ __device__ size_t Q(long long E) { return K(E) + up((size_t)S::NV * E * S::NPE); }
+  static __host__ __device__ size_t Utr(long long E) { return Q(E) + up((size_t)S::NVF * E * S::NPE); }
+  static __host__ __device__ size_t FVtr(long long E) { return Utr(E) + up((size_t)NT * S::NF * E * S::NFN); }
+  static __host__ __device__ size_t Fstar(long long E) { return FVtr(E) + up((size_t)S::NW * S::NF * E * S::NFN); }
+  static __host__ __device__ size_t Work(long long E) { return Fstar(E) + up((size_t)S::NV * D * E * S::NFN); }
+  static __host__ __device__ size_t total(long long E) { return Work(E) + work; }
+};
+
+template <typename R, int D, int NP, int G>
+__global__ void __launch_bounds__(G * Shape<D, NP>::NPE, 1)
+    k_block_steps(const NskParams p, R* __restrict__ Ug, R* __restrict__ Kg, R* __restrict__ Rout, const int mode,
+                  const NskLsrkCoef coef, const R dt, const int nsteps, int* __restrict__ err) {
+  using S = Shape<D, NP>;
+  using L = BlockLayout<R, D, NP, G>;
+  extern __shared__ __align__(16) unsigned char block_smem_raw[];
+  R* sm = reinterpret_cast<R*>(block_smem_raw);
+  const long long E = p.E;
+  R* U = sm + L::U(E);
+  R* K = sm + L::K(E);
+  R* Q = sm + L::Q(E);
+  R* Utr = sm + L::Utr(E);
+  R* FVtr = sm + L::FVtr(E);
+  R* Fstar = sm + L::Fstar(E);
+  R* work = sm + L::Work(E);
+  const int nv = S::NV * p.nne;
+  const bool rk = mode != NSK_MODE_RHS;
+  for (int i = threadIdx.x; i < nv; i += blockDim.x) {
+    U[i] = Ug[i];
+    if (rk) K[i] = Kg[i];
+  }
+  __syncthreads();
+  const int ngroups = (int)((E + G - 1) / G);
+  const int nstage = rk ? 5 : 1;
+  int eflag = 0;
+  for (int step = 0; step < nsteps; ++step) {
+    for (int st = 0; st < nstage; ++st) {
+      if (step == 0 && st == 0) {  // later stages take the traces the volume phase wrote
+        for (long long idx = threadIdx.x; idx < (long long)S::NF * p.nfe; idx += blockDim.x)
+          prolong_item<R, D, NP>(p, U, Utr, idx);
+        __syncthreads();
+      }
+      for (int gi = 0; gi < ngroups; ++gi)  // ends with a block barrier
+        lift_group<R, D, NP, G, 0, true>(p, U, Utr, Q, FVtr, (long long)gi * G, work, eflag);
+      for (long long idx = threadIdx.x; idx < (long long)D * p.nfe; idx += blockDim.x)
+        face_item<R, D, NP>(p, Utr, FVtr, Fstar, idx, eflag);
+      __syncthreads();
+      const bool last = step == nsteps - 1 && st == nstage - 1;
+      for (int gi = 0; gi < ngroups; ++gi)  // ends with a block barrier; traces written in place
+        volume_group<R, D, NP, G, false, true, false>(p, U, Q, Fstar, Utr, FVtr, K, Rout, mode, (R)coef.A[st],
+                                               (R)coef.B[st], dt, (long long)gi * G, work, eflag,
+                                               last ? nullptr : Utr);
+    }
+  }
+  if (rk) {
+    for (int i = threadIdx.x; i < nv; i += blockDim.x) {
+      Ug[i] = U[i];
+      Kg[i] = K[i];
+    }
+  }
+  if (eflag) atomicOr(err, eflag);
+}
+
 // --------------------------------------------------------------------------
 // k_dt: max over nodes of sum_k (|v_k| + sqrt(p_alpha'(rho))) / h_k (FP64), as
 // the bits of a non-negative double (monotone as unsigned integers).
@@ -1703,6 +1810,63 @@ int launch_stage_np(const NskParams& p, int np, bool fp32, const NskBuffers& b, 
 #define NSK_CASE(NPV)                                                                                     \
   case NPV:                                                                                               \
     return fp32 ? launch_stage<float, D, NPV>(p, b, l, s) : launch_stage<double, D, NPV>(p, b, l, s);
+    NSK_CASE(2)
+    NSK_CASE(3)
+    NSK_CASE(4)
+    NSK_CASE(5)
+    NSK_CASE(6)
+#undef NSK_CASE
+    default:
+      return NSK_ERR_ARG;
+  }
+}
+
+// shared memory the single-block schedule needs for a mesh (0 when N is not compiled here)
+template <typename R, int D, int NP>
+size_t block_bytes_t(const NskParams& p) {
+  return sizeof(R) * BlockLayout<R, D, NP, group_for<D, NP>(256)>::total(p.E);
+}
+
+template <typename R, int D, int NP>
+int launch_block_t(const NskParams& p, const NskBuffers& b, int mode, const NskLsrkCoef& coef, double dt,
+                   int nsteps, void* Rout, cudaStream_t s) {
+  constexpr int G = group_for<D, NP>(256);
+  static const bool attr_ok = cudaFuncSetAttribute(k_block_steps<R, D, NP, G>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   kBlockSmemMax) == cudaSuccess;
+  if (!attr_ok) return NSK_ERR_CUDA;
+  const size_t bytes = block_bytes_t<R, D, NP>(p);
+  if (bytes > (size_t)kBlockSmemMax) return NSK_ERR_ARG;
+  k_block_steps<R, D, NP, G><<<1, G * Shape<D, NP>::NPE, bytes, s>>>(p, (R*)b.U, (R*)b.K, (R*)Rout, mode, coef,
+                                                                        (R)dt, nsteps, b.err);
+  return cudaGetLastError() == cudaSuccess ? 1 : NSK_ERR_CUDA;
+}
+
+template <int D>
+size_t block_bytes_np(const NskParams& p, int np, bool fp32) {
+  switch (np) {
+#define NSK_CASE(NPV) \
+  case NPV:           \
+    return fp32 ? block_bytes_t<float, D, NPV>(p) : block_bytes_t<double, D, NPV>(p);
+    NSK_CASE(2)
+    NSK_CASE(3)
+    NSK_CASE(4)
+    NSK_CASE(5)
+    NSK_CASE(6)
+#undef NSK_CASE
+    default:
+      return (size_t)-1;
+  }
+}
+
+template <int D>
+int launch_block_np(const NskParams& p, int np, bool fp32, const NskBuffers& b, int mode, const NskLsrkCoef& coef,
+                    double dt, int nsteps, void* Rout, cudaStream_t s) {
+  switch (np) {
+#define NSK_CASE(NPV)                                                                        \
+  case NPV:                                                                                  \
+    return fp32 ? launch_block_t<float, D, NPV>(p, b, mode, coef, dt, nsteps, Rout, s)      \
+                : launch_block_t<double, D, NPV>(p, b, mode, coef, dt, nsteps, Rout, s);
     NSK_CASE(2)
     NSK_CASE(3)
     NSK_CASE(4)

@@ -1,6 +1,7 @@
 // nsk_mlp.cu -- tensor-core building blocks of the learned c-closure: the tcgen05 BF16
 // GEMM exposed through the C ABI (nsk_gemm_bf16) for testing and reuse.
 #include "nsk_kernels.cuh"
+#include "nsk_nvtx.h"
 #include "nsk_tc.cuh"
 #include "nsk_test_hooks.h"
 
@@ -414,6 +415,7 @@ int nsk_mlp_set_fused_forward(nsk_mlp* m, int on) {
 }
 
 int nsk_mlp_forward(nsk_mlp* m, const void* X, int rows, float* Y) {
+  const NskRange nvtx_range("nsk_mlp_forward");
   if (!m || !X || !Y || rows < 1 || rows > m->max_rows) return NSK_ERR_ARG;
   return mlp_forward_on(m, (const __nv_bfloat16*)X, rows, Y, m->stream, m->err);
 }
@@ -429,6 +431,7 @@ int nsk_mlp_gradients(nsk_mlp* m, const void* X, const float* T, int batch, floa
 }
 
 int nsk_mlp_train_step(nsk_mlp* m, const void* X, const float* T, int batch, double lr, double* loss) {
+  const NskRange nvtx_range("nsk_mlp_train_step");
   if (!m || !X || !T || batch < 16 || batch > m->max_batch || (batch % 16) || !(lr > 0.0)) return NSK_ERR_ARG;
   int st = mlp_grad(m, (const __nv_bfloat16*)X, T, batch);
   if (st) return st;

@@ -9,6 +9,7 @@ still works, but every call raises: there is no CPU fallback.
 from __future__ import annotations
 
 import ctypes as C
+import os
 from pathlib import Path
 
 import numpy as np
@@ -23,6 +24,8 @@ NSK_ERR_NONPHYSICAL = -3
 NSK_ERR_TIMEOUT = -4
 NSK_ERR_STATE = -5
 NSK_ERR_NOMEM = -6
+NSK_ERR_IO = -7
+NSK_ERR_BOUNDS = -8
 NSK_NODES_GAUSS = 0
 NSK_NODES_GAUSS_LOBATTO = 1
 NSK_FP64 = 0
@@ -73,6 +76,8 @@ SIGNATURES = {
     "nsk_autotune": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), _dp]),
     "nsk_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_void_p)]),
     "nsk_measure_fma_rate": (C.c_int, [C.c_int, C.c_int, _dp, _dp, C.c_void_p]),
+    "nsk_save_checkpoint": (C.c_int, [C.c_void_p, C.c_char_p, C.c_double, C.c_longlong]),
+    "nsk_load_checkpoint": (C.c_int, [C.c_void_p, C.c_char_p, _dp, C.POINTER(C.c_longlong)]),
     "nsk_batch_step": (C.c_int, [C.c_void_p, C.c_int, C.c_double, _dp, _dp]),
     "nsk_batch_set_schedule": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int]),
     "nsk_batch_get_schedule": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
@@ -83,6 +88,7 @@ SIGNATURES = {
     "nsk_test_hook_block_batch_barrier": (C.c_int, [C.c_void_p]),
     "nsk_test_hook_tc_grid_cap": (C.c_int, [C.c_int]),
     "nsk_test_hook_math": (C.c_int, [C.c_int, C.c_void_p, C.c_void_p, C.c_longlong, C.c_void_p]),
+    "nsk_test_hook_corrupt_neighbours": (C.c_int, [C.c_void_p]),
     "nsk_batch_destroy": (None, [C.c_void_p]),
     "nsk_gemm_bf16": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                 C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_int,
@@ -119,11 +125,12 @@ class NskError(RuntimeError):
 
 
 def load_library(path: str | Path | None = None):
-    """Load libnsk.so (built by build.build_library()); raises if it is absent."""
+    """Load libnsk.so (built by build.build_library()), or the library the environment variable
+    NSK_LIBRARY names (e.g. the bounds-checking libnsk_check.so); raises if it is absent."""
     global _lib
     if _lib is not None and path is None:
         return _lib
-    p = Path(path) if path else LIB_PATH
+    p = Path(path) if path else Path(os.environ.get("NSK_LIBRARY") or LIB_PATH)
     if not p.exists():
         raise RuntimeError(f"libnsk.so not found at {p}: build it with paper_1912_12059_gb300.build.build_library() "
                            "(there is no CPU fallback)")
@@ -360,6 +367,20 @@ class Solver:
                "nsk_step_esdirk")
         return {"newton": st[0], "krylov": st[1], "rhs": st[2], "failed": st[3]}
 
+    def save_checkpoint(self, path, t=0.0, step=0):
+        """Write the state (FP64), the parameters and the caller's time and step counter to path
+        (the binary format of nsk_save_checkpoint in include/nsk.h)."""
+        _check(load_library().nsk_save_checkpoint(self.ctx, str(path).encode(), float(t), int(step)),
+               "nsk_save_checkpoint")
+
+    def load_checkpoint(self, path):
+        """Read a checkpoint of a context with this mesh; sets the parameters and the state and
+        returns (t, step). Stepping on gives the same bits as never stopping."""
+        t, step = C.c_double(), C.c_longlong()
+        _check(load_library().nsk_load_checkpoint(self.ctx, str(path).encode(), C.byref(t), C.byref(step)),
+               "nsk_load_checkpoint")
+        return t.value, step.value
+
     def diagnostics(self):
         m, e, l2 = C.c_double(), C.c_double(), C.c_double()
         _check(load_library().nsk_diagnostics(self.ctx, C.byref(m), C.byref(e), C.byref(l2)), "nsk_diagnostics")
@@ -367,7 +388,8 @@ class Solver:
 
     def set_schedule(self, tpb=256, fused_face=0):
         """fused_face: 0 separate face pass, 1 (or True) face fluxes in the volume kernel, 2 the
-        lean two-launch stage (lifting recomputed on chip by the volume kernel)."""
+        lean two-launch stage (lifting recomputed on chip by the volume kernel), 3 the
+        single-block schedule for small meshes (a whole call in one launch)."""
         _check(load_library().nsk_set_schedule(self.ctx, tpb, int(fused_face)), "nsk_set_schedule")
 
     def get_schedule(self):
@@ -417,19 +439,20 @@ class Solver:
         _check(load_library().nsk_closure_judge(self.ctx, C.byref(e)), "nsk_closure_judge")
         return e.value
 
-    KERNELS = ("k_prolong", "k_lift", "k_face", "k_volume")
+    KERNELS = ("k_prolong", "k_lift", "k_face", "k_volume", "k_block")
 
     def set_profiling(self, on=True):
         _check(load_library().nsk_set_profiling(self.ctx, int(bool(on))), "nsk_set_profiling")
 
     def get_profile(self, reset=False):
         """{kernel: (total ms, launches)} accumulated while profiling was on."""
-        ms = (C.c_double * 4)()
-        cnt = (C.c_longlong * 4)()
-        n = load_library().nsk_get_profile(self.ctx, ms, cnt, 4, int(bool(reset)))
+        nk = len(self.KERNELS)
+        ms = (C.c_double * nk)()
+        cnt = (C.c_longlong * nk)()
+        n = load_library().nsk_get_profile(self.ctx, ms, cnt, nk, int(bool(reset)))
         if n < 0:
             raise NskError(n, "nsk_get_profile")
-        return {self.KERNELS[k]: (ms[k], cnt[k]) for k in range(min(n, 4))}
+        return {self.KERNELS[k]: (ms[k], cnt[k]) for k in range(min(n, nk)) if cnt[k] or k < 4}
 
     @property
     def launch_count(self):

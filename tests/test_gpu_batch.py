@@ -26,14 +26,15 @@ def _state(s, seed):
 @pytest.mark.parametrize("dim,ne,N", [(3, (5, 4, 3), 2), (3, (5, 4, 3), 3), (3, (5, 4, 3), 4), (3, (3, 2, 3), 5),
                                       (2, (7, 5), 3), (2, (6, 3), 5), (1, (9,), 3), (1, (5,), 1)])
 def test_schedules_are_bit_identical(gpu, precision, dim, ne, N):
-    """Separate face pass, face fluxes in the volume kernel, and the lean two-launch stage (the
-    lifting recomputed on chip), at both block sizes: the same bits."""
+    """Separate face pass, face fluxes in the volume kernel, the lean two-launch stage (the
+    lifting recomputed on chip) and the single-block schedule (where the mesh fits one block; the
+    separate face pass elsewhere), at both block sizes: the same bits."""
     s = nsk.Solver(dim, ne, N, [0] * dim, [1] * dim, 0, precision)
     s.set_params(**PRM)
     U = _state(s, 1)
     results = []
     for tpb in (128, 256):
-        for fused in (0, 1, 2):
+        for fused in (0, 1, 2, 3):
             s.set_schedule(tpb, fused)
             s.set_state(U)
             R = s.rhs()

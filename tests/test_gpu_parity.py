@@ -335,3 +335,32 @@ def test_full_size_head_on_collision_tiled(gpu):
     err, per_var = state_rel_err(Ug, Uo)
     assert err <= 1e-12, per_var
     s.close()
+
+
+@pytest.mark.parametrize("name", ["slab1d_gll", "slab1d_gl_paper_params"])
+def test_single_block_schedule(gpu, name):
+    """The single-block schedule (a small mesh's whole nsk_step call in one launch, arrays in shared
+    memory): one launch per call, 100 steps within 1e-11 of the oracle per variable, and the same
+    bits as the separate face pass (residual and steps; the residual's oracle parity is the
+    separate pass's)."""
+    s, o, U = _physical_case(name)
+    dt = o.timestep(U, 0.5)
+    s.set_schedule(256, 3)
+    s.set_state(U)
+    s.set_profiling(True)
+    n0 = s.launch_count
+    s.step(dt, 100)
+    prof = s.get_profile(reset=True)
+    assert s.launch_count - n0 == 1 and prof["k_block"][1] == 1
+    Ub = s.get_state()
+    err, per_var = state_rel_err(Ub, o.step(U, dt, 100))
+    assert err <= 1e-11, per_var
+    s.set_state(U)
+    Rg = s.rhs()
+    s.set_schedule(256, 0)
+    s.set_state(U)
+    assert np.array_equal(s.rhs(), Rg)
+    s.step(dt, 100)
+    assert np.array_equal(s.get_state(), Ub)
+    s.set_profiling(False)
+    s.close()
