@@ -3,7 +3,7 @@ state, wave speeds, time step and diagnostic sums in FP64.
 
 Single-operator bound: the FP64 bound of the parity tests scaled from the FP64
 to the FP32 unit roundoff (about 1e-6 of (2/h)(N+1)^2 max|flux|, plus 1e-5 of
-the residual). Over time the benchmark spec's acceptance is the density L2 error
+the residual). Over time the FP32 operator's acceptance is the density L2 error
 relative to the FP64 run, required <= 1e-4; it is measured here on small
 droplet problems and reported by the benchmark at full size.
 """
