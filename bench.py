@@ -1155,8 +1155,11 @@ def run_gemm(args, rank, world):
     m.init_params(seed=0)
     flops = 2 * rows * (144 * 256 + 256 * 256 + 256 * 64)
     fwd = {}
-    for fused in (True, False):
+    # the fused kernel where it applies (warp-specialised, operands by TMA), the fused kernel that runs
+    # its stages one after another, and the three per-layer GEMMs
+    for name, fused, serial in (("fused", True, 0), ("fused_serial", True, 1), ("three_gemms", False, 0)):
         m.set_fused_forward(fused)
+        nsk._test_hook_mlp_fwd_kernel(serial)
         for _ in range(args.warmup):
             m.forward(X, Y)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -1167,9 +1170,10 @@ def run_gemm(args, rank, world):
         e1.record()
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / args.steps
-        fwd["fused" if fused else "three_gemms"] = {"ms": ms, "tflops": flops / ms / 1e9,
-                                                     "frac_of_bf16_peak": flops / ms / 1e9 / tc_peak,
-                                                     "hbm_gbs": (rows * 144 * 2 + rows * 64 * 4) / ms / 1e6}
+        fwd[name] = {"ms": ms, "tflops": flops / ms / 1e9,
+                     "frac_of_bf16_peak": flops / ms / 1e9 / tc_peak,
+                     "hbm_gbs": (rows * 144 * 2 + rows * 64 * 4) / ms / 1e6}
+    nsk._test_hook_mlp_fwd_kernel(0)
     m.close()
     if rank == 0:
         ms = fwd["fused"]["ms"]

@@ -32,6 +32,15 @@ int nsk_test_hook_block_batch_barrier(nsk_batch* batch);
  * the same with and without a cap. NSK_ERR_ARG for a negative cap. */
 int nsk_test_hook_tc_grid_cap(int max_ctas);
 
+/* Selects the kernel of the fused inference forward (nsk_mlp_forward with the
+ * fused forward on): 0 (the default) the warp-specialised kernel, whose operands
+ * arrive by TMA and whose load, MMA and epilogue stages overlap, wherever it
+ * applies (n_out <= 64 and its buffers fit in shared memory); 1 always the
+ * kernel that runs the stages one after another. Both perform the same MMAs in
+ * the same order with the same epilogue arithmetic. Process-wide. NSK_ERR_ARG
+ * for another value. */
+int nsk_test_hook_mlp_fwd_kernel(int which);
+
 /* The FP64 reciprocal (fn = 0) and square root (fn = 1) the stage kernels use
  * (Newton-Raphson from the FP32 hardware approximations; CUDA's own division
  * and sqrt outside 2^-120 < x < 2^120), evaluated on the device arrays x -> y

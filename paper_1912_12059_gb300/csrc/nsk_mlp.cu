@@ -8,8 +8,15 @@
 namespace nsk {
 namespace tc {
 int g_grid_cap = 0;
+int g_fwd_kernel = 0;
 }  // namespace tc
 }  // namespace nsk
+
+extern "C" int nsk_test_hook_mlp_fwd_kernel(int which) {
+  if (which < 0 || which > 1) return NSK_ERR_ARG;
+  nsk::tc::g_fwd_kernel = which;
+  return NSK_OK;
+}
 
 extern "C" int nsk_test_hook_tc_grid_cap(int max_ctas) {
   if (max_ctas < 0) return NSK_ERR_ARG;

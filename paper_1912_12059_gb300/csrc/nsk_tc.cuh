@@ -13,6 +13,7 @@
 // i.e. rows 32w..32w+31 of the tile) and applies one of the fused epilogues below.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
 
@@ -727,6 +728,398 @@ __global__ void __launch_bounds__(kFwThreads, 1) k_mlp_fwd3(const MlpFwdArgs a) 
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tm), "r"(512));
 }
 
+// ---------------------------------------------------------------------------
+// Warp-specialised fused forward: the same network, the same MMAs in the same K order and the
+// same GELU and BF16 rounding as k_mlp_fwd3, with the stages overlapped:
+//  - operands arrive by TMA (cp.async.bulk.tensor, boxes 8 K columns wide that land directly in
+//    the K-major no-swizzle core-matrix layout below); one warp issues the loads, one warp the
+//    MMAs, and kWsEpiWarps warps run the epilogues;
+//  - W2 stays resident; W1 and W3 stream through a ring of slabs of 16 K columns;
+//  - a layer's activations are written in 64-column chunks into a two-slot ring, and the next
+//    layer's MMAs consume chunk c while the epilogue produces chunk c + 1;
+//  - layer 1 of the next tile accumulates in TMEM columns [0, H1) while the epilogue works on
+//    layer 2 ([256, 256 + H2)) and drains layer 3 ([256, 256 + NO), NO <= 64: inside layer 2's
+//    first chunk, which the epilogue has read before the first layer-3 MMA is issued).
+// Operand layout in shared memory (what one TMA box of 8 K columns x R rows writes, boxes side by
+// side along K): element (r, k) at (k / 8) R 16 + r 16 + (k % 8) 2 bytes, so core matrices
+// adjacent along K are R 16 bytes apart (the descriptor's leading byte offset) and along M or N
+// 128 bytes apart (its stride byte offset).
+// ---------------------------------------------------------------------------
+constexpr int kWsEpiWarps = 16;                       // 4 per TMEM lane quarter
+constexpr int kWsThreads = (kWsEpiWarps + 2) * 32;    // + the TMA warp and the MMA warp
+constexpr int kWsHChunk = 64;                         // activation columns per ring slot
+constexpr int kWsHSlot = kBM * kWsHChunk * 2;         // bytes of one activation slot
+constexpr int kWsMaxRing = 4;
+
+struct FwdMaps {
+  CUtensorMap x, w1, w2, w3;  // X [M][ldx], W1 [H1][K1], W2 [H2][H1], W3 [NO][H2], boxes 8 x rows
+};
+
+__host__ __device__ inline int ws_slot_bytes(const MlpFwdArgs& a) { return (a.H1 > a.NO ? a.H1 : a.NO) * 32; }
+__host__ __device__ inline int ws_off_x(const MlpFwdArgs& a) { return fw_align(a.H2 * a.H1 * 2); }
+__host__ __device__ inline int ws_off_h(const MlpFwdArgs& a) { return ws_off_x(a) + fw_align(kBM * a.K1 * 2); }
+__host__ __device__ inline int ws_off_w(const MlpFwdArgs& a) { return ws_off_h(a) + 2 * kWsHSlot; }
+__host__ __device__ inline int ws_off_bias(const MlpFwdArgs& a, int ns) {
+  return ws_off_w(a) + fw_align(ns * ws_slot_bytes(a));
+}
+__host__ __device__ inline int ws_smem_bytes(const MlpFwdArgs& a, int ns) {
+  return ws_off_bias(a, ns) + (a.H1 + a.H2 + a.NO) * 4;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int c0, int c1, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+__device__ __forceinline__ void ws_mma(uint32_t d, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+}
+__device__ __forceinline__ void ws_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar));
+}
+
+// Wait for the phase of parity `parity` of an mbarrier, bounded in time; gives up early when
+// another role has already aborted (flag set), and sets the flag and the error word on a timeout.
+__device__ __forceinline__ bool ws_wait(uint32_t bar, uint32_t parity, int* err, volatile int* abort_flag) {
+  const unsigned long long t0 = tc_global_ns();
+  while (true) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (*abort_flag) return false;
+    if (tc_global_ns() - t0 > kWaitNs) {
+      atomicOr(err, NSK_EBIT_TIMEOUT);
+      *abort_flag = 1;
+      return false;
+    }
+  }
+}
+// the same for all lanes of a warp, with a warp-uniform result
+__device__ __forceinline__ bool ws_wait_warp(uint32_t bar, uint32_t parity, int* err, volatile int* abort_flag) {
+  const bool ok = ws_wait(bar, parity, err, abort_flag);
+  return __all_sync(0xffffffffu, ok);
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* v) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// GELU(accumulator + bias) of 16 columns of the warp's 32 rows as BF16 into an activation slot:
+// the thread's row r, slot-local columns [kk, kk + 16) (kk a multiple of 16); bias: the 16 biases
+// in shared memory (every lane reads the same addresses: broadcast loads)
+__device__ __forceinline__ void ws_gelu16(uint32_t taddr, const float* bias, unsigned char* slot, int r, int kk) {
+  uint32_t v[16];
+  tmem_ld16(taddr, v);
+  float b[16];
+#pragma unroll
+  for (int g = 0; g < 4; ++g) {
+    const float4 t = reinterpret_cast<const float4*>(bias)[g];
+    b[4 * g] = t.x;
+    b[4 * g + 1] = t.y;
+    b[4 * g + 2] = t.z;
+    b[4 * g + 3] = t.w;
+  }
+#pragma unroll
+  for (int g = 0; g < 2; ++g) {
+    __align__(16) __nv_bfloat16 h[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) h[j] = __float2bfloat16_rn(gelu(__uint_as_float(v[g * 8 + j]) + b[g * 8 + j]));
+    *reinterpret_cast<uint4*>(slot + ((kk >> 3) + g) * (kBM * 16) + r * 16) = *reinterpret_cast<const uint4*>(h);
+  }
+}
+
+// barrier indices in the kernel's array
+enum WsBar : int {
+  WB_W2 = 0, WB_XFULL, WB_XFREE, WB_A1FULL, WB_A1FREE, WB_A2FULL, WB_A2FREE, WB_A3FULL, WB_FINAL,
+  WB_HFULL, WB_HFREE = WB_HFULL + 2, WB_WFULL = WB_HFREE + 2, WB_WFREE = WB_WFULL + kWsMaxRing,
+  WB_COUNT = WB_WFREE + kWsMaxRing
+};
+
+__global__ void __launch_bounds__(kWsThreads, 1)
+    k_mlp_fwd3_ws(const MlpFwdArgs a, const int ns, const __grid_constant__ FwdMaps maps) {
+  extern __shared__ __align__(128) unsigned char ws_smem[];
+  __shared__ __align__(8) uint64_t bars[WB_COUNT];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int aborted_s;
+  volatile int* aborted = &aborted_s;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ntiles = (a.M + kBM - 1) / kBM;
+  const int slotb = ws_slot_bytes(a);
+  const uint32_t aW2 = smem_u32(ws_smem), aX = smem_u32(ws_smem + ws_off_x(a)), aH = smem_u32(ws_smem + ws_off_h(a));
+  const uint32_t aW = smem_u32(ws_smem + ws_off_w(a));
+  unsigned char* sH = ws_smem + ws_off_h(a);
+  float* sB = reinterpret_cast<float*>(ws_smem + ws_off_bias(a, ns));  // b1 | b2 | b3
+  auto bar = [&](int i) { return smem_u32(&bars[i]); };
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (threadIdx.x == 0) {
+    aborted_s = 0;
+    for (int i = 0; i < WB_COUNT; ++i) {
+      const bool epi = i == WB_A1FREE || i == WB_A2FREE || i == WB_HFULL || i == WB_HFULL + 1;
+      mbar_init(bar(i), epi ? kWsEpiWarps : 1);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  for (int i = threadIdx.x; i < a.H1 + a.H2 + a.NO; i += kWsThreads)
+    sB[i] = i < a.H1 ? a.b1[i] : (i < a.H1 + a.H2 ? a.b2[i - a.H1] : a.b3[i - a.H1 - a.H2]);
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tm = tmem_slot;
+
+  if (warp == kWsEpiWarps) {
+    // ---- TMA producer: W2 once; per tile: the next tile's X and W1 slabs, then this tile's W3 slabs
+    // (the order in which the MMA warp consumes the ring) ----
+    if (lane == 0) {
+      uint32_t xph = 1u, r = 0u, nx = 0u;
+      int armed[kWsMaxRing];
+      for (int i = 0; i < kWsMaxRing; ++i) armed[i] = 0;
+      bool ok = true;
+      auto load_x = [&](int t) {
+        ok = ok && ws_wait(bar(WB_XFREE), xph, a.err, aborted);
+        xph ^= 1u;
+        if (!ok) return;
+        mbar_expect_tx(bar(WB_XFULL), (uint32_t)(kBM * a.K1 * 2));
+        for (int b = 0; b < a.K1 / 8; ++b) tma_load_2d(aX + (uint32_t)(b * kBM * 16), &maps.x, 8 * b, t * kBM, bar(WB_XFULL));
+        ++nx;
+      };
+      auto load_slab = [&](const CUtensorMap* m, int rows, int k0) {
+        const uint32_t s = r % (uint32_t)ns;
+        ok = ok && ws_wait(bar(WB_WFREE + s), ((r / ns) & 1u) ^ 1u, a.err, aborted);
+        if (!ok) return;
+        const uint32_t dst = aW + s * (uint32_t)slotb;
+        mbar_expect_tx(bar(WB_WFULL + s), (uint32_t)(rows * 32));
+        tma_load_2d(dst, m, k0, 0, bar(WB_WFULL + s));
+        tma_load_2d(dst + (uint32_t)(rows * 16), m, k0 + 8, 0, bar(WB_WFULL + s));
+        armed[s] = (int)(r / ns) + 1;
+        ++r;
+      };
+      mbar_expect_tx(bar(WB_W2), (uint32_t)(a.H2 * a.H1 * 2));
+      for (int b = 0; b < a.H1 / 8; ++b) tma_load_2d(aW2 + (uint32_t)(b * a.H2 * 16), &maps.w2, 8 * b, 0, bar(WB_W2));
+      int t = blockIdx.x;
+      if (t < ntiles) {
+        load_x(t);
+        for (int k0 = 0; ok && k0 < a.K1; k0 += 16) load_slab(&maps.w1, a.H1, k0);
+      }
+      for (; ok && t < ntiles; t += gridDim.x) {
+        if (t + (int)gridDim.x < ntiles) {
+          load_x(t + gridDim.x);
+          for (int k0 = 0; ok && k0 < a.K1; k0 += 16) load_slab(&maps.w1, a.H1, k0);
+        }
+        for (int k0 = 0; ok && k0 < a.H2; k0 += 16) load_slab(&maps.w3, a.NO, k0);
+      }
+      // every copy this thread started has landed before the CTA exits (bounded waits; all have on
+      // the normal path, where the MMA warp consumed them)
+      volatile int never = 0;
+      ws_wait(bar(WB_W2), 0u, a.err, &never);
+      if (nx > 0) ws_wait(bar(WB_XFULL), (nx - 1u) & 1u, a.err, &never);
+      for (int s = 0; s < ns; ++s)
+        if (armed[s] > 0) ws_wait(bar(WB_WFULL + s), (uint32_t)(armed[s] - 1) & 1u, a.err, &never);
+    }
+  } else if (warp == kWsEpiWarps + 1) {
+    // ---- MMA issuer: L1(first); per tile t: L2(t) chunk by chunk, L1(next), L3(t) chunk by chunk ----
+    if (lane == 0) {
+      uint32_t xph = 0u, a1f = 1u, a2f = 1u, r = 0u, v = 0u;
+      const uint32_t id1 = idesc_bf16(kBM, a.H1), id2 = idesc_bf16(kBM, a.H2), id3 = idesc_bf16(kBM, a.NO);
+      bool ok = ws_wait(bar(WB_W2), 0u, a.err, aborted);
+      auto layer1 = [&]() {
+        ok = ok && ws_wait(bar(WB_A1FREE), a1f, a.err, aborted);
+        a1f ^= 1u;
+        ok = ok && ws_wait(bar(WB_XFULL), xph, a.err, aborted);
+        xph ^= 1u;
+        for (int s = 0; ok && s < a.K1 / 16; ++s) {
+          const uint32_t rs = r % (uint32_t)ns;
+          ok = ws_wait(bar(WB_WFULL + rs), (r / ns) & 1u, a.err, aborted);
+          if (!ok) break;
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          ws_mma(tm, sdesc(aX + (uint32_t)(s * 2 * kBM * 16), kBM * 16, 128),
+                 sdesc(aW + rs * (uint32_t)slotb, (uint32_t)(a.H1 * 16), 128), id1, s > 0 ? 1u : 0u);
+          ws_commit(bar(WB_WFREE + rs));
+          ++r;
+        }
+        if (ok) {
+          ws_commit(bar(WB_XFREE));
+          ws_commit(bar(WB_A1FULL));
+        }
+      };
+      int t = blockIdx.x;
+      if (ok && t < ntiles) layer1();
+      for (; ok && t < ntiles; t += gridDim.x) {
+        ok = ws_wait(bar(WB_A2FREE), a2f, a.err, aborted);
+        a2f ^= 1u;
+        for (int c = 0; ok && c < a.H1; c += kWsHChunk) {  // layer 2: activation chunks x resident W2
+          const uint32_t hs = v & 1u;
+          ok = ws_wait(bar(WB_HFULL + hs), (v >> 1) & 1u, a.err, aborted);
+          if (!ok) break;
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          const int w = min(kWsHChunk, a.H1 - c);
+          for (int s = 0; s < w / 16; ++s)
+            ws_mma(tm + 256u, sdesc(aH + hs * kWsHSlot + (uint32_t)(s * 2 * kBM * 16), kBM * 16, 128),
+                   sdesc(aW2 + (uint32_t)(((c + 16 * s) / 8) * a.H2 * 16), (uint32_t)(a.H2 * 16), 128), id2,
+                   (c > 0 || s > 0) ? 1u : 0u);
+          ws_commit(bar(WB_HFREE + hs));
+          ++v;
+        }
+        if (!ok) break;
+        ws_commit(bar(WB_A2FULL));
+        if (t + (int)gridDim.x < ntiles) layer1();
+        for (int c = 0; ok && c < a.H2; c += kWsHChunk) {  // layer 3: activation chunks x streamed W3
+          const uint32_t hs = v & 1u;
+          ok = ws_wait(bar(WB_HFULL + hs), (v >> 1) & 1u, a.err, aborted);
+          if (!ok) break;
+          const int w = min(kWsHChunk, a.H2 - c);
+          for (int s = 0; ok && s < w / 16; ++s) {
+            const uint32_t rs = r % (uint32_t)ns;
+            ok = ws_wait(bar(WB_WFULL + rs), (r / ns) & 1u, a.err, aborted);
+            if (!ok) break;
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            ws_mma(tm + 256u, sdesc(aH + hs * kWsHSlot + (uint32_t)(s * 2 * kBM * 16), kBM * 16, 128),
+                   sdesc(aW + rs * (uint32_t)slotb, (uint32_t)(a.NO * 16), 128), id3, (c > 0 || s > 0) ? 1u : 0u);
+            ws_commit(bar(WB_WFREE + rs));
+            ++r;
+          }
+          ws_commit(bar(WB_HFREE + hs));
+          ++v;
+        }
+        if (ok) ws_commit(bar(WB_A3FULL));
+      }
+      // every MMA this thread issued has completed before TMEM is released (bounded wait)
+      ws_commit(bar(WB_FINAL));
+      volatile int never = 0;
+      ws_wait(bar(WB_FINAL), 0u, a.err, &never);
+    }
+  } else {
+    // ---- epilogue warps: warp w reads TMEM lanes 32 (w % 4).. (rows q 32 + lane) and the 16-column
+    // block w / 4 of each 64-column chunk ----
+    const int q = warp & 3, sub = warp >> 2, r = q * 32 + lane;
+    const uint32_t lanes = (uint32_t)(q * 32) << 16;
+    uint32_t f1 = 0u, f2 = 0u, f3 = 0u, u = 0u;
+    bool ok = true;
+    auto gelu_layer = [&](uint32_t col0, int H, const float* bias) {
+      for (int c = 0; ok && c < H; c += kWsHChunk) {
+        const uint32_t hs = u & 1u;
+        ok = ws_wait_warp(bar(WB_HFREE + hs), ((u >> 1) & 1u) ^ 1u, a.err, aborted);
+        if (!ok) break;
+        const int cc = c + sub * 16;
+        if (cc < H) ws_gelu16(tm + lanes + col0 + (uint32_t)cc, bias + cc, sH + hs * kWsHSlot, r, sub * 16);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(bar(WB_HFULL + hs));
+        ++u;
+      }
+    };
+    for (int t = blockIdx.x; ok && t < ntiles; t += gridDim.x) {
+      ok = ws_wait_warp(bar(WB_A1FULL), f1, a.err, aborted);
+      f1 ^= 1u;
+      if (!ok) break;
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      gelu_layer(0u, a.H1, sB);
+      if (!ok) break;
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(bar(WB_A1FREE));
+      ok = ws_wait_warp(bar(WB_A2FULL), f2, a.err, aborted);
+      f2 ^= 1u;
+      if (!ok) break;
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      gelu_layer(256u, a.H2, sB + a.H1);
+      if (!ok) break;
+      ok = ws_wait_warp(bar(WB_A3FULL), f3, a.err, aborted);
+      f3 ^= 1u;
+      if (!ok) break;
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      if (sub * 16 < a.NO) {  // layer 3: + b3 -> Y
+        uint32_t v[16];
+        tmem_ld16(tm + lanes + 256u + (uint32_t)(sub * 16), v);
+        const int m = t * kBM + r;
+        if (m < a.M) {
+          const float* b3 = sB + a.H1 + a.H2 + sub * 16;
+          float* y = a.Y + (size_t)m * a.ldy + sub * 16;
+#pragma unroll
+          for (int g = 0; g < 4; ++g)
+            *reinterpret_cast<float4*>(y + 4 * g) =
+                make_float4(__uint_as_float(v[4 * g]) + b3[4 * g], __uint_as_float(v[4 * g + 1]) + b3[4 * g + 1],
+                            __uint_as_float(v[4 * g + 2]) + b3[4 * g + 2], __uint_as_float(v[4 * g + 3]) + b3[4 * g + 3]);
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(bar(WB_A2FREE));
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tm), "r"(512));
+  }
+}
+
+// cuTensorMapEncodeTiled, taken from the driver through the runtime (no link-time dependency)
+typedef CUresult (*TmapEncodeFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+inline TmapEncodeFn tmap_encode_fn() {
+  static TmapEncodeFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<TmapEncodeFn>(p);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+// 2D BF16 tensor map of a row-major [rows][ld] matrix, columns [0, cols) used; boxes of
+// 8 columns x box_rows rows; rows beyond the matrix read as zero
+inline bool bf16_tmap(CUtensorMap* m, const void* base, int cols, int rows, int ld, int box_rows) {
+  const TmapEncodeFn fn = tmap_encode_fn();
+  if (!fn) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  const cuuint32_t box[2] = {8u, (cuuint32_t)box_rows};
+  const cuuint32_t es[2] = {1u, 1u};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// which fused forward launch_mlp_fwd3 uses: 0 the warp-specialised kernel where it applies,
+// 1 always k_mlp_fwd3 (set only by the test hook nsk_test_hook_mlp_fwd_kernel)
+extern int g_fwd_kernel;
+
 // fused forward when the network fits (NSK_ERR_ARG otherwise: the caller uses the per-layer GEMMs)
 inline int launch_mlp_fwd3(const MlpFwdArgs& a, cudaStream_t s) {
   auto a16 = [](const void* p) { return ((uintptr_t)p & 15u) == 0; };
@@ -752,6 +1145,27 @@ inline int launch_mlp_fwd3(const MlpFwdArgs& a, cudaStream_t s) {
     attr_done = true;
   }
   const int ntiles = (a.M + kBM - 1) / kBM;
+  // the warp-specialised kernel: layer 3 fits in layer 2's first activation chunk, the largest
+  // ring of W1/W3 slabs (2 to 4) that fits in shared memory, and the tensor maps can be made
+  if (g_fwd_kernel == 0 && a.NO <= kWsHChunk) {
+    int ns = kWsMaxRing;
+    while (ns >= 2 && ws_smem_bytes(a, ns) > kFwSmemMax) --ns;
+    FwdMaps maps;
+    if (ns >= 2 && bf16_tmap(&maps.x, a.X, a.K1, a.M, a.ldx, kBM) && bf16_tmap(&maps.w1, a.W1, a.K1, a.H1, a.K1, a.H1) &&
+        bf16_tmap(&maps.w2, a.W2, a.H1, a.H2, a.H1, a.H2) && bf16_tmap(&maps.w3, a.W3, a.H2, a.NO, a.H2, a.NO)) {
+      static bool ws_attr = false;
+      if (!ws_attr) {
+        if (cudaFuncSetAttribute(k_mlp_fwd3_ws, cudaFuncAttributeMaxDynamicSharedMemorySize, kFwSmemMax) !=
+            cudaSuccess) {
+          cudaGetLastError();
+          return NSK_ERR_CUDA;
+        }
+        ws_attr = true;
+      }
+      k_mlp_fwd3_ws<<<persistent_grid(ntiles, sms), kWsThreads, ws_smem_bytes(a, ns), s>>>(a, ns, maps);
+      return cudaGetLastError() == cudaSuccess ? NSK_OK : NSK_ERR_CUDA;
+    }
+  }
   k_mlp_fwd3<<<persistent_grid(ntiles, sms), kFwThreads, smem, s>>>(a);
   return cudaGetLastError() == cudaSuccess ? NSK_OK : NSK_ERR_CUDA;
 }

@@ -87,6 +87,7 @@ SIGNATURES = {
     "nsk_batch_set_timeout": (C.c_int, [C.c_void_p, C.c_double]),
     "nsk_test_hook_block_batch_barrier": (C.c_int, [C.c_void_p]),
     "nsk_test_hook_tc_grid_cap": (C.c_int, [C.c_int]),
+    "nsk_test_hook_mlp_fwd_kernel": (C.c_int, [C.c_int]),
     "nsk_test_hook_math": (C.c_int, [C.c_int, C.c_void_p, C.c_void_p, C.c_longlong, C.c_void_p]),
     "nsk_test_hook_corrupt_neighbours": (C.c_int, [C.c_void_p]),
     "nsk_batch_destroy": (None, [C.c_void_p]),
@@ -206,6 +207,12 @@ def nsk_rhs_static_scratch(dim, nelem, lo, hi, N, node_type, T, kappa, alpha, be
 def _test_hook_tc_grid_cap(max_ctas):
     """Test-only (include/nsk_test_hooks.h): cap the persistent tensor-core grids (0: no cap)."""
     _check(load_library().nsk_test_hook_tc_grid_cap(int(max_ctas)), "nsk_test_hook_tc_grid_cap")
+
+
+def _test_hook_mlp_fwd_kernel(which):
+    """Test-only (include/nsk_test_hooks.h): the fused forward's kernel, 0 the warp-specialised
+    TMA kernel where it applies, 1 always the stage-by-stage kernel."""
+    _check(load_library().nsk_test_hook_mlp_fwd_kernel(int(which)), "nsk_test_hook_mlp_fwd_kernel")
 
 
 def _test_hook_math(fn, x, y, stream=None):

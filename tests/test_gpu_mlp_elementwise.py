@@ -186,3 +186,40 @@ def test_grid_cap_leaves_results_unchanged(gpu, grid_cap):
     torch.cuda.synchronize()
     assert torch.equal(Y0, Y1)
     m.close()
+
+
+@pytest.fixture
+def fwd_kernel():
+    """Select the fused forward's kernel through the test hook; always reset to the default."""
+    yield lambda which: nsk._test_hook_mlp_fwd_kernel(which)
+    nsk._test_hook_mlp_fwd_kernel(0)
+
+
+@pytest.mark.parametrize("n_in,h1,h2,n_out,rows,cap", [(140, 256, 256, 64, 2000, 3), (140, 256, 256, 64, 60000, 0),
+                                                      (40, 64, 128, 32, 300, 1), (70, 128, 256, 16, 1000, 2),
+                                                      (24, 48, 80, 16, 777, 2)])
+def test_warp_specialised_forward_equals_serial_kernel(gpu, grid_cap, fwd_kernel, n_in, h1, h2, n_out, rows, cap):
+    """The warp-specialised forward (operands by TMA, load, MMA and epilogue stages overlapped across
+    activation chunks and row tiles) issues the same MMAs in the same K order with the same epilogue
+    arithmetic as the stage-by-stage kernel: the same outputs bit for bit, with several row tiles
+    per CTA, a ragged last tile, and hidden widths that are not multiples of its 64-column chunk."""
+    import torch
+
+    m, p = _network(n_in, h1, h2, n_out, 256, rows, seed=21)
+    m.set_fused_forward(True)
+    X, Xq, _ = _inputs(rows, n_in, m.n_in_pad, 22, gpu)
+    grid_cap(cap)
+    Ys = torch.full((rows, n_out), float("nan"), dtype=torch.float32, device=gpu)
+    Yw = torch.full((rows, n_out), float("nan"), dtype=torch.float32, device=gpu)
+    fwd_kernel(1)
+    m.forward(X, Ys)
+    fwd_kernel(0)
+    m.forward(X, Yw)
+    torch.cuda.synchronize()
+    assert torch.isfinite(Yw).all()
+    assert torch.equal(Ys, Yw), float((Ys - Yw).abs().max())
+    if rows <= 2000:  # and both within the elementwise bound of the oracle network
+        y_ref, E_y, _ = forward_bound(p, Xq)
+        got = Yw.cpu().double().numpy()
+        assert not (np.abs(got - y_ref) > 2.0 * E_y).any()
+    m.close()
