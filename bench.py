@@ -147,7 +147,8 @@ BATCH_KINDS = {0: "one launch per phase", 1: "persistent cooperative", 2: "insta
 def pick_schedule(s, fixed):
     """The autotuner's stage schedule, or a fixed "TPB,FUSED" one (profiling runs: under a
     profiler the autotuner's timings are serialised and would pick another schedule); FUSED is
-    0 (separate face pass), 1 (face fluxes in the volume kernel) or 2 (the lean stage)."""
+    0 (separate face pass), 1 (face fluxes in the volume kernel), 2 (the lean stage), 3 (the
+    single-block schedule) or 4 (the line-per-thread FP32 kernels)."""
     if fixed:
         tpb, fused = (int(v) for v in fixed.split(","))
         s.set_schedule(tpb, fused)

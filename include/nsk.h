@@ -289,7 +289,12 @@ int nsk_measure_fma_rate(int precision, int iters, double* tflops, double* ms, v
  *     a call's steps (fixed dt, no learned closure) or one residual in a single
  *     launch, on copies of the arrays in shared memory (relaxation model II,
  *     meshes whose arrays fit in 200 KB, e.g. 1D up to about 400 elements at
- *     N = 3 in FP64); where it does not apply the separate face pass runs.
+ *     N = 3 in FP64); where it does not apply the separate face pass runs;
+ *   4 the separate face pass with line-per-thread lifting and volume kernels
+ *     for the FP32 operator of relaxation model II on 3D elements with N = 3
+ *     (16 threads per element, each owning a line of 4 nodes: 16-byte loads
+ *     and stores, contractions along the line in registers); elsewhere the
+ *     separate face pass runs.
  * Default: tpb 256, separate face pass. Every expression that could be
  * contracted into a fused multiply-add in more than one way is written as an
  * explicit fma, and every schedule evaluates each value with the same code,
@@ -298,7 +303,7 @@ int nsk_measure_fma_rate(int precision, int iters, double* tflops, double* ms, v
 int nsk_set_schedule(nsk_ctx* ctx, int tpb, int fused_face);
 int nsk_get_schedule(nsk_ctx* ctx, int* tpb, int* fused_face);
 /* Autotuner: times one residual evaluation under each schedule (tpb 128 and
- * 256 with fused_face 0, 1, 2, and 3 where it applies; fused_face 0 and 1 for
+ * 256 with fused_face 0, 1, 2, and 3 and 4 where they apply; fused_face 0 and 1 for
  * the original NSK equations) on the context's current state (the state is not
  * modified), keeps the fastest and returns it (any output may be NULL; ms_out =
  * its time). */

@@ -287,6 +287,12 @@ int launch_block(nsk_ctx* c, int nsteps, double dt, void* Rout) {
   return NSK_OK;
 }
 
+// the line schedule (fused_face 4) has kernels for the FP32 operator of relaxation model II on
+// 3D elements with N = 3 (elsewhere it runs as the separate face pass)
+bool line_eligible(const nsk_ctx* c) {
+  return c->precision == NSK_FP32_MIXED && c->dim == 3 && c->np == 4 && c->p.model != NSK_MODEL_NSK && !c->fv_path();
+}
+
 int launch_stage(nsk_ctx* c, NskLaunch l) {
   if (l.fused_face == 3) {  // single-block schedule: a residual in one launch; otherwise the separate face pass
     if (l.mode == NSK_MODE_RHS && block_eligible(c)) return launch_block(c, 0, 0.0, l.Rout);
@@ -295,7 +301,9 @@ int launch_stage(nsk_ctx* c, NskLaunch l) {
   // kernels 0..3 = prolong, lift, face, volume
   const int mask = c->p.model == NSK_MODEL_NSK ? (l.mode == NSK_MODE_LIFT ? 3 : 15)
                                                 : ((l.traces_ready ? 0 : 1) | 2 |
-                                                   (l.mode == NSK_MODE_LIFT ? 0 : ((l.fused_face ? 0 : 4) | 8)));
+                                                   (l.mode == NSK_MODE_LIFT
+                                                        ? 0
+                                                        : (((l.fused_face == 0 || l.fused_face == 4) ? 4 : 0) | 8)));
   l.ev = prof_group(c, mask);
   int r;
   const bool f32 = c->precision == NSK_FP32_MIXED;
@@ -877,7 +885,7 @@ int nsk_get_sizes(nsk_ctx* c, long long* n_elem, int* nodes_per_elem, int* nvar)
 long long nsk_launch_count(nsk_ctx* c) { return c ? c->launches : -1; }
 
 int nsk_set_schedule(nsk_ctx* c, int tpb, int fused_face) {
-  if (!c || (tpb != 128 && tpb != 256) || fused_face < 0 || fused_face > 3) return NSK_ERR_ARG;
+  if (!c || (tpb != 128 && tpb != 256) || fused_face < 0 || fused_face > 4) return NSK_ERR_ARG;
   c->tpb = tpb;
   c->fused_face = fused_face;
   return NSK_OK;
@@ -903,11 +911,17 @@ int nsk_autotune(nsk_ctx* c, int* tpb_out, int* fused_out, double* ms_out) {
   c->prof_on = false;
   // the lean two-launch stage applies to relaxation model II only (the original NSK equations
   // have their own stage kernels and take the schedule's block size alone)
-  const int nsched = c->p.model == NSK_MODEL_NSK ? 2 : (block_eligible(c) ? 4 : 3);
+  // and the line schedule to the FP32 operator on 3D elements with N = 3
+  int sched[5], nsched = 0;
+  sched[nsched++] = 0;
+  sched[nsched++] = 1;
+  if (c->p.model != NSK_MODEL_NSK) sched[nsched++] = 2;
+  if (c->p.model != NSK_MODEL_NSK && block_eligible(c)) sched[nsched++] = 3;
+  if (line_eligible(c)) sched[nsched++] = 4;
   for (int it = 0; it < 2 && st == NSK_OK; ++it)
     for (int f = 0; f < nsched && st == NSK_OK; ++f) {
       c->tpb = tpbs[it];
-      c->fused_face = f;
+      c->fused_face = sched[f];
       NskLaunch l = {NSK_MODE_RHS, c->rbuf, 0.0, 0.0, nullptr, 0.0, nullptr, c->tpb, c->fused_face};
       st = launch_stage(c, l);  // warm-up; leaves b.Utr holding the traces of U
       if (st) break;

@@ -1720,6 +1720,10 @@ __host__ __device__ constexpr int group_for(int tpb) {
   return tpb / Shape<D, NP>::NPE > 0 ? tpb / Shape<D, NP>::NPE : 1;
 }
 
+}  // namespace nsk
+#include "nsk_line.cuh"
+namespace nsk {
+
 template <typename R, int D, int NP, int G, bool FUSED>
 int launch_stage_g(const NskParams& p, const NskBuffers& b, const NskLaunch& l, cudaStream_t s) {
   using S = Shape<D, NP>;
@@ -1792,13 +1796,19 @@ int launch_stage_lean(const NskParams& p, const NskBuffers& b, const NskLaunch& 
 }
 
 // schedule: tpb in {128, 256} (elements per block = tpb / nodes per element); face fluxes in
-// their own pass (fused_face 0), inside the volume kernel (1), or the lean two-launch stage (2)
+// their own pass (fused_face 0), inside the volume kernel (1), the lean two-launch stage (2), or
+// the separate face pass with line-per-thread lifting and volume kernels (4, FP32 3D N = 3)
 template <typename R, int D, int NP>
 int launch_stage(const NskParams& p, const NskBuffers& b, const NskLaunch& l, cudaStream_t s) {
   constexpr int G128 = group_for<D, NP>(128), G256 = group_for<D, NP>(256);
   if (l.fused_face == 2)
     return l.tpb == 128 ? launch_stage_lean<R, D, NP, G128>(p, b, l, s) : launch_stage_lean<R, D, NP, G256>(p, b, l, s);
-  const bool fused = l.fused_face != 0;
+  if constexpr (std::is_same<R, float>::value && D == 3 && NP == 4) {
+    // line schedule (fused_face 4): 16 threads per element, 8 or 16 elements per block; for other
+    // precisions and shapes it is the separate face pass
+    if (l.fused_face == 4) return l.tpb == 128 ? launch_stage_line<8>(p, b, l, s) : launch_stage_line<16>(p, b, l, s);
+  }
+  const bool fused = l.fused_face == 1;
   if (l.tpb == 128)
     return fused ? launch_stage_g<R, D, NP, G128, true>(p, b, l, s) : launch_stage_g<R, D, NP, G128, false>(p, b, l, s);
   return fused ? launch_stage_g<R, D, NP, G256, true>(p, b, l, s) : launch_stage_g<R, D, NP, G256, false>(p, b, l, s);

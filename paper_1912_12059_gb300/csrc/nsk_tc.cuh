@@ -794,6 +794,15 @@ __device__ __forceinline__ void ws_commit(uint32_t bar) {
 // Wait for the phase of parity `parity` of an mbarrier, bounded in time; gives up early when
 // another role has already aborted (flag set), and sets the flag and the error word on a timeout.
 __device__ __forceinline__ bool ws_wait(uint32_t bar, uint32_t parity, int* err, volatile int* abort_flag) {
+  {  // the common case: the phase has completed; no clock read
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
   const unsigned long long t0 = tc_global_ns();
   while (true) {
     uint32_t done;
@@ -829,19 +838,25 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* v) {
 
 // GELU(accumulator + bias) of 16 columns of the warp's 32 rows as BF16 into an activation slot:
 // the thread's row r, slot-local columns [kk, kk + 16) (kk a multiple of 16); bias: the 16 biases
-// in shared memory (every lane reads the same addresses: broadcast loads)
-__device__ __forceinline__ void ws_gelu16(uint32_t taddr, const float* bias, unsigned char* slot, int r, int kk) {
-  uint32_t v[16];
-  tmem_ld16(taddr, v);
+// in shared memory at shared-window address `bias` (every lane reads the same addresses: broadcast loads)
+// four floats from shared memory (a shared-window address: ld.shared, not a generic load)
+__device__ __forceinline__ float4 lds_f4(uint32_t a) {
+  float4 r;
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w) : "r"(a));
+  return r;
+}
+__device__ __forceinline__ void ws_gelu16(uint32_t taddr, uint32_t bias, unsigned char* slot, int r, int kk) {
   float b[16];
 #pragma unroll
   for (int g = 0; g < 4; ++g) {
-    const float4 t = reinterpret_cast<const float4*>(bias)[g];
+    const float4 t = lds_f4(bias + 16u * g);
     b[4 * g] = t.x;
     b[4 * g + 1] = t.y;
     b[4 * g + 2] = t.z;
     b[4 * g + 3] = t.w;
   }
+  uint32_t v[16];
+  tmem_ld16(taddr, v);
 #pragma unroll
   for (int g = 0; g < 2; ++g) {
     __align__(16) __nv_bfloat16 h[8];
@@ -1022,13 +1037,14 @@ __global__ void __launch_bounds__(kWsThreads, 1)
     const uint32_t lanes = (uint32_t)(q * 32) << 16;
     uint32_t f1 = 0u, f2 = 0u, f3 = 0u, u = 0u;
     bool ok = true;
-    auto gelu_layer = [&](uint32_t col0, int H, const float* bias) {
+    const uint32_t aB = smem_u32(sB);
+    auto gelu_layer = [&](uint32_t col0, int H, uint32_t bias) {
       for (int c = 0; ok && c < H; c += kWsHChunk) {
         const uint32_t hs = u & 1u;
         ok = ws_wait_warp(bar(WB_HFREE + hs), ((u >> 1) & 1u) ^ 1u, a.err, aborted);
         if (!ok) break;
         const int cc = c + sub * 16;
-        if (cc < H) ws_gelu16(tm + lanes + col0 + (uint32_t)cc, bias + cc, sH + hs * kWsHSlot, r, sub * 16);
+        if (cc < H) ws_gelu16(tm + lanes + col0 + (uint32_t)cc, bias + 4u * cc, sH + hs * kWsHSlot, r, sub * 16);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;");
         __syncwarp();
@@ -1041,7 +1057,7 @@ __global__ void __launch_bounds__(kWsThreads, 1)
       f1 ^= 1u;
       if (!ok) break;
       asm volatile("tcgen05.fence::after_thread_sync;");
-      gelu_layer(0u, a.H1, sB);
+      gelu_layer(0u, a.H1, aB);
       if (!ok) break;
       asm volatile("tcgen05.fence::before_thread_sync;");
       __syncwarp();
@@ -1050,7 +1066,7 @@ __global__ void __launch_bounds__(kWsThreads, 1)
       f2 ^= 1u;
       if (!ok) break;
       asm volatile("tcgen05.fence::after_thread_sync;");
-      gelu_layer(256u, a.H2, sB + a.H1);
+      gelu_layer(256u, a.H2, aB + 4u * a.H1);
       if (!ok) break;
       ok = ws_wait_warp(bar(WB_A3FULL), f3, a.err, aborted);
       f3 ^= 1u;
@@ -1061,13 +1077,15 @@ __global__ void __launch_bounds__(kWsThreads, 1)
         tmem_ld16(tm + lanes + 256u + (uint32_t)(sub * 16), v);
         const int m = t * kBM + r;
         if (m < a.M) {
-          const float* b3 = sB + a.H1 + a.H2 + sub * 16;
+          const uint32_t b3 = aB + 4u * (uint32_t)(a.H1 + a.H2 + sub * 16);
           float* y = a.Y + (size_t)m * a.ldy + sub * 16;
 #pragma unroll
-          for (int g = 0; g < 4; ++g)
+          for (int g = 0; g < 4; ++g) {
+            const float4 bb = lds_f4(b3 + 16u * g);
             *reinterpret_cast<float4*>(y + 4 * g) =
-                make_float4(__uint_as_float(v[4 * g]) + b3[4 * g], __uint_as_float(v[4 * g + 1]) + b3[4 * g + 1],
-                            __uint_as_float(v[4 * g + 2]) + b3[4 * g + 2], __uint_as_float(v[4 * g + 3]) + b3[4 * g + 3]);
+                make_float4(__uint_as_float(v[4 * g]) + bb.x, __uint_as_float(v[4 * g + 1]) + bb.y,
+                            __uint_as_float(v[4 * g + 2]) + bb.z, __uint_as_float(v[4 * g + 3]) + bb.w);
+          }
         }
       }
       asm volatile("tcgen05.fence::before_thread_sync;");

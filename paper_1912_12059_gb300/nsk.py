@@ -396,11 +396,12 @@ class Solver:
     def set_schedule(self, tpb=256, fused_face=0):
         """fused_face: 0 separate face pass, 1 (or True) face fluxes in the volume kernel, 2 the
         lean two-launch stage (lifting recomputed on chip by the volume kernel), 3 the
-        single-block schedule for small meshes (a whole call in one launch)."""
+        single-block schedule for small meshes (a whole call in one launch), 4 the separate face
+        pass with line-per-thread lifting and volume kernels (FP32, 3D, N = 3)."""
         _check(load_library().nsk_set_schedule(self.ctx, tpb, int(fused_face)), "nsk_set_schedule")
 
     def get_schedule(self):
-        """(tpb, fused_face) with fused_face 0, 1 or 2 (see set_schedule)."""
+        """(tpb, fused_face) with fused_face 0 to 4 (see set_schedule)."""
         t, f = C.c_int(), C.c_int()
         _check(load_library().nsk_get_schedule(self.ctx, C.byref(t), C.byref(f)), "nsk_get_schedule")
         return t.value, f.value

@@ -10,6 +10,7 @@ stepped alone; the bounded grid-barrier wait must end with NSK_ERR_TIMEOUT
 import numpy as np
 import pytest
 
+import oracle as O
 from paper_1912_12059_gb300 import inputs, nsk
 
 pytestmark = pytest.mark.gpu
@@ -27,14 +28,15 @@ def _state(s, seed):
                                       (2, (7, 5), 3), (2, (6, 3), 5), (1, (9,), 3), (1, (5,), 1)])
 def test_schedules_are_bit_identical(gpu, precision, dim, ne, N):
     """Separate face pass, face fluxes in the volume kernel, the lean two-launch stage (the
-    lifting recomputed on chip) and the single-block schedule (where the mesh fits one block; the
-    separate face pass elsewhere), at both block sizes: the same bits."""
+    lifting recomputed on chip), the single-block schedule (where the mesh fits one block; the
+    separate face pass elsewhere) and the line-per-thread kernels (FP32 3D N = 3; the separate face
+    pass elsewhere), at both block sizes: the same bits."""
     s = nsk.Solver(dim, ne, N, [0] * dim, [1] * dim, 0, precision)
     s.set_params(**PRM)
     U = _state(s, 1)
     results = []
     for tpb in (128, 256):
-        for fused in (0, 1, 2, 3):
+        for fused in (0, 1, 2, 3, 4):
             s.set_schedule(tpb, fused)
             s.set_state(U)
             R = s.rhs()
@@ -47,7 +49,7 @@ def test_schedules_are_bit_identical(gpu, precision, dim, ne, N):
 
 
 @pytest.mark.parametrize("precision", [nsk.NSK_FP64, nsk.NSK_FP32_MIXED])
-@pytest.mark.parametrize("fused", [0, 1, 2])
+@pytest.mark.parametrize("fused", [0, 1, 2, 4])
 def test_volume_kernel_traces_equal_a_prolongation_pass(gpu, precision, fused):
     """Inside one nsk_step call every stage after the first takes the face traces that the
     previous stage's volume kernel wrote; a call starts with a prolongation pass. Four steps
@@ -222,3 +224,25 @@ def test_batch_barrier_wait_is_bounded(gpu):
     b.close()
     for s, _ in inst:
         s.close()
+
+
+@pytest.mark.parametrize("tpb", [128, 256])
+def test_line_schedule_on_a_droplet_collision(gpu, tpb):
+    """The line-per-thread FP32 kernels on a 16^3 head-on droplet collision (256 or 512 blocks,
+    the interfaces crossing element lines in every direction): the residual, the state after 20
+    steps and the diagnostics equal the separate face pass bit for bit."""
+    rv, rl, _ = O.maxwell(0.85)
+    runs = []
+    for fused in (0, 4):
+        s = nsk.Solver(3, (16, 16, 16), 3, [0, 0, 0], [1, 1, 1], 0, nsk.NSK_FP32_MIXED)
+        s.set_params(**PRM)
+        s.set_schedule(tpb, fused)
+        v = inputs.collision_velocity(40.0, 0.2, 1e-4, rv, rl)
+        s.set_state(inputs.head_on_collision(s.node_coords(), v, 0.2, rho_vap=rv, rho_liq=rl, kappa=1e-4))
+        R = s.rhs()
+        s.step(-0.5, 20)
+        runs.append((R, s.get_state(), s.diagnostics()))
+        s.close()
+    assert np.array_equal(runs[0][0], runs[1][0])
+    assert np.array_equal(runs[0][1], runs[1][1])
+    assert runs[0][2] == runs[1][2]
