@@ -344,9 +344,12 @@ int nsk_batch_step(nsk_batch* batch, int nsteps, double cfl, double* step_ms, do
  * the cooperative persistent kernel, 0 for one launch per phase covering all
  * instances, 2 for each instance's own stage launches one after another in the
  * captured graph: the schedule of choice when every instance fills the GPU by
- * itself) and the autotuner over all ten schedules (times one residual of the
- * whole batch under each; the instances' states are not modified). Returns
- * NSK_ERR_ARG for tpb not 128 or 256 or persistent outside 0..2. */
+ * itself; there fused_face may also be 2, the lean stage, or 4, the line
+ * kernels for the instances they apply to) and the autotuner over all sixteen
+ * schedules (times one residual of the whole batch under each; the instances'
+ * states are not modified). Returns NSK_ERR_ARG for tpb not 128 or 256,
+ * persistent outside 0..2, fused_face outside 0..4, 3, or 2 or 4 with
+ * persistent other than 2. */
 int nsk_batch_set_schedule(nsk_batch* batch, int tpb, int fused_face, int persistent);
 int nsk_batch_get_schedule(nsk_batch* batch, int* tpb, int* fused_face, int* persistent);
 int nsk_batch_autotune(nsk_batch* batch, int* tpb_out, int* fused_out, int* persistent_out, double* ms_out);

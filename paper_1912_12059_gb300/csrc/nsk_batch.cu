@@ -507,14 +507,15 @@ int launch_instances_lean(nsk_batch* bt, int mode, double A, double B, int tpb, 
 // launch per phase; 2: every instance's own launches)
 // trace flags of every stage of a step under the separate face schedule: traces come from the
 // previous stage's volume phase (the step starts from traces prolonged before the first step)
-int step_traces(int fused) { return fused ? 0 : 3; }
+// (the line schedule, fused_face 4, is a separate face schedule)
+int step_traces(int fused) { return (fused == 0 || fused == 4) ? 3 : 0; }
 
 // stamps: the last stage of a step whose per-instance latencies are measured (each instance's
 // completion stamped after its last kernel; one launch for all instances stamps them together)
 int launch_batch(nsk_batch* bt, int mode, double A, double B, int tpb, int fused, int persistent, int traces,
                  bool stamps = false, int stage = -1) {
   if (persistent == 2 && fused == 2) return launch_instances_lean(bt, mode, A, B, tpb, stage, stamps);
-  if (fused) traces = 0;  // the fused volume phase reads the traces: they are prolonged every stage
+  if (fused == 1) traces = 0;  // the fused volume phase reads the traces: they are prolonged every stage
   if (persistent == 2) return launch_instances(bt, mode, A, B, tpb, fused, traces, stamps);
   const int r = persistent ? launch_persistent(bt, mode, A, B, tpb, fused, traces)
                            : launch_phases(bt, mode, A, B, tpb, fused, traces);
@@ -675,8 +676,8 @@ int nsk_batch_create(nsk_batch** out, int n, nsk_ctx* const* instances) {
 }
 
 int nsk_batch_set_schedule(nsk_batch* bt, int tpb, int fused_face, int persistent) {
-  if (!bt || (tpb != 128 && tpb != 256) || persistent < 0 || persistent > 2 || fused_face < 0 || fused_face > 2 ||
-      (fused_face == 2 && persistent != 2))
+  if (!bt || (tpb != 128 && tpb != 256) || persistent < 0 || persistent > 2 || fused_face < 0 || fused_face > 4 ||
+      fused_face == 3 || (fused_face >= 2 && persistent != 2))
     return NSK_ERR_ARG;
   bt->tpb = tpb;
   bt->fused = fused_face;
@@ -704,7 +705,8 @@ int nsk_batch_autotune(nsk_batch* bt, int* tpb_out, int* fused_out, int* persist
   const int tpbs[2] = {128, 256};
   for (int per = 0; per < 3 && st == NSK_OK; ++per)
     for (int ti = 0; ti < 2 && st == NSK_OK; ++ti)
-      for (int f = 0; f < (per == 2 ? 3 : 2) && st == NSK_OK; ++f) {
+      for (int fi = 0; fi < (per == 2 ? 4 : 2) && st == NSK_OK; ++fi) {
+        const int f = fi == 3 ? 4 : fi;  // instance schedule: separate, fused, lean, line
         // warm-up with a prolongation pass (residual: state untouched), then time the stage as a
         // step runs it (rewriting the traces of the unchanged state leaves them as they are; the
         // lean stage as a middle stage of a step: traces read from the trace buffer, the next
@@ -788,7 +790,7 @@ int nsk_batch_step(nsk_batch* bt, int nsteps, double cfl, double* step_ms, doubl
     bt->graph_cfl = cfl;
     bt->graph_stamps = (int)stamps;
   }
-  if (nsteps > 0 && !bt->fused) {  // the traces of the current states, for the first stage
+  if (nsteps > 0 && step_traces(bt->fused)) {  // the traces of the current states, for the first stage
     const int r = launch_prolong(bt, bt->tpb);
     if (r) return r;
   }
