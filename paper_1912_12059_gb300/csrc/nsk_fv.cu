@@ -430,6 +430,242 @@ __device__ __forceinline__ void fv_update_body(const NskParams& p, const FvParam
   if (eflag) atomicOr(err, eflag);
 }
 
+// ---- lane groups: W lanes per element (lane j = node or sub-cell j), for the cooperative kernel ----
+// The same values as the bodies above, with the same operations in the same order; what one
+// thread did for every node or sub-cell of an element in turn, lane j does for its own, and the
+// values of other nodes arrive by width-W shuffles. Every lane of a warp runs the same number of
+// iterations (the caller's loops are warp-uniform), so the shuffles always see the whole warp;
+// lanes of inactive groups (past the mesh, or elements of the other role) compute on zeros and
+// store nothing.
+template <int NP>
+__host__ __device__ constexpr int fv_w() {
+  return NP <= 4 ? 4 : 8;
+}
+__device__ __forceinline__ double grp_get(double x, int lane, int W) { return __shfl_sync(0xffffffffu, x, lane, W); }
+
+template <int NP>
+__device__ __forceinline__ void fv_faces_group(const NskParams& p, const FvParams& f, const double* __restrict__ U,
+                                               const int* __restrict__ flags, double* __restrict__ Uf,
+                                               double* __restrict__ Gf, double* __restrict__ SL,
+                                               int* __restrict__ err, const long long e, const int j,
+                                               const int role) {
+  constexpr int W = fv_w<NP>();
+  const bool active = e < p.E && flags[e] == role;
+  const bool mine = active && j < NP;
+  int eflag = 0;
+  if (role == 0) {  // DG elements: the six face traces, one per lane in turn
+    if (active)
+      for (int k = j; k < 6; k += W) Uf[(e * 2 + k / 3) * 3 + k % 3] = dg_trace<NP>(p, U, e, k % 3, k / 3);
+    return;
+  }
+  double P[3] = {0.0, 0.0, 0.0};
+  if (mine) {
+    const double c[3] = {U[e * NP + j], U[(size_t)p.nne + e * NP + j], U[2 * (size_t)p.nne + e * NP + j]};
+    if (bad(c[0])) eflag |= NSK_EBIT_RHO;
+    prim(c, P);
+  }
+  // the value beyond the element's face on the lane's side (lane 0: side 0, lane NP - 1: side 1)
+  double Pn[3] = {0.0, 0.0, 0.0}, dn = 1.0;
+  const int sd = j == 0 ? 0 : 1;
+  if (active && (j == 0 || j == NP - 1)) {
+    const long long en = nbr(p, f, e, sd);
+    if (en < 0) {
+      prim(f.Ub[sd], Pn);
+      dn = 0.5 * f.dx;
+    } else if (flags[en]) {
+      const int jn = sd ? 0 : NP - 1;
+      const double c[3] = {U[en * NP + jn], U[(size_t)p.nne + en * NP + jn], U[2 * (size_t)p.nne + en * NP + jn]};
+      prim(c, Pn);
+      dn = f.dx;
+    } else {
+      double c[3];
+#pragma unroll
+      for (int v = 0; v < 3; ++v) c[v] = dg_trace<NP>(p, U, en, v, sd ? 0 : 1);
+      prim(c, Pn);
+      dn = 0.5 * f.dx;
+    }
+  }
+  const int base = (threadIdx.x & 31) & ~(W - 1);
+  const double idx = 1.0 / f.dx;
+  double slope[3];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    const double Pm = grp_get(P[q], base + (j > 0 ? j - 1 : 0), W);  // P[j - 1]
+    const double Pp = grp_get(P[q], base + (j < NP - 1 ? j + 1 : j), W);  // P[j + 1]
+    const double lq = j > 0 ? (P[q] - Pm) * idx : (P[q] - Pn[q]) / dn;
+    const double rq = j < NP - 1 ? (Pp - P[q]) * idx : (Pn[q] - P[q]) / dn;
+    slope[q] = minmod(lq, rq);
+    if (mine) SL[(e * NP + j) * 3 + q] = slope[q];
+  }
+  if (active && (j == 0 || j == NP - 1)) {  // NP >= 2: lanes 0 and NP - 1 are different
+    double Pf[3], Uo[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) Pf[q] = j == 0 ? P[q] - 0.5 * f.dx * slope[q] : P[q] + 0.5 * f.dx * slope[q];
+    cons(Pf, Uo);
+#pragma unroll
+    for (int v = 0; v < 3; ++v) Uf[(e * 2 + sd) * 3 + v] = Uo[v];
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+      Gf[(e * 2 + sd) * 2 + q] = j == 0 ? (P[1 + q] - Pn[1 + q]) / dn : (Pn[1 + q] - P[1 + q]) / dn;
+  }
+  if (eflag) atomicOr(err, eflag);
+}
+
+template <int NP>
+__device__ __forceinline__ void fv_lift_group(const NskParams& p, const FvParams& f, const double* __restrict__ U,
+                                              const int* __restrict__ flags, const double* __restrict__ Uf,
+                                              double* __restrict__ Q, double* __restrict__ Gf, const long long e,
+                                              const int j) {
+  constexpr int W = fv_w<NP>();
+  const bool active = e < p.E && !flags[e];
+  const bool mine = active && j < NP;
+  const auto& t = p.td;
+  const int base = (threadIdx.x & 31) & ~(W - 1);
+  double ws[2][2] = {{0.0, 0.0}, {0.0, 0.0}}, w[2] = {0.0, 0.0};
+  if (active) {
+#pragma unroll
+    for (int sd = 0; sd < 2; ++sd) {
+      const double* Ui = Uf + (e * 2 + sd) * 3;
+      const double* Uo = outer(p, f, Uf, e, sd);
+      ws[sd][0] = 0.5 * (Ui[1] / Ui[0] + Uo[1] / Uo[0]);
+      ws[sd][1] = 0.5 * (Ui[2] + Uo[2]);
+    }
+  }
+  if (mine) {
+    const double rho = U[e * NP + j];
+    w[0] = U[(size_t)p.nne + e * NP + j] / rho;
+    w[1] = U[2 * (size_t)p.nne + e * NP + j];
+  }
+  double q[2];
+  const int i = j < NP ? j : 0;
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    double s = 0.0;
+#pragma unroll
+    for (int jj = 0; jj < NP; ++jj) s = fma(t.dk[0][i * NSK_MAXNP + jj], grp_get(w[c], base + jj, W), s);
+    q[c] = fma(ws[1][c], t.lpk[0][i], fma(-ws[0][c], t.lmk[0][i], -s));
+    if (mine) Q[(size_t)c * p.nne + e * NP + j] = q[c];
+  }
+  // traces of the lifted gradient: lane k < 4 sums (side k / 2, component k % 2) over the nodes
+  const int ksd = (j >> 1) & 1, kc = j & 1;
+  const double* L = ksd ? t.lp : t.lm;
+  double s = 0.0;
+#pragma unroll
+  for (int jj = 0; jj < NP; ++jj) {
+    const double q0 = grp_get(q[0], base + jj, W), q1 = grp_get(q[1], base + jj, W);
+    s = fma(L[jj], kc ? q1 : q0, s);
+  }
+  if (active && j < 4) Gf[(e * 2 + ksd) * 2 + kc] = s;
+}
+
+template <int NP>
+__device__ __forceinline__ void fv_update_group(const NskParams& p, const FvParams& f, double* __restrict__ U,
+                                                double* __restrict__ K, const int* __restrict__ flags,
+                                                const double* __restrict__ Gf, const double* __restrict__ SL,
+                                                const double* __restrict__ Q, const double* __restrict__ Fh,
+                                                const double A, const double B, const double dt,
+                                                int* __restrict__ err, const long long e, const int j,
+                                                const int role) {
+  constexpr int W = fv_w<NP>();
+  const bool active = e < p.E && flags[e] == role;
+  const bool mine = active && j < NP;
+  const auto& t = p.td;
+  const int base = (threadIdx.x & 31) & ~(W - 1);
+  const int i = j < NP ? j : 0;
+  int eflag = 0;
+  double u[3] = {1.0, 0.0, 0.0}, r[3];
+  if (mine)
+#pragma unroll
+    for (int v = 0; v < 3; ++v) u[v] = U[(size_t)v * p.nne + e * NP + j];
+  double Fl[3] = {0.0, 0.0, 0.0}, Fr[3] = {0.0, 0.0, 0.0};
+  if (active)
+#pragma unroll
+    for (int v = 0; v < 3; ++v) {
+      Fl[v] = Fh[e * 3 + v];
+      Fr[v] = Fh[(e + 1) * 3 + v];
+    }
+  if (role == 0) {  // DG weak form: lane j the nodal fluxes of node j and the residual of node j
+    double F[3], qc = 0.0;
+    {
+      const double rho = u[0], vel = u[1] / rho;
+      if (mine && bad(rho)) eflag |= NSK_EBIT_RHO;
+      const double qv = mine ? Q[e * NP + j] : 0.0;
+      qc = mine ? Q[(size_t)p.nne + e * NP + j] : 0.0;
+      F[0] = u[1];
+      F[1] = fma(u[1], vel, eos_pa64(p, rho)) - (4.0 / 3.0) * t.mu * qv;
+      F[2] = -t.kb * qc;
+    }
+#pragma unroll
+    for (int v = 0; v < 3; ++v) {
+      double s = 0.0;
+#pragma unroll
+      for (int jj = 0; jj < NP; ++jj) s = fma(t.dk[0][i * NSK_MAXNP + jj], grp_get(F[v], base + jj, W), s);
+      r[v] = fma(Fl[v], t.lmk[0][i], fma(-Fr[v], t.lpk[0][i], s));
+    }
+    r[1] = fma(t.alpha * u[0], qc, r[1]);
+    r[2] = fma(t.ab, u[0] - u[2], r[2]);
+  } else {  // FV sub-cell balance: lane j the flux on sub-cell face j + 1 (j < NP - 1)
+    double P[3], s[3] = {0.0, 0.0, 0.0};
+    prim(u, P);
+    if (mine)
+#pragma unroll
+      for (int q = 0; q < 3; ++q) s[q] = SL[(e * NP + j) * 3 + q];
+    const double idx = 1.0 / f.dx;
+    double Pn[3], sn[3];  // sub-cell j + 1
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      Pn[q] = grp_get(P[q], base + (j + 1 < W ? j + 1 : j), W);
+      sn[q] = grp_get(s[q], base + (j + 1 < W ? j + 1 : j), W);
+    }
+    double Fs[3] = {0.0, 0.0, 0.0}, g1 = 0.0;  // the flux and c_x on sub-cell face j + 1
+    if (mine && j < NP - 1) {
+      double PL[3], PR[3], UL[3], UR[3], g[2], fvv[3], F[3];
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        PL[q] = P[q] + 0.5 * f.dx * s[q];
+        PR[q] = Pn[q] - 0.5 * f.dx * sn[q];
+      }
+      cons(PL, UL);
+      cons(PR, UR);
+      g[0] = (Pn[1] - P[1]) * idx;
+      g[1] = (Pn[2] - P[2]) * idx;
+      g1 = g[1];
+      numflux(p, UL, UR, F, eflag);
+      visc(p, g, fvv);
+#pragma unroll
+      for (int v = 0; v < 3; ++v) Fs[v] = F[v] - fvv[v];
+    }
+    // the flux and c_x on the sub-cell's left face: the element face (lane 0) or lane j - 1's
+    double Fm[3], gm;
+#pragma unroll
+    for (int v = 0; v < 3; ++v) Fm[v] = grp_get(Fs[v], base + (j > 0 ? j - 1 : 0), W);
+    gm = grp_get(g1, base + (j > 0 ? j - 1 : 0), W);
+    if (j == 0) {
+#pragma unroll
+      for (int v = 0; v < 3; ++v) Fm[v] = Fl[v];
+      gm = active ? Gf[(e * 2 + 0) * 2 + 1] : 0.0;
+    }
+    if (j == NP - 1) {
+#pragma unroll
+      for (int v = 0; v < 3; ++v) Fs[v] = Fr[v];
+      g1 = active ? Gf[(e * 2 + 1) * 2 + 1] : 0.0;
+    }
+#pragma unroll
+    for (int v = 0; v < 3; ++v) r[v] = -(Fs[v] - Fm[v]) * idx;
+    r[1] = fma(t.alpha * u[0], 0.5 * (gm + g1), r[1]);
+    r[2] = fma(t.ab, u[0] - u[2], r[2]);
+  }
+  if (mine)
+#pragma unroll
+    for (int v = 0; v < 3; ++v) {
+      const size_t g = (size_t)v * p.nne + e * NP + j;
+      const double kv = fma(A, K[g], dt * r[v]);
+      K[g] = kv;
+      U[g] = fma(B, kv, u[v]);
+    }
+  if (eflag) atomicOr(err, eflag);
+}
+
 // ---- one launch per kernel (any mesh size) ----------------------------------------------------
 template <int NP>
 __global__ void __launch_bounds__(128) k_fv_switch(const NskParams p, const FvParams f, double* __restrict__ U,
@@ -475,11 +711,13 @@ __global__ void __launch_bounds__(128)
 
 // ---- small meshes: all steps of one call in one cooperative launch ---------------------------
 // An FP64 warp instruction occupies the SM's FP64 pipe for the same time whether 4 or 32 lanes
-// are active, so a small mesh runs fastest with one warp of up to 32 elements per SM. For
-// E <= kCoopMaxE the switch pass and the four phases of each stage run in one cooperative launch
-// of 2 ceil((E + 1) / 32) one-warp blocks (the face-state and update phases give DG and FV elements
-// to separate halves of the grid), separated by the bounded grid barrier; nsteps steps then cost
-// one launch instead of 21 per step. Fixed dt only.
+// are active, so a small mesh runs fastest spread thinly, one warp per SM, and its time is the
+// length of one element's serial chain. For E <= kCoopMaxE the switch pass and the four phases of
+// each stage run in one cooperative launch of one-warp blocks (the face-state and update phases
+// give DG and FV elements to separate halves of the grid), separated by the bounded grid barrier;
+// nsteps steps then cost one launch instead of 21 per step. Fixed dt only. The element phases run
+// in lane groups (one lane per node or sub-cell), which splits each element's chain: a sub-cell
+// element's three internal HLLC solves run side by side instead of one after another.
 constexpr int kCoopMaxE = 4096;
 struct LsrkCoef {
   double A[5], B[5];
@@ -499,23 +737,27 @@ __global__ void __launch_bounds__(32) k_fv_coop(const NskParams p, const FvParam
   // faces and update: the first half of the blocks takes the DG elements, the second the FV ones
   const unsigned half = gridDim.x / 2;
   const int role = blockIdx.x >= half;
-  const long long rfirst = (long long)(blockIdx.x - role * half) * blockDim.x + threadIdx.x,
-                  rstride = (long long)half * blockDim.x;
+  // the element phases in lane groups (W lanes per element, 32 / W elements per one-warp block
+  // and iteration; the loop bounds are uniform over the warp)
+  constexpr int W = fv_w<NP>(), EPW = 32 / W;
+  const int j = threadIdx.x % W, grp = threadIdx.x / W;
+  const long long gfirst = (long long)blockIdx.x * EPW, gstride = (long long)gridDim.x * EPW;
+  const long long rgfirst = (long long)(blockIdx.x - role * half) * EPW, rgstride = (long long)half * EPW;
   for (int step = 0; step < nsteps; ++step) {
     if (switching) {
       for (long long e = first; e < p.E; e += stride) fv_switch_body<NP>(p, f, U, flags, ind, e);
       if (!grid_barrier(bar, err, timeout_ns)) return;
     }
     for (int st = 0; st < 5; ++st) {
-      for (long long e = rfirst; e < p.E; e += rstride) fv_faces_body<NP>(p, f, U, flags, Uf, Gf, SL, err, e, role);
+      for (long long eb = rgfirst; eb < p.E; eb += rgstride)
+        fv_faces_group<NP>(p, f, U, flags, Uf, Gf, SL, err, eb + grp, j, role);
       if (!grid_barrier(bar, err, timeout_ns)) return;
-      for (long long e = first; e < p.E; e += stride) fv_lift_body<NP>(p, f, U, flags, Uf, Q, Gf, e);
+      for (long long eb = gfirst; eb < p.E; eb += gstride) fv_lift_group<NP>(p, f, U, flags, Uf, Q, Gf, eb + grp, j);
       if (!grid_barrier(bar, err, timeout_ns)) return;
       for (long long fc = first; fc < nfaces; fc += stride) fv_flux_body(p, f, Uf, Gf, Fh, err, fc);
       if (!grid_barrier(bar, err, timeout_ns)) return;
-      for (long long e = rfirst; e < p.E; e += rstride)
-        fv_update_body<NP>(p, f, U, K, nullptr, flags, Gf, SL, Q, Fh, NSK_MODE_LSRK, rk.A[st], rk.B[st], dt, err, e,
-                           role);
+      for (long long eb = rgfirst; eb < p.E; eb += rgstride)
+        fv_update_group<NP>(p, f, U, K, flags, Gf, SL, Q, Fh, rk.A[st], rk.B[st], dt, err, eb + grp, j, role);
       if (!grid_barrier(bar, err, timeout_ns)) return;
     }
   }
@@ -545,7 +787,10 @@ template <int NP>
 int launch_coop_t(const NskParams& p, const FvParams& f, const FvBuffers& fb, const NskBuffers& b, int nsteps,
                   int switching, double dt, const double* A, const double* B, cudaStream_t s) {
   auto kern = k_fv_coop<NP>;
-  const int grid = 2 * (int)((p.E + 1 + 31) / 32);  // every element and face, twice (DG and FV roles)
+  // one element group per warp in each role half (and every face covered by the one-thread loops)
+  constexpr int EPW = 32 / fv_w<NP>();
+  const long long ng = (p.E + EPW - 1) / EPW, nf = (p.E + 1 + 31) / 32;
+  const int grid = 2 * (int)(ng > nf ? ng : nf);
   int per_sm = 0, dev = 0, sms = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32, 0) != cudaSuccess ||
       cudaGetDevice(&dev) != cudaSuccess ||

@@ -78,3 +78,25 @@ def test_fp32_density_error_vs_fp64(gpu, case):
     assert abs(m32 - m64) <= 1e-6 * m64
     s64.close()
     s32.close()
+
+
+def test_line_schedule_at_full_size(gpu):
+    """The benchmark's FP32 configuration, the 64^3 head-on collision (N = 3, We = 40), under the
+    line-per-thread kernels the autotuner picks there (schedule 128,4) against the separate face
+    pass with node-per-thread kernels (256,0): residual and three steps equal bit for bit, and the
+    density after the steps within the FP32 bound of the FP64 run."""
+    wl = inputs.head_on_collision_3d(we=40.0, nelem=64)
+    out = {}
+    for prec, sched in ((nsk.NSK_FP32_MIXED, (256, 0)), (nsk.NSK_FP32_MIXED, (128, 4)), (nsk.NSK_FP64, (256, 0))):
+        s = nsk.Solver(3, wl.nelem, 3, [0, 0, 0], [1, 1, 1], 0, prec)
+        s.set_params(T=wl.T, kappa=wl.kappa, alpha=wl.alpha, beta=wl.beta, mu=wl.mu)
+        s.set_schedule(*sched)
+        s.set_state(wl.initial_state(s.node_coords()))
+        R = s.rhs() if prec == nsk.NSK_FP32_MIXED else None
+        s.step(2.3e-6, 3)
+        out[(prec, sched)] = (R, s.get_state())
+        s.close()
+    a, b = out[(nsk.NSK_FP32_MIXED, (256, 0))], out[(nsk.NSK_FP32_MIXED, (128, 4))]
+    assert np.array_equal(a[0], b[0])
+    assert np.array_equal(a[1], b[1])
+    assert _density_l2_rel(b[1], out[(nsk.NSK_FP64, (256, 0))][1]) <= 1e-5

@@ -132,11 +132,12 @@ def test_switch_parity(gpu, N):
     s.close()
 
 
-@pytest.mark.parametrize("N", [2, 3])
+@pytest.mark.parametrize("N", [2, 3, 4, 5])
 def test_riemann_problem_100_steps(gpu, N):
     """The sharp-interface Riemann problem (Sec. 4) on 40 elements: 100 LSRK4 steps with the
-    switches before every step (one cooperative launch for the call), same dt on both sides;
-    flags equal, state within 1e-10."""
+    switches before every step (one cooperative launch for the call, its element phases in lane
+    groups of 4 lanes up to N = 3 and 8 above), same dt on both sides; flags equal, state within
+    1e-10."""
     E = 40
     s, o = make_pair(E, N, dirichlet=True)
     U = inputs.riemann_1d(o.coords(), 2.0, 0.1, 0.5)
