@@ -297,27 +297,41 @@ __device__ __forceinline__ void fv_lift_body(const NskParams& p, const FvParams&
 
 // face fc between elements fc - 1 and fc (face 0 and, with Dirichlet boundaries, face E are
 // the boundary faces); Fh[fc][3] = convective flux - mean viscous flux
-__device__ __forceinline__ void fv_flux_body(const NskParams& p, const FvParams& f, const double* __restrict__ Uf,
-                                             const double* __restrict__ Gf, double* __restrict__ Fh,
-                                             int* __restrict__ err, const long long fc) {
-  const long long nfaces = f.dirichlet ? p.E + 1 : p.E;
-  if (fc >= nfaces) return;
+// the flux Fo on face fc (0 <= fc < number of faces)
+__device__ __forceinline__ void fv_face_flux(const NskParams& p, const FvParams& f, const double* __restrict__ Uf,
+                                             const double* __restrict__ Gf, const long long fc, double* Fo,
+                                             int& eflag) {
   const long long eR = fc < p.E ? fc : -1;
   const long long eL = fc > 0 ? fc - 1 : (f.dirichlet ? -1 : p.E - 1);
   const double* L = eL >= 0 ? Uf + (eL * 2 + 1) * 3 : f.Ub[0];
   const double* R = eR >= 0 ? Uf + (eR * 2 + 0) * 3 : f.Ub[1];
   const double* gL = eL >= 0 ? Gf + (eL * 2 + 1) * 2 : Gf + (eR * 2 + 0) * 2;
   const double* gR = eR >= 0 ? Gf + (eR * 2 + 0) * 2 : Gf + (eL * 2 + 1) * 2;
-  int eflag = 0;
   double F[3], vl[3], vr[3];
   numflux(p, L, R, F, eflag);
   visc(p, gL, vl);
   visc(p, gR, vr);
 #pragma unroll
-  for (int v = 0; v < 3; ++v) Fh[fc * 3 + v] = F[v] - 0.5 * (vl[v] + vr[v]);
+  for (int v = 0; v < 3; ++v) Fo[v] = F[v] - 0.5 * (vl[v] + vr[v]);
+}
+// the face of element e on side sd (periodic: the right face of element E - 1 is face 0)
+__device__ __forceinline__ long long fv_face_of(const NskParams& p, const FvParams& f, long long e, int sd) {
+  return sd == 0 ? e : ((e + 1 < p.E || f.dirichlet) ? e + 1 : 0);
+}
+
+__device__ __forceinline__ void fv_flux_body(const NskParams& p, const FvParams& f, const double* __restrict__ Uf,
+                                             const double* __restrict__ Gf, double* __restrict__ Fh,
+                                             int* __restrict__ err, const long long fc) {
+  const long long nfaces = f.dirichlet ? p.E + 1 : p.E;
+  if (fc >= nfaces) return;
+  int eflag = 0;
+  double F[3];
+  fv_face_flux(p, f, Uf, Gf, fc, F, eflag);
+#pragma unroll
+  for (int v = 0; v < 3; ++v) Fh[fc * 3 + v] = F[v];
   if (!f.dirichlet && fc == 0) {  // periodic: face 0 is also the right face of element E - 1
 #pragma unroll
-    for (int v = 0; v < 3; ++v) Fh[p.E * 3 + v] = F[v] - 0.5 * (vl[v] + vr[v]);
+    for (int v = 0; v < 3; ++v) Fh[p.E * 3 + v] = F[v];
   }
   if (eflag) atomicOr(err, eflag);
 }
@@ -439,7 +453,7 @@ __device__ __forceinline__ void fv_update_body(const NskParams& p, const FvParam
 // store nothing.
 template <int NP>
 __host__ __device__ constexpr int fv_w() {
-  return NP <= 4 ? 4 : 8;
+  return 8;  // > NP: a lane for each of an element's NP + 1 sub-cell faces
 }
 __device__ __forceinline__ double grp_get(double x, int lane, int W) { return __shfl_sync(0xffffffffu, x, lane, W); }
 
@@ -558,15 +572,21 @@ __device__ __forceinline__ void fv_lift_group(const NskParams& p, const FvParams
   if (active && j < 4) Gf[(e * 2 + ksd) * 2 + kc] = s;
 }
 
+// The update phase with the element-face fluxes evaluated in the element's own lane group (each
+// face by both its elements, with the same function and inputs as the face pass: the same bits),
+// so the cooperative kernel needs no face phase: lane j in [0, NP] takes face j of the element's
+// NP + 1 sub-cell faces (0 and NP are the element's faces; DG elements need only those), lane
+// j < NP the residual and update of node or sub-cell j.
 template <int NP>
 __device__ __forceinline__ void fv_update_group(const NskParams& p, const FvParams& f, double* __restrict__ U,
                                                 double* __restrict__ K, const int* __restrict__ flags,
-                                                const double* __restrict__ Gf, const double* __restrict__ SL,
-                                                const double* __restrict__ Q, const double* __restrict__ Fh,
+                                                const double* __restrict__ Uf, const double* __restrict__ Gf,
+                                                const double* __restrict__ SL, const double* __restrict__ Q,
                                                 const double A, const double B, const double dt,
                                                 int* __restrict__ err, const long long e, const int j,
                                                 const int role) {
   constexpr int W = fv_w<NP>();
+  static_assert(NP < W, "a lane for each of the NP + 1 sub-cell faces");
   const bool active = e < p.E && flags[e] == role;
   const bool mine = active && j < NP;
   const auto& t = p.td;
@@ -577,15 +597,17 @@ __device__ __forceinline__ void fv_update_group(const NskParams& p, const FvPara
   if (mine)
 #pragma unroll
     for (int v = 0; v < 3; ++v) u[v] = U[(size_t)v * p.nne + e * NP + j];
-  double Fl[3] = {0.0, 0.0, 0.0}, Fr[3] = {0.0, 0.0, 0.0};
-  if (active)
+  // the element's faces: lane 0 the left one, lane NP the right one
+  double Fe[3] = {0.0, 0.0, 0.0};
+  if (active && (j == 0 || j == NP)) fv_face_flux(p, f, Uf, Gf, fv_face_of(p, f, e, j == 0 ? 0 : 1), Fe, eflag);
+  if (role == 0) {  // DG weak form: lane j the nodal fluxes of node j and the residual of node j
+    double Fl[3], Fr[3];
 #pragma unroll
     for (int v = 0; v < 3; ++v) {
-      Fl[v] = Fh[e * 3 + v];
-      Fr[v] = Fh[(e + 1) * 3 + v];
+      Fl[v] = grp_get(Fe[v], base, W);
+      Fr[v] = grp_get(Fe[v], base + NP, W);
     }
-  if (role == 0) {  // DG weak form: lane j the nodal fluxes of node j and the residual of node j
-    double F[3], qc = 0.0;
+    double F[3], qc;
     {
       const double rho = u[0], vel = u[1] / rho;
       if (mine && bad(rho)) eflag |= NSK_EBIT_RHO;
@@ -604,55 +626,47 @@ __device__ __forceinline__ void fv_update_group(const NskParams& p, const FvPara
     }
     r[1] = fma(t.alpha * u[0], qc, r[1]);
     r[2] = fma(t.ab, u[0] - u[2], r[2]);
-  } else {  // FV sub-cell balance: lane j the flux on sub-cell face j + 1 (j < NP - 1)
+  } else {  // FV sub-cell balance: lane j (0 < j < NP) the flux on the face between sub-cells j - 1, j
     double P[3], s[3] = {0.0, 0.0, 0.0};
     prim(u, P);
     if (mine)
 #pragma unroll
       for (int q = 0; q < 3; ++q) s[q] = SL[(e * NP + j) * 3 + q];
     const double idx = 1.0 / f.dx;
-    double Pn[3], sn[3];  // sub-cell j + 1
+    double Pm[3], sm[3];  // sub-cell j - 1
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
-      Pn[q] = grp_get(P[q], base + (j + 1 < W ? j + 1 : j), W);
-      sn[q] = grp_get(s[q], base + (j + 1 < W ? j + 1 : j), W);
+      Pm[q] = grp_get(P[q], base + (j > 0 ? j - 1 : 0), W);
+      sm[q] = grp_get(s[q], base + (j > 0 ? j - 1 : 0), W);
     }
-    double Fs[3] = {0.0, 0.0, 0.0}, g1 = 0.0;  // the flux and c_x on sub-cell face j + 1
-    if (mine && j < NP - 1) {
+    double Fs[3] = {Fe[0], Fe[1], Fe[2]}, gf = 0.0;  // the flux and c_x on sub-cell face j
+    if (active && j > 0 && j < NP) {
       double PL[3], PR[3], UL[3], UR[3], g[2], fvv[3], F[3];
 #pragma unroll
       for (int q = 0; q < 3; ++q) {
-        PL[q] = P[q] + 0.5 * f.dx * s[q];
-        PR[q] = Pn[q] - 0.5 * f.dx * sn[q];
+        PL[q] = Pm[q] + 0.5 * f.dx * sm[q];
+        PR[q] = P[q] - 0.5 * f.dx * s[q];
       }
       cons(PL, UL);
       cons(PR, UR);
-      g[0] = (Pn[1] - P[1]) * idx;
-      g[1] = (Pn[2] - P[2]) * idx;
-      g1 = g[1];
+      g[0] = (P[1] - Pm[1]) * idx;
+      g[1] = (P[2] - Pm[2]) * idx;
+      gf = g[1];
       numflux(p, UL, UR, F, eflag);
       visc(p, g, fvv);
 #pragma unroll
       for (int v = 0; v < 3; ++v) Fs[v] = F[v] - fvv[v];
+    } else if (active && (j == 0 || j == NP)) {
+      gf = Gf[(e * 2 + (j == 0 ? 0 : 1)) * 2 + 1];
     }
-    // the flux and c_x on the sub-cell's left face: the element face (lane 0) or lane j - 1's
-    double Fm[3], gm;
+    // sub-cell j: faces j (own) and j + 1 (lane j + 1)
+    double Fp[3];
 #pragma unroll
-    for (int v = 0; v < 3; ++v) Fm[v] = grp_get(Fs[v], base + (j > 0 ? j - 1 : 0), W);
-    gm = grp_get(g1, base + (j > 0 ? j - 1 : 0), W);
-    if (j == 0) {
+    for (int v = 0; v < 3; ++v) Fp[v] = grp_get(Fs[v], base + (j + 1 < W ? j + 1 : j), W);
+    const double gp = grp_get(gf, base + (j + 1 < W ? j + 1 : j), W);
 #pragma unroll
-      for (int v = 0; v < 3; ++v) Fm[v] = Fl[v];
-      gm = active ? Gf[(e * 2 + 0) * 2 + 1] : 0.0;
-    }
-    if (j == NP - 1) {
-#pragma unroll
-      for (int v = 0; v < 3; ++v) Fs[v] = Fr[v];
-      g1 = active ? Gf[(e * 2 + 1) * 2 + 1] : 0.0;
-    }
-#pragma unroll
-    for (int v = 0; v < 3; ++v) r[v] = -(Fs[v] - Fm[v]) * idx;
-    r[1] = fma(t.alpha * u[0], 0.5 * (gm + g1), r[1]);
+    for (int v = 0; v < 3; ++v) r[v] = -(Fp[v] - Fs[v]) * idx;
+    r[1] = fma(t.alpha * u[0], 0.5 * (gf + gp), r[1]);
     r[2] = fma(t.ab, u[0] - u[2], r[2]);
   }
   if (mine)
@@ -716,8 +730,9 @@ __global__ void __launch_bounds__(128)
 // each stage run in one cooperative launch of one-warp blocks (the face-state and update phases
 // give DG and FV elements to separate halves of the grid), separated by the bounded grid barrier;
 // nsteps steps then cost one launch instead of 21 per step. Fixed dt only. The element phases run
-// in lane groups (one lane per node or sub-cell), which splits each element's chain: a sub-cell
-// element's three internal HLLC solves run side by side instead of one after another.
+// in lane groups (one lane per node or sub-cell face), which splits each element's chain: a
+// sub-cell element's internal HLLC solves run side by side instead of one after another, and the
+// update's groups evaluate the element-face fluxes themselves, so a stage has three phases.
 constexpr int kCoopMaxE = 4096;
 struct LsrkCoef {
   double A[5], B[5];
@@ -728,12 +743,11 @@ __global__ void __launch_bounds__(32) k_fv_coop(const NskParams p, const FvParam
                                                 double* __restrict__ K, int* __restrict__ flags,
                                                 double* __restrict__ ind, double* __restrict__ Uf,
                                                 double* __restrict__ Gf, double* __restrict__ SL,
-                                                double* __restrict__ Q, double* __restrict__ Fh, const int nsteps,
+                                                double* __restrict__ Q, const int nsteps,
                                                 const int switching, const double dt, const LsrkCoef rk,
                                                 unsigned* __restrict__ bar, int* __restrict__ err,
                                                 const unsigned long long timeout_ns) {
   const long long first = (long long)blockIdx.x * blockDim.x + threadIdx.x, stride = (long long)gridDim.x * blockDim.x;
-  const long long nfaces = f.dirichlet ? p.E + 1 : p.E;
   // faces and update: the first half of the blocks takes the DG elements, the second the FV ones
   const unsigned half = gridDim.x / 2;
   const int role = blockIdx.x >= half;
@@ -754,10 +768,9 @@ __global__ void __launch_bounds__(32) k_fv_coop(const NskParams p, const FvParam
       if (!grid_barrier(bar, err, timeout_ns)) return;
       for (long long eb = gfirst; eb < p.E; eb += gstride) fv_lift_group<NP>(p, f, U, flags, Uf, Q, Gf, eb + grp, j);
       if (!grid_barrier(bar, err, timeout_ns)) return;
-      for (long long fc = first; fc < nfaces; fc += stride) fv_flux_body(p, f, Uf, Gf, Fh, err, fc);
-      if (!grid_barrier(bar, err, timeout_ns)) return;
+      // (the element-face fluxes are evaluated by the update's lane groups: no face phase)
       for (long long eb = rgfirst; eb < p.E; eb += rgstride)
-        fv_update_group<NP>(p, f, U, K, flags, Gf, SL, Q, Fh, rk.A[st], rk.B[st], dt, err, eb + grp, j, role);
+        fv_update_group<NP>(p, f, U, K, flags, Uf, Gf, SL, Q, rk.A[st], rk.B[st], dt, err, eb + grp, j, role);
       if (!grid_barrier(bar, err, timeout_ns)) return;
     }
   }
@@ -815,7 +828,7 @@ int launch_coop_t(const NskParams& p, const FvParams& f, const FvBuffers& fb, co
   // a barrier that timed out in an earlier launch may have left its arrival count behind
   if (cudaMemsetAsync(fb.bar, 0, 2 * sizeof(unsigned), s) != cudaSuccess) return NSK_ERR_CUDA;
   if (cudaLaunchKernelEx(&cfg, kern, p, f, (double*)b.U, (double*)b.K, fb.flags, fb.ind, fb.Uf, fb.Gf, fb.SL,
-                         (double*)b.Q, fb.Fh, nsteps, switching, dt, rk, fb.bar, b.err, timeout_ns) != cudaSuccess)
+                         (double*)b.Q, nsteps, switching, dt, rk, fb.bar, b.err, timeout_ns) != cudaSuccess)
     return NSK_ERR_CUDA;
   return 1;
 }
