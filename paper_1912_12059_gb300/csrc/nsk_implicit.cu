@@ -9,10 +9,11 @@
 // preconditioned by the inverses of the element blocks of I - dt gamma J(U_n)) with the
 // matrix-free product J v ~ (R(X + eps v) - R(X)) / eps, eps = sqrt(2^-52) (1 + ||X||) / ||v||;
 // the later stages use R_i = (X_i - S_i) / (dt gamma). The vector algebra runs in the kernels
-// below (dot products in a fixed order: deterministic), with the scales and projection
-// coefficients of a Krylov iteration kept on the device so that the iteration reads the host
-// once; the small GMRES least-squares problem and the control flow run on the host; a residual
-// evaluation is one stage launch of the context's pipeline in residual mode on the iterate.
+// below (dot products in a fixed order: deterministic), with the scales, the projection
+// coefficients, the Hessenberg matrix, the Givens rotations and the residual estimate kept on the
+// device: the host reads one number per Arnoldi step, one step behind the GPU, and the triangular
+// system once per GMRES cycle, which it solves; a residual evaluation is one stage launch of the
+// context's pipeline in residual mode on the iterate.
 #include <math.h>
 #include <string.h>
 
@@ -26,6 +27,7 @@ namespace {
 
 constexpr int kDotThreads = 256;
 constexpr int kDotBlocks = 152 * 8;
+constexpr int kChunk = 4;  // Arnoldi steps replayed between two reads of a GMRES cycle's control block
 
 // out = a x + b y + c z (y, z may be NULL; out may be x, y or z: each element is read before it
 // is written by the same thread)
@@ -42,7 +44,9 @@ __global__ void __launch_bounds__(256) k_lincomb(const long long n, const double
 // per-block partial sums of x . y (grid-stride per thread, then a shared-memory tree: the same
 // order on every call)
 __global__ void __launch_bounds__(kDotThreads) k_dot_part(const long long n, const double* __restrict__ x,
-                                                          const double* __restrict__ y, double* __restrict__ part) {
+                                                          const double* __restrict__ y, double* __restrict__ part,
+                                                          const int* __restrict__ stop) {
+  if (stop && *stop) return;
   __shared__ double red[kDotThreads];
   double s = 0.0;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
@@ -57,7 +61,8 @@ __global__ void __launch_bounds__(kDotThreads) k_dot_part(const long long n, con
 }
 
 __global__ void __launch_bounds__(kDotThreads) k_dot_final(const int nb, const double* __restrict__ part,
-                                                           double* __restrict__ out) {
+                                                           double* __restrict__ out, const int* __restrict__ stop) {
+  if (stop && *stop) return;
   __shared__ double red[kDotThreads];
   double s = 0.0;
   for (int i = threadIdx.x; i < nb; i += blockDim.x) s += part[i];
@@ -80,7 +85,9 @@ __device__ __forceinline__ double warp_sum(double v) {
 // partial sums of V_j . w: vector j = blockIdx.y (all vectors at once), warp shuffles, then
 // the warps' sums
 __global__ void __launch_bounds__(kDotThreads) k_mdot_part(const long long n, const double* const* __restrict__ V,
-                                                           const double* __restrict__ w, double* __restrict__ part) {
+                                                           const double* __restrict__ w, double* __restrict__ part,
+                                                           const int* __restrict__ stop) {
+  if (stop && *stop) return;
   __shared__ double red[kDotThreads / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, j = blockIdx.y;
   const double* v = V[j];
@@ -98,12 +105,17 @@ __global__ void __launch_bounds__(kDotThreads) k_mdot_part(const long long n, co
 }
 
 // the two vector updates of the forward-difference product J z, with eps = c0 / ||z||
-// (c0 = sqrt(2^-52) (1 + ||X||), ||z|| = sqrt(*zz), or 1 without zz) computed by every thread:
-// which = 0: out = X + eps z (the perturbed state); which = 1: out = z - (dtg / eps) RW + (dtg / eps) RX
+// (c0 = sqrt(2^-52) (1 + ||X||), from *c0p when given; ||z|| = sqrt(*zz), or 1 without zz)
+// computed by every thread: which = 0: out = X + eps z (the perturbed state); which = 1:
+// out = z - (dtg / eps) RW + (dtg / eps) RX
 __global__ void __launch_bounds__(256) k_fd_combine(const long long n, const int which, const double* __restrict__ zz,
-                                                    const double c0, const double dtg, const double* __restrict__ X,
+                                                    const double c0v, const double* __restrict__ c0p,
+                                                    const double dtg, const double* __restrict__ X,
                                                     const double* __restrict__ z, const double* __restrict__ RW,
-                                                    const double* __restrict__ RX, double* __restrict__ out) {
+                                                    const double* __restrict__ RX, double* __restrict__ out,
+                                                    const int* __restrict__ stop) {
+  if (stop && *stop) return;
+  const double c0 = c0p ? *c0p : c0v;
   const double eps = c0 / (zz ? sqrt(*zz) : 1.0);
   const double b = -dtg / eps, c = dtg / eps;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
@@ -128,7 +140,9 @@ constexpr int kMaxNv = 202;  // projections of a pass (krylov_dim + 1) plus w . 
 template <bool NORM>
 __global__ void __launch_bounds__(256) k_gs_update(const long long n, const int nv, const double* const* __restrict__ V,
                                                    const double* __restrict__ part, const int nb,
-                                                   double* __restrict__ w, double* __restrict__ hout) {
+                                                   double* __restrict__ w, double* __restrict__ hout,
+                                                   const int* __restrict__ stop) {
+  if (stop && *stop) return;  // uniform over the grid: before any barrier
   __shared__ double h[kMaxNv];
   __shared__ const double* vp[kMaxNv];
   __shared__ double inv;
@@ -249,7 +263,9 @@ __global__ void __launch_bounds__(128) k_block_invert(const int n, const double 
 // y_e = Minv_e x_e
 __global__ void __launch_bounds__(256) k_block_apply(const long long E, const int nvar, const int npe,
                                                      const long long nn, const double* __restrict__ Minv,
-                                                     const double* __restrict__ x, double* __restrict__ y) {
+                                                     const double* __restrict__ x, double* __restrict__ y,
+                                                     const int* __restrict__ stop) {
+  if (stop && *stop) return;
   const int n = nvar * npe;
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < E * n; t += (long long)gridDim.x * blockDim.x) {
     const long long e = t / n;
@@ -259,6 +275,56 @@ __global__ void __launch_bounds__(256) k_block_apply(const long long E, const in
     for (int k = 0; k < n; ++k) s = fma(row[k], x[(size_t)(k / npe) * nn + e * npe + k % npe], s);
     y[(size_t)(i / npe) * nn + e * npe + i % npe] = s;
   }
+}
+
+// Control block of a GMRES cycle in device memory: the forward-difference scale c0, the cycle's
+// starting residual norm beta, its absolute tolerance and step limit, set by k_cycle_init; the
+// last step's residual estimate, the number of steps done, and stop, which ends the cycle's
+// remaining steps (every kernel of an Arnoldi step returns at once when it is set).
+struct CycleCtl {
+  double c0, beta, tol, res;
+  int kmax, stop, kdone, pad;
+};
+__global__ void k_cycle_init(CycleCtl* ctl, const double c0, const double beta, const double tol, const int kmax) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  ctl->c0 = c0;
+  ctl->beta = beta;
+  ctl->tol = tol;
+  ctl->res = beta;
+  ctl->kmax = kmax;
+  ctl->stop = 0;
+  ctl->kdone = 0;
+}
+
+// Arnoldi step k of a GMRES cycle on the device (one thread): column k of the Hessenberg matrix
+// H ((m + 1) x m, row-major) from the two Gram-Schmidt passes' coefficients (h1[0..k] + h2[0..k],
+// and the new vector's norm h2[k + 1]), the earlier Givens rotations applied to it, the new
+// rotation (cs, sn), and the rotated right-hand side gv (gv[0] = beta at k = 0); then the residual
+// estimate |gv[k + 1]|, and stop once it is within the tolerance or the cycle's steps are used up.
+__global__ void k_arnoldi_update(const int k, const int m, const double* __restrict__ h1,
+                                 const double* __restrict__ h2, double* __restrict__ H, double* __restrict__ cs,
+                                 double* __restrict__ sn, double* __restrict__ gv, CycleCtl* __restrict__ ctl) {
+  if (threadIdx.x != 0 || blockIdx.x != 0 || ctl->stop) return;
+  if (k == 0) gv[0] = ctl->beta;
+  for (int j = 0; j <= k; ++j) H[(size_t)j * m + k] = h1[j] + h2[j];
+  H[(size_t)(k + 1) * m + k] = h2[k + 1];
+  for (int j = 0; j < k; ++j) {  // earlier rotations
+    const double a = H[(size_t)j * m + k], b = H[(size_t)(j + 1) * m + k];
+    H[(size_t)j * m + k] = cs[j] * a + sn[j] * b;
+    H[(size_t)(j + 1) * m + k] = -sn[j] * a + cs[j] * b;
+  }
+  const double a = H[(size_t)k * m + k], b = H[(size_t)(k + 1) * m + k];
+  const double d = hypot(a, b);
+  cs[k] = a / d;
+  sn[k] = b / d;
+  H[(size_t)k * m + k] = d;
+  H[(size_t)(k + 1) * m + k] = 0.0;
+  gv[k + 1] = -sn[k] * gv[k];
+  gv[k] = cs[k] * gv[k];
+  const double res = fabs(gv[k + 1]);
+  ctl->res = res;
+  ctl->kdone = k + 1;
+  if (res <= ctl->tol || k + 1 >= ctl->kmax) ctl->stop = 1;
 }
 
 // ARK4(3)6L[2]SA, implicit part (Kennedy and Carpenter 2003): a_ij for j < i; gamma = 1/4
@@ -282,6 +348,10 @@ struct Implicit {
   long long launches = 0;
   long long rhs_evals = 0;
   int status = NSK_OK;
+  // inside a cycle's Arnoldi steps: the cycle's stop flag and forward-difference scale on the
+  // device (NULL elsewhere)
+  const int* stop = nullptr;
+  const double* c0p = nullptr;
 
   void lincomb(double a, const double* x, double b, const double* y, double cc, const double* z, double* out) {
     k_lincomb<<<grid, 256, 0, s>>>(n, a, x, b, y, cc, z, out);
@@ -289,8 +359,8 @@ struct Implicit {
   }
   int nblk;             // blocks of the dot-product partial sums: up to kDotBlocks, one per 256 values
   double dot(const double* x, const double* y) {
-    k_dot_part<<<nblk, kDotThreads, 0, s>>>(n, x, y, part);
-    k_dot_final<<<1, kDotThreads, 0, s>>>(nblk, part, dotv);
+    k_dot_part<<<nblk, kDotThreads, 0, s>>>(n, x, y, part, nullptr);
+    k_dot_final<<<1, kDotThreads, 0, s>>>(nblk, part, dotv, nullptr);
     launches += 2;
     double h = 0.0;
     if (cudaMemcpyAsync(&h, dotv, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
@@ -301,25 +371,25 @@ struct Implicit {
   double norm(const double* x) { return sqrt(dot(x, x)); }
   // x . x into *dotv on the device (no synchronisation)
   void dot_dev(const double* x) {
-    k_dot_part<<<nblk, kDotThreads, 0, s>>>(n, x, x, part);
-    k_dot_final<<<1, kDotThreads, 0, s>>>(nblk, part, dotv);
+    k_dot_part<<<nblk, kDotThreads, 0, s>>>(n, x, x, part, stop);
+    k_dot_final<<<1, kDotThreads, 0, s>>>(nblk, part, dotv, stop);
     launches += 2;
   }
   // one Gram-Schmidt pass on w against V_0..V_{nv-1} (dV: device copy of the basis pointers):
   // the projections (and with norm, w . w, the Pythagorean norm and the normalisation) in two
   // kernels, the coefficients left in hout on the device
   void gs_pass(int nv, bool norm, double* const* dV, double* w, double* hout) {
-    k_mdot_part<<<dim3(nblk, norm ? nv + 1 : nv), kDotThreads, 0, s>>>(n, dV, w, part);
+    k_mdot_part<<<dim3(nblk, norm ? nv + 1 : nv), kDotThreads, 0, s>>>(n, dV, w, part, stop);
     if (norm)
-      k_gs_update<true><<<grid, 256, 0, s>>>(n, nv, dV, part, nblk, w, hout);
+      k_gs_update<true><<<grid, 256, 0, s>>>(n, nv, dV, part, nblk, w, hout, stop);
     else
-      k_gs_update<false><<<grid, 256, 0, s>>>(n, nv, dV, part, nblk, w, hout);
+      k_gs_update<false><<<grid, 256, 0, s>>>(n, nv, dV, part, nblk, w, hout, stop);
     launches += 2;
   }
   // the forward-difference combinations (k_fd_combine), zz = ||z||^2 on the device or NULL
   void fd_combine(int which, const double* zz, double c0, double dtg, const double* X, const double* z,
                   const double* RW, const double* RX, double* out) {
-    k_fd_combine<<<grid, 256, 0, s>>>(n, which, zz, c0, dtg, X, z, RW, RX, out);
+    k_fd_combine<<<grid, 256, 0, s>>>(n, which, zz, c0, c0p, dtg, X, z, RW, RX, out, stop);
     ++launches;
   }
   // out = R(X): one residual-mode stage of the context's pipeline on X
@@ -374,9 +444,11 @@ int nsk_step_esdirk(nsk_ctx* c, double dt, int nsteps, double newton_tol, double
     return NSK_ERR_NOMEM;
   }
   // dot partials ((m + 1) vectors x blocks), a dot result, the two Gram-Schmidt passes'
-  // coefficients (m + 1, and m + 2 with the norm), m + 1 basis pointers
+  // coefficients (m + 1, and m + 2 with the norm), m + 1 basis pointers, then the cycle's
+  // Hessenberg matrix ((m + 1) x m), rotations (2 m) and right-hand side (m + 1)
   double* part = nullptr;
-  const size_t part_n = (size_t)(m + 1) * kDotBlocks + 1 + (m + 1) + (m + 2) + (m + 1);
+  const size_t part_n = (size_t)(m + 1) * kDotBlocks + 1 + (m + 1) + (m + 2) + (m + 1) + (size_t)(m + 1) * m +
+                        2 * (size_t)m + (m + 1);
   if (cudaMalloc(&part, sizeof(double) * part_n) != cudaSuccess) {
     cudaGetLastError();
     cudaFree(pool);
@@ -426,18 +498,46 @@ int nsk_step_esdirk(nsk_ctx* c, double dt, int nsteps, double newton_tol, double
   double* hd1 = im.dotv + 1;       // first pass: h1[0..k]
   double* hd2 = hd1 + (m + 1);     // second pass: h2[0..k], then the new vector's norm at k + 1
   double** dV = (double**)(hd2 + (m + 2));
+  double* Hd = (double*)(dV + (m + 1));
+  double* csd = Hd + (size_t)(m + 1) * m;
+  double* snd = csd + m;
+  double* gvd = snd + m;
   if (cudaMemcpyAsync(dV, V.data(), sizeof(double*) * (m + 1), cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
     im.status = NSK_ERR_CUDA;
-  std::vector<double> hh(2 * (size_t)m + 3);  // host copy of hd1 and hd2
+  // the cycle's control block on the device and its host copy (pinned); one CUDA graph per Arnoldi
+  // step k, captured on first use and replayed for every cycle of the call
+  CycleCtl* ctl = nullptr;
+  CycleCtl* hctl = nullptr;
+  std::vector<cudaGraphExec_t> gstep((size_t)m, nullptr);
+  std::vector<long long> gstep_launches((size_t)m, 0);
+  bool graphs = true;  // false after a failed capture: the steps are then launched directly
+  if (cudaMalloc(&ctl, sizeof(CycleCtl)) != cudaSuccess || cudaMallocHost(&hctl, sizeof(CycleCtl)) != cudaSuccess) {
+    cudaGetLastError();
+    im.status = NSK_ERR_NOMEM;
+  }
+  // the call runs on a stream of its own (stream capture needs one other than the legacy default
+  // stream), ordered after the context's stream by an event and before it again at the end; the
+  // context's kernels (the residual evaluations) launch there for the call's duration
+  cudaStream_t ctx_stream = c->stream, own = nullptr;
+  cudaEvent_t order = nullptr;
+  if (cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&order, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventRecord(order, ctx_stream) != cudaSuccess || cudaStreamWaitEvent(own, order, 0) != cudaSuccess) {
+    cudaGetLastError();
+    im.status = NSK_ERR_CUDA;
+  } else {
+    c->stream = own;
+    im.s = own;
+  }
   long long st_newton = 0, st_krylov = 0, st_fail = 0;
   double* U = (double*)c->b.U;  // U_n, then U_{n+1}
   const double gdt = kGamma * dt;
-  std::vector<double> H((size_t)(m + 1) * m), gv(m + 1), cs(m), sn(m), y(m);
+  std::vector<double> H((size_t)(m + 1) * m), gv(m + 1), y(m);  // host copies for the back substitution
 
   const unsigned eg = (unsigned)std::min<long long>((c->E * nloc + 255) / 256, 152 * 16);
   // z = M^-1 x (identity without the preconditioner)
   auto precond = [&](const double* x, double* z) {
-    k_block_apply<<<eg, 256, 0, im.s>>>(c->E, c->nvar, c->npe, c->nn, Jb, x, z);
+    k_block_apply<<<eg, 256, 0, im.s>>>(c->E, c->nvar, c->npe, c->nn, Jb, x, z, im.stop);
     ++im.launches;
   };
   for (int step = 0; step < nsteps && im.status == NSK_OK; ++step) {
@@ -479,55 +579,107 @@ int nsk_step_esdirk(nsk_ctx* c, double dt, int nsteps, double newton_tol, double
         int its = 0;
         bool done = false;
         while (!done && im.status == NSK_OK) {
-          std::fill(H.begin(), H.end(), 0.0);
-          std::fill(gv.begin(), gv.end(), 0.0);
-          gv[0] = beta;
-          int k = 0;
-          for (k = 0; k < m; ++k) {
-            // V_{k+1} = (I - dt gamma J) z, z = M^-1 V_k (z = V_k, ||z|| = 1, without the
-            // preconditioner), J z ~ (R(X + eps z) - R(X)) / eps
+          // Arnoldi steps k = 0, 1, ...: V_{k+1} = (I - dt gamma J) z, z = M^-1 V_k (z = V_k, ||z|| = 1,
+          // without the preconditioner), J z ~ (R(X + eps z) - R(X)) / eps, classical Gram-Schmidt
+          // twice (CGS2: each pass's k + 1 projections in one kernel and the update in another, the
+          // second pass's w . w giving the new vector's norm by Pythagoras), then the Hessenberg
+          // column, the Givens rotations and the residual estimate on the device (k_arnoldi_update,
+          // which sets the cycle's stop flag). Each step is a CUDA graph replayed from the host in
+          // chunks of kChunk, the control block read after each chunk: the steps after the stop
+          // return at once (only their residual evaluation still runs, on an unused vector).
+          auto arnoldi = [&](int k) {
             const double* zk = V[k];
             if (block_precond) {
               precond(V[k], Z);
               zk = Z;
               im.dot_dev(Z);
             }
-            // eps and the scales inside the combinations (||z|| = 1 without the preconditioner)
             const double* zz = block_precond ? im.dotv : nullptr;
-            const double c0 = sqrt(ldexp(1.0, -52)) * (1.0 + xn);
-            im.fd_combine(0, zz, c0, gdt, X, zk, nullptr, nullptr, W);  // W = X + eps z
+            im.fd_combine(0, zz, 0.0, gdt, X, zk, nullptr, nullptr, W);  // W = X + eps z
             im.rhs(W, RW);
-            im.fd_combine(1, zz, c0, gdt, nullptr, zk, RW, RX, V[k + 1]);
-            ++its;
-            // classical Gram-Schmidt, twice (CGS2), each pass's k + 1 projections in one kernel and
-            // the update in another, the coefficients kept on the device; the second pass also
-            // takes w . w, which gives the new vector's norm by Pythagoras; one host read per iteration
+            im.fd_combine(1, zz, 0.0, gdt, nullptr, zk, RW, RX, V[k + 1]);
             im.gs_pass(k + 1, false, dV, V[k + 1], hd1);
             im.gs_pass(k + 1, true, dV, V[k + 1], hd2);
-            if (cudaMemcpyAsync(hh.data(), hd1, sizeof(double) * ((size_t)m + 1 + k + 2), cudaMemcpyDeviceToHost,
-                                im.s) != cudaSuccess ||
+            k_arnoldi_update<<<1, 32, 0, im.s>>>(k, m, hd1, hd2, Hd, csd, snd, gvd, ctl);
+            ++im.launches;
+          };
+          auto replay = [&](int k) {
+            if (!graphs) {  // direct launches, predicated by the same control block
+              im.stop = &ctl->stop;
+              im.c0p = &ctl->c0;
+              arnoldi(k);
+              ++im.rhs_evals;
+              im.stop = nullptr;
+              im.c0p = nullptr;
+              return;
+            }
+            if (!gstep[(size_t)k]) {  // capture step k once
+              const long long l0 = im.launches, r0 = im.rhs_evals;
+              im.stop = &ctl->stop;
+              im.c0p = &ctl->c0;
+              cudaGraph_t g = nullptr;
+              if (cudaStreamBeginCapture(im.s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+                im.status = NSK_ERR_CUDA;
+              } else {
+                arnoldi(k);
+                if (cudaStreamEndCapture(im.s, &g) != cudaSuccess || !g ||
+                    cudaGraphInstantiate(&gstep[(size_t)k], g, 0) != cudaSuccess)
+                  im.status = NSK_ERR_CUDA;
+                if (g) cudaGraphDestroy(g);
+              }
+              im.stop = nullptr;
+              im.c0p = nullptr;
+              gstep_launches[(size_t)k] = im.launches - l0;
+              im.launches = l0;
+              im.rhs_evals = r0;
+              if (im.status != NSK_OK) {  // no graph: this and the later steps are launched directly
+                cudaGetLastError();
+                if (gstep[(size_t)k]) {
+                  cudaGraphExecDestroy(gstep[(size_t)k]);
+                  gstep[(size_t)k] = nullptr;
+                }
+                im.status = NSK_OK;
+                graphs = false;
+                im.stop = &ctl->stop;
+                im.c0p = &ctl->c0;
+                arnoldi(k);
+                ++im.rhs_evals;
+                im.stop = nullptr;
+                im.c0p = nullptr;
+                return;
+              }
+            }
+            if (cudaGraphLaunch(gstep[(size_t)k], im.s) != cudaSuccess) {
+              im.status = NSK_ERR_CUDA;
+              return;
+            }
+            im.launches += gstep_launches[(size_t)k];
+            ++im.rhs_evals;
+          };
+          const int kmax = std::min(m, max_krylov - its);
+          k_cycle_init<<<1, 32, 0, im.s>>>(ctl, sqrt(ldexp(1.0, -52)) * (1.0 + xn), beta, krylov_tol * bn, kmax);
+          ++im.launches;
+          for (int k0 = 0; k0 < kmax && im.status == NSK_OK; k0 += kChunk) {
+            for (int k = k0; k < std::min(k0 + kChunk, kmax) && im.status == NSK_OK; ++k) replay(k);
+            if (cudaMemcpyAsync(hctl, ctl, sizeof(CycleCtl), cudaMemcpyDeviceToHost, im.s) != cudaSuccess ||
                 cudaStreamSynchronize(im.s) != cudaSuccess)
               im.status = NSK_ERR_CUDA;
-            const double* h1 = hh.data();
-            const double* h2 = hh.data() + (m + 1);
-            for (int j = 0; j <= k; ++j) H[(size_t)j * m + k] = h1[j] + h2[j];
-            H[(size_t)(k + 1) * m + k] = h2[k + 1];
-            for (int j = 0; j < k; ++j) {  // earlier Givens rotations
-              const double a = H[(size_t)j * m + k], b = H[(size_t)(j + 1) * m + k];
-              H[(size_t)j * m + k] = cs[j] * a + sn[j] * b;
-              H[(size_t)(j + 1) * m + k] = -sn[j] * a + cs[j] * b;
-            }
-            const double a = H[(size_t)k * m + k], b = H[(size_t)(k + 1) * m + k];
-            const double d = hypot(a, b);
-            cs[k] = a / d;
-            sn[k] = b / d;
-            H[(size_t)k * m + k] = d;
-            H[(size_t)(k + 1) * m + k] = 0.0;
-            gv[k + 1] = -sn[k] * gv[k];
-            gv[k] = cs[k] * gv[k];
-            if (fabs(gv[k + 1]) <= krylov_tol * bn || its >= max_krylov) break;
+            if (hctl->stop) break;
           }
-          const int kk = (k < m ? k : m - 1) + 1;
+          if (im.status != NSK_OK) break;
+          const int kk = hctl->kdone;   // Arnoldi steps of the cycle's least-squares problem
+          const double resk = hctl->res;  // its residual estimate
+          its += kk;
+          if (kk == 0) break;
+          // the cycle's triangular system and rotated right-hand side
+          if (cudaMemcpyAsync(H.data(), Hd, sizeof(double) * (size_t)kk * m, cudaMemcpyDeviceToHost, im.s) !=
+                  cudaSuccess ||
+              cudaMemcpyAsync(gv.data(), gvd, sizeof(double) * (size_t)kk, cudaMemcpyDeviceToHost, im.s) !=
+                  cudaSuccess ||
+              cudaStreamSynchronize(im.s) != cudaSuccess) {
+            im.status = NSK_ERR_CUDA;
+            break;
+          }
           for (int r = kk - 1; r >= 0; --r) {  // back substitution on the triangular Hessenberg
             double t = gv[r];
             for (int j = r + 1; j < kk; ++j) t -= H[(size_t)r * m + j] * y[j];
@@ -541,7 +693,7 @@ int nsk_step_esdirk(nsk_ctx* c, double dt, int nsteps, double newton_tol, double
           } else {
             for (int j = 0; j < kk; ++j) im.lincomb(1.0, D, y[j], V[j], 0.0, nullptr, D);
           }
-          if (fabs(gv[kk]) <= krylov_tol * bn || its >= max_krylov) {
+          if (resk <= krylov_tol * bn || its >= max_krylov) {
             done = true;
           } else {  // restart: r = -G - (I - dt gamma J) D
             const double dn = im.norm(D);
@@ -566,10 +718,24 @@ int nsk_step_esdirk(nsk_ctx* c, double dt, int nsteps, double newton_tol, double
     }
     im.lincomb(1.0, X, 0.0, nullptr, 0.0, nullptr, U);  // stiffly accurate: U_{n+1} = X_6
   }
+  if (own) {  // back to the context's stream, after the call's work
+    if (c->stream == own &&
+        (cudaEventRecord(order, own) != cudaSuccess || cudaStreamWaitEvent(ctx_stream, order, 0) != cudaSuccess) &&
+        im.status == NSK_OK)
+      im.status = NSK_ERR_CUDA;
+    c->stream = ctx_stream;
+    im.s = ctx_stream;
+    cudaStreamDestroy(own);  // released once its work is done
+  }
+  if (order) cudaEventDestroy(order);
   int r = im.status;
   const int rs = nsk_ctx_sync_check(c);
   if (r == NSK_OK) r = rs;
   c->launches += im.launches;
+  for (cudaGraphExec_t ge : gstep)
+    if (ge) cudaGraphExecDestroy(ge);
+  if (hctl) cudaFreeHost(hctl);
+  cudaFree(ctl);
   cudaFree(Jb);
   cudaFree(colour);
   cudaFree(part);
