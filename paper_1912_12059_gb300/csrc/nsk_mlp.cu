@@ -487,29 +487,45 @@ __global__ void k_elem_mean(const long long E, const int npe, const R* __restric
   if (lane == 0) mean[e] = acc / (float)npe;
 }
 
-template <typename R>
-__global__ void k_closure_features(const NskParams p, const int npe, const int dim, const R* __restrict__ U,
-                                   const float* __restrict__ mean_e, __nv_bfloat16* __restrict__ X,
-                                   const int nin_pad) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const int nf = npe + 2 * dim;
-  if (i >= p.E * nf) return;
-  const long long e = i / nf;
-  const int f = (int)(i % nf);
+// one warp per element: lane f takes features f, f + 32, ... (no division per value; the face
+// neighbours from the element's Cartesian position)
+template <typename R, int D>
+__global__ void __launch_bounds__(256) k_closure_features(const NskParams p, const int npe, const R* __restrict__ U,
+                                                          const float* __restrict__ mean_e,
+                                                          __nv_bfloat16* __restrict__ X, const int nin_pad) {
+  const long long e = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (e >= p.E) return;
+  const int nf = npe + 2 * D;
   const float mean = mean_e[e];
-  float v;
-  if (f < npe) {
-    v = (float)U[e * npe + f] - mean;
-  } else {
-    const int j = f - npe;
-    v = mean_e[nsk::nbr_elem(p, e, j >> 1, (j & 1) ? 1 : -1)] - mean;
-  }
-  v /= kFeatScale;
-  const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+  const nsk::ElemIdx ex = nsk::elem_idx<D>(p, (int)e);
   __nv_bfloat16* row = X + e * nin_pad;
-  row[f] = hi;
-  row[nf + f] = __float2bfloat16_rn(v - __bfloat162float(hi));
-  if (f < nin_pad - 2 * nf) row[2 * nf + f] = __float2bfloat16_rn(0.f);  // zero padding columns
+  for (int f = lane; f < nf; f += 32) {
+    float v;
+    if (f < npe) {
+      v = (float)U[e * npe + f] - mean;
+    } else {
+      const int j = f - npe;
+      v = mean_e[nsk::nbr_of(p, ex, j >> 1, (j & 1) ? 1 : -1)] - mean;
+    }
+    v /= kFeatScale;
+    const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+    row[f] = hi;
+    row[nf + f] = __float2bfloat16_rn(v - __bfloat162float(hi));
+  }
+  for (int f = 2 * nf + lane; f < nin_pad; f += 32) row[f] = __float2bfloat16_rn(0.f);  // zero padding columns
+}
+
+template <typename R>
+int launch_features(const nsk_ctx* c, const R* U, const float* mean, __nv_bfloat16* X, int nin_pad) {
+  const unsigned g = nb(c->E * 32);
+  if (c->dim == 1)
+    k_closure_features<R, 1><<<g, 256, 0, c->stream>>>(c->p, c->npe, U, mean, X, nin_pad);
+  else if (c->dim == 2)
+    k_closure_features<R, 2><<<g, 256, 0, c->stream>>>(c->p, c->npe, U, mean, X, nin_pad);
+  else
+    k_closure_features<R, 3><<<g, 256, 0, c->stream>>>(c->p, c->npe, U, mean, X, nin_pad);
+  return cudaGetLastError() == cudaSuccess ? NSK_OK : NSK_ERR_CUDA;
 }
 
 template <typename R>
@@ -552,23 +568,21 @@ double closure_scale(const nsk_ctx* c) { return c->p.kappa / c->p.alpha * c->p.r
 
 int closure_features(nsk_ctx* c, void* X) {
   const int nin_pad = round16(2 * (c->npe + 2 * c->dim));
-  const long long n = c->E * (c->npe + 2 * c->dim);
   if (!c->cl_mean && cudaMalloc((void**)&c->cl_mean, sizeof(float) * c->E) != cudaSuccess) {
     cudaGetLastError();
     return NSK_ERR_NOMEM;
   }
   float* mean = c->cl_mean;
+  int st;
   if (c->precision == NSK_FP32_MIXED) {
     k_elem_mean<float><<<nb(c->E * 32), 256, 0, c->stream>>>(c->E, c->npe, (const float*)c->b.U, mean);
-    k_closure_features<float><<<nb(n), 256, 0, c->stream>>>(c->p, c->npe, c->dim, (const float*)c->b.U, mean,
-                                                            (__nv_bfloat16*)X, nin_pad);
+    st = launch_features<float>(c, (const float*)c->b.U, mean, (__nv_bfloat16*)X, nin_pad);
   } else {
     k_elem_mean<double><<<nb(c->E * 32), 256, 0, c->stream>>>(c->E, c->npe, (const double*)c->b.U, mean);
-    k_closure_features<double><<<nb(n), 256, 0, c->stream>>>(c->p, c->npe, c->dim, (const double*)c->b.U, mean,
-                                                             (__nv_bfloat16*)X, nin_pad);
+    st = launch_features<double>(c, (const double*)c->b.U, mean, (__nv_bfloat16*)X, nin_pad);
   }
   c->launches += 2;
-  return cudaGetLastError() == cudaSuccess ? NSK_OK : NSK_ERR_CUDA;
+  return st;
 }
 
 }  // namespace
