@@ -734,7 +734,8 @@ __global__ void __launch_bounds__(kFwThreads, 1) k_mlp_fwd3(const MlpFwdArgs a) 
 //  - operands arrive by TMA (cp.async.bulk.tensor, boxes 8 K columns wide that land directly in
 //    the K-major no-swizzle core-matrix layout below); one warp issues the loads, one warp the
 //    MMAs, and kWsEpiWarps warps run the epilogues;
-//  - W2 stays resident; W1 and W3 stream through a ring of slabs of 16 K columns;
+//  - W2 stays resident; the row tile X and W1 stream together through a ring of entries, one
+//    16-column slab of each per layer-1 K step, and W3 in one entry per 64-column activation chunk;
 //  - a layer's activations are written in 64-column chunks into a two-slot ring, and the next
 //    layer's MMAs consume chunk c while the epilogue produces chunk c + 1;
 //  - layer 1 of the next tile accumulates in TMEM columns [0, H1) while the epilogue works on
@@ -749,15 +750,19 @@ constexpr int kWsEpiWarps = 16;                       // 4 per TMEM lane quarter
 constexpr int kWsThreads = (kWsEpiWarps + 2) * 32;    // + the TMA warp and the MMA warp
 constexpr int kWsHChunk = 64;                         // activation columns per ring slot
 constexpr int kWsHSlot = kBM * kWsHChunk * 2;         // bytes of one activation slot
-constexpr int kWsMaxRing = 4;
+constexpr int kWsMaxRing = 6;
+constexpr int kWsXSlab = kBM * 16 * 2;                // bytes of a 16-column slab of the row tile
 
 struct FwdMaps {
   CUtensorMap x, w1, w2, w3;  // X [M][ldx], W1 [H1][K1], W2 [H2][H1], W3 [NO][H2], boxes 8 x rows
 };
 
-__host__ __device__ inline int ws_slot_bytes(const MlpFwdArgs& a) { return (a.H1 > a.NO ? a.H1 : a.NO) * 32; }
-__host__ __device__ inline int ws_off_x(const MlpFwdArgs& a) { return fw_align(a.H2 * a.H1 * 2); }
-__host__ __device__ inline int ws_off_h(const MlpFwdArgs& a) { return ws_off_x(a) + fw_align(kBM * a.K1 * 2); }
+// a ring slot holds a 16-column slab of the row tile X with the matching W1 slab (H1 rows), or a W3
+// chunk (NO rows x one activation chunk of 64 columns)
+__host__ __device__ inline int ws_slot_bytes(const MlpFwdArgs& a) {
+  return kWsXSlab + a.H1 * 32 > a.NO * kWsHChunk * 2 ? kWsXSlab + a.H1 * 32 : a.NO * kWsHChunk * 2;
+}
+__host__ __device__ inline int ws_off_h(const MlpFwdArgs& a) { return fw_align(a.H2 * a.H1 * 2); }
 __host__ __device__ inline int ws_off_w(const MlpFwdArgs& a) { return ws_off_h(a) + 2 * kWsHSlot; }
 __host__ __device__ inline int ws_off_bias(const MlpFwdArgs& a, int ns) {
   return ws_off_w(a) + fw_align(ns * ws_slot_bytes(a));
@@ -868,7 +873,7 @@ __device__ __forceinline__ void ws_gelu16(uint32_t taddr, uint32_t bias, unsigne
 
 // barrier indices in the kernel's array
 enum WsBar : int {
-  WB_W2 = 0, WB_XFULL, WB_XFREE, WB_A1FULL, WB_A1FREE, WB_A2FULL, WB_A2FREE, WB_A3FULL, WB_FINAL,
+  WB_W2 = 0, WB_A1FULL, WB_A1FREE, WB_A2FULL, WB_A2FREE, WB_A3FULL, WB_FINAL,
   WB_HFULL, WB_HFREE = WB_HFULL + 2, WB_WFULL = WB_HFREE + 2, WB_WFREE = WB_WFULL + kWsMaxRing,
   WB_COUNT = WB_WFREE + kWsMaxRing
 };
@@ -883,7 +888,7 @@ __global__ void __launch_bounds__(kWsThreads, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ntiles = (a.M + kBM - 1) / kBM;
   const int slotb = ws_slot_bytes(a);
-  const uint32_t aW2 = smem_u32(ws_smem), aX = smem_u32(ws_smem + ws_off_x(a)), aH = smem_u32(ws_smem + ws_off_h(a));
+  const uint32_t aW2 = smem_u32(ws_smem), aH = smem_u32(ws_smem + ws_off_h(a));
   const uint32_t aW = smem_u32(ws_smem + ws_off_w(a));
   unsigned char* sH = ws_smem + ws_off_h(a);
   float* sB = reinterpret_cast<float*>(ws_smem + ws_off_bias(a, ns));  // b1 | b2 | b3
@@ -910,79 +915,77 @@ __global__ void __launch_bounds__(kWsThreads, 1)
   const uint32_t tm = tmem_slot;
 
   if (warp == kWsEpiWarps) {
-    // ---- TMA producer: W2 once; per tile: the next tile's X and W1 slabs, then this tile's W3 slabs
+    // ---- TMA producer: W2 once; per tile: the next tile's X and W1 slabs, then this tile's W3 chunks
     // (the order in which the MMA warp consumes the ring) ----
     if (lane == 0) {
-      uint32_t xph = 1u, r = 0u, nx = 0u;
+      uint32_t r = 0u;
       int armed[kWsMaxRing];
       for (int i = 0; i < kWsMaxRing; ++i) armed[i] = 0;
       bool ok = true;
-      auto load_x = [&](int t) {
-        ok = ok && ws_wait(bar(WB_XFREE), xph, a.err, aborted);
-        xph ^= 1u;
+      // X columns [k0, k0 + 16) of row tile t (rows beyond M read as zero), then the W1 slab
+      auto load_xw1 = [&](int t, int k0) {
+        const uint32_t s = r % (uint32_t)ns;
+        ok = ok && ws_wait(bar(WB_WFREE + s), ((r / ns) & 1u) ^ 1u, a.err, aborted);
         if (!ok) return;
-        mbar_expect_tx(bar(WB_XFULL), (uint32_t)(kBM * a.K1 * 2));
-        for (int b = 0; b < a.K1 / 8; ++b) tma_load_2d(aX + (uint32_t)(b * kBM * 16), &maps.x, 8 * b, t * kBM, bar(WB_XFULL));
-        ++nx;
+        const uint32_t dst = aW + s * (uint32_t)slotb, w1 = dst + (uint32_t)kWsXSlab;
+        mbar_expect_tx(bar(WB_WFULL + s), (uint32_t)(kWsXSlab + a.H1 * 32));
+        tma_load_2d(dst, &maps.x, k0, t * kBM, bar(WB_WFULL + s));
+        tma_load_2d(dst + (uint32_t)(kBM * 16), &maps.x, k0 + 8, t * kBM, bar(WB_WFULL + s));
+        tma_load_2d(w1, &maps.w1, k0, 0, bar(WB_WFULL + s));
+        tma_load_2d(w1 + (uint32_t)(a.H1 * 16), &maps.w1, k0 + 8, 0, bar(WB_WFULL + s));
+        armed[s] = (int)(r / ns) + 1;
+        ++r;
       };
-      auto load_slab = [&](const CUtensorMap* m, int rows, int k0) {
+      // W3 columns [k0, k0 + w) of one activation chunk (w <= 64): w / 8 boxes side by side
+      auto load_w3_chunk = [&](int k0, int w) {
         const uint32_t s = r % (uint32_t)ns;
         ok = ok && ws_wait(bar(WB_WFREE + s), ((r / ns) & 1u) ^ 1u, a.err, aborted);
         if (!ok) return;
         const uint32_t dst = aW + s * (uint32_t)slotb;
-        mbar_expect_tx(bar(WB_WFULL + s), (uint32_t)(rows * 32));
-        tma_load_2d(dst, m, k0, 0, bar(WB_WFULL + s));
-        tma_load_2d(dst + (uint32_t)(rows * 16), m, k0 + 8, 0, bar(WB_WFULL + s));
+        mbar_expect_tx(bar(WB_WFULL + s), (uint32_t)(a.NO * w * 2));
+        for (int b = 0; b < w / 8; ++b)
+          tma_load_2d(dst + (uint32_t)(b * a.NO * 16), &maps.w3, k0 + 8 * b, 0, bar(WB_WFULL + s));
         armed[s] = (int)(r / ns) + 1;
         ++r;
       };
       mbar_expect_tx(bar(WB_W2), (uint32_t)(a.H2 * a.H1 * 2));
       for (int b = 0; b < a.H1 / 8; ++b) tma_load_2d(aW2 + (uint32_t)(b * a.H2 * 16), &maps.w2, 8 * b, 0, bar(WB_W2));
       int t = blockIdx.x;
-      if (t < ntiles) {
-        load_x(t);
-        for (int k0 = 0; ok && k0 < a.K1; k0 += 16) load_slab(&maps.w1, a.H1, k0);
-      }
+      if (t < ntiles)
+        for (int k0 = 0; ok && k0 < a.K1; k0 += 16) load_xw1(t, k0);
       for (; ok && t < ntiles; t += gridDim.x) {
-        if (t + (int)gridDim.x < ntiles) {
-          load_x(t + gridDim.x);
-          for (int k0 = 0; ok && k0 < a.K1; k0 += 16) load_slab(&maps.w1, a.H1, k0);
-        }
-        for (int k0 = 0; ok && k0 < a.H2; k0 += 16) load_slab(&maps.w3, a.NO, k0);
+        if (t + (int)gridDim.x < ntiles)
+          for (int k0 = 0; ok && k0 < a.K1; k0 += 16) load_xw1(t + gridDim.x, k0);
+        for (int k0 = 0; ok && k0 < a.H2; k0 += kWsHChunk) load_w3_chunk(k0, min(kWsHChunk, a.H2 - k0));
       }
       // every copy this thread started has landed before the CTA exits (bounded waits; all have on
       // the normal path, where the MMA warp consumed them)
       volatile int never = 0;
       ws_wait(bar(WB_W2), 0u, a.err, &never);
-      if (nx > 0) ws_wait(bar(WB_XFULL), (nx - 1u) & 1u, a.err, &never);
       for (int s = 0; s < ns; ++s)
         if (armed[s] > 0) ws_wait(bar(WB_WFULL + s), (uint32_t)(armed[s] - 1) & 1u, a.err, &never);
     }
   } else if (warp == kWsEpiWarps + 1) {
     // ---- MMA issuer: L1(first); per tile t: L2(t) chunk by chunk, L1(next), L3(t) chunk by chunk ----
     if (lane == 0) {
-      uint32_t xph = 0u, a1f = 1u, a2f = 1u, r = 0u, v = 0u;
+      uint32_t a1f = 1u, a2f = 1u, r = 0u, v = 0u;
       const uint32_t id1 = idesc_bf16(kBM, a.H1), id2 = idesc_bf16(kBM, a.H2), id3 = idesc_bf16(kBM, a.NO);
       bool ok = ws_wait(bar(WB_W2), 0u, a.err, aborted);
       auto layer1 = [&]() {
         ok = ok && ws_wait(bar(WB_A1FREE), a1f, a.err, aborted);
         a1f ^= 1u;
-        ok = ok && ws_wait(bar(WB_XFULL), xph, a.err, aborted);
-        xph ^= 1u;
-        for (int s = 0; ok && s < a.K1 / 16; ++s) {
+        for (int s = 0; ok && s < a.K1 / 16; ++s) {  // one ring entry per K step: X slab, W1 slab
           const uint32_t rs = r % (uint32_t)ns;
           ok = ws_wait(bar(WB_WFULL + rs), (r / ns) & 1u, a.err, aborted);
           if (!ok) break;
           asm volatile("tcgen05.fence::after_thread_sync;");
-          ws_mma(tm, sdesc(aX + (uint32_t)(s * 2 * kBM * 16), kBM * 16, 128),
-                 sdesc(aW + rs * (uint32_t)slotb, (uint32_t)(a.H1 * 16), 128), id1, s > 0 ? 1u : 0u);
+          const uint32_t e0 = aW + rs * (uint32_t)slotb;
+          ws_mma(tm, sdesc(e0, kBM * 16, 128), sdesc(e0 + (uint32_t)kWsXSlab, (uint32_t)(a.H1 * 16), 128), id1,
+                 s > 0 ? 1u : 0u);
           ws_commit(bar(WB_WFREE + rs));
           ++r;
         }
-        if (ok) {
-          ws_commit(bar(WB_XFREE));
-          ws_commit(bar(WB_A1FULL));
-        }
+        if (ok) ws_commit(bar(WB_A1FULL));
       };
       int t = blockIdx.x;
       if (ok && t < ntiles) layer1();
@@ -1010,16 +1013,16 @@ __global__ void __launch_bounds__(kWsThreads, 1)
           ok = ws_wait(bar(WB_HFULL + hs), (v >> 1) & 1u, a.err, aborted);
           if (!ok) break;
           const int w = min(kWsHChunk, a.H2 - c);
-          for (int s = 0; ok && s < w / 16; ++s) {
-            const uint32_t rs = r % (uint32_t)ns;
-            ok = ws_wait(bar(WB_WFULL + rs), (r / ns) & 1u, a.err, aborted);
-            if (!ok) break;
-            asm volatile("tcgen05.fence::after_thread_sync;");
+          const uint32_t rs = r % (uint32_t)ns;  // the chunk's W3 columns: one ring entry
+          ok = ws_wait(bar(WB_WFULL + rs), (r / ns) & 1u, a.err, aborted);
+          if (!ok) break;
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          for (int s = 0; s < w / 16; ++s)
             ws_mma(tm + 256u, sdesc(aH + hs * kWsHSlot + (uint32_t)(s * 2 * kBM * 16), kBM * 16, 128),
-                   sdesc(aW + rs * (uint32_t)slotb, (uint32_t)(a.NO * 16), 128), id3, (c > 0 || s > 0) ? 1u : 0u);
-            ws_commit(bar(WB_WFREE + rs));
-            ++r;
-          }
+                   sdesc(aW + rs * (uint32_t)slotb + (uint32_t)(s * 2 * a.NO * 16), (uint32_t)(a.NO * 16), 128), id3,
+                   (c > 0 || s > 0) ? 1u : 0u);
+          ws_commit(bar(WB_WFREE + rs));
+          ++r;
           ws_commit(bar(WB_HFREE + hs));
           ++v;
         }
