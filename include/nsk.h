@@ -344,11 +344,14 @@ int nsk_batch_step(nsk_batch* batch, int nsteps, double cfl, double* step_ms, do
  * the cooperative persistent kernel, 0 for one launch per phase covering all
  * instances, 2 for each instance's own stage launches one after another in the
  * captured graph: the schedule of choice when every instance fills the GPU by
- * itself; there fused_face may also be 2, the lean stage, or 4, the line
- * kernels for the instances they apply to) and the autotuner over all sixteen
- * schedules (times one residual of the whole batch under each; the instances'
+ * itself; there fused_face may also be 2, the lean stage, 4, the line kernels
+ * for the instances they apply to, or 5, each instance's own schedule, as set
+ * by nsk_set_schedule or nsk_autotune on its context: tpb and fused_face 0, 1
+ * or 4, the other schedules running as the separate face pass, and tpb ignored)
+ * and the autotuner, which first autotunes every instance's context, then times
+ * one residual of the whole batch under each batch schedule (the instances'
  * states are not modified). Returns NSK_ERR_ARG for tpb not 128 or 256,
- * persistent outside 0..2, fused_face outside 0..4, 3, or 2 or 4 with
+ * persistent outside 0..2, fused_face outside 0..5, 3, or 2, 4 or 5 with
  * persistent other than 2. */
 int nsk_batch_set_schedule(nsk_batch* batch, int tpb, int fused_face, int persistent);
 int nsk_batch_get_schedule(nsk_batch* batch, int* tpb, int* fused_face, int* persistent);

@@ -46,6 +46,7 @@ struct nsk_batch {
   std::vector<BatchInst> h_inst[2];  // per tpb choice
   cudaGraphExec_t graph;
   int graph_tpb, graph_fused, graph_dtmode, graph_persistent;
+  unsigned long long graph_inst_sched;  // the instances' own schedules the graph was captured with
   double graph_cfl;
   bool no_graph;          // capture or instantiation unavailable: stages launched directly
   long long launches;
@@ -458,13 +459,18 @@ int launch_stamp(nsk_batch* bt, unsigned long long* slot, int n) {
 // instance schedule: every instance's own stage kernels, one instance after another; with
 // stamps (the last stage of a step whose latencies are measured) each instance's completion
 // is stamped right after its last kernel
+// fused 5: each instance's own schedule (its tpb and fused_face; the lean and single-block schedules
+// run as the separate face pass there)
+int inst_fused(const nsk_ctx* c) { return (c->fused_face == 1 || c->fused_face == 4) ? c->fused_face : 0; }
 int launch_instances(nsk_batch* bt, int mode, double A, double B, int tpb, int fused, int traces,
                      bool stamps = false) {
   for (int i = 0; i < bt->n; ++i) {
     nsk_ctx* c = bt->inst[i];
-    NskLaunch l = {mode, c->rbuf, A, B, c->b.dt, 0.0, nullptr, tpb, fused};
-    l.traces_ready = traces & 1;
-    l.utr_next = (traces & 2) ? c->b.Utr : nullptr;  // separate face schedule: written in place
+    const int fi = fused == 5 ? inst_fused(c) : fused;
+    const int tr = fi == 1 ? 0 : traces;  // the fused volume phase prolongs every stage
+    NskLaunch l = {mode, c->rbuf, A, B, c->b.dt, 0.0, nullptr, fused == 5 ? c->tpb : tpb, fi};
+    l.traces_ready = tr & 1;
+    l.utr_next = (tr & 2) ? c->b.Utr : nullptr;  // separate face schedule: written in place
     const int r = nsk_launch_stage_d3(c->p, c->np, c->precision == NSK_FP32_MIXED, c->b, l, bt->stream);
     if (r < 0) return r;
     bt->launches += r;
@@ -503,12 +509,22 @@ int launch_instances_lean(nsk_batch* bt, int mode, double A, double B, int tpb, 
   return NSK_OK;
 }
 
+// the instances' schedules as one number (tpb and effective fused_face of each, in order)
+unsigned long long inst_schedules(const nsk_batch* bt) {
+  unsigned long long h = 1469598103934665603ull;  // FNV-1a over the pairs
+  for (const nsk_ctx* c : bt->inst) {
+    h = (h ^ (unsigned long long)(c->tpb == 128 ? 1 : 2)) * 1099511628211ull;
+    h = (h ^ (unsigned long long)inst_fused(c)) * 1099511628211ull;
+  }
+  return h;
+}
+
 // one stage of the whole batch under a schedule (persistent 1: one cooperative launch; 0: one
 // launch per phase; 2: every instance's own launches)
 // trace flags of every stage of a step under the separate face schedule: traces come from the
 // previous stage's volume phase (the step starts from traces prolonged before the first step)
 // (the line schedule, fused_face 4, is a separate face schedule)
-int step_traces(int fused) { return (fused == 0 || fused == 4) ? 3 : 0; }
+int step_traces(int fused) { return (fused == 0 || fused == 4 || fused == 5) ? 3 : 0; }
 
 // stamps: the last stage of a step whose per-instance latencies are measured (each instance's
 // completion stamped after its last kernel; one launch for all instances stamps them together)
@@ -676,7 +692,7 @@ int nsk_batch_create(nsk_batch** out, int n, nsk_ctx* const* instances) {
 }
 
 int nsk_batch_set_schedule(nsk_batch* bt, int tpb, int fused_face, int persistent) {
-  if (!bt || (tpb != 128 && tpb != 256) || persistent < 0 || persistent > 2 || fused_face < 0 || fused_face > 4 ||
+  if (!bt || (tpb != 128 && tpb != 256) || persistent < 0 || persistent > 2 || fused_face < 0 || fused_face > 5 ||
       fused_face == 3 || (fused_face >= 2 && persistent != 2))
     return NSK_ERR_ARG;
   bt->tpb = tpb;
@@ -698,6 +714,11 @@ int nsk_batch_autotune(nsk_batch* bt, int* tpb_out, int* fused_out, int* persist
   if (!bt) return NSK_ERR_ARG;
   for (nsk_ctx* c : bt->inst)
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return NSK_ERR_CUDA;
+  // every instance's own schedule first (the candidate "each instance's own schedule")
+  for (nsk_ctx* c : bt->inst) {
+    const int r = nsk_autotune(c, nullptr, nullptr, nullptr);
+    if (r) return r;
+  }
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return NSK_ERR_CUDA;
   double best = 1e300;
@@ -705,8 +726,10 @@ int nsk_batch_autotune(nsk_batch* bt, int* tpb_out, int* fused_out, int* persist
   const int tpbs[2] = {128, 256};
   for (int per = 0; per < 3 && st == NSK_OK; ++per)
     for (int ti = 0; ti < 2 && st == NSK_OK; ++ti)
-      for (int fi = 0; fi < (per == 2 ? 4 : 2) && st == NSK_OK; ++fi) {
-        const int f = fi == 3 ? 4 : fi;  // instance schedule: separate, fused, lean, line
+      for (int fi = 0; fi < (per == 2 ? 5 : 2) && st == NSK_OK; ++fi) {
+        // instance schedule: separate, fused, lean, line, and each instance's own (tuned above)
+        const int f = fi == 3 ? 4 : (fi == 4 ? 5 : fi);
+        if (f == 5 && ti == 1) continue;  // the instances' own block sizes: one timing
         // warm-up with a prolongation pass (residual: state untouched), then time the stage as a
         // step runs it (rewriting the traces of the unchanged state leaves them as they are; the
         // lean stage as a middle stage of a step: traces read from the trace buffer, the next
@@ -764,7 +787,7 @@ int nsk_batch_step(nsk_batch* bt, int nsteps, double cfl, double* step_ms, doubl
   if (!bt->no_graph &&
       (!bt->graph || bt->graph_tpb != bt->tpb || bt->graph_fused != bt->fused || bt->graph_dtmode != dtmode ||
        bt->graph_persistent != bt->persistent || (dtmode && bt->graph_cfl != cfl) ||
-       bt->graph_stamps != (int)stamps)) {
+       bt->graph_stamps != (int)stamps || (bt->fused == 5 && bt->graph_inst_sched != inst_schedules(bt)))) {
     destroy_graph(bt);
     cudaGraph_t g;
     if (cudaStreamBeginCapture(bt->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return NSK_ERR_CUDA;
@@ -789,6 +812,7 @@ int nsk_batch_step(nsk_batch* bt, int nsteps, double cfl, double* step_ms, doubl
     bt->graph_persistent = bt->persistent;
     bt->graph_cfl = cfl;
     bt->graph_stamps = (int)stamps;
+    bt->graph_inst_sched = inst_schedules(bt);
   }
   if (nsteps > 0 && step_traces(bt->fused)) {  // the traces of the current states, for the first stage
     const int r = launch_prolong(bt, bt->tpb);

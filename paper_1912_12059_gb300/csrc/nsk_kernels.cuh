@@ -957,7 +957,7 @@ template <typename R, int D, int NP>
 __device__ __forceinline__ void volume_node_fluxes(const NskParams& p, const R* u, const R (&tau)[D][D],
                                                    const R* gc, R* sf, const int le, const int n) {
   using S = Shape<D, NP>;
-  constexpr int NPE = S::NPE, NW = S::NW, NV = S::NV;
+  constexpr int NPE = S::NPE, NV = S::NV;
   const auto& t = TabSel<R>::get(p);
   R inv, pa;
   if constexpr (TraceComps<R>::extra > 0) {  // FP64: one division for 1/rho and 1/(3 - rho)
@@ -992,7 +992,7 @@ __device__ __forceinline__ void volume_residual_update(const NskParams& p, const
                                                        R* __restrict__ Rout, const int g, const int le,
                                                        const int n) {
   using S = Shape<D, NP>;
-  constexpr int NPE = S::NPE, NFN = S::NFN, NW = S::NW, NV = S::NV, NF = S::NF;
+  constexpr int NPE = S::NPE, NFN = S::NFN, NV = S::NV, NF = S::NF;
   const auto& t = TabSel<R>::get(p);
   const size_t nn = (size_t)p.nne;  // distance between the planes of two nodal variables
   // res_v = sum_k [ sum_j dk[i][j] F_k(j) - F*_{k,+} lpk[i] + F*_{k,-} lmk[i] ]  (2/h_k folded in),

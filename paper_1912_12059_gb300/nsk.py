@@ -499,7 +499,8 @@ class Batch:
     def set_schedule(self, tpb=256, fused_face=False, persistent=1):
         """persistent: 1 cooperative persistent kernel, 0 one launch per phase, 2 each instance's
         own stage launches (True/False map to 1/0); fused_face 0 or 1, or with the instance
-        schedule also 2 (the lean stage) or 4 (the line kernels where they apply)."""
+        schedule also 2 (the lean stage), 4 (the line kernels where they apply) or 5 (each
+        instance's own schedule; tpb is then ignored)."""
         _check(load_library().nsk_batch_set_schedule(self.h, tpb, int(fused_face), int(persistent)),
                "nsk_batch_set_schedule")
 

@@ -116,9 +116,12 @@ def test_batch_equals_solo_runs(gpu, precision, adaptive):
     for s, U in inst:
         s.set_state(U)
         s.compute_dt(0.5)
+    # the instances' own schedules, used by the batch schedule fused_face = 5
+    for (s, _), sched in zip(inst, ((128, 4), (256, 1), (256, 0), (128, 1))):
+        s.set_schedule(*sched)
     b = nsk.Batch([s for s, _ in inst])
     for tpb, fused, persistent in ((256, True, 1), (128, False, 1), (256, False, 0), (128, True, 0), (256, False, 2),
-                                   (128, True, 2), (256, 2, 2), (128, 2, 2), (256, 4, 2), (128, 4, 2)):
+                                   (128, True, 2), (256, 2, 2), (128, 2, 2), (256, 4, 2), (128, 4, 2), (256, 5, 2)):
         for s, U in inst:
             s.set_state(U)
             s.compute_dt(0.5)
@@ -173,7 +176,7 @@ def test_batch_autotune_graph_and_launch_count(gpu):
     b = nsk.Batch([s for s, _ in inst])
     tpb, fused, persistent, ms = b.autotune()
     assert tpb in (128, 256) and persistent in (0, 1, 2) and ms > 0 and b.get_schedule() == (tpb, fused, persistent)
-    assert fused in (0, 1) or (fused in (2, 4) and persistent == 2)
+    assert fused in (0, 1) or (fused in (2, 4, 5) and persistent == 2)
     # separate face schedule: one prolongation launch per call, then per stage the persistent
     # kernel, or lifting, face and volume launches (the volume phase writes the next traces)
     for persistent, per_stage in ((1, 1), (0, 3), (2, 3 * len(inst))):
@@ -200,6 +203,8 @@ def test_batch_autotune_graph_and_launch_count(gpu):
         b.set_schedule(256, 2, 1)  # the lean stage runs under the instance schedule only
     with pytest.raises(nsk.NskError):
         b.set_schedule(256, 4, 0)  # so do the line kernels
+    with pytest.raises(nsk.NskError):
+        b.set_schedule(256, 5, 1)  # and the instances' own schedules
     b.close()
     for s, _ in inst:
         s.close()
