@@ -22,8 +22,8 @@ LIB = PKG / "libnsk.so"
 BUILD_CHECK = PKG / "_build_check"
 LIB_CHECK = PKG / "libnsk_check.so"
 
-SOURCES = ["nsk_api.cu", "nsk_aux.cu", "nsk_dg1.cu", "nsk_dg2.cu", "nsk_dg3.cu", "nsk_batch.cu", "nsk_mlp.cu",
-           "nsk_orig.cu", "nsk_fv.cu", "nsk_implicit.cu"]
+SOURCES = ["nsk_api.cu", "nsk_aux.cu", "nsk_dg1.cu", "nsk_dg2.cu", "nsk_dg3.cu", "nsk_dg3f.cu", "nsk_batch.cu",
+           "nsk_mlp.cu", "nsk_orig.cu", "nsk_fv.cu", "nsk_implicit.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

@@ -1831,6 +1831,19 @@ int launch_stage_np(const NskParams& p, int np, bool fp32, const NskBuffers& b, 
   }
 }
 
+// the stage launches of one precision (a translation unit per precision builds in parallel)
+template <typename R, int D>
+int launch_stage_np_r(const NskParams& p, int np, const NskBuffers& b, const NskLaunch& l, cudaStream_t s) {
+  switch (np) {
+    case 2: return launch_stage<R, D, 2>(p, b, l, s);
+    case 3: return launch_stage<R, D, 3>(p, b, l, s);
+    case 4: return launch_stage<R, D, 4>(p, b, l, s);
+    case 5: return launch_stage<R, D, 5>(p, b, l, s);
+    case 6: return launch_stage<R, D, 6>(p, b, l, s);
+    default: return NSK_ERR_ARG;
+  }
+}
+
 // shared memory the single-block schedule needs for a mesh (0 when N is not compiled here)
 template <typename R, int D, int NP>
 size_t block_bytes_t(const NskParams& p) {
@@ -1850,6 +1863,31 @@ int launch_block_t(const NskParams& p, const NskBuffers& b, int mode, const NskL
   k_block_steps<R, D, NP, G><<<1, G * Shape<D, NP>::NPE, bytes, s>>>(p, (R*)b.U, (R*)b.K, (R*)Rout, mode, coef,
                                                                         (R)dt, nsteps, b.err);
   return cudaGetLastError() == cudaSuccess ? 1 : NSK_ERR_CUDA;
+}
+
+// the single-block schedule of one precision
+template <typename R, int D>
+size_t block_bytes_np_r(const NskParams& p, int np) {
+  switch (np) {
+    case 2: return block_bytes_t<R, D, 2>(p);
+    case 3: return block_bytes_t<R, D, 3>(p);
+    case 4: return block_bytes_t<R, D, 4>(p);
+    case 5: return block_bytes_t<R, D, 5>(p);
+    case 6: return block_bytes_t<R, D, 6>(p);
+    default: return (size_t)-1;
+  }
+}
+template <typename R, int D>
+int launch_block_np_r(const NskParams& p, int np, const NskBuffers& b, int mode, const NskLsrkCoef& coef, double dt,
+                      int nsteps, void* Rout, cudaStream_t s) {
+  switch (np) {
+    case 2: return launch_block_t<R, D, 2>(p, b, mode, coef, dt, nsteps, Rout, s);
+    case 3: return launch_block_t<R, D, 3>(p, b, mode, coef, dt, nsteps, Rout, s);
+    case 4: return launch_block_t<R, D, 4>(p, b, mode, coef, dt, nsteps, Rout, s);
+    case 5: return launch_block_t<R, D, 5>(p, b, mode, coef, dt, nsteps, Rout, s);
+    case 6: return launch_block_t<R, D, 6>(p, b, mode, coef, dt, nsteps, Rout, s);
+    default: return NSK_ERR_ARG;
+  }
 }
 
 template <int D>
