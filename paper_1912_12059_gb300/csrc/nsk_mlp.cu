@@ -623,8 +623,67 @@ __global__ void __launch_bounds__(G * nsk::Shape<D, NP>::NPE)
   }
 }
 
+// the same for FP32 3D elements with N = 3, one thread per x-line of 4 nodes (16 per element,
+// G elements per block): 16-byte loads and stores, the x-face traces from the thread's own line,
+// the y- and z-face traces four face nodes per thread from the staged c (same arithmetic)
+template <int G>
+__global__ void __launch_bounds__(G * 16)
+    k_closure_apply_line(const NskParams p, float* __restrict__ U, const float* __restrict__ Y, const float s,
+                         float* __restrict__ Utr) {
+  constexpr int NPE = 64, NFN = 16;
+  __shared__ __align__(16) float sc[G * NPE];
+  const int le = threadIdx.x >> 4, t = threadIdx.x & 15;
+  const int e = blockIdx.x * G + le;
+  const bool valid = e < p.E;
+  const size_t nn = (size_t)p.nne;
+  const int g0 = e * NPE + 4 * t;
+  const auto& T = TabSel<float>::get(p);
+  float* o = Utr + (size_t)4 * 6 * p.nfe + (size_t)e * NFN;  // the c plane of the traces
+  float cv[4];
+  if (valid) {
+    const float4 r = *reinterpret_cast<const float4*>(U + g0);
+    const float4 y = *reinterpret_cast<const float4*>(Y + g0);
+    cv[0] = r.x + s * y.x;
+    cv[1] = r.y + s * y.y;
+    cv[2] = r.z + s * y.z;
+    cv[3] = r.w + s * y.w;
+    const float4 c4 = make_float4(cv[0], cv[1], cv[2], cv[3]);
+    *reinterpret_cast<float4*>(U + 4 * nn + g0) = c4;
+    *reinterpret_cast<float4*>(sc + le * NPE + 4 * t) = c4;
+#pragma unroll
+    for (int sd = 0; sd < 2; ++sd) {  // x faces at face node t
+      const float* L = sd ? T.lp : T.lm;
+      float acc = 0.f;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) acc = fmaf(L[i], cv[i], acc);
+      o[(size_t)sd * p.nfe + t] = acc;
+    }
+  }
+  __syncthreads();
+  if (valid) {  // y and z faces: four face nodes of one slot per thread
+    const int slot = 2 + (t >> 2), k = slot >> 1, g = t & 3;
+    const float* L = (slot & 1) ? T.lp : T.lm;
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) {
+      const float4 ln = *reinterpret_cast<const float4*>(sc + le * NPE + 4 * (k == 1 ? jj + 4 * g : g + 4 * jj));
+      acc[0] = fmaf(L[jj], ln.x, acc[0]);
+      acc[1] = fmaf(L[jj], ln.y, acc[1]);
+      acc[2] = fmaf(L[jj], ln.z, acc[2]);
+      acc[3] = fmaf(L[jj], ln.w, acc[3]);
+    }
+    *reinterpret_cast<float4*>(o + (size_t)slot * p.nfe + 4 * g) = make_float4(acc[0], acc[1], acc[2], acc[3]);
+  }
+}
+
 template <typename R, int D, int NP>
 int launch_apply_tr(const nsk_ctx* c, float s, void* utr) {
+  if constexpr (std::is_same<R, float>::value && D == 3 && NP == 4) {
+    constexpr int GL = 16;
+    k_closure_apply_line<GL><<<(unsigned)((c->E + GL - 1) / GL), GL * 16, 0, c->stream>>>(c->p, (float*)c->b.U, c->cl_Y,
+                                                                                         s, (float*)utr);
+    return cudaGetLastError() == cudaSuccess ? NSK_OK : NSK_ERR_CUDA;
+  }
   constexpr int G = nsk::group_for<D, NP>(256);
   k_closure_apply_tr<R, D, NP, G><<<(unsigned)((c->E + G - 1) / G), G * nsk::Shape<D, NP>::NPE, 0, c->stream>>>(
       c->p, (R*)c->b.U, c->cl_Y, s, (R*)utr);
