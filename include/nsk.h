@@ -333,18 +333,19 @@ int nsk_batch_create(nsk_batch** out, int n, nsk_ctx* const* instances);
  * ([step][instance], ms): the time from the start of the step to the moment
  * that instance's new state is complete in device memory, from the GPU's
  * global timer read by one-thread kernels at the start of the step and right
- * after the launch that finishes the instance (the instance schedule
- * finishes instances one after another; the single-launch schedules finish
- * all of them with their last launch). The stamps add n + 1 tiny launches
+ * after the launch that finishes the instance (the instance schedule runs
+ * instance i on stream i mod 4 of four streams forked from the batch's stream
+ * and joined back after every stage, and finishes the instances of one stream
+ * one after another; the single-launch schedules finish all of them with their
+ * last launch). The stamps add n + 1 tiny launches
  * to a measured step (a separately captured graph) and a device-to-device
  * copy of n + 1 words after it; the batch keeps their buffers until it is
  * destroyed. Returns as nsk_step. */
 int nsk_batch_step(nsk_batch* batch, int nsteps, double cfl, double* step_ms, double* per_instance_latency_ms);
 /* Batch schedule (tpb and fused_face as for a context; persistent = 1 for
  * the cooperative persistent kernel, 0 for one launch per phase covering all
- * instances, 2 for each instance's own stage launches one after another in the
- * captured graph: the schedule of choice when every instance fills the GPU by
- * itself; there fused_face may also be 2, the lean stage, 4, the line kernels
+ * instances, 2 for each instance's own stage launches in the captured graph,
+ * on four streams (small instances run side by side); there fused_face may also be 2, the lean stage, 4, the line kernels
  * for the instances they apply to, or 5, each instance's own schedule, as set
  * by nsk_set_schedule or nsk_autotune on its context: tpb and fused_face 0, 1
  * or 4, the other schedules running as the separate face pass, and tpb ignored)

@@ -65,6 +65,12 @@ struct nsk_batch {
   unsigned long long* d_hist;
   long long hist_cap;      // steps the history holds
   int graph_stamps;        // the captured graph carries the stamp kernels
+  // instance schedule: instance i launches on aux[i % naux], forked from and joined back to stream
+  // around every stage (small instances that cannot fill the GPU alone run side by side)
+  static constexpr int kAux = 4;
+  int naux;
+  cudaStream_t aux[kAux];
+  cudaEvent_t ev_fork, ev_join[kAux];
 };
 
 namespace {
@@ -450,13 +456,31 @@ __global__ void k_stamp(unsigned long long* __restrict__ slot, const int n) {
   if (i < n) slot[i] = nsk::global_ns();
 }
 
-int launch_stamp(nsk_batch* bt, unsigned long long* slot, int n) {
-  k_stamp<<<(n + 255) / 256, 256, 0, bt->stream>>>(slot, n);
+int launch_stamp(nsk_batch* bt, unsigned long long* slot, int n, cudaStream_t s = nullptr) {
+  k_stamp<<<(n + 255) / 256, 256, 0, s ? s : bt->stream>>>(slot, n);
   ++bt->launches;
   return cudaGetLastError() == cudaSuccess ? NSK_OK : NSK_ERR_CUDA;
 }
 
-// instance schedule: every instance's own stage kernels, one instance after another; with
+// the instance schedule's streams: fork from the batch stream before a stage, join after it
+int fork_aux(nsk_batch* bt) {
+  if (bt->naux < 2) return NSK_OK;
+  if (cudaEventRecord(bt->ev_fork, bt->stream) != cudaSuccess) return NSK_ERR_CUDA;
+  for (int j = 0; j < bt->naux; ++j)
+    if (cudaStreamWaitEvent(bt->aux[j], bt->ev_fork, 0) != cudaSuccess) return NSK_ERR_CUDA;
+  return NSK_OK;
+}
+int join_aux(nsk_batch* bt) {
+  if (bt->naux < 2) return NSK_OK;
+  for (int j = 0; j < bt->naux; ++j)
+    if (cudaEventRecord(bt->ev_join[j], bt->aux[j]) != cudaSuccess ||
+        cudaStreamWaitEvent(bt->stream, bt->ev_join[j], 0) != cudaSuccess)
+      return NSK_ERR_CUDA;
+  return NSK_OK;
+}
+cudaStream_t inst_stream(const nsk_batch* bt, int i) { return bt->naux < 2 ? bt->stream : bt->aux[i % bt->naux]; }
+
+// instance schedule: every instance's own stage kernels, instance i on stream i mod naux; with
 // stamps (the last stage of a step whose latencies are measured) each instance's completion
 // is stamped right after its last kernel
 // fused 5: each instance's own schedule (its tpb and fused_face; the lean and single-block schedules
@@ -471,11 +495,11 @@ int launch_instances(nsk_batch* bt, int mode, double A, double B, int tpb, int f
     NskLaunch l = {mode, c->rbuf, A, B, c->b.dt, 0.0, nullptr, fused == 5 ? c->tpb : tpb, fi};
     l.traces_ready = tr & 1;
     l.utr_next = (tr & 2) ? c->b.Utr : nullptr;  // separate face schedule: written in place
-    const int r = nsk_launch_stage_d3(c->p, c->np, c->precision == NSK_FP32_MIXED, c->b, l, bt->stream);
+    const int r = nsk_launch_stage_d3(c->p, c->np, c->precision == NSK_FP32_MIXED, c->b, l, inst_stream(bt, i));
     if (r < 0) return r;
     bt->launches += r;
     if (stamps) {
-      const int st = launch_stamp(bt, bt->d_stamp + 1 + i, 1);
+      const int st = launch_stamp(bt, bt->d_stamp + 1 + i, 1, inst_stream(bt, i));
       if (st) return st;
     }
   }
@@ -498,11 +522,11 @@ int launch_instances_lean(nsk_batch* bt, int mode, double A, double B, int tpb, 
       l.traces_ready = stage > 0;
       l.utr_next = stage < 4 ? bufs[(stage + 1) & 1] : nullptr;
     }
-    const int r = nsk_launch_stage_d3(c->p, c->np, c->precision == NSK_FP32_MIXED, b, l, bt->stream);
+    const int r = nsk_launch_stage_d3(c->p, c->np, c->precision == NSK_FP32_MIXED, b, l, inst_stream(bt, i));
     if (r < 0) return r;
     bt->launches += r;
     if (stamps) {
-      const int st = launch_stamp(bt, bt->d_stamp + 1 + i, 1);
+      const int st = launch_stamp(bt, bt->d_stamp + 1 + i, 1, inst_stream(bt, i));
       if (st) return st;
     }
   }
@@ -530,9 +554,17 @@ int step_traces(int fused) { return (fused == 0 || fused == 4 || fused == 5) ? 3
 // completion stamped after its last kernel; one launch for all instances stamps them together)
 int launch_batch(nsk_batch* bt, int mode, double A, double B, int tpb, int fused, int persistent, int traces,
                  bool stamps = false, int stage = -1) {
-  if (persistent == 2 && fused == 2) return launch_instances_lean(bt, mode, A, B, tpb, stage, stamps);
+  if (persistent == 2) {  // the instance schedule, forked onto the auxiliary streams
+    int r = fork_aux(bt);
+    if (r) return r;
+    if (fused == 2)
+      r = launch_instances_lean(bt, mode, A, B, tpb, stage, stamps);
+    else
+      r = launch_instances(bt, mode, A, B, tpb, fused, fused == 1 ? 0 : traces, stamps);
+    const int j = join_aux(bt);
+    return r ? r : j;
+  }
   if (fused == 1) traces = 0;  // the fused volume phase reads the traces: they are prolonged every stage
-  if (persistent == 2) return launch_instances(bt, mode, A, B, tpb, fused, traces, stamps);
   const int r = persistent ? launch_persistent(bt, mode, A, B, tpb, fused, traces)
                            : launch_phases(bt, mode, A, B, tpb, fused, traces);
   if (r || !stamps) return r;
@@ -654,7 +686,13 @@ int nsk_batch_create(nsk_batch** out, int n, nsk_ctx* const* instances) {
       }
     }
   }
-  if (cudaStreamCreateWithFlags(&bt->stream, cudaStreamNonBlocking) != cudaSuccess ||
+  bt->naux = n < nsk_batch::kAux ? n : nsk_batch::kAux;
+  if (bt->naux < 2) bt->naux = 0;
+  bool aux_ok = bt->naux == 0 || cudaEventCreateWithFlags(&bt->ev_fork, cudaEventDisableTiming) == cudaSuccess;
+  for (int j = 0; j < bt->naux && aux_ok; ++j)
+    aux_ok = cudaStreamCreateWithFlags(&bt->aux[j], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&bt->ev_join[j], cudaEventDisableTiming) == cudaSuccess;
+  if (!aux_ok || cudaStreamCreateWithFlags(&bt->stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaMalloc(&bt->d_pinst, 2 * sizeof(BatchInst) * n) != cudaSuccess ||
       cudaMalloc(&bt->d_inst, 2 * sizeof(BatchInst) * n) != cudaSuccess ||
       cudaMalloc(&bt->d_bar, 2 * sizeof(unsigned)) != cudaSuccess || cudaMalloc(&bt->d_err, sizeof(int)) != cudaSuccess) {
@@ -895,6 +933,11 @@ void nsk_batch_destroy(nsk_batch* bt) {
   if (bt->d_err) cudaFree(bt->d_err);
   if (bt->d_stamp) cudaFree(bt->d_stamp);
   if (bt->d_hist) cudaFree(bt->d_hist);
+  for (int j = 0; j < bt->naux; ++j) {
+    if (bt->aux[j]) cudaStreamDestroy(bt->aux[j]);
+    if (bt->ev_join[j]) cudaEventDestroy(bt->ev_join[j]);
+  }
+  if (bt->ev_fork) cudaEventDestroy(bt->ev_fork);
   if (bt->stream) cudaStreamDestroy(bt->stream);
   delete bt;
 }
