@@ -475,50 +475,114 @@ constexpr float kFeatScale = 0.5f;  // feature scale: density deviations within 
 // lo = bf16(v - hi) (columns [0, nf) and [nf, 2 nf)), so the tensor cores see about 16
 // significant bits of the input. The quasi-equilibrium c - rho is invariant under adding a
 // constant to rho, so the element mean itself is not an input.
-// element means of rho (one warp per element)
+// element means of rho, one thread per element (16-byte loads where the element's values fill
+// whole 16-byte units: many loads in flight per thread)
 template <typename R>
-__global__ void k_elem_mean(const long long E, const int npe, const R* __restrict__ U, float* __restrict__ mean) {
-  const long long e = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
+__global__ void __launch_bounds__(256) k_elem_mean(const long long E, const int npe, const R* __restrict__ U,
+                                                   float* __restrict__ mean) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= E) return;
+  const R* u = U + e * npe;
   float acc = 0.f;
-  for (int n = lane; n < npe; n += 32) acc += (float)U[e * npe + n];
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if (lane == 0) mean[e] = acc / (float)npe;
+  if (sizeof(R) == 4 && (npe & 3) == 0) {
+    const float4* u4 = reinterpret_cast<const float4*>(u);
+    for (int q = 0; q < npe / 4; ++q) {
+      const float4 v = u4[q];
+      acc += (v.x + v.y) + (v.z + v.w);
+    }
+  } else {
+    for (int n = 0; n < npe; ++n) acc += (float)u[n];
+  }
+  mean[e] = acc / (float)npe;
 }
 
-// one warp per element: lane f takes features f, f + 32, ... (no division per value; the face
-// neighbours from the element's Cartesian position)
+// four elements per warp (their loads issued together), lane f taking features f, f + 32, ... of
+// each (no division per value; the face neighbours from the element's Cartesian position)
+constexpr int kFeatEpw = 4;
 template <typename R, int D>
 __global__ void __launch_bounds__(256) k_closure_features(const NskParams p, const int npe, const R* __restrict__ U,
                                                           const float* __restrict__ mean_e,
                                                           __nv_bfloat16* __restrict__ X, const int nin_pad) {
-  const long long e = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long e0 = (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * kFeatEpw;
   const int lane = threadIdx.x & 31;
-  if (e >= p.E) return;
   const int nf = npe + 2 * D;
-  const float mean = mean_e[e];
-  const nsk::ElemIdx ex = nsk::elem_idx<D>(p, (int)e);
-  __nv_bfloat16* row = X + e * nin_pad;
-  for (int f = lane; f < nf; f += 32) {
-    float v;
-    if (f < npe) {
-      v = (float)U[e * npe + f] - mean;
-    } else {
-      const int j = f - npe;
-      v = mean_e[nsk::nbr_of(p, ex, j >> 1, (j & 1) ? 1 : -1)] - mean;
+#pragma unroll
+  for (int q = 0; q < kFeatEpw; ++q) {
+    const long long e = e0 + q;
+    if (e >= p.E) return;  // uniform over the warp
+    const float mean = mean_e[e];
+    const nsk::ElemIdx ex = nsk::elem_idx<D>(p, (int)e);
+    __nv_bfloat16* row = X + e * nin_pad;
+    for (int f = lane; f < nf; f += 32) {
+      float v;
+      if (f < npe) {
+        v = (float)U[e * npe + f] - mean;
+      } else {
+        const int j = f - npe;
+        v = mean_e[nsk::nbr_of(p, ex, j >> 1, (j & 1) ? 1 : -1)] - mean;
+      }
+      v /= kFeatScale;
+      const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+      row[f] = hi;
+      row[nf + f] = __float2bfloat16_rn(v - __bfloat162float(hi));
     }
-    v /= kFeatScale;
-    const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-    row[f] = hi;
-    row[nf + f] = __float2bfloat16_rn(v - __bfloat162float(hi));
+    for (int f = 2 * nf + lane; f < nin_pad; f += 32) row[f] = __float2bfloat16_rn(0.f);  // zero padding columns
   }
-  for (int f = 2 * nf + lane; f < nin_pad; f += 32) row[f] = __float2bfloat16_rn(0.f);  // zero padding columns
+}
+
+// FP32 3D elements with N = 3 (64 nodes, 70 features, rows of 144): one thread per element, its
+// 64 densities by 16-byte loads, the row built in registers and written with 16-byte stores
+__global__ void __launch_bounds__(128) k_closure_features64(const NskParams p, const float* __restrict__ U,
+                                                            const float* __restrict__ mean_e,
+                                                            __nv_bfloat16* __restrict__ X) {
+  constexpr int NPE = 64, NF = NPE + 6, PAD = 144;
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= p.E) return;
+  const float mean = mean_e[e];
+  const nsk::ElemIdx ex = nsk::elem_idx<3>(p, (int)e);
+  float v[NF];
+  const float4* u4 = reinterpret_cast<const float4*>(U + e * NPE);
+#pragma unroll
+  for (int q = 0; q < NPE / 4; ++q) {
+    const float4 t = u4[q];
+    v[4 * q] = t.x - mean;
+    v[4 * q + 1] = t.y - mean;
+    v[4 * q + 2] = t.z - mean;
+    v[4 * q + 3] = t.w - mean;
+  }
+#pragma unroll
+  for (int j = 0; j < 6; ++j) v[NPE + j] = mean_e[nsk::nbr_of(p, ex, j >> 1, (j & 1) ? 1 : -1)] - mean;
+  uint4* row = reinterpret_cast<uint4*>(X + e * PAD);
+#pragma unroll
+  for (int g = 0; g < PAD / 8; ++g) {
+    uint32_t w[4];
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      uint32_t pair = 0;
+#pragma unroll
+      for (int b = 0; b < 2; ++b) {
+        const int col = 8 * g + 2 * h + b;
+        __nv_bfloat16 o = __float2bfloat16_rn(0.f);
+        if (col < 2 * NF) {
+          const float s = v[col < NF ? col : col - NF] / kFeatScale;
+          const __nv_bfloat16 hi = __float2bfloat16_rn(s);
+          o = col < NF ? hi : __float2bfloat16_rn(s - __bfloat162float(hi));
+        }
+        pair |= (uint32_t)__bfloat16_as_ushort(o) << (16 * b);
+      }
+      w[h] = pair;
+    }
+    row[g] = make_uint4(w[0], w[1], w[2], w[3]);
+  }
 }
 
 template <typename R>
 int launch_features(const nsk_ctx* c, const R* U, const float* mean, __nv_bfloat16* X, int nin_pad) {
-  const unsigned g = nb(c->E * 32);
+  if (sizeof(R) == 4 && c->dim == 3 && c->npe == 64 && nin_pad == 144 && ((uintptr_t)X & 15u) == 0) {
+    k_closure_features64<<<(unsigned)((c->E + 127) / 128), 128, 0, c->stream>>>(c->p, (const float*)U, mean, X);
+    return cudaGetLastError() == cudaSuccess ? NSK_OK : NSK_ERR_CUDA;
+  }
+  const unsigned g = nb((c->E + kFeatEpw - 1) / kFeatEpw * 32);
   if (c->dim == 1)
     k_closure_features<R, 1><<<g, 256, 0, c->stream>>>(c->p, c->npe, U, mean, X, nin_pad);
   else if (c->dim == 2)
@@ -575,10 +639,10 @@ int closure_features(nsk_ctx* c, void* X) {
   float* mean = c->cl_mean;
   int st;
   if (c->precision == NSK_FP32_MIXED) {
-    k_elem_mean<float><<<nb(c->E * 32), 256, 0, c->stream>>>(c->E, c->npe, (const float*)c->b.U, mean);
+    k_elem_mean<float><<<nb(c->E), 256, 0, c->stream>>>(c->E, c->npe, (const float*)c->b.U, mean);
     st = launch_features<float>(c, (const float*)c->b.U, mean, (__nv_bfloat16*)X, nin_pad);
   } else {
-    k_elem_mean<double><<<nb(c->E * 32), 256, 0, c->stream>>>(c->E, c->npe, (const double*)c->b.U, mean);
+    k_elem_mean<double><<<nb(c->E), 256, 0, c->stream>>>(c->E, c->npe, (const double*)c->b.U, mean);
     st = launch_features<double>(c, (const double*)c->b.U, mean, (__nv_bfloat16*)X, nin_pad);
   }
   c->launches += 2;
