@@ -83,6 +83,16 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t
   return d;
 }
 
+// the same for a K-major operand in a swizzled layout (what a TMA box with that swizzle writes):
+// rows of 32 (kSw32) or 128 (kSw128) bytes along K, their 16-byte chunks permuted within each
+// group of 8 rows, groups sbo bytes apart; a K step inside a row is an offset of the start
+// address (the permutation follows the address bits, so the group base must be aligned to the
+// group size: 256 or 1024 bytes). The leading byte offset is unused (16 bytes, encoded 1).
+constexpr uint32_t kSw32 = 6u, kSw128 = 2u;  // layout type, descriptor bits 61-63
+__device__ __forceinline__ uint64_t sdesc_sw(uint32_t saddr, uint32_t sbo, uint32_t layout) {
+  return sdesc(saddr, 16u, sbo) | ((uint64_t)layout << 61);
+}
+
 // instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, shape M x N
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
@@ -114,14 +124,36 @@ __device__ __forceinline__ float fast_ex2(float x) {
 __device__ __forceinline__ float gelu(float x) {
   constexpr float kW = 0.84932180028801904f;   // sqrt(log2(e) / 2)
   constexpr float kP = 0.27273748087922250f;   // 0.3275911 / sqrt(log2(e))
-  const float w = x * kW;
+  // every product rounded on its own (no contraction), as gelu2 below repeats it
+  const float w = __fmul_rn(x, kW);
   const float aw = fabsf(w);
   const float t = fast_rcp(fmaf(kP, aw, 1.0f));
-  const float poly =
-      t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.061405429f, -1.453152027f), 1.421413741f), -0.284496736f), 0.254829592f);
-  const float erf_abs = fmaf(-poly, fast_ex2(-(w * w)), 1.0f);  // erf(|x| / sqrt 2)
-  const float h = 0.5f * x;
+  const float poly = __fmul_rn(
+      t, fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.061405429f, -1.453152027f), 1.421413741f), -0.284496736f), 0.254829592f));
+  const float erf_abs = fmaf(-poly, fast_ex2(-__fmul_rn(w, w)), 1.0f);  // erf(|x| / sqrt 2)
+  const float h = __fmul_rn(0.5f, x);
   return fmaf(h, copysignf(erf_abs, x), h);
+}
+// the same GELU on two values at once, operation for operation (the packed FP32 instructions round
+// each lane as the scalar ones do, so the results equal gelu's bit for bit): half the FP32
+// instructions of two scalar evaluations; the Horner coefficients are negated so that the
+// negation of the polynomial is exact and free
+__device__ __forceinline__ float2 f2s(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 gelu2(float2 x) {
+  const float2 w = __fmul2_rn(x, f2s(0.84932180028801904f));
+  const float2 aw = make_float2(fabsf(w.x), fabsf(w.y));
+  const float2 d = __ffma2_rn(f2s(0.27273748087922250f), aw, f2s(1.0f));
+  const float2 t = make_float2(fast_rcp(d.x), fast_rcp(d.y));
+  float2 pn = __ffma2_rn(t, f2s(-1.061405429f), f2s(1.453152027f));
+  pn = __ffma2_rn(t, pn, f2s(-1.421413741f));
+  pn = __ffma2_rn(t, pn, f2s(0.284496736f));
+  pn = __ffma2_rn(t, pn, f2s(-0.254829592f));
+  const float2 poly_neg = __fmul2_rn(t, pn);  // -poly of gelu
+  const float2 ww = __fmul2_rn(w, w);
+  const float2 e = make_float2(fast_ex2(-ww.x), fast_ex2(-ww.y));
+  const float2 erf_abs = __ffma2_rn(poly_neg, e, f2s(1.0f));
+  const float2 h = __fmul2_rn(x, f2s(0.5f));
+  return __ffma2_rn(h, make_float2(copysignf(erf_abs.x, x.x), copysignf(erf_abs.y, x.y)), h);
 }
 __device__ __forceinline__ float gelu_grad(float x) {
   return 0.5f * (1.0f + erff(x * 0.70710678118654752f)) + x * 0.3989422804014327f * __expf(-0.5f * x * x);
@@ -732,43 +764,57 @@ __global__ void __launch_bounds__(kFwThreads, 1) k_mlp_fwd3(const MlpFwdArgs a) 
 // Warp-specialised fused forward: the same network, the same MMAs in the same K order and the
 // same GELU and BF16 rounding as k_mlp_fwd3, with the stages overlapped:
 //  - operands arrive by TMA (cp.async.bulk.tensor, boxes 8 K columns wide that land directly in
-//    the K-major no-swizzle core-matrix layout below); one warp issues the loads, one warp the
-//    MMAs, and kWsEpiWarps warps run the epilogues;
+//    the K-major no-swizzle core-matrix layout below); one warp loads the row tiles and W1, one
+//    W2 and W3, one warp issues the MMAs of layers 2 and 3, one those of layer 1, and
+//    kWsEpiWarps warps run the epilogues; every role blocks only on its own barriers;
 //  - W2 stays resident; the row tile X and W1 stream together through a ring of entries, one
-//    16-column slab of each per layer-1 K step, and W3 in one entry per 64-column activation chunk;
+//    16-column slab of each per layer-1 K step, and W3 through a ring of two 64-column chunks;
 //  - a layer's activations are written in 64-column chunks into a two-slot ring, and the next
 //    layer's MMAs consume chunk c while the epilogue produces chunk c + 1;
 //  - layer 1 of the next tile accumulates in TMEM columns [0, H1) while the epilogue works on
 //    layer 2 ([256, 256 + H2)) and drains layer 3 ([256, 256 + NO), NO <= 64: inside layer 2's
-//    first chunk, which the epilogue has read before the first layer-3 MMA is issued).
-// Operand layout in shared memory (what one TMA box of 8 K columns x R rows writes, boxes side by
-// side along K): element (r, k) at (k / 8) R 16 + r 16 + (k % 8) 2 bytes, so core matrices
-// adjacent along K are R 16 bytes apart (the descriptor's leading byte offset) and along M or N
-// 128 bytes apart (its stride byte offset).
+//    first chunk, which the epilogue has read before the first layer-3 MMA is issued); the two
+//    MMA warps issue independently (disjoint accumulators; each commit tracks its own thread's
+//    MMAs), so that layer 1 of the next tile streams while layer 3 waits for activations;
+//  - the epilogue stages its layer-3 block in the activation slots (in bytes only its own warp
+//    writes there) and stores it 64 bytes per row, eight rows per warp instruction.
+// Operand layouts in shared memory, chosen for few TMA requests (one per box row): the row-tile
+// and W1 slabs are boxes of 16 K columns (32-byte rows, 32-byte swizzle), W2 and the W3 chunks
+// boxes of 64 K columns (128-byte rows, 128-byte swizzle, W2's boxes side by side along K); the
+// activation slots, written by the epilogue, are in the no-swizzle core-matrix layout: element
+// (r, k) at (k / 8) 128 16 + r 16 + (k % 8) 2 bytes, core matrices adjacent along K 2048 bytes
+// apart (the descriptor's leading byte offset) and along M 128 bytes apart (its stride offset).
 // ---------------------------------------------------------------------------
 constexpr int kWsEpiWarps = 16;                       // 4 per TMEM lane quarter
-constexpr int kWsThreads = (kWsEpiWarps + 2) * 32;    // + the TMA warp and the MMA warp
+constexpr int kWsThreads = (kWsEpiWarps + 4) * 32;    // + two TMA warps and two MMA warps
 constexpr int kWsHChunk = 64;                         // activation columns per ring slot
 constexpr int kWsHSlot = kBM * kWsHChunk * 2;         // bytes of one activation slot
 constexpr int kWsMaxRing = 6;
 constexpr int kWsXSlab = kBM * 16 * 2;                // bytes of a 16-column slab of the row tile
 
 struct FwdMaps {
-  CUtensorMap x, w1, w2, w3;  // X [M][ldx], W1 [H1][K1], W2 [H2][H1], W3 [NO][H2], boxes 8 x rows
+  // X [M][ldx] and W1 [H1][K1]: boxes of 16 columns x 128 / H1 rows, 32-byte swizzle; W2 [H2][H1]
+  // and W3 [NO][H2]: boxes of 64 columns x H2 / NO rows, 128-byte swizzle
+  CUtensorMap x, w1, w2, w3;
 };
 
-// a ring slot holds a 16-column slab of the row tile X with the matching W1 slab (H1 rows), or a W3
-// chunk (NO rows x one activation chunk of 64 columns)
-__host__ __device__ inline int ws_slot_bytes(const MlpFwdArgs& a) {
-  return kWsXSlab + a.H1 * 32 > a.NO * kWsHChunk * 2 ? kWsXSlab + a.H1 * 32 : a.NO * kWsHChunk * 2;
-}
-__host__ __device__ inline int ws_off_h(const MlpFwdArgs& a) { return fw_align(a.H2 * a.H1 * 2); }
+// shared memory: W2 [H2][H1] | two activation slots | ns row-tile/W1 entries | two W3 chunks |
+// b1 b2; a ring entry holds a 16-column slab of the row tile X with the matching W1 slab (H1
+// rows), a W3 chunk the NO rows of 64 columns of W3 (b3 is read from global memory)
+__host__ __device__ inline int ws_slot_bytes(const MlpFwdArgs& a) { return kWsXSlab + a.H1 * 32; }
+__host__ __device__ inline int ws_w3_slot_bytes(const MlpFwdArgs& a) { return a.NO * kWsHChunk * 2; }
+// W2 in boxes of 64 K columns (the last one zero-filled beyond H1)
+__host__ __device__ inline int ws_w2_bytes(const MlpFwdArgs& a) { return (a.H1 + 63) / 64 * a.H2 * 128; }
+__host__ __device__ inline int ws_off_h(const MlpFwdArgs& a) { return fw_align(ws_w2_bytes(a)); }
 __host__ __device__ inline int ws_off_w(const MlpFwdArgs& a) { return ws_off_h(a) + 2 * kWsHSlot; }
+__host__ __device__ inline int ws_off_w3(const MlpFwdArgs& a, int ns) {
+  return fw_align(ws_off_w(a) + ns * ws_slot_bytes(a));
+}
 __host__ __device__ inline int ws_off_bias(const MlpFwdArgs& a, int ns) {
-  return ws_off_w(a) + fw_align(ns * ws_slot_bytes(a));
+  return ws_off_w3(a, ns) + 2 * ws_w3_slot_bytes(a);
 }
 __host__ __device__ inline int ws_smem_bytes(const MlpFwdArgs& a, int ns) {
-  return ws_off_bias(a, ns) + (a.H1 + a.H2 + a.NO) * 4;
+  return ws_off_bias(a, ns) + (a.H1 + a.H2) * 4;
 }
 
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int c0, int c1, uint32_t bar) {
@@ -782,6 +828,16 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
 }
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+// whether the phase of parity `parity` of an mbarrier has completed (does not block)
+__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return done != 0;
 }
 __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
@@ -799,15 +855,7 @@ __device__ __forceinline__ void ws_commit(uint32_t bar) {
 // Wait for the phase of parity `parity` of an mbarrier, bounded in time; gives up early when
 // another role has already aborted (flag set), and sets the flag and the error word on a timeout.
 __device__ __forceinline__ bool ws_wait(uint32_t bar, uint32_t parity, int* err, volatile int* abort_flag) {
-  {  // the common case: the phase has completed; no clock read
-    uint32_t done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    if (done) return true;
-  }
+  if (mbar_test(bar, parity)) return true;  // the common case: the phase has completed; no clock read
   const unsigned long long t0 = tc_global_ns();
   while (true) {
     uint32_t done;
@@ -864,34 +912,48 @@ __device__ __forceinline__ void ws_gelu16(uint32_t taddr, uint32_t bias, unsigne
   tmem_ld16(taddr, v);
 #pragma unroll
   for (int g = 0; g < 2; ++g) {
-    __align__(16) __nv_bfloat16 h[8];
+    uint32_t pk[4];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) h[j] = __float2bfloat16_rn(gelu(__uint_as_float(v[g * 8 + j]) + b[g * 8 + j]));
-    *reinterpret_cast<uint4*>(slot + ((kk >> 3) + g) * (kBM * 16) + r * 16) = *reinterpret_cast<const uint4*>(h);
+    for (int j = 0; j < 4; ++j) {  // columns 8 g + 2 j, + 1: the same values as gelu(acc + b), paired
+      const int c = g * 8 + 2 * j;
+      const float2 y = gelu2(__fadd2_rn(make_float2(__uint_as_float(v[c]), __uint_as_float(v[c + 1])),
+                                        make_float2(b[c], b[c + 1])));
+      const __nv_bfloat162 hb = __floats2bfloat162_rn(y.x, y.y);
+      pk[j] = *reinterpret_cast<const uint32_t*>(&hb);
+    }
+    *reinterpret_cast<uint4*>(slot + ((kk >> 3) + g) * (kBM * 16) + r * 16) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
   }
 }
 
 // barrier indices in the kernel's array
 enum WsBar : int {
-  WB_W2 = 0, WB_A1FULL, WB_A1FREE, WB_A2FULL, WB_A2FREE, WB_A3FULL, WB_FINAL,
-  WB_HFULL, WB_HFREE = WB_HFULL + 2, WB_WFULL = WB_HFREE + 2, WB_WFREE = WB_WFULL + kWsMaxRing,
+  WB_W2 = 0, WB_A1FULL, WB_A1FREE, WB_A2FULL, WB_A2FREE, WB_A3FULL, WB_FINAL, WB_FINAL1,
+  WB_HFULL, WB_HFREE = WB_HFULL + 2, WB_3FULL = WB_HFREE + 2, WB_3FREE = WB_3FULL + 2,
+  WB_WFULL = WB_3FREE + 2, WB_WFREE = WB_WFULL + kWsMaxRing,
   WB_COUNT = WB_WFREE + kWsMaxRing
 };
 
 __global__ void __launch_bounds__(kWsThreads, 1)
     k_mlp_fwd3_ws(const MlpFwdArgs a, const int ns, const __grid_constant__ FwdMaps maps) {
-  extern __shared__ __align__(128) unsigned char ws_smem[];
+  extern __shared__ __align__(1024) unsigned char ws_smem[];
   __shared__ __align__(8) uint64_t bars[WB_COUNT];
+  // the 128-byte-swizzled operands (W2 at the base, the W3 chunks) need their 1024-byte pattern
+  // aligned in the shared window: checked before any copy is issued
+  if ((smem_u32(ws_smem) & 1023u) != 0u) {
+    if (threadIdx.x == 0) atomicOr(a.err, NSK_EBIT_BOUNDS);
+    return;
+  }
   __shared__ uint32_t tmem_slot;
   __shared__ int aborted_s;
   volatile int* aborted = &aborted_s;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ntiles = (a.M + kBM - 1) / kBM;
   const int slotb = ws_slot_bytes(a);
-  const uint32_t aW2 = smem_u32(ws_smem), aH = smem_u32(ws_smem + ws_off_h(a));
-  const uint32_t aW = smem_u32(ws_smem + ws_off_w(a));
+  const uint32_t aW2 = smem_u32(ws_smem), aW3 = smem_u32(ws_smem + ws_off_w3(a, ns));
+  const uint32_t aH = smem_u32(ws_smem + ws_off_h(a)), aW = smem_u32(ws_smem + ws_off_w(a));
+  const int w3b = ws_w3_slot_bytes(a);
   unsigned char* sH = ws_smem + ws_off_h(a);
-  float* sB = reinterpret_cast<float*>(ws_smem + ws_off_bias(a, ns));  // b1 | b2 | b3
+  float* sB = reinterpret_cast<float*>(ws_smem + ws_off_bias(a, ns));  // b1 | b2
   auto bar = [&](int i) { return smem_u32(&bars[i]); };
 
   if (warp == 0) {
@@ -907,16 +969,15 @@ __global__ void __launch_bounds__(kWsThreads, 1)
     }
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
-  for (int i = threadIdx.x; i < a.H1 + a.H2 + a.NO; i += kWsThreads)
-    sB[i] = i < a.H1 ? a.b1[i] : (i < a.H1 + a.H2 ? a.b2[i - a.H1] : a.b3[i - a.H1 - a.H2]);
+  for (int i = threadIdx.x; i < a.H1 + a.H2; i += kWsThreads) sB[i] = i < a.H1 ? a.b1[i] : a.b2[i - a.H1];
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tm = tmem_slot;
 
   if (warp == kWsEpiWarps) {
-    // ---- TMA producer: W2 once; per tile: the next tile's X and W1 slabs, then this tile's W3 chunks
-    // (the order in which the MMA warp consumes the ring) ----
+    // ---- TMA producer of the ring: the X and W1 slabs of every tile of this CTA in order (the order
+    // in which the layer-1 MMA warp consumes them) ----
     if (lane == 0) {
       uint32_t r = 0u;
       int armed[kWsMaxRing];
@@ -930,69 +991,54 @@ __global__ void __launch_bounds__(kWsThreads, 1)
         const uint32_t dst = aW + s * (uint32_t)slotb, w1 = dst + (uint32_t)kWsXSlab;
         mbar_expect_tx(bar(WB_WFULL + s), (uint32_t)(kWsXSlab + a.H1 * 32));
         tma_load_2d(dst, &maps.x, k0, t * kBM, bar(WB_WFULL + s));
-        tma_load_2d(dst + (uint32_t)(kBM * 16), &maps.x, k0 + 8, t * kBM, bar(WB_WFULL + s));
         tma_load_2d(w1, &maps.w1, k0, 0, bar(WB_WFULL + s));
-        tma_load_2d(w1 + (uint32_t)(a.H1 * 16), &maps.w1, k0 + 8, 0, bar(WB_WFULL + s));
         armed[s] = (int)(r / ns) + 1;
         ++r;
       };
-      // W3 columns [k0, k0 + w) of one activation chunk (w <= 64): w / 8 boxes side by side
-      auto load_w3_chunk = [&](int k0, int w) {
-        const uint32_t s = r % (uint32_t)ns;
-        ok = ok && ws_wait(bar(WB_WFREE + s), ((r / ns) & 1u) ^ 1u, a.err, aborted);
-        if (!ok) return;
-        const uint32_t dst = aW + s * (uint32_t)slotb;
-        mbar_expect_tx(bar(WB_WFULL + s), (uint32_t)(a.NO * w * 2));
-        for (int b = 0; b < w / 8; ++b)
-          tma_load_2d(dst + (uint32_t)(b * a.NO * 16), &maps.w3, k0 + 8 * b, 0, bar(WB_WFULL + s));
-        armed[s] = (int)(r / ns) + 1;
-        ++r;
-      };
-      mbar_expect_tx(bar(WB_W2), (uint32_t)(a.H2 * a.H1 * 2));
-      for (int b = 0; b < a.H1 / 8; ++b) tma_load_2d(aW2 + (uint32_t)(b * a.H2 * 16), &maps.w2, 8 * b, 0, bar(WB_W2));
-      int t = blockIdx.x;
-      if (t < ntiles)
+      for (int t = blockIdx.x; ok && t < ntiles; t += gridDim.x)
         for (int k0 = 0; ok && k0 < a.K1; k0 += 16) load_xw1(t, k0);
-      for (; ok && t < ntiles; t += gridDim.x) {
-        if (t + (int)gridDim.x < ntiles)
-          for (int k0 = 0; ok && k0 < a.K1; k0 += 16) load_xw1(t + gridDim.x, k0);
-        for (int k0 = 0; ok && k0 < a.H2; k0 += kWsHChunk) load_w3_chunk(k0, min(kWsHChunk, a.H2 - k0));
-      }
       // every copy this thread started has landed before the CTA exits (bounded waits; all have on
       // the normal path, where the MMA warp consumed them)
       volatile int never = 0;
-      ws_wait(bar(WB_W2), 0u, a.err, &never);
       for (int s = 0; s < ns; ++s)
         if (armed[s] > 0) ws_wait(bar(WB_WFULL + s), (uint32_t)(armed[s] - 1) & 1u, a.err, &never);
     }
-  } else if (warp == kWsEpiWarps + 1) {
-    // ---- MMA issuer: L1(first); per tile t: L2(t) chunk by chunk, L1(next), L3(t) chunk by chunk ----
+  } else if (warp == kWsEpiWarps + 3) {
+    // ---- TMA producer of the weights: W2 once, then per tile the W3 chunks through their ring ----
     if (lane == 0) {
-      uint32_t a1f = 1u, a2f = 1u, r = 0u, v = 0u;
-      const uint32_t id1 = idesc_bf16(kBM, a.H1), id2 = idesc_bf16(kBM, a.H2), id3 = idesc_bf16(kBM, a.NO);
-      bool ok = ws_wait(bar(WB_W2), 0u, a.err, aborted);
-      auto layer1 = [&]() {
-        ok = ok && ws_wait(bar(WB_A1FREE), a1f, a.err, aborted);
-        a1f ^= 1u;
-        for (int s = 0; ok && s < a.K1 / 16; ++s) {  // one ring entry per K step: X slab, W1 slab
-          const uint32_t rs = r % (uint32_t)ns;
-          ok = ws_wait(bar(WB_WFULL + rs), (r / ns) & 1u, a.err, aborted);
+      uint32_t r3 = 0u;
+      int armed[2] = {0, 0};
+      bool ok = true;
+      mbar_expect_tx(bar(WB_W2), (uint32_t)ws_w2_bytes(a));
+      for (int b = 0; b < (a.H1 + 63) / 64; ++b)
+        tma_load_2d(aW2 + (uint32_t)(b * a.H2 * 128), &maps.w2, 64 * b, 0, bar(WB_W2));
+      for (int t = blockIdx.x; ok && t < ntiles; t += gridDim.x)
+        for (int k0 = 0; ok && k0 < a.H2; k0 += kWsHChunk) {  // W3 columns [k0, k0 + 64): one box
+          const uint32_t s = r3 & 1u;
+          ok = ws_wait(bar(WB_3FREE + s), ((r3 >> 1) & 1u) ^ 1u, a.err, aborted);
           if (!ok) break;
-          asm volatile("tcgen05.fence::after_thread_sync;");
-          const uint32_t e0 = aW + rs * (uint32_t)slotb;
-          ws_mma(tm, sdesc(e0, kBM * 16, 128), sdesc(e0 + (uint32_t)kWsXSlab, (uint32_t)(a.H1 * 16), 128), id1,
-                 s > 0 ? 1u : 0u);
-          ws_commit(bar(WB_WFREE + rs));
-          ++r;
+          mbar_expect_tx(bar(WB_3FULL + s), (uint32_t)w3b);
+          tma_load_2d(aW3 + s * (uint32_t)w3b, &maps.w3, k0, 0, bar(WB_3FULL + s));
+          armed[s] = (int)(r3 >> 1) + 1;
+          ++r3;
         }
-        if (ok) ws_commit(bar(WB_A1FULL));
-      };
-      int t = blockIdx.x;
-      if (ok && t < ntiles) layer1();
-      for (; ok && t < ntiles; t += gridDim.x) {
+      // every copy this thread started has landed before the CTA exits (bounded waits)
+      volatile int never = 0;
+      ws_wait(bar(WB_W2), 0u, a.err, &never);
+      for (int s = 0; s < 2; ++s)
+        if (armed[s] > 0) ws_wait(bar(WB_3FULL + s), (uint32_t)(armed[s] - 1) & 1u, a.err, &never);
+    }
+  } else if (warp == kWsEpiWarps + 1) {
+    // ---- MMA issuer of layers 2 and 3: per tile, L2 chunk by chunk (resident W2), then L3 chunk
+    // by chunk (W3 from its ring), each chunk as soon as its activations are in ----
+    if (lane == 0) {
+      uint32_t a2f = 1u, v = 0u, r3 = 0u;
+      const uint32_t id2 = idesc_bf16(kBM, a.H2), id3 = idesc_bf16(kBM, a.NO);
+      bool ok = ws_wait(bar(WB_W2), 0u, a.err, aborted);
+      for (int t = blockIdx.x; ok && t < ntiles; t += gridDim.x) {
         ok = ws_wait(bar(WB_A2FREE), a2f, a.err, aborted);
         a2f ^= 1u;
-        for (int c = 0; ok && c < a.H1; c += kWsHChunk) {  // layer 2: activation chunks x resident W2
+        for (int c = 0; ok && c < a.H1; c += kWsHChunk) {  // layer 2: activation chunks x W2
           const uint32_t hs = v & 1u;
           ok = ws_wait(bar(WB_HFULL + hs), (v >> 1) & 1u, a.err, aborted);
           if (!ok) break;
@@ -1000,30 +1046,27 @@ __global__ void __launch_bounds__(kWsThreads, 1)
           const int w = min(kWsHChunk, a.H1 - c);
           for (int s = 0; s < w / 16; ++s)
             ws_mma(tm + 256u, sdesc(aH + hs * kWsHSlot + (uint32_t)(s * 2 * kBM * 16), kBM * 16, 128),
-                   sdesc(aW2 + (uint32_t)(((c + 16 * s) / 8) * a.H2 * 16), (uint32_t)(a.H2 * 16), 128), id2,
-                   (c > 0 || s > 0) ? 1u : 0u);
+                   sdesc_sw(aW2 + (uint32_t)(((c + 16 * s) / 64) * a.H2 * 128 + ((c + 16 * s) % 64) * 2), 1024u,
+                            kSw128),
+                   id2, (c > 0 || s > 0) ? 1u : 0u);
           ws_commit(bar(WB_HFREE + hs));
           ++v;
         }
         if (!ok) break;
         ws_commit(bar(WB_A2FULL));
-        if (t + (int)gridDim.x < ntiles) layer1();
-        for (int c = 0; ok && c < a.H2; c += kWsHChunk) {  // layer 3: activation chunks x streamed W3
-          const uint32_t hs = v & 1u;
-          ok = ws_wait(bar(WB_HFULL + hs), (v >> 1) & 1u, a.err, aborted);
-          if (!ok) break;
-          const int w = min(kWsHChunk, a.H2 - c);
-          const uint32_t rs = r % (uint32_t)ns;  // the chunk's W3 columns: one ring entry
-          ok = ws_wait(bar(WB_WFULL + rs), (r / ns) & 1u, a.err, aborted);
+        for (int c = 0; ok && c < a.H2; c += kWsHChunk) {  // layer 3: activation chunks x W3 chunks
+          const uint32_t hs = v & 1u, s3 = r3 & 1u;
+          ok = ws_wait(bar(WB_HFULL + hs), (v >> 1) & 1u, a.err, aborted) &&
+               ws_wait(bar(WB_3FULL + s3), (r3 >> 1) & 1u, a.err, aborted);
           if (!ok) break;
           asm volatile("tcgen05.fence::after_thread_sync;");
+          const int w = min(kWsHChunk, a.H2 - c);
           for (int s = 0; s < w / 16; ++s)
             ws_mma(tm + 256u, sdesc(aH + hs * kWsHSlot + (uint32_t)(s * 2 * kBM * 16), kBM * 16, 128),
-                   sdesc(aW + rs * (uint32_t)slotb + (uint32_t)(s * 2 * a.NO * 16), (uint32_t)(a.NO * 16), 128), id3,
-                   (c > 0 || s > 0) ? 1u : 0u);
-          ws_commit(bar(WB_WFREE + rs));
-          ++r;
+                   sdesc_sw(aW3 + s3 * (uint32_t)w3b + (uint32_t)(s * 32), 1024u, kSw128), id3, (c > 0 || s > 0) ? 1u : 0u);
+          ws_commit(bar(WB_3FREE + s3));
           ws_commit(bar(WB_HFREE + hs));
+          ++r3;
           ++v;
         }
         if (ok) ws_commit(bar(WB_A3FULL));
@@ -1032,6 +1075,32 @@ __global__ void __launch_bounds__(kWsThreads, 1)
       ws_commit(bar(WB_FINAL));
       volatile int never = 0;
       ws_wait(bar(WB_FINAL), 0u, a.err, &never);
+    }
+  } else if (warp == kWsEpiWarps + 2) {
+    // ---- MMA issuer of layer 1: per tile, once the epilogue has released the accumulator, one K
+    // step per ring entry (X slab, W1 slab) as the entries land ----
+    if (lane == 0) {
+      uint32_t a1f = 1u, r = 0u;
+      const uint32_t id1 = idesc_bf16(kBM, a.H1);
+      bool ok = true;
+      for (int t = blockIdx.x; ok && t < ntiles; t += gridDim.x) {
+        ok = ws_wait(bar(WB_A1FREE), a1f, a.err, aborted);
+        a1f ^= 1u;
+        for (int s = 0; ok && s < a.K1 / 16; ++s) {
+          const uint32_t rs = r % (uint32_t)ns;
+          ok = ws_wait(bar(WB_WFULL + rs), (r / ns) & 1u, a.err, aborted);
+          if (!ok) break;
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          const uint32_t e0 = aW + rs * (uint32_t)slotb;
+          ws_mma(tm, sdesc_sw(e0, 256u, kSw32), sdesc_sw(e0 + (uint32_t)kWsXSlab, 256u, kSw32), id1, s > 0 ? 1u : 0u);
+          ws_commit(bar(WB_WFREE + rs));
+          ++r;
+        }
+        if (ok) ws_commit(bar(WB_A1FULL));
+      }
+      ws_commit(bar(WB_FINAL1));
+      volatile int never = 0;
+      ws_wait(bar(WB_FINAL1), 0u, a.err, &never);
     }
   } else {
     // ---- epilogue warps: warp w reads TMEM lanes 32 (w % 4).. (rows q 32 + lane) and the 16-column
@@ -1071,29 +1140,42 @@ __global__ void __launch_bounds__(kWsThreads, 1)
       asm volatile("tcgen05.fence::after_thread_sync;");
       gelu_layer(256u, a.H2, aB + 4u * a.H1);
       if (!ok) break;
+      float b3[16];  // requested before the wait for layer 3, used after it
+      if (sub * 16 < a.NO)
+#pragma unroll
+        for (int i = 0; i < 16; ++i) b3[i] = __ldg(a.b3 + sub * 16 + i);
       ok = ws_wait_warp(bar(WB_A3FULL), f3, a.err, aborted);
       f3 ^= 1u;
       if (!ok) break;
       asm volatile("tcgen05.fence::after_thread_sync;");
-      if (sub * 16 < a.NO) {  // layer 3: + b3 -> Y
-        uint32_t v[16];
-        tmem_ld16(tm + lanes + 256u + (uint32_t)(sub * 16), v);
-        const int m = t * kBM + r;
-        if (m < a.M) {
-          const uint32_t b3 = aB + 4u * (uint32_t)(a.H1 + a.H2 + sub * 16);
-          float* y = a.Y + (size_t)m * a.ldy + sub * 16;
-#pragma unroll
-          for (int g = 0; g < 4; ++g) {
-            const float4 bb = lds_f4(b3 + 16u * g);
-            *reinterpret_cast<float4*>(y + 4 * g) =
-                make_float4(__uint_as_float(v[4 * g]) + bb.x, __uint_as_float(v[4 * g + 1]) + bb.y,
-                            __uint_as_float(v[4 * g + 2]) + bb.z, __uint_as_float(v[4 * g + 3]) + bb.w);
-          }
-        }
-      }
+      uint32_t v[16];
+      if (sub * 16 < a.NO) tmem_ld16(tm + lanes + 256u + (uint32_t)(sub * 16), v);
       asm volatile("tcgen05.fence::before_thread_sync;");
       __syncwarp();
-      if (lane == 0) mbar_arrive(bar(WB_A2FREE));
+      if (lane == 0) mbar_arrive(bar(WB_A2FREE));  // layer 2's and 3's accumulator read
+      if (sub * 16 < a.NO) {  // layer 3: + b3 -> Y
+        // the warp's 32 rows x 16 columns, staged by 16-byte column group j in 512 bytes of the
+        // activation slots that this warp alone writes (its bytes of activation chunks 0 and 1;
+        // every MMA reading them has completed), then stored 64 bytes per row, 8 rows per
+        // instruction
+        auto piece = [&](int j) {
+          return sH + (j >> 1) * kWsHSlot + (2 * sub + (j & 1)) * (kBM * 16) + q * 512;
+        };
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          *reinterpret_cast<float4*>(piece(j) + lane * 16) =
+              make_float4(__uint_as_float(v[4 * j]) + b3[4 * j], __uint_as_float(v[4 * j + 1]) + b3[4 * j + 1],
+                          __uint_as_float(v[4 * j + 2]) + b3[4 * j + 2], __uint_as_float(v[4 * j + 3]) + b3[4 * j + 3]);
+        __syncwarp();
+        const int j = lane >> 3;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int rr = 8 * i + (lane & 7), m = t * kBM + q * 32 + rr;
+          const float4 y = *reinterpret_cast<const float4*>(piece(j) + rr * 16);
+          if (m < a.M) *reinterpret_cast<float4*>(a.Y + (size_t)m * a.ldy + sub * 16 + 4 * j) = y;
+        }
+        __syncwarp();
+      }
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -1124,16 +1206,17 @@ inline TmapEncodeFn tmap_encode_fn() {
   return fn;
 }
 // 2D BF16 tensor map of a row-major [rows][ld] matrix, columns [0, cols) used; boxes of
-// 8 columns x box_rows rows; rows beyond the matrix read as zero
-inline bool bf16_tmap(CUtensorMap* m, const void* base, int cols, int rows, int ld, int box_rows) {
+// box_cols x box_rows with the given swizzle; elements beyond the matrix read as zero
+inline bool bf16_tmap(CUtensorMap* m, const void* base, int cols, int rows, int ld, int box_cols, int box_rows,
+                      CUtensorMapSwizzle swizzle) {
   const TmapEncodeFn fn = tmap_encode_fn();
   if (!fn) return false;
   const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
   const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
-  const cuuint32_t box[2] = {8u, (cuuint32_t)box_rows};
+  const cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
   const cuuint32_t es[2] = {1u, 1u};
   return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -1166,14 +1249,18 @@ inline int launch_mlp_fwd3(const MlpFwdArgs& a, cudaStream_t s) {
     attr_done = true;
   }
   const int ntiles = (a.M + kBM - 1) / kBM;
-  // the warp-specialised kernel: layer 3 fits in layer 2's first activation chunk, the largest
-  // ring of W1/W3 slabs (2 to 4) that fits in shared memory, and the tensor maps can be made
+  // the warp-specialised kernel: layer 3 fits in layer 2's first activation chunk, W2 and W3 fit
+  // resident beside a ring of at least 2 row-tile/W1 slabs (the largest that fits, up to
+  // kWsMaxRing), and the tensor maps can be made
   if (g_fwd_kernel == 0 && a.NO <= kWsHChunk) {
     int ns = kWsMaxRing;
     while (ns >= 2 && ws_smem_bytes(a, ns) > kFwSmemMax) --ns;
     FwdMaps maps;
-    if (ns >= 2 && bf16_tmap(&maps.x, a.X, a.K1, a.M, a.ldx, kBM) && bf16_tmap(&maps.w1, a.W1, a.K1, a.H1, a.K1, a.H1) &&
-        bf16_tmap(&maps.w2, a.W2, a.H1, a.H2, a.H1, a.H2) && bf16_tmap(&maps.w3, a.W3, a.H2, a.NO, a.H2, a.NO)) {
+    constexpr CUtensorMapSwizzle k32 = CU_TENSOR_MAP_SWIZZLE_32B, k128 = CU_TENSOR_MAP_SWIZZLE_128B;
+    if (ns >= 2 && bf16_tmap(&maps.x, a.X, a.K1, a.M, a.ldx, 16, kBM, k32) &&
+        bf16_tmap(&maps.w1, a.W1, a.K1, a.H1, a.K1, 16, a.H1, k32) &&
+        bf16_tmap(&maps.w2, a.W2, a.H1, a.H2, a.H1, 64, a.H2, k128) &&
+        bf16_tmap(&maps.w3, a.W3, a.H2, a.NO, a.H2, 64, a.NO, k128)) {
       static bool ws_attr = false;
       if (!ws_attr) {
         if (cudaFuncSetAttribute(k_mlp_fwd3_ws, cudaFuncAttributeMaxDynamicSharedMemorySize, kFwSmemMax) !=
