@@ -496,6 +496,24 @@ __global__ void __launch_bounds__(256) k_elem_mean(const long long E, const int 
   mean[e] = acc / (float)npe;
 }
 
+// the same for FP32 elements of 64 nodes, half a warp per element (lane q loads nodes 4q..4q+3:
+// 16-byte loads that together read the element's 256 bytes at once); the sum in the same order,
+// ((0 + s_0) + s_1) + ... + s_15 with s_q = (u_4q + u_4q+1) + (u_4q+2 + u_4q+3), gathered by
+// shuffles within the half warp
+__global__ void __launch_bounds__(256) k_elem_mean64(const long long E, const float* __restrict__ U,
+                                                     float* __restrict__ mean) {
+  const long long e = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 4;
+  if (e >= E) return;  // whole half warps: E is counted in elements
+  const int q = threadIdx.x & 15;
+  const unsigned half = (threadIdx.x & 16) ? 0xffff0000u : 0x0000ffffu;
+  const float4 v = reinterpret_cast<const float4*>(U + e * 64)[q];
+  const float sq = (v.x + v.y) + (v.z + v.w);
+  float acc = 0.f;
+#pragma unroll
+  for (int k = 0; k < 16; ++k) acc += __shfl_sync(half, sq, k, 16);
+  if (q == 0) mean[e] = acc / 64.0f;
+}
+
 // four elements per warp (their loads issued together), lane f taking features f, f + 32, ... of
 // each (no division per value; the face neighbours from the element's Cartesian position)
 constexpr int kFeatEpw = 4;
@@ -530,56 +548,51 @@ __global__ void __launch_bounds__(256) k_closure_features(const NskParams p, con
   }
 }
 
-// FP32 3D elements with N = 3 (64 nodes, 70 features, rows of 144): one thread per element, its
-// 64 densities by 16-byte loads, the row built in registers and written with 16-byte stores
-__global__ void __launch_bounds__(128) k_closure_features64(const NskParams p, const float* __restrict__ U,
+// FP32 3D elements with N = 3 (64 nodes, 70 features, rows of 144 BF16 = 288 bytes): half a
+// warp per element; lane q takes nodes 4q..4q+3 (one 16-byte load), writes their four high parts
+// (columns 4q.., 8 bytes) and four low parts (columns 70 + 4q.., two 4-byte stores), lanes 0-5
+// the face-neighbour means (columns 64 + q and 134 + q), lanes 6-7 the zero padding (140-143):
+// every store of a half warp lands in the element's row. The same operations per value as
+// k_closure_features.
+__global__ void __launch_bounds__(256) k_closure_features64(const NskParams p, const float* __restrict__ U,
                                                             const float* __restrict__ mean_e,
                                                             __nv_bfloat16* __restrict__ X) {
   constexpr int NPE = 64, NF = NPE + 6, PAD = 144;
-  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long e = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 4;
   if (e >= p.E) return;
+  const int q = threadIdx.x & 15;
   const float mean = mean_e[e];
-  const nsk::ElemIdx ex = nsk::elem_idx<3>(p, (int)e);
-  float v[NF];
-  const float4* u4 = reinterpret_cast<const float4*>(U + e * NPE);
-#pragma unroll
-  for (int q = 0; q < NPE / 4; ++q) {
-    const float4 t = u4[q];
-    v[4 * q] = t.x - mean;
-    v[4 * q + 1] = t.y - mean;
-    v[4 * q + 2] = t.z - mean;
-    v[4 * q + 3] = t.w - mean;
-  }
-#pragma unroll
-  for (int j = 0; j < 6; ++j) v[NPE + j] = mean_e[nsk::nbr_of(p, ex, j >> 1, (j & 1) ? 1 : -1)] - mean;
-  uint4* row = reinterpret_cast<uint4*>(X + e * PAD);
-#pragma unroll
-  for (int g = 0; g < PAD / 8; ++g) {
-    uint32_t w[4];
-#pragma unroll
-    for (int h = 0; h < 4; ++h) {
-      uint32_t pair = 0;
-#pragma unroll
-      for (int b = 0; b < 2; ++b) {
-        const int col = 8 * g + 2 * h + b;
-        __nv_bfloat16 o = __float2bfloat16_rn(0.f);
-        if (col < 2 * NF) {
-          const float s = v[col < NF ? col : col - NF] / kFeatScale;
-          const __nv_bfloat16 hi = __float2bfloat16_rn(s);
-          o = col < NF ? hi : __float2bfloat16_rn(s - __bfloat162float(hi));
-        }
-        pair |= (uint32_t)__bfloat16_as_ushort(o) << (16 * b);
-      }
-      w[h] = pair;
-    }
-    row[g] = make_uint4(w[0], w[1], w[2], w[3]);
+  unsigned char* row = reinterpret_cast<unsigned char*>(X + e * PAD);
+  auto hi_lo = [](float v, uint32_t& hb, uint32_t& lb) {
+    const float s = v / kFeatScale;
+    const __nv_bfloat16 hi = __float2bfloat16_rn(s);
+    hb = __bfloat16_as_ushort(hi);
+    lb = __bfloat16_as_ushort(__float2bfloat16_rn(s - __bfloat162float(hi)));
+  };
+  const float4 t = reinterpret_cast<const float4*>(U + e * NPE)[q];
+  uint32_t h[4], l[4];
+  hi_lo(t.x - mean, h[0], l[0]);
+  hi_lo(t.y - mean, h[1], l[1]);
+  hi_lo(t.z - mean, h[2], l[2]);
+  hi_lo(t.w - mean, h[3], l[3]);
+  *reinterpret_cast<uint2*>(row + 8 * q) = make_uint2(h[0] | (h[1] << 16), h[2] | (h[3] << 16));
+  *reinterpret_cast<uint32_t*>(row + 2 * NF + 8 * q) = l[0] | (l[1] << 16);
+  *reinterpret_cast<uint32_t*>(row + 2 * NF + 8 * q + 4) = l[2] | (l[3] << 16);
+  if (q < 6) {
+    const nsk::ElemIdx ex = nsk::elem_idx<3>(p, (int)e);
+    uint32_t hb, lb;
+    hi_lo(mean_e[nsk::nbr_of(p, ex, q >> 1, (q & 1) ? 1 : -1)] - mean, hb, lb);
+    *reinterpret_cast<unsigned short*>(row + 2 * (NPE + q)) = (unsigned short)hb;
+    *reinterpret_cast<unsigned short*>(row + 2 * (NF + NPE + q)) = (unsigned short)lb;
+  } else if (q < 8) {
+    *reinterpret_cast<uint32_t*>(row + 2 * (2 * NF) + 4 * (q - 6)) = 0u;
   }
 }
 
 template <typename R>
 int launch_features(const nsk_ctx* c, const R* U, const float* mean, __nv_bfloat16* X, int nin_pad) {
   if (sizeof(R) == 4 && c->dim == 3 && c->npe == 64 && nin_pad == 144 && ((uintptr_t)X & 15u) == 0) {
-    k_closure_features64<<<(unsigned)((c->E + 127) / 128), 128, 0, c->stream>>>(c->p, (const float*)U, mean, X);
+    k_closure_features64<<<(unsigned)((c->E * 16 + 255) / 256), 256, 0, c->stream>>>(c->p, (const float*)U, mean, X);
     return cudaGetLastError() == cudaSuccess ? NSK_OK : NSK_ERR_CUDA;
   }
   const unsigned g = nb((c->E + kFeatEpw - 1) / kFeatEpw * 32);
@@ -639,7 +652,10 @@ int closure_features(nsk_ctx* c, void* X) {
   float* mean = c->cl_mean;
   int st;
   if (c->precision == NSK_FP32_MIXED) {
-    k_elem_mean<float><<<nb(c->E), 256, 0, c->stream>>>(c->E, c->npe, (const float*)c->b.U, mean);
+    if (c->npe == 64 && ((uintptr_t)c->b.U & 15u) == 0)
+      k_elem_mean64<<<(unsigned)((c->E * 16 + 255) / 256), 256, 0, c->stream>>>(c->E, (const float*)c->b.U, mean);
+    else
+      k_elem_mean<float><<<nb(c->E), 256, 0, c->stream>>>(c->E, c->npe, (const float*)c->b.U, mean);
     st = launch_features<float>(c, (const float*)c->b.U, mean, (__nv_bfloat16*)X, nin_pad);
   } else {
     k_elem_mean<double><<<nb(c->E), 256, 0, c->stream>>>(c->E, c->npe, (const double*)c->b.U, mean);

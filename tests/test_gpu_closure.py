@@ -159,6 +159,51 @@ def test_closure_features_and_targets(gpu):
     s.close()
 
 
+def test_fp32_feature_rows_bit_exact(gpu):
+    """The FP32 operator's feature rows (half a warp per element: 16-byte loads of the element's
+    densities, the row written by the same half warp) hold exactly the BF16 pairs of the per-value
+    arithmetic, restated here in FP32: the element mean as the sum in node quadruples,
+    ((0 + s_0) + s_1) + ..., s_q = (u_4q + u_4q+1) + (u_4q+2 + u_4q+3), divided by 64; then for each
+    value v (node density or face-neighbour mean, minus the element mean) s = v / 0.5,
+    hi = bf16(s), lo = bf16(s - hi); zero padding. Mesh 7^3 (ragged over 256-thread blocks)."""
+    import torch
+
+    ne = 7
+    s, U = _collision_solver(ne=ne, precision=nsk.NSK_FP32_MIXED)
+    s.set_state(U)
+    E, npe = s.E, s.npe
+    X = torch.full((E, 144), float("nan"), dtype=torch.bfloat16, device=gpu)
+    s.closure_features(X)
+    rho = s.get_state()[0].astype(np.float32)  # the device's FP32 densities
+    f32 = np.float32
+    quad = rho.reshape(E, 16, 4)
+    sq = (quad[:, :, 0] + quad[:, :, 1]) + (quad[:, :, 2] + quad[:, :, 3])
+    acc = np.zeros(E, dtype=f32)
+    for k in range(16):
+        acc = acc + sq[:, k]
+    mean = acc / f32(64.0)
+    vals = np.zeros((E, npe + 6), dtype=f32)
+    vals[:, :npe] = rho - mean[:, None]
+    for e in range(E):
+        c = [e % ne, (e // ne) % ne, e // (ne * ne)]
+        j = 0
+        for k in range(3):
+            for d in (-1, 1):
+                cc = list(c)
+                cc[k] = (cc[k] + d) % ne
+                vals[e, npe + j] = mean[cc[0] + ne * cc[1] + ne * ne * cc[2]] - mean[e]
+                j += 1
+    sc = vals / f32(0.5)
+    hi = torch.from_numpy(sc).to(torch.bfloat16)
+    lo = torch.from_numpy(sc - hi.float().numpy()).to(torch.bfloat16)
+    want = torch.zeros((E, 144), dtype=torch.bfloat16)
+    want[:, :npe + 6] = hi
+    want[:, npe + 6:2 * (npe + 6)] = lo
+    got = X.cpu()
+    assert torch.equal(got.view(torch.int16), want.view(torch.int16))
+    s.close()
+
+
 def test_closure_replaces_the_stiff_c_equation(gpu):
     """Train on snapshots of the explicit run, then run the closure to the same time."""
     import torch
