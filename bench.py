@@ -397,10 +397,8 @@ def run_gpu(args, wl, rank, world):
     barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        s.set_state(U_host)
-        s.step(dt, 1)
-        s.get_state(out=U_host)
+    for _ in range(e2e_steps):  # nsk_step_host: the state in, one step, the state out
+        s.step_host(U_host, dt, 1)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     barrier()

@@ -212,6 +212,22 @@ int nsk_compute_dt(nsk_ctx* ctx, double cfl, double* dt_out);
  * word. */
 int nsk_step(nsk_ctx* ctx, double dt, int nsteps);
 
+/* nsk_step for a state held in host memory: U_in (host, the layout of U) is
+ * copied in, nsteps steps of step dt > 0 are taken, and the final state is
+ * copied out to U_out (host; it may be U_in). The results equal
+ * nsk_set_state(U_in, NSK_HOST), nsk_step and nsk_get_state(U_out, NSK_HOST)
+ * bit for bit. For FP64 relaxation-model 3D meshes at N = 3 with the separate
+ * face pass (nsk_set_schedule fused_face 0, 128 or 256 threads), profiling off,
+ * a z extent that is a multiple of 8 elements and slabs of a multiple of 16
+ * elements, the copies overlap the computation: the state arrives in 8 z-slabs
+ * on a second stream while the first stage's prolongation and lifting run slab
+ * by slab behind it, and the last stage's volume kernel runs slab by slab with
+ * each slab copied out as soon as it is written; otherwise the three calls are
+ * made in turn. Pinned host memory gives the copies their full rate.
+ * Synchronises before returning (the host buffers are no longer in use then,
+ * also after an error); errors as nsk_step. */
+int nsk_step_host(nsk_ctx* ctx, const double* U_in, double* U_out, double dt, int nsteps);
+
 /* Implicit time integration (Sec. 3.1): nsteps steps of size dt of the six-stage, fourth-order
  * ESDIRK the paper cites (the implicit tableau of Kennedy and Carpenter's ARK4(3)6L[2]SA,
  * gamma = 1/4, stiffly accurate, L-stable) on the context's residual (nsk_rhs). Each implicit

@@ -350,6 +350,9 @@ void free_ctx(nsk_ctx* c) {
                   c->fvb.flags, c->fvb.ind, c->fvb.Uf, c->fvb.Gf, c->fvb.SL, c->fvb.Fh, c->fvb.bar};
   for (void* q : ptrs)
     if (q) cudaFree(q);
+  if (c->io_stream) cudaStreamDestroy(c->io_stream);
+  for (cudaEvent_t ev : c->io_ev)
+    if (ev) cudaEventDestroy(ev);
   free(c->fv_params);
   for (cudaEvent_t ev : c->prof_pool) cudaEventDestroy(ev);
   delete c;
@@ -739,6 +742,127 @@ int nsk_step(nsk_ctx* c, double dt, int nsteps) {
     if (r) return r;
   }
   return sync_and_check(c);
+}
+
+// ---- the host-state step: the state in from host memory, the steps, the state out ----
+namespace {
+// the overlapped path applies: FP64 relaxation model without closure or sub-cells, 3D, N = 3,
+// the separate face pass, no profiling, and NSK_IO_SLABS z-slabs of whole blocks of every
+// stage kernel (each slab whole z planes, a multiple of the 16 elements of a 256-thread
+// prolongation or face-pass block; the lifting and volume blocks hold 2 or 4 elements)
+bool host_overlap_eligible(const nsk_ctx* c) {
+  if (c->precision != NSK_FP64 || c->dim != 3 || c->np != 4 || c->p.model == NSK_MODEL_NSK || c->fv_path() ||
+      c->closure_mode == NSK_C_LEARNED || c->fused_face != 0 || (c->tpb != 128 && c->tpb != 256) || c->prof_on)
+    return false;
+  return c->ne[2] % NSK_IO_SLABS == 0 && (c->E / NSK_IO_SLABS) % 16 == 0;
+}
+int io_setup(nsk_ctx* c) {
+  if (!c->io_stream) {
+    if (cudaStreamCreateWithFlags(&c->io_stream, cudaStreamNonBlocking) != cudaSuccess) {
+      c->io_stream = nullptr;
+      cudaGetLastError();
+      return NSK_ERR_CUDA;
+    }
+  }
+  for (cudaEvent_t& ev : c->io_ev)
+    if (!ev && cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+      ev = nullptr;
+      cudaGetLastError();
+      return NSK_ERR_CUDA;
+    }
+  return NSK_OK;
+}
+// the queued steps of the overlapped path (the copies on io_stream, the kernels on the context's
+// stream); returns at the first error, with work possibly still queued
+int host_steps(nsk_ctx* c, const double* U_in, double* U_out, double dt, int nsteps) {
+  constexpr int NS = NSK_IO_SLABS;
+  const long long slab = c->E / NS, sn = slab * c->npe;
+  const size_t sbytes = sizeof(double) * (size_t)sn;
+  double* U = (double*)c->b.U;
+  cudaEvent_t* ev = c->io_ev;  // [0, NS): slab k in; [NS, 2 NS): slab k written; 2 NS: prior work
+  auto copy = [&](double* dst, const double* src, int k, cudaMemcpyKind kind) -> int {
+    for (int v = 0; v < c->nvar; ++v) {
+      const size_t off = (size_t)v * (size_t)c->nn + (size_t)k * (size_t)sn;
+      if (cudaMemcpyAsync(dst + off, src + off, sbytes, kind, c->io_stream) != cudaSuccess) return NSK_ERR_CUDA;
+    }
+    return NSK_OK;
+  };
+  auto part = [&](const NskLaunch& l, int which, int k0, int nk) -> int {
+    const int r = nsk_launch_stage_part_d3(c->p, c->np, false, c->b, l, c->stream, which, (long long)k0 * slab,
+                                           (long long)nk * slab);
+    if (r < 0) return r;
+    c->launches += r;
+    return NSK_OK;
+  };
+  // the copies in, slab by slab, once the context's stream has finished what it holds
+  if (cudaEventRecord(ev[2 * NS], c->stream) != cudaSuccess || cudaStreamWaitEvent(c->io_stream, ev[2 * NS], 0))
+    return NSK_ERR_CUDA;
+  for (int k = 0; k < NS; ++k) {
+    if (copy(U, U_in, k, cudaMemcpyHostToDevice) || cudaEventRecord(ev[k], c->io_stream) != cudaSuccess)
+      return NSK_ERR_CUDA;
+  }
+  if (cudaMemsetAsync(c->b.K, 0, c->rsize * (size_t)c->nvar * (size_t)c->nn, c->stream) != cudaSuccess)
+    return NSK_ERR_CUDA;
+  bool ready = false;  // b.Utr holds the traces of U
+  for (int s = 0; s < nsteps; ++s)
+    for (int st = 0; st < 5; ++st) {
+      NskLaunch l = {NSK_MODE_LSRK, nullptr, kA[st], kB[st], nullptr, dt, nullptr, c->tpb, 0};
+      const bool first = s == 0 && st == 0, last = s == nsteps - 1 && st == 4;
+      l.traces_ready = ready;
+      l.utr_next = last ? nullptr : c->b.Utr;  // the volume kernel writes the next stage's traces
+      int r = NSK_OK;
+      if (first) {
+        // the prolongation of slab k once it has arrived, the lifting of slab k - 1 once slabs
+        // k - 2 .. k have their traces (z neighbours; periodic, so slabs NS - 1 and 0 last), then
+        // the face pass and the volume kernel over the mesh
+        for (int k = 0; k < NS && r == NSK_OK; ++k) {
+          if (cudaStreamWaitEvent(c->stream, ev[k], 0) != cudaSuccess) return NSK_ERR_CUDA;
+          r = part(l, 0, k, 1);
+          if (r == NSK_OK && k >= 2) r = part(l, 1, k - 1, 1);
+        }
+        if (r == NSK_OK) r = part(l, 1, NS - 1, 1);
+        if (r == NSK_OK) r = part(l, 1, 0, 1);
+        if (r == NSK_OK) r = part(l, 2, 0, NS);
+        if (r == NSK_OK) r = part(l, 3, 0, NS);
+      } else if (last) {
+        // the lifting and face pass over the mesh, then the volume kernel slab by slab, each slab
+        // copied out once written
+        r = part(l, 1, 0, NS);
+        if (r == NSK_OK) r = part(l, 2, 0, NS);
+        for (int k = 0; k < NS && r == NSK_OK; ++k) {
+          r = part(l, 3, k, 1);
+          if (r == NSK_OK && (cudaEventRecord(ev[NS + k], c->stream) != cudaSuccess ||
+                              cudaStreamWaitEvent(c->io_stream, ev[NS + k], 0) != cudaSuccess))
+            r = NSK_ERR_CUDA;
+          if (r == NSK_OK) r = copy(U_out, U, k, cudaMemcpyDeviceToHost);
+        }
+      } else {
+        r = launch_stage(c, l);
+      }
+      if (r) return r;
+      ready = !last;
+    }
+  return NSK_OK;
+}
+}  // namespace
+
+int nsk_step_host(nsk_ctx* c, const double* U_in, double* U_out, double dt, int nsteps) {
+  const NskRange nvtx_range("nsk_step_host");
+  if (!c || !U_in || !U_out || nsteps < 1 || !isfinite(dt) || dt <= 0.0) return NSK_ERR_ARG;
+  if (!c->params_set) return NSK_ERR_STATE;
+  if (!host_overlap_eligible(c) || io_setup(c) != NSK_OK) {  // the three calls in turn
+    int r = nsk_set_state(c, U_in, NSK_HOST);
+    if (r == NSK_OK) r = nsk_step(c, dt, nsteps);
+    if (r == NSK_OK) r = nsk_get_state(c, U_out, NSK_HOST);
+    return r;
+  }
+  c->state_set = true;
+  const int r = host_steps(c, U_in, U_out, dt, nsteps);
+  // the caller's host buffers are not touched once the call returns, whatever happened
+  const bool io_ok = cudaStreamSynchronize(c->io_stream) == cudaSuccess;
+  const int rc = sync_and_check(c);
+  if (r) return r;
+  return io_ok ? rc : NSK_ERR_CUDA;
 }
 
 // ---- 1D sub-cell shock capturing and Dirichlet boundaries ----

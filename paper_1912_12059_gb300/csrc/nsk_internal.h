@@ -155,6 +155,10 @@ int nsk_launch_stage_nsk(int dim, const NskParams& p, int np, const NskBuffers& 
 int nsk_launch_dt_nsk(const NskParams& p, int dim, const NskBuffers& b, double cfl, int N, cudaStream_t s);
 int nsk_launch_stage_d3(const NskParams& p, int np, bool fp32, const NskBuffers& b, const NskLaunch& l,
                         cudaStream_t s);
+// one part (0 prolongation, 1 lifting, 2 face pass, 3 volume) of a separate-face 3D stage over the
+// elements [e0, e0 + ne), whole blocks of every kernel (FP64, N = 3); launches made or an error
+int nsk_launch_stage_part_d3(const NskParams& p, int np, bool fp32, const NskBuffers& b, const NskLaunch& l,
+                             cudaStream_t s, int part, long long e0, long long ne);
 // Single-block schedule (nsk_set_schedule fused_face = 3): the bytes of shared memory a mesh
 // needs, and one launch running nsteps LSRK steps (mode LSRK, fixed dt) or one residual (mode
 // RHS, into Rout) in one block; returns 1 (launches), NSK_ERR_ARG when the mesh does not fit.
@@ -200,6 +204,9 @@ int nsk_fv_launch_coop(const NskParams& p, const void* fvp, int np, const FvBuff
 int nsk_fv_fill_params(void* fvp, int np, const double* xi, const double* gauss_x, const double* gauss_w, double h,
                        int dirichlet, const double* Ub_lo, const double* Ub_hi, double upper, double lower);
 
+// z-slabs of the host-state step's overlapped copies
+constexpr int NSK_IO_SLABS = 8;
+
 struct nsk_ctx {
   int dim, N, np, npe, nfn, nvar, nq, node_type, precision;
   long long E, nn;
@@ -240,6 +247,9 @@ struct nsk_ctx {
   double fv_Ub[2][3];          // boundary states
   void* fv_params;             // host copy of the kernels' parameter block
   FvBuffers fvb;
+  // the host-state step (nsk_step_host): its copy stream and events, made on first use
+  cudaStream_t io_stream;
+  cudaEvent_t io_ev[2 * NSK_IO_SLABS + 1];
   bool fv_path() const { return fv_on || fv_dirichlet; }
 };
 

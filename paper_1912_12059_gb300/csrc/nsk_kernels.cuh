@@ -1419,11 +1419,14 @@ __device__ __forceinline__ void volume_lean_group(const NskParams& p, R* __restr
 }
 
 // ---- stand-alone stage kernels ---------------------------------------------
+// blk_off (every stage kernel): the index of the grid's first block, for launches over a range
+// of whole blocks of the mesh (the host-state step's slabs); the bounds checks stay the mesh's.
 // grid (ceil(E nfn / 256), 2d): blockIdx.y is the face slot
 template <typename R, int D, int NP>
-__global__ void __launch_bounds__(256) k_prolong(const NskParams p, const R* __restrict__ U, R* __restrict__ Utr) {
+__global__ void __launch_bounds__(256) k_prolong(const NskParams p, const R* __restrict__ U, R* __restrict__ Utr,
+                                                 const int blk_off = 0) {
   using S = Shape<D, NP>;
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  const int idx = (blockIdx.x + blk_off) * blockDim.x + threadIdx.x;
   if (idx < p.nfe) {
     const int e = idx / S::NFN;
     prolong_trace<R, D, NP>(p, U + (size_t)e * S::NPE, (size_t)p.nne, Utr, e, blockIdx.y, idx % S::NFN);
@@ -1449,10 +1452,10 @@ __host__ __device__ constexpr int lift_min_blocks() {
 template <typename R, int D, int NP, int G, bool QF>
 __global__ void __launch_bounds__(G * Shape<D, NP>::NPE, (lift_min_blocks<R, G * Shape<D, NP>::NPE>()))
     k_lift(const NskParams p, const R* __restrict__ U, const R* __restrict__ Utr, R* __restrict__ Q,
-           R* __restrict__ FVtr, int* __restrict__ err) {
+           R* __restrict__ FVtr, int* __restrict__ err, const int blk_off = 0) {
   __shared__ __align__(16) R sm[lift_smem<R, D, NP, G>()];
   int eflag = 0;
-  lift_group<R, D, NP, G, 0, QF>(p, U, Utr, Q, FVtr, (long long)blockIdx.x * G, sm, eflag);
+  lift_group<R, D, NP, G, 0, QF>(p, U, Utr, Q, FVtr, (long long)(blockIdx.x + blk_off) * G, sm, eflag);
   if (eflag) atomicOr(err, eflag);
 }
 
@@ -1460,9 +1463,9 @@ __global__ void __launch_bounds__(G * Shape<D, NP>::NPE, (lift_min_blocks<R, G *
 template <typename R, int D, int NP>
 __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? 6 : 1)) k_face(const NskParams p, const R* __restrict__ Utr,
                                               const R* __restrict__ FVtr, R* __restrict__ Fstar,
-                                              int* __restrict__ err) {
+                                              int* __restrict__ err, const int blk_off = 0) {
   using S = Shape<D, NP>;
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  const int idx = (blockIdx.x + blk_off) * blockDim.x + threadIdx.x;
   int eflag = 0;
   if (idx < p.nfe) face_at<R, D, NP>(p, Utr, FVtr, Fstar, blockIdx.y, idx / S::NFN, idx % S::NFN, eflag);
   if (eflag) atomicOr(err, eflag);
@@ -1479,12 +1482,12 @@ __global__ void __launch_bounds__(G * Shape<D, NP>::NPE, (volume_min_blocks<R, G
     k_volume(const NskParams p, R* __restrict__ U, const R* __restrict__ Q, const R* __restrict__ Fstar,
              const R* __restrict__ Utr, const R* __restrict__ FVtr, R* __restrict__ K, R* __restrict__ Rout,
              const int mode, const R A, const R B, const double* __restrict__ dtp, const R dtv,
-             int* __restrict__ err, R* __restrict__ UtrNext) {
+             int* __restrict__ err, R* __restrict__ UtrNext, const int blk_off = 0) {
   __shared__ __align__(16) R sm[volume_smem<R, D, NP, G, FUSED>()];
   const R dt = dtp ? (R)*dtp : dtv;
   int eflag = 0;
-  volume_group<R, D, NP, G, FUSED>(p, U, Q, Fstar, Utr, FVtr, K, Rout, mode, A, B, dt, (long long)blockIdx.x * G,
-                                   sm, eflag, UtrNext);
+  volume_group<R, D, NP, G, FUSED>(p, U, Q, Fstar, Utr, FVtr, K, Rout, mode, A, B, dt,
+                                   (long long)(blockIdx.x + blk_off) * G, sm, eflag, UtrNext);
   if (eflag) atomicOr(err, eflag);
 }
 
@@ -1758,6 +1761,42 @@ int launch_stage_g(const NskParams& p, const NskBuffers& b, const NskLaunch& l, 
   }
   if (cudaGetLastError() != cudaSuccess) return NSK_ERR_CUDA;
   return nl;
+}
+
+// One part of a separate-face Runge-Kutta stage over the elements [e0, e0 + ne) (the host-state
+// step's slab launches): part 0 the prolongation, 1 the lifting (viscous form stored), 2 the
+// face pass over the faces (e, +k) of those elements, 3 the volume kernel with the update l
+// describes. The range must be whole blocks of every kernel: e0 and ne multiples of G and of the
+// 256 / nfn elements of a prolongation or face-pass block. Returns 1 (launches made),
+// NSK_ERR_ARG, or NSK_ERR_CUDA.
+template <typename R, int D, int NP, int G>
+int launch_stage_part(const NskParams& p, const NskBuffers& b, const NskLaunch& l, cudaStream_t s, int part,
+                      long long e0, long long ne) {
+  using S = Shape<D, NP>;
+  const long long f0 = e0 * S::NFN, nf = ne * S::NFN;
+  if (e0 < 0 || ne <= 0 || e0 + ne > p.E || e0 % G || ne % G || f0 % 256 || nf % 256) return NSK_ERR_ARG;
+  const unsigned fb = (unsigned)(nf / 256), eb = (unsigned)(ne / G);
+  const int foff = (int)(f0 / 256), eoff = (int)(e0 / G);
+  switch (part) {
+    case 0:
+      k_prolong<R, D, NP><<<dim3(fb, S::NF), 256, 0, s>>>(p, (const R*)b.U, (R*)b.Utr, foff);
+      break;
+    case 1:
+      k_lift<R, D, NP, G, true><<<eb, G * S::NPE, 0, s>>>(p, (const R*)b.U, (const R*)b.Utr, (R*)b.Q, (R*)b.FVtr,
+                                                           b.err, eoff);
+      break;
+    case 2:
+      k_face<R, D, NP><<<dim3(fb, D), 256, 0, s>>>(p, (const R*)b.Utr, (const R*)b.FVtr, (R*)b.Fstar, b.err, foff);
+      break;
+    case 3:
+      k_volume<R, D, NP, G, false><<<eb, G * S::NPE, 0, s>>>(
+          p, (R*)b.U, (const R*)b.Q, (const R*)b.Fstar, (const R*)b.Utr, (const R*)b.FVtr, (R*)b.K, (R*)l.Rout,
+          l.mode, (R)l.A, (R)l.B, l.dt_dev, (R)l.dt_val, b.err, (R*)l.utr_next, eoff);
+      break;
+    default:
+      return NSK_ERR_ARG;
+  }
+  return cudaGetLastError() == cudaSuccess ? 1 : NSK_ERR_CUDA;
 }
 
 // the lean schedule's two launches (a residual-free lifting stage, mode LIFT, takes the

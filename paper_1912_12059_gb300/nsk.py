@@ -60,6 +60,7 @@ SIGNATURES = {
     "nsk_lift": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "nsk_compute_dt": (C.c_int, [C.c_void_p, C.c_double, _dp]),
     "nsk_step": (C.c_int, [C.c_void_p, C.c_double, C.c_int]),
+    "nsk_step_host": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int]),
     "nsk_step_esdirk": (C.c_int, [C.c_void_p, C.c_double, C.c_int, C.c_double, C.c_double, C.c_int, C.c_int,
                                   C.c_int, C.POINTER(C.c_longlong)]),
     "nsk_diagnostics": (C.c_int, [C.c_void_p, _dp, _dp, _dp]),
@@ -362,6 +363,17 @@ class Solver:
 
     def step(self, dt, nsteps=1):
         _check(load_library().nsk_step(self.ctx, dt, nsteps), "nsk_step")
+
+    def step_host(self, U_in, dt, nsteps=1, out=None):
+        """nsk_step_host: the state from host memory (U_in: a float64 numpy array or CPU tensor,
+        pinned for the full copy rate), nsteps steps, the final state into out (default U_in)."""
+        out = U_in if out is None else out
+        pin, w_in = _buf(U_in, self.nvar * self.n_nodes, False)
+        pout, w_out = _buf(out, self.nvar * self.n_nodes, True)
+        if w_in != NSK_HOST or w_out != NSK_HOST:
+            raise ValueError("step_host takes host arrays")
+        _check(load_library().nsk_step_host(self.ctx, pin, pout, dt, nsteps), "nsk_step_host")
+        return out
 
     def step_esdirk(self, dt, nsteps=1, newton_tol=1e-10, krylov_tol=1e-3, krylov_dim=30, max_krylov=600,
                     block_precond=False):
