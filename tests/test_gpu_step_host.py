@@ -81,3 +81,25 @@ def test_rejects_bad_arguments(gpu):
     with pytest.raises(nsk.NskError):
         s.step_host(U0.copy(), dt, 0)
     s.close()
+
+
+def test_full_size_in_the_benchmark_configuration(gpu):
+    """The 3D head-on collision at 64^3, N = 3, FP64 with the separate face pass of 256 threads
+    (the benchmark's workload and schedule; slabs of 8 z planes): one step through
+    nsk_step_host equals the three calls bit for bit."""
+    import torch
+
+    import bench
+
+    wl = bench.workload_by_name("collision3d")
+    s = nsk.Solver(wl.dim, wl.nelem, wl.N, list(wl.lo[:wl.dim]), list(wl.hi[:wl.dim]), wl.node_type, nsk.NSK_FP64)
+    s.set_params(T=wl.T, kappa=wl.kappa, alpha=wl.alpha, beta=wl.beta, mu=wl.mu)
+    U0 = np.ascontiguousarray(wl.initial_state(s.node_coords()), dtype=np.float64)
+    s.set_state(U0)
+    s.set_schedule(256, 0)
+    dt = s.compute_dt(wl.cfl)
+    want = _three_calls(s, U0, dt, 1)
+    Uh = torch.from_numpy(U0.copy()).pin_memory()
+    s.step_host(Uh, dt, 1)
+    assert np.array_equal(Uh.numpy(), want)
+    s.close()
