@@ -48,8 +48,10 @@ def compulsory_bytes(d, fp_bytes):
 
 # DRAM bytes (read + write) per launch of a kernel at 64^3 elements, N = 3, from one ncu capture
 # at 40^3 elements of the same kernel source, scaled by the element count; None once the kernel
-# changed after the capture (then no traffic is claimed).
-MEASURED_TRAFFIC = {("k_volume", 8, 262144): 5.576e9, ("k_volume", 4, 262144): 2.484e9}
+# changed after the capture (then no traffic is claimed). FP64: k_volume (separate face pass,
+# 11,671 + 9,600 B per element); FP32: the line schedule's volume kernel, k_volume_line
+# (5.83 + 3.63 KB per element).
+MEASURED_TRAFFIC = {("k_volume", 8, 262144): 5.576e9, ("k_volume", 4, 262144): 2.480e9}
 TRAFFIC_SOURCE = "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch at 40^3 elements, scaled to 64^3"
 
 
