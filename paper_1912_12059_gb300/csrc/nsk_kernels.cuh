@@ -855,13 +855,16 @@ __device__ __forceinline__ void face_flux_vals(const NskParams& p, const R* UL, 
     return;
   }
   const R mL = comp1<D>(UL, k), mR = comp1<D>(UR, k);  // normal momenta
-  const R lam_l = fabs(mL * il) + sqrt_s(dl), lam_r = fabs(mR * ir) + sqrt_s(dr);
+  const R vl = mL * il, vr = mR * ir;                  // normal velocities
+  const R lam_l = fabs(vl) + sqrt_s(dl), lam_r = fabs(vr) + sqrt_s(dr);
   const R lam = lam_l > lam_r ? lam_l : lam_r;
   F[0] = mL + mR;
+  // m_k v_a summed over both sides: the normal component m_k v_k + p_alpha once, the tangential
+  // ones as v_k m_a (the direction k is a runtime value: each component selects between them)
+  const R fnn = fma(mL, vl, pl) + fma(mR, vr, pr);
 #pragma unroll
   for (int a = 0; a < D; ++a) {
-    const R ml = UL[1 + a] * il, mr = UR[1 + a] * ir;
-    const R sum = (a == k) ? fma(mL, ml, pl) + fma(mR, mr, pr) : fma(mL, ml, mR * mr);
+    const R sum = (a == k) ? fnn : fma(vl, UL[1 + a], vr * UR[1 + a]);
     F[1 + a] = sum - (VL[a] + VR[a]);
   }
   F[D + 1] = -(VL[D] + VR[D]);
