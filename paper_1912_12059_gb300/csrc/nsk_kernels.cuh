@@ -834,17 +834,24 @@ __device__ __forceinline__ void face_flux_vals(const NskParams& p, const R* UL, 
 #pragma unroll
     for (int v = 0; v < NV; ++v) uk[v] = left ? UL[v] : UR[v];
     const R ik = left ? il : ir, pk = left ? pl : pr;
-    const R mk = left ? mL : mR;
-    F[0] = mk;
+    const R mk = left ? mL : mR, vk = left ? ul : ur;  // vk = mk ik: the upwind normal velocity
+    // the direction k is a runtime value: the normal component is formed once and each component
+    // selects it, the tangential ones from the upwind velocities v_a = m_a ik (same products)
+    R va[D];
 #pragma unroll
-    for (int a = 0; a < D; ++a) F[1 + a] = (a == k) ? fma(mk, uk[1 + a] * ik, pk) : mk * (uk[1 + a] * ik);
+    for (int a = 0; a < D; ++a) va[a] = uk[1 + a] * ik;
+    F[0] = mk;
+    const R fnn = fma(mk, vk, pk);
+#pragma unroll
+    for (int a = 0; a < D; ++a) F[1 + a] = (a == k) ? fnn : mk * va[a];
     if (star) {
       const R SK = left ? SL : SR;
       const R coef = (left ? wl : wr) / (SK - Ss);  // rho of U*_K
       F[0] = fma(SK, coef - uk[0], F[0]);
+      const R usn = coef * Ss;
 #pragma unroll
       for (int a = 0; a < D; ++a) {
-        const R us = (a == k) ? coef * Ss : coef * (uk[1 + a] * ik);
+        const R us = (a == k) ? usn : coef * va[a];
         F[1 + a] = fma(SK, us - uk[1 + a], F[1 + a]);
       }
     }

@@ -165,11 +165,15 @@ __device__ __forceinline__ void face_at(const NskParams& p, const double* __rest
   eflag |= rho_flags(UL[0]) | rho_flags(UR[0]);
   const double pl = pressure_q(p, UL[0], ql), pr = pressure_q(p, UR[0], qr);
   double F[NV];
-  F[0] = 0.5 * (UL[1 + k] + UR[1 + k]);
+  // the normal momenta by selects over compile-time indices (the direction k is a runtime value),
+  // the normal velocities once, the normal momentum flux m_k v_k + p once
+  const double mL = comp1<D>(UL, k), mR = comp1<D>(UR, k);
+  const double vl = mL * il, vr = mR * ir;
+  const double fnn = fma(mL, vl, pl) + fma(mR, vr, pr);
+  F[0] = 0.5 * (mL + mR);
 #pragma unroll
   for (int a = 0; a < D; ++a) {
-    const double ml = UL[1 + a] * il, mr = UR[1 + a] * ir;
-    const double sum = (a == k) ? fma(UL[1 + k], ml, pl) + fma(UR[1 + k], mr, pr) : fma(UL[1 + k], ml, UR[1 + k] * mr);
+    const double sum = (a == k) ? fnn : fma(vl, UL[1 + a], vr * UR[1 + a]);
     F[1 + a] = fma(0.5, sum, -(0.5 * (vL[a * ps] + vR[a * ps])));
   }
   double* o = Fstar + (size_t)k * p.nfe + (eL * NFN + fn);
