@@ -131,11 +131,11 @@ def kernel_cost(kernel, d, n, fp_bytes, traces=0.0, sched=0):
         return fl, by
     if kernel == "k_face":
         eos = 18 if fp64 else 30                                     # both sides (FP32: + 1/rho)
-        per_fn = eos + 6 + 1 + 9 + 7 * (d - 1) + 1 + 3 * (nv - 1)    # lambda, 2 F* (LF), jump
+        per_fn = eos + 6 + 1 + 7 + 5 * (d - 1) + 1 + 3 * (nv - 1)    # lambda (its v_k reused), 2 F* (LF), jump
         return d * nfn * per_fn, fp_bytes * d * nfn * (2 * (nv + xp) + 2 * nw + nv)
     if kernel == "k_volume":
         eos = 10 if fp64 else 8
-        flux = d + 2 * d + d * (d - 1) + 2 * d * d                   # v_a, F^c, F^c - mu tau
+        flux = d + 2 * d + d * (d - 1) // 2 + 2 * d * d              # v_a, F^c (each pair k < a once), F^c - mu tau
         per_node = eos + flux + nv * d * (2 * n + 4) + 2 + (2 * d + 4) + 4 * nv  # stress read, not formed
         by = fp_bytes * (nv * npe + nvf * npe + 2 * d * nfn * nv + 2 * nv * npe + nv * npe)
         return (npe * per_node + traces * nf * nfn * (nv * 2 * n + trace_extra),

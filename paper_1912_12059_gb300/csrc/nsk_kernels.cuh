@@ -979,6 +979,15 @@ __device__ __forceinline__ void volume_node_fluxes(const NskParams& p, const R* 
     pa = Eos<R>::pa(p, u[0]);
   }
   const R mu = t.mu;
+  // the convective momentum flux m_k v_a + p_alpha delta_ka: symmetric, so each pair k < a is
+  // formed once as m_k v_a and serves (a, k) as well
+  R vel[D], off[D][D];
+#pragma unroll
+  for (int a = 0; a < D; ++a) vel[a] = u[1 + a] * inv;
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int j = i + 1; j < D; ++j) off[i][j] = u[1 + i] * vel[j];
 #pragma unroll
   for (int k = 0; k < D; ++k) {
     // node n sits at position i_k of line face_node(n, k) in direction k
@@ -986,7 +995,7 @@ __device__ __forceinline__ void volume_node_fluxes(const NskParams& p, const R* 
     f[0] = u[1 + k];
 #pragma unroll
     for (int a = 0; a < D; ++a) {
-      const R fc = (a == k) ? fma(u[1 + k], u[1 + a] * inv, pa) : u[1 + k] * (u[1 + a] * inv);
+      const R fc = (a == k) ? fma(u[1 + k], vel[k], pa) : (k < a ? off[k][a] : off[a][k]);
       f[(1 + a) * NPE] = fma(-mu, tau[k][a], fc);
     }
     f[(D + 1) * NPE] = gc[k];  // the c flux -(kappa/beta) grad c, its factor applied after the sum

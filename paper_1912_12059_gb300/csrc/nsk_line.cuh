@@ -332,13 +332,21 @@ __global__ void __launch_bounds__(G * 16)
       for (int k = 0; k < 3; ++k) gc[k][i] = f4_at(qv[c++], i);
       const R inv = R(1) / u[0][i];
       const R pa = Eos<R>::pa(p, u[0][i]);
+      // the symmetric convective momentum flux, each pair k < a once (as volume_node_fluxes)
+      R vel[3], off[3][3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) vel[a] = u[1 + a][i] * inv;
+#pragma unroll
+      for (int q = 0; q < 3; ++q)
+#pragma unroll
+        for (int r = q + 1; r < 3; ++r) off[q][r] = u[1 + q][i] * vel[r];
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
         R f[NV];
         f[0] = u[1 + k][i];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-          const R fc = (a == k) ? fmaf(u[1 + k][i], u[1 + a][i] * inv, pa) : u[1 + k][i] * (u[1 + a][i] * inv);
+          const R fc = (a == k) ? fmaf(u[1 + k][i], vel[k], pa) : (k < a ? off[k][a] : off[a][k]);
           f[1 + a] = fmaf(-mu, tau[k][a], fc);
         }
         f[4] = gc[k][i];

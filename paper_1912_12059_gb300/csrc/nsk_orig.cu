@@ -224,6 +224,14 @@ __device__ __forceinline__ void volume_group(const NskParams& p, double* __restr
     const double dd = 1.0 / (u[0] * (3.0 - u[0]));
     const double inv = (3.0 - u[0]) * dd;
     const double pr = pressure_q(p, u[0], u[0] * dd);
+    // the symmetric convective momentum flux, each pair k < a formed once
+    double vel[D], off[D][D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) vel[a] = u[1 + a] * inv;
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+      for (int j = i + 1; j < D; ++j) off[i][j] = u[1 + i] * vel[j];
 #pragma unroll
     for (int k = 0; k < D; ++k) {
       double* f = sf + ((le * D + k) * NV) * NPE + n;
@@ -232,7 +240,7 @@ __device__ __forceinline__ void volume_group(const NskParams& p, double* __restr
       visc_kort<D>(p, k, u[0], q, lap, fv);
 #pragma unroll
       for (int a = 0; a < D; ++a) {
-        const double fc = (a == k) ? fma(u[1 + k], u[1 + a] * inv, pr) : u[1 + k] * (u[1 + a] * inv);
+        const double fc = (a == k) ? fma(u[1 + k], vel[k], pr) : (k < a ? off[k][a] : off[a][k]);
         f[(1 + a) * NPE] = fc - fv[a];
       }
     }
