@@ -63,6 +63,11 @@ def test_error_strings_and_argument_validation(nsk_lib):
     assert nsk_lib.nsk_get_subcell(None, None, None) == nsk.NSK_ERR_ARG
     assert nsk_lib.nsk_subcell_switch(None) == nsk.NSK_ERR_ARG
     assert nsk_lib.nsk_step_esdirk(None, 1e-5, 1, 1e-10, 1e-3, 30, 600, 0, None) == nsk.NSK_ERR_ARG
+    # the host-state step validates its context, buffers, step and count before any copy
+    buf = (C.c_double * 4)()
+    assert nsk_lib.nsk_step_host(None, buf, buf, 1e-5, 1) == nsk.NSK_ERR_ARG
+    assert nsk_lib.nsk_step_host(None, None, buf, 1e-5, 1) == nsk.NSK_ERR_ARG
+    assert nsk_lib.nsk_step_host(None, buf, buf, float("nan"), 1) == nsk.NSK_ERR_ARG
     # the closure and batch calls in the forms the boundary documents (readings R30, R31)
     assert nsk_lib.nsk_set_closure(None, nsk.NSK_C_LEARNED, None, 10, 0.5) == nsk.NSK_ERR_ARG
     lat = (C.c_double * 4)()
